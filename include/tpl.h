@@ -1,0 +1,241 @@
+/*
+ * tpl.h -- C ABI of the GB300 (sm_103a) library for the differentiable
+ * dihedral-angle -> Cartesian-coordinate mapping of proteins and the LRMSD
+ * distance, after Derevyanko & Lamoureux, "TorchProteinLibrary: A
+ * computationally efficient, differentiable representation of protein
+ * structure" (2018).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every tensor pointer is DEVICE memory owned by the caller.  The library
+ *    allocates nothing: scratch space is the caller's `workspace`, sized by the
+ *    matching *_workspace_size() query.
+ *  - Every compute call is asynchronous on `stream` (a cudaStream_t; NULL is
+ *    the legacy default stream), performs no host synchronisation and no
+ *    allocation, and may be captured in a CUDA graph.
+ *  - Errors the host can see (bad sizes, NULL pointers, misalignment, short
+ *    workspace) are returned at once and nothing is launched.  Errors that
+ *    depend on device data (a residue code >= 20, a length outside [0, Lmax],
+ *    a chain with more atoms than Amax) set bits of a per-device status word
+ *    that tpl_get_status() reads and clears; outputs of the affected chain are
+ *    then unspecified but no access leaves the caller's buffers.
+ *  - Floating tensors are contiguous, row-major, 4-byte aligned; the hot-path
+ *    entry points require 16-byte aligned base pointers and Lmax, Amax, Nmax
+ *    multiples of 4 (TPL_ERR_MISALIGNED / TPL_ERR_BAD_SHAPE otherwise).
+ *  - Padding (residue >= length, atom >= num_atoms) is ignored on input and
+ *    written as 0 on output.
+ *
+ * Layouts
+ *  - backbone angles  [B][3][Lmax]  rows phi, psi, omega (radians)
+ *  - backbone coords  [B][3*Lmax][3] atoms N, CA, C of each residue (Angstrom)
+ *  - full-atom angles [B][7][Lmax]  rows phi, psi, omega, chi1, chi2, chi3, chi4
+ *  - sequence         [B][Lmax] uint8 residue codes 0..19 = ALA ARG ASN ASP CYS
+ *                     GLN GLU GLY HIS ILE LEU LYS MET PHE PRO SER THR TRP TYR VAL
+ *  - full-atom coords [B][Amax][3] heavy atoms, residue by residue, each residue
+ *                     N, CA, C, O then its side chain (tpl_residue_atom order)
+ *  - LRMSD clouds     [P][Nmax][3]
+ *
+ * Readings of the paper this library implements
+ *  - the first transform of a chain is the identity (R_0 = I; Section 3 gives
+ *    the identity for a residue index j < 0), so omega_0 is ignored and its
+ *    gradient is 0;
+ *  - omega entry j is the dihedral CA(j-1) C(j-1) N(j) CA(j): the transform
+ *    placing N of residue j (Section 3 itemization);
+ *  - R' (Section 2) is the 122.686 degree rotation about x that gives L
+ *    chirality at CA;
+ *  - side-chain rigid-group geometry (not printed in the paper) comes from an
+ *    authored table of ideal internal coordinates;
+ *  - the LRMSD gradient is the exact derivative of the stated LRMSD with
+ *    respect to the INPUT structure y: (y'_i - U x'_i) / (N LRMSD).
+ */
+#ifndef TPL_H
+#define TPL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int tpl_status;
+#define TPL_OK 0
+#define TPL_ERR_INVALID_ARG 1      /* NULL pointer, negative size, bad option value */
+#define TPL_ERR_BAD_SHAPE 2        /* Lmax / Amax / Nmax not a multiple of 4, or too large */
+#define TPL_ERR_MISALIGNED 3       /* a base pointer is not 16-byte aligned */
+#define TPL_ERR_WORKSPACE 4        /* workspace NULL or smaller than the size query */
+#define TPL_ERR_CUDA 5             /* a CUDA runtime call failed (see tpl_last_error) */
+#define TPL_ERR_NO_DEVICE 6        /* no usable CUDA device */
+
+/* Bits of the device status word (tpl_get_status). */
+#define TPL_STATUS_BAD_RESIDUE 0x1 /* a residue code >= 20 was read */
+#define TPL_STATUS_BAD_LENGTH 0x2  /* a length < 0 or > Lmax, or num_atoms outside [0, Nmax] */
+#define TPL_STATUS_TOO_MANY_ATOMS 0x4 /* a chain needs more than Amax atoms */
+#define TPL_STATUS_ZERO_LRMSD 0x8  /* an LRMSD below 1e-12 A: its gradient is set to 0 */
+
+typedef struct CUstream_st* tpl_stream; /* same type as cudaStream_t */
+
+#define TPL_BWD_AUTO 0
+#define TPL_BWD_RECOMPUTE 1   /* rebuild frames from the angles (fewest HBM bytes) */
+#define TPL_BWD_FROM_COORDS 2 /* read the forward's coordinates instead */
+
+#define TPL_SCHED_AUTO 0
+#define TPL_SCHED_LONGEST_FIRST 1 /* chains sorted by length, longest first */
+#define TPL_SCHED_BATCH_ORDER 2   /* chains in batch order */
+
+/* Launch options; a NULL pointer means all zeros (everything automatic). */
+typedef struct tpl_opts {
+    int bwd_mode;       /* TPL_BWD_* */
+    int threads;        /* threads per CTA of the chain kernels, 0 = tuned default */
+    int res_per_thread; /* backbone residues per thread (1, 2 or 4), 0 = tuned default */
+    int schedule;       /* TPL_SCHED_* */
+} tpl_opts;
+
+/* ------------------------------------------------------------------------ */
+/* Backbone model (paper Section 3)                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Bytes of workspace the backbone calls need for B chains (16-byte aligned). */
+size_t tpl_backbone_workspace_size(int B, int Lmax);
+
+/* Section 3: r_i = R_0 R_1 ... R_i 0 with atom 3j = N (R(omega_j, pi-2.1186,
+ * 1.330)), 3j+1 = CA (R(phi_j, pi-1.9391, 1.460)), 3j+2 = C (R(psi_j,
+ * pi-2.0610, 1.525)); R(alpha, theta, d) is the Section 3 matrix.
+ *   angles  [B][3][Lmax] in, lengths [B] int32 in (device),
+ *   coords  [B][3*Lmax][3] out.
+ * The composition is a parallel prefix scan over rigid transforms (FP32,
+ * carries re-orthonormalised). */
+tpl_status tpl_backbone_forward(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                float* coords, void* workspace, size_t workspace_bytes,
+                                const tpl_opts* opts, tpl_stream stream);
+
+/* Section 3, Eq. 2: grad_angles[b][r][j] = sum_i dL/dr_i . dr_i/dalpha, with
+ * dr_i/dalpha = M_{k-1} dR_k/dalpha M_k^{-1} r_i, evaluated as
+ * u_k . (sum_{i>=k} r_i x g_i - p_k x sum_{i>=k} g_i) by a reverse suffix scan
+ * (u_k, p_k: axis and origin of frame k).
+ *   grad_coords [B][3*Lmax][3] in, grad_angles [B][3][Lmax] out (0 at padding
+ *   and at omega_0).  `coords` is the forward's output; it is read only in
+ *   TPL_BWD_FROM_COORDS mode and may be NULL otherwise. */
+tpl_status tpl_backbone_backward(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                 const float* coords, const float* grad_coords,
+                                 float* grad_angles, void* workspace, size_t workspace_bytes,
+                                 const tpl_opts* opts, tpl_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Full-atom model (paper Section 2)                                         */
+/* ------------------------------------------------------------------------ */
+
+size_t tpl_fullatom_workspace_size(int B, int Lmax);
+
+/* Section 2: per residue M_1 = M_0 R_1(phi), side-chain frames M_1 R' R(chi_1)
+ * R(chi_2) ..., M_3 = M_1 R_3(psi), next M_0 = M_3 R_4(omega_{j+1}); every atom
+ * r = M_g r0 with r0 its standard-frame position in group g.
+ *   angles [B][7][Lmax], seq [B][Lmax] uint8, lengths [B] int32 in;
+ *   coords [B][Amax][3] out, num_atoms [B] int32 out. */
+tpl_status tpl_fullatom_forward(const float* angles, const uint8_t* seq, const int32_t* lengths,
+                                int B, int Lmax, int Amax, float* coords, int32_t* num_atoms,
+                                void* workspace, size_t workspace_bytes, const tpl_opts* opts,
+                                tpl_stream stream);
+
+/* Section 2, Eq. 1: dL/dalpha_i = sum_{k in children(i)} g_k . (F_i r_k),
+ * F_i = M_parent dR_i/dalpha M_i^{-1}, evaluated as u_i . (sum r_k x g_k -
+ * p_i x sum g_k) with a suffix scan over residues for phi/psi/omega and a
+ * suffix over the side-chain groups for chi.
+ *   grad_coords [B][Amax][3] in, grad_angles [B][7][Lmax] out (0 at padding,
+ *   unused chi rows and omega_0).  `coords` is read only in
+ *   TPL_BWD_FROM_COORDS mode and may be NULL otherwise. */
+tpl_status tpl_fullatom_backward(const float* angles, const uint8_t* seq, const int32_t* lengths,
+                                 int B, int Lmax, int Amax, const float* coords,
+                                 const float* grad_coords, float* grad_angles, void* workspace,
+                                 size_t workspace_bytes, const tpl_opts* opts, tpl_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* LRMSD (paper Section 4)                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Workspace for P pairs of at most Nmax atoms.  It carries the rotation U,
+ * the centroids and LRMSD from the forward to the backward: pass the same
+ * workspace, unmodified, to both. */
+size_t tpl_lrmsd_workspace_size(int P, int Nmax);
+
+/* Section 4: LRMSD(x = target, y = input) = min over rigid motions of
+ * sqrt(sum |x_i - M y_i|^2 / N) by the quaternion method: centroids, R =
+ * sum x' y'^T, the 4x4 matrix T(R), its largest eigenpair (lambda, q) solved
+ * in FP64, U(q); the value sum(|x'|^2 + |y'|^2) - 2 lambda is evaluated in the
+ * equivalent residual form sum |y'_i - U x'_i|^2 (FP64 final reduction).
+ *   input, target [P][Nmax][3], num_atoms [P] int32 in; lrmsd [P] float out. */
+tpl_status tpl_lrmsd_forward(const float* input, const float* target, const int32_t* num_atoms,
+                             int P, int Nmax, float* lrmsd, void* workspace,
+                             size_t workspace_bytes, tpl_stream stream);
+
+/* Section 4: grad_input_i = grad_lrmsd[p] (y'_i - U x'_i) / (N LRMSD); 0 when
+ * LRMSD < 1e-12 (status bit TPL_STATUS_ZERO_LRMSD).
+ *   grad_lrmsd [P] in, grad_input [P][Nmax][3] out; `workspace` as filled by
+ *   tpl_lrmsd_forward on the same inputs. */
+tpl_status tpl_lrmsd_backward(const float* grad_lrmsd, const float* input, const float* target,
+                              const int32_t* num_atoms, int P, int Nmax, float* grad_input,
+                              const void* workspace, size_t workspace_bytes, tpl_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Plain FP64 per-chain forms: one CTA per chain (or pair), serial composition */
+/* and serial suffix sums; the error reference and throughput comparator of   */
+/* the FP32 scan kernels.  Same layouts with double; no workspace.            */
+/* ------------------------------------------------------------------------ */
+
+tpl_status tpl_backbone_forward_ref64(const double* angles, const int32_t* lengths, int B,
+                                      int Lmax, double* coords, tpl_stream stream);
+/* `coords` is this form's forward output (frames are read from it). */
+tpl_status tpl_backbone_backward_ref64(const double* angles, const int32_t* lengths, int B,
+                                       int Lmax, const double* coords, const double* grad_coords,
+                                       double* grad_angles, tpl_stream stream);
+tpl_status tpl_fullatom_forward_ref64(const double* angles, const uint8_t* seq,
+                                      const int32_t* lengths, int B, int Lmax, int Amax,
+                                      double* coords, int32_t* num_atoms, tpl_stream stream);
+tpl_status tpl_fullatom_backward_ref64(const double* angles, const uint8_t* seq,
+                                       const int32_t* lengths, int B, int Lmax, int Amax,
+                                       const double* coords, const double* grad_coords,
+                                       double* grad_angles, tpl_stream stream);
+/* lrmsd_state [P][16] doubles (U row-major, centroids of x then y, LRMSD) is
+ * written by the forward and read by the backward. */
+tpl_status tpl_lrmsd_forward_ref64(const double* input, const double* target,
+                                   const int32_t* num_atoms, int P, int Nmax, double* lrmsd,
+                                   double* lrmsd_state, tpl_stream stream);
+tpl_status tpl_lrmsd_backward_ref64(const double* grad_lrmsd, const double* input,
+                                    const double* target, const int32_t* num_atoms, int P,
+                                    int Nmax, const double* lrmsd_state, double* grad_input,
+                                    tpl_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Host helpers: residue tables, sizes, status                               */
+/* ------------------------------------------------------------------------ */
+
+/* Residue `code` (0..19): three-letter name (4 bytes with NUL), heavy-atom
+ * count and number of free chi angles (Section 2: up to 7 angles per
+ * residue).  Host only, no CUDA call. */
+tpl_status tpl_residue_table(int code, char* three_letter, int* n_atoms, int* n_chi);
+
+/* Atom `idx` of residue `code`: PDB name (8 bytes with NUL), rigid group
+ * (0 = M_0 / N, 1 = M_1 / CA, 2 = M_3 / C and O, 3..6 = side-chain groups
+ * 1..4) and its standard-frame position r0 (3 floats).  Host only. */
+tpl_status tpl_residue_atom(int code, int idx, char* name, int* group, float* r0);
+
+/* Atoms of chain b for a host sequence: sum of per-residue counts (-1 on a bad
+ * code).  tpl_fullatom_max_atoms returns the maximum over the batch, i.e. the
+ * smallest valid Amax before rounding up to a multiple of 4.  Host only. */
+int tpl_fullatom_chain_atoms(const uint8_t* seq_host, int length);
+int tpl_fullatom_max_atoms(const uint8_t* seq_host, const int32_t* lengths_host, int B, int Lmax);
+
+/* Reads and clears the current device's status word (TPL_STATUS_* bits):
+ * enqueues the read on `stream` and waits for that stream.  Not capturable. */
+tpl_status tpl_get_status(tpl_stream stream, int* device_status);
+
+/* Message of the last error returned on this thread ("" if none). */
+const char* tpl_last_error(void);
+
+/* Library version, "major.minor.patch". */
+const char* tpl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPL_H */

@@ -1,0 +1,488 @@
+// C ABI of the library (include/tpl.h): argument checks, workspace layout,
+// scheduling (longest-first chain order) and dispatch to the kernels.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/tpl.h"
+#include "kernels.h"
+#include "tables.h"
+#include "tpl_common.cuh"
+
+namespace tpl {
+
+__device__ int g_status = 0;
+
+namespace {
+
+thread_local std::string t_last_error;
+
+tpl_status fail(tpl_status code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+tpl_status fail(tpl_status code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_last_error = buf;
+    return code;
+}
+
+tpl_status ok() {
+    t_last_error.clear();
+    return TPL_OK;
+}
+
+tpl_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(TPL_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ---------------------------------------------------------------------------
+// K8: longest-first order.  One CTA: histogram of lengths in 64 buckets
+// (longest bucket first), exclusive scan, scatter.  Order inside a bucket is
+// arbitrary; results do not depend on it (each chain is computed alone).
+// ---------------------------------------------------------------------------
+constexpr int kBuckets = 64;
+
+__global__ void __launch_bounds__(1024) build_order_kernel(const int32_t* __restrict__ lengths,
+                                                           int B, int Lmax,
+                                                           int32_t* __restrict__ order) {
+    __shared__ int hist[kBuckets];
+    if (threadIdx.x < kBuckets) hist[threadIdx.x] = 0;
+    __syncthreads();
+    auto key = [&](int b) {
+        int L = lengths[b];
+        L = L < 0 ? 0 : (L > Lmax ? Lmax : L);
+        const int bucket = (int)(((long long)L * kBuckets) / ((long long)Lmax + 1));
+        return kBuckets - 1 - bucket;
+    };
+    for (int b = threadIdx.x; b < B; b += blockDim.x) atomicAdd(&hist[key(b)], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int k = 0; k < kBuckets; ++k) {
+            const int c = hist[k];
+            hist[k] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < B; b += blockDim.x) order[atomicAdd(&hist[key(b)], 1)] = b;
+}
+
+int num_sms() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+    return n;
+}
+
+tpl_opts resolve(const tpl_opts* o) {
+    tpl_opts r;
+    memset(&r, 0, sizeof(r));
+    if (o) r = *o;
+    return r;
+}
+
+bool use_order(const tpl_opts& o, int B) {
+    if (o.schedule == TPL_SCHED_BATCH_ORDER) return false;
+    if (o.schedule == TPL_SCHED_LONGEST_FIRST) return true;
+    return B > num_sms();  // more than one wave of chains: longest first
+}
+
+tpl_status check_opts(const tpl_opts& o) {
+    if (o.bwd_mode < TPL_BWD_AUTO || o.bwd_mode > TPL_BWD_FROM_COORDS)
+        return fail(TPL_ERR_INVALID_ARG, "bwd_mode %d unknown", o.bwd_mode);
+    if (o.schedule < TPL_SCHED_AUTO || o.schedule > TPL_SCHED_BATCH_ORDER)
+        return fail(TPL_ERR_INVALID_ARG, "schedule %d unknown", o.schedule);
+    if (o.threads < 0 || o.res_per_thread < 0)
+        return fail(TPL_ERR_INVALID_ARG, "negative launch option");
+    return TPL_OK;
+}
+
+// Backbone defaults: 128 threads x 2 residues (tile 256 residues).
+LaunchCfg backbone_cfg(const tpl_opts& o) {
+    LaunchCfg c;
+    c.threads = o.threads ? o.threads : 128;
+    c.res_per_thread = o.res_per_thread ? o.res_per_thread : 2;
+    c.grid = 0;
+    return c;
+}
+
+LaunchCfg fullatom_cfg(const tpl_opts& o) {
+    LaunchCfg c;
+    c.threads = o.threads ? o.threads : 256;
+    c.res_per_thread = 1;
+    c.grid = 0;
+    return c;
+}
+
+tpl_status check_chain_args(int B, int Lmax, const void* const* ptrs, int nptr) {
+    if (B < 0 || Lmax < 0) return fail(TPL_ERR_INVALID_ARG, "B=%d Lmax=%d must be >= 0", B, Lmax);
+    if (Lmax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Lmax=%d must be a multiple of 4", Lmax);
+    if (B == 0) return TPL_OK;
+    for (int i = 0; i < nptr; ++i) {
+        if (!ptrs[i]) return fail(TPL_ERR_INVALID_ARG, "pointer argument %d is NULL", i);
+        if (!aligned16(ptrs[i])) return fail(TPL_ERR_MISALIGNED, "pointer argument %d not 16-byte aligned", i);
+    }
+    return TPL_OK;
+}
+
+size_t order_bytes(int B) { return align256((size_t)(B > 0 ? B : 1) * sizeof(int32_t)); }
+
+tpl_status check_ws(void* ws, size_t have, size_t need) {
+    if (need == 0) return TPL_OK;
+    if (!ws) return fail(TPL_ERR_WORKSPACE, "workspace is NULL (%zu bytes needed)", need);
+    if (!aligned16(ws)) return fail(TPL_ERR_MISALIGNED, "workspace not 16-byte aligned");
+    if (have < need) return fail(TPL_ERR_WORKSPACE, "workspace %zu bytes < %zu needed", have, need);
+    return TPL_OK;
+}
+
+tpl_status maybe_order(const tpl_opts& o, const int32_t* lengths, int B, int Lmax, void* ws,
+                       const int32_t** order, cudaStream_t s) {
+    *order = nullptr;
+    if (!use_order(o, B)) return TPL_OK;
+    int32_t* ord = static_cast<int32_t*>(ws);
+    cudaError_t e = launch_build_order(lengths, B, Lmax, ord, s);
+    if (e != cudaSuccess) return cuda_fail(e, "build_order");
+    *order = ord;
+    return TPL_OK;
+}
+
+}  // namespace
+
+cudaError_t launch_build_order(const int32_t* lengths, int B, int Lmax, int32_t* order,
+                               cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    build_order_kernel<<<1, 1024, 0, s>>>(lengths, B, Lmax, order);
+    return cudaGetLastError();
+}
+
+cudaError_t read_and_clear_status(cudaStream_t s, int* out) {
+    int zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyToSymbolAsync(g_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+}  // namespace tpl
+
+using namespace tpl;
+
+extern "C" {
+
+const char* tpl_version(void) { return "0.1.0"; }
+
+const char* tpl_last_error(void) { return t_last_error.c_str(); }
+
+size_t tpl_backbone_workspace_size(int B, int Lmax) {
+    (void)Lmax;
+    return order_bytes(B);
+}
+
+size_t tpl_fullatom_workspace_size(int B, int Lmax) {
+    (void)Lmax;
+    return order_bytes(B);
+}
+
+size_t tpl_lrmsd_workspace_size(int P, int Nmax) {
+    if (P <= 0 || Nmax < 0) return 256;
+    return lrmsd_ws_bytes(P, Nmax);
+}
+
+tpl_status tpl_backbone_forward(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                float* coords, void* workspace, size_t workspace_bytes,
+                                const tpl_opts* opts, tpl_stream stream) {
+    tpl_opts o = resolve(opts);
+    tpl_status st = check_opts(o);
+    if (st) return st;
+    const void* ptrs[3] = {angles, lengths, coords};
+    if ((st = check_chain_args(B, Lmax, ptrs, 3))) return st;
+    if (B == 0) return ok();
+    LaunchCfg cfg = backbone_cfg(o);
+    if (!backbone_cfg_supported(cfg.threads, cfg.res_per_thread) ||
+        (cfg.threads == 512 && cfg.res_per_thread == 4))
+        return fail(TPL_ERR_INVALID_ARG, "unsupported backbone launch %d x %d", cfg.threads, cfg.res_per_thread);
+    if ((st = check_ws(workspace, workspace_bytes, tpl_backbone_workspace_size(B, Lmax)))) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int32_t* order;
+    if ((st = maybe_order(o, lengths, B, Lmax, workspace, &order, s))) return st;
+    cudaError_t e = launch_backbone_forward(angles, lengths, order, B, Lmax, coords, cfg, s);
+    if (e != cudaSuccess) return cuda_fail(e, "backbone_forward");
+    return ok();
+}
+
+tpl_status tpl_backbone_backward(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                 const float* coords, const float* grad_coords, float* grad_angles,
+                                 void* workspace, size_t workspace_bytes, const tpl_opts* opts,
+                                 tpl_stream stream) {
+    tpl_opts o = resolve(opts);
+    tpl_status st = check_opts(o);
+    if (st) return st;
+    const bool from_coords = o.bwd_mode == TPL_BWD_FROM_COORDS;
+    const void* ptrs[5] = {angles, lengths, grad_coords, grad_angles, from_coords ? (const void*)coords : angles};
+    if ((st = check_chain_args(B, Lmax, ptrs, 5))) return st;
+    if (B == 0) return ok();
+    LaunchCfg cfg = backbone_cfg(o);
+    if (!backbone_cfg_supported(cfg.threads, cfg.res_per_thread) ||
+        (cfg.threads == 512 && cfg.res_per_thread == 4))
+        return fail(TPL_ERR_INVALID_ARG, "unsupported backbone launch %d x %d", cfg.threads, cfg.res_per_thread);
+    if (!from_coords && Lmax > kMaxTiles * cfg.threads * cfg.res_per_thread)
+        return fail(TPL_ERR_BAD_SHAPE, "Lmax=%d exceeds %d tiles of %d residues", Lmax, kMaxTiles,
+                    cfg.threads * cfg.res_per_thread);
+    if ((st = check_ws(workspace, workspace_bytes, tpl_backbone_workspace_size(B, Lmax)))) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int32_t* order;
+    if ((st = maybe_order(o, lengths, B, Lmax, workspace, &order, s))) return st;
+    cudaError_t e = launch_backbone_backward(angles, lengths, order, B, Lmax, coords, grad_coords,
+                                             grad_angles, from_coords, cfg, s);
+    if (e != cudaSuccess) return cuda_fail(e, "backbone_backward");
+    return ok();
+}
+
+tpl_status tpl_fullatom_forward(const float* angles, const uint8_t* seq, const int32_t* lengths,
+                                int B, int Lmax, int Amax, float* coords, int32_t* num_atoms,
+                                void* workspace, size_t workspace_bytes, const tpl_opts* opts,
+                                tpl_stream stream) {
+    tpl_opts o = resolve(opts);
+    tpl_status st = check_opts(o);
+    if (st) return st;
+    const void* ptrs[5] = {angles, seq, lengths, coords, num_atoms};
+    if ((st = check_chain_args(B, Lmax, ptrs, 5))) return st;
+    if (Amax < 0 || Amax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Amax=%d must be a multiple of 4", Amax);
+    if (B == 0) return ok();
+    LaunchCfg cfg = fullatom_cfg(o);
+    if (!fullatom_cfg_supported(cfg.threads))
+        return fail(TPL_ERR_INVALID_ARG, "unsupported full-atom launch %d threads", cfg.threads);
+    if ((st = check_ws(workspace, workspace_bytes, tpl_fullatom_workspace_size(B, Lmax)))) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int32_t* order;
+    if ((st = maybe_order(o, lengths, B, Lmax, workspace, &order, s))) return st;
+    cudaError_t e = launch_fullatom_forward(angles, seq, lengths, order, B, Lmax, Amax, coords,
+                                            num_atoms, cfg, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fullatom_forward");
+    return ok();
+}
+
+tpl_status tpl_fullatom_backward(const float* angles, const uint8_t* seq, const int32_t* lengths,
+                                 int B, int Lmax, int Amax, const float* coords,
+                                 const float* grad_coords, float* grad_angles, void* workspace,
+                                 size_t workspace_bytes, const tpl_opts* opts, tpl_stream stream) {
+    tpl_opts o = resolve(opts);
+    tpl_status st = check_opts(o);
+    if (st) return st;
+    if (o.bwd_mode == TPL_BWD_FROM_COORDS)
+        return fail(TPL_ERR_INVALID_ARG, "the full-atom backward recomputes its frames; "
+                                         "TPL_BWD_FROM_COORDS is not available");
+    (void)coords;
+    const void* ptrs[5] = {angles, seq, lengths, grad_coords, grad_angles};
+    if ((st = check_chain_args(B, Lmax, ptrs, 5))) return st;
+    if (Amax < 0 || Amax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Amax=%d must be a multiple of 4", Amax);
+    if (B == 0) return ok();
+    LaunchCfg cfg = fullatom_cfg(o);
+    if (!fullatom_cfg_supported(cfg.threads))
+        return fail(TPL_ERR_INVALID_ARG, "unsupported full-atom launch %d threads", cfg.threads);
+    if (Lmax > kMaxTiles * cfg.threads)
+        return fail(TPL_ERR_BAD_SHAPE, "Lmax=%d exceeds %d tiles of %d residues", Lmax, kMaxTiles, cfg.threads);
+    if ((st = check_ws(workspace, workspace_bytes, tpl_fullatom_workspace_size(B, Lmax)))) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int32_t* order;
+    if ((st = maybe_order(o, lengths, B, Lmax, workspace, &order, s))) return st;
+    cudaError_t e = launch_fullatom_backward(angles, seq, lengths, order, B, Lmax, Amax, nullptr,
+                                             grad_coords, grad_angles, false, cfg, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fullatom_backward");
+    return ok();
+}
+
+static tpl_status check_pair_args(int P, int Nmax, const void* const* ptrs, int nptr) {
+    if (P < 0 || Nmax < 0) return fail(TPL_ERR_INVALID_ARG, "P=%d Nmax=%d must be >= 0", P, Nmax);
+    if (Nmax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Nmax=%d must be a multiple of 4", Nmax);
+    if (P > 65535 * 64) return fail(TPL_ERR_BAD_SHAPE, "P=%d too large", P);
+    if (P == 0) return TPL_OK;
+    for (int i = 0; i < nptr; ++i) {
+        if (!ptrs[i]) return fail(TPL_ERR_INVALID_ARG, "pointer argument %d is NULL", i);
+        if (!aligned16(ptrs[i])) return fail(TPL_ERR_MISALIGNED, "pointer argument %d not 16-byte aligned", i);
+    }
+    return TPL_OK;
+}
+
+tpl_status tpl_lrmsd_forward(const float* input, const float* target, const int32_t* num_atoms,
+                             int P, int Nmax, float* lrmsd, void* workspace, size_t workspace_bytes,
+                             tpl_stream stream) {
+    const void* ptrs[4] = {input, target, num_atoms, lrmsd};
+    tpl_status st = check_pair_args(P, Nmax, ptrs, 4);
+    if (st) return st;
+    if (P == 0) return ok();
+    if (P > 65535) return fail(TPL_ERR_BAD_SHAPE, "P=%d exceeds 65535 pairs per call", P);
+    if ((st = check_ws(workspace, workspace_bytes, tpl_lrmsd_workspace_size(P, Nmax)))) return st;
+    cudaError_t e = launch_lrmsd_forward(input, target, num_atoms, P, Nmax, lrmsd, workspace,
+                                         reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "lrmsd_forward");
+    return ok();
+}
+
+tpl_status tpl_lrmsd_backward(const float* grad_lrmsd, const float* input, const float* target,
+                              const int32_t* num_atoms, int P, int Nmax, float* grad_input,
+                              const void* workspace, size_t workspace_bytes, tpl_stream stream) {
+    const void* ptrs[5] = {grad_lrmsd, input, target, num_atoms, grad_input};
+    tpl_status st = check_pair_args(P, Nmax, ptrs, 5);
+    if (st) return st;
+    if (P == 0) return ok();
+    if (P > 65535) return fail(TPL_ERR_BAD_SHAPE, "P=%d exceeds 65535 pairs per call", P);
+    if ((st = check_ws(const_cast<void*>(workspace), workspace_bytes, tpl_lrmsd_workspace_size(P, Nmax))))
+        return st;
+    cudaError_t e = launch_lrmsd_backward(grad_lrmsd, input, target, num_atoms, P, Nmax, grad_input,
+                                          workspace, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "lrmsd_backward");
+    return ok();
+}
+
+// --------------------------------------------------------------------------- FP64 forms
+static tpl_status check_ref_args(int B, int Lmax, const void* const* ptrs, int nptr) {
+    if (B < 0 || Lmax < 0) return fail(TPL_ERR_INVALID_ARG, "sizes must be >= 0");
+    if (B > 2147483647 / 2) return fail(TPL_ERR_BAD_SHAPE, "batch too large");
+    if (B == 0) return TPL_OK;
+    for (int i = 0; i < nptr; ++i)
+        if (!ptrs[i]) return fail(TPL_ERR_INVALID_ARG, "pointer argument %d is NULL", i);
+    return TPL_OK;
+}
+
+tpl_status tpl_backbone_forward_ref64(const double* angles, const int32_t* lengths, int B, int Lmax,
+                                      double* coords, tpl_stream stream) {
+    const void* ptrs[3] = {angles, lengths, coords};
+    tpl_status st = check_ref_args(B, Lmax, ptrs, 3);
+    if (st) return st;
+    cudaError_t e = launch_backbone_forward_ref64(angles, lengths, B, Lmax, coords,
+                                                  reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ok() : cuda_fail(e, "backbone_forward_ref64");
+}
+
+tpl_status tpl_backbone_backward_ref64(const double* angles, const int32_t* lengths, int B,
+                                       int Lmax, const double* coords, const double* grad_coords,
+                                       double* grad_angles, tpl_stream stream) {
+    const void* ptrs[4] = {lengths, coords, grad_coords, grad_angles};
+    tpl_status st = check_ref_args(B, Lmax, ptrs, 4);
+    if (st) return st;
+    cudaError_t e = launch_backbone_backward_ref64(angles, lengths, B, Lmax, coords, grad_coords,
+                                                   grad_angles, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ok() : cuda_fail(e, "backbone_backward_ref64");
+}
+
+tpl_status tpl_fullatom_forward_ref64(const double* angles, const uint8_t* seq,
+                                      const int32_t* lengths, int B, int Lmax, int Amax,
+                                      double* coords, int32_t* num_atoms, tpl_stream stream) {
+    const void* ptrs[5] = {angles, seq, lengths, coords, num_atoms};
+    tpl_status st = check_ref_args(B, Lmax, ptrs, 5);
+    if (st) return st;
+    if (Amax < 0) return fail(TPL_ERR_INVALID_ARG, "Amax must be >= 0");
+    cudaError_t e = launch_fullatom_forward_ref64(angles, seq, lengths, B, Lmax, Amax, coords,
+                                                  num_atoms, reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ok() : cuda_fail(e, "fullatom_forward_ref64");
+}
+
+tpl_status tpl_fullatom_backward_ref64(const double* angles, const uint8_t* seq,
+                                       const int32_t* lengths, int B, int Lmax, int Amax,
+                                       const double* coords, const double* grad_coords,
+                                       double* grad_angles, tpl_stream stream) {
+    const void* ptrs[5] = {seq, lengths, coords, grad_coords, grad_angles};
+    tpl_status st = check_ref_args(B, Lmax, ptrs, 5);
+    if (st) return st;
+    if (Amax < 0) return fail(TPL_ERR_INVALID_ARG, "Amax must be >= 0");
+    cudaError_t e = launch_fullatom_backward_ref64(angles, seq, lengths, B, Lmax, Amax, coords,
+                                                   grad_coords, grad_angles,
+                                                   reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ok() : cuda_fail(e, "fullatom_backward_ref64");
+}
+
+tpl_status tpl_lrmsd_forward_ref64(const double* input, const double* target,
+                                   const int32_t* num_atoms, int P, int Nmax, double* lrmsd,
+                                   double* lrmsd_state, tpl_stream stream) {
+    const void* ptrs[5] = {input, target, num_atoms, lrmsd, lrmsd_state};
+    tpl_status st = check_ref_args(P, Nmax, ptrs, 5);
+    if (st) return st;
+    cudaError_t e = launch_lrmsd_forward_ref64(input, target, num_atoms, P, Nmax, lrmsd, lrmsd_state,
+                                               reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ok() : cuda_fail(e, "lrmsd_forward_ref64");
+}
+
+tpl_status tpl_lrmsd_backward_ref64(const double* grad_lrmsd, const double* input,
+                                    const double* target, const int32_t* num_atoms, int P,
+                                    int Nmax, const double* lrmsd_state, double* grad_input,
+                                    tpl_stream stream) {
+    const void* ptrs[6] = {grad_lrmsd, input, target, num_atoms, lrmsd_state, grad_input};
+    tpl_status st = check_ref_args(P, Nmax, ptrs, 6);
+    if (st) return st;
+    cudaError_t e = launch_lrmsd_backward_ref64(grad_lrmsd, input, target, num_atoms, P, Nmax,
+                                                lrmsd_state, grad_input,
+                                                reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? ok() : cuda_fail(e, "lrmsd_backward_ref64");
+}
+
+// --------------------------------------------------------------------------- host helpers
+tpl_status tpl_residue_table(int code, char* three_letter, int* n_atoms, int* n_chi) {
+    if (code < 0 || code >= kNumTypes) return fail(TPL_ERR_INVALID_ARG, "residue code %d", code);
+    const FaTable& t = fa_table();
+    if (three_letter) {
+        memcpy(three_letter, residue_three(code), 3);
+        three_letter[3] = 0;
+    }
+    if (n_atoms) *n_atoms = t.n_atoms[code];
+    if (n_chi) *n_chi = t.n_chi[code];
+    return ok();
+}
+
+tpl_status tpl_residue_atom(int code, int idx, char* name, int* group, float* r0) {
+    if (code < 0 || code >= kNumTypes) return fail(TPL_ERR_INVALID_ARG, "residue code %d", code);
+    const FaTableD& d = fa_table_d();
+    if (idx < 0 || idx >= d.n_atoms[code]) return fail(TPL_ERR_INVALID_ARG, "atom index %d", idx);
+    if (name) {
+        strncpy(name, residue_atom_name(code, idx), 7);
+        name[7] = 0;
+    }
+    if (group) *group = d.group[code][idx];
+    if (r0)
+        for (int k = 0; k < 3; ++k) r0[k] = (float)d.r0[code][idx][k];
+    return ok();
+}
+
+int tpl_fullatom_chain_atoms(const uint8_t* seq_host, int length) {
+    if (!seq_host || length < 0) return -1;
+    const FaTable& t = fa_table();
+    int n = 0;
+    for (int j = 0; j < length; ++j) {
+        if (seq_host[j] >= kNumTypes) return -1;
+        n += t.n_atoms[seq_host[j]];
+    }
+    return n;
+}
+
+int tpl_fullatom_max_atoms(const uint8_t* seq_host, const int32_t* lengths_host, int B, int Lmax) {
+    if (B < 0 || Lmax < 0 || (B > 0 && (!seq_host || !lengths_host))) return -1;
+    int best = 0;
+    for (int b = 0; b < B; ++b) {
+        const int L = lengths_host[b];
+        if (L < 0 || L > Lmax) return -1;
+        const int n = tpl_fullatom_chain_atoms(seq_host + (size_t)b * Lmax, L);
+        if (n < 0) return -1;
+        if (n > best) best = n;
+    }
+    return best;
+}
+
+tpl_status tpl_get_status(tpl_stream stream, int* device_status) {
+    if (!device_status) return fail(TPL_ERR_INVALID_ARG, "device_status is NULL");
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return fail(TPL_ERR_NO_DEVICE, "no CUDA device");
+    cudaError_t e = read_and_clear_status(reinterpret_cast<cudaStream_t>(stream), device_status);
+    return e == cudaSuccess ? ok() : cuda_fail(e, "get_status");
+}
+
+}  // extern "C"

@@ -1,0 +1,539 @@
+// Backbone model of the paper (Section 3) on sm_103a.
+//
+// K1 bb_fwd_kernel: one CTA per chain (longest first).  Each thread owns K
+// consecutive residues (3K transforms: R(omega_j) R(phi_j) R(psi_j), R_0 = I),
+// composes them serially in registers, then the CTA runs an exclusive
+// parallel prefix scan over the per-thread rigid transforms.  A tile of
+// NT*K residues is finished before the next; the tile total becomes the carry
+// (re-orthonormalised).  Coordinates are staged in shared memory and written
+// with coalesced 16-byte stores.
+//
+// K2 bb_bwd_kernel: the adjoint of Eq. 2 as a reverse suffix scan.  With u_i
+// the x axis of M_i (bond i-1 -> i) and p_i = r_i,
+//   dL/dalpha_i = u_i . (sum_{k>=i} r_k x g_k - p_i x sum_{k>=i} g_k),
+// which equals the paper's sum_k g_k . (M_{i-1} dR_i M_i^{-1} r_k).  Frames
+// are recomputed from the angles (RECOMPUTE: tile carries from a first
+// left-to-right pass, then tiles right-to-left) or read from the forward's
+// coordinates (FROM_COORDS).
+#include "kernels.h"
+#include "tables.h"
+#include "tpl_common.cuh"
+
+namespace tpl {
+
+namespace {
+
+template <int K>
+__device__ __forceinline__ void load_row(const float* __restrict__ row, int j0, int Lmax,
+                                         float (&v)[K]) {
+    if (j0 < Lmax) {
+        if constexpr (K == 4) {
+            float4 q = __ldg(reinterpret_cast<const float4*>(row + j0));
+            v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else if constexpr (K == 2) {
+            float2 q = __ldg(reinterpret_cast<const float2*>(row + j0));
+            v[0] = q.x; v[1] = q.y;
+        } else {
+            v[0] = __ldg(row + j0);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = 0.f;
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void store_row(float* row, int j0, int Lmax, const float (&v)[K]) {
+    if (j0 >= Lmax) return;
+    if constexpr (K == 4) {
+        *reinterpret_cast<float4*>(row + j0) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (K == 2) {
+        *reinterpret_cast<float2*>(row + j0) = make_float2(v[0], v[1]);
+    } else {
+        row[j0] = v[0];
+    }
+}
+
+// 9K consecutive floats (K residues x 3 atoms x xyz) at p, 16/8/4-byte aligned for K = 4/2/1.
+template <int K>
+__device__ __forceinline__ void load_atoms(const float* __restrict__ p, bool ok, float (&v)[9 * K]) {
+    if (!ok) {
+#pragma unroll
+        for (int i = 0; i < 9 * K; ++i) v[i] = 0.f;
+        return;
+    }
+    if constexpr (K == 4) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            float4 q = __ldg(reinterpret_cast<const float4*>(p) + i);
+            v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
+        }
+    } else if constexpr (K == 2) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            float2 q = __ldg(reinterpret_cast<const float2*>(p) + i);
+            v[2 * i] = q.x; v[2 * i + 1] = q.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) v[i] = __ldg(p + i);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void store_stage(float* s, const float (&v)[9 * K]) {
+    if constexpr (K == 4) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            reinterpret_cast<float4*>(s)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    } else if constexpr (K == 2) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) reinterpret_cast<float2*>(s)[i] = make_float2(v[2 * i], v[2 * i + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) s[i] = v[i];
+    }
+}
+
+// Angle row read by the transform placing atom k of a residue: N <- omega (2),
+// CA <- phi (0), C <- psi (1).
+__device__ __forceinline__ constexpr int row_of(int k) { return k == 0 ? 2 : (k == 1 ? 0 : 1); }
+
+// ---------------------------------------------------------------------------
+// K1: forward
+// ---------------------------------------------------------------------------
+template <int NT, int K>
+__global__ void __launch_bounds__(NT) bb_fwd_kernel(const float* __restrict__ angles,
+                                                    const int32_t* __restrict__ lengths,
+                                                    const int32_t* __restrict__ order, int B,
+                                                    int Lmax, float* __restrict__ coords,
+                                                    BackboneConst bc) {
+    constexpr int NW = NT / 32;
+    constexpr int TILE = NT * K;
+    __shared__ RigidS s_rig[NW + 1];
+    __shared__ int s_cnt[NW + 1];
+    __shared__ __align__(16) float s_out[TILE * 9];
+
+    for (int item = blockIdx.x; item < B; item += gridDim.x) {
+        const int b = chain_at(order, item);
+        const int L = clamp_length(lengths, b, Lmax);
+        const float* ang = angles + (size_t)b * 3 * Lmax;
+        float* out = coords + (size_t)b * 9 * Lmax;
+        Rigid carry = rigid_identity();
+        for (int tile0 = 0; tile0 < L; tile0 += TILE) {
+            const int j0 = tile0 + threadIdx.x * K;
+            float a[3][K];
+            load_row<K>(ang, j0, Lmax, a[0]);
+            load_row<K>(ang + Lmax, j0, Lmax, a[1]);
+            load_row<K>(ang + 2 * Lmax, j0, Lmax, a[2]);
+            Rigid A = rigid_identity();
+            float3 pos[3 * K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int j = j0 + k;
+#pragma unroll
+                for (int at = 0; at < 3; ++at) {
+                    if (j < L && (j > 0 || at > 0)) {
+                        float s, c;
+                        sincosf(a[row_of(at)][k], &s, &c);
+                        rigid_mul_R(A, c, s, bc.ct[at], bc.st[at], bc.d[at]);
+                    }
+                    pos[3 * k + at] = A.t;
+                }
+            }
+            Rigid E, T;
+            int ce, ct;
+            block_scan_rigid_count<NT>(A, 0, carry, 0, s_rig, s_cnt, E, ce, T, ct);
+            float v[9 * K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const bool valid = j0 + k < L;
+#pragma unroll
+                for (int at = 0; at < 3; ++at) {
+                    float3 r = point_apply(E, pos[3 * k + at]);
+                    v[9 * k + 3 * at + 0] = valid ? r.x : 0.f;
+                    v[9 * k + 3 * at + 1] = valid ? r.y : 0.f;
+                    v[9 * k + 3 * at + 2] = valid ? r.z : 0.f;
+                }
+            }
+            store_stage<K>(s_out + threadIdx.x * 9 * K, v);
+            __syncthreads();
+            const int nres = min(TILE, Lmax - tile0);  // multiple of 4
+            float4* dst = reinterpret_cast<float4*>(out + 9 * (size_t)tile0);
+            const float4* src = reinterpret_cast<const float4*>(s_out);
+            for (int i = threadIdx.x; i < nres * 9 / 4; i += NT) dst[i] = src[i];
+            carry = T;
+            rigid_reortho(carry);
+            __syncthreads();
+        }
+        const int covered = min(Lmax, ((L + TILE - 1) / TILE) * TILE);
+        float4* o4 = reinterpret_cast<float4*>(out);
+        for (int i = covered * 9 / 4 + threadIdx.x; i < Lmax * 9 / 4; i += NT)
+            o4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// Local product of a thread's K residues (no positions), sin/cos cached.
+template <int K>
+__device__ __forceinline__ Rigid local_product(const float* ang, int j0, int L, int Lmax,
+                                               const BackboneConst& bc, float (&sn)[3 * K],
+                                               float (&cs)[3 * K]) {
+    float a[3][K];
+    load_row<K>(ang, j0, Lmax, a[0]);
+    load_row<K>(ang + Lmax, j0, Lmax, a[1]);
+    load_row<K>(ang + 2 * Lmax, j0, Lmax, a[2]);
+    Rigid A = rigid_identity();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int j = j0 + k;
+#pragma unroll
+        for (int at = 0; at < 3; ++at) {
+            sincosf(a[row_of(at)][k], &sn[3 * k + at], &cs[3 * k + at]);
+            if (j < L && (j > 0 || at > 0))
+                rigid_mul_R(A, cs[3 * k + at], sn[3 * k + at], bc.ct[at], bc.st[at], bc.d[at]);
+        }
+    }
+    return A;
+}
+
+// ---------------------------------------------------------------------------
+// K2: backward, RECOMPUTE mode
+// ---------------------------------------------------------------------------
+template <int NT, int K>
+__global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ angles,
+                                                    const int32_t* __restrict__ lengths,
+                                                    const int32_t* __restrict__ order, int B,
+                                                    int Lmax, const float* __restrict__ grad_coords,
+                                                    float* __restrict__ grad_angles,
+                                                    BackboneConst bc) {
+    constexpr int NW = NT / 32;
+    constexpr int TILE = NT * K;
+    __shared__ RigidS s_rig[NW + 1];
+    __shared__ int s_cnt[NW + 1];
+    __shared__ float s6[6 * (NW + 1)];
+    __shared__ RigidS s_carry[kMaxTiles];
+
+    for (int item = blockIdx.x; item < B; item += gridDim.x) {
+        const int b = chain_at(order, item);
+        const int L = clamp_length(lengths, b, Lmax);
+        const float* ang = angles + (size_t)b * 3 * Lmax;
+        const float* g_in = grad_coords + (size_t)b * 9 * Lmax;
+        float* ga = grad_angles + (size_t)b * 3 * Lmax;
+        const int ntiles = (L + TILE - 1) / TILE;
+
+        // Phase A: frame carried into each tile.
+        Rigid carry = rigid_identity();
+        if (threadIdx.x == 0) store_rigid(s_carry[0], carry);
+        for (int t = 0; t + 1 < ntiles; ++t) {
+            float sn[3 * K], cs[3 * K];
+            Rigid A = local_product<K>(ang, t * TILE + threadIdx.x * K, L, Lmax, bc, sn, cs);
+            Rigid E, T;
+            int ce, ct;
+            block_scan_rigid_count<NT>(A, 0, carry, 0, s_rig, s_cnt, E, ce, T, ct);
+            carry = T;
+            rigid_reortho(carry);
+            if (threadIdx.x == 0) store_rigid(s_carry[t + 1], carry);
+        }
+        __syncthreads();
+
+        // Phase B: tiles right to left with the suffix carry.
+        Sum6 sfx = sum6_zero();
+        for (int t = ntiles - 1; t >= 0; --t) {
+            const int j0 = t * TILE + threadIdx.x * K;
+            carry = load_rigid(s_carry[t]);
+            float sn[3 * K], cs[3 * K];
+            Rigid A = local_product<K>(ang, j0, L, Lmax, bc, sn, cs);
+            Rigid E, T;
+            int ce, ct;
+            block_scan_rigid_count<NT>(A, 0, carry, 0, s_rig, s_cnt, E, ce, T, ct);
+            float g[9 * K];
+            load_atoms<K>(g_in + 9 * (size_t)j0, j0 < Lmax, g);
+
+            // pass 1: per-thread totals of (r x g, g)
+            Sum6 own = sum6_zero();
+            Rigid M = E;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int j = j0 + k;
+                if (j < L) {
+#pragma unroll
+                    for (int at = 0; at < 3; ++at) {
+                        if (j > 0 || at > 0)
+                            rigid_mul_R(M, cs[3 * k + at], sn[3 * k + at], bc.ct[at], bc.st[at], bc.d[at]);
+                        float3 gi = make_float3(g[9 * k + 3 * at], g[9 * k + 3 * at + 1], g[9 * k + 3 * at + 2]);
+                        own.c = f3_add(own.c, f3_cross(M.t, gi));
+                        own.g = f3_add(own.g, gi);
+                    }
+                }
+            }
+            Sum6 after, total;
+            block_suffix_sum6<NT>(own, sfx, s6, after, total);
+
+            // pass 2: gradients, atoms ascending with S = sum over atoms >= current
+            Sum6 S = sum6_add(after, own);
+            M = E;
+            float gr[3][K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int j = j0 + k;
+#pragma unroll
+                for (int at = 0; at < 3; ++at) {
+                    float val = 0.f;
+                    if (j < L) {
+                        const bool has_angle = (j > 0 || at > 0);
+                        if (has_angle)
+                            rigid_mul_R(M, cs[3 * k + at], sn[3 * k + at], bc.ct[at], bc.st[at], bc.d[at]);
+                        float3 gi = make_float3(g[9 * k + 3 * at], g[9 * k + 3 * at + 1], g[9 * k + 3 * at + 2]);
+                        if (has_angle) val = f3_dot(M.c0, f3_sub(S.c, f3_cross(M.t, S.g)));
+                        S.c = f3_sub(S.c, f3_cross(M.t, gi));
+                        S.g = f3_sub(S.g, gi);
+                    }
+                    gr[row_of(at)][k] = val;
+                }
+            }
+            store_row<K>(ga, j0, Lmax, gr[0]);
+            store_row<K>(ga + Lmax, j0, Lmax, gr[1]);
+            store_row<K>(ga + 2 * Lmax, j0, Lmax, gr[2]);
+            sfx = total;
+        }
+        const int covered = min(Lmax, ntiles * TILE);
+        for (int i = covered + threadIdx.x; i < Lmax; i += NT) {
+            ga[i] = 0.f;
+            ga[Lmax + i] = 0.f;
+            ga[2 * Lmax + i] = 0.f;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K2': backward, FROM_COORDS mode: u_i = unit(r_i - r_{i-1}), p_i = r_i.
+// ---------------------------------------------------------------------------
+template <int NT, int K>
+__global__ void __launch_bounds__(NT) bb_bwd_coords_kernel(const int32_t* __restrict__ lengths,
+                                                           const int32_t* __restrict__ order, int B,
+                                                           int Lmax, const float* __restrict__ coords,
+                                                           const float* __restrict__ grad_coords,
+                                                           float* __restrict__ grad_angles) {
+    constexpr int NW = NT / 32;
+    constexpr int TILE = NT * K;
+    __shared__ float s6[6 * (NW + 1)];
+
+    for (int item = blockIdx.x; item < B; item += gridDim.x) {
+        const int b = chain_at(order, item);
+        const int L = clamp_length(lengths, b, Lmax);
+        const float* r_in = coords + (size_t)b * 9 * Lmax;
+        const float* g_in = grad_coords + (size_t)b * 9 * Lmax;
+        float* ga = grad_angles + (size_t)b * 3 * Lmax;
+        const int ntiles = (L + TILE - 1) / TILE;
+        Sum6 sfx = sum6_zero();
+        for (int t = ntiles - 1; t >= 0; --t) {
+            const int j0 = t * TILE + threadIdx.x * K;
+            float g[9 * K], r[9 * K];
+            load_atoms<K>(g_in + 9 * (size_t)j0, j0 < Lmax, g);
+            load_atoms<K>(r_in + 9 * (size_t)j0, j0 < Lmax, r);
+            float3 prev = make_float3(0.f, 0.f, 0.f);
+            if (j0 > 0 && j0 < Lmax) prev = make_float3(r_in[9 * j0 - 3], r_in[9 * j0 - 2], r_in[9 * j0 - 1]);
+            Sum6 own = sum6_zero();
+#pragma unroll
+            for (int q = 0; q < 3 * K; ++q) {
+                if (j0 + q / 3 < L) {
+                    float3 ri = make_float3(r[3 * q], r[3 * q + 1], r[3 * q + 2]);
+                    float3 gi = make_float3(g[3 * q], g[3 * q + 1], g[3 * q + 2]);
+                    own.c = f3_add(own.c, f3_cross(ri, gi));
+                    own.g = f3_add(own.g, gi);
+                }
+            }
+            Sum6 after, total;
+            block_suffix_sum6<NT>(own, sfx, s6, after, total);
+            Sum6 S = sum6_add(after, own);
+            float gr[3][K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int j = j0 + k;
+#pragma unroll
+                for (int at = 0; at < 3; ++at) {
+                    const int q = 3 * k + at;
+                    float val = 0.f;
+                    float3 ri = make_float3(r[3 * q], r[3 * q + 1], r[3 * q + 2]);
+                    if (j < L) {
+                        float3 gi = make_float3(g[3 * q], g[3 * q + 1], g[3 * q + 2]);
+                        if (j > 0 || at > 0) {
+                            float3 u = f3_sub(ri, prev);
+                            u = f3_scale(rsqrtf(f3_dot(u, u)), u);
+                            val = f3_dot(u, f3_sub(S.c, f3_cross(ri, S.g)));
+                        }
+                        S.c = f3_sub(S.c, f3_cross(ri, gi));
+                        S.g = f3_sub(S.g, gi);
+                    }
+                    prev = ri;
+                    gr[row_of(at)][k] = val;
+                }
+            }
+            store_row<K>(ga, j0, Lmax, gr[0]);
+            store_row<K>(ga + Lmax, j0, Lmax, gr[1]);
+            store_row<K>(ga + 2 * Lmax, j0, Lmax, gr[2]);
+            sfx = total;
+        }
+        const int covered = min(Lmax, ntiles * TILE);
+        for (int i = covered + threadIdx.x; i < Lmax; i += NT) {
+            ga[i] = 0.f;
+            ga[Lmax + i] = 0.f;
+            ga[2 * Lmax + i] = 0.f;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K7: plain FP64 per-chain forms (one CTA per chain, thread 0 serial).
+// ---------------------------------------------------------------------------
+__global__ void bb_fwd_ref64_kernel(const double* __restrict__ angles,
+                                    const int32_t* __restrict__ lengths, int B, int Lmax,
+                                    double* __restrict__ coords, BackboneConstD bc) {
+    const int b = blockIdx.x;
+    const int L = clamp_length(lengths, b, Lmax);
+    double* out = coords + (size_t)b * 9 * Lmax;
+    for (int i = 9 * L + threadIdx.x; i < 9 * Lmax; i += blockDim.x) out[i] = 0.0;
+    if (threadIdx.x != 0) return;
+    const double* ang = angles + (size_t)b * 3 * Lmax;
+    // M = [Q | t] as a dense 3x4, M <- M R with R the Section 3 matrix
+    double M[12] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0};
+    for (int j = 0; j < L; ++j)
+        for (int at = 0; at < 3; ++at) {
+            const int i = 3 * j + at;
+            if (i > 0) {
+                double sa, ca;
+                sincos(ang[row_of(at) * Lmax + j], &sa, &ca);
+                const double ct = bc.ct[at], st = bc.st[at], d = bc.d[at];
+                const double R[12] = {ct, sa * st, ca * st, d * ct, 0.0, ca, -sa, 0.0,
+                                      -st, sa * ct, ca * ct, -d * st};
+                double N[12];
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 4; ++c) {
+                        double s = (c == 3) ? M[4 * r + 3] : 0.0;
+                        for (int k = 0; k < 3; ++k) s += M[4 * r + k] * R[4 * k + c];
+                        N[4 * r + c] = s;
+                    }
+                for (int k = 0; k < 12; ++k) M[k] = N[k];
+            }
+            out[3 * i + 0] = M[3];
+            out[3 * i + 1] = M[7];
+            out[3 * i + 2] = M[11];
+        }
+}
+
+__global__ void bb_bwd_ref64_kernel(const int32_t* __restrict__ lengths, int B, int Lmax,
+                                    const double* __restrict__ coords,
+                                    const double* __restrict__ grad_coords,
+                                    double* __restrict__ grad_angles) {
+    const int b = blockIdx.x;
+    const int L = clamp_length(lengths, b, Lmax);
+    double* ga = grad_angles + (size_t)b * 3 * Lmax;
+    for (int i = L + threadIdx.x; i < Lmax; i += blockDim.x) {
+        ga[i] = 0.0;
+        ga[Lmax + i] = 0.0;
+        ga[2 * Lmax + i] = 0.0;
+    }
+    if (threadIdx.x != 0 || L == 0) return;
+    const double* r = coords + (size_t)b * 9 * Lmax;
+    const double* g = grad_coords + (size_t)b * 9 * Lmax;
+    double Sc[3] = {0, 0, 0}, Sg[3] = {0, 0, 0};
+    for (int i = 3 * L - 1; i >= 1; --i) {
+        const double* ri = r + 3 * i;
+        const double* gi = g + 3 * i;
+        Sc[0] += ri[1] * gi[2] - ri[2] * gi[1];
+        Sc[1] += ri[2] * gi[0] - ri[0] * gi[2];
+        Sc[2] += ri[0] * gi[1] - ri[1] * gi[0];
+        Sg[0] += gi[0]; Sg[1] += gi[1]; Sg[2] += gi[2];
+        double u[3] = {ri[0] - ri[-3], ri[1] - ri[-2], ri[2] - ri[-1]};
+        const double n = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        u[0] /= n; u[1] /= n; u[2] /= n;
+        const double w0 = Sc[0] - (ri[1] * Sg[2] - ri[2] * Sg[1]);
+        const double w1 = Sc[1] - (ri[2] * Sg[0] - ri[0] * Sg[2]);
+        const double w2 = Sc[2] - (ri[0] * Sg[1] - ri[1] * Sg[0]);
+        ga[row_of(i % 3) * Lmax + i / 3] = u[0] * w0 + u[1] * w1 + u[2] * w2;
+    }
+    ga[2 * Lmax + 0] = 0.0;  // omega_0: R_0 = I carries no angle
+}
+
+template <int NT, int K>
+cudaError_t fwd_t(const float* angles, const int32_t* lengths, const int32_t* order, int B,
+                  int Lmax, float* coords, int grid, cudaStream_t s) {
+    bb_fwd_kernel<NT, K><<<grid, NT, 0, s>>>(angles, lengths, order, B, Lmax, coords,
+                                             backbone_const());
+    return cudaGetLastError();
+}
+
+template <int NT, int K>
+cudaError_t bwd_t(const float* angles, const int32_t* lengths, const int32_t* order, int B,
+                  int Lmax, const float* coords, const float* grad_coords, float* grad_angles,
+                  bool from_coords, int grid, cudaStream_t s) {
+    if (from_coords)
+        bb_bwd_coords_kernel<NT, K><<<grid, NT, 0, s>>>(lengths, order, B, Lmax, coords,
+                                                        grad_coords, grad_angles);
+    else
+        bb_bwd_kernel<NT, K><<<grid, NT, 0, s>>>(angles, lengths, order, B, Lmax, grad_coords,
+                                                 grad_angles, backbone_const());
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool backbone_cfg_supported(int threads, int k) {
+    return (threads == 64 || threads == 128 || threads == 256 || threads == 512) &&
+           (k == 1 || k == 2 || k == 4);
+}
+
+#define TPL_BB_DISPATCH(FN, ...)                                              \
+    switch (cfg.threads * 8 + cfg.res_per_thread) {                           \
+        case 64 * 8 + 1: return FN<64, 1>(__VA_ARGS__);                       \
+        case 64 * 8 + 2: return FN<64, 2>(__VA_ARGS__);                       \
+        case 64 * 8 + 4: return FN<64, 4>(__VA_ARGS__);                       \
+        case 128 * 8 + 1: return FN<128, 1>(__VA_ARGS__);                     \
+        case 128 * 8 + 2: return FN<128, 2>(__VA_ARGS__);                     \
+        case 128 * 8 + 4: return FN<128, 4>(__VA_ARGS__);                     \
+        case 256 * 8 + 1: return FN<256, 1>(__VA_ARGS__);                     \
+        case 256 * 8 + 2: return FN<256, 2>(__VA_ARGS__);                     \
+        case 256 * 8 + 4: return FN<256, 4>(__VA_ARGS__);                     \
+        case 512 * 8 + 1: return FN<512, 1>(__VA_ARGS__);                     \
+        case 512 * 8 + 2: return FN<512, 2>(__VA_ARGS__);                     \
+        default: return cudaErrorInvalidValue;                                \
+    }
+
+cudaError_t launch_backbone_forward(const float* angles, const int32_t* lengths,
+                                    const int32_t* order, int B, int Lmax, float* coords,
+                                    LaunchCfg cfg, cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    const int grid = cfg.grid > 0 ? cfg.grid : B;
+    TPL_BB_DISPATCH(fwd_t, angles, lengths, order, B, Lmax, coords, grid, s)
+}
+
+cudaError_t launch_backbone_backward(const float* angles, const int32_t* lengths,
+                                     const int32_t* order, int B, int Lmax, const float* coords,
+                                     const float* grad_coords, float* grad_angles,
+                                     bool from_coords, LaunchCfg cfg, cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    const int grid = cfg.grid > 0 ? cfg.grid : B;
+    TPL_BB_DISPATCH(bwd_t, angles, lengths, order, B, Lmax, coords, grad_coords, grad_angles,
+                    from_coords, grid, s)
+}
+
+cudaError_t launch_backbone_forward_ref64(const double* angles, const int32_t* lengths, int B,
+                                          int Lmax, double* coords, cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    bb_fwd_ref64_kernel<<<B, 128, 0, s>>>(angles, lengths, B, Lmax, coords, backbone_const_d());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backbone_backward_ref64(const double* angles, const int32_t* lengths, int B,
+                                           int Lmax, const double* coords,
+                                           const double* grad_coords, double* grad_angles,
+                                           cudaStream_t s) {
+    (void)angles;
+    if (B == 0) return cudaSuccess;
+    bb_bwd_ref64_kernel<<<B, 128, 0, s>>>(lengths, B, Lmax, coords, grad_coords, grad_angles);
+    return cudaGetLastError();
+}
+
+}  // namespace tpl

@@ -1,0 +1,599 @@
+// Full-atom model of the paper (Section 2) on sm_103a.
+//
+// K3 fa_fwd_kernel: one CTA per chain (longest first), one residue per
+// thread.  The residue-to-residue transform T_j = R_1(phi_j) R_3(psi_j)
+// R_4(omega_{j+1}) is scanned across the CTA (exclusive prefix = M_0 of
+// residue j, the frame of its N), together with an exclusive scan of the
+// per-residue atom counts (the residue's first output atom).  Each thread then
+// builds M_1, M_3 and the side-chain frames M_1 R' R(chi_1) R(chi_2) ... and
+// places its atoms r = M_g r0 into a shared-memory tile that the CTA writes
+// out with coalesced stores.  The residue tables live in shared memory.
+//
+// K4 fa_bwd_kernel: Eq. 1 as suffix sums.  For a frame with x axis u and
+// origin p, dL/dalpha = u . sum_{k downstream} (r_k - p) x g_k.  chi_k
+// gradients are local to the residue (suffix over its side-chain groups);
+// phi, psi and omega add the sum over all later residues, a reverse
+// suffix scan of (sum r x g, sum g) across the CTA.  Frames are recomputed
+// from the angles; long chains use tile carries from a first pass.
+#include "kernels.h"
+#include "tables.h"
+#include "tpl_common.cuh"
+
+namespace tpl {
+
+namespace {
+
+__device__ __forceinline__ void copy_table(FaTable& dst, const FaTable& src) {
+    const int n = sizeof(FaTable) / 4;
+    const int* s = reinterpret_cast<const int*>(&src);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = s[i];
+}
+
+__device__ __forceinline__ int residue_type(const uint8_t* __restrict__ sq, int j, bool valid) {
+    if (!valid) return kGlyCode;
+    int t = sq[j];
+    if (t >= kNumTypes) {
+        flag_status(TPL_STATUS_BAD_RESIDUE);
+        t = kGlyCode;
+    }
+    return t;
+}
+
+// Residue transform T_j = R(phi) R(psi) R(omega_{j+1}) (the last residue of a
+// chain has no R_4).  Returns the sin/cos of phi and psi for reuse.
+__device__ __forceinline__ Rigid residue_transform(const FaTable& tab, const float* ang, int Lmax,
+                                                   int j, int L, float& sp, float& cp, float& ss,
+                                                   float& cs) {
+    Rigid A = rigid_identity();
+    if (j >= L) return A;
+    sincosf(ang[j], &sp, &cp);
+    sincosf(ang[Lmax + j], &ss, &cs);
+    A = rigid_R(cp, sp, tab.bb.ct[1], tab.bb.st[1], tab.bb.d[1]);
+    rigid_mul_R(A, cs, ss, tab.bb.ct[2], tab.bb.st[2], tab.bb.d[2]);
+    if (j + 1 < L) {
+        float so, co;
+        sincosf(ang[2 * Lmax + j + 1], &so, &co);
+        rigid_mul_R(A, co, so, tab.bb.ct[0], tab.bb.st[0], tab.bb.d[0]);
+    }
+    return A;
+}
+
+__device__ __forceinline__ void stage_atom(float* stage, int slot, float3 r) {
+    stage[3 * slot + 0] = r.x;
+    stage[3 * slot + 1] = r.y;
+    stage[3 * slot + 2] = r.z;
+}
+
+// ---------------------------------------------------------------------------
+// K3: forward
+// ---------------------------------------------------------------------------
+template <int NT>
+__global__ void __launch_bounds__(NT) fa_fwd_kernel(const float* __restrict__ angles,
+                                                    const uint8_t* __restrict__ seq,
+                                                    const int32_t* __restrict__ lengths,
+                                                    const int32_t* __restrict__ order, int B,
+                                                    int Lmax, int Amax, float* __restrict__ coords,
+                                                    int32_t* __restrict__ num_atoms,
+                                                    const __grid_constant__ FaTable tab) {
+    constexpr int NW = NT / 32;
+    __shared__ FaTable s_tab;
+    __shared__ RigidS s_rig[NW + 1];
+    __shared__ int s_cnt[NW + 1];
+    extern __shared__ float4 s_dyn[];
+    float* stage = reinterpret_cast<float*>(s_dyn);  // NT * kMaxAtoms * 3 floats
+
+    copy_table(s_tab, tab);
+    __syncthreads();
+
+    for (int item = blockIdx.x; item < B; item += gridDim.x) {
+        const int b = chain_at(order, item);
+        const int L = clamp_length(lengths, b, Lmax);
+        const float* ang = angles + (size_t)b * 7 * Lmax;
+        const uint8_t* sq = seq + (size_t)b * Lmax;
+        float* out = coords + (size_t)b * Amax * 3;
+        Rigid carry = rigid_identity();
+        int acarry = 0;
+        for (int tile0 = 0; tile0 < L; tile0 += NT) {
+            const int j = tile0 + threadIdx.x;
+            const bool valid = j < L;
+            const int type = residue_type(sq, j, valid);
+            const int cnt = valid ? s_tab.n_atoms[type] : 0;
+            float sp = 0.f, cp = 1.f, ss = 0.f, cs = 1.f;
+            Rigid A = residue_transform(s_tab, ang, Lmax, j, L, sp, cp, ss, cs);
+            Rigid E, T;
+            int a0, atot;
+            block_scan_rigid_count<NT>(A, cnt, carry, acarry, s_rig, s_cnt, E, a0, T, atot);
+            const int base = a0 - acarry;  // slot of this residue's first atom in the tile
+            if (valid) {
+                stage_atom(stage, base + 0, E.t);  // N = M_0 0
+                Rigid M1 = E;
+                rigid_mul_R(M1, cp, sp, s_tab.bb.ct[1], s_tab.bb.st[1], s_tab.bb.d[1]);
+                stage_atom(stage, base + 1, M1.t);  // CA = M_1 0
+                Rigid M3 = M1;
+                rigid_mul_R(M3, cs, ss, s_tab.bb.ct[2], s_tab.bb.st[2], s_tab.bb.d[2]);
+                stage_atom(stage, base + 2, M3.t);  // C = M_3 0
+                const float4 o = s_tab.o_r0;
+                stage_atom(stage, base + 3, point_apply(M3, make_float3(o.x, o.y, o.z)));
+                Rigid S = M1;
+                rigid_mul_Rx(S, s_tab.rp_c, s_tab.rp_s);  // M_1 R'
+                const int ng = s_tab.n_groups[type], nchi = s_tab.n_chi[type];
+                int e = 0;
+                for (int k = 0; k < ng; ++k) {
+                    float sc, cc;
+                    if (k < nchi) {
+                        sincosf(ang[(3 + k) * Lmax + j], &sc, &cc);
+                    } else {
+                        cc = s_tab.fixchi[type][k].x;
+                        sc = s_tab.fixchi[type][k].y;
+                    }
+                    const float4 gk = s_tab.grp[type][k];
+                    rigid_mul_R(S, cc, sc, gk.x, gk.y, gk.z);
+                    const int end = s_tab.grp_end[type][k];
+                    for (; e < end; ++e) {
+                        const float4 r0 = s_tab.side[type][e];
+                        stage_atom(stage, base + (int)r0.w, point_apply(S, make_float3(r0.x, r0.y, r0.z)));
+                    }
+                }
+            }
+            __syncthreads();
+            const int tile_cnt = atot - acarry;
+            int ncopy = tile_cnt;
+            if (acarry + tile_cnt > Amax) {
+                ncopy = max(0, Amax - acarry);
+                if (threadIdx.x == 0) flag_status(TPL_STATUS_TOO_MANY_ATOMS);
+            }
+            float* dst = out + 3 * (size_t)acarry;
+            for (int i = threadIdx.x; i < 3 * ncopy; i += NT) dst[i] = stage[i];
+            carry = T;
+            rigid_reortho(carry);
+            acarry = atot;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) num_atoms[b] = acarry;
+        for (int i = 3 * min(acarry, Amax) + threadIdx.x; i < 3 * Amax; i += NT) out[i] = 0.f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K4: backward (frames recomputed from the angles)
+// ---------------------------------------------------------------------------
+template <int NT>
+__global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ angles,
+                                                    const uint8_t* __restrict__ seq,
+                                                    const int32_t* __restrict__ lengths,
+                                                    const int32_t* __restrict__ order, int B,
+                                                    int Lmax, int Amax,
+                                                    const float* __restrict__ grad_coords,
+                                                    float* __restrict__ grad_angles,
+                                                    const __grid_constant__ FaTable tab) {
+    constexpr int NW = NT / 32;
+    __shared__ FaTable s_tab;
+    __shared__ RigidS s_rig[NW + 1];
+    __shared__ int s_cnt[NW + 1];
+    __shared__ float s6[6 * (NW + 1)];
+    __shared__ RigidS s_carry[kMaxTiles];
+    __shared__ int s_acarry[kMaxTiles];
+    extern __shared__ float4 s_dyn[];
+    float* stage = reinterpret_cast<float*>(s_dyn);  // g of the tile's atoms
+
+    copy_table(s_tab, tab);
+    __syncthreads();
+
+    for (int item = blockIdx.x; item < B; item += gridDim.x) {
+        const int b = chain_at(order, item);
+        const int L = clamp_length(lengths, b, Lmax);
+        const float* ang = angles + (size_t)b * 7 * Lmax;
+        const uint8_t* sq = seq + (size_t)b * Lmax;
+        const float* g_in = grad_coords + (size_t)b * Amax * 3;
+        float* ga = grad_angles + (size_t)b * 7 * Lmax;
+        const int ntiles = (L + NT - 1) / NT;
+
+        // Phase A: frame and atom offset carried into each tile.
+        Rigid carry = rigid_identity();
+        int acarry = 0;
+        if (threadIdx.x == 0) {
+            store_rigid(s_carry[0], carry);
+            s_acarry[0] = 0;
+        }
+        for (int t = 0; t + 1 < ntiles; ++t) {
+            const int j = t * NT + threadIdx.x;
+            const bool valid = j < L;
+            const int type = residue_type(sq, j, valid);
+            float sp, cp, ss, cs;
+            Rigid A = residue_transform(s_tab, ang, Lmax, j, L, sp, cp, ss, cs);
+            Rigid E, T;
+            int a0, atot;
+            block_scan_rigid_count<NT>(A, valid ? s_tab.n_atoms[type] : 0, carry, acarry, s_rig,
+                                       s_cnt, E, a0, T, atot);
+            carry = T;
+            rigid_reortho(carry);
+            acarry = atot;
+            if (threadIdx.x == 0) {
+                store_rigid(s_carry[t + 1], carry);
+                s_acarry[t + 1] = acarry;
+            }
+        }
+        __syncthreads();
+
+        // Phase B: tiles right to left.
+        Sum6 sfx = sum6_zero();
+        for (int t = ntiles - 1; t >= 0; --t) {
+            carry = load_rigid(s_carry[t]);
+            acarry = s_acarry[t];
+            const int j = t * NT + threadIdx.x;
+            const bool valid = j < L;
+            const int type = residue_type(sq, j, valid);
+            float sp = 0.f, cp = 1.f, ss = 0.f, cs = 1.f;
+            Rigid A = residue_transform(s_tab, ang, Lmax, j, L, sp, cp, ss, cs);
+            Rigid E, T;
+            int a0, atot;
+            block_scan_rigid_count<NT>(A, valid ? s_tab.n_atoms[type] : 0, carry, acarry, s_rig,
+                                       s_cnt, E, a0, T, atot);
+            // stage the tile's upstream gradient
+            {
+                const int n = 3 * max(0, min(atot, Amax) - acarry);
+                const float* src = g_in + 3 * (size_t)acarry;
+                for (int i = threadIdx.x; i < n; i += NT) stage[i] = __ldg(src + i);
+            }
+            __syncthreads();
+            const int base = a0 - acarry;
+            float gchi[kMaxGroups] = {0.f, 0.f, 0.f, 0.f};
+            Sum6 all = sum6_zero(), nsum = sum6_zero(), csum = sum6_zero();
+            float3 u_phi = make_float3(0.f, 0.f, 0.f), p_phi = u_phi, u_psi = u_phi, p_psi = u_phi;
+            const bool in_range = valid && a0 + s_tab.n_atoms[type] <= Amax;
+            if (in_range) {
+                auto gat = [&](int slot) {
+                    return make_float3(stage[3 * slot], stage[3 * slot + 1], stage[3 * slot + 2]);
+                };
+                auto add = [](Sum6& s, float3 r, float3 g) {
+                    s.c = f3_add(s.c, f3_cross(r, g));
+                    s.g = f3_add(s.g, g);
+                };
+                // backbone atoms
+                add(nsum, E.t, gat(base + 0));
+                Rigid M1 = E;
+                rigid_mul_R(M1, cp, sp, s_tab.bb.ct[1], s_tab.bb.st[1], s_tab.bb.d[1]);
+                u_phi = M1.c0;
+                p_phi = M1.t;
+                add(all, M1.t, gat(base + 1));
+                Rigid M3 = M1;
+                rigid_mul_R(M3, cs, ss, s_tab.bb.ct[2], s_tab.bb.st[2], s_tab.bb.d[2]);
+                u_psi = M3.c0;
+                p_psi = M3.t;
+                add(csum, M3.t, gat(base + 2));
+                const float4 o = s_tab.o_r0;
+                add(csum, point_apply(M3, make_float3(o.x, o.y, o.z)), gat(base + 3));
+                // side chain: per-group sums, then chi gradients by a suffix over groups
+                Rigid S = M1;
+                rigid_mul_Rx(S, s_tab.rp_c, s_tab.rp_s);
+                const int ng = s_tab.n_groups[type], nchi = s_tab.n_chi[type];
+                float3 gu[kMaxGroups], gp[kMaxGroups];
+                Sum6 gs[kMaxGroups];
+                int e = 0;
+#pragma unroll
+                for (int k = 0; k < kMaxGroups; ++k) {
+                    gs[k] = sum6_zero();
+                    gu[k] = make_float3(0.f, 0.f, 0.f);
+                    gp[k] = gu[k];
+                    if (k < ng) {
+                        float sc, cc;
+                        if (k < nchi) {
+                            sincosf(ang[(3 + k) * Lmax + j], &sc, &cc);
+                        } else {
+                            cc = s_tab.fixchi[type][k].x;
+                            sc = s_tab.fixchi[type][k].y;
+                        }
+                        const float4 gk = s_tab.grp[type][k];
+                        rigid_mul_R(S, cc, sc, gk.x, gk.y, gk.z);
+                        gu[k] = S.c0;
+                        gp[k] = S.t;
+                        const int end = s_tab.grp_end[type][k];
+                        for (; e < end; ++e) {
+                            const float4 r0 = s_tab.side[type][e];
+                            add(gs[k], point_apply(S, make_float3(r0.x, r0.y, r0.z)), gat(base + (int)r0.w));
+                        }
+                    }
+                }
+                Sum6 suf = sum6_zero();
+#pragma unroll
+                for (int k = kMaxGroups - 1; k >= 0; --k) {
+                    suf = sum6_add(suf, gs[k]);
+                    if (k < nchi) gchi[k] = f3_dot(gu[k], f3_sub(suf.c, f3_cross(gp[k], suf.g)));
+                }
+                // all = CA + side chain + C + O (N kept apart: not downstream of phi)
+                all = sum6_add(sum6_add(all, suf), csum);
+            }
+            Sum6 own = sum6_add(all, nsum);
+            Sum6 after, total;
+            block_suffix_sum6<NT>(own, sfx, s6, after, total);
+            if (j < Lmax) {
+                float gphi = 0.f, gpsi = 0.f, gomg = 0.f;
+                if (in_range) {
+                    Sum6 x = sum6_add(csum, after);
+                    gpsi = f3_dot(u_psi, f3_sub(x.c, f3_cross(p_psi, x.g)));
+                    x = sum6_add(all, after);
+                    gphi = f3_dot(u_phi, f3_sub(x.c, f3_cross(p_phi, x.g)));
+                    if (j > 0) {
+                        x = sum6_add(own, after);
+                        gomg = f3_dot(E.c0, f3_sub(x.c, f3_cross(E.t, x.g)));
+                    }
+                }
+                ga[j] = gphi;
+                ga[Lmax + j] = gpsi;
+                ga[2 * Lmax + j] = gomg;
+#pragma unroll
+                for (int k = 0; k < kMaxGroups; ++k) ga[(3 + k) * Lmax + j] = gchi[k];
+            }
+            sfx = total;
+            __syncthreads();
+        }
+        const int covered = min(Lmax, ntiles * NT);
+        for (int i = covered + threadIdx.x; i < Lmax; i += NT)
+#pragma unroll
+            for (int r = 0; r < 7; ++r) ga[r * Lmax + i] = 0.f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K7: plain FP64 per-chain forms (one CTA per chain, thread 0 serial).
+// ---------------------------------------------------------------------------
+struct Frame64 {
+    double m[12];  // dense 3x4 row-major
+};
+
+__device__ void f64_identity(Frame64& f) {
+    for (int k = 0; k < 12; ++k) f.m[k] = 0.0;
+    f.m[0] = f.m[5] = f.m[10] = 1.0;
+}
+
+// f <- f * R(alpha, theta, d), R the dense Section 3 matrix
+__device__ void f64_mul_R(Frame64& f, double alpha, double ct, double st, double d) {
+    double sa, ca;
+    sincos(alpha, &sa, &ca);
+    const double R[12] = {ct, sa * st, ca * st, d * ct, 0.0, ca, -sa, 0.0, -st, sa * ct, ca * ct, -d * st};
+    double N[12];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 4; ++c) {
+            double s = (c == 3) ? f.m[4 * r + 3] : 0.0;
+            for (int k = 0; k < 3; ++k) s += f.m[4 * r + k] * R[4 * k + c];
+            N[4 * r + c] = s;
+        }
+    for (int k = 0; k < 12; ++k) f.m[k] = N[k];
+}
+
+__device__ void f64_mul_Rx(Frame64& f, double c, double s) {
+    for (int r = 0; r < 3; ++r) {
+        const double a1 = f.m[4 * r + 1], a2 = f.m[4 * r + 2];
+        f.m[4 * r + 1] = c * a1 + s * a2;
+        f.m[4 * r + 2] = -s * a1 + c * a2;
+    }
+}
+
+__device__ void f64_point(const Frame64& f, const double* v, double* out) {
+    for (int r = 0; r < 3; ++r)
+        out[r] = f.m[4 * r] * v[0] + f.m[4 * r + 1] * v[1] + f.m[4 * r + 2] * v[2] + f.m[4 * r + 3];
+}
+
+__global__ void fa_fwd_ref64_kernel(const double* __restrict__ angles,
+                                    const uint8_t* __restrict__ seq,
+                                    const int32_t* __restrict__ lengths, int B, int Lmax, int Amax,
+                                    double* __restrict__ coords, int32_t* __restrict__ num_atoms,
+                                    const __grid_constant__ FaTableD tab) {
+    const int b = blockIdx.x;
+    const int L = clamp_length(lengths, b, Lmax);
+    const double* ang = angles + (size_t)b * 7 * Lmax;
+    const uint8_t* sq = seq + (size_t)b * Lmax;
+    double* out = coords + (size_t)b * Amax * 3;
+    // total atom count (every thread, for the zero fill)
+    int total = 0;
+    for (int j = 0; j < L; ++j) total += tab.n_atoms[sq[j] < kNumTypes ? sq[j] : kGlyCode];
+    for (int i = 3 * min(total, Amax) + threadIdx.x; i < 3 * Amax; i += blockDim.x) out[i] = 0.0;
+    if (threadIdx.x != 0) return;
+    Frame64 M0, M1, M3, S[kMaxGroups + 1];
+    f64_identity(M0);
+    int a = 0;
+    for (int j = 0; j < L; ++j) {
+        int type = sq[j];
+        if (type >= kNumTypes) {
+            flag_status(TPL_STATUS_BAD_RESIDUE);
+            type = kGlyCode;
+        }
+        M1 = M0;
+        f64_mul_R(M1, ang[j], tab.bb.ct[1], tab.bb.st[1], tab.bb.d[1]);
+        M3 = M1;
+        f64_mul_R(M3, ang[Lmax + j], tab.bb.ct[2], tab.bb.st[2], tab.bb.d[2]);
+        S[0] = M1;
+        f64_mul_Rx(S[0], tab.rp_c, tab.rp_s);
+        for (int k = 0; k < tab.n_groups[type]; ++k) {
+            S[k + 1] = S[k];
+            const double chi = (k < tab.n_chi[type]) ? ang[(3 + k) * Lmax + j] : tab.fixchi[type][k];
+            f64_mul_R(S[k + 1], chi, tab.grp_ct[type][k], tab.grp_st[type][k], tab.grp_d[type][k]);
+        }
+        for (int t = 0; t < tab.n_atoms[type]; ++t, ++a) {
+            const int g = tab.group[type][t];
+            const Frame64& F = g == 0 ? M0 : (g == 1 ? M1 : (g == 2 ? M3 : S[g - 2]));
+            if (a < Amax) f64_point(F, tab.r0[type][t], out + 3 * a);
+        }
+        if (j + 1 < L) {
+            M0 = M3;
+            f64_mul_R(M0, ang[2 * Lmax + j + 1], tab.bb.ct[0], tab.bb.st[0], tab.bb.d[0]);
+        }
+    }
+    if (a > Amax) flag_status(TPL_STATUS_TOO_MANY_ATOMS);
+    num_atoms[b] = a;
+}
+
+__device__ void cross_acc(double* acc, const double* r, const double* p, const double* g) {
+    const double x = r[0] - p[0], y = r[1] - p[1], z = r[2] - p[2];
+    acc[0] += y * g[2] - z * g[1];
+    acc[1] += z * g[0] - x * g[2];
+    acc[2] += x * g[1] - y * g[0];
+}
+
+__device__ double axis_dot(const double* from, const double* to, const double* acc) {
+    double u[3] = {to[0] - from[0], to[1] - from[1], to[2] - from[2]};
+    const double n = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    return (u[0] * acc[0] + u[1] * acc[1] + u[2] * acc[2]) / n;
+}
+
+__global__ void fa_bwd_ref64_kernel(const uint8_t* __restrict__ seq,
+                                    const int32_t* __restrict__ lengths, int B, int Lmax, int Amax,
+                                    const double* __restrict__ coords,
+                                    const double* __restrict__ grad_coords,
+                                    double* __restrict__ grad_angles,
+                                    const __grid_constant__ FaTableD tab) {
+    const int b = blockIdx.x;
+    const int L = clamp_length(lengths, b, Lmax);
+    const uint8_t* sq = seq + (size_t)b * Lmax;
+    double* ga = grad_angles + (size_t)b * 7 * Lmax;
+    for (int i = threadIdx.x; i < 7 * Lmax; i += blockDim.x) ga[i] = 0.0;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const double* r = coords + (size_t)b * Amax * 3;
+    const double* g = grad_coords + (size_t)b * Amax * 3;
+    auto type_of = [&](int j) { return sq[j] < kNumTypes ? (int)sq[j] : kGlyCode; };
+    int off = 0;
+    for (int j = 0; j < L; ++j) off += tab.n_atoms[type_of(j)];
+    if (off > Amax) return;  // flagged by the forward
+    // Sc = sum r x g and Sg = sum g over residues after the current one
+    double Sc[3] = {0, 0, 0}, Sg[3] = {0, 0, 0};
+    for (int j = L - 1; j >= 0; --j) {
+        const int type = type_of(j);
+        const int n = tab.n_atoms[type];
+        off -= n;
+        const double* rr = r + 3 * off;
+        const double* gg = g + 3 * off;
+        // chi_k: atoms of groups >= k about the axis origin(k-1) -> origin(k)
+        for (int k = 0; k < tab.n_chi[type]; ++k) {
+            const int o1 = tab.origin[type][k];
+            const int o0 = (k == 0) ? 1 : tab.origin[type][k - 1];
+            double acc[3] = {0, 0, 0};
+            for (int t = 0; t < n; ++t)
+                if (tab.group[type][t] >= 3 + k) cross_acc(acc, rr + 3 * t, rr + 3 * o1, gg + 3 * t);
+            ga[(3 + k) * Lmax + j] = axis_dot(rr + 3 * o0, rr + 3 * o1, acc);
+        }
+        // Residue sums about the origin: all atoms, and C + O.
+        double Ac[3] = {0, 0, 0}, Ag[3] = {0, 0, 0}, Cc[3] = {0, 0, 0}, Cg[3] = {0, 0, 0};
+        const double zero[3] = {0, 0, 0};
+        for (int t = 0; t < n; ++t) {
+            if (t == 0) continue;  // N handled with omega
+            cross_acc(Ac, rr + 3 * t, zero, gg + 3 * t);
+            for (int c = 0; c < 3; ++c) Ag[c] += gg[3 * t + c];
+            if (tab.group[type][t] == 2) {
+                cross_acc(Cc, rr + 3 * t, zero, gg + 3 * t);
+                for (int c = 0; c < 3; ++c) Cg[c] += gg[3 * t + c];
+            }
+        }
+        auto about = [](const double* c, const double* gsum, const double* p, double* o) {
+            o[0] = c[0] - (p[1] * gsum[2] - p[2] * gsum[1]);
+            o[1] = c[1] - (p[2] * gsum[0] - p[0] * gsum[2]);
+            o[2] = c[2] - (p[0] * gsum[1] - p[1] * gsum[0]);
+        };
+        double x[3], sc[3], sg[3];
+        // psi: C, O and later residues about CA -> C
+        for (int c = 0; c < 3; ++c) { sc[c] = Cc[c] + Sc[c]; sg[c] = Cg[c] + Sg[c]; }
+        about(sc, sg, rr + 6, x);
+        ga[Lmax + j] = axis_dot(rr + 3, rr + 6, x);
+        // phi: all but N and later residues about N -> CA
+        for (int c = 0; c < 3; ++c) { sc[c] = Ac[c] + Sc[c]; sg[c] = Ag[c] + Sg[c]; }
+        about(sc, sg, rr + 3, x);
+        ga[j] = axis_dot(rr, rr + 3, x);
+        // add N to the residue sums
+        cross_acc(Ac, rr, zero, gg);
+        for (int c = 0; c < 3; ++c) Ag[c] += gg[c];
+        for (int c = 0; c < 3; ++c) { Sc[c] += Ac[c]; Sg[c] += Ag[c]; }
+        // omega_j (j >= 1): residues >= j about C_{j-1} -> N_j
+        if (j >= 1) {
+            const int nprev = tab.n_atoms[type_of(j - 1)];
+            const double* cprev = r + 3 * (off - nprev + 2);
+            about(Sc, Sg, rr, x);
+            ga[2 * Lmax + j] = axis_dot(cprev, rr, x);
+        }
+    }
+}
+
+template <int NT>
+cudaError_t fa_fwd_t(const float* angles, const uint8_t* seq, const int32_t* lengths,
+                     const int32_t* order, int B, int Lmax, int Amax, float* coords,
+                     int32_t* num_atoms, int grid, cudaStream_t s) {
+    const size_t smem = (size_t)NT * kMaxAtoms * 3 * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(fa_fwd_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fa_fwd_kernel<NT><<<grid, NT, smem, s>>>(angles, seq, lengths, order, B, Lmax, Amax, coords,
+                                             num_atoms, fa_table());
+    return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t fa_bwd_t(const float* angles, const uint8_t* seq, const int32_t* lengths,
+                     const int32_t* order, int B, int Lmax, int Amax, const float* grad_coords,
+                     float* grad_angles, int grid, cudaStream_t s) {
+    const size_t smem = (size_t)NT * kMaxAtoms * 3 * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(fa_bwd_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fa_bwd_kernel<NT><<<grid, NT, smem, s>>>(angles, seq, lengths, order, B, Lmax, Amax,
+                                             grad_coords, grad_angles, fa_table());
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool fullatom_cfg_supported(int threads) {
+    return threads == 64 || threads == 128 || threads == 256 || threads == 512;
+}
+
+cudaError_t launch_fullatom_forward(const float* angles, const uint8_t* seq,
+                                    const int32_t* lengths, const int32_t* order, int B, int Lmax,
+                                    int Amax, float* coords, int32_t* num_atoms, LaunchCfg cfg,
+                                    cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    const int grid = cfg.grid > 0 ? cfg.grid : B;
+    switch (cfg.threads) {
+        case 64: return fa_fwd_t<64>(angles, seq, lengths, order, B, Lmax, Amax, coords, num_atoms, grid, s);
+        case 128: return fa_fwd_t<128>(angles, seq, lengths, order, B, Lmax, Amax, coords, num_atoms, grid, s);
+        case 256: return fa_fwd_t<256>(angles, seq, lengths, order, B, Lmax, Amax, coords, num_atoms, grid, s);
+        case 512: return fa_fwd_t<512>(angles, seq, lengths, order, B, Lmax, Amax, coords, num_atoms, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
+                                     const int32_t* lengths, const int32_t* order, int B,
+                                     int Lmax, int Amax, const float* coords,
+                                     const float* grad_coords, float* grad_angles,
+                                     bool from_coords, LaunchCfg cfg, cudaStream_t s) {
+    (void)coords;
+    if (from_coords) return cudaErrorNotSupported;
+    if (B == 0) return cudaSuccess;
+    const int grid = cfg.grid > 0 ? cfg.grid : B;
+    switch (cfg.threads) {
+        case 64: return fa_bwd_t<64>(angles, seq, lengths, order, B, Lmax, Amax, grad_coords, grad_angles, grid, s);
+        case 128: return fa_bwd_t<128>(angles, seq, lengths, order, B, Lmax, Amax, grad_coords, grad_angles, grid, s);
+        case 256: return fa_bwd_t<256>(angles, seq, lengths, order, B, Lmax, Amax, grad_coords, grad_angles, grid, s);
+        case 512: return fa_bwd_t<512>(angles, seq, lengths, order, B, Lmax, Amax, grad_coords, grad_angles, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fullatom_forward_ref64(const double* angles, const uint8_t* seq,
+                                          const int32_t* lengths, int B, int Lmax, int Amax,
+                                          double* coords, int32_t* num_atoms, cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    fa_fwd_ref64_kernel<<<B, 128, 0, s>>>(angles, seq, lengths, B, Lmax, Amax, coords, num_atoms,
+                                          fa_table_d());
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fullatom_backward_ref64(const double* angles, const uint8_t* seq,
+                                           const int32_t* lengths, int B, int Lmax, int Amax,
+                                           const double* coords, const double* grad_coords,
+                                           double* grad_angles, cudaStream_t s) {
+    (void)angles;
+    if (B == 0) return cudaSuccess;
+    fa_bwd_ref64_kernel<<<B, 128, 0, s>>>(seq, lengths, B, Lmax, Amax, coords, grad_coords,
+                                          grad_angles, fa_table_d());
+    return cudaGetLastError();
+}
+
+}  // namespace tpl

@@ -1,0 +1,82 @@
+// Host-side launchers of the sm_103a kernels (called by the C ABI in api.cu).
+// Every launcher enqueues on `stream`, returns the launch error (cudaSuccess
+// when all launches were accepted) and never synchronises.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tpl {
+
+struct LaunchCfg {
+    int threads;        // CTA size
+    int res_per_thread; // backbone only
+    int grid;           // CTAs (0 = one per chain)
+};
+
+// Largest number of tiles of one chain kept in shared memory by the backward
+// kernels (phase carries); the host rejects Lmax beyond kMaxTiles * tile.
+constexpr int kMaxTiles = 64;
+
+// K8: longest-first chain order (bucketed by length) into `order` [B].
+cudaError_t launch_build_order(const int32_t* lengths, int B, int Lmax, int32_t* order,
+                               cudaStream_t s);
+
+// K1 / K2: backbone FP32 scan kernels.
+bool backbone_cfg_supported(int threads, int res_per_thread);
+cudaError_t launch_backbone_forward(const float* angles, const int32_t* lengths,
+                                    const int32_t* order, int B, int Lmax, float* coords,
+                                    LaunchCfg cfg, cudaStream_t s);
+cudaError_t launch_backbone_backward(const float* angles, const int32_t* lengths,
+                                     const int32_t* order, int B, int Lmax,
+                                     const float* coords, const float* grad_coords,
+                                     float* grad_angles, bool from_coords, LaunchCfg cfg,
+                                     cudaStream_t s);
+
+// K3 / K4: full-atom FP32 scan kernels.
+bool fullatom_cfg_supported(int threads);
+cudaError_t launch_fullatom_forward(const float* angles, const uint8_t* seq,
+                                    const int32_t* lengths, const int32_t* order, int B, int Lmax,
+                                    int Amax, float* coords, int32_t* num_atoms, LaunchCfg cfg,
+                                    cudaStream_t s);
+cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
+                                     const int32_t* lengths, const int32_t* order, int B,
+                                     int Lmax, int Amax, const float* coords,
+                                     const float* grad_coords, float* grad_angles,
+                                     bool from_coords, LaunchCfg cfg, cudaStream_t s);
+
+// K5 / K6: LRMSD.  The workspace layout is private to lrmsd.cu.
+size_t lrmsd_ws_bytes(int P, int Nmax);
+cudaError_t launch_lrmsd_forward(const float* input, const float* target,
+                                 const int32_t* num_atoms, int P, int Nmax, float* lrmsd,
+                                 void* ws, cudaStream_t s);
+cudaError_t launch_lrmsd_backward(const float* grad_lrmsd, const float* input,
+                                  const float* target, const int32_t* num_atoms, int P, int Nmax,
+                                  float* grad_input, const void* ws, cudaStream_t s);
+
+// K7: plain FP64 per-chain forms.
+cudaError_t launch_backbone_forward_ref64(const double* angles, const int32_t* lengths, int B,
+                                          int Lmax, double* coords, cudaStream_t s);
+cudaError_t launch_backbone_backward_ref64(const double* angles, const int32_t* lengths, int B,
+                                           int Lmax, const double* coords,
+                                           const double* grad_coords, double* grad_angles,
+                                           cudaStream_t s);
+cudaError_t launch_fullatom_forward_ref64(const double* angles, const uint8_t* seq,
+                                          const int32_t* lengths, int B, int Lmax, int Amax,
+                                          double* coords, int32_t* num_atoms, cudaStream_t s);
+cudaError_t launch_fullatom_backward_ref64(const double* angles, const uint8_t* seq,
+                                           const int32_t* lengths, int B, int Lmax, int Amax,
+                                           const double* coords, const double* grad_coords,
+                                           double* grad_angles, cudaStream_t s);
+cudaError_t launch_lrmsd_forward_ref64(const double* input, const double* target,
+                                       const int32_t* num_atoms, int P, int Nmax, double* lrmsd,
+                                       double* state, cudaStream_t s);
+cudaError_t launch_lrmsd_backward_ref64(const double* grad_lrmsd, const double* input,
+                                        const double* target, const int32_t* num_atoms, int P,
+                                        int Nmax, const double* state, double* grad_input,
+                                        cudaStream_t s);
+
+// Reads and clears the device status word (blocking on `s`).
+cudaError_t read_and_clear_status(cudaStream_t s, int* out);
+
+}  // namespace tpl

@@ -1,0 +1,601 @@
+// LRMSD of the paper (Section 4) on sm_103a.
+//
+// Forward, three launches:
+//  K5a lrmsd_moments: grid (chunks, pairs), 2048 atoms per chunk.  Each CTA
+//      streams its chunk once (16-byte loads) and reduces, in FP32, the
+//      moments shifted by the pair's first atom: sum dx, sum dy, sum dx dy^T
+//      (x = target, y = input, as in the paper's R = sum x y^T).
+//  K5b lrmsd_solve: one thread per pair, FP64.  Sums the chunk partials,
+//      centres R, builds the 4x4 matrix T(R), finds its largest eigenvalue by
+//      Newton's method on the characteristic polynomial from an upper bound
+//      and the eigenvector q from the adjugate of (T - lambda I) (the
+//      quaternion-characteristic-polynomial approach of Theobald, Acta Cryst.
+//      A61 (2005) 478), then U(q).  Batched one pair per lane because FP64
+//      issue is scarce on this GPU.
+//  K5c lrmsd_residual: grid (chunks, pairs).  LRMSD^2 = (sum |x'|^2 + |y'|^2 -
+//      2 lambda)/N equals sum |y'_i - U x'_i|^2 / N at the optimum; the
+//      residual form has no cancellation, so it is summed in FP32 per chunk and
+//      the chunk partials in FP64 by the last CTA of the pair.
+// Backward:
+//  K6 lrmsd_grad: grad_y_i = w (y'_i - U x'_i) / (N LRMSD).
+#include "kernels.h"
+#include "tpl_common.cuh"
+
+namespace tpl {
+
+namespace {
+
+constexpr int kNT = 256;     // threads per CTA
+constexpr int kAPT = 8;      // atoms per thread (two groups of 4)
+constexpr int kChunk = kNT * kAPT;
+constexpr int kMom = 15;     // sum dx (3), sum dy (3), sum dx dy^T (9)
+
+struct WsLayout {
+    size_t part1, part2, state, lr64, counter, total;
+    int nch;
+};
+
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+__host__ __device__ inline WsLayout ws_layout(int P, int Nmax) {
+    WsLayout w;
+    w.nch = (Nmax + kChunk - 1) / kChunk;
+    if (w.nch < 1) w.nch = 1;
+    size_t o = 0;
+    w.part1 = o; o = align256(o + (size_t)P * w.nch * 16 * sizeof(float));
+    w.part2 = o; o = align256(o + (size_t)P * w.nch * sizeof(float));
+    w.state = o; o = align256(o + (size_t)P * 16 * sizeof(float));  // U(9) xc(3) yc(3) scale
+    w.lr64 = o; o = align256(o + (size_t)P * sizeof(double));
+    w.counter = o; o = align256(o + (size_t)P * sizeof(int));
+    w.total = o;
+    return w;
+}
+
+__device__ __forceinline__ int pair_atoms(const int32_t* num_atoms, int p, int Nmax) {
+    int n = num_atoms[p];
+    if (n < 0 || n > Nmax) {
+        flag_status(TPL_STATUS_BAD_LENGTH);
+        n = n < 0 ? 0 : Nmax;
+    }
+    return n;
+}
+
+__device__ __forceinline__ int num_chunks(int n) { return n <= 0 ? 1 : (n + kChunk - 1) / kChunk; }
+
+// Four consecutive atoms (12 floats, 16-byte aligned) into xyz[4].
+__device__ __forceinline__ void load4(const float* __restrict__ p, float3 (&v)[4]) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+    float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+    v[0] = make_float3(a.x, a.y, a.z);
+    v[1] = make_float3(a.w, b.x, b.y);
+    v[2] = make_float3(b.z, b.w, c.x);
+    v[3] = make_float3(c.y, c.z, c.w);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// K5a
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kNT) lrmsd_moments_kernel(const float* __restrict__ input,
+                                                            const float* __restrict__ target,
+                                                            const int32_t* __restrict__ num_atoms,
+                                                            int P, int Nmax, float* __restrict__ part1,
+                                                            int nch_max) {
+    __shared__ float s_red[kNT / 32][kMom];
+    const int p = blockIdx.y, c = blockIdx.x;
+    const int n = pair_atoms(num_atoms, p, Nmax);
+    if (c >= num_chunks(n)) return;
+    const float* x = target + (size_t)p * Nmax * 3;
+    const float* y = input + (size_t)p * Nmax * 3;
+    float3 sx = make_float3(0.f, 0.f, 0.f), sy = sx;
+    if (n > 0) {
+        sx = make_float3(__ldg(x), __ldg(x + 1), __ldg(x + 2));
+        sy = make_float3(__ldg(y), __ldg(y + 1), __ldg(y + 2));
+    }
+    float m[kMom];
+#pragma unroll
+    for (int k = 0; k < kMom; ++k) m[k] = 0.f;
+#pragma unroll
+    for (int s = 0; s < kAPT / 4; ++s) {
+        const int i0 = c * kChunk + 4 * (threadIdx.x + kNT * s);
+        if (i0 < n) {
+            float3 xv[4], yv[4];
+            load4(x + 3 * (size_t)i0, xv);
+            load4(y + 3 * (size_t)i0, yv);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (i0 + q < n) {
+                    const float3 dx = f3_sub(xv[q], sx), dy = f3_sub(yv[q], sy);
+                    m[0] += dx.x; m[1] += dx.y; m[2] += dx.z;
+                    m[3] += dy.x; m[4] += dy.y; m[5] += dy.z;
+                    m[6] = fmaf(dx.x, dy.x, m[6]); m[7] = fmaf(dx.x, dy.y, m[7]); m[8] = fmaf(dx.x, dy.z, m[8]);
+                    m[9] = fmaf(dx.y, dy.x, m[9]); m[10] = fmaf(dx.y, dy.y, m[10]); m[11] = fmaf(dx.y, dy.z, m[11]);
+                    m[12] = fmaf(dx.z, dy.x, m[12]); m[13] = fmaf(dx.z, dy.y, m[13]); m[14] = fmaf(dx.z, dy.z, m[14]);
+                }
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kMom; ++k) {
+        const float v = warp_sum(m[k]);
+        if (lane == 0) s_red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kMom) {
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < kNT / 32; ++w) v += s_red[w][threadIdx.x];
+        part1[((size_t)p * nch_max + c) * 16 + threadIdx.x] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K5b
+// ---------------------------------------------------------------------------
+__device__ double det3(double a, double b, double c, double d, double e, double f, double g,
+                       double h, double i) {
+    return a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
+}
+
+// Cofactor (r, c) of the symmetric 4x4 A.
+__device__ double cofactor4(const double (&A)[4][4], int r, int c) {
+    double m[9];
+    int k = 0;
+    for (int i = 0; i < 4; ++i) {
+        if (i == r) continue;
+        for (int j = 0; j < 4; ++j) {
+            if (j == c) continue;
+            m[k++] = A[i][j];
+        }
+    }
+    const double d = det3(m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7], m[8]);
+    return ((r + c) & 1) ? -d : d;
+}
+
+__global__ void lrmsd_solve_kernel(const float* __restrict__ input, const float* __restrict__ target,
+                                   const int32_t* __restrict__ num_atoms, int P, int Nmax,
+                                   const float* __restrict__ part1, int nch_max,
+                                   float* __restrict__ state, int* __restrict__ counter) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    const int n = pair_atoms(num_atoms, p, Nmax);
+    counter[p] = 0;
+    float* st = state + 16 * (size_t)p;
+    double S[kMom];
+    for (int k = 0; k < kMom; ++k) S[k] = 0.0;
+    const int nch = num_chunks(n);
+    for (int c = 0; c < nch; ++c)
+        for (int k = 0; k < kMom; ++k) S[k] += (double)part1[((size_t)p * nch_max + c) * 16 + k];
+    double U[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    double xc[3] = {0, 0, 0}, yc[3] = {0, 0, 0};
+    if (n > 0) {
+        const float* x = target + (size_t)p * Nmax * 3;
+        const float* y = input + (size_t)p * Nmax * 3;
+        const double inv = 1.0 / n;
+        double mx[3], my[3];
+        for (int a = 0; a < 3; ++a) {
+            mx[a] = S[a] * inv;
+            my[a] = S[3 + a] * inv;
+            xc[a] = (double)x[a] + mx[a];
+            yc[a] = (double)y[a] + my[a];
+        }
+        // centred R_ab = sum x'_a y'_b
+        double R[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) R[a][b] = S[6 + 3 * a + b] - n * mx[a] * my[b];
+        // T(R) of Section 4
+        double T[4][4];
+        T[0][0] = R[0][0] + R[1][1] + R[2][2];
+        T[0][1] = T[1][0] = R[1][2] - R[2][1];
+        T[0][2] = T[2][0] = R[2][0] - R[0][2];
+        T[0][3] = T[3][0] = R[0][1] - R[1][0];
+        T[1][1] = R[0][0] - R[1][1] - R[2][2];
+        T[1][2] = T[2][1] = R[0][1] + R[1][0];
+        T[1][3] = T[3][1] = R[0][2] + R[2][0];
+        T[2][2] = -R[0][0] + R[1][1] - R[2][2];
+        T[2][3] = T[3][2] = R[1][2] + R[2][1];
+        T[3][3] = -R[0][0] - R[1][1] + R[2][2];
+        // characteristic polynomial of the trace-free T: l^4 + c2 l^2 + c1 l + c0,
+        // c2 = -tr(T^2)/2, c1 = -tr(T^3)/3, c0 = det T (Newton's identities)
+        double T2[4][4];
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+                double s = 0.0;
+                for (int k = 0; k < 4; ++k) s += T[i][k] * T[k][j];
+                T2[i][j] = s;
+            }
+        double tr2 = 0.0, tr3 = 0.0;
+        for (int i = 0; i < 4; ++i) {
+            tr2 += T2[i][i];
+            for (int j = 0; j < 4; ++j) tr3 += T2[i][j] * T[j][i];
+        }
+        double det = 0.0;
+        for (int j = 0; j < 4; ++j) det += T[0][j] * cofactor4(T, 0, j);
+        const double c2 = -0.5 * tr2, c1 = -tr3 / 3.0, c0 = det;
+        // Newton from sqrt(tr T^2) >= largest eigenvalue: monotone for a real-rooted polynomial
+        double lam = sqrt(tr2);
+        for (int it = 0; it < 100; ++it) {
+            const double l2 = lam * lam;
+            const double pv = (l2 + c2) * l2 + c1 * lam + c0;
+            const double dp = (4.0 * l2 + 2.0 * c2) * lam + c1;
+            if (dp == 0.0) break;
+            const double step = pv / dp;
+            lam -= step;
+            if (fabs(step) <= 1e-15 * fabs(lam) + 1e-300) break;
+        }
+        // eigenvector: largest column of adj(T - lambda I)
+        double A[4][4];
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) A[i][j] = T[i][j] - (i == j ? lam : 0.0);
+        double best = -1.0, q[4] = {1.0, 0.0, 0.0, 0.0};
+        for (int col = 0; col < 4; ++col) {
+            double v[4], nn = 0.0;
+            for (int r = 0; r < 4; ++r) {
+                v[r] = cofactor4(A, col, r);
+                nn += v[r] * v[r];
+            }
+            if (nn > best) {
+                best = nn;
+                for (int r = 0; r < 4; ++r) q[r] = v[r];
+            }
+        }
+        if (best > 0.0) {
+            const double s = 1.0 / sqrt(best);
+            for (int r = 0; r < 4; ++r) q[r] *= s;
+        } else {
+            q[0] = 1.0; q[1] = q[2] = q[3] = 0.0;
+        }
+        // U(q) of Section 4
+        const double q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+        U[0] = q0 * q0 + q1 * q1 - q2 * q2 - q3 * q3;
+        U[1] = 2.0 * (q1 * q2 - q0 * q3);
+        U[2] = 2.0 * (q1 * q3 + q0 * q2);
+        U[3] = 2.0 * (q1 * q2 + q0 * q3);
+        U[4] = q0 * q0 - q1 * q1 + q2 * q2 - q3 * q3;
+        U[5] = 2.0 * (q2 * q3 - q0 * q1);
+        U[6] = 2.0 * (q1 * q3 - q0 * q2);
+        U[7] = 2.0 * (q2 * q3 + q0 * q1);
+        U[8] = q0 * q0 - q1 * q1 - q2 * q2 + q3 * q3;
+    }
+    for (int k = 0; k < 9; ++k) st[k] = (float)U[k];
+    for (int k = 0; k < 3; ++k) {
+        st[9 + k] = (float)xc[k];
+        st[12 + k] = (float)yc[k];
+    }
+    st[15] = 0.f;
+}
+
+// U x + loads of the per-pair state
+struct PairState {
+    float3 u0, u1, u2;  // rows of U
+    float3 xc, yc;
+    float scale;
+};
+
+__device__ __forceinline__ PairState load_state(const float* st) {
+    PairState s;
+    s.u0 = make_float3(st[0], st[1], st[2]);
+    s.u1 = make_float3(st[3], st[4], st[5]);
+    s.u2 = make_float3(st[6], st[7], st[8]);
+    s.xc = make_float3(st[9], st[10], st[11]);
+    s.yc = make_float3(st[12], st[13], st[14]);
+    s.scale = st[15];
+    return s;
+}
+
+__device__ __forceinline__ float3 residual(const PairState& s, float3 x, float3 y) {
+    const float3 xp = f3_sub(x, s.xc), yp = f3_sub(y, s.yc);
+    return make_float3(yp.x - f3_dot(s.u0, xp), yp.y - f3_dot(s.u1, xp), yp.z - f3_dot(s.u2, xp));
+}
+
+// ---------------------------------------------------------------------------
+// K5c
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kNT) lrmsd_residual_kernel(
+    const float* __restrict__ input, const float* __restrict__ target,
+    const int32_t* __restrict__ num_atoms, int P, int Nmax, float* __restrict__ part2,
+    float* __restrict__ state, double* __restrict__ lr64, int* __restrict__ counter,
+    float* __restrict__ lrmsd, int nch_max) {
+    __shared__ float s_red[kNT / 32];
+    __shared__ int s_last;
+    const int p = blockIdx.y, c = blockIdx.x;
+    const int n = pair_atoms(num_atoms, p, Nmax);
+    const int nch = num_chunks(n);
+    if (c >= nch) return;
+    const float* x = target + (size_t)p * Nmax * 3;
+    const float* y = input + (size_t)p * Nmax * 3;
+    const PairState ps = load_state(state + 16 * (size_t)p);
+    float acc = 0.f;
+#pragma unroll
+    for (int s = 0; s < kAPT / 4; ++s) {
+        const int i0 = c * kChunk + 4 * (threadIdx.x + kNT * s);
+        if (i0 < n) {
+            float3 xv[4], yv[4];
+            load4(x + 3 * (size_t)i0, xv);
+            load4(y + 3 * (size_t)i0, yv);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (i0 + q < n) {
+                    const float3 r = residual(ps, xv[q], yv[q]);
+                    acc += f3_dot(r, r);
+                }
+        }
+    }
+    acc = warp_sum(acc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float v = 0.f;
+        for (int w = 0; w < kNT / 32; ++w) v += s_red[w];
+        part2[(size_t)p * nch_max + c] = v;
+        __threadfence();
+        s_last = (atomicAdd(counter + p, 1) == nch - 1);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        double sum = 0.0;
+        for (int k = 0; k < nch; ++k) sum += (double)__ldcg(part2 + (size_t)p * nch_max + k);
+        const double lr = n > 0 ? sqrt(sum / n) : 0.0;
+        double scale = 0.0;
+        if (lr >= 1e-12) {
+            scale = 1.0 / (n * lr);
+        } else if (n > 0) {
+            flag_status(TPL_STATUS_ZERO_LRMSD);
+        }
+        lr64[p] = lr;
+        lrmsd[p] = (float)lr;
+        state[16 * (size_t)p + 15] = (float)scale;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K6
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kNT) lrmsd_grad_kernel(const float* __restrict__ grad_lrmsd,
+                                                         const float* __restrict__ input,
+                                                         const float* __restrict__ target,
+                                                         const int32_t* __restrict__ num_atoms,
+                                                         int P, int Nmax, const float* __restrict__ state,
+                                                         float* __restrict__ grad_input) {
+    const int p = blockIdx.y, c = blockIdx.x;
+    const int n = pair_atoms(num_atoms, p, Nmax);
+    const float* x = target + (size_t)p * Nmax * 3;
+    const float* y = input + (size_t)p * Nmax * 3;
+    float* gy = grad_input + (size_t)p * Nmax * 3;
+    const PairState ps = load_state(state + 16 * (size_t)p);
+    const float w = __ldg(grad_lrmsd + p) * ps.scale;
+#pragma unroll
+    for (int s = 0; s < kAPT / 4; ++s) {
+        const int i0 = c * kChunk + 4 * (threadIdx.x + kNT * s);
+        if (i0 >= Nmax) continue;
+        float g[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) g[k] = 0.f;
+        if (i0 < n) {
+            float3 xv[4], yv[4];
+            load4(x + 3 * (size_t)i0, xv);
+            load4(y + 3 * (size_t)i0, yv);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (i0 + q < n) {
+                    const float3 r = residual(ps, xv[q], yv[q]);
+                    g[3 * q] = w * r.x;
+                    g[3 * q + 1] = w * r.y;
+                    g[3 * q + 2] = w * r.z;
+                }
+        }
+        float4* o = reinterpret_cast<float4*>(gy + 3 * (size_t)i0);
+        o[0] = make_float4(g[0], g[1], g[2], g[3]);
+        o[1] = make_float4(g[4], g[5], g[6], g[7]);
+        o[2] = make_float4(g[8], g[9], g[10], g[11]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K7: plain FP64 per-pair form (one CTA per pair, FP64 block sums, cyclic
+// Jacobi on T, LRMSD by the closed form of Section 4).
+// ---------------------------------------------------------------------------
+constexpr int kRefNT = 128;
+
+template <int V>
+__device__ void block_sum64(double (&v)[V], double* s) {
+    for (int k = 0; k < V; ++k) s[k * kRefNT + threadIdx.x] = v[k];
+    __syncthreads();
+    for (int w = kRefNT / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int k = 0; k < V; ++k) s[k * kRefNT + threadIdx.x] += s[k * kRefNT + threadIdx.x + w];
+        __syncthreads();
+    }
+    for (int k = 0; k < V; ++k) v[k] = s[k * kRefNT];
+    __syncthreads();
+}
+
+__device__ void jacobi4(double (&A)[4][4], double (&V)[4][4]) {
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < 4; ++i)
+            for (int j = i + 1; j < 4; ++j) off += A[i][j] * A[i][j];
+        if (off < 1e-300) break;
+        for (int p = 0; p < 3; ++p)
+            for (int q = p + 1; q < 4; ++q) {
+                if (A[p][q] == 0.0) continue;
+                const double th = 0.5 * (A[q][q] - A[p][p]) / A[p][q];
+                const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(1.0 + th * th));
+                const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                for (int k = 0; k < 4; ++k) {
+                    const double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - s * akq;
+                    A[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 4; ++k) {
+                    const double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - s * aqk;
+                    A[q][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 4; ++k) {
+                    const double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - s * vkq;
+                    V[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+}
+
+__global__ void __launch_bounds__(kRefNT) lrmsd_fwd_ref64_kernel(
+    const double* __restrict__ input, const double* __restrict__ target,
+    const int32_t* __restrict__ num_atoms, int P, int Nmax, double* __restrict__ lrmsd,
+    double* __restrict__ state) {
+    __shared__ double s[10 * kRefNT];
+    __shared__ double s_c[6];
+    const int p = blockIdx.x;
+    const int n = pair_atoms(num_atoms, p, Nmax);
+    const double* x = target + (size_t)p * Nmax * 3;
+    const double* y = input + (size_t)p * Nmax * 3;
+    double c6[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = threadIdx.x; i < n; i += kRefNT)
+        for (int a = 0; a < 3; ++a) {
+            c6[a] += x[3 * i + a];
+            c6[3 + a] += y[3 * i + a];
+        }
+    block_sum64<6>(c6, s);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 6; ++k) s_c[k] = n > 0 ? c6[k] / n : 0.0;
+    __syncthreads();
+    double m[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // R (9), E0
+    for (int i = threadIdx.x; i < n; i += kRefNT) {
+        double xp[3], yp[3];
+        for (int a = 0; a < 3; ++a) {
+            xp[a] = x[3 * i + a] - s_c[a];
+            yp[a] = y[3 * i + a] - s_c[3 + a];
+        }
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) m[3 * a + b] += xp[a] * yp[b];
+        m[9] += xp[0] * xp[0] + xp[1] * xp[1] + xp[2] * xp[2] + yp[0] * yp[0] + yp[1] * yp[1] + yp[2] * yp[2];
+    }
+    block_sum64<10>(m, s);
+    if (threadIdx.x != 0) return;
+    double* st = state + 16 * (size_t)p;
+    double U[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    double lr = 0.0;
+    if (n > 0) {
+        const double* R = m;  // R[3a+b]
+        double A[4][4] = {
+            {R[0] + R[4] + R[8], R[5] - R[7], R[6] - R[2], R[1] - R[3]},
+            {R[5] - R[7], R[0] - R[4] - R[8], R[1] + R[3], R[2] + R[6]},
+            {R[6] - R[2], R[1] + R[3], -R[0] + R[4] - R[8], R[5] + R[7]},
+            {R[1] - R[3], R[2] + R[6], R[5] + R[7], -R[0] - R[4] + R[8]}};
+        double V[4][4];
+        jacobi4(A, V);
+        int best = 0;
+        for (int k = 1; k < 4; ++k)
+            if (A[k][k] > A[best][best]) best = k;
+        const double lam = A[best][best];
+        double q[4] = {V[0][best], V[1][best], V[2][best], V[3][best]};
+        const double qn = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+        for (int k = 0; k < 4; ++k) q[k] /= qn;
+        U[0] = q[0] * q[0] + q[1] * q[1] - q[2] * q[2] - q[3] * q[3];
+        U[1] = 2 * (q[1] * q[2] - q[0] * q[3]);
+        U[2] = 2 * (q[1] * q[3] + q[0] * q[2]);
+        U[3] = 2 * (q[1] * q[2] + q[0] * q[3]);
+        U[4] = q[0] * q[0] - q[1] * q[1] + q[2] * q[2] - q[3] * q[3];
+        U[5] = 2 * (q[2] * q[3] - q[0] * q[1]);
+        U[6] = 2 * (q[1] * q[3] - q[0] * q[2]);
+        U[7] = 2 * (q[2] * q[3] + q[0] * q[1]);
+        U[8] = q[0] * q[0] - q[1] * q[1] - q[2] * q[2] + q[3] * q[3];
+        const double rad = (m[9] - 2.0 * lam) / n;
+        lr = sqrt(rad > 0.0 ? rad : 0.0);
+    }
+    for (int k = 0; k < 9; ++k) st[k] = U[k];
+    for (int k = 0; k < 6; ++k) st[9 + k] = s_c[k];
+    st[15] = lr;
+    lrmsd[p] = lr;
+}
+
+__global__ void __launch_bounds__(kRefNT) lrmsd_bwd_ref64_kernel(
+    const double* __restrict__ grad_lrmsd, const double* __restrict__ input,
+    const double* __restrict__ target, const int32_t* __restrict__ num_atoms, int P, int Nmax,
+    const double* __restrict__ state, double* __restrict__ grad_input) {
+    const int p = blockIdx.x;
+    const int n = pair_atoms(num_atoms, p, Nmax);
+    const double* st = state + 16 * (size_t)p;
+    const double lr = st[15];
+    const double w = (n > 0 && lr >= 1e-12) ? grad_lrmsd[p] / (n * lr) : 0.0;
+    const double* x = target + (size_t)p * Nmax * 3;
+    const double* y = input + (size_t)p * Nmax * 3;
+    double* g = grad_input + (size_t)p * Nmax * 3;
+    for (int i = threadIdx.x; i < Nmax; i += kRefNT) {
+        if (i >= n) {
+            g[3 * i] = g[3 * i + 1] = g[3 * i + 2] = 0.0;
+            continue;
+        }
+        const double xp[3] = {x[3 * i] - st[9], x[3 * i + 1] - st[10], x[3 * i + 2] - st[11]};
+        for (int a = 0; a < 3; ++a)
+            g[3 * i + a] = w * ((y[3 * i + a] - st[12 + a]) -
+                                (st[3 * a] * xp[0] + st[3 * a + 1] * xp[1] + st[3 * a + 2] * xp[2]));
+    }
+}
+
+}  // namespace
+
+size_t lrmsd_ws_bytes(int P, int Nmax) { return ws_layout(P, Nmax).total; }
+
+cudaError_t launch_lrmsd_forward(const float* input, const float* target, const int32_t* num_atoms,
+                                 int P, int Nmax, float* lrmsd, void* ws, cudaStream_t s) {
+    if (P == 0) return cudaSuccess;
+    const WsLayout L = ws_layout(P, Nmax);
+    char* base = static_cast<char*>(ws);
+    float* part1 = reinterpret_cast<float*>(base + L.part1);
+    float* part2 = reinterpret_cast<float*>(base + L.part2);
+    float* state = reinterpret_cast<float*>(base + L.state);
+    double* lr64 = reinterpret_cast<double*>(base + L.lr64);
+    int* counter = reinterpret_cast<int*>(base + L.counter);
+    const dim3 grid(L.nch, P);
+    lrmsd_moments_kernel<<<grid, kNT, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.nch);
+    lrmsd_solve_kernel<<<(P + 63) / 64, 64, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.nch,
+                                                    state, counter);
+    lrmsd_residual_kernel<<<grid, kNT, 0, s>>>(input, target, num_atoms, P, Nmax, part2, state, lr64,
+                                               counter, lrmsd, L.nch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lrmsd_backward(const float* grad_lrmsd, const float* input, const float* target,
+                                  const int32_t* num_atoms, int P, int Nmax, float* grad_input,
+                                  const void* ws, cudaStream_t s) {
+    if (P == 0) return cudaSuccess;
+    const WsLayout L = ws_layout(P, Nmax);
+    const float* state = reinterpret_cast<const float*>(static_cast<const char*>(ws) + L.state);
+    const dim3 grid(L.nch, P);
+    lrmsd_grad_kernel<<<grid, kNT, 0, s>>>(grad_lrmsd, input, target, num_atoms, P, Nmax, state,
+                                           grad_input);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lrmsd_forward_ref64(const double* input, const double* target,
+                                       const int32_t* num_atoms, int P, int Nmax, double* lrmsd,
+                                       double* state, cudaStream_t s) {
+    if (P == 0) return cudaSuccess;
+    lrmsd_fwd_ref64_kernel<<<P, kRefNT, 0, s>>>(input, target, num_atoms, P, Nmax, lrmsd, state);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lrmsd_backward_ref64(const double* grad_lrmsd, const double* input,
+                                        const double* target, const int32_t* num_atoms, int P,
+                                        int Nmax, const double* state, double* grad_input,
+                                        cudaStream_t s) {
+    if (P == 0) return cudaSuccess;
+    lrmsd_bwd_ref64_kernel<<<P, kRefNT, 0, s>>>(grad_lrmsd, input, target, num_atoms, P, Nmax, state,
+                                                grad_input);
+    return cudaGetLastError();
+}
+
+}  // namespace tpl

@@ -1,0 +1,128 @@
+"""Full-atom model (Section 2): FP32 scan kernels and the FP64 per-chain form
+against the FP64 CPU oracle, element by element.  Tolerances as for the backbone:
+coordinates <= 2e-3 A, gradients <= 1e-4 relative per chain, FP64 form 1e-9.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1812_01108_gb300 as tpl
+import workloads
+from tests.gpu_util import dev, host, rel_err, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+COORD_TOL = 2e-3
+GRAD_TOL = 1e-4
+LENGTHS = np.array([0, 1, 2, 31, 64, 255, 256, 257, 350, 513, 700], np.int32)
+
+
+def _inputs(lengths, seed, omega_noise=0.0):
+    rng = np.random.default_rng(seed)
+    a, seq = workloads.fullatom_inputs(lengths, rng)
+    if omega_noise:
+        a[:, 2] += rng.normal(0, omega_noise, size=a[:, 2].shape).astype(np.float32)
+        a *= (np.arange(a.shape[2])[None, :] < lengths[:, None])[:, None, :]
+    Amax = workloads.pad_to(max(oracle.max_atoms(seq, lengths), 1))
+    g = workloads.upstream_grad((len(lengths), Amax, 3), rng)
+    return a, seq, g, Amax
+
+
+def _run_fp32(a, seq, lengths, g, Amax, opts=None):
+    d = require_gpu()
+    A, S, Ln = dev(a, d), dev(seq, d), dev(lengths, d)
+    B, _, Lmax = a.shape
+    coords = torch.full((B, Amax, 3), float("nan"), device=d)
+    na = torch.full((B,), -1, dtype=torch.int32, device=d)
+    ws = torch.empty(tpl.tpl_fullatom_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    tpl.tpl_fullatom_forward(A, S, Ln, coords, na, ws, opts)
+    ga = torch.full_like(A, float("nan"))
+    tpl.tpl_fullatom_backward(A, S, Ln, None, dev(g, d), ga, ws, opts)
+    torch.cuda.synchronize()
+    return host(coords), host(na), host(ga)
+
+
+@pytest.fixture(scope="module")
+def reference():
+    a, seq, g, Amax = _inputs(LENGTHS, 21, omega_noise=0.2)
+    c64, na64 = oracle.fullatom_forward(a, seq, LENGTHS, Amax)
+    # the upstream gradient is defined on real atoms only
+    g = g * (np.arange(Amax)[None, :] < na64[:, None])[:, :, None]
+    g64 = oracle.fullatom_backward(a, seq, LENGTHS, g)
+    return a, seq, g.astype(np.float32), Amax, c64, na64, g64
+
+
+@pytest.mark.parametrize("threads", [256, 64, 128, 512])
+def test_fp32_scan_matches_oracle(reference, threads):
+    a, seq, g, Amax, c64, na64, g64 = reference
+    c32, na32, ga32 = _run_fp32(a, seq, LENGTHS, g, Amax, {"threads": threads})
+    assert np.array_equal(na32, na64)  # atom counts bit-exact
+    assert np.abs(c32 - c64).max() <= COORD_TOL
+    assert rel_err(ga32, g64) <= GRAD_TOL
+    for b in range(len(LENGTHS)):
+        assert np.all(c32[b, na64[b]:] == 0)
+        assert np.all(ga32[b, :, LENGTHS[b]:] == 0)
+    # unused chi rows and omega_0 are exactly zero
+    for b, L in enumerate(LENGTHS):
+        for j in range(L):
+            nchi = tpl.residue_table(int(seq[b, j]))[2]
+            assert np.all(ga32[b, 3 + nchi:, j] == 0)
+        if L:
+            assert ga32[b, 2, 0] == 0
+
+
+def test_schedule_independent(reference):
+    a, seq, g, Amax, *_ = reference
+    r1 = _run_fp32(a, seq, LENGTHS, g, Amax, {"schedule": tpl.SCHED_LONGEST_FIRST})
+    r2 = _run_fp32(a, seq, LENGTHS, g, Amax, {"schedule": tpl.SCHED_BATCH_ORDER})
+    for x, y in zip(r1, r2):
+        assert np.array_equal(x, y)
+
+
+def test_fp64_per_chain_form_matches_oracle(reference):
+    d = require_gpu()
+    a, seq, g, Amax, c64, na64, g64 = reference
+    A = dev(a.astype(np.float64), d)
+    S, Ln = dev(seq, d), dev(LENGTHS, d)
+    B = a.shape[0]
+    coords = torch.full((B, Amax, 3), float("nan"), dtype=torch.float64, device=d)
+    na = torch.zeros((B,), dtype=torch.int32, device=d)
+    tpl.tpl_fullatom_forward_ref64(A, S, Ln, coords, na)
+    ga = torch.full_like(A, float("nan"))
+    tpl.tpl_fullatom_backward_ref64(A, S, Ln, coords, dev(g.astype(np.float64), d), ga)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(na), na64)
+    assert np.abs(host(coords) - c64).max() < 1e-9
+    assert rel_err(host(ga), g64) < 1e-9
+
+
+def test_backbone_atoms_equal_backbone_kernel():
+    # Section 5's cross-check, on the GPU: N/CA/C of the full-atom kernel equal
+    # the backbone kernel's within FP32 rounding.
+    d = require_gpu()
+    lengths = np.array([300, 120], np.int32)
+    a, seq, g, Amax = _inputs(lengths, 4)
+    c32, na32, _ = _run_fp32(a, seq, lengths, g, Amax)
+    bb = tpl.backbone(dev(np.ascontiguousarray(a[:, :3]), d), dev(lengths, d))
+    bb = host(bb)
+    for b, L in enumerate(lengths):
+        off = 0
+        for j in range(L):
+            assert np.abs(c32[b, off:off + 3] - bb[b, 3 * j:3 * j + 3]).max() < 1e-3
+            off += tpl.residue_table(int(seq[b, j]))[1]
+
+
+def test_bad_residue_and_too_many_atoms_set_status():
+    d = require_gpu()
+    tpl.tpl_get_status()
+    lengths = np.array([10, 10], np.int32)
+    a, seq, g, Amax = _inputs(lengths, 6)
+    seq = seq.copy()
+    seq[0, 3] = 31
+    _run_fp32(a, seq, lengths, g, Amax)
+    assert tpl.tpl_get_status() & tpl.STATUS_BAD_RESIDUE
+    seq[0, 3] = 1
+    c32, na32, _ = _run_fp32(a, seq, lengths, g, 12)  # Amax far too small
+    assert tpl.tpl_get_status() & tpl.STATUS_TOO_MANY_ATOMS
+    assert np.all(np.isfinite(c32))
