@@ -513,12 +513,27 @@ __global__ void fa_bwd_ref64_kernel(const uint8_t* __restrict__ seq,
     }
 }
 
+// The dynamic shared-memory limit is raised once per device and kernel, so no
+// attribute call happens during a stream capture after the first launch.
+template <typename K>
+cudaError_t smem_attr_once(K kernel, int bytes, bool* done_per_device) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (done_per_device[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done_per_device[dev] = true;
+    return e;
+}
+
 template <int NT>
 cudaError_t fa_fwd_t(const float* angles, const uint8_t* seq, const int32_t* lengths,
                      const int32_t* order, int B, int Lmax, int Amax, float* coords,
                      int32_t* num_atoms, int grid, cudaStream_t s) {
     const size_t smem = (size_t)NT * kMaxAtoms * 3 * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(fa_fwd_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static bool done[64] = {false};
+    cudaError_t e = smem_attr_once(fa_fwd_kernel<NT>, (int)smem, done);
     if (e != cudaSuccess) return e;
     fa_fwd_kernel<NT><<<grid, NT, smem, s>>>(angles, seq, lengths, order, B, Lmax, Amax, coords,
                                              num_atoms, fa_table());
@@ -530,7 +545,8 @@ cudaError_t fa_bwd_t(const float* angles, const uint8_t* seq, const int32_t* len
                      const int32_t* order, int B, int Lmax, int Amax, const float* grad_coords,
                      float* grad_angles, int grid, cudaStream_t s) {
     const size_t smem = (size_t)NT * kMaxAtoms * 3 * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(fa_bwd_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static bool done[64] = {false};
+    cudaError_t e = smem_attr_once(fa_bwd_kernel<NT>, (int)smem, done);
     if (e != cudaSuccess) return e;
     fa_bwd_kernel<NT><<<grid, NT, smem, s>>>(angles, seq, lengths, order, B, Lmax, Amax,
                                              grad_coords, grad_angles, fa_table());

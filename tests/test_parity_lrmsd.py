@@ -21,7 +21,8 @@ def _clouds(sizes, seed, noise=0.5):
     rng = np.random.default_rng(seed)
     P = len(sizes)
     Nmax = workloads.pad_to(max(max(sizes), 1))
-    x, y, _ = workloads.lrmsd_clouds(P, 1, 2, rng, Nmax=Nmax, noise=noise)
+    # full clouds first (non-degenerate), then cut to the requested sizes
+    x, y, _ = workloads.lrmsd_clouds(P, Nmax, Nmax, rng, Nmax=Nmax, noise=noise)
     n = np.array(sizes, np.int32)
     mask = (np.arange(Nmax)[None, :] < n[:, None])[:, :, None]
     return (x * mask).astype(np.float32), (y * mask).astype(np.float32), n
