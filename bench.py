@@ -220,10 +220,8 @@ def run_tpl(args):
     stream = torch.cuda.current_stream(dev)
 
     names = ["fullatom_forward", "lrmsd_forward", "lrmsd_backward", "fullatom_backward"]
-    launches = {"fullatom_forward": 1, "lrmsd_forward": 3, "lrmsd_backward": 1, "fullatom_backward": 1}
-    order_launch = 1 if B > torch.cuda.get_device_properties(dev).multi_processor_count else 0
-    launches["fullatom_forward"] += order_launch
-    launches["fullatom_backward"] += order_launch
+    # our kernels per call: schedule + forward; moments + solve + residual; gradient; backward
+    launches = {"fullatom_forward": 2, "lrmsd_forward": 3, "lrmsd_backward": 1, "fullatom_backward": 1}
 
     calls = [
         lambda: tpl.tpl_fullatom_forward(A, S, Ln, coords, na, fa_ws, opts),

@@ -72,6 +72,8 @@ typedef int tpl_status;
 #define TPL_STATUS_BAD_LENGTH 0x2  /* a length < 0 or > Lmax, or num_atoms outside [0, Nmax] */
 #define TPL_STATUS_TOO_MANY_ATOMS 0x4 /* a chain needs more than Amax atoms */
 #define TPL_STATUS_ZERO_LRMSD 0x8  /* an LRMSD below 1e-12 A: its gradient is set to 0 */
+#define TPL_STATUS_TIMEOUT 0x10    /* a bounded wait between CTAs gave up (results invalid) */
+#define TPL_STATUS_BAD_WORKSPACE 0x20 /* a backward was given a workspace its forward did not fill */
 
 typedef struct CUstream_st* tpl_stream; /* same type as cudaStream_t */
 
@@ -95,7 +97,11 @@ typedef struct tpl_opts {
 /* Backbone model (paper Section 3)                                          */
 /* ------------------------------------------------------------------------ */
 
-/* Bytes of workspace the backbone calls need for B chains (16-byte aligned). */
+/* Bytes of workspace the backbone calls need for B chains of at most Lmax
+ * residues.  The forward fills it (tile schedule, per-tile start frames); the
+ * backward must get the same workspace, unmodified, with the same inputs and
+ * options.  A backward given a workspace no forward filled sets
+ * TPL_STATUS_BAD_WORKSPACE and writes zero gradients. */
 size_t tpl_backbone_workspace_size(int B, int Lmax);
 
 /* Section 3: r_i = R_0 R_1 ... R_i 0 with atom 3j = N (R(omega_j, pi-2.1186,
@@ -103,8 +109,10 @@ size_t tpl_backbone_workspace_size(int B, int Lmax);
  * pi-2.0610, 1.525)); R(alpha, theta, d) is the Section 3 matrix.
  *   angles  [B][3][Lmax] in, lengths [B] int32 in (device),
  *   coords  [B][3*Lmax][3] out.
- * The composition is a parallel prefix scan over rigid transforms (FP32,
- * carries re-orthonormalised). */
+ * The chain is cut into tiles (threads x res_per_thread residues); persistent
+ * CTAs take tiles from a work counter, scan the rigid transforms inside a tile
+ * in parallel (FP32) and chain the tiles by a bounded look-back over the
+ * earlier tiles' aggregates (re-orthonormalised). */
 tpl_status tpl_backbone_forward(const float* angles, const int32_t* lengths, int B, int Lmax,
                                 float* coords, void* workspace, size_t workspace_bytes,
                                 const tpl_opts* opts, tpl_stream stream);
@@ -115,7 +123,8 @@ tpl_status tpl_backbone_forward(const float* angles, const int32_t* lengths, int
  * (u_k, p_k: axis and origin of frame k).
  *   grad_coords [B][3*Lmax][3] in, grad_angles [B][3][Lmax] out (0 at padding
  *   and at omega_0).  `coords` is the forward's output; it is read only in
- *   TPL_BWD_FROM_COORDS mode and may be NULL otherwise. */
+ *   TPL_BWD_FROM_COORDS mode and may be NULL otherwise.  `workspace` is the
+ *   one the forward filled. */
 tpl_status tpl_backbone_backward(const float* angles, const int32_t* lengths, int B, int Lmax,
                                  const float* coords, const float* grad_coords,
                                  float* grad_angles, void* workspace, size_t workspace_bytes,
@@ -125,6 +134,8 @@ tpl_status tpl_backbone_backward(const float* angles, const int32_t* lengths, in
 /* Full-atom model (paper Section 2)                                         */
 /* ------------------------------------------------------------------------ */
 
+/* Workspace of the full-atom calls; the same contract as the backbone's (the
+ * backward reuses the forward's schedule and tile-start frames). */
 size_t tpl_fullatom_workspace_size(int B, int Lmax);
 
 /* Section 2: per residue M_1 = M_0 R_1(phi), side-chain frames M_1 R' R(chi_1)
@@ -142,8 +153,9 @@ tpl_status tpl_fullatom_forward(const float* angles, const uint8_t* seq, const i
  * p_i x sum g_k) with a suffix scan over residues for phi/psi/omega and a
  * suffix over the side-chain groups for chi.
  *   grad_coords [B][Amax][3] in, grad_angles [B][7][Lmax] out (0 at padding,
- *   unused chi rows and omega_0).  `coords` is read only in
- *   TPL_BWD_FROM_COORDS mode and may be NULL otherwise. */
+ *   unused chi rows and omega_0).  Frames are rebuilt from the angles and the
+ *   forward's tile-start frames (`workspace` as filled by the forward);
+ *   `coords` is unused and may be NULL (TPL_BWD_FROM_COORDS is rejected). */
 tpl_status tpl_fullatom_backward(const float* angles, const uint8_t* seq, const int32_t* lengths,
                                  int B, int Lmax, int Amax, const float* coords,
                                  const float* grad_coords, float* grad_angles, void* workspace,

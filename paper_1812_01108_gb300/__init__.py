@@ -40,6 +40,7 @@ _lock = threading.Lock()
 BWD_AUTO, BWD_RECOMPUTE, BWD_FROM_COORDS = 0, 1, 2
 SCHED_AUTO, SCHED_LONGEST_FIRST, SCHED_BATCH_ORDER = 0, 1, 2
 STATUS_BAD_RESIDUE, STATUS_BAD_LENGTH, STATUS_TOO_MANY_ATOMS, STATUS_ZERO_LRMSD = 1, 2, 4, 8
+STATUS_TIMEOUT, STATUS_BAD_WORKSPACE = 16, 32
 
 
 class TplError(RuntimeError):
@@ -318,16 +319,15 @@ class BackboneFn(torch.autograd.Function):
         coords = torch.empty((B, 3 * Lmax, 3), dtype=torch.float32, device=angles.device)
         ws = _workspace(tpl_backbone_workspace_size(B, Lmax), angles.device)
         tpl_backbone_forward(angles, lengths, coords, ws, opts)
-        ctx.save_for_backward(angles, lengths, coords)
+        # the backward reuses the forward's tile schedule and tile-start frames
+        ctx.save_for_backward(angles, lengths, coords, ws)
         ctx.opts = opts
         return coords
 
     @staticmethod
     def backward(ctx, grad_coords):
-        angles, lengths, coords = ctx.saved_tensors
-        B, _, Lmax = angles.shape
+        angles, lengths, coords, ws = ctx.saved_tensors
         ga = torch.empty_like(angles)
-        ws = _workspace(tpl_backbone_workspace_size(B, Lmax), angles.device)
         tpl_backbone_backward(angles, lengths, coords, grad_coords.contiguous(), ga, ws, ctx.opts)
         return ga, None, None
 
@@ -342,17 +342,15 @@ class FullAtomFn(torch.autograd.Function):
         num_atoms = torch.empty((B,), dtype=torch.int32, device=angles.device)
         ws = _workspace(tpl_fullatom_workspace_size(B, Lmax), angles.device)
         tpl_fullatom_forward(angles, seq, lengths, coords, num_atoms, ws, opts)
-        ctx.save_for_backward(angles, seq, lengths)
+        ctx.save_for_backward(angles, seq, lengths, ws)
         ctx.opts = opts
         ctx.mark_non_differentiable(num_atoms)
         return coords, num_atoms
 
     @staticmethod
     def backward(ctx, grad_coords, _grad_num):
-        angles, seq, lengths = ctx.saved_tensors
-        B, _, Lmax = angles.shape
+        angles, seq, lengths, ws = ctx.saved_tensors
         ga = torch.empty_like(angles)
-        ws = _workspace(tpl_fullatom_workspace_size(B, Lmax), angles.device)
         tpl_fullatom_backward(angles, seq, lengths, None, grad_coords.contiguous(), ga, ws, ctx.opts)
         return ga, None, None, None, None
 

@@ -4,10 +4,13 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/tpl.h"
 #include "kernels.h"
+#include "sched.cuh"
 #include "tables.h"
 #include "tpl_common.cuh"
 
@@ -41,46 +44,80 @@ tpl_status cuda_fail(cudaError_t e, const char* where) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // ---------------------------------------------------------------------------
-// K8: longest-first order.  One CTA: histogram of lengths in 64 buckets
-// (longest bucket first), exclusive scan, scatter.  Order inside a bucket is
-// arbitrary; results do not depend on it (each chain is computed alone).
+// K8: the tile list.  One CTA: chain order (batch order, or longest first by a
+// 64-bucket counting sort), tiles per chain, exclusive scan, list entries; it
+// also zeroes the forward look-back flags and work counter.
 // ---------------------------------------------------------------------------
 constexpr int kBuckets = 64;
+constexpr int kSchedThreads = 1024;
 
-__global__ void __launch_bounds__(1024) build_order_kernel(const int32_t* __restrict__ lengths,
-                                                           int B, int Lmax,
-                                                           int32_t* __restrict__ order) {
+__global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* __restrict__ lengths,
+                                                                 int B, int Lmax, int tile,
+                                                                 int longest_first, ChainWs ws) {
     __shared__ int hist[kBuckets];
-    if (threadIdx.x < kBuckets) hist[threadIdx.x] = 0;
-    __syncthreads();
-    auto key = [&](int b) {
-        int L = lengths[b];
-        L = L < 0 ? 0 : (L > Lmax ? Lmax : L);
-        const int bucket = (int)(((long long)L * kBuckets) / ((long long)Lmax + 1));
-        return kBuckets - 1 - bucket;
+    __shared__ int s_part[kSchedThreads];
+    int* order = reinterpret_cast<int*>(ws.bagg);  // scratch: the backward's area is free here
+    for (int i = threadIdx.x; i < B * ws.tmax; i += kSchedThreads) ws.fflag[i] = 0;
+    auto len = [&](int b) {
+        const int L = lengths[b];
+        return L < 0 ? 0 : (L > Lmax ? Lmax : L);
     };
-    for (int b = threadIdx.x; b < B; b += blockDim.x) atomicAdd(&hist[key(b)], 1);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int k = 0; k < kBuckets; ++k) {
-            const int c = hist[k];
-            hist[k] = run;
-            run += c;
+    if (longest_first) {
+        if (threadIdx.x < kBuckets) hist[threadIdx.x] = 0;
+        __syncthreads();
+        auto key = [&](int b) {
+            return kBuckets - 1 - (int)(((long long)len(b) * kBuckets) / ((long long)Lmax + 1));
+        };
+        for (int b = threadIdx.x; b < B; b += kSchedThreads) atomicAdd(&hist[key(b)], 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int k = 0; k < kBuckets; ++k) {
+                const int c = hist[k];
+                hist[k] = run;
+                run += c;
+            }
         }
+        __syncthreads();
+        for (int b = threadIdx.x; b < B; b += kSchedThreads) order[atomicAdd(&hist[key(b)], 1)] = b;
+    } else {
+        for (int b = threadIdx.x; b < B; b += kSchedThreads) order[b] = b;
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < B; b += blockDim.x) order[atomicAdd(&hist[key(b)], 1)] = b;
-}
-
-int num_sms() {
-    int dev = 0, n = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
-    return n;
+    // each thread owns a contiguous run of the ordered chains
+    const int per = (B + kSchedThreads - 1) / kSchedThreads;
+    const int i0 = threadIdx.x * per, i1 = min(B, i0 + per);
+    auto ntiles = [&](int b) {
+        const int L = len(b);
+        return L > 0 ? (L + tile - 1) / tile : 1;  // an empty chain still gets one tile (zero fill)
+    };
+    int mine = 0;
+    for (int i = i0; i < i1; ++i) mine += ntiles(order[i]);
+    s_part[threadIdx.x] = mine;
+    __syncthreads();
+    for (int off = 1; off < kSchedThreads; off <<= 1) {  // inclusive Hillis-Steele scan
+        const int v = threadIdx.x >= off ? s_part[threadIdx.x - off] : 0;
+        __syncthreads();
+        s_part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int base = s_part[threadIdx.x] - mine;
+    for (int i = i0; i < i1; ++i) {
+        const int b = order[i];
+        const int n = ntiles(b);
+        for (int k = 0; k < n; ++k) ws.tiles[base + k] = make_int2(b, k);
+        base += n;
+    }
+    if (threadIdx.x == 0) {
+        ws.hdr[kHdrTiles] = s_part[kSchedThreads - 1];
+        ws.hdr[kHdrFwdNext] = 0;
+        ws.hdr[kHdrTile] = tile;
+        ws.hdr[kHdrMagic] = kWsMagic;
+        ws.hdr[kHdrB] = B;
+        ws.hdr[kHdrLmax] = Lmax;
+    }
 }
 
 tpl_opts resolve(const tpl_opts* o) {
@@ -90,11 +127,7 @@ tpl_opts resolve(const tpl_opts* o) {
     return r;
 }
 
-bool use_order(const tpl_opts& o, int B) {
-    if (o.schedule == TPL_SCHED_BATCH_ORDER) return false;
-    if (o.schedule == TPL_SCHED_LONGEST_FIRST) return true;
-    return B > num_sms();  // more than one wave of chains: longest first
-}
+bool longest_first(const tpl_opts& o) { return o.schedule == TPL_SCHED_LONGEST_FIRST; }
 
 tpl_status check_opts(const tpl_opts& o) {
     if (o.bwd_mode < TPL_BWD_AUTO || o.bwd_mode > TPL_BWD_FROM_COORDS)
@@ -111,7 +144,6 @@ LaunchCfg backbone_cfg(const tpl_opts& o) {
     LaunchCfg c;
     c.threads = o.threads ? o.threads : 128;
     c.res_per_thread = o.res_per_thread ? o.res_per_thread : 2;
-    c.grid = 0;
     return c;
 }
 
@@ -119,7 +151,6 @@ LaunchCfg fullatom_cfg(const tpl_opts& o) {
     LaunchCfg c;
     c.threads = o.threads ? o.threads : 256;
     c.res_per_thread = 1;
-    c.grid = 0;
     return c;
 }
 
@@ -134,8 +165,6 @@ tpl_status check_chain_args(int B, int Lmax, const void* const* ptrs, int nptr) 
     return TPL_OK;
 }
 
-size_t order_bytes(int B) { return align256((size_t)(B > 0 ? B : 1) * sizeof(int32_t)); }
-
 tpl_status check_ws(void* ws, size_t have, size_t need) {
     if (need == 0) return TPL_OK;
     if (!ws) return fail(TPL_ERR_WORKSPACE, "workspace is NULL (%zu bytes needed)", need);
@@ -144,24 +173,44 @@ tpl_status check_ws(void* ws, size_t have, size_t need) {
     return TPL_OK;
 }
 
-tpl_status maybe_order(const tpl_opts& o, const int32_t* lengths, int B, int Lmax, void* ws,
-                       const int32_t** order, cudaStream_t s) {
-    *order = nullptr;
-    if (!use_order(o, B)) return TPL_OK;
-    int32_t* ord = static_cast<int32_t*>(ws);
-    cudaError_t e = launch_build_order(lengths, B, Lmax, ord, s);
-    if (e != cudaSuccess) return cuda_fail(e, "build_order");
-    *order = ord;
-    return TPL_OK;
-}
-
 }  // namespace
 
-cudaError_t launch_build_order(const int32_t* lengths, int B, int Lmax, int32_t* order,
-                               cudaStream_t s) {
-    if (B == 0) return cudaSuccess;
-    build_order_kernel<<<1, 1024, 0, s>>>(lengths, B, Lmax, order);
+size_t chain_ws_bytes(int B, int Lmax) { return chain_ws_layout(nullptr, B, Lmax, nullptr); }
+
+cudaError_t launch_schedule(const int32_t* lengths, int B, int Lmax, int tile, bool longest_first,
+                            const ChainWs& ws, cudaStream_t s) {
+    schedule_kernel<<<1, kSchedThreads, 0, s>>>(lengths, B, Lmax, tile, longest_first ? 1 : 0, ws);
     return cudaGetLastError();
+}
+
+cudaError_t reset_backward_flags(const ChainWs& ws, cudaStream_t s) {
+    return cudaMemsetAsync(ws.bflag, 0, (size_t)(ws.slots + 4) * sizeof(int), s);
+}
+
+// CTAs of a persistent launch: SMs x resident CTAs per SM, cached per kernel
+// and device (the occupancy query is a host-side call, safe during capture).
+int persistent_grid(const void* kernel, int threads, size_t smem) {
+    struct Entry {
+        const void* k;
+        int dev, threads;
+        size_t smem;
+        int grid;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry& e : cache)
+        if (e.k == kernel && e.dev == dev && e.threads == threads && e.smem == smem) return e.grid;
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 1;
+    cache.push_back(Entry{kernel, dev, threads, smem, per_sm * sms});
+    return per_sm * sms;
 }
 
 cudaError_t read_and_clear_status(cudaStream_t s, int* out) {
@@ -183,15 +232,9 @@ const char* tpl_version(void) { return "0.1.0"; }
 
 const char* tpl_last_error(void) { return t_last_error.c_str(); }
 
-size_t tpl_backbone_workspace_size(int B, int Lmax) {
-    (void)Lmax;
-    return order_bytes(B);
-}
+size_t tpl_backbone_workspace_size(int B, int Lmax) { return chain_ws_bytes(B, Lmax); }
 
-size_t tpl_fullatom_workspace_size(int B, int Lmax) {
-    (void)Lmax;
-    return order_bytes(B);
-}
+size_t tpl_fullatom_workspace_size(int B, int Lmax) { return chain_ws_bytes(B, Lmax); }
 
 size_t tpl_lrmsd_workspace_size(int P, int Nmax) {
     if (P <= 0 || Nmax < 0) return 256;
@@ -213,9 +256,8 @@ tpl_status tpl_backbone_forward(const float* angles, const int32_t* lengths, int
         return fail(TPL_ERR_INVALID_ARG, "unsupported backbone launch %d x %d", cfg.threads, cfg.res_per_thread);
     if ((st = check_ws(workspace, workspace_bytes, tpl_backbone_workspace_size(B, Lmax)))) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int32_t* order;
-    if ((st = maybe_order(o, lengths, B, Lmax, workspace, &order, s))) return st;
-    cudaError_t e = launch_backbone_forward(angles, lengths, order, B, Lmax, coords, cfg, s);
+    cudaError_t e = launch_backbone_forward(angles, lengths, B, Lmax, coords, longest_first(o),
+                                            workspace, cfg, s);
     if (e != cudaSuccess) return cuda_fail(e, "backbone_forward");
     return ok();
 }
@@ -235,15 +277,10 @@ tpl_status tpl_backbone_backward(const float* angles, const int32_t* lengths, in
     if (!backbone_cfg_supported(cfg.threads, cfg.res_per_thread) ||
         (cfg.threads == 512 && cfg.res_per_thread == 4))
         return fail(TPL_ERR_INVALID_ARG, "unsupported backbone launch %d x %d", cfg.threads, cfg.res_per_thread);
-    if (!from_coords && Lmax > kMaxTiles * cfg.threads * cfg.res_per_thread)
-        return fail(TPL_ERR_BAD_SHAPE, "Lmax=%d exceeds %d tiles of %d residues", Lmax, kMaxTiles,
-                    cfg.threads * cfg.res_per_thread);
     if ((st = check_ws(workspace, workspace_bytes, tpl_backbone_workspace_size(B, Lmax)))) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int32_t* order;
-    if ((st = maybe_order(o, lengths, B, Lmax, workspace, &order, s))) return st;
-    cudaError_t e = launch_backbone_backward(angles, lengths, order, B, Lmax, coords, grad_coords,
-                                             grad_angles, from_coords, cfg, s);
+    cudaError_t e = launch_backbone_backward(angles, lengths, B, Lmax, coords, grad_coords,
+                                             grad_angles, from_coords, workspace, cfg, s);
     if (e != cudaSuccess) return cuda_fail(e, "backbone_backward");
     return ok();
 }
@@ -264,10 +301,8 @@ tpl_status tpl_fullatom_forward(const float* angles, const uint8_t* seq, const i
         return fail(TPL_ERR_INVALID_ARG, "unsupported full-atom launch %d threads", cfg.threads);
     if ((st = check_ws(workspace, workspace_bytes, tpl_fullatom_workspace_size(B, Lmax)))) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int32_t* order;
-    if ((st = maybe_order(o, lengths, B, Lmax, workspace, &order, s))) return st;
-    cudaError_t e = launch_fullatom_forward(angles, seq, lengths, order, B, Lmax, Amax, coords,
-                                            num_atoms, cfg, s);
+    cudaError_t e = launch_fullatom_forward(angles, seq, lengths, B, Lmax, Amax, coords, num_atoms,
+                                            longest_first(o), workspace, cfg, s);
     if (e != cudaSuccess) return cuda_fail(e, "fullatom_forward");
     return ok();
 }
@@ -290,14 +325,10 @@ tpl_status tpl_fullatom_backward(const float* angles, const uint8_t* seq, const 
     LaunchCfg cfg = fullatom_cfg(o);
     if (!fullatom_cfg_supported(cfg.threads))
         return fail(TPL_ERR_INVALID_ARG, "unsupported full-atom launch %d threads", cfg.threads);
-    if (Lmax > kMaxTiles * cfg.threads)
-        return fail(TPL_ERR_BAD_SHAPE, "Lmax=%d exceeds %d tiles of %d residues", Lmax, kMaxTiles, cfg.threads);
     if ((st = check_ws(workspace, workspace_bytes, tpl_fullatom_workspace_size(B, Lmax)))) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int32_t* order;
-    if ((st = maybe_order(o, lengths, B, Lmax, workspace, &order, s))) return st;
-    cudaError_t e = launch_fullatom_backward(angles, seq, lengths, order, B, Lmax, Amax, nullptr,
-                                             grad_coords, grad_angles, false, cfg, s);
+    cudaError_t e = launch_fullatom_backward(angles, seq, lengths, B, Lmax, Amax, grad_coords,
+                                             grad_angles, workspace, cfg, s);
     if (e != cudaSuccess) return cuda_fail(e, "fullatom_backward");
     return ok();
 }

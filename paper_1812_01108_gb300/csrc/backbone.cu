@@ -17,6 +17,7 @@
 // coordinates (FROM_COORDS).
 #include "kernels.h"
 #include "tables.h"
+#include "sched.cuh"
 #include "tpl_common.cuh"
 
 namespace tpl {
@@ -100,76 +101,87 @@ __device__ __forceinline__ void store_stage(float* s, const float (&v)[9 * K]) {
 __device__ __forceinline__ constexpr int row_of(int k) { return k == 0 ? 2 : (k == 1 ? 0 : 1); }
 
 // ---------------------------------------------------------------------------
-// K1: forward
+// K1: forward.  One tile (NT*K residues) per step of a persistent CTA.
 // ---------------------------------------------------------------------------
 template <int NT, int K>
 __global__ void __launch_bounds__(NT) bb_fwd_kernel(const float* __restrict__ angles,
-                                                    const int32_t* __restrict__ lengths,
-                                                    const int32_t* __restrict__ order, int B,
-                                                    int Lmax, float* __restrict__ coords,
+                                                    const int32_t* __restrict__ lengths, int Lmax,
+                                                    float* __restrict__ coords, ChainWs ws,
                                                     BackboneConst bc) {
     constexpr int NW = NT / 32;
     constexpr int TILE = NT * K;
     __shared__ RigidS s_rig[NW + 1];
     __shared__ int s_cnt[NW + 1];
+    __shared__ RigidS s_pre;
+    __shared__ int s_v;
     __shared__ __align__(16) float s_out[TILE * 9];
 
-    for (int item = blockIdx.x; item < B; item += gridDim.x) {
-        const int b = chain_at(order, item);
+    const int ntiles = ws.hdr[kHdrTiles];
+    for (;;) {
+        const int v = next_tile(ws.hdr + kHdrFwdNext, &s_v);
+        if (v >= ntiles) break;
+        const int2 ct = ws.tiles[v];
+        const int b = ct.x, t = ct.y;
         const int L = clamp_length(lengths, b, Lmax);
+        const int T = L > 0 ? (L + TILE - 1) / TILE : 1;
+        const int slot0 = b * ws.tmax;
         const float* ang = angles + (size_t)b * 3 * Lmax;
         float* out = coords + (size_t)b * 9 * Lmax;
-        Rigid carry = rigid_identity();
-        for (int tile0 = 0; tile0 < L; tile0 += TILE) {
-            const int j0 = tile0 + threadIdx.x * K;
-            float a[3][K];
-            load_row<K>(ang, j0, Lmax, a[0]);
-            load_row<K>(ang + Lmax, j0, Lmax, a[1]);
-            load_row<K>(ang + 2 * Lmax, j0, Lmax, a[2]);
-            Rigid A = rigid_identity();
-            float3 pos[3 * K];
+        const int tile0 = t * TILE;
+        const int j0 = tile0 + threadIdx.x * K;
+        float a[3][K];
+        load_row<K>(ang, j0, Lmax, a[0]);
+        load_row<K>(ang + Lmax, j0, Lmax, a[1]);
+        load_row<K>(ang + 2 * Lmax, j0, Lmax, a[2]);
+        Rigid A = rigid_identity();
+        float3 pos[3 * K];
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const int j = j0 + k;
+        for (int k = 0; k < K; ++k) {
+            const int j = j0 + k;
 #pragma unroll
-                for (int at = 0; at < 3; ++at) {
-                    if (j < L && (j > 0 || at > 0)) {
-                        float s, c;
-                        sincosf(a[row_of(at)][k], &s, &c);
-                        rigid_mul_R(A, c, s, bc.ct[at], bc.st[at], bc.d[at]);
-                    }
-                    pos[3 * k + at] = A.t;
+            for (int at = 0; at < 3; ++at) {
+                if (j < L && (j > 0 || at > 0)) {
+                    float s, c;
+                    sincosf(a[row_of(at)][k], &s, &c);
+                    rigid_mul_R(A, c, s, bc.ct[at], bc.st[at], bc.d[at]);
                 }
+                pos[3 * k + at] = A.t;
             }
-            Rigid E, T;
-            int ce, ct;
-            block_scan_rigid_count<NT>(A, 0, carry, 0, s_rig, s_cnt, E, ce, T, ct);
-            float v[9 * K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const bool valid = j0 + k < L;
-#pragma unroll
-                for (int at = 0; at < 3; ++at) {
-                    float3 r = point_apply(E, pos[3 * k + at]);
-                    v[9 * k + 3 * at + 0] = valid ? r.x : 0.f;
-                    v[9 * k + 3 * at + 1] = valid ? r.y : 0.f;
-                    v[9 * k + 3 * at + 2] = valid ? r.z : 0.f;
-                }
-            }
-            store_stage<K>(s_out + threadIdx.x * 9 * K, v);
-            __syncthreads();
-            const int nres = min(TILE, Lmax - tile0);  // multiple of 4
-            float4* dst = reinterpret_cast<float4*>(out + 9 * (size_t)tile0);
-            const float4* src = reinterpret_cast<const float4*>(s_out);
-            for (int i = threadIdx.x; i < nres * 9 / 4; i += NT) dst[i] = src[i];
-            carry = T;
-            rigid_reortho(carry);
-            __syncthreads();
         }
-        const int covered = min(Lmax, ((L + TILE - 1) / TILE) * TILE);
-        float4* o4 = reinterpret_cast<float4*>(out);
-        for (int i = covered * 9 / 4 + threadIdx.x; i < Lmax * 9 / 4; i += NT)
-            o4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        Rigid E, Tot;
+        int ce, ctot;
+        block_scan_rigid_count<NT>(A, 0, s_rig, s_cnt, E, ce, Tot, ctot);
+        if (threadIdx.x == 0) {
+            int pc;
+            const Rigid P = lookback_prefix(ws, slot0, t, Tot, 0, pc);
+            store_rigid(s_pre, P);
+            store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, 0);
+        }
+        __syncthreads();
+        E = rigid_mul(load_rigid(s_pre), E);
+        float vv[9 * K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const bool valid = j0 + k < L;
+#pragma unroll
+            for (int at = 0; at < 3; ++at) {
+                const float3 r = point_apply(E, pos[3 * k + at]);
+                vv[9 * k + 3 * at + 0] = valid ? r.x : 0.f;
+                vv[9 * k + 3 * at + 1] = valid ? r.y : 0.f;
+                vv[9 * k + 3 * at + 2] = valid ? r.z : 0.f;
+            }
+        }
+        store_stage<K>(s_out + threadIdx.x * 9 * K, vv);
+        __syncthreads();
+        const int nres = min(TILE, Lmax - tile0);  // multiple of 4
+        float4* dst = reinterpret_cast<float4*>(out + 9 * (size_t)tile0);
+        const float4* src = reinterpret_cast<const float4*>(s_out);
+        for (int i = threadIdx.x; i < nres * 9 / 4; i += NT) dst[i] = src[i];
+        if (t == T - 1) {  // zero the residues past the last tile
+            float4* o4 = reinterpret_cast<float4*>(out);
+            for (int i = min(Lmax, T * TILE) * 9 / 4 + threadIdx.x; i < Lmax * 9 / 4; i += NT)
+                o4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     }
 }
 
@@ -196,61 +208,66 @@ __device__ __forceinline__ Rigid local_product(const float* ang, int j0, int L, 
     return A;
 }
 
+__device__ __forceinline__ bool ws_matches(const ChainWs& ws, int tile, int B, int Lmax) {
+    return ws.hdr[kHdrMagic] == kWsMagic && ws.hdr[kHdrTile] == tile && ws.hdr[kHdrB] == B &&
+           ws.hdr[kHdrLmax] == Lmax;
+}
+
 // ---------------------------------------------------------------------------
-// K2: backward, RECOMPUTE mode
+// K2: backward.  Tiles of a chain are taken last to first; frames are rebuilt
+// from the angles and the forward's tile-start frames (RECOMPUTE) or read from
+// the forward's coordinates (FROM_COORDS).
 // ---------------------------------------------------------------------------
-template <int NT, int K>
+template <int NT, int K, bool FROM_COORDS>
 __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ angles,
-                                                    const int32_t* __restrict__ lengths,
-                                                    const int32_t* __restrict__ order, int B,
-                                                    int Lmax, const float* __restrict__ grad_coords,
-                                                    float* __restrict__ grad_angles,
+                                                    const int32_t* __restrict__ lengths, int B,
+                                                    int Lmax, const float* __restrict__ coords,
+                                                    const float* __restrict__ grad_coords,
+                                                    float* __restrict__ grad_angles, ChainWs ws,
                                                     BackboneConst bc) {
     constexpr int NW = NT / 32;
     constexpr int TILE = NT * K;
     __shared__ RigidS s_rig[NW + 1];
     __shared__ int s_cnt[NW + 1];
     __shared__ float s6[6 * (NW + 1)];
-    __shared__ RigidS s_carry[kMaxTiles];
+    __shared__ float s_suf[6];
+    __shared__ int s_v;
 
-    for (int item = blockIdx.x; item < B; item += gridDim.x) {
-        const int b = chain_at(order, item);
+    const bool ok = ws_matches(ws, TILE, B, Lmax);
+    if (!ok) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) flag_status(TPL_STATUS_BAD_WORKSPACE);
+        for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < (size_t)B * 3 * Lmax; i += (size_t)gridDim.x * NT)
+            grad_angles[i] = 0.f;
+        return;
+    }
+    const int ntiles = ws.hdr[kHdrTiles];
+    for (;;) {
+        const int v = next_tile(ws.bflag + ws.slots, &s_v);
+        if (v >= ntiles) break;
+        const int2 ct = ws.tiles[v];
+        const int b = ct.x;
         const int L = clamp_length(lengths, b, Lmax);
+        const int T = L > 0 ? (L + TILE - 1) / TILE : 1;
+        const int t = T - 1 - ct.y;  // last tile first
+        const int slot0 = b * ws.tmax;
         const float* ang = angles + (size_t)b * 3 * Lmax;
         const float* g_in = grad_coords + (size_t)b * 9 * Lmax;
         float* ga = grad_angles + (size_t)b * 3 * Lmax;
-        const int ntiles = (L + TILE - 1) / TILE;
+        const int j0 = t * TILE + threadIdx.x * K;
 
-        // Phase A: frame carried into each tile.
-        Rigid carry = rigid_identity();
-        if (threadIdx.x == 0) store_rigid(s_carry[0], carry);
-        for (int t = 0; t + 1 < ntiles; ++t) {
-            float sn[3 * K], cs[3 * K];
-            Rigid A = local_product<K>(ang, t * TILE + threadIdx.x * K, L, Lmax, bc, sn, cs);
-            Rigid E, T;
-            int ce, ct;
-            block_scan_rigid_count<NT>(A, 0, carry, 0, s_rig, s_cnt, E, ce, T, ct);
-            carry = T;
-            rigid_reortho(carry);
-            if (threadIdx.x == 0) store_rigid(s_carry[t + 1], carry);
-        }
-        __syncthreads();
-
-        // Phase B: tiles right to left with the suffix carry.
-        Sum6 sfx = sum6_zero();
-        for (int t = ntiles - 1; t >= 0; --t) {
-            const int j0 = t * TILE + threadIdx.x * K;
-            carry = load_rigid(s_carry[t]);
+        float g[9 * K];
+        load_atoms<K>(g_in + 9 * (size_t)j0, j0 < Lmax, g);
+        Sum6 own = sum6_zero();
+        float gr[3][K];
+        if constexpr (!FROM_COORDS) {
             float sn[3 * K], cs[3 * K];
             Rigid A = local_product<K>(ang, j0, L, Lmax, bc, sn, cs);
-            Rigid E, T;
-            int ce, ct;
-            block_scan_rigid_count<NT>(A, 0, carry, 0, s_rig, s_cnt, E, ce, T, ct);
-            float g[9 * K];
-            load_atoms<K>(g_in + 9 * (size_t)j0, j0 < Lmax, g);
-
+            Rigid E, Tot;
+            int ce, ctot;
+            block_scan_rigid_count<NT>(A, 0, s_rig, s_cnt, E, ce, Tot, ctot);
+            int pc;
+            E = rigid_mul(load_rigid_prev(ws.start + 4 * (size_t)(slot0 + t), pc), E);
             // pass 1: per-thread totals of (r x g, g)
-            Sum6 own = sum6_zero();
             Rigid M = E;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -260,19 +277,26 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
                     for (int at = 0; at < 3; ++at) {
                         if (j > 0 || at > 0)
                             rigid_mul_R(M, cs[3 * k + at], sn[3 * k + at], bc.ct[at], bc.st[at], bc.d[at]);
-                        float3 gi = make_float3(g[9 * k + 3 * at], g[9 * k + 3 * at + 1], g[9 * k + 3 * at + 2]);
+                        const float3 gi = make_float3(g[9 * k + 3 * at], g[9 * k + 3 * at + 1], g[9 * k + 3 * at + 2]);
                         own.c = f3_add(own.c, f3_cross(M.t, gi));
                         own.g = f3_add(own.g, gi);
                     }
                 }
             }
             Sum6 after, total;
-            block_suffix_sum6<NT>(own, sfx, s6, after, total);
-
+            block_suffix_sum6<NT>(own, s6, after, total);
+            if (threadIdx.x == 0) {
+                const Sum6 suf = lookback_suffix(ws, slot0, t, T, total);
+                s_suf[0] = suf.c.x; s_suf[1] = suf.c.y; s_suf[2] = suf.c.z;
+                s_suf[3] = suf.g.x; s_suf[4] = suf.g.y; s_suf[5] = suf.g.z;
+            }
+            __syncthreads();
+            Sum6 later;
+            later.c = make_float3(s_suf[0], s_suf[1], s_suf[2]);
+            later.g = make_float3(s_suf[3], s_suf[4], s_suf[5]);
             // pass 2: gradients, atoms ascending with S = sum over atoms >= current
-            Sum6 S = sum6_add(after, own);
+            Sum6 S = sum6_add(sum6_add(after, later), own);
             M = E;
-            float gr[3][K];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const int j = j0 + k;
@@ -283,7 +307,7 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
                         const bool has_angle = (j > 0 || at > 0);
                         if (has_angle)
                             rigid_mul_R(M, cs[3 * k + at], sn[3 * k + at], bc.ct[at], bc.st[at], bc.d[at]);
-                        float3 gi = make_float3(g[9 * k + 3 * at], g[9 * k + 3 * at + 1], g[9 * k + 3 * at + 2]);
+                        const float3 gi = make_float3(g[9 * k + 3 * at], g[9 * k + 3 * at + 1], g[9 * k + 3 * at + 2]);
                         if (has_angle) val = f3_dot(M.c0, f3_sub(S.c, f3_cross(M.t, S.g)));
                         S.c = f3_sub(S.c, f3_cross(M.t, gi));
                         S.g = f3_sub(S.g, gi);
@@ -291,63 +315,33 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
                     gr[row_of(at)][k] = val;
                 }
             }
-            store_row<K>(ga, j0, Lmax, gr[0]);
-            store_row<K>(ga + Lmax, j0, Lmax, gr[1]);
-            store_row<K>(ga + 2 * Lmax, j0, Lmax, gr[2]);
-            sfx = total;
-        }
-        const int covered = min(Lmax, ntiles * TILE);
-        for (int i = covered + threadIdx.x; i < Lmax; i += NT) {
-            ga[i] = 0.f;
-            ga[Lmax + i] = 0.f;
-            ga[2 * Lmax + i] = 0.f;
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// K2': backward, FROM_COORDS mode: u_i = unit(r_i - r_{i-1}), p_i = r_i.
-// ---------------------------------------------------------------------------
-template <int NT, int K>
-__global__ void __launch_bounds__(NT) bb_bwd_coords_kernel(const int32_t* __restrict__ lengths,
-                                                           const int32_t* __restrict__ order, int B,
-                                                           int Lmax, const float* __restrict__ coords,
-                                                           const float* __restrict__ grad_coords,
-                                                           float* __restrict__ grad_angles) {
-    constexpr int NW = NT / 32;
-    constexpr int TILE = NT * K;
-    __shared__ float s6[6 * (NW + 1)];
-
-    for (int item = blockIdx.x; item < B; item += gridDim.x) {
-        const int b = chain_at(order, item);
-        const int L = clamp_length(lengths, b, Lmax);
-        const float* r_in = coords + (size_t)b * 9 * Lmax;
-        const float* g_in = grad_coords + (size_t)b * 9 * Lmax;
-        float* ga = grad_angles + (size_t)b * 3 * Lmax;
-        const int ntiles = (L + TILE - 1) / TILE;
-        Sum6 sfx = sum6_zero();
-        for (int t = ntiles - 1; t >= 0; --t) {
-            const int j0 = t * TILE + threadIdx.x * K;
-            float g[9 * K], r[9 * K];
-            load_atoms<K>(g_in + 9 * (size_t)j0, j0 < Lmax, g);
+        } else {
+            const float* r_in = coords + (size_t)b * 9 * Lmax;
+            float r[9 * K];
             load_atoms<K>(r_in + 9 * (size_t)j0, j0 < Lmax, r);
             float3 prev = make_float3(0.f, 0.f, 0.f);
             if (j0 > 0 && j0 < Lmax) prev = make_float3(r_in[9 * j0 - 3], r_in[9 * j0 - 2], r_in[9 * j0 - 1]);
-            Sum6 own = sum6_zero();
 #pragma unroll
             for (int q = 0; q < 3 * K; ++q) {
                 if (j0 + q / 3 < L) {
-                    float3 ri = make_float3(r[3 * q], r[3 * q + 1], r[3 * q + 2]);
-                    float3 gi = make_float3(g[3 * q], g[3 * q + 1], g[3 * q + 2]);
+                    const float3 ri = make_float3(r[3 * q], r[3 * q + 1], r[3 * q + 2]);
+                    const float3 gi = make_float3(g[3 * q], g[3 * q + 1], g[3 * q + 2]);
                     own.c = f3_add(own.c, f3_cross(ri, gi));
                     own.g = f3_add(own.g, gi);
                 }
             }
             Sum6 after, total;
-            block_suffix_sum6<NT>(own, sfx, s6, after, total);
-            Sum6 S = sum6_add(after, own);
-            float gr[3][K];
+            block_suffix_sum6<NT>(own, s6, after, total);
+            if (threadIdx.x == 0) {
+                const Sum6 suf = lookback_suffix(ws, slot0, t, T, total);
+                s_suf[0] = suf.c.x; s_suf[1] = suf.c.y; s_suf[2] = suf.c.z;
+                s_suf[3] = suf.g.x; s_suf[4] = suf.g.y; s_suf[5] = suf.g.z;
+            }
+            __syncthreads();
+            Sum6 later;
+            later.c = make_float3(s_suf[0], s_suf[1], s_suf[2]);
+            later.g = make_float3(s_suf[3], s_suf[4], s_suf[5]);
+            Sum6 S = sum6_add(sum6_add(after, later), own);
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const int j = j0 + k;
@@ -355,9 +349,9 @@ __global__ void __launch_bounds__(NT) bb_bwd_coords_kernel(const int32_t* __rest
                 for (int at = 0; at < 3; ++at) {
                     const int q = 3 * k + at;
                     float val = 0.f;
-                    float3 ri = make_float3(r[3 * q], r[3 * q + 1], r[3 * q + 2]);
+                    const float3 ri = make_float3(r[3 * q], r[3 * q + 1], r[3 * q + 2]);
                     if (j < L) {
-                        float3 gi = make_float3(g[3 * q], g[3 * q + 1], g[3 * q + 2]);
+                        const float3 gi = make_float3(g[3 * q], g[3 * q + 1], g[3 * q + 2]);
                         if (j > 0 || at > 0) {
                             float3 u = f3_sub(ri, prev);
                             u = f3_scale(rsqrtf(f3_dot(u, u)), u);
@@ -370,18 +364,17 @@ __global__ void __launch_bounds__(NT) bb_bwd_coords_kernel(const int32_t* __rest
                     gr[row_of(at)][k] = val;
                 }
             }
-            store_row<K>(ga, j0, Lmax, gr[0]);
-            store_row<K>(ga + Lmax, j0, Lmax, gr[1]);
-            store_row<K>(ga + 2 * Lmax, j0, Lmax, gr[2]);
-            sfx = total;
         }
-        const int covered = min(Lmax, ntiles * TILE);
-        for (int i = covered + threadIdx.x; i < Lmax; i += NT) {
-            ga[i] = 0.f;
-            ga[Lmax + i] = 0.f;
-            ga[2 * Lmax + i] = 0.f;
+        store_row<K>(ga, j0, Lmax, gr[0]);
+        store_row<K>(ga + Lmax, j0, Lmax, gr[1]);
+        store_row<K>(ga + 2 * Lmax, j0, Lmax, gr[2]);
+        if (t == T - 1) {
+            for (int i = min(Lmax, T * TILE) + threadIdx.x; i < Lmax; i += NT) {
+                ga[i] = 0.f;
+                ga[Lmax + i] = 0.f;
+                ga[2 * Lmax + i] = 0.f;
+            }
         }
-        __syncthreads();
     }
 }
 
@@ -458,23 +451,26 @@ __global__ void bb_bwd_ref64_kernel(const int32_t* __restrict__ lengths, int B, 
 }
 
 template <int NT, int K>
-cudaError_t fwd_t(const float* angles, const int32_t* lengths, const int32_t* order, int B,
-                  int Lmax, float* coords, int grid, cudaStream_t s) {
-    bb_fwd_kernel<NT, K><<<grid, NT, 0, s>>>(angles, lengths, order, B, Lmax, coords,
-                                             backbone_const());
+cudaError_t fwd_t(const float* angles, const int32_t* lengths, int B, int Lmax, float* coords,
+                  const ChainWs& ws, cudaStream_t s) {
+    const int grid = persistent_grid((const void*)bb_fwd_kernel<NT, K>, NT, 0);
+    bb_fwd_kernel<NT, K><<<grid, NT, 0, s>>>(angles, lengths, Lmax, coords, ws, backbone_const());
     return cudaGetLastError();
 }
 
 template <int NT, int K>
-cudaError_t bwd_t(const float* angles, const int32_t* lengths, const int32_t* order, int B,
-                  int Lmax, const float* coords, const float* grad_coords, float* grad_angles,
-                  bool from_coords, int grid, cudaStream_t s) {
-    if (from_coords)
-        bb_bwd_coords_kernel<NT, K><<<grid, NT, 0, s>>>(lengths, order, B, Lmax, coords,
-                                                        grad_coords, grad_angles);
-    else
-        bb_bwd_kernel<NT, K><<<grid, NT, 0, s>>>(angles, lengths, order, B, Lmax, grad_coords,
-                                                 grad_angles, backbone_const());
+cudaError_t bwd_t(const float* angles, const int32_t* lengths, int B, int Lmax,
+                  const float* coords, const float* grad_coords, float* grad_angles,
+                  bool from_coords, const ChainWs& ws, cudaStream_t s) {
+    if (from_coords) {
+        const int grid = persistent_grid((const void*)bb_bwd_kernel<NT, K, true>, NT, 0);
+        bb_bwd_kernel<NT, K, true><<<grid, NT, 0, s>>>(angles, lengths, B, Lmax, coords, grad_coords,
+                                                        grad_angles, ws, backbone_const());
+    } else {
+        const int grid = persistent_grid((const void*)bb_bwd_kernel<NT, K, false>, NT, 0);
+        bb_bwd_kernel<NT, K, false><<<grid, NT, 0, s>>>(angles, lengths, B, Lmax, coords, grad_coords,
+                                                         grad_angles, ws, backbone_const());
+    }
     return cudaGetLastError();
 }
 
@@ -501,22 +497,27 @@ bool backbone_cfg_supported(int threads, int k) {
         default: return cudaErrorInvalidValue;                                \
     }
 
-cudaError_t launch_backbone_forward(const float* angles, const int32_t* lengths,
-                                    const int32_t* order, int B, int Lmax, float* coords,
+cudaError_t launch_backbone_forward(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                    float* coords, bool longest_first, void* workspace,
                                     LaunchCfg cfg, cudaStream_t s) {
     if (B == 0) return cudaSuccess;
-    const int grid = cfg.grid > 0 ? cfg.grid : B;
-    TPL_BB_DISPATCH(fwd_t, angles, lengths, order, B, Lmax, coords, grid, s)
+    ChainWs ws;
+    chain_ws_layout(workspace, B, Lmax, &ws);
+    cudaError_t e = launch_schedule(lengths, B, Lmax, cfg.threads * cfg.res_per_thread, longest_first, ws, s);
+    if (e != cudaSuccess) return e;
+    TPL_BB_DISPATCH(fwd_t, angles, lengths, B, Lmax, coords, ws, s)
 }
 
-cudaError_t launch_backbone_backward(const float* angles, const int32_t* lengths,
-                                     const int32_t* order, int B, int Lmax, const float* coords,
-                                     const float* grad_coords, float* grad_angles,
-                                     bool from_coords, LaunchCfg cfg, cudaStream_t s) {
+cudaError_t launch_backbone_backward(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                     const float* coords, const float* grad_coords,
+                                     float* grad_angles, bool from_coords, void* workspace,
+                                     LaunchCfg cfg, cudaStream_t s) {
     if (B == 0) return cudaSuccess;
-    const int grid = cfg.grid > 0 ? cfg.grid : B;
-    TPL_BB_DISPATCH(bwd_t, angles, lengths, order, B, Lmax, coords, grad_coords, grad_angles,
-                    from_coords, grid, s)
+    ChainWs ws;
+    chain_ws_layout(workspace, B, Lmax, &ws);
+    cudaError_t e = reset_backward_flags(ws, s);
+    if (e != cudaSuccess) return e;
+    TPL_BB_DISPATCH(bwd_t, angles, lengths, B, Lmax, coords, grad_coords, grad_angles, from_coords, ws, s)
 }
 
 cudaError_t launch_backbone_forward_ref64(const double* angles, const int32_t* lengths, int B,

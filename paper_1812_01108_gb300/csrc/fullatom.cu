@@ -16,6 +16,7 @@
 // suffix scan of (sum r x g, sum g) across the CTA.  Frames are recomputed
 // from the angles; long chains use tile carries from a first pass.
 #include "kernels.h"
+#include "sched.cuh"
 #include "tables.h"
 #include "tpl_common.cuh"
 
@@ -65,61 +66,241 @@ __device__ __forceinline__ void stage_atom(float* stage, int slot, float3 r) {
     stage[3 * slot + 2] = r.z;
 }
 
+// Copy of the float range [g0, g1) between global memory and a shared buffer
+// laid out so that stage[off + i] <-> global[g0 + i], off = g0 mod 4: the
+// 16-byte aligned middle moves as float4, the ragged ends as floats.
+template <int NT, bool TO_GLOBAL>
+__device__ __forceinline__ void copy_range(float* __restrict__ glob, float* __restrict__ stage,
+                                           int g0, int g1) {
+    if (g1 <= g0) return;
+    const int off = g0 & 3;
+    const int head = min(g1, (g0 + 3) & ~3);
+    const int tail = max(head, g1 & ~3);
+    for (int i = g0 + threadIdx.x; i < head; i += NT) {
+        if (TO_GLOBAL) glob[i] = stage[off + i - g0];
+        else stage[off + i - g0] = __ldg(glob + i);
+    }
+    for (int q = head / 4 + threadIdx.x; q < tail / 4; q += NT) {
+        float4* sp = reinterpret_cast<float4*>(stage + off + 4 * q - g0);
+        float4* gp = reinterpret_cast<float4*>(glob) + q;
+        if (TO_GLOBAL) *gp = *sp;
+        else *sp = __ldg(gp);
+    }
+    for (int i = tail + threadIdx.x; i < g1; i += NT) {
+        if (TO_GLOBAL) glob[i] = stage[off + i - g0];
+        else stage[off + i - g0] = __ldg(glob + i);
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void zero_range(float* __restrict__ glob, int g0, int g1) {
+    if (g1 <= g0) return;
+    const int head = min(g1, (g0 + 3) & ~3);
+    const int tail = max(head, g1 & ~3);
+    for (int i = g0 + threadIdx.x; i < head; i += NT) glob[i] = 0.f;
+    for (int q = head / 4 + threadIdx.x; q < tail / 4; q += NT)
+        reinterpret_cast<float4*>(glob)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = tail + threadIdx.x; i < g1; i += NT) glob[i] = 0.f;
+}
+
+__device__ __forceinline__ bool ws_matches(const ChainWs& ws, int tile, int B, int Lmax) {
+    return ws.hdr[kHdrMagic] == kWsMagic && ws.hdr[kHdrTile] == tile && ws.hdr[kHdrB] == B &&
+           ws.hdr[kHdrLmax] == Lmax;
+}
+
 // ---------------------------------------------------------------------------
-// K3: forward
+// K3: forward.  One tile of NT residues per step of a persistent CTA.
 // ---------------------------------------------------------------------------
 template <int NT>
 __global__ void __launch_bounds__(NT) fa_fwd_kernel(const float* __restrict__ angles,
                                                     const uint8_t* __restrict__ seq,
-                                                    const int32_t* __restrict__ lengths,
-                                                    const int32_t* __restrict__ order, int B,
-                                                    int Lmax, int Amax, float* __restrict__ coords,
-                                                    int32_t* __restrict__ num_atoms,
+                                                    const int32_t* __restrict__ lengths, int Lmax,
+                                                    int Amax, float* __restrict__ coords,
+                                                    int32_t* __restrict__ num_atoms, ChainWs ws,
                                                     const __grid_constant__ FaTable tab) {
     constexpr int NW = NT / 32;
     __shared__ FaTable s_tab;
     __shared__ RigidS s_rig[NW + 1];
     __shared__ int s_cnt[NW + 1];
+    __shared__ RigidS s_pre;
+    __shared__ int s_pre_cnt;
+    __shared__ int s_v;
     extern __shared__ float4 s_dyn[];
-    float* stage = reinterpret_cast<float*>(s_dyn);  // NT * kMaxAtoms * 3 floats
+    float* stage = reinterpret_cast<float*>(s_dyn);  // 4 + NT * kMaxAtoms * 3 floats
 
     copy_table(s_tab, tab);
-    __syncthreads();
-
-    for (int item = blockIdx.x; item < B; item += gridDim.x) {
-        const int b = chain_at(order, item);
+    const int ntiles = ws.hdr[kHdrTiles];
+    for (;;) {
+        const int v = next_tile(ws.hdr + kHdrFwdNext, &s_v);
+        if (v >= ntiles) break;
+        const int2 ct = ws.tiles[v];
+        const int b = ct.x, t = ct.y;
         const int L = clamp_length(lengths, b, Lmax);
+        const int T = L > 0 ? (L + NT - 1) / NT : 1;
+        const int slot0 = b * ws.tmax;
         const float* ang = angles + (size_t)b * 7 * Lmax;
         const uint8_t* sq = seq + (size_t)b * Lmax;
         float* out = coords + (size_t)b * Amax * 3;
-        Rigid carry = rigid_identity();
-        int acarry = 0;
-        for (int tile0 = 0; tile0 < L; tile0 += NT) {
-            const int j = tile0 + threadIdx.x;
-            const bool valid = j < L;
-            const int type = residue_type(sq, j, valid);
-            const int cnt = valid ? s_tab.n_atoms[type] : 0;
-            float sp = 0.f, cp = 1.f, ss = 0.f, cs = 1.f;
-            Rigid A = residue_transform(s_tab, ang, Lmax, j, L, sp, cp, ss, cs);
-            Rigid E, T;
-            int a0, atot;
-            block_scan_rigid_count<NT>(A, cnt, carry, acarry, s_rig, s_cnt, E, a0, T, atot);
-            const int base = a0 - acarry;  // slot of this residue's first atom in the tile
-            if (valid) {
-                stage_atom(stage, base + 0, E.t);  // N = M_0 0
-                Rigid M1 = E;
-                rigid_mul_R(M1, cp, sp, s_tab.bb.ct[1], s_tab.bb.st[1], s_tab.bb.d[1]);
-                stage_atom(stage, base + 1, M1.t);  // CA = M_1 0
-                Rigid M3 = M1;
-                rigid_mul_R(M3, cs, ss, s_tab.bb.ct[2], s_tab.bb.st[2], s_tab.bb.d[2]);
-                stage_atom(stage, base + 2, M3.t);  // C = M_3 0
-                const float4 o = s_tab.o_r0;
-                stage_atom(stage, base + 3, point_apply(M3, make_float3(o.x, o.y, o.z)));
-                Rigid S = M1;
-                rigid_mul_Rx(S, s_tab.rp_c, s_tab.rp_s);  // M_1 R'
-                const int ng = s_tab.n_groups[type], nchi = s_tab.n_chi[type];
-                int e = 0;
-                for (int k = 0; k < ng; ++k) {
+
+        const int j = t * NT + threadIdx.x;
+        const bool valid = j < L;
+        const int type = residue_type(sq, j, valid);
+        const int cnt = valid ? s_tab.n_atoms[type] : 0;
+        float sp = 0.f, cp = 1.f, ss = 0.f, cs = 1.f;
+        const Rigid A = residue_transform(s_tab, ang, Lmax, j, L, sp, cp, ss, cs);
+        Rigid E, Tot;
+        int a0, ctot;
+        block_scan_rigid_count<NT>(A, cnt, s_rig, s_cnt, E, a0, Tot, ctot);
+        if (threadIdx.x == 0) {
+            int pc;
+            const Rigid P = lookback_prefix(ws, slot0, t, Tot, ctot, pc);
+            store_rigid(s_pre, P);
+            s_pre_cnt = pc;
+            store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, pc);
+        }
+        __syncthreads();
+        const int pc = s_pre_cnt;
+        E = rigid_mul(load_rigid(s_pre), E);
+        const int soff = (3 * pc) & 3;  // stage[soff + 3 * slot] is the tile's atom `slot`
+        if (valid) {
+            float* st = stage + soff + 3 * a0;
+            stage_atom(st, 0, E.t);  // N = M_0 0
+            Rigid M1 = E;
+            rigid_mul_R(M1, cp, sp, s_tab.bb.ct[1], s_tab.bb.st[1], s_tab.bb.d[1]);
+            stage_atom(st, 1, M1.t);  // CA = M_1 0
+            Rigid M3 = M1;
+            rigid_mul_R(M3, cs, ss, s_tab.bb.ct[2], s_tab.bb.st[2], s_tab.bb.d[2]);
+            stage_atom(st, 2, M3.t);  // C = M_3 0
+            const float4 o = s_tab.o_r0;
+            stage_atom(st, 3, point_apply(M3, make_float3(o.x, o.y, o.z)));
+            Rigid S = M1;
+            rigid_mul_Rx(S, s_tab.rp_c, s_tab.rp_s);  // M_1 R'
+            const int ng = s_tab.n_groups[type], nchi = s_tab.n_chi[type];
+            int e = 0;
+            for (int k = 0; k < ng; ++k) {
+                float sc, cc;
+                if (k < nchi) {
+                    sincosf(ang[(3 + k) * Lmax + j], &sc, &cc);
+                } else {
+                    cc = s_tab.fixchi[type][k].x;
+                    sc = s_tab.fixchi[type][k].y;
+                }
+                const float4 gk = s_tab.grp[type][k];
+                rigid_mul_R(S, cc, sc, gk.x, gk.y, gk.z);
+                const int end = s_tab.grp_end[type][k];
+                for (; e < end; ++e) {
+                    const float4 r0 = s_tab.side[type][e];
+                    stage_atom(st, (int)r0.w, point_apply(S, make_float3(r0.x, r0.y, r0.z)));
+                }
+            }
+        }
+        __syncthreads();
+        const int end_atom = pc + ctot;
+        if (end_atom > Amax && threadIdx.x == 0) flag_status(TPL_STATUS_TOO_MANY_ATOMS);
+        copy_range<NT, true>(out, stage, 3 * pc, 3 * min(end_atom, Amax));
+        if (t == T - 1) {
+            if (threadIdx.x == 0) num_atoms[b] = end_atom;
+            zero_range<NT>(out, 3 * min(end_atom, Amax), 3 * Amax);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K4: backward (frames recomputed from the angles and the forward's tile
+// starts; tiles of a chain taken last to first).
+// ---------------------------------------------------------------------------
+template <int NT>
+__global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ angles,
+                                                    const uint8_t* __restrict__ seq,
+                                                    const int32_t* __restrict__ lengths, int B,
+                                                    int Lmax, int Amax,
+                                                    const float* __restrict__ grad_coords,
+                                                    float* __restrict__ grad_angles, ChainWs ws,
+                                                    const __grid_constant__ FaTable tab) {
+    constexpr int NW = NT / 32;
+    __shared__ FaTable s_tab;
+    __shared__ RigidS s_rig[NW + 1];
+    __shared__ int s_cnt[NW + 1];
+    __shared__ float s6[6 * (NW + 1)];
+    __shared__ float s_suf[6];
+    __shared__ int s_v;
+    extern __shared__ float4 s_dyn[];
+    float* stage = reinterpret_cast<float*>(s_dyn);  // g of the tile's atoms
+
+    if (!ws_matches(ws, NT, B, Lmax)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) flag_status(TPL_STATUS_BAD_WORKSPACE);
+        for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < (size_t)B * 7 * Lmax; i += (size_t)gridDim.x * NT)
+            grad_angles[i] = 0.f;
+        return;
+    }
+    copy_table(s_tab, tab);
+    const int ntiles = ws.hdr[kHdrTiles];
+    for (;;) {
+        const int v = next_tile(ws.bflag + ws.slots, &s_v);
+        if (v >= ntiles) break;
+        const int2 ct = ws.tiles[v];
+        const int b = ct.x;
+        const int L = clamp_length(lengths, b, Lmax);
+        const int T = L > 0 ? (L + NT - 1) / NT : 1;
+        const int t = T - 1 - ct.y;  // last tile first
+        const int slot0 = b * ws.tmax;
+        const float* ang = angles + (size_t)b * 7 * Lmax;
+        const uint8_t* sq = seq + (size_t)b * Lmax;
+        const float* g_in = grad_coords + (size_t)b * Amax * 3;
+        float* ga = grad_angles + (size_t)b * 7 * Lmax;
+
+        const int j = t * NT + threadIdx.x;
+        const bool valid = j < L;
+        const int type = residue_type(sq, j, valid);
+        float sp = 0.f, cp = 1.f, ss = 0.f, cs = 1.f;
+        const Rigid A = residue_transform(s_tab, ang, Lmax, j, L, sp, cp, ss, cs);
+        Rigid E, Tot;
+        int a0, ctot;
+        block_scan_rigid_count<NT>(A, valid ? s_tab.n_atoms[type] : 0, s_rig, s_cnt, E, a0, Tot, ctot);
+        int pc;
+        E = rigid_mul(load_rigid_prev(ws.start + 4 * (size_t)(slot0 + t), pc), E);
+        const int soff = (3 * pc) & 3;
+        copy_range<NT, false>(const_cast<float*>(g_in), stage, 3 * pc, 3 * min(pc + ctot, Amax));
+        __syncthreads();
+
+        float gchi[kMaxGroups] = {0.f, 0.f, 0.f, 0.f};
+        Sum6 all = sum6_zero(), nsum = sum6_zero(), csum = sum6_zero();
+        float3 u_phi = make_float3(0.f, 0.f, 0.f), p_phi = u_phi, u_psi = u_phi, p_psi = u_phi;
+        const bool in_range = valid && pc + a0 + s_tab.n_atoms[type] <= Amax;
+        if (in_range) {
+            const float* st = stage + soff + 3 * a0;
+            auto gat = [&](int slot) {
+                return make_float3(st[3 * slot], st[3 * slot + 1], st[3 * slot + 2]);
+            };
+            auto add = [](Sum6& s, float3 r, float3 g) {
+                s.c = f3_add(s.c, f3_cross(r, g));
+                s.g = f3_add(s.g, g);
+            };
+            add(nsum, E.t, gat(0));
+            Rigid M1 = E;
+            rigid_mul_R(M1, cp, sp, s_tab.bb.ct[1], s_tab.bb.st[1], s_tab.bb.d[1]);
+            u_phi = M1.c0;
+            p_phi = M1.t;
+            add(all, M1.t, gat(1));
+            Rigid M3 = M1;
+            rigid_mul_R(M3, cs, ss, s_tab.bb.ct[2], s_tab.bb.st[2], s_tab.bb.d[2]);
+            u_psi = M3.c0;
+            p_psi = M3.t;
+            add(csum, M3.t, gat(2));
+            const float4 o = s_tab.o_r0;
+            add(csum, point_apply(M3, make_float3(o.x, o.y, o.z)), gat(3));
+            Rigid S = M1;
+            rigid_mul_Rx(S, s_tab.rp_c, s_tab.rp_s);
+            const int ng = s_tab.n_groups[type], nchi = s_tab.n_chi[type];
+            float3 gu[kMaxGroups], gp[kMaxGroups];
+            Sum6 gs[kMaxGroups];
+            int e = 0;
+#pragma unroll
+            for (int k = 0; k < kMaxGroups; ++k) {
+                gs[k] = sum6_zero();
+                gu[k] = make_float3(0.f, 0.f, 0.f);
+                gp[k] = gu[k];
+                if (k < ng) {
                     float sc, cc;
                     if (k < nchi) {
                         sincosf(ang[(3 + k) * Lmax + j], &sc, &cc);
@@ -129,209 +310,60 @@ __global__ void __launch_bounds__(NT) fa_fwd_kernel(const float* __restrict__ an
                     }
                     const float4 gk = s_tab.grp[type][k];
                     rigid_mul_R(S, cc, sc, gk.x, gk.y, gk.z);
+                    gu[k] = S.c0;
+                    gp[k] = S.t;
                     const int end = s_tab.grp_end[type][k];
                     for (; e < end; ++e) {
                         const float4 r0 = s_tab.side[type][e];
-                        stage_atom(stage, base + (int)r0.w, point_apply(S, make_float3(r0.x, r0.y, r0.z)));
+                        add(gs[k], point_apply(S, make_float3(r0.x, r0.y, r0.z)), gat((int)r0.w));
                     }
                 }
             }
-            __syncthreads();
-            const int tile_cnt = atot - acarry;
-            int ncopy = tile_cnt;
-            if (acarry + tile_cnt > Amax) {
-                ncopy = max(0, Amax - acarry);
-                if (threadIdx.x == 0) flag_status(TPL_STATUS_TOO_MANY_ATOMS);
+            Sum6 suf = sum6_zero();
+#pragma unroll
+            for (int k = kMaxGroups - 1; k >= 0; --k) {
+                suf = sum6_add(suf, gs[k]);
+                if (k < nchi) gchi[k] = f3_dot(gu[k], f3_sub(suf.c, f3_cross(gp[k], suf.g)));
             }
-            float* dst = out + 3 * (size_t)acarry;
-            for (int i = threadIdx.x; i < 3 * ncopy; i += NT) dst[i] = stage[i];
-            carry = T;
-            rigid_reortho(carry);
-            acarry = atot;
-            __syncthreads();
+            // all = CA + side chain + C + O (N is not downstream of phi)
+            all = sum6_add(sum6_add(all, suf), csum);
         }
-        if (threadIdx.x == 0) num_atoms[b] = acarry;
-        for (int i = 3 * min(acarry, Amax) + threadIdx.x; i < 3 * Amax; i += NT) out[i] = 0.f;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// K4: backward (frames recomputed from the angles)
-// ---------------------------------------------------------------------------
-template <int NT>
-__global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ angles,
-                                                    const uint8_t* __restrict__ seq,
-                                                    const int32_t* __restrict__ lengths,
-                                                    const int32_t* __restrict__ order, int B,
-                                                    int Lmax, int Amax,
-                                                    const float* __restrict__ grad_coords,
-                                                    float* __restrict__ grad_angles,
-                                                    const __grid_constant__ FaTable tab) {
-    constexpr int NW = NT / 32;
-    __shared__ FaTable s_tab;
-    __shared__ RigidS s_rig[NW + 1];
-    __shared__ int s_cnt[NW + 1];
-    __shared__ float s6[6 * (NW + 1)];
-    __shared__ RigidS s_carry[kMaxTiles];
-    __shared__ int s_acarry[kMaxTiles];
-    extern __shared__ float4 s_dyn[];
-    float* stage = reinterpret_cast<float*>(s_dyn);  // g of the tile's atoms
-
-    copy_table(s_tab, tab);
-    __syncthreads();
-
-    for (int item = blockIdx.x; item < B; item += gridDim.x) {
-        const int b = chain_at(order, item);
-        const int L = clamp_length(lengths, b, Lmax);
-        const float* ang = angles + (size_t)b * 7 * Lmax;
-        const uint8_t* sq = seq + (size_t)b * Lmax;
-        const float* g_in = grad_coords + (size_t)b * Amax * 3;
-        float* ga = grad_angles + (size_t)b * 7 * Lmax;
-        const int ntiles = (L + NT - 1) / NT;
-
-        // Phase A: frame and atom offset carried into each tile.
-        Rigid carry = rigid_identity();
-        int acarry = 0;
+        const Sum6 own = sum6_add(all, nsum);
+        Sum6 after, total;
+        block_suffix_sum6<NT>(own, s6, after, total);
         if (threadIdx.x == 0) {
-            store_rigid(s_carry[0], carry);
-            s_acarry[0] = 0;
-        }
-        for (int t = 0; t + 1 < ntiles; ++t) {
-            const int j = t * NT + threadIdx.x;
-            const bool valid = j < L;
-            const int type = residue_type(sq, j, valid);
-            float sp, cp, ss, cs;
-            Rigid A = residue_transform(s_tab, ang, Lmax, j, L, sp, cp, ss, cs);
-            Rigid E, T;
-            int a0, atot;
-            block_scan_rigid_count<NT>(A, valid ? s_tab.n_atoms[type] : 0, carry, acarry, s_rig,
-                                       s_cnt, E, a0, T, atot);
-            carry = T;
-            rigid_reortho(carry);
-            acarry = atot;
-            if (threadIdx.x == 0) {
-                store_rigid(s_carry[t + 1], carry);
-                s_acarry[t + 1] = acarry;
-            }
+            const Sum6 suf = lookback_suffix(ws, slot0, t, T, total);
+            s_suf[0] = suf.c.x; s_suf[1] = suf.c.y; s_suf[2] = suf.c.z;
+            s_suf[3] = suf.g.x; s_suf[4] = suf.g.y; s_suf[5] = suf.g.z;
         }
         __syncthreads();
-
-        // Phase B: tiles right to left.
-        Sum6 sfx = sum6_zero();
-        for (int t = ntiles - 1; t >= 0; --t) {
-            carry = load_rigid(s_carry[t]);
-            acarry = s_acarry[t];
-            const int j = t * NT + threadIdx.x;
-            const bool valid = j < L;
-            const int type = residue_type(sq, j, valid);
-            float sp = 0.f, cp = 1.f, ss = 0.f, cs = 1.f;
-            Rigid A = residue_transform(s_tab, ang, Lmax, j, L, sp, cp, ss, cs);
-            Rigid E, T;
-            int a0, atot;
-            block_scan_rigid_count<NT>(A, valid ? s_tab.n_atoms[type] : 0, carry, acarry, s_rig,
-                                       s_cnt, E, a0, T, atot);
-            // stage the tile's upstream gradient
-            {
-                const int n = 3 * max(0, min(atot, Amax) - acarry);
-                const float* src = g_in + 3 * (size_t)acarry;
-                for (int i = threadIdx.x; i < n; i += NT) stage[i] = __ldg(src + i);
-            }
-            __syncthreads();
-            const int base = a0 - acarry;
-            float gchi[kMaxGroups] = {0.f, 0.f, 0.f, 0.f};
-            Sum6 all = sum6_zero(), nsum = sum6_zero(), csum = sum6_zero();
-            float3 u_phi = make_float3(0.f, 0.f, 0.f), p_phi = u_phi, u_psi = u_phi, p_psi = u_phi;
-            const bool in_range = valid && a0 + s_tab.n_atoms[type] <= Amax;
+        Sum6 later;
+        later.c = make_float3(s_suf[0], s_suf[1], s_suf[2]);
+        later.g = make_float3(s_suf[3], s_suf[4], s_suf[5]);
+        after = sum6_add(after, later);
+        if (j < Lmax) {
+            float gphi = 0.f, gpsi = 0.f, gomg = 0.f;
             if (in_range) {
-                auto gat = [&](int slot) {
-                    return make_float3(stage[3 * slot], stage[3 * slot + 1], stage[3 * slot + 2]);
-                };
-                auto add = [](Sum6& s, float3 r, float3 g) {
-                    s.c = f3_add(s.c, f3_cross(r, g));
-                    s.g = f3_add(s.g, g);
-                };
-                // backbone atoms
-                add(nsum, E.t, gat(base + 0));
-                Rigid M1 = E;
-                rigid_mul_R(M1, cp, sp, s_tab.bb.ct[1], s_tab.bb.st[1], s_tab.bb.d[1]);
-                u_phi = M1.c0;
-                p_phi = M1.t;
-                add(all, M1.t, gat(base + 1));
-                Rigid M3 = M1;
-                rigid_mul_R(M3, cs, ss, s_tab.bb.ct[2], s_tab.bb.st[2], s_tab.bb.d[2]);
-                u_psi = M3.c0;
-                p_psi = M3.t;
-                add(csum, M3.t, gat(base + 2));
-                const float4 o = s_tab.o_r0;
-                add(csum, point_apply(M3, make_float3(o.x, o.y, o.z)), gat(base + 3));
-                // side chain: per-group sums, then chi gradients by a suffix over groups
-                Rigid S = M1;
-                rigid_mul_Rx(S, s_tab.rp_c, s_tab.rp_s);
-                const int ng = s_tab.n_groups[type], nchi = s_tab.n_chi[type];
-                float3 gu[kMaxGroups], gp[kMaxGroups];
-                Sum6 gs[kMaxGroups];
-                int e = 0;
-#pragma unroll
-                for (int k = 0; k < kMaxGroups; ++k) {
-                    gs[k] = sum6_zero();
-                    gu[k] = make_float3(0.f, 0.f, 0.f);
-                    gp[k] = gu[k];
-                    if (k < ng) {
-                        float sc, cc;
-                        if (k < nchi) {
-                            sincosf(ang[(3 + k) * Lmax + j], &sc, &cc);
-                        } else {
-                            cc = s_tab.fixchi[type][k].x;
-                            sc = s_tab.fixchi[type][k].y;
-                        }
-                        const float4 gk = s_tab.grp[type][k];
-                        rigid_mul_R(S, cc, sc, gk.x, gk.y, gk.z);
-                        gu[k] = S.c0;
-                        gp[k] = S.t;
-                        const int end = s_tab.grp_end[type][k];
-                        for (; e < end; ++e) {
-                            const float4 r0 = s_tab.side[type][e];
-                            add(gs[k], point_apply(S, make_float3(r0.x, r0.y, r0.z)), gat(base + (int)r0.w));
-                        }
-                    }
+                Sum6 x = sum6_add(csum, after);
+                gpsi = f3_dot(u_psi, f3_sub(x.c, f3_cross(p_psi, x.g)));
+                x = sum6_add(all, after);
+                gphi = f3_dot(u_phi, f3_sub(x.c, f3_cross(p_phi, x.g)));
+                if (j > 0) {
+                    x = sum6_add(own, after);
+                    gomg = f3_dot(E.c0, f3_sub(x.c, f3_cross(E.t, x.g)));
                 }
-                Sum6 suf = sum6_zero();
-#pragma unroll
-                for (int k = kMaxGroups - 1; k >= 0; --k) {
-                    suf = sum6_add(suf, gs[k]);
-                    if (k < nchi) gchi[k] = f3_dot(gu[k], f3_sub(suf.c, f3_cross(gp[k], suf.g)));
-                }
-                // all = CA + side chain + C + O (N kept apart: not downstream of phi)
-                all = sum6_add(sum6_add(all, suf), csum);
             }
-            Sum6 own = sum6_add(all, nsum);
-            Sum6 after, total;
-            block_suffix_sum6<NT>(own, sfx, s6, after, total);
-            if (j < Lmax) {
-                float gphi = 0.f, gpsi = 0.f, gomg = 0.f;
-                if (in_range) {
-                    Sum6 x = sum6_add(csum, after);
-                    gpsi = f3_dot(u_psi, f3_sub(x.c, f3_cross(p_psi, x.g)));
-                    x = sum6_add(all, after);
-                    gphi = f3_dot(u_phi, f3_sub(x.c, f3_cross(p_phi, x.g)));
-                    if (j > 0) {
-                        x = sum6_add(own, after);
-                        gomg = f3_dot(E.c0, f3_sub(x.c, f3_cross(E.t, x.g)));
-                    }
-                }
-                ga[j] = gphi;
-                ga[Lmax + j] = gpsi;
-                ga[2 * Lmax + j] = gomg;
+            ga[j] = gphi;
+            ga[Lmax + j] = gpsi;
+            ga[2 * Lmax + j] = gomg;
 #pragma unroll
-                for (int k = 0; k < kMaxGroups; ++k) ga[(3 + k) * Lmax + j] = gchi[k];
-            }
-            sfx = total;
-            __syncthreads();
+            for (int k = 0; k < kMaxGroups; ++k) ga[(3 + k) * Lmax + j] = gchi[k];
         }
-        const int covered = min(Lmax, ntiles * NT);
-        for (int i = covered + threadIdx.x; i < Lmax; i += NT)
+        if (t == T - 1) {
+            for (int i = min(Lmax, T * NT) + threadIdx.x; i < Lmax; i += NT)
 #pragma unroll
-            for (int r = 0; r < 7; ++r) ga[r * Lmax + i] = 0.f;
+                for (int r = 0; r < 7; ++r) ga[r * Lmax + i] = 0.f;
+        }
     }
 }
 
@@ -528,28 +560,30 @@ cudaError_t smem_attr_once(K kernel, int bytes, bool* done_per_device) {
 }
 
 template <int NT>
-cudaError_t fa_fwd_t(const float* angles, const uint8_t* seq, const int32_t* lengths,
-                     const int32_t* order, int B, int Lmax, int Amax, float* coords,
-                     int32_t* num_atoms, int grid, cudaStream_t s) {
-    const size_t smem = (size_t)NT * kMaxAtoms * 3 * sizeof(float);
+cudaError_t fa_fwd_t(const float* angles, const uint8_t* seq, const int32_t* lengths, int Lmax,
+                     int Amax, float* coords, int32_t* num_atoms, const ChainWs& ws,
+                     cudaStream_t s) {
+    const size_t smem = (size_t)(4 + NT * kMaxAtoms * 3) * sizeof(float);
     static bool done[64] = {false};
     cudaError_t e = smem_attr_once(fa_fwd_kernel<NT>, (int)smem, done);
     if (e != cudaSuccess) return e;
-    fa_fwd_kernel<NT><<<grid, NT, smem, s>>>(angles, seq, lengths, order, B, Lmax, Amax, coords,
-                                             num_atoms, fa_table());
+    const int grid = persistent_grid((const void*)fa_fwd_kernel<NT>, NT, smem);
+    fa_fwd_kernel<NT><<<grid, NT, smem, s>>>(angles, seq, lengths, Lmax, Amax, coords, num_atoms,
+                                             ws, fa_table());
     return cudaGetLastError();
 }
 
 template <int NT>
-cudaError_t fa_bwd_t(const float* angles, const uint8_t* seq, const int32_t* lengths,
-                     const int32_t* order, int B, int Lmax, int Amax, const float* grad_coords,
-                     float* grad_angles, int grid, cudaStream_t s) {
-    const size_t smem = (size_t)NT * kMaxAtoms * 3 * sizeof(float);
+cudaError_t fa_bwd_t(const float* angles, const uint8_t* seq, const int32_t* lengths, int B,
+                     int Lmax, int Amax, const float* grad_coords, float* grad_angles,
+                     const ChainWs& ws, cudaStream_t s) {
+    const size_t smem = (size_t)(4 + NT * kMaxAtoms * 3) * sizeof(float);
     static bool done[64] = {false};
     cudaError_t e = smem_attr_once(fa_bwd_kernel<NT>, (int)smem, done);
     if (e != cudaSuccess) return e;
-    fa_bwd_kernel<NT><<<grid, NT, smem, s>>>(angles, seq, lengths, order, B, Lmax, Amax,
-                                             grad_coords, grad_angles, fa_table());
+    const int grid = persistent_grid((const void*)fa_bwd_kernel<NT>, NT, smem);
+    fa_bwd_kernel<NT><<<grid, NT, smem, s>>>(angles, seq, lengths, B, Lmax, Amax, grad_coords,
+                                             grad_angles, ws, fa_table());
     return cudaGetLastError();
 }
 
@@ -560,34 +594,37 @@ bool fullatom_cfg_supported(int threads) {
 }
 
 cudaError_t launch_fullatom_forward(const float* angles, const uint8_t* seq,
-                                    const int32_t* lengths, const int32_t* order, int B, int Lmax,
-                                    int Amax, float* coords, int32_t* num_atoms, LaunchCfg cfg,
-                                    cudaStream_t s) {
+                                    const int32_t* lengths, int B, int Lmax, int Amax,
+                                    float* coords, int32_t* num_atoms, bool longest_first,
+                                    void* workspace, LaunchCfg cfg, cudaStream_t s) {
     if (B == 0) return cudaSuccess;
-    const int grid = cfg.grid > 0 ? cfg.grid : B;
+    ChainWs ws;
+    chain_ws_layout(workspace, B, Lmax, &ws);
+    cudaError_t e = launch_schedule(lengths, B, Lmax, cfg.threads, longest_first, ws, s);
+    if (e != cudaSuccess) return e;
     switch (cfg.threads) {
-        case 64: return fa_fwd_t<64>(angles, seq, lengths, order, B, Lmax, Amax, coords, num_atoms, grid, s);
-        case 128: return fa_fwd_t<128>(angles, seq, lengths, order, B, Lmax, Amax, coords, num_atoms, grid, s);
-        case 256: return fa_fwd_t<256>(angles, seq, lengths, order, B, Lmax, Amax, coords, num_atoms, grid, s);
-        case 512: return fa_fwd_t<512>(angles, seq, lengths, order, B, Lmax, Amax, coords, num_atoms, grid, s);
+        case 64: return fa_fwd_t<64>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s);
+        case 128: return fa_fwd_t<128>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s);
+        case 256: return fa_fwd_t<256>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s);
+        case 512: return fa_fwd_t<512>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
-                                     const int32_t* lengths, const int32_t* order, int B,
-                                     int Lmax, int Amax, const float* coords,
+                                     const int32_t* lengths, int B, int Lmax, int Amax,
                                      const float* grad_coords, float* grad_angles,
-                                     bool from_coords, LaunchCfg cfg, cudaStream_t s) {
-    (void)coords;
-    if (from_coords) return cudaErrorNotSupported;
+                                     void* workspace, LaunchCfg cfg, cudaStream_t s) {
     if (B == 0) return cudaSuccess;
-    const int grid = cfg.grid > 0 ? cfg.grid : B;
+    ChainWs ws;
+    chain_ws_layout(workspace, B, Lmax, &ws);
+    cudaError_t e = reset_backward_flags(ws, s);
+    if (e != cudaSuccess) return e;
     switch (cfg.threads) {
-        case 64: return fa_bwd_t<64>(angles, seq, lengths, order, B, Lmax, Amax, grad_coords, grad_angles, grid, s);
-        case 128: return fa_bwd_t<128>(angles, seq, lengths, order, B, Lmax, Amax, grad_coords, grad_angles, grid, s);
-        case 256: return fa_bwd_t<256>(angles, seq, lengths, order, B, Lmax, Amax, grad_coords, grad_angles, grid, s);
-        case 512: return fa_bwd_t<512>(angles, seq, lengths, order, B, Lmax, Amax, grad_coords, grad_angles, grid, s);
+        case 64: return fa_bwd_t<64>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);
+        case 128: return fa_bwd_t<128>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);
+        case 256: return fa_bwd_t<256>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);
+        case 512: return fa_bwd_t<512>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);
         default: return cudaErrorInvalidValue;
     }
 }

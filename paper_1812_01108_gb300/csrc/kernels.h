@@ -9,41 +9,34 @@
 namespace tpl {
 
 struct LaunchCfg {
-    int threads;        // CTA size
-    int res_per_thread; // backbone only
-    int grid;           // CTAs (0 = one per chain)
+    int threads;        // CTA size (= residues per tile of the full-atom kernels)
+    int res_per_thread; // backbone only (tile = threads * res_per_thread)
 };
 
-// Largest number of tiles of one chain kept in shared memory by the backward
-// kernels (phase carries); the host rejects Lmax beyond kMaxTiles * tile.
-constexpr int kMaxTiles = 64;
-
-// K8: longest-first chain order (bucketed by length) into `order` [B].
-cudaError_t launch_build_order(const int32_t* lengths, int B, int Lmax, int32_t* order,
-                               cudaStream_t s);
+// Bytes of the chain workspace (tile list, look-back flags and aggregates,
+// tile-start frames) for B chains of at most Lmax residues.
+size_t chain_ws_bytes(int B, int Lmax);
 
 // K1 / K2: backbone FP32 scan kernels.
 bool backbone_cfg_supported(int threads, int res_per_thread);
-cudaError_t launch_backbone_forward(const float* angles, const int32_t* lengths,
-                                    const int32_t* order, int B, int Lmax, float* coords,
+cudaError_t launch_backbone_forward(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                    float* coords, bool longest_first, void* workspace,
                                     LaunchCfg cfg, cudaStream_t s);
-cudaError_t launch_backbone_backward(const float* angles, const int32_t* lengths,
-                                     const int32_t* order, int B, int Lmax,
+cudaError_t launch_backbone_backward(const float* angles, const int32_t* lengths, int B, int Lmax,
                                      const float* coords, const float* grad_coords,
-                                     float* grad_angles, bool from_coords, LaunchCfg cfg,
-                                     cudaStream_t s);
+                                     float* grad_angles, bool from_coords, void* workspace,
+                                     LaunchCfg cfg, cudaStream_t s);
 
 // K3 / K4: full-atom FP32 scan kernels.
 bool fullatom_cfg_supported(int threads);
 cudaError_t launch_fullatom_forward(const float* angles, const uint8_t* seq,
-                                    const int32_t* lengths, const int32_t* order, int B, int Lmax,
-                                    int Amax, float* coords, int32_t* num_atoms, LaunchCfg cfg,
-                                    cudaStream_t s);
+                                    const int32_t* lengths, int B, int Lmax, int Amax,
+                                    float* coords, int32_t* num_atoms, bool longest_first,
+                                    void* workspace, LaunchCfg cfg, cudaStream_t s);
 cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
-                                     const int32_t* lengths, const int32_t* order, int B,
-                                     int Lmax, int Amax, const float* coords,
+                                     const int32_t* lengths, int B, int Lmax, int Amax,
                                      const float* grad_coords, float* grad_angles,
-                                     bool from_coords, LaunchCfg cfg, cudaStream_t s);
+                                     void* workspace, LaunchCfg cfg, cudaStream_t s);
 
 // K5 / K6: LRMSD.  The workspace layout is private to lrmsd.cu.
 size_t lrmsd_ws_bytes(int P, int Nmax);

@@ -138,24 +138,34 @@ __global__ void __launch_bounds__(kNT) lrmsd_moments_kernel(const float* __restr
 // ---------------------------------------------------------------------------
 // K5b
 // ---------------------------------------------------------------------------
-__device__ double det3(double a, double b, double c, double d, double e, double f, double g,
-                       double h, double i) {
-    return a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
-}
-
-// Cofactor (r, c) of the symmetric 4x4 A.
-__device__ double cofactor4(const double (&A)[4][4], int r, int c) {
-    double m[9];
-    int k = 0;
-    for (int i = 0; i < 4; ++i) {
-        if (i == r) continue;
-        for (int j = 0; j < 4; ++j) {
-            if (j == c) continue;
-            m[k++] = A[i][j];
-        }
-    }
-    const double d = det3(m[0], m[1], m[2], m[3], m[4], m[5], m[6], m[7], m[8]);
-    return ((r + c) & 1) ? -d : d;
+// Adjugate of a symmetric 4x4 matrix by Laplace expansion along rows (0,1) |
+// (2,3): the six 2x2 minors of each row pair give every cofactor.  Returns the
+// determinant; adj is written row-major (adj = det * inverse).
+__device__ __forceinline__ double adjugate4(double a00, double a01, double a02, double a03,
+                                            double a11, double a12, double a13, double a22,
+                                            double a23, double a33, double (&m)[16]) {
+    const double a10 = a01, a20 = a02, a21 = a12, a30 = a03, a31 = a13, a32 = a23;
+    const double s0 = a00 * a11 - a10 * a01, s1 = a00 * a12 - a10 * a02, s2 = a00 * a13 - a10 * a03;
+    const double s3 = a01 * a12 - a11 * a02, s4 = a01 * a13 - a11 * a03, s5 = a02 * a13 - a12 * a03;
+    const double c5 = a22 * a33 - a32 * a23, c4 = a21 * a33 - a31 * a23, c3 = a21 * a32 - a31 * a22;
+    const double c2 = a20 * a33 - a30 * a23, c1 = a20 * a32 - a30 * a22, c0 = a20 * a31 - a30 * a21;
+    m[0] = a11 * c5 - a12 * c4 + a13 * c3;
+    m[1] = -a01 * c5 + a02 * c4 - a03 * c3;
+    m[2] = a31 * s5 - a32 * s4 + a33 * s3;
+    m[3] = -a21 * s5 + a22 * s4 - a23 * s3;
+    m[4] = -a10 * c5 + a12 * c2 - a13 * c1;
+    m[5] = a00 * c5 - a02 * c2 + a03 * c1;
+    m[6] = -a30 * s5 + a32 * s2 - a33 * s1;
+    m[7] = a20 * s5 - a22 * s2 + a23 * s1;
+    m[8] = a10 * c4 - a11 * c2 + a13 * c0;
+    m[9] = -a00 * c4 + a01 * c2 - a03 * c0;
+    m[10] = a30 * s4 - a31 * s2 + a33 * s0;
+    m[11] = -a20 * s4 + a21 * s2 - a23 * s0;
+    m[12] = -a10 * c3 + a11 * c1 - a12 * c0;
+    m[13] = a00 * c3 - a01 * c1 + a02 * c0;
+    m[14] = -a30 * s3 + a31 * s1 - a32 * s0;
+    m[15] = a20 * s3 - a21 * s1 + a22 * s0;
+    return s0 * c5 - s1 * c4 + s2 * c3 + s3 * c2 - s4 * c1 + s5 * c0;
 }
 
 __global__ void lrmsd_solve_kernel(const float* __restrict__ input, const float* __restrict__ target,
@@ -168,10 +178,17 @@ __global__ void lrmsd_solve_kernel(const float* __restrict__ input, const float*
     counter[p] = 0;
     float* st = state + 16 * (size_t)p;
     double S[kMom];
+#pragma unroll
     for (int k = 0; k < kMom; ++k) S[k] = 0.0;
     const int nch = num_chunks(n);
-    for (int c = 0; c < nch; ++c)
-        for (int k = 0; k < kMom; ++k) S[k] += (double)part1[((size_t)p * nch_max + c) * 16 + k];
+    for (int c = 0; c < nch; ++c) {
+        const float4* q = reinterpret_cast<const float4*>(part1 + ((size_t)p * nch_max + c) * 16);
+        const float4 v0 = q[0], v1 = q[1], v2 = q[2], v3 = q[3];
+        S[0] += v0.x; S[1] += v0.y; S[2] += v0.z; S[3] += v0.w;
+        S[4] += v1.x; S[5] += v1.y; S[6] += v1.z; S[7] += v1.w;
+        S[8] += v2.x; S[9] += v2.y; S[10] += v2.z; S[11] += v2.w;
+        S[12] += v3.x; S[13] += v3.y; S[14] += v3.z;
+    }
     double U[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
     double xc[3] = {0, 0, 0}, yc[3] = {0, 0, 0};
     if (n > 0) {
@@ -179,6 +196,7 @@ __global__ void lrmsd_solve_kernel(const float* __restrict__ input, const float*
         const float* y = input + (size_t)p * Nmax * 3;
         const double inv = 1.0 / n;
         double mx[3], my[3];
+#pragma unroll
         for (int a = 0; a < 3; ++a) {
             mx[a] = S[a] * inv;
             my[a] = S[3 + a] * inv;
@@ -186,41 +204,25 @@ __global__ void lrmsd_solve_kernel(const float* __restrict__ input, const float*
             yc[a] = (double)y[a] + my[a];
         }
         // centred R_ab = sum x'_a y'_b
-        double R[3][3];
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) R[a][b] = S[6 + 3 * a + b] - n * mx[a] * my[b];
-        // T(R) of Section 4
-        double T[4][4];
-        T[0][0] = R[0][0] + R[1][1] + R[2][2];
-        T[0][1] = T[1][0] = R[1][2] - R[2][1];
-        T[0][2] = T[2][0] = R[2][0] - R[0][2];
-        T[0][3] = T[3][0] = R[0][1] - R[1][0];
-        T[1][1] = R[0][0] - R[1][1] - R[2][2];
-        T[1][2] = T[2][1] = R[0][1] + R[1][0];
-        T[1][3] = T[3][1] = R[0][2] + R[2][0];
-        T[2][2] = -R[0][0] + R[1][1] - R[2][2];
-        T[2][3] = T[3][2] = R[1][2] + R[2][1];
-        T[3][3] = -R[0][0] - R[1][1] + R[2][2];
-        // characteristic polynomial of the trace-free T: l^4 + c2 l^2 + c1 l + c0,
-        // c2 = -tr(T^2)/2, c1 = -tr(T^3)/3, c0 = det T (Newton's identities)
-        double T2[4][4];
-        for (int i = 0; i < 4; ++i)
-            for (int j = 0; j < 4; ++j) {
-                double s = 0.0;
-                for (int k = 0; k < 4; ++k) s += T[i][k] * T[k][j];
-                T2[i][j] = s;
-            }
-        double tr2 = 0.0, tr3 = 0.0;
-        for (int i = 0; i < 4; ++i) {
-            tr2 += T2[i][i];
-            for (int j = 0; j < 4; ++j) tr3 += T2[i][j] * T[j][i];
-        }
-        double det = 0.0;
-        for (int j = 0; j < 4; ++j) det += T[0][j] * cofactor4(T, 0, j);
-        const double c2 = -0.5 * tr2, c1 = -tr3 / 3.0, c0 = det;
-        // Newton from sqrt(tr T^2) >= largest eigenvalue: monotone for a real-rooted polynomial
-        double lam = sqrt(tr2);
-        for (int it = 0; it < 100; ++it) {
+        const double r00 = S[6] - n * mx[0] * my[0], r01 = S[7] - n * mx[0] * my[1], r02 = S[8] - n * mx[0] * my[2];
+        const double r10 = S[9] - n * mx[1] * my[0], r11 = S[10] - n * mx[1] * my[1], r12 = S[11] - n * mx[1] * my[2];
+        const double r20 = S[12] - n * mx[2] * my[0], r21 = S[13] - n * mx[2] * my[1], r22 = S[14] - n * mx[2] * my[2];
+        // T(R) of Section 4 (symmetric, trace 0)
+        const double t00 = r00 + r11 + r22, t01 = r12 - r21, t02 = r20 - r02, t03 = r01 - r10;
+        const double t11 = r00 - r11 - r22, t12 = r01 + r10, t13 = r02 + r20;
+        const double t22 = -r00 + r11 - r22, t23 = r12 + r21, t33 = -r00 - r11 + r22;
+        // characteristic polynomial l^4 + c2 l^2 + c1 l + c0 of T:
+        // c2 = -tr(T^2)/2 = -2 |R|^2, c1 = -tr(T^3)/3 = -8 det R, c0 = det T
+        const double fro = r00 * r00 + r01 * r01 + r02 * r02 + r10 * r10 + r11 * r11 + r12 * r12 +
+                           r20 * r20 + r21 * r21 + r22 * r22;
+        const double detR = r00 * (r11 * r22 - r12 * r21) - r01 * (r10 * r22 - r12 * r20) +
+                            r02 * (r10 * r21 - r11 * r20);
+        double m[16];
+        const double c0 = adjugate4(t00, t01, t02, t03, t11, t12, t13, t22, t23, t33, m);
+        const double c2 = -2.0 * fro, c1 = -8.0 * detR;
+        // Newton from 2|R| = sqrt(tr T^2) >= lambda_max; monotone for a real-rooted polynomial
+        double lam = 2.0 * sqrt(fro);
+        for (int it = 0; it < 60; ++it) {
             const double l2 = lam * lam;
             const double pv = (l2 + c2) * l2 + c1 * lam + c0;
             const double dp = (4.0 * l2 + 2.0 * c2) * lam + c1;
@@ -229,30 +231,26 @@ __global__ void lrmsd_solve_kernel(const float* __restrict__ input, const float*
             lam -= step;
             if (fabs(step) <= 1e-15 * fabs(lam) + 1e-300) break;
         }
-        // eigenvector: largest column of adj(T - lambda I)
-        double A[4][4];
-        for (int i = 0; i < 4; ++i)
-            for (int j = 0; j < 4; ++j) A[i][j] = T[i][j] - (i == j ? lam : 0.0);
-        double best = -1.0, q[4] = {1.0, 0.0, 0.0, 0.0};
-        for (int col = 0; col < 4; ++col) {
-            double v[4], nn = 0.0;
-            for (int r = 0; r < 4; ++r) {
-                v[r] = cofactor4(A, col, r);
-                nn += v[r] * v[r];
-            }
+        // eigenvector of lambda: the largest column of adj(T - lambda I)
+        adjugate4(t00 - lam, t01, t02, t03, t11 - lam, t12, t13, t22 - lam, t23, t33 - lam, m);
+        double q0 = m[0], q1 = m[4], q2 = m[8], q3 = m[12];
+        double best = q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3;
+#pragma unroll
+        for (int col = 1; col < 4; ++col) {
+            const double v0 = m[col], v1 = m[4 + col], v2 = m[8 + col], v3 = m[12 + col];
+            const double nn = v0 * v0 + v1 * v1 + v2 * v2 + v3 * v3;
             if (nn > best) {
                 best = nn;
-                for (int r = 0; r < 4; ++r) q[r] = v[r];
+                q0 = v0; q1 = v1; q2 = v2; q3 = v3;
             }
         }
         if (best > 0.0) {
-            const double s = 1.0 / sqrt(best);
-            for (int r = 0; r < 4; ++r) q[r] *= s;
+            const double s = rsqrt(best);
+            q0 *= s; q1 *= s; q2 *= s; q3 *= s;
         } else {
-            q[0] = 1.0; q[1] = q[2] = q[3] = 0.0;
+            q0 = 1.0; q1 = q2 = q3 = 0.0;
         }
         // U(q) of Section 4
-        const double q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
         U[0] = q0 * q0 + q1 * q1 - q2 * q2 - q3 * q3;
         U[1] = 2.0 * (q1 * q2 - q0 * q3);
         U[2] = 2.0 * (q1 * q3 + q0 * q2);
@@ -263,7 +261,9 @@ __global__ void lrmsd_solve_kernel(const float* __restrict__ input, const float*
         U[7] = 2.0 * (q2 * q3 + q0 * q1);
         U[8] = q0 * q0 - q1 * q1 - q2 * q2 + q3 * q3;
     }
+#pragma unroll
     for (int k = 0; k < 9; ++k) st[k] = (float)U[k];
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
         st[9 + k] = (float)xc[k];
         st[12 + k] = (float)yc[k];

@@ -1,0 +1,198 @@
+// Tile scheduling shared by the chain kernels (backbone and full atom).
+//
+// A chain of L residues is cut into tiles of TILE residues.  A schedule kernel
+// writes the list of (chain, tile) pairs, chains longest first, and zeroes the
+// forward flags and work counter.  The chain kernels are persistent: each CTA
+// takes the next list entry from an atomic counter, so every tile a CTA waits
+// for was taken earlier by a CTA that is running and never waits on a later
+// one (no deadlock, whatever order the hardware starts CTAs in).
+//
+// Cross-tile dependencies use aggregate-only look-back: a tile publishes its
+// own aggregate (flag + data), then combines the aggregates of all the tiles
+// it depends on in a fixed order.  Nothing waits on a wait, and the rounding
+// of the result does not depend on timing (results are deterministic).
+//  - forward: prefix of the rigid transforms (and atom counts) of tiles < t;
+//    the prefix (frame at the tile start) is stored for the backward;
+//  - backward: suffix of the (sum r x g, sum g) of tiles > t, the tiles of a
+//    chain taken last-to-first.
+// Every wait is bounded: after kSpinLimit polls the kernel sets
+// TPL_STATUS_TIMEOUT, takes zero for the missing term and goes on.
+#pragma once
+
+#include "tpl_common.cuh"
+
+namespace tpl {
+
+constexpr int kMinTile = 64;          // smallest tile of any launch shape (sizes the workspace)
+constexpr int kSpinLimit = 1 << 20;   // polls of one flag (x 100 ns sleep) before giving up
+constexpr int kWsMagic = 0x54504c31;  // written by the schedule kernel, checked by the backward
+
+// Header words.
+enum {
+    kHdrTiles = 0,     // number of list entries
+    kHdrFwdNext = 1,   // forward work counter
+    kHdrTile = 2,      // tile size the schedule was built for
+    kHdrMagic = 3,
+    kHdrB = 4,
+    kHdrLmax = 5,
+};
+
+struct ChainWs {
+    int* hdr;        // 64 ints
+    int2* tiles;     // [B * tmax] (chain, tile)
+    int* fflag;      // [B * tmax] forward aggregate flags
+    float4* fagg;    // [B * tmax][4] forward aggregate: rigid (12 floats) + atom count
+    float4* start;   // [B * tmax][4] frame at the tile start + first atom index
+    int* bflag;      // [B * tmax + 4]: backward flags; word B * tmax is the backward work counter
+    float4* bagg;    // [B * tmax][2] backward aggregate (c, g)
+    int tmax;        // tiles per chain for the smallest tile
+    int slots;       // B * tmax
+};
+
+__host__ __device__ inline size_t ws_align(size_t x) { return (x + 255) & ~size_t(255); }
+
+__host__ __device__ inline int ws_tmax(int Lmax) {
+    int t = (Lmax + kMinTile - 1) / kMinTile;
+    return t < 1 ? 1 : t;
+}
+
+// Offsets of the regions; `base` may be null to only size the workspace.
+__host__ __device__ inline size_t chain_ws_layout(void* base, int B, int Lmax, ChainWs* w) {
+    const int tmax = ws_tmax(Lmax);
+    const size_t slots = (size_t)(B > 0 ? B : 1) * tmax;
+    size_t o = 0;
+    const size_t hdr = o; o = ws_align(o + 64 * sizeof(int));
+    const size_t tiles = o; o = ws_align(o + slots * sizeof(int2));
+    const size_t fflag = o; o = ws_align(o + slots * sizeof(int));
+    const size_t fagg = o; o = ws_align(o + slots * 4 * sizeof(float4));
+    const size_t start = o; o = ws_align(o + slots * 4 * sizeof(float4));
+    const size_t bflag = o; o = ws_align(o + (slots + 4) * sizeof(int));
+    const size_t bagg = o; o = ws_align(o + slots * 2 * sizeof(float4));
+    if (w) {
+        char* c = static_cast<char*>(base);
+        w->hdr = reinterpret_cast<int*>(c + hdr);
+        w->tiles = reinterpret_cast<int2*>(c + tiles);
+        w->fflag = reinterpret_cast<int*>(c + fflag);
+        w->fagg = reinterpret_cast<float4*>(c + fagg);
+        w->start = reinterpret_cast<float4*>(c + start);
+        w->bflag = reinterpret_cast<int*>(c + bflag);
+        w->bagg = reinterpret_cast<float4*>(c + bagg);
+        w->tmax = tmax;
+        w->slots = (int)slots;
+    }
+    return o;
+}
+
+// ---------------------------------------------------------------------------
+// flag publication / acquisition (release / acquire at GPU scope)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void flag_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int flag_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded wait for a nonzero flag.  Returns false (and flags the status word)
+// on timeout.
+__device__ __forceinline__ bool wait_flag(const int* p) {
+    for (int it = 0; it < kSpinLimit; ++it) {
+        if (flag_acquire(p) != 0) return true;
+        __nanosleep(100);
+    }
+    flag_status(TPL_STATUS_TIMEOUT);
+    return false;
+}
+
+__device__ __forceinline__ void store_rigid_g(float4* dst, const Rigid& m, int cnt) {
+    dst[0] = make_float4(m.c0.x, m.c0.y, m.c0.z, m.c1.x);
+    dst[1] = make_float4(m.c1.y, m.c1.z, m.c2.x, m.c2.y);
+    dst[2] = make_float4(m.c2.z, m.t.x, m.t.y, m.t.z);
+    dst[3] = make_float4(__int_as_float(cnt), 0.f, 0.f, 0.f);
+}
+
+// L2 reads (the data was written by another CTA of this launch).
+__device__ __forceinline__ Rigid load_rigid_g(const float4* src, int& cnt) {
+    const float4 a = __ldcg(src), b = __ldcg(src + 1), c = __ldcg(src + 2), d = __ldcg(src + 3);
+    Rigid m;
+    m.c0 = make_float3(a.x, a.y, a.z);
+    m.c1 = make_float3(a.w, b.x, b.y);
+    m.c2 = make_float3(b.z, b.w, c.x);
+    m.t = make_float3(c.y, c.z, c.w);
+    cnt = __float_as_int(d.x);
+    return m;
+}
+
+// Plain reads of data written by an earlier launch (the forward's tile starts).
+__device__ __forceinline__ Rigid load_rigid_prev(const float4* src, int& cnt) {
+    const float4 a = src[0], b = src[1], c = src[2], d = src[3];
+    Rigid m;
+    m.c0 = make_float3(a.x, a.y, a.z);
+    m.c1 = make_float3(a.w, b.x, b.y);
+    m.c2 = make_float3(b.z, b.w, c.x);
+    m.t = make_float3(c.y, c.z, c.w);
+    cnt = __float_as_int(d.x);
+    return m;
+}
+
+// Forward look-back (thread 0): publishes this tile's aggregate, then returns
+// the product of the aggregates of tiles 0..t-1 (A_0 (A_1 (... A_{t-1}))) and
+// their atom count.
+__device__ __forceinline__ Rigid lookback_prefix(const ChainWs& ws, int slot0, int t,
+                                                 const Rigid& agg, int agg_cnt, int& pre_cnt) {
+    store_rigid_g(ws.fagg + 4 * (size_t)(slot0 + t), agg, agg_cnt);
+    __threadfence();
+    flag_release(ws.fflag + slot0 + t, 1);
+    Rigid acc = rigid_identity();
+    int cnt = 0;
+    for (int tp = t - 1; tp >= 0; --tp) {
+        if (!wait_flag(ws.fflag + slot0 + tp)) continue;
+        int c;
+        const Rigid a = load_rigid_g(ws.fagg + 4 * (size_t)(slot0 + tp), c);
+        acc = rigid_mul(a, acc);
+        cnt += c;
+    }
+    rigid_reortho(acc);
+    pre_cnt = cnt;
+    return acc;
+}
+
+// Backward look-back (thread 0): publishes this tile's (c, g) total, then
+// returns the sum over tiles t+1..T-1 (added in increasing tile order).
+__device__ __forceinline__ Sum6 lookback_suffix(const ChainWs& ws, int slot0, int t, int T,
+                                                const Sum6& agg) {
+    float4* d = ws.bagg + 2 * (size_t)(slot0 + t);
+    d[0] = make_float4(agg.c.x, agg.c.y, agg.c.z, agg.g.x);
+    d[1] = make_float4(agg.g.y, agg.g.z, 0.f, 0.f);
+    __threadfence();
+    flag_release(ws.bflag + slot0 + t, 1);
+    Sum6 acc = sum6_zero();
+    for (int tp = t + 1; tp < T; ++tp) {
+        if (!wait_flag(ws.bflag + slot0 + tp)) continue;
+        const float4* s = ws.bagg + 2 * (size_t)(slot0 + tp);
+        const float4 a = __ldcg(s), b = __ldcg(s + 1);
+        Sum6 v;
+        v.c = make_float3(a.x, a.y, a.z);
+        v.g = make_float3(a.w, b.x, b.y);
+        acc = sum6_add(acc, v);
+    }
+    return acc;
+}
+
+// Next list entry for this CTA (all threads call; one atomic per CTA).
+__device__ __forceinline__ int next_tile(int* counter, int* s_v) {
+    __syncthreads();
+    if (threadIdx.x == 0) *s_v = atomicAdd(counter, 1);
+    __syncthreads();
+    return *s_v;
+}
+
+// Host side: schedule kernel (api.cu) and the persistent grid size.
+cudaError_t launch_schedule(const int32_t* lengths, int B, int Lmax, int tile, bool longest_first,
+                            const ChainWs& ws, cudaStream_t s);
+cudaError_t reset_backward_flags(const ChainWs& ws, cudaStream_t s);
+int persistent_grid(const void* kernel, int threads, size_t smem);
+
+}  // namespace tpl

@@ -155,16 +155,15 @@ __device__ __forceinline__ Rigid load_rigid(const RigidS& s) {
 
 // ---------------------------------------------------------------------------
 // Block-wide exclusive scan of rigid transforms (product in thread order) and
-// of an int count.  `scratch` must hold NW+1 RigidS and NW+1 ints.  On return
-// `excl` is carry * x_0 * ... * x_{tid-1}, `cnt_excl` is cnt_carry + sum of
-// earlier counts, and `total` / `cnt_total` include every thread.  All threads
-// of the CTA must call it (it has two __syncthreads).
+// of an int count.  `s_rig` / `s_cnt` hold NW+1 entries.  On return `excl` is
+// x_0 * ... * x_{tid-1}, `cnt_excl` the sum of earlier counts, and `total` /
+// `cnt_total` include every thread.  All threads of the CTA must call it (two
+// __syncthreads); the caller composes a carry in front.
 // ---------------------------------------------------------------------------
 template <int NT>
-__device__ __forceinline__ void block_scan_rigid_count(const Rigid& x, int cnt, const Rigid& carry,
-                                                       int cnt_carry, RigidS* s_rig, int* s_cnt,
-                                                       Rigid& excl, int& cnt_excl, Rigid& total,
-                                                       int& cnt_total) {
+__device__ __forceinline__ void block_scan_rigid_count(const Rigid& x, int cnt, RigidS* s_rig,
+                                                       int* s_cnt, Rigid& excl, int& cnt_excl,
+                                                       Rigid& total, int& cnt_total) {
     constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -204,12 +203,12 @@ __device__ __forceinline__ void block_scan_rigid_count(const Rigid& x, int cnt, 
             cex = 0;
         }
         if (lane < NW) {
-            store_rigid(s_rig[lane], rigid_mul(carry, wex));
-            s_cnt[lane] = cnt_carry + cex;
+            store_rigid(s_rig[lane], wex);
+            s_cnt[lane] = cex;
         }
         if (lane == NW - 1) {
-            store_rigid(s_rig[NW], rigid_mul(carry, w));
-            s_cnt[NW] = cnt_carry + cw;
+            store_rigid(s_rig[NW], w);
+            s_cnt[NW] = cw;
         }
     }
     __syncthreads();
@@ -227,8 +226,8 @@ __device__ __forceinline__ void block_scan_rigid_count(const Rigid& x, int cnt, 
 
 // ---------------------------------------------------------------------------
 // Block-wide exclusive REVERSE (suffix) scan of a 6-float sum (r x g, g):
-// `after` = carry + sum over threads with a larger index; `total` = carry +
-// sum over all threads.  scratch: NW+1 float[6].  Two __syncthreads.
+// `after` = sum over threads with a larger index; `total` = sum over all
+// threads.  scratch: NW+1 float[6].  Two __syncthreads.
 // ---------------------------------------------------------------------------
 struct Sum6 {
     float3 c, g;
@@ -258,8 +257,8 @@ __device__ __forceinline__ Sum6 shfl_down_sum6(const Sum6& a, int delta) {
 }
 
 template <int NT>
-__device__ __forceinline__ void block_suffix_sum6(const Sum6& x, const Sum6& carry, float* s6,
-                                                  Sum6& after, Sum6& total) {
+__device__ __forceinline__ void block_suffix_sum6(const Sum6& x, float* s6, Sum6& after,
+                                                  Sum6& total) {
     constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -292,13 +291,13 @@ __device__ __forceinline__ void block_suffix_sum6(const Sum6& x, const Sum6& car
         if (lane >= NW - 1) wex = sum6_zero();
         __syncwarp();
         if (lane < NW) {
-            Sum6 v = sum6_add(carry, wex);
+            const Sum6 v = wex;
             float* p = s6 + 6 * lane;
             p[0] = v.c.x; p[1] = v.c.y; p[2] = v.c.z;
             p[3] = v.g.x; p[4] = v.g.y; p[5] = v.g.z;
         }
         if (lane == 0) {
-            Sum6 v = sum6_add(carry, w);
+            const Sum6 v = w;
             float* p = s6 + 6 * NW;
             p[0] = v.c.x; p[1] = v.c.y; p[2] = v.c.z;
             p[3] = v.g.x; p[4] = v.g.y; p[5] = v.g.z;
@@ -315,13 +314,6 @@ __device__ __forceinline__ void block_suffix_sum6(const Sum6& x, const Sum6& car
     const float* q = s6 + 6 * NW;
     total.c = make_float3(q[0], q[1], q[2]);
     total.g = make_float3(q[3], q[4], q[5]);
-}
-
-// ---------------------------------------------------------------------------
-// Longest-first chain order (built by tpl_build_order) or batch order.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int chain_at(const int32_t* order, int i) {
-    return order ? order[i] : i;
 }
 
 __device__ __forceinline__ int clamp_length(const int32_t* lengths, int b, int Lmax) {

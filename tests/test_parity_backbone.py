@@ -130,3 +130,17 @@ def test_bad_length_sets_status_without_faulting():
     st = tpl.tpl_get_status()
     assert st & tpl.STATUS_BAD_LENGTH
     assert np.all(c32[2] == 0)  # negative length treated as empty
+
+
+def test_backward_without_forward_workspace_flags_and_zeroes():
+    d = require_gpu()
+    tpl.tpl_get_status()
+    lengths = np.array([30, 12], np.int32)
+    a, g = _inputs(lengths, 9)
+    A, Ln = dev(a, d), dev(lengths, d)
+    B, _, Lmax = a.shape
+    ws = torch.zeros(tpl.tpl_backbone_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    ga = torch.full_like(A, float("nan"))
+    tpl.tpl_backbone_backward(A, Ln, None, dev(g, d), ga, ws)
+    assert tpl.tpl_get_status() & tpl.STATUS_BAD_WORKSPACE
+    assert torch.all(ga == 0)

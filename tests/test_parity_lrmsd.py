@@ -50,10 +50,10 @@ def test_matches_oracle_across_chunk_boundaries():
     l32, g32 = _run(x, y, n, w)
     l64 = oracle.lrmsd_forward(x, y, n)
     g64 = oracle.lrmsd_backward(w, x, y, n)
-    big = n >= 4  # 1-3 atoms: LRMSD is ~0 (rounding); compared below
-    assert np.abs(l32 - l64)[big].max() <= LRMSD_TOL
-    assert rel_err(g32[big], g64[big]) <= GRAD_TOL
-    assert np.abs(l32[~big]).max() < 1e-4
+    assert np.abs(l32 - l64).max() <= LRMSD_TOL
+    # 1-2 atoms: the optimal rotation is not unique, so only the value is compared
+    unique = n >= 3
+    assert rel_err(g32[unique], g64[unique]) <= GRAD_TOL
     for p, k in enumerate(n):
         assert np.all(g32[p, k:] == 0)
 
