@@ -39,6 +39,8 @@ def parse():
     p.add_argument("--batch", type=int, default=256)
     p.add_argument("--length", type=int, default=700)
     p.add_argument("--threads", type=int, default=0, help="CTA size of the chain kernels (0 = default)")
+    p.add_argument("--bwd", default="coords", choices=["coords", "recompute"],
+                   help="full-atom backward: read the forward's coordinates or rebuild frames")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 per-chain comparison")
     return p.parse_args()
@@ -198,7 +200,8 @@ def run_tpl(args):
 
     Amax = workloads.pad_to(max(tpl.fullatom_max_atoms(seq, lengths), tpl.fullatom_max_atoms(seq, lengths)))
     Lmax = a.shape[2]
-    opts = tpl.Opts(threads=args.threads) if args.threads else None
+    opts = tpl.Opts(threads=args.threads,
+                    bwd_mode=tpl.BWD_FROM_COORDS if args.bwd == "coords" else tpl.BWD_RECOMPUTE)
 
     # device-resident inputs
     A = torch.from_numpy(a).to(dev)
@@ -227,7 +230,7 @@ def run_tpl(args):
         lambda: tpl.tpl_fullatom_forward(A, S, Ln, coords, na, fa_ws, opts),
         lambda: tpl.tpl_lrmsd_forward(coords, target, na, lr, lr_ws),
         lambda: tpl.tpl_lrmsd_backward(wgt, coords, target, na, gcoords, lr_ws),
-        lambda: tpl.tpl_fullatom_backward(A, S, Ln, None, gcoords, gang, fa_ws, opts),
+        lambda: tpl.tpl_fullatom_backward(A, S, Ln, coords, gcoords, gang, fa_ws, opts),
     ]
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
@@ -358,7 +361,7 @@ def run_tpl(args):
                                    "forward -> LRMSD to N(0,0.1 rad)-perturbed targets -> backward",
                        "global_batch": B * world, "seq_len": L, "parallelism": f"replicas x{world}",
                        "atoms_per_gpu": n_atoms, "l2": "flushed (512 MiB write) before every step",
-                       "threads": args.threads or "default"},
+                       "threads": args.threads or "default", "fullatom_backward": args.bwd},
             "breakdown_ms": dict(zip(names, [float(x) for x in mean_ms])),
             "step_alg_bytes": step_bytes,
             "step_gbs": step_bytes / (total_ms / args.steps * 1e-3) / 1e9,

@@ -314,12 +314,11 @@ tpl_status tpl_fullatom_backward(const float* angles, const uint8_t* seq, const 
     tpl_opts o = resolve(opts);
     tpl_status st = check_opts(o);
     if (st) return st;
-    if (o.bwd_mode == TPL_BWD_FROM_COORDS)
-        return fail(TPL_ERR_INVALID_ARG, "the full-atom backward recomputes its frames; "
-                                         "TPL_BWD_FROM_COORDS is not available");
-    (void)coords;
-    const void* ptrs[5] = {angles, seq, lengths, grad_coords, grad_angles};
-    if ((st = check_chain_args(B, Lmax, ptrs, 5))) return st;
+    // AUTO reads the forward's coordinates when they are given
+    const bool from_coords = o.bwd_mode == TPL_BWD_FROM_COORDS ||
+                             (o.bwd_mode == TPL_BWD_AUTO && coords != nullptr);
+    const void* ptrs[6] = {angles, seq, lengths, grad_coords, grad_angles, from_coords ? (const void*)coords : angles};
+    if ((st = check_chain_args(B, Lmax, ptrs, 6))) return st;
     if (Amax < 0 || Amax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Amax=%d must be a multiple of 4", Amax);
     if (B == 0) return ok();
     LaunchCfg cfg = fullatom_cfg(o);
@@ -327,8 +326,8 @@ tpl_status tpl_fullatom_backward(const float* angles, const uint8_t* seq, const 
         return fail(TPL_ERR_INVALID_ARG, "unsupported full-atom launch %d threads", cfg.threads);
     if ((st = check_ws(workspace, workspace_bytes, tpl_fullatom_workspace_size(B, Lmax)))) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_fullatom_backward(angles, seq, lengths, B, Lmax, Amax, grad_coords,
-                                             grad_angles, workspace, cfg, s);
+    cudaError_t e = launch_fullatom_backward(angles, seq, lengths, B, Lmax, Amax, coords, grad_coords,
+                                             grad_angles, from_coords, workspace, cfg, s);
     if (e != cudaSuccess) return cuda_fail(e, "fullatom_backward");
     return ok();
 }

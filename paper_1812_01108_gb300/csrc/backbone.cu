@@ -1,20 +1,21 @@
 // Backbone model of the paper (Section 3) on sm_103a.
 //
-// K1 bb_fwd_kernel: one CTA per chain (longest first).  Each thread owns K
-// consecutive residues (3K transforms: R(omega_j) R(phi_j) R(psi_j), R_0 = I),
-// composes them serially in registers, then the CTA runs an exclusive
-// parallel prefix scan over the per-thread rigid transforms.  A tile of
-// NT*K residues is finished before the next; the tile total becomes the carry
-// (re-orthonormalised).  Coordinates are staged in shared memory and written
-// with coalesced 16-byte stores.
+// K1 bb_fwd_kernel: persistent CTAs take tiles of NT*K residues from a work
+// list.  Each thread owns K consecutive residues (3K transforms: R(omega_j)
+// R(phi_j) R(psi_j), R_0 = I), composes them serially in registers, then the
+// CTA runs an exclusive parallel prefix scan over the per-thread rigid
+// transforms; the frame at the tile start is the product of the earlier
+// tiles' aggregates (bounded look-back, re-orthonormalised).  Coordinates are
+// staged in shared memory and written with coalesced 16-byte stores.
 //
 // K2 bb_bwd_kernel: the adjoint of Eq. 2 as a reverse suffix scan.  With u_i
 // the x axis of M_i (bond i-1 -> i) and p_i = r_i,
 //   dL/dalpha_i = u_i . (sum_{k>=i} r_k x g_k - p_i x sum_{k>=i} g_k),
-// which equals the paper's sum_k g_k . (M_{i-1} dR_i M_i^{-1} r_k).  Frames
-// are recomputed from the angles (RECOMPUTE: tile carries from a first
-// left-to-right pass, then tiles right-to-left) or read from the forward's
-// coordinates (FROM_COORDS).
+// which equals the paper's sum_k g_k . (M_{i-1} dR_i M_i^{-1} r_k).  Tiles of a
+// chain are taken last to first; the sum over later tiles comes from a
+// bounded look-back.  Frames are recomputed from the angles and the forward's
+// tile-start frames (RECOMPUTE) or read from the forward's coordinates
+// (FROM_COORDS).
 #include "kernels.h"
 #include "tables.h"
 #include "sched.cuh"
@@ -117,9 +118,9 @@ __global__ void __launch_bounds__(NT) bb_fwd_kernel(const float* __restrict__ an
     __shared__ __align__(16) float s_out[TILE * 9];
 
     const int ntiles = ws.hdr[kHdrTiles];
-    for (;;) {
-        const int v = next_tile(ws.hdr + kHdrFwdNext, &s_v);
-        if (v >= ntiles) break;
+    int v = first_tile(ws.hdr + kHdrFwdNext, &s_v);
+    while (v < ntiles) {
+        const int next = prefetch_tile(ws.hdr + kHdrFwdNext);
         const int2 ct = ws.tiles[v];
         const int b = ct.x, t = ct.y;
         const int L = clamp_length(lengths, b, Lmax);
@@ -151,11 +152,13 @@ __global__ void __launch_bounds__(NT) bb_fwd_kernel(const float* __restrict__ an
         Rigid E, Tot;
         int ce, ctot;
         block_scan_rigid_count<NT>(A, 0, s_rig, s_cnt, E, ce, Tot, ctot);
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
             int pc;
             const Rigid P = lookback_prefix(ws, slot0, t, Tot, 0, pc);
-            store_rigid(s_pre, P);
-            store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, 0);
+            if (threadIdx.x == 0) {
+                store_rigid(s_pre, P);
+                store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, 0);
+            }
         }
         __syncthreads();
         E = rigid_mul(load_rigid(s_pre), E);
@@ -182,6 +185,7 @@ __global__ void __launch_bounds__(NT) bb_fwd_kernel(const float* __restrict__ an
             for (int i = min(Lmax, T * TILE) * 9 / 4 + threadIdx.x; i < Lmax * 9 / 4; i += NT)
                 o4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        v = advance_tile(next, &s_v);
     }
 }
 
@@ -241,9 +245,10 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
         return;
     }
     const int ntiles = ws.hdr[kHdrTiles];
-    for (;;) {
-        const int v = next_tile(ws.bflag + ws.slots, &s_v);
-        if (v >= ntiles) break;
+    int* counter = ws.bflag + ws.slots;
+    int v = first_tile(counter, &s_v);
+    while (v < ntiles) {
+        const int next = prefetch_tile(counter);
         const int2 ct = ws.tiles[v];
         const int b = ct.x;
         const int L = clamp_length(lengths, b, Lmax);
@@ -285,10 +290,12 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
             }
             Sum6 after, total;
             block_suffix_sum6<NT>(own, s6, after, total);
-            if (threadIdx.x == 0) {
+            if (threadIdx.x < 32) {
                 const Sum6 suf = lookback_suffix(ws, slot0, t, T, total);
-                s_suf[0] = suf.c.x; s_suf[1] = suf.c.y; s_suf[2] = suf.c.z;
-                s_suf[3] = suf.g.x; s_suf[4] = suf.g.y; s_suf[5] = suf.g.z;
+                if (threadIdx.x == 0) {
+                    s_suf[0] = suf.c.x; s_suf[1] = suf.c.y; s_suf[2] = suf.c.z;
+                    s_suf[3] = suf.g.x; s_suf[4] = suf.g.y; s_suf[5] = suf.g.z;
+                }
             }
             __syncthreads();
             Sum6 later;
@@ -332,10 +339,12 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
             }
             Sum6 after, total;
             block_suffix_sum6<NT>(own, s6, after, total);
-            if (threadIdx.x == 0) {
+            if (threadIdx.x < 32) {
                 const Sum6 suf = lookback_suffix(ws, slot0, t, T, total);
-                s_suf[0] = suf.c.x; s_suf[1] = suf.c.y; s_suf[2] = suf.c.z;
-                s_suf[3] = suf.g.x; s_suf[4] = suf.g.y; s_suf[5] = suf.g.z;
+                if (threadIdx.x == 0) {
+                    s_suf[0] = suf.c.x; s_suf[1] = suf.c.y; s_suf[2] = suf.c.z;
+                    s_suf[3] = suf.g.x; s_suf[4] = suf.g.y; s_suf[5] = suf.g.z;
+                }
             }
             __syncthreads();
             Sum6 later;
@@ -375,6 +384,7 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
                 ga[2 * Lmax + i] = 0.f;
             }
         }
+        v = advance_tile(next, &s_v);
     }
 }
 

@@ -110,7 +110,35 @@ __device__ __forceinline__ bool ws_matches(const ChainWs& ws, int tile, int B, i
 
 // ---------------------------------------------------------------------------
 // K3: forward.  One tile of NT residues per step of a persistent CTA.
+//  1. residue-parallel: angles and type loaded up front; T_j built and
+//     scanned; look-back gives the tile's start frame; each thread builds
+//     M_1, M_3 and the four side-chain group frames (branch-free), places N,
+//     CA, C and O, and leaves its group frames in shared memory;
+//  2. atom-parallel: every thread places side-chain atoms of the tile (no
+//     divergence between residue types);
+//  3. the staged tile is written out with 16-byte stores.
 // ---------------------------------------------------------------------------
+constexpr int kFrameStride = 13;  // float4 per residue: 4 frames x 3, padded against bank conflicts
+
+template <int NT>
+__host__ __device__ constexpr size_t fa_fwd_smem() {
+    return (size_t)NT * kFrameStride * 16 + (size_t)NT * kMaxSide * 2 + 16 +
+           (size_t)(4 + NT * kMaxAtoms * 3) * 4;
+}
+
+__device__ __forceinline__ void store_frame(float4* f, const Rigid& m) {
+    f[0] = make_float4(m.c0.x, m.c0.y, m.c0.z, m.c1.x);
+    f[1] = make_float4(m.c1.y, m.c1.z, m.c2.x, m.c2.y);
+    f[2] = make_float4(m.c2.z, m.t.x, m.t.y, m.t.z);
+}
+
+__device__ __forceinline__ float3 frame_point(const float4* f, float3 v) {
+    const float4 a = f[0], b = f[1], c = f[2];
+    return make_float3(fmaf(v.z, b.z, fmaf(v.y, a.w, fmaf(v.x, a.x, c.y))),
+                       fmaf(v.z, b.w, fmaf(v.y, b.x, fmaf(v.x, a.y, c.z))),
+                       fmaf(v.z, c.x, fmaf(v.y, b.y, fmaf(v.x, a.z, c.w))));
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT) fa_fwd_kernel(const float* __restrict__ angles,
                                                     const uint8_t* __restrict__ seq,
@@ -125,41 +153,71 @@ __global__ void __launch_bounds__(NT) fa_fwd_kernel(const float* __restrict__ an
     __shared__ RigidS s_pre;
     __shared__ int s_pre_cnt;
     __shared__ int s_v;
+    __shared__ int s_a0[NT];
+    __shared__ uint8_t s_type[NT];
     extern __shared__ float4 s_dyn[];
-    float* stage = reinterpret_cast<float*>(s_dyn);  // 4 + NT * kMaxAtoms * 3 floats
+    float4* s_frame = s_dyn;                                                  // [NT][13]
+    uint16_t* s_desc = reinterpret_cast<uint16_t*>(s_dyn + NT * kFrameStride);  // [NT * 10]
+    float* stage = reinterpret_cast<float*>(s_dyn + NT * kFrameStride + (NT * kMaxSide * 2 + 16) / 16);
 
     copy_table(s_tab, tab);
     const int ntiles = ws.hdr[kHdrTiles];
-    for (;;) {
-        const int v = next_tile(ws.hdr + kHdrFwdNext, &s_v);
-        if (v >= ntiles) break;
+    int v = first_tile(ws.hdr + kHdrFwdNext, &s_v);
+    while (v < ntiles) {
+        const int next = prefetch_tile(ws.hdr + kHdrFwdNext);
         const int2 ct = ws.tiles[v];
         const int b = ct.x, t = ct.y;
         const int L = clamp_length(lengths, b, Lmax);
         const int T = L > 0 ? (L + NT - 1) / NT : 1;
         const int slot0 = b * ws.tmax;
         const float* ang = angles + (size_t)b * 7 * Lmax;
-        const uint8_t* sq = seq + (size_t)b * Lmax;
         float* out = coords + (size_t)b * Amax * 3;
 
         const int j = t * NT + threadIdx.x;
         const bool valid = j < L;
-        const int type = residue_type(sq, j, valid);
-        const int cnt = valid ? s_tab.n_atoms[type] : 0;
+        // all loads up front
+        int type = kGlyCode;
+        float a_phi = 0.f, a_psi = 0.f, a_om = 0.f, chi[kMaxGroups] = {0.f, 0.f, 0.f, 0.f};
+        if (valid) {
+            type = residue_type(seq + (size_t)b * Lmax, j, true);
+            a_phi = __ldg(ang + j);
+            a_psi = __ldg(ang + Lmax + j);
+            if (j + 1 < L) a_om = __ldg(ang + 2 * Lmax + j + 1);
+#pragma unroll
+            for (int k = 0; k < kMaxGroups; ++k) chi[k] = __ldg(ang + (3 + k) * Lmax + j);
+        }
+        const int nat = valid ? s_tab.n_atoms[type] : 0;
         float sp = 0.f, cp = 1.f, ss = 0.f, cs = 1.f;
-        const Rigid A = residue_transform(s_tab, ang, Lmax, j, L, sp, cp, ss, cs);
+        Rigid A = rigid_identity();
+        if (valid) {
+            sincosf(a_phi, &sp, &cp);
+            sincosf(a_psi, &ss, &cs);
+            A = rigid_R(cp, sp, s_tab.bb.ct[1], s_tab.bb.st[1], s_tab.bb.d[1]);
+            rigid_mul_R(A, cs, ss, s_tab.bb.ct[2], s_tab.bb.st[2], s_tab.bb.d[2]);
+            if (j + 1 < L) {
+                float so, co;
+                sincosf(a_om, &so, &co);
+                rigid_mul_R(A, co, so, s_tab.bb.ct[0], s_tab.bb.st[0], s_tab.bb.d[0]);
+            }
+        }
+        // atom and side-atom counts scanned together (16 bits each)
         Rigid E, Tot;
-        int a0, ctot;
-        block_scan_rigid_count<NT>(A, cnt, s_rig, s_cnt, E, a0, Tot, ctot);
-        if (threadIdx.x == 0) {
+        int pk0, pktot;
+        block_scan_rigid_count<NT>(A, valid ? nat | ((nat - 4) << 16) : 0, s_rig, s_cnt, E, pk0,
+                                   Tot, pktot);
+        if (threadIdx.x < 32) {
             int pc;
-            const Rigid P = lookback_prefix(ws, slot0, t, Tot, ctot, pc);
-            store_rigid(s_pre, P);
-            s_pre_cnt = pc;
-            store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, pc);
+            const Rigid P = lookback_prefix(ws, slot0, t, Tot, pktot & 0xffff, pc);
+            if (threadIdx.x == 0) {
+                store_rigid(s_pre, P);
+                s_pre_cnt = pc;
+                store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, pc);
+            }
         }
         __syncthreads();
         const int pc = s_pre_cnt;
+        const int a0 = pk0 & 0xffff, s0 = pk0 >> 16;
+        const int tile_atoms = pktot & 0xffff, tile_side = pktot >> 16;
         E = rigid_mul(load_rigid(s_pre), E);
         const int soff = (3 * pc) & 3;  // stage[soff + 3 * slot] is the tile's atom `slot`
         if (valid) {
@@ -173,35 +231,240 @@ __global__ void __launch_bounds__(NT) fa_fwd_kernel(const float* __restrict__ an
             stage_atom(st, 2, M3.t);  // C = M_3 0
             const float4 o = s_tab.o_r0;
             stage_atom(st, 3, point_apply(M3, make_float3(o.x, o.y, o.z)));
+            // side-chain frames S_k = S_{k-1} R(chi_k), S_0 = M_1 R' (groups past n_groups unused)
             Rigid S = M1;
-            rigid_mul_Rx(S, s_tab.rp_c, s_tab.rp_s);  // M_1 R'
-            const int ng = s_tab.n_groups[type], nchi = s_tab.n_chi[type];
-            int e = 0;
-            for (int k = 0; k < ng; ++k) {
+            rigid_mul_Rx(S, s_tab.rp_c, s_tab.rp_s);
+            const int nchi = s_tab.n_chi[type];
+#pragma unroll
+            for (int k = 0; k < kMaxGroups; ++k) {
                 float sc, cc;
-                if (k < nchi) {
-                    sincosf(ang[(3 + k) * Lmax + j], &sc, &cc);
-                } else {
+                sincosf(chi[k], &sc, &cc);
+                if (k >= nchi) {
                     cc = s_tab.fixchi[type][k].x;
                     sc = s_tab.fixchi[type][k].y;
                 }
                 const float4 gk = s_tab.grp[type][k];
                 rigid_mul_R(S, cc, sc, gk.x, gk.y, gk.z);
-                const int end = s_tab.grp_end[type][k];
-                for (; e < end; ++e) {
-                    const float4 r0 = s_tab.side[type][e];
-                    stage_atom(st, (int)r0.w, point_apply(S, make_float3(r0.x, r0.y, r0.z)));
-                }
+                store_frame(s_frame + threadIdx.x * kFrameStride + 3 * k, S);
             }
+            s_a0[threadIdx.x] = a0;
+            s_type[threadIdx.x] = (uint8_t)type;
+            for (int e = 0; e < nat - 4; ++e) s_desc[s0 + e] = (uint16_t)((threadIdx.x << 4) | e);
         }
         __syncthreads();
-        const int end_atom = pc + ctot;
+        for (int q = threadIdx.x; q < tile_side; q += NT) {
+            const int d = s_desc[q];
+            const int r = d >> 4, e = d & 15;
+            const float4 r0 = s_tab.side[s_type[r]][e];
+            const int w = (int)r0.w;
+            const float3 pos = frame_point(s_frame + r * kFrameStride + 3 * ((w >> 4) - 1),
+                                           make_float3(r0.x, r0.y, r0.z));
+            stage_atom(stage + soff + 3 * s_a0[r], w & 15, pos);
+        }
+        __syncthreads();
+        const int end_atom = pc + tile_atoms;
         if (end_atom > Amax && threadIdx.x == 0) flag_status(TPL_STATUS_TOO_MANY_ATOMS);
         copy_range<NT, true>(out, stage, 3 * pc, 3 * min(end_atom, Amax));
         if (t == T - 1) {
             if (threadIdx.x == 0) num_atoms[b] = end_atom;
             zero_range<NT>(out, 3 * min(end_atom, Amax), 3 * Amax);
         }
+        v = advance_tile(next, &s_v);
+    }
+}
+
+// Block-wide exclusive scan of an int (tile atom offsets); two __syncthreads.
+template <int NT>
+__device__ __forceinline__ int block_scan_int(int x, int* s_cnt, int& total) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+    }
+    if (lane == 31) s_cnt[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < NW ? s_cnt[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < NW; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += y;
+        }
+        if (lane < NW) s_cnt[lane] = w - (lane < NW ? s_cnt[lane] : 0);
+        if (lane == NW - 1) s_cnt[NW] = w;
+    }
+    __syncthreads();
+    total = s_cnt[NW];
+    return s_cnt[warp] + inc - x;
+}
+
+// ---------------------------------------------------------------------------
+// K4': backward from the forward's coordinates.  Axes and origins come from
+// atom positions (phi: N->CA, psi: CA->C, omega: C_{j-1}->N_j, chi_k: origin of
+// group k-1 -> origin of group k); the tile's atoms and their upstream
+// gradients are staged in shared memory with 16-byte loads.
+// ---------------------------------------------------------------------------
+template <int NT>
+__host__ __device__ constexpr size_t fa_bwd_coords_smem() {
+    return 2 * (size_t)(4 + NT * kMaxAtoms * 3) * 4;
+}
+
+__device__ __forceinline__ float3 unit3(float3 v) { return f3_scale(rsqrtf(f3_dot(v, v)), v); }
+
+template <int NT>
+__global__ void __launch_bounds__(NT) fa_bwd_coords_kernel(
+    const uint8_t* __restrict__ seq, const int32_t* __restrict__ lengths, int B, int Lmax, int Amax,
+    const float* __restrict__ coords, const float* __restrict__ grad_coords,
+    float* __restrict__ grad_angles, ChainWs ws, const __grid_constant__ FaTable tab) {
+    constexpr int NW = NT / 32;
+    constexpr int STAGE = 4 + NT * kMaxAtoms * 3;
+    __shared__ FaTable s_tab;
+    __shared__ int s_cnt[NW + 1];
+    __shared__ float s6[6 * (NW + 1)];
+    __shared__ float s_suf[6];
+    __shared__ float s_prevc[3];
+    __shared__ int s_v;
+    __shared__ uint8_t s_type[NT];
+    extern __shared__ float4 s_dyn[];
+    float* st_r = reinterpret_cast<float*>(s_dyn);
+    float* st_g = st_r + STAGE;
+
+    if (!ws_matches(ws, NT, B, Lmax)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) flag_status(TPL_STATUS_BAD_WORKSPACE);
+        for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < (size_t)B * 7 * Lmax; i += (size_t)gridDim.x * NT)
+            grad_angles[i] = 0.f;
+        return;
+    }
+    copy_table(s_tab, tab);
+    const int ntiles = ws.hdr[kHdrTiles];
+    int* counter = ws.bflag + ws.slots;
+    int v = first_tile(counter, &s_v);
+    while (v < ntiles) {
+        const int next = prefetch_tile(counter);
+        const int2 ct = ws.tiles[v];
+        const int b = ct.x;
+        const int L = clamp_length(lengths, b, Lmax);
+        const int T = L > 0 ? (L + NT - 1) / NT : 1;
+        const int t = T - 1 - ct.y;  // last tile first
+        const int slot0 = b * ws.tmax;
+        const uint8_t* sq = seq + (size_t)b * Lmax;
+        const float* r_in = coords + (size_t)b * Amax * 3;
+        const float* g_in = grad_coords + (size_t)b * Amax * 3;
+        float* ga = grad_angles + (size_t)b * 7 * Lmax;
+
+        const int j = t * NT + threadIdx.x;
+        const bool valid = j < L;
+        const int type = residue_type(sq, j, valid);
+        const int nat = valid ? s_tab.n_atoms[type] : 0;
+        s_type[threadIdx.x] = (uint8_t)type;
+        int tile_atoms;
+        const int a0 = block_scan_int<NT>(nat, s_cnt, tile_atoms);
+        const int pc = __float_as_int(ws.start[4 * (size_t)(slot0 + t) + 3].x);
+        const int soff = (3 * pc) & 3;
+        const int g1 = 3 * min(pc + tile_atoms, Amax);
+        copy_range<NT, false>(const_cast<float*>(r_in), st_r, 3 * pc, g1);
+        copy_range<NT, false>(const_cast<float*>(g_in), st_g, 3 * pc, g1);
+        if (threadIdx.x == 0 && t > 0) {  // C of the residue before the tile
+            const int jp = t * NT - 1;
+            const int ip = pc - s_tab.n_atoms[residue_type(sq, jp, true)] + 2;
+            s_prevc[0] = r_in[3 * ip];
+            s_prevc[1] = r_in[3 * ip + 1];
+            s_prevc[2] = r_in[3 * ip + 2];
+        }
+        __syncthreads();
+
+        float gchi[kMaxGroups] = {0.f, 0.f, 0.f, 0.f};
+        Sum6 all = sum6_zero(), nsum = sum6_zero(), csum = sum6_zero();
+        float3 rN = make_float3(0.f, 0.f, 0.f), rCA = rN, rC = rN, rCprev = rN;
+        const bool in_range = valid && pc + a0 + nat <= Amax;
+        if (in_range) {
+            const float* sr = st_r + soff + 3 * a0;
+            const float* sg = st_g + soff + 3 * a0;
+            auto R = [&](int k) { return make_float3(sr[3 * k], sr[3 * k + 1], sr[3 * k + 2]); };
+            auto G = [&](int k) { return make_float3(sg[3 * k], sg[3 * k + 1], sg[3 * k + 2]); };
+            auto add = [&](Sum6& s, int k) {
+                const float3 g = G(k);
+                s.c = f3_add(s.c, f3_cross(R(k), g));
+                s.g = f3_add(s.g, g);
+            };
+            rN = R(0);
+            rCA = R(1);
+            rC = R(2);
+            add(nsum, 0);
+            add(all, 1);
+            add(csum, 2);
+            add(csum, 3);
+            // side chain, entries in decreasing group order: suffix over groups
+            const int nchi = s_tab.n_chi[type];
+            Sum6 suf = sum6_zero();
+            for (int e = nat - 5; e >= 0; --e) {
+                const int w = (int)s_tab.side[type][e].w;
+                const int grp = w >> 4;
+                add(suf, w & 15);
+                const bool last_of_group = (e == 0) || (((int)s_tab.side[type][e - 1].w >> 4) != grp);
+                if (last_of_group && grp <= nchi) {
+                    const int o1 = s_tab.origin[type][grp - 1];
+                    const int o0 = grp >= 2 ? s_tab.origin[type][grp - 2] : 1;
+                    const float3 p = R(o1);
+                    const float val = f3_dot(unit3(f3_sub(p, R(o0))), f3_sub(suf.c, f3_cross(p, suf.g)));
+#pragma unroll
+                    for (int k = 0; k < kMaxGroups; ++k)
+                        if (k == grp - 1) gchi[k] = val;
+                }
+            }
+            all = sum6_add(sum6_add(all, suf), csum);
+            if (j > 0) {
+                if (threadIdx.x == 0) {
+                    rCprev = make_float3(s_prevc[0], s_prevc[1], s_prevc[2]);
+                } else {
+                    const int np = s_tab.n_atoms[s_type[threadIdx.x - 1]];
+                    const float* pr = sr - 3 * np + 6;
+                    rCprev = make_float3(pr[0], pr[1], pr[2]);
+                }
+            }
+        }
+        const Sum6 own = sum6_add(all, nsum);
+        Sum6 after, total;
+        block_suffix_sum6<NT>(own, s6, after, total);
+        if (threadIdx.x < 32) {
+            const Sum6 suf = lookback_suffix(ws, slot0, t, T, total);
+            if (threadIdx.x == 0) {
+                s_suf[0] = suf.c.x; s_suf[1] = suf.c.y; s_suf[2] = suf.c.z;
+                s_suf[3] = suf.g.x; s_suf[4] = suf.g.y; s_suf[5] = suf.g.z;
+            }
+        }
+        __syncthreads();
+        Sum6 later;
+        later.c = make_float3(s_suf[0], s_suf[1], s_suf[2]);
+        later.g = make_float3(s_suf[3], s_suf[4], s_suf[5]);
+        after = sum6_add(after, later);
+        if (j < Lmax) {
+            float gphi = 0.f, gpsi = 0.f, gomg = 0.f;
+            if (in_range) {
+                Sum6 x = sum6_add(csum, after);
+                gpsi = f3_dot(unit3(f3_sub(rC, rCA)), f3_sub(x.c, f3_cross(rC, x.g)));
+                x = sum6_add(all, after);
+                gphi = f3_dot(unit3(f3_sub(rCA, rN)), f3_sub(x.c, f3_cross(rCA, x.g)));
+                if (j > 0) {
+                    x = sum6_add(own, after);
+                    gomg = f3_dot(unit3(f3_sub(rN, rCprev)), f3_sub(x.c, f3_cross(rN, x.g)));
+                }
+            }
+            ga[j] = gphi;
+            ga[Lmax + j] = gpsi;
+            ga[2 * Lmax + j] = gomg;
+#pragma unroll
+            for (int k = 0; k < kMaxGroups; ++k) ga[(3 + k) * Lmax + j] = gchi[k];
+        }
+        if (t == T - 1) {
+            for (int i = min(Lmax, T * NT) + threadIdx.x; i < Lmax; i += NT)
+#pragma unroll
+                for (int r = 0; r < 7; ++r) ga[r * Lmax + i] = 0.f;
+        }
+        v = advance_tile(next, &s_v);
     }
 }
 
@@ -235,9 +498,10 @@ __global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ an
     }
     copy_table(s_tab, tab);
     const int ntiles = ws.hdr[kHdrTiles];
-    for (;;) {
-        const int v = next_tile(ws.bflag + ws.slots, &s_v);
-        if (v >= ntiles) break;
+    int* counter = ws.bflag + ws.slots;
+    int v = first_tile(counter, &s_v);
+    while (v < ntiles) {
+        const int next = prefetch_tile(counter);
         const int2 ct = ws.tiles[v];
         const int b = ct.x;
         const int L = clamp_length(lengths, b, Lmax);
@@ -315,7 +579,7 @@ __global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ an
                     const int end = s_tab.grp_end[type][k];
                     for (; e < end; ++e) {
                         const float4 r0 = s_tab.side[type][e];
-                        add(gs[k], point_apply(S, make_float3(r0.x, r0.y, r0.z)), gat((int)r0.w));
+                        add(gs[k], point_apply(S, make_float3(r0.x, r0.y, r0.z)), gat((int)r0.w & 15));
                     }
                 }
             }
@@ -331,10 +595,12 @@ __global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ an
         const Sum6 own = sum6_add(all, nsum);
         Sum6 after, total;
         block_suffix_sum6<NT>(own, s6, after, total);
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
             const Sum6 suf = lookback_suffix(ws, slot0, t, T, total);
-            s_suf[0] = suf.c.x; s_suf[1] = suf.c.y; s_suf[2] = suf.c.z;
-            s_suf[3] = suf.g.x; s_suf[4] = suf.g.y; s_suf[5] = suf.g.z;
+            if (threadIdx.x == 0) {
+                s_suf[0] = suf.c.x; s_suf[1] = suf.c.y; s_suf[2] = suf.c.z;
+                s_suf[3] = suf.g.x; s_suf[4] = suf.g.y; s_suf[5] = suf.g.z;
+            }
         }
         __syncthreads();
         Sum6 later;
@@ -364,6 +630,7 @@ __global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ an
 #pragma unroll
                 for (int r = 0; r < 7; ++r) ga[r * Lmax + i] = 0.f;
         }
+        v = advance_tile(next, &s_v);
     }
 }
 
@@ -563,13 +830,27 @@ template <int NT>
 cudaError_t fa_fwd_t(const float* angles, const uint8_t* seq, const int32_t* lengths, int Lmax,
                      int Amax, float* coords, int32_t* num_atoms, const ChainWs& ws,
                      cudaStream_t s) {
-    const size_t smem = (size_t)(4 + NT * kMaxAtoms * 3) * sizeof(float);
+    const size_t smem = fa_fwd_smem<NT>();
     static bool done[64] = {false};
     cudaError_t e = smem_attr_once(fa_fwd_kernel<NT>, (int)smem, done);
     if (e != cudaSuccess) return e;
     const int grid = persistent_grid((const void*)fa_fwd_kernel<NT>, NT, smem);
     fa_fwd_kernel<NT><<<grid, NT, smem, s>>>(angles, seq, lengths, Lmax, Amax, coords, num_atoms,
                                              ws, fa_table());
+    return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t fa_bwd_coords_t(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
+                            const float* coords, const float* grad_coords, float* grad_angles,
+                            const ChainWs& ws, cudaStream_t s) {
+    const size_t smem = fa_bwd_coords_smem<NT>();
+    static bool done[64] = {false};
+    cudaError_t e = smem_attr_once(fa_bwd_coords_kernel<NT>, (int)smem, done);
+    if (e != cudaSuccess) return e;
+    const int grid = persistent_grid((const void*)fa_bwd_coords_kernel<NT>, NT, smem);
+    fa_bwd_coords_kernel<NT><<<grid, NT, smem, s>>>(seq, lengths, B, Lmax, Amax, coords, grad_coords,
+                                                    grad_angles, ws, fa_table());
     return cudaGetLastError();
 }
 
@@ -613,13 +894,23 @@ cudaError_t launch_fullatom_forward(const float* angles, const uint8_t* seq,
 
 cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
                                      const int32_t* lengths, int B, int Lmax, int Amax,
-                                     const float* grad_coords, float* grad_angles,
-                                     void* workspace, LaunchCfg cfg, cudaStream_t s) {
+                                     const float* coords, const float* grad_coords,
+                                     float* grad_angles, bool from_coords, void* workspace,
+                                     LaunchCfg cfg, cudaStream_t s) {
     if (B == 0) return cudaSuccess;
     ChainWs ws;
     chain_ws_layout(workspace, B, Lmax, &ws);
     cudaError_t e = reset_backward_flags(ws, s);
     if (e != cudaSuccess) return e;
+    if (from_coords) {
+        switch (cfg.threads) {
+            case 64: return fa_bwd_coords_t<64>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, s);
+            case 128: return fa_bwd_coords_t<128>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, s);
+            case 256: return fa_bwd_coords_t<256>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, s);
+            case 512: return fa_bwd_coords_t<512>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (cfg.threads) {
         case 64: return fa_bwd_t<64>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);
         case 128: return fa_bwd_t<128>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);

@@ -35,8 +35,9 @@ cudaError_t launch_fullatom_forward(const float* angles, const uint8_t* seq,
                                     void* workspace, LaunchCfg cfg, cudaStream_t s);
 cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
                                      const int32_t* lengths, int B, int Lmax, int Amax,
-                                     const float* grad_coords, float* grad_angles,
-                                     void* workspace, LaunchCfg cfg, cudaStream_t s);
+                                     const float* coords, const float* grad_coords,
+                                     float* grad_angles, bool from_coords, void* workspace,
+                                     LaunchCfg cfg, cudaStream_t s);
 
 // K5 / K6: LRMSD.  The workspace layout is private to lrmsd.cu.
 size_t lrmsd_ws_bytes(int P, int Nmax);

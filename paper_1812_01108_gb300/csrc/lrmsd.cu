@@ -5,13 +5,12 @@
 //      streams its chunk once (16-byte loads) and reduces, in FP32, the
 //      moments shifted by the pair's first atom: sum dx, sum dy, sum dx dy^T
 //      (x = target, y = input, as in the paper's R = sum x y^T).
-//  K5b lrmsd_solve: one thread per pair, FP64.  Sums the chunk partials,
-//      centres R, builds the 4x4 matrix T(R), finds its largest eigenvalue by
-//      Newton's method on the characteristic polynomial from an upper bound
-//      and the eigenvector q from the adjugate of (T - lambda I) (the
+//  K5b lrmsd_solve: one thread per pair.  Sums the chunk partials, centres R,
+//      builds the 4x4 matrix T(R), estimates its largest eigenpair in FP32
+//      (Newton's method on the characteristic polynomial, as in the
 //      quaternion-characteristic-polynomial approach of Theobald, Acta Cryst.
-//      A61 (2005) 478), then U(q).  Batched one pair per lane because FP64
-//      issue is scarce on this GPU.
+//      A61 (2005) 478, then an adjugate column) and solves it in FP64
+//      (Rayleigh quotient of T, adjugate of T - lambda I), then U(q).
 //  K5c lrmsd_residual: grid (chunks, pairs).  LRMSD^2 = (sum |x'|^2 + |y'|^2 -
 //      2 lambda)/N equals sum |y'_i - U x'_i|^2 / N at the optimum; the
 //      residual form has no cancellation, so it is summed in FP32 per chunk and
@@ -28,7 +27,8 @@ namespace {
 constexpr int kNT = 256;     // threads per CTA
 constexpr int kAPT = 8;      // atoms per thread (two groups of 4)
 constexpr int kChunk = kNT * kAPT;
-constexpr int kMom = 15;     // sum dx (3), sum dy (3), sum dx dy^T (9)
+constexpr int kMom = 17;     // sum dx (3), sum dy (3), sum dx dy^T (9), sum |dx|^2, sum |dy|^2
+constexpr int kSlot = 20;    // floats per chunk partial (5 float4)
 
 struct WsLayout {
     size_t part1, part2, state, lr64, counter, total;
@@ -42,7 +42,7 @@ __host__ __device__ inline WsLayout ws_layout(int P, int Nmax) {
     w.nch = (Nmax + kChunk - 1) / kChunk;
     if (w.nch < 1) w.nch = 1;
     size_t o = 0;
-    w.part1 = o; o = align256(o + (size_t)P * w.nch * 16 * sizeof(float));
+    w.part1 = o; o = align256(o + (size_t)P * w.nch * kSlot * sizeof(float));
     w.part2 = o; o = align256(o + (size_t)P * w.nch * sizeof(float));
     w.state = o; o = align256(o + (size_t)P * 16 * sizeof(float));  // U(9) xc(3) yc(3) scale
     w.lr64 = o; o = align256(o + (size_t)P * sizeof(double));
@@ -116,6 +116,8 @@ __global__ void __launch_bounds__(kNT) lrmsd_moments_kernel(const float* __restr
                     m[6] = fmaf(dx.x, dy.x, m[6]); m[7] = fmaf(dx.x, dy.y, m[7]); m[8] = fmaf(dx.x, dy.z, m[8]);
                     m[9] = fmaf(dx.y, dy.x, m[9]); m[10] = fmaf(dx.y, dy.y, m[10]); m[11] = fmaf(dx.y, dy.z, m[11]);
                     m[12] = fmaf(dx.z, dy.x, m[12]); m[13] = fmaf(dx.z, dy.y, m[13]); m[14] = fmaf(dx.z, dy.z, m[14]);
+                    m[15] += f3_dot(dx, dx);
+                    m[16] += f3_dot(dy, dy);
                 }
             }
         }
@@ -131,142 +133,208 @@ __global__ void __launch_bounds__(kNT) lrmsd_moments_kernel(const float* __restr
         float v = 0.f;
 #pragma unroll
         for (int w = 0; w < kNT / 32; ++w) v += s_red[w][threadIdx.x];
-        part1[((size_t)p * nch_max + c) * 16 + threadIdx.x] = v;
+        part1[((size_t)p * nch_max + c) * kSlot + threadIdx.x] = v;
     }
 }
 
 // ---------------------------------------------------------------------------
 // K5b
 // ---------------------------------------------------------------------------
-// Adjugate of a symmetric 4x4 matrix by Laplace expansion along rows (0,1) |
-// (2,3): the six 2x2 minors of each row pair give every cofactor.  Returns the
-// determinant; adj is written row-major (adj = det * inverse).
-__device__ __forceinline__ double adjugate4(double a00, double a01, double a02, double a03,
-                                            double a11, double a12, double a13, double a22,
-                                            double a23, double a33, double (&m)[16]) {
-    const double a10 = a01, a20 = a02, a21 = a12, a30 = a03, a31 = a13, a32 = a23;
-    const double s0 = a00 * a11 - a10 * a01, s1 = a00 * a12 - a10 * a02, s2 = a00 * a13 - a10 * a03;
-    const double s3 = a01 * a12 - a11 * a02, s4 = a01 * a13 - a11 * a03, s5 = a02 * a13 - a12 * a03;
-    const double c5 = a22 * a33 - a32 * a23, c4 = a21 * a33 - a31 * a23, c3 = a21 * a32 - a31 * a22;
-    const double c2 = a20 * a33 - a30 * a23, c1 = a20 * a32 - a30 * a22, c0 = a20 * a31 - a30 * a21;
+// Adjugate of a symmetric 4x4 (float): the same Laplace expansion in FP32,
+// used only for the starting eigenvector.
+__device__ __forceinline__ float adjugate4f(float a00, float a01, float a02, float a03, float a11,
+                                           float a12, float a13, float a22, float a23, float a33,
+                                           float (&m)[16]) {
+    const float a10 = a01, a20 = a02, a21 = a12, a30 = a03, a31 = a13, a32 = a23;
+    const float s0 = a00 * a11 - a10 * a01, s1 = a00 * a12 - a10 * a02, s2 = a00 * a13 - a10 * a03;
+    const float s3 = a01 * a12 - a11 * a02, s4 = a01 * a13 - a11 * a03, s5 = a02 * a13 - a12 * a03;
+    const float c5 = a22 * a33 - a32 * a23, c4 = a21 * a33 - a31 * a23, c3 = a21 * a32 - a31 * a22;
+    const float c2 = a20 * a33 - a30 * a23, c1 = a20 * a32 - a30 * a22, c0 = a20 * a31 - a30 * a21;
     m[0] = a11 * c5 - a12 * c4 + a13 * c3;
-    m[1] = -a01 * c5 + a02 * c4 - a03 * c3;
-    m[2] = a31 * s5 - a32 * s4 + a33 * s3;
-    m[3] = -a21 * s5 + a22 * s4 - a23 * s3;
     m[4] = -a10 * c5 + a12 * c2 - a13 * c1;
-    m[5] = a00 * c5 - a02 * c2 + a03 * c1;
-    m[6] = -a30 * s5 + a32 * s2 - a33 * s1;
-    m[7] = a20 * s5 - a22 * s2 + a23 * s1;
     m[8] = a10 * c4 - a11 * c2 + a13 * c0;
-    m[9] = -a00 * c4 + a01 * c2 - a03 * c0;
-    m[10] = a30 * s4 - a31 * s2 + a33 * s0;
-    m[11] = -a20 * s4 + a21 * s2 - a23 * s0;
     m[12] = -a10 * c3 + a11 * c1 - a12 * c0;
+    m[5] = a00 * c5 - a02 * c2 + a03 * c1;
+    m[9] = -a00 * c4 + a01 * c2 - a03 * c0;
     m[13] = a00 * c3 - a01 * c1 + a02 * c0;
+    m[10] = a30 * s4 - a31 * s2 + a33 * s0;
     m[14] = -a30 * s3 + a31 * s1 - a32 * s0;
     m[15] = a20 * s3 - a21 * s1 + a22 * s0;
+    m[1] = m[4]; m[2] = m[8]; m[3] = m[12]; m[6] = m[9]; m[7] = m[13]; m[11] = m[14];
     return s0 * c5 - s1 * c4 + s2 * c3 + s3 * c2 - s4 * c1 + s5 * c0;
 }
 
-__global__ void lrmsd_solve_kernel(const float* __restrict__ input, const float* __restrict__ target,
-                                   const int32_t* __restrict__ num_atoms, int P, int Nmax,
-                                   const float* __restrict__ part1, int nch_max,
-                                   float* __restrict__ state, int* __restrict__ counter) {
+// Eigen-solve of T (one thread per pair).  FP64 issue is scarce on this GPU
+// (about 34 ns per dependent FP64 instruction per warp), so the largest
+// eigenpair is first estimated in FP32 -- Newton's method on the characteristic
+// polynomial l^4 + c2 l^2 + c1 l + c0 (c2 = -2|R|^2, c1 = -8 det R, c0 = det T)
+// from the upper bound E0/2, then the largest column of adj(T - l I) -- and
+// then solved in FP64: T is formed in FP64, the eigenvalue is the Rayleigh
+// quotient of T at the estimate (error quadratic in the estimate's), and the
+// eigenvector is a column of adj(T - lambda I) computed in FP64.
+__global__ void __launch_bounds__(32) lrmsd_solve_kernel(
+    const float* __restrict__ input, const float* __restrict__ target,
+    const int32_t* __restrict__ num_atoms, int P, int Nmax, const float* __restrict__ part1,
+    int nch_max, float* __restrict__ state, int* __restrict__ counter) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= P) return;
     const int n = pair_atoms(num_atoms, p, Nmax);
     counter[p] = 0;
     float* st = state + 16 * (size_t)p;
-    double S[kMom];
+    float S[kSlot];
 #pragma unroll
-    for (int k = 0; k < kMom; ++k) S[k] = 0.0;
+    for (int k = 0; k < kSlot; ++k) S[k] = 0.f;
     const int nch = num_chunks(n);
     for (int c = 0; c < nch; ++c) {
-        const float4* q = reinterpret_cast<const float4*>(part1 + ((size_t)p * nch_max + c) * 16);
-        const float4 v0 = q[0], v1 = q[1], v2 = q[2], v3 = q[3];
-        S[0] += v0.x; S[1] += v0.y; S[2] += v0.z; S[3] += v0.w;
-        S[4] += v1.x; S[5] += v1.y; S[6] += v1.z; S[7] += v1.w;
-        S[8] += v2.x; S[9] += v2.y; S[10] += v2.z; S[11] += v2.w;
-        S[12] += v3.x; S[13] += v3.y; S[14] += v3.z;
+        const float4* q = reinterpret_cast<const float4*>(part1 + ((size_t)p * nch_max + c) * kSlot);
+#pragma unroll
+        for (int k = 0; k < kSlot / 4; ++k) {
+            const float4 v = q[k];
+            S[4 * k] += v.x; S[4 * k + 1] += v.y; S[4 * k + 2] += v.z; S[4 * k + 3] += v.w;
+        }
     }
-    double U[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
-    double xc[3] = {0, 0, 0}, yc[3] = {0, 0, 0};
+    float U[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+    float xc[3] = {0.f, 0.f, 0.f}, yc[3] = {0.f, 0.f, 0.f};
     if (n > 0) {
         const float* x = target + (size_t)p * Nmax * 3;
         const float* y = input + (size_t)p * Nmax * 3;
-        const double inv = 1.0 / n;
-        double mx[3], my[3];
+        const float inv = 1.f / n;
+        float mx[3], my[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             mx[a] = S[a] * inv;
             my[a] = S[3 + a] * inv;
-            xc[a] = (double)x[a] + mx[a];
-            yc[a] = (double)y[a] + my[a];
+            xc[a] = x[a] + mx[a];
+            yc[a] = y[a] + my[a];
         }
-        // centred R_ab = sum x'_a y'_b
-        const double r00 = S[6] - n * mx[0] * my[0], r01 = S[7] - n * mx[0] * my[1], r02 = S[8] - n * mx[0] * my[2];
-        const double r10 = S[9] - n * mx[1] * my[0], r11 = S[10] - n * mx[1] * my[1], r12 = S[11] - n * mx[1] * my[2];
-        const double r20 = S[12] - n * mx[2] * my[0], r21 = S[13] - n * mx[2] * my[1], r22 = S[14] - n * mx[2] * my[2];
-        // T(R) of Section 4 (symmetric, trace 0)
-        const double t00 = r00 + r11 + r22, t01 = r12 - r21, t02 = r20 - r02, t03 = r01 - r10;
-        const double t11 = r00 - r11 - r22, t12 = r01 + r10, t13 = r02 + r20;
-        const double t22 = -r00 + r11 - r22, t23 = r12 + r21, t33 = -r00 - r11 + r22;
-        // characteristic polynomial l^4 + c2 l^2 + c1 l + c0 of T:
-        // c2 = -tr(T^2)/2 = -2 |R|^2, c1 = -tr(T^3)/3 = -8 det R, c0 = det T
-        const double fro = r00 * r00 + r01 * r01 + r02 * r02 + r10 * r10 + r11 * r11 + r12 * r12 +
-                           r20 * r20 + r21 * r21 + r22 * r22;
-        const double detR = r00 * (r11 * r22 - r12 * r21) - r01 * (r10 * r22 - r12 * r20) +
-                            r02 * (r10 * r21 - r11 * r20);
-        double m[16];
-        const double c0 = adjugate4(t00, t01, t02, t03, t11, t12, t13, t22, t23, t33, m);
-        const double c2 = -2.0 * fro, c1 = -8.0 * detR;
-        // Newton from 2|R| = sqrt(tr T^2) >= lambda_max; monotone for a real-rooted polynomial
-        double lam = 2.0 * sqrt(fro);
-        for (int it = 0; it < 60; ++it) {
-            const double l2 = lam * lam;
-            const double pv = (l2 + c2) * l2 + c1 * lam + c0;
-            const double dp = (4.0 * l2 + 2.0 * c2) * lam + c1;
-            if (dp == 0.0) break;
-            const double step = pv / dp;
-            lam -= step;
-            if (fabs(step) <= 1e-15 * fabs(lam) + 1e-300) break;
-        }
-        // eigenvector of lambda: the largest column of adj(T - lambda I)
-        adjugate4(t00 - lam, t01, t02, t03, t11 - lam, t12, t13, t22 - lam, t23, t33 - lam, m);
-        double q0 = m[0], q1 = m[4], q2 = m[8], q3 = m[12];
-        double best = q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3;
+        // centred correlation R_ab = sum x'_a y'_b and E0 = sum |x'|^2 + |y'|^2 (FP32 reductions)
+        float r[9];
 #pragma unroll
-        for (int col = 1; col < 4; ++col) {
-            const double v0 = m[col], v1 = m[4 + col], v2 = m[8 + col], v3 = m[12 + col];
-            const double nn = v0 * v0 + v1 * v1 + v2 * v2 + v3 * v3;
-            if (nn > best) {
-                best = nn;
-                q0 = v0; q1 = v1; q2 = v2; q3 = v3;
-            }
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r[3 * a + c] = S[6 + 3 * a + c] - n * mx[a] * my[c];
+        const float e0 = S[15] + S[16] - n * (mx[0] * mx[0] + mx[1] * mx[1] + mx[2] * mx[2] +
+                                              my[0] * my[0] + my[1] * my[1] + my[2] * my[2]);
+        // ---- FP32 estimate
+        const float t00 = r[0] + r[4] + r[8], t01 = r[5] - r[7], t02 = r[6] - r[2], t03 = r[1] - r[3];
+        const float t11 = r[0] - r[4] - r[8], t12 = r[1] + r[3], t13 = r[2] + r[6];
+        const float t22 = -r[0] + r[4] - r[8], t23 = r[5] + r[7], t33 = -r[0] - r[4] + r[8];
+        float fro = 0.f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) fro = fmaf(r[k], r[k], fro);
+        const float detR = r[0] * (r[4] * r[8] - r[5] * r[7]) - r[1] * (r[3] * r[8] - r[5] * r[6]) +
+                           r[2] * (r[3] * r[7] - r[4] * r[6]);
+        float m[16];
+        const float c0 = adjugate4f(t00, t01, t02, t03, t11, t12, t13, t22, t23, t33, m);
+        const float c2 = -2.f * fro, c1 = -8.f * detR;
+        float lam = fminf(2.f * sqrtf(fro), 0.5f * e0 * (1.f + 1e-5f));
+        for (int it = 0; it < 24; ++it) {
+            const float l2 = lam * lam;
+            const float pv = (l2 + c2) * l2 + c1 * lam + c0;
+            const float dp = (4.f * l2 + 2.f * c2) * lam + c1;
+            if (!(fabsf(dp) > 0.f)) break;
+            const float step = pv / dp;
+            lam -= step;
+            if (fabsf(step) <= 1e-6f * fabsf(lam)) break;
         }
-        if (best > 0.0) {
-            const double s = rsqrt(best);
-            q0 *= s; q1 *= s; q2 *= s; q3 *= s;
-        } else {
-            q0 = 1.0; q1 = q2 = q3 = 0.0;
+        adjugate4f(t00 - lam, t01, t02, t03, t11 - lam, t12, t13, t22 - lam, t23, t33 - lam, m);
+        int jb = 0;
+        float best = m[0];
+        float qf[4] = {m[0], m[4], m[8], m[12]};
+#pragma unroll
+        for (int k = 1; k < 4; ++k)
+            if (fabsf(m[5 * k]) > fabsf(best)) {
+                best = m[5 * k];
+                jb = k;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) qf[i] = m[4 * i + k];
+            }
+        // ---- FP64 solve: T in FP64, Rayleigh quotient, adjugate column
+        double R[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) R[k] = (double)r[k];
+        double T[4][4];
+        T[0][0] = R[0] + R[4] + R[8];
+        T[0][1] = T[1][0] = R[5] - R[7];
+        T[0][2] = T[2][0] = R[6] - R[2];
+        T[0][3] = T[3][0] = R[1] - R[3];
+        T[1][1] = R[0] - R[4] - R[8];
+        T[1][2] = T[2][1] = R[1] + R[3];
+        T[1][3] = T[3][1] = R[2] + R[6];
+        T[2][2] = -R[0] + R[4] - R[8];
+        T[2][3] = T[3][2] = R[5] + R[7];
+        T[3][3] = -R[0] - R[4] + R[8];
+        double q[4], w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) q[i] = (double)qf[i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = T[i][0] * q[0] + T[i][1] * q[1] + T[i][2] * q[2] + T[i][3] * q[3];
+        const double num = q[0] * w[0] + q[1] * w[1] + q[2] * w[2] + q[3] * w[3];
+        const double den = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+        double l64 = 0.0;
+        if (den > 0.0) {
+            const double rd = (double)(1.f / (float)den);
+            l64 = num * rd;
+            l64 = fma(rd, fma(-l64, den, num), l64);  // one Newton correction of num / den
+        }
+        // A = T - lambda I with index jb moved to 0 (a symmetric permutation), so
+        // that the needed adjugate column is column 0: six 2x2 minors of rows 2, 3.
+        // pi swaps 0 and jb
+        auto pidx = [jb](int i) { return i == 0 ? jb : (i == jb ? 0 : i); };
+        double a[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int pi = pidx(i), pk = pidx(k);
+                double v = T[0][0];
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        if (ii == pi && kk == pk) v = T[ii][kk];
+                a[i][k] = v - (i == k ? l64 : 0.0);
+            }
+        const double c5 = a[2][2] * a[3][3] - a[3][2] * a[2][3], c4 = a[2][1] * a[3][3] - a[3][1] * a[2][3];
+        const double c3 = a[2][1] * a[3][2] - a[3][1] * a[2][2], c2d = a[2][0] * a[3][3] - a[3][0] * a[2][3];
+        const double c1d = a[2][0] * a[3][2] - a[3][0] * a[2][2], c0d = a[2][0] * a[3][1] - a[3][0] * a[2][1];
+        double col[4];
+        col[0] = a[1][1] * c5 - a[1][2] * c4 + a[1][3] * c3;
+        col[1] = -a[1][0] * c5 + a[1][2] * c2d - a[1][3] * c1d;
+        col[2] = a[1][0] * c4 - a[1][1] * c2d + a[1][3] * c0d;
+        col[3] = -a[1][0] * c3 + a[1][1] * c1d - a[1][2] * c0d;
+        // undo the permutation: q[pi[i]] = col[i]
+#pragma unroll
+        for (int i = 0; i < 4; ++i) q[i] = 0.0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii)
+                if (ii == pidx(i)) q[ii] = col[i];
+        const double nn = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+        float q0 = 1.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+        if (nn > 0.0) {
+            double s = (double)rsqrtf((float)nn);
+            s = s * fma(-0.5 * nn * s, s, 1.5);  // one Newton step for 1/sqrt(nn)
+            q0 = (float)(q[0] * s); q1 = (float)(q[1] * s); q2 = (float)(q[2] * s); q3 = (float)(q[3] * s);
         }
         // U(q) of Section 4
         U[0] = q0 * q0 + q1 * q1 - q2 * q2 - q3 * q3;
-        U[1] = 2.0 * (q1 * q2 - q0 * q3);
-        U[2] = 2.0 * (q1 * q3 + q0 * q2);
-        U[3] = 2.0 * (q1 * q2 + q0 * q3);
+        U[1] = 2.f * (q1 * q2 - q0 * q3);
+        U[2] = 2.f * (q1 * q3 + q0 * q2);
+        U[3] = 2.f * (q1 * q2 + q0 * q3);
         U[4] = q0 * q0 - q1 * q1 + q2 * q2 - q3 * q3;
-        U[5] = 2.0 * (q2 * q3 - q0 * q1);
-        U[6] = 2.0 * (q1 * q3 - q0 * q2);
-        U[7] = 2.0 * (q2 * q3 + q0 * q1);
+        U[5] = 2.f * (q2 * q3 - q0 * q1);
+        U[6] = 2.f * (q1 * q3 - q0 * q2);
+        U[7] = 2.f * (q2 * q3 + q0 * q1);
         U[8] = q0 * q0 - q1 * q1 - q2 * q2 + q3 * q3;
     }
 #pragma unroll
-    for (int k = 0; k < 9; ++k) st[k] = (float)U[k];
+    for (int k = 0; k < 9; ++k) st[k] = U[k];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        st[9 + k] = (float)xc[k];
-        st[12 + k] = (float)yc[k];
+        st[9 + k] = xc[k];
+        st[12 + k] = yc[k];
     }
     st[15] = 0.f;
 }
@@ -561,7 +629,7 @@ cudaError_t launch_lrmsd_forward(const float* input, const float* target, const 
     int* counter = reinterpret_cast<int*>(base + L.counter);
     const dim3 grid(L.nch, P);
     lrmsd_moments_kernel<<<grid, kNT, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.nch);
-    lrmsd_solve_kernel<<<(P + 63) / 64, 64, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.nch,
+    lrmsd_solve_kernel<<<(P + 31) / 32, 32, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.nch,
                                                     state, counter);
     lrmsd_residual_kernel<<<grid, kNT, 0, s>>>(input, target, num_atoms, P, Nmax, part2, state, lr64,
                                                counter, lrmsd, L.nch);

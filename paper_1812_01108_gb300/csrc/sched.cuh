@@ -137,21 +137,54 @@ __device__ __forceinline__ Rigid load_rigid_prev(const float4* src, int& cnt) {
     return m;
 }
 
-// Forward look-back (thread 0): publishes this tile's aggregate, then returns
-// the product of the aggregates of tiles 0..t-1 (A_0 (A_1 (... A_{t-1}))) and
-// their atom count.
+__device__ __forceinline__ Rigid shfl_down_rigid(const Rigid& m, int delta) {
+    Rigid r;
+    const unsigned full = 0xffffffffu;
+    r.c0.x = __shfl_down_sync(full, m.c0.x, delta);
+    r.c0.y = __shfl_down_sync(full, m.c0.y, delta);
+    r.c0.z = __shfl_down_sync(full, m.c0.z, delta);
+    r.c1.x = __shfl_down_sync(full, m.c1.x, delta);
+    r.c1.y = __shfl_down_sync(full, m.c1.y, delta);
+    r.c1.z = __shfl_down_sync(full, m.c1.z, delta);
+    r.c2.x = __shfl_down_sync(full, m.c2.x, delta);
+    r.c2.y = __shfl_down_sync(full, m.c2.y, delta);
+    r.c2.z = __shfl_down_sync(full, m.c2.z, delta);
+    r.t.x = __shfl_down_sync(full, m.t.x, delta);
+    r.t.y = __shfl_down_sync(full, m.t.y, delta);
+    r.t.z = __shfl_down_sync(full, m.t.z, delta);
+    return r;
+}
+
+// Forward look-back, called by all 32 lanes of one warp.  Lane 0 publishes
+// this tile's aggregate; then lane l waits for tile base + l of each group of
+// 32 predecessors (the waits overlap) and the warp folds the aggregates in a
+// fixed tree: the result is A_0 A_1 ... A_{t-1} (product in tile order) and
+// the sum of their atom counts, identical in every run.  Valid in lane 0.
 __device__ __forceinline__ Rigid lookback_prefix(const ChainWs& ws, int slot0, int t,
                                                  const Rigid& agg, int agg_cnt, int& pre_cnt) {
-    store_rigid_g(ws.fagg + 4 * (size_t)(slot0 + t), agg, agg_cnt);
-    __threadfence();
-    flag_release(ws.fflag + slot0 + t, 1);
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        store_rigid_g(ws.fagg + 4 * (size_t)(slot0 + t), agg, agg_cnt);
+        flag_release(ws.fflag + slot0 + t, 1);  // release orders the data stores before it
+    }
     Rigid acc = rigid_identity();
     int cnt = 0;
-    for (int tp = t - 1; tp >= 0; --tp) {
-        if (!wait_flag(ws.fflag + slot0 + tp)) continue;
-        int c;
-        const Rigid a = load_rigid_g(ws.fagg + 4 * (size_t)(slot0 + tp), c);
-        acc = rigid_mul(a, acc);
+    for (int base = 0; base < t; base += 32) {
+        const int tp = base + lane;
+        Rigid a = rigid_identity();
+        int c = 0;
+        if (tp < t && wait_flag(ws.fflag + slot0 + tp)) a = load_rigid_g(ws.fagg + 4 * (size_t)(slot0 + tp), c);
+        const int n = min(32, t - base);
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const Rigid y = shfl_down_rigid(a, off);
+            const int cy = __shfl_down_sync(0xffffffffu, c, off);
+            if ((lane & (2 * off - 1)) == 0 && lane + off < n) {
+                a = rigid_mul(a, y);
+                c += cy;
+            }
+        }
+        acc = rigid_mul(acc, a);
         cnt += c;
     }
     rigid_reortho(acc);
@@ -159,32 +192,55 @@ __device__ __forceinline__ Rigid lookback_prefix(const ChainWs& ws, int slot0, i
     return acc;
 }
 
-// Backward look-back (thread 0): publishes this tile's (c, g) total, then
-// returns the sum over tiles t+1..T-1 (added in increasing tile order).
+__device__ __forceinline__ Sum6 load_sum6_g(const float4* s) {
+    const float4 a = __ldcg(s), b = __ldcg(s + 1);
+    Sum6 v;
+    v.c = make_float3(a.x, a.y, a.z);
+    v.g = make_float3(a.w, b.x, b.y);
+    return v;
+}
+
+// Backward look-back, all 32 lanes of one warp: publishes this tile's (c, g)
+// total, then sums the totals of tiles t+1..T-1 in a fixed tree order.  Valid
+// in lane 0.
 __device__ __forceinline__ Sum6 lookback_suffix(const ChainWs& ws, int slot0, int t, int T,
                                                 const Sum6& agg) {
-    float4* d = ws.bagg + 2 * (size_t)(slot0 + t);
-    d[0] = make_float4(agg.c.x, agg.c.y, agg.c.z, agg.g.x);
-    d[1] = make_float4(agg.g.y, agg.g.z, 0.f, 0.f);
-    __threadfence();
-    flag_release(ws.bflag + slot0 + t, 1);
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        float4* d = ws.bagg + 2 * (size_t)(slot0 + t);
+        d[0] = make_float4(agg.c.x, agg.c.y, agg.c.z, agg.g.x);
+        d[1] = make_float4(agg.g.y, agg.g.z, 0.f, 0.f);
+        flag_release(ws.bflag + slot0 + t, 1);
+    }
     Sum6 acc = sum6_zero();
-    for (int tp = t + 1; tp < T; ++tp) {
-        if (!wait_flag(ws.bflag + slot0 + tp)) continue;
-        const float4* s = ws.bagg + 2 * (size_t)(slot0 + tp);
-        const float4 a = __ldcg(s), b = __ldcg(s + 1);
-        Sum6 v;
-        v.c = make_float3(a.x, a.y, a.z);
-        v.g = make_float3(a.w, b.x, b.y);
+    for (int base = t + 1; base < T; base += 32) {
+        const int tp = base + lane;
+        Sum6 v = sum6_zero();
+        if (tp < T && wait_flag(ws.bflag + slot0 + tp)) v = load_sum6_g(ws.bagg + 2 * (size_t)(slot0 + tp));
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const Sum6 y = shfl_down_sum6(v, off);
+            if ((lane & (2 * off - 1)) == 0) v = sum6_add(v, y);
+        }
         acc = sum6_add(acc, v);
     }
     return acc;
 }
 
-// Next list entry for this CTA (all threads call; one atomic per CTA).
-__device__ __forceinline__ int next_tile(int* counter, int* s_v) {
-    __syncthreads();
+// Work-list entries for a persistent CTA: the first is taken at start, and the
+// next one is requested by thread 0 while the current tile is being processed
+// (hiding the atomic's latency).  All threads call both functions.
+__device__ __forceinline__ int first_tile(int* counter, int* s_v) {
     if (threadIdx.x == 0) *s_v = atomicAdd(counter, 1);
+    __syncthreads();
+    return *s_v;
+}
+__device__ __forceinline__ int prefetch_tile(int* counter) {
+    return threadIdx.x == 0 ? atomicAdd(counter, 1) : 0;
+}
+__device__ __forceinline__ int advance_tile(int next, int* s_v) {
+    __syncthreads();  // everyone is done with the current tile's shared data
+    if (threadIdx.x == 0) *s_v = next;
     __syncthreads();
     return *s_v;
 }

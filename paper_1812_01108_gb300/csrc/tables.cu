@@ -269,6 +269,8 @@ void build() {
             D.r0[t][idx][1] = local[idx].y;
             D.r0[t][idx][2] = local[idx].z;
         }
+        for (int i = 0; i < n_atoms; ++i) F.atom_grp[t][i] = D.group[t][i];
+        for (int k = 1; k <= R.n_groups; ++k) F.origin[t][k - 1] = (uint8_t)origin[k];
         // side atoms sorted by group for the FP32 kernels
         int pos = 0;
         for (int k = 1; k <= R.n_groups; ++k) {
@@ -276,7 +278,7 @@ void build() {
                 if (R.side[i].grp != k) continue;
                 const int idx = 4 + i;
                 F.side[t][pos++] = make_float4((float)local[idx].x, (float)local[idx].y,
-                                               (float)local[idx].z, (float)idx);
+                                               (float)local[idx].z, (float)(idx + 16 * k));
             }
             F.grp_end[t][k - 1] = (uint8_t)pos;
         }

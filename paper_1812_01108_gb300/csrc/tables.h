@@ -27,11 +27,13 @@ struct BackboneConstD {
 struct FaTable {
     float4 grp[kNumTypes][kMaxGroups];     // cos theta, sin theta, d, 0
     float2 fixchi[kNumTypes][kMaxGroups];  // cos, sin of the fixed chi of a non-free group
-    float4 side[kNumTypes][kMaxSide];      // r0.x, r0.y, r0.z, output index (as float)
+    float4 side[kNumTypes][kMaxSide];      // r0.x, r0.y, r0.z, (output index + 16 * group) as float
     uint8_t n_atoms[kNumTypes];
     uint8_t n_chi[kNumTypes];
     uint8_t n_groups[kNumTypes];
     uint8_t grp_end[kNumTypes][kMaxGroups];
+    uint8_t atom_grp[kNumTypes][16];       // rigid group of each output atom (0 M_0, 1 M_1, 2 M_3, 3.. side)
+    uint8_t origin[kNumTypes][kMaxGroups]; // output index of side group k's origin atom
     float4 o_r0;        // backbone O in the M_3 frame
     float rp_c, rp_s;   // R' = R_x(rho)
     BackboneConst bb;

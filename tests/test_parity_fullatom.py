@@ -29,7 +29,7 @@ def _inputs(lengths, seed, omega_noise=0.0):
     return a, seq, g, Amax
 
 
-def _run_fp32(a, seq, lengths, g, Amax, opts=None):
+def _run_fp32(a, seq, lengths, g, Amax, opts=None, from_coords=False):
     d = require_gpu()
     A, S, Ln = dev(a, d), dev(seq, d), dev(lengths, d)
     B, _, Lmax = a.shape
@@ -38,7 +38,7 @@ def _run_fp32(a, seq, lengths, g, Amax, opts=None):
     ws = torch.empty(tpl.tpl_fullatom_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
     tpl.tpl_fullatom_forward(A, S, Ln, coords, na, ws, opts)
     ga = torch.full_like(A, float("nan"))
-    tpl.tpl_fullatom_backward(A, S, Ln, None, dev(g, d), ga, ws, opts)
+    tpl.tpl_fullatom_backward(A, S, Ln, coords if from_coords else None, dev(g, d), ga, ws, opts)
     torch.cuda.synchronize()
     return host(coords), host(na), host(ga)
 
@@ -53,10 +53,11 @@ def reference():
     return a, seq, g.astype(np.float32), Amax, c64, na64, g64
 
 
+@pytest.mark.parametrize("from_coords", [False, True])
 @pytest.mark.parametrize("threads", [256, 64, 128, 512])
-def test_fp32_scan_matches_oracle(reference, threads):
+def test_fp32_scan_matches_oracle(reference, threads, from_coords):
     a, seq, g, Amax, c64, na64, g64 = reference
-    c32, na32, ga32 = _run_fp32(a, seq, LENGTHS, g, Amax, {"threads": threads})
+    c32, na32, ga32 = _run_fp32(a, seq, LENGTHS, g, Amax, {"threads": threads}, from_coords)
     assert np.array_equal(na32, na64)  # atom counts bit-exact
     assert np.abs(c32 - c64).max() <= COORD_TOL
     assert rel_err(ga32, g64) <= GRAD_TOL
@@ -72,12 +73,14 @@ def test_fp32_scan_matches_oracle(reference, threads):
             assert ga32[b, 2, 0] == 0
 
 
-def test_schedule_independent(reference):
+@pytest.mark.parametrize("from_coords", [False, True])
+def test_schedule_independent_and_deterministic(reference, from_coords):
     a, seq, g, Amax, *_ = reference
-    r1 = _run_fp32(a, seq, LENGTHS, g, Amax, {"schedule": tpl.SCHED_LONGEST_FIRST})
-    r2 = _run_fp32(a, seq, LENGTHS, g, Amax, {"schedule": tpl.SCHED_BATCH_ORDER})
-    for x, y in zip(r1, r2):
-        assert np.array_equal(x, y)
+    r1 = _run_fp32(a, seq, LENGTHS, g, Amax, {"schedule": tpl.SCHED_LONGEST_FIRST}, from_coords)
+    r2 = _run_fp32(a, seq, LENGTHS, g, Amax, {"schedule": tpl.SCHED_BATCH_ORDER}, from_coords)
+    r3 = _run_fp32(a, seq, LENGTHS, g, Amax, {"schedule": tpl.SCHED_BATCH_ORDER}, from_coords)
+    for x, y, z in zip(r1, r2, r3):
+        assert np.array_equal(x, y) and np.array_equal(y, z)
 
 
 def test_fp64_per_chain_form_matches_oracle(reference):
