@@ -113,14 +113,12 @@ __global__ void __launch_bounds__(NT) bb_fwd_kernel(const float* __restrict__ an
     constexpr int TILE = NT * K;
     __shared__ RigidS s_rig[NW + 1];
     __shared__ int s_cnt[NW + 1];
-    __shared__ RigidS s_pre;
     __shared__ int s_v;
     __shared__ __align__(16) float s_out[TILE * 9];
 
     const int ntiles = ws.hdr[kHdrTiles];
-    int v = first_tile(ws.hdr + kHdrFwdNext, &s_v);
+    int v = take_tile(ws.hdr + kHdrFwdNext, &s_v);
     while (v < ntiles) {
-        const int next = prefetch_tile(ws.hdr + kHdrFwdNext);
         const int2 ct = ws.tiles[v];
         const int b = ct.x, t = ct.y;
         const int L = clamp_length(lengths, b, Lmax);
@@ -152,16 +150,12 @@ __global__ void __launch_bounds__(NT) bb_fwd_kernel(const float* __restrict__ an
         Rigid E, Tot;
         int ce, ctot;
         block_scan_rigid_count<NT>(A, 0, s_rig, s_cnt, E, ce, Tot, ctot);
-        if (threadIdx.x < 32) {
-            int pc;
-            const Rigid P = lookback_prefix(ws, slot0, t, Tot, 0, pc);
-            if (threadIdx.x == 0) {
-                store_rigid(s_pre, P);
-                store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, 0);
-            }
-        }
-        __syncthreads();
-        E = rigid_mul(load_rigid(s_pre), E);
+        if (threadIdx.x == NT - 32) publish_prefix_agg(ws, slot0 + t, Tot, 0);
+        const int requested = request_tile(ws.hdr + kHdrFwdNext);
+        int pc;
+        const Rigid P = gather_prefix(ws, slot0, t, pc);  // every warp gathers it
+        if (threadIdx.x == 0) store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, 0);
+        E = rigid_mul(P, E);
         float vv[9 * K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -185,7 +179,7 @@ __global__ void __launch_bounds__(NT) bb_fwd_kernel(const float* __restrict__ an
             for (int i = min(Lmax, T * TILE) * 9 / 4 + threadIdx.x; i < Lmax * 9 / 4; i += NT)
                 o4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        v = advance_tile(next, &s_v);
+        v = next_tile(requested, &s_v);
     }
 }
 
@@ -234,7 +228,6 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
     __shared__ RigidS s_rig[NW + 1];
     __shared__ int s_cnt[NW + 1];
     __shared__ float s6[6 * (NW + 1)];
-    __shared__ float s_suf[6];
     __shared__ int s_v;
 
     const bool ok = ws_matches(ws, TILE, B, Lmax);
@@ -246,9 +239,8 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
     }
     const int ntiles = ws.hdr[kHdrTiles];
     int* counter = ws.bflag + ws.slots;
-    int v = first_tile(counter, &s_v);
+    int v = take_tile(counter, &s_v);
     while (v < ntiles) {
-        const int next = prefetch_tile(counter);
         const int2 ct = ws.tiles[v];
         const int b = ct.x;
         const int L = clamp_length(lengths, b, Lmax);
@@ -257,6 +249,7 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
         const int slot0 = b * ws.tmax;
         const float* ang = angles + (size_t)b * 3 * Lmax;
         const float* g_in = grad_coords + (size_t)b * 9 * Lmax;
+        int requested = 0;
         float* ga = grad_angles + (size_t)b * 3 * Lmax;
         const int j0 = t * TILE + threadIdx.x * K;
 
@@ -290,17 +283,9 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
             }
             Sum6 after, total;
             block_suffix_sum6<NT>(own, s6, after, total);
-            if (threadIdx.x < 32) {
-                const Sum6 suf = lookback_suffix(ws, slot0, t, T, total);
-                if (threadIdx.x == 0) {
-                    s_suf[0] = suf.c.x; s_suf[1] = suf.c.y; s_suf[2] = suf.c.z;
-                    s_suf[3] = suf.g.x; s_suf[4] = suf.g.y; s_suf[5] = suf.g.z;
-                }
-            }
-            __syncthreads();
-            Sum6 later;
-            later.c = make_float3(s_suf[0], s_suf[1], s_suf[2]);
-            later.g = make_float3(s_suf[3], s_suf[4], s_suf[5]);
+            if (threadIdx.x == NT - 32) publish_suffix_agg(ws, slot0 + t, total);
+            requested = request_tile(counter);
+            const Sum6 later = gather_suffix(ws, slot0, t, T);  // every warp gathers it
             // pass 2: gradients, atoms ascending with S = sum over atoms >= current
             Sum6 S = sum6_add(sum6_add(after, later), own);
             M = E;
@@ -339,17 +324,9 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
             }
             Sum6 after, total;
             block_suffix_sum6<NT>(own, s6, after, total);
-            if (threadIdx.x < 32) {
-                const Sum6 suf = lookback_suffix(ws, slot0, t, T, total);
-                if (threadIdx.x == 0) {
-                    s_suf[0] = suf.c.x; s_suf[1] = suf.c.y; s_suf[2] = suf.c.z;
-                    s_suf[3] = suf.g.x; s_suf[4] = suf.g.y; s_suf[5] = suf.g.z;
-                }
-            }
-            __syncthreads();
-            Sum6 later;
-            later.c = make_float3(s_suf[0], s_suf[1], s_suf[2]);
-            later.g = make_float3(s_suf[3], s_suf[4], s_suf[5]);
+            if (threadIdx.x == NT - 32) publish_suffix_agg(ws, slot0 + t, total);
+            requested = request_tile(counter);
+            const Sum6 later = gather_suffix(ws, slot0, t, T);  // every warp gathers it
             Sum6 S = sum6_add(sum6_add(after, later), own);
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -384,7 +361,7 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
                 ga[2 * Lmax + i] = 0.f;
             }
         }
-        v = advance_tile(next, &s_v);
+        v = next_tile(requested, &s_v);
     }
 }
 

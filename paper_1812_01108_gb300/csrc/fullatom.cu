@@ -92,6 +92,58 @@ __device__ __forceinline__ void copy_range(float* __restrict__ glob, float* __re
     }
 }
 
+// Store of the float range [g0, g1) from a shared buffer with stage[i - g0] <->
+// global[i]: 16-byte aligned global stores, gathered from shared memory.
+template <int NT>
+__device__ __forceinline__ void store_range(float* __restrict__ glob, const float* __restrict__ stage,
+                                            int g0, int g1) {
+    if (g1 <= g0) return;
+    const int head = min(g1, (g0 + 3) & ~3);
+    const int tail = max(head, g1 & ~3);
+    for (int i = g0 + threadIdx.x; i < head; i += NT) glob[i] = stage[i - g0];
+    for (int q = head / 4 + threadIdx.x; q < tail / 4; q += NT) {
+        const float* sp = stage + 4 * q - g0;
+        reinterpret_cast<float4*>(glob)[q] = make_float4(sp[0], sp[1], sp[2], sp[3]);
+    }
+    for (int i = tail + threadIdx.x; i < g1; i += NT) glob[i] = stage[i - g0];
+}
+
+// Store of the float range [g0, g1) of tile-local atom coordinates stage[i -
+// g0] (3 floats per atom), each atom mapped by P on the way: 16-byte aligned
+// global stores; an aligned chunk spans at most two atoms.
+template <int NT>
+__device__ __forceinline__ void store_range_transformed(float* __restrict__ glob,
+                                                        const float* __restrict__ stage,
+                                                        const Rigid& P, int g0, int g1) {
+    if (g1 <= g0) return;
+    auto atom = [&](int a) {
+        return point_apply(P, make_float3(stage[3 * a], stage[3 * a + 1], stage[3 * a + 2]));
+    };
+    auto comp = [](float3 r, int c) { return c == 0 ? r.x : (c == 1 ? r.y : r.z); };
+    const int head = min(g1, (g0 + 3) & ~3);
+    const int tail = max(head, g1 & ~3);
+    for (int i = g0 + threadIdx.x; i < head; i += NT) {
+        const int f = i - g0;
+        glob[i] = comp(atom(f / 3), f % 3);
+    }
+    for (int q = head / 4 + threadIdx.x; q < tail / 4; q += NT) {
+        const int f = 4 * q - g0;
+        const int a0 = f / 3, c0 = f - 3 * a0;
+        const float3 r0 = atom(a0), r1 = atom(a0 + 1);
+        float v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = c0 + k;
+            v[k] = c < 3 ? comp(r0, c) : comp(r1, c - 3);
+        }
+        reinterpret_cast<float4*>(glob)[q] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+    for (int i = tail + threadIdx.x; i < g1; i += NT) {
+        const int f = i - g0;
+        glob[i] = comp(atom(f / 3), f % 3);
+    }
+}
+
 template <int NT>
 __device__ __forceinline__ void zero_range(float* __restrict__ glob, int g0, int g1) {
     if (g1 <= g0) return;
@@ -140,18 +192,16 @@ __device__ __forceinline__ float3 frame_point(const float4* f, float3 v) {
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT) fa_fwd_kernel(const float* __restrict__ angles,
-                                                    const uint8_t* __restrict__ seq,
-                                                    const int32_t* __restrict__ lengths, int Lmax,
-                                                    int Amax, float* __restrict__ coords,
-                                                    int32_t* __restrict__ num_atoms, ChainWs ws,
-                                                    const __grid_constant__ FaTable tab) {
+__global__ void __launch_bounds__(NT, 2) fa_fwd_kernel(const float* __restrict__ angles,
+                                                       const uint8_t* __restrict__ seq,
+                                                       const int32_t* __restrict__ lengths, int Lmax,
+                                                       int Amax, float* __restrict__ coords,
+                                                       int32_t* __restrict__ num_atoms, ChainWs ws,
+                                                       const __grid_constant__ FaTable tab) {
     constexpr int NW = NT / 32;
     __shared__ FaTable s_tab;
     __shared__ RigidS s_rig[NW + 1];
     __shared__ int s_cnt[NW + 1];
-    __shared__ RigidS s_pre;
-    __shared__ int s_pre_cnt;
     __shared__ int s_v;
     __shared__ int s_a0[NT];
     __shared__ uint8_t s_type[NT];
@@ -162,9 +212,8 @@ __global__ void __launch_bounds__(NT) fa_fwd_kernel(const float* __restrict__ an
 
     copy_table(s_tab, tab);
     const int ntiles = ws.hdr[kHdrTiles];
-    int v = first_tile(ws.hdr + kHdrFwdNext, &s_v);
+    int v = take_tile(ws.hdr + kHdrFwdNext, &s_v);
     while (v < ntiles) {
-        const int next = prefetch_tile(ws.hdr + kHdrFwdNext);
         const int2 ct = ws.tiles[v];
         const int b = ct.x, t = ct.y;
         const int L = clamp_length(lengths, b, Lmax);
@@ -175,16 +224,13 @@ __global__ void __launch_bounds__(NT) fa_fwd_kernel(const float* __restrict__ an
 
         const int j = t * NT + threadIdx.x;
         const bool valid = j < L;
-        // all loads up front
         int type = kGlyCode;
-        float a_phi = 0.f, a_psi = 0.f, a_om = 0.f, chi[kMaxGroups] = {0.f, 0.f, 0.f, 0.f};
+        float a_phi = 0.f, a_psi = 0.f, a_om = 0.f;
         if (valid) {
             type = residue_type(seq + (size_t)b * Lmax, j, true);
             a_phi = __ldg(ang + j);
             a_psi = __ldg(ang + Lmax + j);
             if (j + 1 < L) a_om = __ldg(ang + 2 * Lmax + j + 1);
-#pragma unroll
-            for (int k = 0; k < kMaxGroups; ++k) chi[k] = __ldg(ang + (3 + k) * Lmax + j);
         }
         const int nat = valid ? s_tab.n_atoms[type] : 0;
         float sp = 0.f, cp = 1.f, ss = 0.f, cs = 1.f;
@@ -205,23 +251,13 @@ __global__ void __launch_bounds__(NT) fa_fwd_kernel(const float* __restrict__ an
         int pk0, pktot;
         block_scan_rigid_count<NT>(A, valid ? nat | ((nat - 4) << 16) : 0, s_rig, s_cnt, E, pk0,
                                    Tot, pktot);
-        if (threadIdx.x < 32) {
-            int pc;
-            const Rigid P = lookback_prefix(ws, slot0, t, Tot, pktot & 0xffff, pc);
-            if (threadIdx.x == 0) {
-                store_rigid(s_pre, P);
-                s_pre_cnt = pc;
-                store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, pc);
-            }
-        }
-        __syncthreads();
-        const int pc = s_pre_cnt;
         const int a0 = pk0 & 0xffff, s0 = pk0 >> 16;
         const int tile_atoms = pktot & 0xffff, tile_side = pktot >> 16;
-        E = rigid_mul(load_rigid(s_pre), E);
-        const int soff = (3 * pc) & 3;  // stage[soff + 3 * slot] is the tile's atom `slot`
+        // publish the tile's aggregate now (successors need it); the prefix is
+        // gathered later by every warp, so no warp waits on another for it
+        if (threadIdx.x == NT - 32) publish_prefix_agg(ws, slot0 + t, Tot, tile_atoms);
         if (valid) {
-            float* st = stage + soff + 3 * a0;
+            float* st = stage + 3 * a0;
             stage_atom(st, 0, E.t);  // N = M_0 0
             Rigid M1 = E;
             rigid_mul_R(M1, cp, sp, s_tab.bb.ct[1], s_tab.bb.st[1], s_tab.bb.d[1]);
@@ -238,7 +274,7 @@ __global__ void __launch_bounds__(NT) fa_fwd_kernel(const float* __restrict__ an
 #pragma unroll
             for (int k = 0; k < kMaxGroups; ++k) {
                 float sc, cc;
-                sincosf(chi[k], &sc, &cc);
+                sincosf(__ldg(ang + (3 + k) * Lmax + j), &sc, &cc);
                 if (k >= nchi) {
                     cc = s_tab.fixchi[type][k].x;
                     sc = s_tab.fixchi[type][k].y;
@@ -252,6 +288,7 @@ __global__ void __launch_bounds__(NT) fa_fwd_kernel(const float* __restrict__ an
             for (int e = 0; e < nat - 4; ++e) s_desc[s0 + e] = (uint16_t)((threadIdx.x << 4) | e);
         }
         __syncthreads();
+        const int requested = request_tile(ws.hdr + kHdrFwdNext);
         for (int q = threadIdx.x; q < tile_side; q += NT) {
             const int d = s_desc[q];
             const int r = d >> 4, e = d & 15;
@@ -259,17 +296,21 @@ __global__ void __launch_bounds__(NT) fa_fwd_kernel(const float* __restrict__ an
             const int w = (int)r0.w;
             const float3 pos = frame_point(s_frame + r * kFrameStride + 3 * ((w >> 4) - 1),
                                            make_float3(r0.x, r0.y, r0.z));
-            stage_atom(stage + soff + 3 * s_a0[r], w & 15, pos);
+            stage_atom(stage + 3 * s_a0[r], w & 15, pos);
         }
         __syncthreads();
+        // frame at the tile start (every warp gathers it), applied while storing
+        int pc;
+        const Rigid P = gather_prefix(ws, slot0, t, pc);
+        if (threadIdx.x == 0) store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, pc);
         const int end_atom = pc + tile_atoms;
         if (end_atom > Amax && threadIdx.x == 0) flag_status(TPL_STATUS_TOO_MANY_ATOMS);
-        copy_range<NT, true>(out, stage, 3 * pc, 3 * min(end_atom, Amax));
+        store_range_transformed<NT>(out, stage, P, 3 * pc, 3 * min(end_atom, Amax));
         if (t == T - 1) {
             if (threadIdx.x == 0) num_atoms[b] = end_atom;
             zero_range<NT>(out, 3 * min(end_atom, Amax), 3 * Amax);
         }
-        v = advance_tile(next, &s_v);
+        v = next_tile(requested, &s_v);
     }
 }
 
@@ -324,7 +365,6 @@ __global__ void __launch_bounds__(NT) fa_bwd_coords_kernel(
     __shared__ FaTable s_tab;
     __shared__ int s_cnt[NW + 1];
     __shared__ float s6[6 * (NW + 1)];
-    __shared__ float s_suf[6];
     __shared__ float s_prevc[3];
     __shared__ int s_v;
     __shared__ uint8_t s_type[NT];
@@ -341,9 +381,8 @@ __global__ void __launch_bounds__(NT) fa_bwd_coords_kernel(
     copy_table(s_tab, tab);
     const int ntiles = ws.hdr[kHdrTiles];
     int* counter = ws.bflag + ws.slots;
-    int v = first_tile(counter, &s_v);
+    int v = take_tile(counter, &s_v);
     while (v < ntiles) {
-        const int next = prefetch_tile(counter);
         const int2 ct = ws.tiles[v];
         const int b = ct.x;
         const int L = clamp_length(lengths, b, Lmax);
@@ -429,18 +468,9 @@ __global__ void __launch_bounds__(NT) fa_bwd_coords_kernel(
         const Sum6 own = sum6_add(all, nsum);
         Sum6 after, total;
         block_suffix_sum6<NT>(own, s6, after, total);
-        if (threadIdx.x < 32) {
-            const Sum6 suf = lookback_suffix(ws, slot0, t, T, total);
-            if (threadIdx.x == 0) {
-                s_suf[0] = suf.c.x; s_suf[1] = suf.c.y; s_suf[2] = suf.c.z;
-                s_suf[3] = suf.g.x; s_suf[4] = suf.g.y; s_suf[5] = suf.g.z;
-            }
-        }
-        __syncthreads();
-        Sum6 later;
-        later.c = make_float3(s_suf[0], s_suf[1], s_suf[2]);
-        later.g = make_float3(s_suf[3], s_suf[4], s_suf[5]);
-        after = sum6_add(after, later);
+        if (threadIdx.x == NT - 32) publish_suffix_agg(ws, slot0 + t, total);
+        const int requested = request_tile(counter);
+        after = sum6_add(after, gather_suffix(ws, slot0, t, T));  // every warp gathers it
         if (j < Lmax) {
             float gphi = 0.f, gpsi = 0.f, gomg = 0.f;
             if (in_range) {
@@ -464,7 +494,7 @@ __global__ void __launch_bounds__(NT) fa_bwd_coords_kernel(
 #pragma unroll
                 for (int r = 0; r < 7; ++r) ga[r * Lmax + i] = 0.f;
         }
-        v = advance_tile(next, &s_v);
+        v = next_tile(requested, &s_v);
     }
 }
 
@@ -485,7 +515,6 @@ __global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ an
     __shared__ RigidS s_rig[NW + 1];
     __shared__ int s_cnt[NW + 1];
     __shared__ float s6[6 * (NW + 1)];
-    __shared__ float s_suf[6];
     __shared__ int s_v;
     extern __shared__ float4 s_dyn[];
     float* stage = reinterpret_cast<float*>(s_dyn);  // g of the tile's atoms
@@ -499,9 +528,8 @@ __global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ an
     copy_table(s_tab, tab);
     const int ntiles = ws.hdr[kHdrTiles];
     int* counter = ws.bflag + ws.slots;
-    int v = first_tile(counter, &s_v);
+    int v = take_tile(counter, &s_v);
     while (v < ntiles) {
-        const int next = prefetch_tile(counter);
         const int2 ct = ws.tiles[v];
         const int b = ct.x;
         const int L = clamp_length(lengths, b, Lmax);
@@ -595,18 +623,9 @@ __global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ an
         const Sum6 own = sum6_add(all, nsum);
         Sum6 after, total;
         block_suffix_sum6<NT>(own, s6, after, total);
-        if (threadIdx.x < 32) {
-            const Sum6 suf = lookback_suffix(ws, slot0, t, T, total);
-            if (threadIdx.x == 0) {
-                s_suf[0] = suf.c.x; s_suf[1] = suf.c.y; s_suf[2] = suf.c.z;
-                s_suf[3] = suf.g.x; s_suf[4] = suf.g.y; s_suf[5] = suf.g.z;
-            }
-        }
-        __syncthreads();
-        Sum6 later;
-        later.c = make_float3(s_suf[0], s_suf[1], s_suf[2]);
-        later.g = make_float3(s_suf[3], s_suf[4], s_suf[5]);
-        after = sum6_add(after, later);
+        if (threadIdx.x == NT - 32) publish_suffix_agg(ws, slot0 + t, total);
+        const int requested = request_tile(counter);
+        after = sum6_add(after, gather_suffix(ws, slot0, t, T));  // every warp gathers it
         if (j < Lmax) {
             float gphi = 0.f, gpsi = 0.f, gomg = 0.f;
             if (in_range) {
@@ -630,7 +649,7 @@ __global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ an
 #pragma unroll
                 for (int r = 0; r < 7; ++r) ga[r * Lmax + i] = 0.f;
         }
-        v = advance_tile(next, &s_v);
+        v = next_tile(requested, &s_v);
     }
 }
 

@@ -164,6 +164,24 @@ __device__ __forceinline__ float adjugate4f(float a00, float a01, float a02, flo
     return s0 * c5 - s1 * c4 + s2 * c3 + s3 * c2 - s4 * c1 + s5 * c0;
 }
 
+// Cofactor (R, C) of a 4x4 matrix: signed determinant of the 3x3 minor.
+template <int R, int C>
+__device__ __forceinline__ double cofactor(const double (&A)[4][4]) {
+    constexpr int r0 = R == 0 ? 1 : 0, r1 = R <= 1 ? 2 : 1, r2 = R <= 2 ? 3 : 2;
+    constexpr int c0 = C == 0 ? 1 : 0, c1 = C <= 1 ? 2 : 1, c2 = C <= 2 ? 3 : 2;
+    const double d = A[r0][c0] * (A[r1][c1] * A[r2][c2] - A[r1][c2] * A[r2][c1]) -
+                     A[r0][c1] * (A[r1][c0] * A[r2][c2] - A[r1][c2] * A[r2][c0]) +
+                     A[r0][c2] * (A[r1][c0] * A[r2][c1] - A[r1][c1] * A[r2][c0]);
+    return ((R + C) & 1) ? -d : d;
+}
+template <int R>
+__device__ __forceinline__ void adj_row(const double (&A)[4][4], double (&q)[4]) {
+    q[0] = cofactor<R, 0>(A);
+    q[1] = cofactor<R, 1>(A);
+    q[2] = cofactor<R, 2>(A);
+    q[3] = cofactor<R, 3>(A);
+}
+
 // Eigen-solve of T (one thread per pair).  FP64 issue is scarce on this GPU
 // (about 34 ns per dependent FP64 instruction per warp), so the largest
 // eigenpair is first estimated in FP32 -- Newton's method on the characteristic
@@ -215,25 +233,31 @@ __global__ void __launch_bounds__(32) lrmsd_solve_kernel(
             for (int c = 0; c < 3; ++c) r[3 * a + c] = S[6 + 3 * a + c] - n * mx[a] * my[c];
         const float e0 = S[15] + S[16] - n * (mx[0] * mx[0] + mx[1] * mx[1] + mx[2] * mx[2] +
                                               my[0] * my[0] + my[1] * my[1] + my[2] * my[2]);
-        // ---- FP32 estimate
-        const float t00 = r[0] + r[4] + r[8], t01 = r[5] - r[7], t02 = r[6] - r[2], t03 = r[1] - r[3];
-        const float t11 = r[0] - r[4] - r[8], t12 = r[1] + r[3], t13 = r[2] + r[6];
-        const float t22 = -r[0] + r[4] - r[8], t23 = r[5] + r[7], t33 = -r[0] - r[4] + r[8];
+        // ---- FP32 estimate on R / |R| (T, lambda and the adjugate are O(1);
+        // the eigenvectors do not depend on the scale)
         float fro = 0.f;
 #pragma unroll
         for (int k = 0; k < 9; ++k) fro = fmaf(r[k], r[k], fro);
+        if (!(fro > 0.f)) goto store;  // R = 0 (one atom, or all atoms coincide): U = I
+        {
+        const float sc = rsqrtf(fro);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) r[k] *= sc;
+        const float t00 = r[0] + r[4] + r[8], t01 = r[5] - r[7], t02 = r[6] - r[2], t03 = r[1] - r[3];
+        const float t11 = r[0] - r[4] - r[8], t12 = r[1] + r[3], t13 = r[2] + r[6];
+        const float t22 = -r[0] + r[4] - r[8], t23 = r[5] + r[7], t33 = -r[0] - r[4] + r[8];
         const float detR = r[0] * (r[4] * r[8] - r[5] * r[7]) - r[1] * (r[3] * r[8] - r[5] * r[6]) +
                            r[2] * (r[3] * r[7] - r[4] * r[6]);
         float m[16];
         const float c0 = adjugate4f(t00, t01, t02, t03, t11, t12, t13, t22, t23, t33, m);
-        const float c2 = -2.f * fro, c1 = -8.f * detR;
-        float lam = fminf(2.f * sqrtf(fro), 0.5f * e0 * (1.f + 1e-5f));
+        const float c2 = -2.f, c1 = -8.f * detR;  // |R| = 1 after scaling
+        float lam = fminf(2.f, 0.5f * e0 * sc * (1.f + 1e-5f));
         for (int it = 0; it < 24; ++it) {
             const float l2 = lam * lam;
             const float pv = (l2 + c2) * l2 + c1 * lam + c0;
             const float dp = (4.f * l2 + 2.f * c2) * lam + c1;
             if (!(fabsf(dp) > 0.f)) break;
-            const float step = pv / dp;
+            const float step = __fdividef(pv, dp);
             lam -= step;
             if (fabsf(step) <= 1e-6f * fabsf(lam)) break;
         }
@@ -249,6 +273,14 @@ __global__ void __launch_bounds__(32) lrmsd_solve_kernel(
 #pragma unroll
                 for (int i = 0; i < 4; ++i) qf[i] = m[4 * i + k];
             }
+        if (fabsf(best) > 0.f) {
+            const float ib = 1.f / fabsf(best);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) qf[i] *= ib;
+        } else {
+            qf[0] = 1.f; qf[1] = qf[2] = qf[3] = 0.f;
+            jb = 0;
+        }
         // ---- FP64 solve: T in FP64, Rayleigh quotient, adjugate column
         double R[9];
 #pragma unroll
@@ -277,40 +309,18 @@ __global__ void __launch_bounds__(32) lrmsd_solve_kernel(
             l64 = num * rd;
             l64 = fma(rd, fma(-l64, den, num), l64);  // one Newton correction of num / den
         }
-        // A = T - lambda I with index jb moved to 0 (a symmetric permutation), so
-        // that the needed adjugate column is column 0: six 2x2 minors of rows 2, 3.
-        // pi swaps 0 and jb
-        auto pidx = [jb](int i) { return i == 0 ? jb : (i == jb ? 0 : i); };
-        double a[4][4];
+        // eigenvector: row jb of adj(T - lambda I) (symmetric, so also column jb)
+        double A[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int pi = pidx(i), pk = pidx(k);
-                double v = T[0][0];
-#pragma unroll
-                for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        if (ii == pi && kk == pk) v = T[ii][kk];
-                a[i][k] = v - (i == k ? l64 : 0.0);
-            }
-        const double c5 = a[2][2] * a[3][3] - a[3][2] * a[2][3], c4 = a[2][1] * a[3][3] - a[3][1] * a[2][3];
-        const double c3 = a[2][1] * a[3][2] - a[3][1] * a[2][2], c2d = a[2][0] * a[3][3] - a[3][0] * a[2][3];
-        const double c1d = a[2][0] * a[3][2] - a[3][0] * a[2][2], c0d = a[2][0] * a[3][1] - a[3][0] * a[2][1];
-        double col[4];
-        col[0] = a[1][1] * c5 - a[1][2] * c4 + a[1][3] * c3;
-        col[1] = -a[1][0] * c5 + a[1][2] * c2d - a[1][3] * c1d;
-        col[2] = a[1][0] * c4 - a[1][1] * c2d + a[1][3] * c0d;
-        col[3] = -a[1][0] * c3 + a[1][1] * c1d - a[1][2] * c0d;
-        // undo the permutation: q[pi[i]] = col[i]
-#pragma unroll
-        for (int i = 0; i < 4; ++i) q[i] = 0.0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int ii = 0; ii < 4; ++ii)
-                if (ii == pidx(i)) q[ii] = col[i];
+            for (int k = 0; k < 4; ++k) A[i][k] = T[i][k] - (i == k ? l64 : 0.0);
+        switch (jb) {
+            case 0: adj_row<0>(A, q); break;
+            case 1: adj_row<1>(A, q); break;
+            case 2: adj_row<2>(A, q); break;
+            default: adj_row<3>(A, q); break;
+        }
         const double nn = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
         float q0 = 1.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
         if (nn > 0.0) {
@@ -328,7 +338,9 @@ __global__ void __launch_bounds__(32) lrmsd_solve_kernel(
         U[6] = 2.f * (q1 * q3 - q0 * q2);
         U[7] = 2.f * (q2 * q3 + q0 * q1);
         U[8] = q0 * q0 - q1 * q1 - q2 * q2 + q3 * q3;
+        }
     }
+store:
 #pragma unroll
     for (int k = 0; k < 9; ++k) st[k] = U[k];
 #pragma unroll

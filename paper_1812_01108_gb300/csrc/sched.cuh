@@ -155,18 +155,40 @@ __device__ __forceinline__ Rigid shfl_down_rigid(const Rigid& m, int delta) {
     return r;
 }
 
-// Forward look-back, called by all 32 lanes of one warp.  Lane 0 publishes
-// this tile's aggregate; then lane l waits for tile base + l of each group of
-// 32 predecessors (the waits overlap) and the warp folds the aggregates in a
-// fixed tree: the result is A_0 A_1 ... A_{t-1} (product in tile order) and
-// the sum of their atom counts, identical in every run.  Valid in lane 0.
-__device__ __forceinline__ Rigid lookback_prefix(const ChainWs& ws, int slot0, int t,
-                                                 const Rigid& agg, int agg_cnt, int& pre_cnt) {
+__device__ __forceinline__ Rigid shfl_rigid(const Rigid& m, int src) {
+    Rigid r;
+    const unsigned full = 0xffffffffu;
+    r.c0.x = __shfl_sync(full, m.c0.x, src);
+    r.c0.y = __shfl_sync(full, m.c0.y, src);
+    r.c0.z = __shfl_sync(full, m.c0.z, src);
+    r.c1.x = __shfl_sync(full, m.c1.x, src);
+    r.c1.y = __shfl_sync(full, m.c1.y, src);
+    r.c1.z = __shfl_sync(full, m.c1.z, src);
+    r.c2.x = __shfl_sync(full, m.c2.x, src);
+    r.c2.y = __shfl_sync(full, m.c2.y, src);
+    r.c2.z = __shfl_sync(full, m.c2.z, src);
+    r.t.x = __shfl_sync(full, m.t.x, src);
+    r.t.y = __shfl_sync(full, m.t.y, src);
+    r.t.z = __shfl_sync(full, m.t.z, src);
+    return r;
+}
+
+// Publication of a tile's forward aggregate (one thread).  The release store
+// orders the data stores before the flag.
+__device__ __forceinline__ void publish_prefix_agg(const ChainWs& ws, int slot, const Rigid& agg,
+                                                   int cnt) {
+    store_rigid_g(ws.fagg + 4 * (size_t)slot, agg, cnt);
+    flag_release(ws.fflag + slot, 1);
+}
+
+// Forward look-back, called by all 32 lanes of a warp (every warp that needs
+// the result calls it; no cross-warp synchronisation).  Lane l waits for tile
+// base + l of each group of 32 predecessors (the waits overlap) and the warp
+// folds the aggregates in a fixed tree: the result, in every lane, is
+// A_0 A_1 ... A_{t-1} (product in tile order, re-orthonormalised) and the sum
+// of their atom counts, identical in every run.
+__device__ __forceinline__ Rigid gather_prefix(const ChainWs& ws, int slot0, int t, int& pre_cnt) {
     const int lane = threadIdx.x & 31;
-    if (lane == 0) {
-        store_rigid_g(ws.fagg + 4 * (size_t)(slot0 + t), agg, agg_cnt);
-        flag_release(ws.fflag + slot0 + t, 1);  // release orders the data stores before it
-    }
     Rigid acc = rigid_identity();
     int cnt = 0;
     for (int base = 0; base < t; base += 32) {
@@ -177,6 +199,7 @@ __device__ __forceinline__ Rigid lookback_prefix(const ChainWs& ws, int slot0, i
         const int n = min(32, t - base);
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
+            if (off >= n) break;
             const Rigid y = shfl_down_rigid(a, off);
             const int cy = __shfl_down_sync(0xffffffffu, c, off);
             if ((lane & (2 * off - 1)) == 0 && lane + off < n) {
@@ -184,10 +207,10 @@ __device__ __forceinline__ Rigid lookback_prefix(const ChainWs& ws, int slot0, i
                 c += cy;
             }
         }
-        acc = rigid_mul(acc, a);
-        cnt += c;
+        acc = rigid_mul(acc, shfl_rigid(a, 0));
+        cnt += __shfl_sync(0xffffffffu, c, 0);
     }
-    rigid_reortho(acc);
+    if (t > 0) rigid_reortho(acc);
     pre_cnt = cnt;
     return acc;
 }
@@ -200,18 +223,17 @@ __device__ __forceinline__ Sum6 load_sum6_g(const float4* s) {
     return v;
 }
 
-// Backward look-back, all 32 lanes of one warp: publishes this tile's (c, g)
-// total, then sums the totals of tiles t+1..T-1 in a fixed tree order.  Valid
-// in lane 0.
-__device__ __forceinline__ Sum6 lookback_suffix(const ChainWs& ws, int slot0, int t, int T,
-                                                const Sum6& agg) {
+__device__ __forceinline__ void publish_suffix_agg(const ChainWs& ws, int slot, const Sum6& agg) {
+    float4* d = ws.bagg + 2 * (size_t)slot;
+    d[0] = make_float4(agg.c.x, agg.c.y, agg.c.z, agg.g.x);
+    d[1] = make_float4(agg.g.y, agg.g.z, 0.f, 0.f);
+    flag_release(ws.bflag + slot, 1);
+}
+
+// Backward look-back, all 32 lanes of a warp: the sum of the totals of tiles
+// t+1..T-1 in a fixed tree order, in every lane.
+__device__ __forceinline__ Sum6 gather_suffix(const ChainWs& ws, int slot0, int t, int T) {
     const int lane = threadIdx.x & 31;
-    if (lane == 0) {
-        float4* d = ws.bagg + 2 * (size_t)(slot0 + t);
-        d[0] = make_float4(agg.c.x, agg.c.y, agg.c.z, agg.g.x);
-        d[1] = make_float4(agg.g.y, agg.g.z, 0.f, 0.f);
-        flag_release(ws.bflag + slot0 + t, 1);
-    }
     Sum6 acc = sum6_zero();
     for (int base = t + 1; base < T; base += 32) {
         const int tp = base + lane;
@@ -224,23 +246,30 @@ __device__ __forceinline__ Sum6 lookback_suffix(const ChainWs& ws, int slot0, in
         }
         acc = sum6_add(acc, v);
     }
-    return acc;
+    Sum6 r;
+    r.c = make_float3(__shfl_sync(0xffffffffu, acc.c.x, 0), __shfl_sync(0xffffffffu, acc.c.y, 0),
+                      __shfl_sync(0xffffffffu, acc.c.z, 0));
+    r.g = make_float3(__shfl_sync(0xffffffffu, acc.g.x, 0), __shfl_sync(0xffffffffu, acc.g.y, 0),
+                      __shfl_sync(0xffffffffu, acc.g.z, 0));
+    return r;
 }
 
-// Work-list entries for a persistent CTA: the first is taken at start, and the
-// next one is requested by thread 0 while the current tile is being processed
-// (hiding the atomic's latency).  All threads call both functions.
-__device__ __forceinline__ int first_tile(int* counter, int* s_v) {
+// Work-list entries for a persistent CTA.  take_tile() is called once at the
+// start; during a tile thread 0 requests the next entry late (request_tile),
+// after the tile's aggregate is published, and next_tile() hands it to the CTA.
+// A taken tile therefore starts right away, so a tile waiting on it never
+// waits on work that has not begun.
+__device__ __forceinline__ int take_tile(int* counter, int* s_v) {
     if (threadIdx.x == 0) *s_v = atomicAdd(counter, 1);
     __syncthreads();
     return *s_v;
 }
-__device__ __forceinline__ int prefetch_tile(int* counter) {
+__device__ __forceinline__ int request_tile(int* counter) {
     return threadIdx.x == 0 ? atomicAdd(counter, 1) : 0;
 }
-__device__ __forceinline__ int advance_tile(int next, int* s_v) {
-    __syncthreads();  // everyone is done with the current tile's shared data
-    if (threadIdx.x == 0) *s_v = next;
+__device__ __forceinline__ int next_tile(int requested, int* s_v) {
+    __syncthreads();  // everyone is done with this tile's shared data
+    if (threadIdx.x == 0) *s_v = requested;
     __syncthreads();
     return *s_v;
 }
