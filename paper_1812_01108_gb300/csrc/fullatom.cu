@@ -170,45 +170,29 @@ __device__ __forceinline__ bool ws_matches(const ChainWs& ws, int tile, int B, i
 //     divergence between residue types);
 //  3. the staged tile is written out with 16-byte stores.
 // ---------------------------------------------------------------------------
-constexpr int kFrameStride = 13;  // float4 per residue: 4 frames x 3, padded against bank conflicts
-
 template <int NT>
 __host__ __device__ constexpr size_t fa_fwd_smem() {
-    return (size_t)NT * kFrameStride * 16 + (size_t)NT * kMaxSide * 2 + 16 +
-           (size_t)(4 + NT * kMaxAtoms * 3) * 4;
+    return (size_t)(4 + NT * kMaxAtoms * 3) * 4;
 }
 
-__device__ __forceinline__ void store_frame(float4* f, const Rigid& m) {
-    f[0] = make_float4(m.c0.x, m.c0.y, m.c0.z, m.c1.x);
-    f[1] = make_float4(m.c1.y, m.c1.z, m.c2.x, m.c2.y);
-    f[2] = make_float4(m.c2.z, m.t.x, m.t.y, m.t.z);
-}
-
-__device__ __forceinline__ float3 frame_point(const float4* f, float3 v) {
-    const float4 a = f[0], b = f[1], c = f[2];
-    return make_float3(fmaf(v.z, b.z, fmaf(v.y, a.w, fmaf(v.x, a.x, c.y))),
-                       fmaf(v.z, b.w, fmaf(v.y, b.x, fmaf(v.x, a.y, c.z))),
-                       fmaf(v.z, c.x, fmaf(v.y, b.y, fmaf(v.x, a.z, c.w))));
+// CTAs per SM the forward and backward kernels are compiled for (register cap)
+template <int NT>
+__host__ __device__ constexpr int fa_min_blocks() {
+    return NT >= 512 ? 1 : (NT >= 256 ? 3 : 6);
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT, 2) fa_fwd_kernel(const float* __restrict__ angles,
-                                                       const uint8_t* __restrict__ seq,
-                                                       const int32_t* __restrict__ lengths, int Lmax,
-                                                       int Amax, float* __restrict__ coords,
-                                                       int32_t* __restrict__ num_atoms, ChainWs ws,
-                                                       const __grid_constant__ FaTable tab) {
+__global__ void __launch_bounds__(NT, fa_min_blocks<NT>()) fa_fwd_kernel(
+    const float* __restrict__ angles, const uint8_t* __restrict__ seq,
+    const int32_t* __restrict__ lengths, int Lmax, int Amax, float* __restrict__ coords,
+    int32_t* __restrict__ num_atoms, ChainWs ws, const __grid_constant__ FaTable tab) {
     constexpr int NW = NT / 32;
     __shared__ FaTable s_tab;
     __shared__ RigidS s_rig[NW + 1];
     __shared__ int s_cnt[NW + 1];
     __shared__ int s_v;
-    __shared__ int s_a0[NT];
-    __shared__ uint8_t s_type[NT];
     extern __shared__ float4 s_dyn[];
-    float4* s_frame = s_dyn;                                                  // [NT][13]
-    uint16_t* s_desc = reinterpret_cast<uint16_t*>(s_dyn + NT * kFrameStride);  // [NT * 10]
-    float* stage = reinterpret_cast<float*>(s_dyn + NT * kFrameStride + (NT * kMaxSide * 2 + 16) / 16);
+    float* stage = reinterpret_cast<float*>(s_dyn);  // tile-local atoms, 3 floats each
 
     copy_table(s_tab, tab);
     const int ntiles = ws.hdr[kHdrTiles];
@@ -246,16 +230,13 @@ __global__ void __launch_bounds__(NT, 2) fa_fwd_kernel(const float* __restrict__
                 rigid_mul_R(A, co, so, s_tab.bb.ct[0], s_tab.bb.st[0], s_tab.bb.d[0]);
             }
         }
-        // atom and side-atom counts scanned together (16 bits each)
         Rigid E, Tot;
-        int pk0, pktot;
-        block_scan_rigid_count<NT>(A, valid ? nat | ((nat - 4) << 16) : 0, s_rig, s_cnt, E, pk0,
-                                   Tot, pktot);
-        const int a0 = pk0 & 0xffff, s0 = pk0 >> 16;
-        const int tile_atoms = pktot & 0xffff, tile_side = pktot >> 16;
-        // publish the tile's aggregate now (successors need it); the prefix is
-        // gathered later by every warp, so no warp waits on another for it
+        int a0, tile_atoms;
+        block_scan_rigid_count<NT>(A, nat, s_rig, s_cnt, E, a0, Tot, tile_atoms);
+        // publish the tile's aggregate now (successors need it); every warp
+        // gathers the prefix later, so no warp waits on another for it
         if (threadIdx.x == NT - 32) publish_prefix_agg(ws, slot0 + t, Tot, tile_atoms);
+        // residue atoms in tile-local coordinates (E is relative to the tile start)
         if (valid) {
             float* st = stage + 3 * a0;
             stage_atom(st, 0, E.t);  // N = M_0 0
@@ -267,36 +248,27 @@ __global__ void __launch_bounds__(NT, 2) fa_fwd_kernel(const float* __restrict__
             stage_atom(st, 2, M3.t);  // C = M_3 0
             const float4 o = s_tab.o_r0;
             stage_atom(st, 3, point_apply(M3, make_float3(o.x, o.y, o.z)));
-            // side-chain frames S_k = S_{k-1} R(chi_k), S_0 = M_1 R' (groups past n_groups unused)
+            // side-chain groups: S_k = S_{k-1} R(chi_k), S_0 = M_1 R'; atoms r = S_k r0
             Rigid S = M1;
             rigid_mul_Rx(S, s_tab.rp_c, s_tab.rp_s);
-            const int nchi = s_tab.n_chi[type];
-#pragma unroll
-            for (int k = 0; k < kMaxGroups; ++k) {
+            const int ng = s_tab.n_groups[type], nchi = s_tab.n_chi[type];
+            int e = 0;
+            for (int k = 0; k < ng; ++k) {
                 float sc, cc;
-                sincosf(__ldg(ang + (3 + k) * Lmax + j), &sc, &cc);
-                if (k >= nchi) {
+                if (k < nchi) {
+                    sincosf(__ldg(ang + (3 + k) * Lmax + j), &sc, &cc);
+                } else {
                     cc = s_tab.fixchi[type][k].x;
                     sc = s_tab.fixchi[type][k].y;
                 }
                 const float4 gk = s_tab.grp[type][k];
                 rigid_mul_R(S, cc, sc, gk.x, gk.y, gk.z);
-                store_frame(s_frame + threadIdx.x * kFrameStride + 3 * k, S);
+                const int end = s_tab.grp_end[type][k];
+                for (; e < end; ++e) {
+                    const float4 r0 = s_tab.side[type][e];
+                    stage_atom(st, (int)r0.w & 15, point_apply(S, make_float3(r0.x, r0.y, r0.z)));
+                }
             }
-            s_a0[threadIdx.x] = a0;
-            s_type[threadIdx.x] = (uint8_t)type;
-            for (int e = 0; e < nat - 4; ++e) s_desc[s0 + e] = (uint16_t)((threadIdx.x << 4) | e);
-        }
-        __syncthreads();
-        const int requested = request_tile(ws.hdr + kHdrFwdNext);
-        for (int q = threadIdx.x; q < tile_side; q += NT) {
-            const int d = s_desc[q];
-            const int r = d >> 4, e = d & 15;
-            const float4 r0 = s_tab.side[s_type[r]][e];
-            const int w = (int)r0.w;
-            const float3 pos = frame_point(s_frame + r * kFrameStride + 3 * ((w >> 4) - 1),
-                                           make_float3(r0.x, r0.y, r0.z));
-            stage_atom(stage + 3 * s_a0[r], w & 15, pos);
         }
         __syncthreads();
         // frame at the tile start (every warp gathers it), applied while storing
@@ -310,7 +282,7 @@ __global__ void __launch_bounds__(NT, 2) fa_fwd_kernel(const float* __restrict__
             if (threadIdx.x == 0) num_atoms[b] = end_atom;
             zero_range<NT>(out, 3 * min(end_atom, Amax), 3 * Amax);
         }
-        v = next_tile(requested, &s_v);
+        v = next_tile(request_tile(ws.hdr + kHdrFwdNext), &s_v);
     }
 }
 
@@ -356,7 +328,7 @@ __host__ __device__ constexpr size_t fa_bwd_coords_smem() {
 __device__ __forceinline__ float3 unit3(float3 v) { return f3_scale(rsqrtf(f3_dot(v, v)), v); }
 
 template <int NT>
-__global__ void __launch_bounds__(NT) fa_bwd_coords_kernel(
+__global__ void __launch_bounds__(NT, fa_min_blocks<NT>() > 2 ? fa_min_blocks<NT>() - 1 : 1) fa_bwd_coords_kernel(
     const uint8_t* __restrict__ seq, const int32_t* __restrict__ lengths, int B, int Lmax, int Amax,
     const float* __restrict__ coords, const float* __restrict__ grad_coords,
     float* __restrict__ grad_angles, ChainWs ws, const __grid_constant__ FaTable tab) {
