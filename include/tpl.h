@@ -188,6 +188,25 @@ tpl_status tpl_lrmsd_backward(const float* grad_lrmsd, const float* input, const
                               const int32_t* num_atoms, int P, int Nmax, float* grad_input,
                               const void* workspace, size_t workspace_bytes, tpl_stream stream);
 
+/* Allocation-free variant of tpl_lrmsd_forward, for callers that can neither
+ * allocate device memory nor pass a workspace (for example code whose device
+ * memory is all owned by another runtime's allocator, or an interface without
+ * a scratch argument).  The paper has no counterpart; this is an interface
+ * convenience.  The scratch is a fixed array inside the library: every GPU
+ * that loads the library holds it (about 1.7 MB) until the process exits.
+ *   Limits: P <= 4096 pairs, Nmax <= 8192 atoms; larger sizes return
+ *   TPL_ERR_BAD_SHAPE and launch nothing.  Inputs and outputs as in
+ *   tpl_lrmsd_forward; no allocation, no workspace.
+ *   The first call on a device looks up the scratch array's device address
+ *   (once per device); make that first call before any stream capture.
+ *   All calls share the one array and it keeps the last call's contents, so
+ *   calls that overlap on the GPU (different streams without ordering between
+ *   them) race; there is no backward companion (tpl_lrmsd_backward needs the
+ *   workspace of tpl_lrmsd_forward). */
+tpl_status tpl_lrmsd_forward_noalloc(const float* input, const float* target,
+                                     const int32_t* num_atoms, int P, int Nmax, float* lrmsd,
+                                     tpl_stream stream);
+
 /* ------------------------------------------------------------------------ */
 /* Plain FP64 per-chain forms: one CTA per chain (or pair), serial composition */
 /* and serial suffix sums; the error reference and throughput comparator of   */

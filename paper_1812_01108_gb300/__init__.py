@@ -25,7 +25,8 @@ import torch
 __all__ = [
     "TplError", "Opts", "library_path", "load_library", "tpl_backbone_forward",
     "tpl_backbone_backward", "tpl_fullatom_forward", "tpl_fullatom_backward",
-    "tpl_lrmsd_forward", "tpl_lrmsd_backward", "tpl_backbone_forward_ref64",
+    "tpl_lrmsd_forward", "tpl_lrmsd_backward", "tpl_lrmsd_forward_noalloc",
+    "tpl_backbone_forward_ref64",
     "tpl_backbone_backward_ref64", "tpl_fullatom_forward_ref64", "tpl_fullatom_backward_ref64",
     "tpl_lrmsd_forward_ref64", "tpl_lrmsd_backward_ref64", "tpl_get_status", "backbone",
     "fullatom", "lrmsd", "residue_table", "fullatom_max_atoms", "BWD_RECOMPUTE",
@@ -85,6 +86,7 @@ def load_library():
             "tpl_fullatom_backward": ([P, P, P, I, I, I, P, P, P, P, Z, O, P], I),
             "tpl_lrmsd_forward": ([P, P, P, I, I, P, P, Z, P], I),
             "tpl_lrmsd_backward": ([P, P, P, P, I, I, P, P, Z, P], I),
+            "tpl_lrmsd_forward_noalloc": ([P, P, P, I, I, P, P], I),
             "tpl_backbone_forward_ref64": ([P, P, I, I, P, P], I),
             "tpl_backbone_backward_ref64": ([P, P, I, I, P, P, P, P], I),
             "tpl_fullatom_forward_ref64": ([P, P, P, I, I, I, P, P, P], I),
@@ -200,6 +202,15 @@ def tpl_lrmsd_forward(input, target, num_atoms, lrmsd_out, workspace, stream=Non
         _ptr(_cuda(num_atoms, torch.int32, "num_atoms")), P, Nmax,
         _ptr(_cuda(lrmsd_out, torch.float32, "lrmsd")), _ptr(workspace),
         workspace.numel() * workspace.element_size(), _stream(input, stream)))
+
+
+def tpl_lrmsd_forward_noalloc(input, target, num_atoms, lrmsd_out, stream=None):
+    """LRMSD forward with the library's fixed internal scratch (no workspace)."""
+    P, Nmax, _ = input.shape
+    _check("tpl_lrmsd_forward_noalloc", load_library().tpl_lrmsd_forward_noalloc(
+        _ptr(_cuda(input, torch.float32, "input")), _ptr(_cuda(target, torch.float32, "target")),
+        _ptr(_cuda(num_atoms, torch.int32, "num_atoms")), P, Nmax,
+        _ptr(_cuda(lrmsd_out, torch.float32, "lrmsd")), _stream(input, stream)))
 
 
 def tpl_lrmsd_backward(grad_lrmsd, input, target, num_atoms, grad_input, workspace, stream=None):

@@ -375,6 +375,24 @@ tpl_status tpl_lrmsd_backward(const float* grad_lrmsd, const float* input, const
     return ok();
 }
 
+tpl_status tpl_lrmsd_forward_noalloc(const float* input, const float* target,
+                                     const int32_t* num_atoms, int P, int Nmax, float* lrmsd,
+                                     tpl_stream stream) {
+    const void* ptrs[4] = {input, target, num_atoms, lrmsd};
+    tpl_status st = check_pair_args(P, Nmax, ptrs, 4);
+    if (st) return st;
+    if (P == 0) return ok();
+    if (P > lrmsd_noalloc_max_pairs() || Nmax > lrmsd_noalloc_max_atoms())
+        return fail(TPL_ERR_BAD_SHAPE,
+                    "P=%d, Nmax=%d exceed the allocation-free limits (P <= %d, Nmax <= %d); "
+                    "use tpl_lrmsd_forward with a workspace",
+                    P, Nmax, lrmsd_noalloc_max_pairs(), lrmsd_noalloc_max_atoms());
+    cudaError_t e = launch_lrmsd_forward_noalloc(input, target, num_atoms, P, Nmax, lrmsd,
+                                                 reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "lrmsd_forward_noalloc");
+    return ok();
+}
+
 // --------------------------------------------------------------------------- FP64 forms
 static tpl_status check_ref_args(int B, int Lmax, const void* const* ptrs, int nptr) {
     if (B < 0 || Lmax < 0) return fail(TPL_ERR_INVALID_ARG, "sizes must be >= 0");

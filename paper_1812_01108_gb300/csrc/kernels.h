@@ -48,6 +48,15 @@ cudaError_t launch_lrmsd_backward(const float* grad_lrmsd, const float* input,
                                   const float* target, const int32_t* num_atoms, int P, int Nmax,
                                   float* grad_input, const void* ws, cudaStream_t s);
 
+// LRMSD forward with its scratch in a fixed device array (no workspace, no
+// allocation); sizes above the maxima are rejected by the caller.
+int lrmsd_noalloc_max_pairs();
+int lrmsd_noalloc_max_atoms();
+size_t lrmsd_noalloc_scratch_bytes();
+cudaError_t launch_lrmsd_forward_noalloc(const float* input, const float* target,
+                                         const int32_t* num_atoms, int P, int Nmax, float* lrmsd,
+                                         cudaStream_t s);
+
 // K7: plain FP64 per-chain forms.
 cudaError_t launch_backbone_forward_ref64(const double* angles, const int32_t* lengths, int B,
                                           int Lmax, double* coords, cudaStream_t s);

@@ -17,6 +17,8 @@
 //      the chunk partials in FP64 by the last CTA of the pair.
 // Backward:
 //  K6 lrmsd_grad: grad_y_i = w (y'_i - U x'_i) / (N LRMSD).
+#include <mutex>
+
 #include "kernels.h"
 #include "tpl_common.cuh"
 
@@ -35,10 +37,10 @@ struct WsLayout {
     int nch;
 };
 
-__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+__host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-__host__ __device__ inline WsLayout ws_layout(int P, int Nmax) {
-    WsLayout w;
+__host__ __device__ constexpr WsLayout ws_layout(int P, int Nmax) {
+    WsLayout w{};
     w.nch = (Nmax + kChunk - 1) / kChunk;
     if (w.nch < 1) w.nch = 1;
     size_t o = 0;
@@ -676,6 +678,62 @@ cudaError_t launch_lrmsd_backward_ref64(const double* grad_lrmsd, const double* 
     lrmsd_bwd_ref64_kernel<<<P, kRefNT, 0, s>>>(grad_lrmsd, input, target, num_atoms, P, Nmax, state,
                                                 grad_input);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free LRMSD forward.
+//
+// Some callers cannot allocate device memory and cannot hand this library a
+// workspace either: code running under a framework or runtime whose allocator
+// owns all device memory and refuses new allocations once a run is planned, or
+// behind an interface that has no argument for scratch memory.  For them the
+// forward keeps its scratch in the fixed array below, which lives in the
+// library's own device memory: every GPU that loads the library holds
+// kNoAllocScratchBytes for it until the process exits.  The caller still owns
+// the inputs and the output.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocMaxPairs = 4096;
+constexpr int kNoAllocMaxAtoms = 8192;
+constexpr size_t kNoAllocScratchBytes = ws_layout(kNoAllocMaxPairs, kNoAllocMaxAtoms).total;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name only stands in for the symbol, so the address is looked up
+// with cudaGetSymbolAddress, once per device, with that device current.
+static cudaError_t noalloc_scratch_address(void** out) {
+    static std::mutex mu;
+    static void* addr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = p;
+    }
+    *out = addr[dev];
+    return cudaSuccess;
+}
+
+int lrmsd_noalloc_max_pairs() { return kNoAllocMaxPairs; }
+int lrmsd_noalloc_max_atoms() { return kNoAllocMaxAtoms; }
+size_t lrmsd_noalloc_scratch_bytes() { return kNoAllocScratchBytes; }
+
+cudaError_t launch_lrmsd_forward_noalloc(const float* input, const float* target,
+                                         const int32_t* num_atoms, int P, int Nmax, float* lrmsd,
+                                         cudaStream_t s) {
+    if (P == 0) return cudaSuccess;
+    void* scratch = nullptr;
+    cudaError_t e = noalloc_scratch_address(&scratch);
+    if (e != cudaSuccess) return e;
+    // Nothing in the scratch has to start at zero: every chunk partial that is
+    // read is written first in the same call, and the per-pair completion
+    // counters are reset by the solve kernel before the residual kernel counts.
+    return launch_lrmsd_forward(input, target, num_atoms, P, Nmax, lrmsd, scratch, s);
 }
 
 }  // namespace tpl
