@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
                                                                  int B, int Lmax, int tile,
                                                                  int longest_first, ChainWs ws) {
     __shared__ int hist[kBuckets];
-    __shared__ int s_part[kSchedThreads];
+    __shared__ int s_part[33];
     int* order = reinterpret_cast<int*>(ws.bagg);  // scratch: the backward's area is free here
     for (int i = threadIdx.x; i < B * ws.tmax; i += kSchedThreads) ws.fflag[i] = 0;
     auto len = [&](int b) {
@@ -95,15 +95,29 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
     };
     int mine = 0;
     for (int i = i0; i < i1; ++i) mine += ntiles(order[i]);
-    s_part[threadIdx.x] = mine;
-    __syncthreads();
-    for (int off = 1; off < kSchedThreads; off <<= 1) {  // inclusive Hillis-Steele scan
-        const int v = threadIdx.x >= off ? s_part[threadIdx.x - off] : 0;
-        __syncthreads();
-        s_part[threadIdx.x] += v;
-        __syncthreads();
+    // block-wide exclusive scan of `mine`: warp shuffles, then the warp totals
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = mine;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
     }
-    int base = s_part[threadIdx.x] - mine;
+    if (lane == 31) s_part[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const int w = s_part[lane];
+        int wi = w;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += y;
+        }
+        s_part[lane] = wi - w;  // exclusive prefix of warp totals
+        if (lane == 31) s_part[32] = wi;
+    }
+    __syncthreads();
+    int base = s_part[warp] + inc - mine;
     for (int i = i0; i < i1; ++i) {
         const int b = order[i];
         const int n = ntiles(b);
@@ -111,7 +125,7 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
         base += n;
     }
     if (threadIdx.x == 0) {
-        ws.hdr[kHdrTiles] = s_part[kSchedThreads - 1];
+        ws.hdr[kHdrTiles] = s_part[32];
         ws.hdr[kHdrFwdNext] = 0;
         ws.hdr[kHdrTile] = tile;
         ws.hdr[kHdrMagic] = kWsMagic;

@@ -108,40 +108,32 @@ __device__ __forceinline__ void store_range(float* __restrict__ glob, const floa
     for (int i = tail + threadIdx.x; i < g1; i += NT) glob[i] = stage[i - g0];
 }
 
-// Store of the float range [g0, g1) of tile-local atom coordinates stage[i -
-// g0] (3 floats per atom), each atom mapped by P on the way: 16-byte aligned
-// global stores; an aligned chunk spans at most two atoms.
+// Asynchronous copy (cp.async, no register round trip) of the float range
+// [g0, g1) of global memory into stage[off + i - g0], off = g0 mod 4: 16-byte
+// copies for the aligned middle, 4-byte copies for the ragged ends.  The caller
+// commits and waits (cp_async_wait_all) before a barrier.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 template <int NT>
-__device__ __forceinline__ void store_range_transformed(float* __restrict__ glob,
-                                                        const float* __restrict__ stage,
-                                                        const Rigid& P, int g0, int g1) {
+__device__ __forceinline__ void async_copy_range(const float* __restrict__ glob, float* __restrict__ stage,
+                                                 int g0, int g1) {
     if (g1 <= g0) return;
-    auto atom = [&](int a) {
-        return point_apply(P, make_float3(stage[3 * a], stage[3 * a + 1], stage[3 * a + 2]));
-    };
-    auto comp = [](float3 r, int c) { return c == 0 ? r.x : (c == 1 ? r.y : r.z); };
+    const int off = g0 & 3;
     const int head = min(g1, (g0 + 3) & ~3);
     const int tail = max(head, g1 & ~3);
-    for (int i = g0 + threadIdx.x; i < head; i += NT) {
-        const int f = i - g0;
-        glob[i] = comp(atom(f / 3), f % 3);
-    }
-    for (int q = head / 4 + threadIdx.x; q < tail / 4; q += NT) {
-        const int f = 4 * q - g0;
-        const int a0 = f / 3, c0 = f - 3 * a0;
-        const float3 r0 = atom(a0), r1 = atom(a0 + 1);
-        float v[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int c = c0 + k;
-            v[k] = c < 3 ? comp(r0, c) : comp(r1, c - 3);
-        }
-        reinterpret_cast<float4*>(glob)[q] = make_float4(v[0], v[1], v[2], v[3]);
-    }
-    for (int i = tail + threadIdx.x; i < g1; i += NT) {
-        const int f = i - g0;
-        glob[i] = comp(atom(f / 3), f % 3);
-    }
+    for (int i = g0 + threadIdx.x; i < head; i += NT) cp_async4(stage + off + i - g0, glob + i);
+    for (int q = head / 4 + threadIdx.x; q < tail / 4; q += NT) cp_async16(stage + off + 4 * q - g0, glob + 4 * q);
+    for (int i = tail + threadIdx.x; i < g1; i += NT) cp_async4(stage + off + i - g0, glob + i);
 }
 
 template <int NT>
@@ -256,7 +248,9 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT>()) fa_fwd_kernel(
             for (int k = 0; k < ng; ++k) {
                 float sc, cc;
                 if (k < nchi) {
-                    sincosf(__ldg(ang + (3 + k) * Lmax + j), &sc, &cc);
+                    // chi moves only its own side chain (no error propagates along
+                    // the chain): the SFU sine/cosine is accurate enough here
+                    __sincosf(__ldg(ang + (3 + k) * Lmax + j), &sc, &cc);
                 } else {
                     cc = s_tab.fixchi[type][k].x;
                     sc = s_tab.fixchi[type][k].y;
@@ -271,13 +265,21 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT>()) fa_fwd_kernel(
             }
         }
         __syncthreads();
-        // frame at the tile start (every warp gathers it), applied while storing
+        // frame at the tile start (every warp gathers it), applied in place
         int pc;
         const Rigid P = gather_prefix(ws, slot0, t, pc);
-        if (threadIdx.x == 0) store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, pc);
+        if (threadIdx.x == 0) store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, pc, tile_atoms);
         const int end_atom = pc + tile_atoms;
+        const int nout = max(0, min(end_atom, Amax) - pc);
+        for (int a = threadIdx.x; a < nout; a += NT) {
+            const float3 r = point_apply(P, make_float3(stage[3 * a], stage[3 * a + 1], stage[3 * a + 2]));
+            stage[3 * a] = r.x;
+            stage[3 * a + 1] = r.y;
+            stage[3 * a + 2] = r.z;
+        }
+        __syncthreads();
         if (end_atom > Amax && threadIdx.x == 0) flag_status(TPL_STATUS_TOO_MANY_ATOMS);
-        store_range_transformed<NT>(out, stage, P, 3 * pc, 3 * min(end_atom, Amax));
+        store_range<NT>(out, stage, 3 * pc, 3 * (pc + nout));
         if (t == T - 1) {
             if (threadIdx.x == 0) num_atoms[b] = end_atom;
             zero_range<NT>(out, 3 * min(end_atom, Amax), 3 * Amax);
@@ -366,6 +368,14 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT>() > 2 ? fa_min_blocks<NT
         const float* g_in = grad_coords + (size_t)b * Amax * 3;
         float* ga = grad_angles + (size_t)b * 7 * Lmax;
 
+        // the forward recorded the tile's first atom and atom count: start the
+        // staging copies right away, then scan the counts while they fly
+        const float4 sd = ws.start[4 * (size_t)(slot0 + t) + 3];
+        const int pc = __float_as_int(sd.x);
+        const int soff = (3 * pc) & 3;
+        const int g1 = 3 * min(pc + __float_as_int(sd.y), Amax);
+        async_copy_range<NT>(r_in, st_r, 3 * pc, g1);
+        async_copy_range<NT>(g_in, st_g, 3 * pc, g1);
         const int j = t * NT + threadIdx.x;
         const bool valid = j < L;
         const int type = residue_type(sq, j, valid);
@@ -373,11 +383,6 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT>() > 2 ? fa_min_blocks<NT
         s_type[threadIdx.x] = (uint8_t)type;
         int tile_atoms;
         const int a0 = block_scan_int<NT>(nat, s_cnt, tile_atoms);
-        const int pc = __float_as_int(ws.start[4 * (size_t)(slot0 + t) + 3].x);
-        const int soff = (3 * pc) & 3;
-        const int g1 = 3 * min(pc + tile_atoms, Amax);
-        copy_range<NT, false>(const_cast<float*>(r_in), st_r, 3 * pc, g1);
-        copy_range<NT, false>(const_cast<float*>(g_in), st_g, 3 * pc, g1);
         if (threadIdx.x == 0 && t > 0) {  // C of the residue before the tile
             const int jp = t * NT - 1;
             const int ip = pc - s_tab.n_atoms[residue_type(sq, jp, true)] + 2;
@@ -385,6 +390,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT>() > 2 ? fa_min_blocks<NT
             s_prevc[1] = r_in[3 * ip + 1];
             s_prevc[2] = r_in[3 * ip + 2];
         }
+        cp_async_wait_all();
         __syncthreads();
 
         float gchi[kMaxGroups] = {0.f, 0.f, 0.f, 0.f};

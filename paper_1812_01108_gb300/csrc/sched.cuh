@@ -106,11 +106,11 @@ __device__ __forceinline__ bool wait_flag(const int* p) {
     return false;
 }
 
-__device__ __forceinline__ void store_rigid_g(float4* dst, const Rigid& m, int cnt) {
+__device__ __forceinline__ void store_rigid_g(float4* dst, const Rigid& m, int cnt, int cnt2 = 0) {
     dst[0] = make_float4(m.c0.x, m.c0.y, m.c0.z, m.c1.x);
     dst[1] = make_float4(m.c1.y, m.c1.z, m.c2.x, m.c2.y);
     dst[2] = make_float4(m.c2.z, m.t.x, m.t.y, m.t.z);
-    dst[3] = make_float4(__int_as_float(cnt), 0.f, 0.f, 0.f);
+    dst[3] = make_float4(__int_as_float(cnt), __int_as_float(cnt2), 0.f, 0.f);
 }
 
 // L2 reads (the data was written by another CTA of this launch).
