@@ -1,17 +1,25 @@
-"""Throughput benchmark of the hot path: one step = full-atom forward -> LRMSD
-forward (to perturbed target structures) -> LRMSD backward -> full-atom
-backward, on synthetic inputs shaped like the paper's workloads.
+"""Throughput benchmark of the hot path on synthetic inputs shaped like the
+paper's workloads.  Prints one JSON line (rank 0).
 
-Default workload: the training-step shape, 256 chains x 700 residues with
-uniformly random residue types (the largest full-atom configuration).  Prints
-one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on a
-bounded sample of the same workload instead.
+Workloads (``--workload``):
+  training_step   (default) full-atom training step, 256 chains x 700 residues,
+                  uniform residue types: full-atom forward -> LRMSD forward (to
+                  structures built from N(0, 0.1 rad)-perturbed angles) -> LRMSD
+                  backward -> full-atom backward.  Unit: residues/s.
+  backbone_uneven backbone step over 4096 chains of log-uniform lengths in
+                  [50, 1000]: backbone forward -> LRMSD -> backbone backward.
+                  Unit: residues/s.
+  lrmsd_batch     16384 coordinate-set pairs of U{100..5000} atoms: LRMSD
+                  forward + backward.  Unit: atoms/s (atoms of the input side).
 
-Timing: W warm-up steps, then K timed steps; each timed step is bracketed by
-CUDA events on the launching stream, and L2 is flushed (a 512 MiB write)
-before every step outside the timed interval.  Under torchrun each rank runs
-its own batch (weak scaling, no data-path collective); the elapsed time is the
-max over ranks.
+``--impl reference`` times the FP64 CPU oracle, as it stands, on a bounded
+sample of the same workload instead.
+
+Timing: W warm-up steps, then K timed steps; every C-ABI call of a step is a
+CUDA graph replayed between CUDA events on the launching stream, and L2 is
+flushed (a 512 MiB write, outside the events) before every step.  Under
+torchrun each rank runs its own batch (weak scaling, no data-path collective);
+the elapsed time is the max over ranks.
 """
 from __future__ import annotations
 
@@ -28,6 +36,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "residues/s fwd+bwd at FP32 err≤2e-3 Å vs plain FP64 GPU form; HBM roofline %"
+METRIC_LRMSD = "atoms/s LRMSD fwd+bwd vs plain FP64 GPU form; HBM roofline %"
+
+DEFAULT_BATCH = {"training_step": 256, "backbone_uneven": 4096, "lrmsd_batch": 16384}
+
+# DRAM bytes per launch of the dominant kernel from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload, with the
+# profile summary that holds the capture.  None when the kernel changed after
+# the capture.
+TRAFFIC = {
+    "training_step": None,
+    "backbone_uneven": None,
+    "lrmsd_batch": None,
+}
 
 
 def parse():
@@ -36,14 +57,19 @@ def parse():
     p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="tpl", choices=["tpl", "reference"])
-    p.add_argument("--batch", type=int, default=256)
-    p.add_argument("--length", type=int, default=700)
+    p.add_argument("--workload", default="training_step", choices=sorted(DEFAULT_BATCH))
+    p.add_argument("--batch", type=int, default=0, help="chains (or pairs) per GPU; 0 = workload default")
+    p.add_argument("--length", type=int, default=700, help="residues per chain (training_step)")
     p.add_argument("--threads", type=int, default=0, help="CTA size of the chain kernels (0 = default)")
+    p.add_argument("--res-per-thread", type=int, default=0, help="backbone residues per thread (0 = default)")
     p.add_argument("--bwd", default="coords", choices=["coords", "recompute"],
-                   help="full-atom backward: read the forward's coordinates or rebuild frames")
+                   help="chain backward: read the forward's coordinates or rebuild frames")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 per-chain comparison")
-    return p.parse_args()
+    a = p.parse_args()
+    if a.batch <= 0:
+        a.batch = DEFAULT_BATCH[a.workload]
+    return a
 
 
 def dist_env():
@@ -53,14 +79,46 @@ def dist_env():
     return rank, world, local
 
 
-def make_workload(B, L, rank):
+# ----------------------------------------------------------------------------- host inputs
+def make_inputs(args, rank):
+    """Seeded host arrays of the workload (one batch per rank)."""
     import workloads
 
-    rng = workloads.rng_for(4, salt=rank)
-    lengths = np.full(B, L, np.int32)
-    a, seq = workloads.fullatom_inputs(lengths, rng)
-    ta = workloads.perturb_angles(a, lengths, rng, rows=(0, 1, 3, 4, 5, 6))
-    return a, seq, lengths, ta
+    if args.workload == "training_step":
+        rng = workloads.rng_for(4, salt=rank)
+        lengths = np.full(args.batch, args.length, np.int32)
+        a, seq = workloads.fullatom_inputs(lengths, rng)
+        ta = workloads.perturb_angles(a, lengths, rng, rows=(0, 1, 3, 4, 5, 6))
+        return {"angles": a, "seq": seq, "lengths": lengths, "target_angles": ta}
+    if args.workload == "backbone_uneven":
+        rng = workloads.rng_for(2, salt=rank)
+        lengths = workloads.lengths_loguniform(args.batch, 50, 1000, rng)
+        a = workloads.backbone_angles(lengths, rng, Lmax=workloads.pad_to(1000))
+        ta = workloads.perturb_angles(a, lengths, rng)
+        return {"angles": a, "lengths": lengths, "target_angles": ta}
+    rng = workloads.rng_for(3, salt=rank)
+    x, y, n = workloads.lrmsd_clouds(args.batch, 100, 5000, rng)
+    return {"input": x, "target": y, "num_atoms": n}
+
+
+def describe(args, world):
+    B = args.batch
+    if args.workload == "training_step":
+        return (METRIC, "residues/s", {
+            "workload": f"full-atom training step, {B} chains x {args.length} residues per GPU, "
+                        "uniform residue types, phi/psi/chi ~ U[-pi,pi], omega = pi; forward -> "
+                        "LRMSD to N(0,0.1 rad)-perturbed targets -> backward",
+            "global_batch": B * world, "seq_len": args.length})
+    if args.workload == "backbone_uneven":
+        return (METRIC, "residues/s", {
+            "workload": f"backbone step, {B} chains per GPU, lengths log-uniform in [50,1000], "
+                        "phi/psi ~ U[-pi,pi], omega = pi; forward -> LRMSD to "
+                        "N(0,0.1 rad)-perturbed targets -> backward",
+            "global_batch": B * world, "seq_len": "logU[50,1000]"})
+    return (METRIC_LRMSD, "atoms/s", {
+        "workload": f"LRMSD batch, {B} pairs per GPU, atoms U{{100..5000}}, N(0,15 A) clouds, "
+                    "target = rotated + N(0,10 A) shift + N(0,0.5 A) noise; forward + backward",
+        "global_batch": B * world})
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -111,65 +169,326 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- oracle arm
-def oracle_sample(a, seq, lengths, ta, n_chains):
-    """The FP64 CPU oracle, as it stands, on the first n_chains of the batch: one full step."""
+def oracle_step(args, d, n):
+    """One step of the FP64 CPU oracle, as it stands, on the first n chains (or
+    pairs) of the batch.  Returns (seconds, units processed)."""
     import oracle
 
-    s = slice(0, n_chains)
-    Amax = oracle.max_atoms(seq[s], lengths[s])
+    s = slice(0, n)
+    if args.workload == "training_step":
+        a, seq, L, ta = d["angles"][s], d["seq"][s], d["lengths"][s], d["target_angles"][s]
+        Amax = oracle.max_atoms(seq, L)
+        t0 = time.perf_counter()
+        tgt, na = oracle.fullatom_forward(ta, seq, L, Amax)
+        c, na = oracle.fullatom_forward(a, seq, L, Amax)
+        oracle.lrmsd_forward(c, tgt, na)
+        g = oracle.lrmsd_backward(np.full(n, 1.0 / n), c, tgt, na)
+        oracle.fullatom_backward(a, seq, L, g)
+        return time.perf_counter() - t0, int(L.sum())
+    if args.workload == "backbone_uneven":
+        a, L, ta = d["angles"][s], d["lengths"][s], d["target_angles"][s]
+        t0 = time.perf_counter()
+        tgt = oracle.backbone_forward(ta, L)
+        c = oracle.backbone_forward(a, L)
+        na = 3 * L
+        oracle.lrmsd_forward(c, tgt, na)
+        g = oracle.lrmsd_backward(np.full(n, 1.0 / n), c, tgt, na)
+        oracle.backbone_backward(a, L, g)
+        return time.perf_counter() - t0, int(L.sum())
+    x, y, na = d["input"][s], d["target"][s], d["num_atoms"][s]
     t0 = time.perf_counter()
-    tgt, na = oracle.fullatom_forward(ta[s], seq[s], lengths[s], Amax)
-    c, na = oracle.fullatom_forward(a[s], seq[s], lengths[s], Amax)
-    oracle.lrmsd_forward(c, tgt, na)
-    g = oracle.lrmsd_backward(np.full(n_chains, 1.0 / n_chains), c, tgt, na)
-    oracle.fullatom_backward(a[s], seq[s], lengths[s], g)
-    return time.perf_counter() - t0
+    oracle.lrmsd_forward(x, y, na)
+    oracle.lrmsd_backward(np.ones(n), x, y, na)
+    return time.perf_counter() - t0, int(na.sum())
 
 
-def cpu_baseline(a, seq, lengths, ta, budget_s=12.0):
+def oracle_count(args, d, budget_s):
+    """How many chains (pairs) make one oracle step of about budget_s seconds."""
+    t1, _ = oracle_step(args, d, 1)
+    total = len(next(iter(d.values())))
+    return int(max(1, min(total, budget_s / max(t1, 1e-3))))
+
+
+def cpu_baseline(args, d, unit, budget_s=12.0):
     import oracle
 
     oracle.build()
-    t1 = oracle_sample(a, seq, lengths, ta, 1)
-    n = int(max(1, min(len(lengths), budget_s / max(t1, 1e-3))))
-    t = oracle_sample(a, seq, lengths, ta, n)
-    res = int(lengths[:n].sum())
-    return {"value": res / t, "unit": "residues/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} of {len(lengths)} chains x {int(lengths[0])} residues, one full step "
-                      f"(forward, LRMSD forward+backward, backward) in {t:.1f} s, single thread"}
+    n = oracle_count(args, d, budget_s)
+    t, units = oracle_step(args, d, n)
+    total = len(next(iter(d.values())))
+    return {"value": units / t, "unit": unit, "cores": 1, "kind": "oracle",
+            "sample": f"first {n} of {total} chains/pairs of the workload, one full step in "
+                      f"{t:.1f} s, single thread"}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    a, seq, lengths, ta = make_workload(args.batch, args.length, 0)
     import oracle
 
     oracle.build()
-    t1 = oracle_sample(a, seq, lengths, ta, 1)
+    d = make_inputs(args, 0)
+    metric, unit, config = describe(args, 1)
     # the whole run stays near two minutes whatever --steps is
-    per_step = 120.0 / (args.steps + 1)
-    n = int(max(1, min(args.batch, per_step / max(t1, 1e-3))))
+    n = oracle_count(args, d, 120.0 / (args.steps + 1))
     for _ in range(min(args.warmup, 1)):
-        oracle_sample(a, seq, lengths, ta, n)
-    times = [oracle_sample(a, seq, lengths, ta, n) for _ in range(args.steps)]
-    res = int(lengths[:n].sum())
-    value = res * len(times) / sum(times)
+        oracle_step(args, d, n)
+    times, units = [], 0
+    for _ in range(args.steps):
+        t, u = oracle_step(args, d, n)
+        times.append(t)
+        units += u
+    value = units / sum(times)
+    config["sample_chains"] = n
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "residues/s",
+        "impl": "reference", "metric": metric, "value": value, "unit": unit,
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"full-atom training step, {args.batch} chains x {args.length} "
-                               "residues (forward, LRMSD forward+backward, backward)",
-                   "sample_chains": n},
-        "cpu_baseline": {"value": value, "unit": "residues/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{n} chains per step of the same workload, single thread"},
-        "e2e": {"value": value, "unit": "residues/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0},
+        "config": config,
+        "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
+                         "sample": f"first {n} chains/pairs of the workload per step, single thread"},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------- GPU workloads
+class Step:
+    """The C-ABI calls of one step with their bookkeeping.
+
+    calls    [(name, fn)] in launch order
+    launches {name: kernels of ours per call}
+    kernels  {name: [kernel names]}
+    alg      {name: algorithmic bytes per call}
+    units    units (residues or atoms) per step
+    h2d      [(device tensor, pinned host tensor)] inputs of a step
+    d2h      (pinned host tensor, device tensor) the step's result
+    fp64     callable -> dict (errors vs the FP64 per-chain GPU form, its throughput)
+    """
+
+
+def setup_training_step(args, tpl, torch, dev, d):
+    import workloads
+
+    a, seq, lengths, ta = d["angles"], d["seq"], d["lengths"], d["target_angles"]
+    B, Lmax = a.shape[0], a.shape[2]
+    Amax = workloads.pad_to(tpl.fullatom_max_atoms(seq, lengths))
+    opts = tpl.Opts(threads=args.threads,
+                    bwd_mode=tpl.BWD_FROM_COORDS if args.bwd == "coords" else tpl.BWD_RECOMPUTE)
+    A = torch.from_numpy(a).to(dev)
+    S = torch.from_numpy(seq).to(dev)
+    Ln = torch.from_numpy(lengths).to(dev)
+    TA = torch.from_numpy(ta).to(dev)
+    coords = torch.empty((B, Amax, 3), device=dev)
+    target = torch.empty((B, Amax, 3), device=dev)
+    na = torch.empty((B,), dtype=torch.int32, device=dev)
+    na_t = torch.empty_like(na)
+    lr = torch.empty((B,), device=dev)
+    wgt = torch.full((B,), 1.0 / B, device=dev)  # d(mean LRMSD)/d(LRMSD_b)
+    gcoords = torch.empty_like(coords)
+    gang = torch.empty_like(A)
+    fa_ws = torch.empty(tpl.tpl_fullatom_workspace_size(B, Lmax), dtype=torch.uint8, device=dev)
+    lr_ws = torch.empty(tpl.tpl_lrmsd_workspace_size(B, Amax), dtype=torch.uint8, device=dev)
+    tpl.tpl_fullatom_forward(TA, S, Ln, target, na_t, fa_ws, opts)  # target structures
+    torch.cuda.synchronize()
+    n_atoms = int(na_t.sum().item())
+
+    st = Step()
+    st.calls = [
+        ("fullatom_forward", lambda: tpl.tpl_fullatom_forward(A, S, Ln, coords, na, fa_ws, opts)),
+        ("lrmsd_forward", lambda: tpl.tpl_lrmsd_forward(coords, target, na, lr, lr_ws)),
+        ("lrmsd_backward", lambda: tpl.tpl_lrmsd_backward(wgt, coords, target, na, gcoords, lr_ws)),
+        ("fullatom_backward",
+         lambda: tpl.tpl_fullatom_backward(A, S, Ln, coords, gcoords, gang, fa_ws, opts)),
+    ]
+    bwd_kernel = "fa_bwd_coords_kernel" if args.bwd == "coords" else "fa_bwd_kernel"
+    st.kernels = {"fullatom_forward": ["schedule_kernel", "fa_fwd_kernel"],
+                  "lrmsd_forward": ["lrmsd_moments_kernel", "lrmsd_solve_kernel", "lrmsd_residual_kernel"],
+                  "lrmsd_backward": ["lrmsd_grad_kernel"], "fullatom_backward": [bwd_kernel]}
+    st.launches = {k: len(v) for k, v in st.kernels.items()}
+    res = int(lengths.sum())
+    st.alg = {
+        "fullatom_forward": res * (28 + 1) + 12 * n_atoms,
+        "lrmsd_forward": 24 * n_atoms,
+        "lrmsd_backward": 36 * n_atoms,
+        "fullatom_backward": res * (28 + 1 + 28) + 12 * n_atoms,
+    }
+    st.units = res
+    st.extra_config = {"atoms_per_gpu": n_atoms, "threads": args.threads or "default",
+                       "fullatom_backward": args.bwd}
+    tgt_host = target.cpu().pin_memory()
+    st.h2d = [(A, torch.from_numpy(a).pin_memory()), (S, torch.from_numpy(seq).pin_memory()),
+              (Ln, torch.from_numpy(lengths).pin_memory()), (target, tgt_host)]
+    st.d2h = (torch.empty((B,), dtype=torch.float32).pin_memory(), lr)
+
+    def fp64():
+        A64 = torch.from_numpy(a.astype(np.float64)).to(dev)
+        c64 = torch.zeros((B, Amax, 3), dtype=torch.float64, device=dev)
+        t64 = torch.zeros_like(c64)
+        na64 = torch.zeros((B,), dtype=torch.int32, device=dev)
+        lr64 = torch.zeros((B,), dtype=torch.float64, device=dev)
+        state = torch.zeros((B, 16), dtype=torch.float64, device=dev)
+        gc = torch.zeros_like(c64)
+        ga = torch.zeros_like(A64)
+        w = torch.full((B,), 1.0 / B, dtype=torch.float64, device=dev)
+        # the FP64 form gets the FP32 step's own target so only the step's arithmetic differs
+        t64.copy_(target.double())
+
+        def step64():
+            tpl.tpl_fullatom_forward_ref64(A64, S, Ln, c64, na64)
+            tpl.tpl_lrmsd_forward_ref64(c64, t64, na64, lr64, state)
+            tpl.tpl_lrmsd_backward_ref64(w, c64, t64, na64, state, gc)
+            tpl.tpl_fullatom_backward_ref64(A64, S, Ln, c64, gc, ga)
+
+        ms = time_once(torch, step64)
+        return {"fp64_gpu_form": {"value": res / (ms * 1e-3), "unit": "residues/s", "ms_per_step": ms},
+                "errors_vs_fp64_gpu": errors(torch, coords, c64, gang, ga, lr, lr64)}
+
+    st.fp64 = fp64
+    return st
+
+
+def setup_backbone_uneven(args, tpl, torch, dev, d):
+    a, lengths, ta = d["angles"], d["lengths"], d["target_angles"]
+    B, Lmax = a.shape[0], a.shape[2]
+    opts = tpl.Opts(threads=args.threads, res_per_thread=args.res_per_thread,
+                    bwd_mode=tpl.BWD_FROM_COORDS if args.bwd == "coords" else tpl.BWD_RECOMPUTE)
+    A = torch.from_numpy(a).to(dev)
+    Ln = torch.from_numpy(lengths).to(dev)
+    na_host = (3 * lengths).astype(np.int32)
+    na = torch.from_numpy(na_host).to(dev)
+    coords = torch.empty((B, 3 * Lmax, 3), device=dev)
+    target = torch.empty_like(coords)
+    lr = torch.empty((B,), device=dev)
+    wgt = torch.full((B,), 1.0 / B, device=dev)
+    gcoords = torch.empty_like(coords)
+    gang = torch.empty_like(A)
+    bb_ws = torch.empty(tpl.tpl_backbone_workspace_size(B, Lmax), dtype=torch.uint8, device=dev)
+    lr_ws = torch.empty(tpl.tpl_lrmsd_workspace_size(B, 3 * Lmax), dtype=torch.uint8, device=dev)
+    tpl.tpl_backbone_forward(torch.from_numpy(ta).to(dev), Ln, target, bb_ws, opts)
+    torch.cuda.synchronize()
+    n_atoms = int(na_host.sum())
+    res = int(lengths.sum())
+
+    st = Step()
+    st.calls = [
+        ("backbone_forward", lambda: tpl.tpl_backbone_forward(A, Ln, coords, bb_ws, opts)),
+        ("lrmsd_forward", lambda: tpl.tpl_lrmsd_forward(coords, target, na, lr, lr_ws)),
+        ("lrmsd_backward", lambda: tpl.tpl_lrmsd_backward(wgt, coords, target, na, gcoords, lr_ws)),
+        ("backbone_backward",
+         lambda: tpl.tpl_backbone_backward(A, Ln, coords, gcoords, gang, bb_ws, opts)),
+    ]
+    st.kernels = {"backbone_forward": ["schedule_kernel", "bb_fwd_kernel"],
+                  "lrmsd_forward": ["lrmsd_moments_kernel", "lrmsd_solve_kernel", "lrmsd_residual_kernel"],
+                  "lrmsd_backward": ["lrmsd_grad_kernel"], "backbone_backward": ["bb_bwd_kernel"]}
+    st.launches = {k: len(v) for k, v in st.kernels.items()}
+    st.alg = {"backbone_forward": 48 * res, "lrmsd_forward": 24 * n_atoms,
+              "lrmsd_backward": 36 * n_atoms, "backbone_backward": 60 * res}
+    st.units = res
+    st.extra_config = {"atoms_per_gpu": n_atoms, "threads": args.threads or "default",
+                       "res_per_thread": args.res_per_thread or "default", "backbone_backward": args.bwd}
+    st.h2d = [(A, torch.from_numpy(a).pin_memory()), (Ln, torch.from_numpy(lengths).pin_memory()),
+              (na, torch.from_numpy(na_host).pin_memory()), (target, target.cpu().pin_memory())]
+    st.d2h = (torch.empty((B,), dtype=torch.float32).pin_memory(), lr)
+
+    def fp64():
+        A64 = torch.from_numpy(a.astype(np.float64)).to(dev)
+        c64 = torch.zeros((B, 3 * Lmax, 3), dtype=torch.float64, device=dev)
+        t64 = target.double()
+        lr64 = torch.zeros((B,), dtype=torch.float64, device=dev)
+        state = torch.zeros((B, 16), dtype=torch.float64, device=dev)
+        gc = torch.zeros_like(c64)
+        ga = torch.zeros_like(A64)
+        w = torch.full((B,), 1.0 / B, dtype=torch.float64, device=dev)
+
+        def step64():
+            tpl.tpl_backbone_forward_ref64(A64, Ln, c64)
+            tpl.tpl_lrmsd_forward_ref64(c64, t64, na, lr64, state)
+            tpl.tpl_lrmsd_backward_ref64(w, c64, t64, na, state, gc)
+            tpl.tpl_backbone_backward_ref64(A64, Ln, c64, gc, ga)
+
+        ms = time_once(torch, step64)
+        return {"fp64_gpu_form": {"value": res / (ms * 1e-3), "unit": "residues/s", "ms_per_step": ms},
+                "errors_vs_fp64_gpu": errors(torch, coords, c64, gang, ga, lr, lr64)}
+
+    st.fp64 = fp64
+    return st
+
+
+def setup_lrmsd_batch(args, tpl, torch, dev, d):
+    x, y, n = d["input"], d["target"], d["num_atoms"]
+    P, Nmax = x.shape[0], x.shape[1]
+    X = torch.from_numpy(x).to(dev)
+    Y = torch.from_numpy(y).to(dev)
+    NA = torch.from_numpy(n).to(dev)
+    lr = torch.empty((P,), device=dev)
+    up = torch.ones((P,), device=dev)
+    gx = torch.empty_like(X)
+    ws = torch.empty(tpl.tpl_lrmsd_workspace_size(P, Nmax), dtype=torch.uint8, device=dev)
+    n_atoms = int(n.sum())
+
+    st = Step()
+    st.calls = [("lrmsd_forward", lambda: tpl.tpl_lrmsd_forward(X, Y, NA, lr, ws)),
+                ("lrmsd_backward", lambda: tpl.tpl_lrmsd_backward(up, X, Y, NA, gx, ws))]
+    st.kernels = {"lrmsd_forward": ["lrmsd_moments_kernel", "lrmsd_solve_kernel", "lrmsd_residual_kernel"],
+                  "lrmsd_backward": ["lrmsd_grad_kernel"]}
+    st.launches = {k: len(v) for k, v in st.kernels.items()}
+    st.alg = {"lrmsd_forward": 24 * n_atoms, "lrmsd_backward": 36 * n_atoms}
+    st.units = n_atoms
+    st.extra_config = {"atoms_per_gpu": n_atoms, "Nmax": Nmax}
+    st.h2d = [(X, torch.from_numpy(x).pin_memory()), (Y, torch.from_numpy(y).pin_memory()),
+              (NA, torch.from_numpy(n).pin_memory())]
+    st.d2h = (torch.empty((P,), dtype=torch.float32).pin_memory(), lr)
+
+    def fp64():
+        X64, Y64 = X.double(), Y.double()
+        lr64 = torch.zeros((P,), dtype=torch.float64, device=dev)
+        state = torch.zeros((P, 16), dtype=torch.float64, device=dev)
+        g64 = torch.zeros_like(X64)
+        up64 = torch.ones((P,), dtype=torch.float64, device=dev)
+
+        def step64():
+            tpl.tpl_lrmsd_forward_ref64(X64, Y64, NA, lr64, state)
+            tpl.tpl_lrmsd_backward_ref64(up64, X64, Y64, NA, state, g64)
+
+        ms = time_once(torch, step64)
+        g32 = gx.double().reshape(P, -1)
+        g6 = g64.reshape(P, -1)
+        grad_rel = float(((g32 - g6).norm(dim=1) / g6.norm(dim=1).clamp_min(1e-300)).max().item())
+        return {"fp64_gpu_form": {"value": n_atoms / (ms * 1e-3), "unit": "atoms/s", "ms_per_step": ms},
+                "errors_vs_fp64_gpu": {"lrmsd_max_abs_A": float((lr.double() - lr64).abs().max().item()),
+                                       "grad_rel_max": grad_rel}}
+
+    st.fp64 = fp64
+    return st
+
+
+def time_once(torch, fn):
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def errors(torch, c32, c64, g32, g64, lr32, lr64):
+    """Max-abs coordinate error, per-chain relative angle-gradient error (max over
+    chains) and max-abs LRMSD error of the FP32 step against the FP64 form."""
+    B = c32.shape[0]
+    a = g32.double().reshape(B, -1)
+    b = g64.reshape(B, -1)
+    return {"coord_max_abs_A": float((c32.double() - c64).abs().max().item()),
+            "grad_rel_max": float(((a - b).norm(dim=1) / b.norm(dim=1).clamp_min(1e-300)).max().item()),
+            "lrmsd_max_abs_A": float((lr32.double() - lr64).abs().max().item())}
+
+
+SETUP = {"training_step": setup_training_step, "backbone_uneven": setup_backbone_uneven,
+         "lrmsd_batch": setup_lrmsd_batch}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -194,59 +513,31 @@ def run_tpl(args):
         dist.barrier()
     tpl.load_library()
 
-    B, L = args.batch, args.length
-    a, seq, lengths, ta = make_workload(B, L, rank)
-    import workloads
-
-    Amax = workloads.pad_to(max(tpl.fullatom_max_atoms(seq, lengths), tpl.fullatom_max_atoms(seq, lengths)))
-    Lmax = a.shape[2]
-    opts = tpl.Opts(threads=args.threads,
-                    bwd_mode=tpl.BWD_FROM_COORDS if args.bwd == "coords" else tpl.BWD_RECOMPUTE)
-
-    # device-resident inputs
-    A = torch.from_numpy(a).to(dev)
-    S = torch.from_numpy(seq).to(dev)
-    Ln = torch.from_numpy(lengths).to(dev)
-    TA = torch.from_numpy(ta).to(dev)
-    coords = torch.empty((B, Amax, 3), device=dev)
-    target = torch.empty((B, Amax, 3), device=dev)
-    na = torch.empty((B,), dtype=torch.int32, device=dev)
-    na_t = torch.empty_like(na)
-    lr = torch.empty((B,), device=dev)
-    wgt = torch.full((B,), 1.0 / B, device=dev)  # d(mean LRMSD)/d(LRMSD_b)
-    gcoords = torch.empty_like(coords)
-    gang = torch.empty_like(A)
-    fa_ws = torch.empty(tpl.tpl_fullatom_workspace_size(B, Lmax), dtype=torch.uint8, device=dev)
-    lr_ws = torch.empty(tpl.tpl_lrmsd_workspace_size(B, Amax), dtype=torch.uint8, device=dev)
-    tpl.tpl_fullatom_forward(TA, S, Ln, target, na_t, fa_ws, opts)  # target structures
+    d = make_inputs(args, rank)
+    st = SETUP[args.workload](args, tpl, torch, dev, d)
+    metric, unit, config = describe(args, world)
+    names = [n for n, _ in st.calls]
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    names = ["fullatom_forward", "lrmsd_forward", "lrmsd_backward", "fullatom_backward"]
-    # our kernels per call: schedule + forward; moments + solve + residual; gradient; backward
-    launches = {"fullatom_forward": 2, "lrmsd_forward": 3, "lrmsd_backward": 1, "fullatom_backward": 1}
-
-    calls = [
-        lambda: tpl.tpl_fullatom_forward(A, S, Ln, coords, na, fa_ws, opts),
-        lambda: tpl.tpl_lrmsd_forward(coords, target, na, lr, lr_ws),
-        lambda: tpl.tpl_lrmsd_backward(wgt, coords, target, na, gcoords, lr_ws),
-        lambda: tpl.tpl_fullatom_backward(A, S, Ln, coords, gcoords, gang, fa_ws, opts),
-    ]
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
-        for c in calls:
+        for _, c in st.calls:
             c()
     torch.cuda.synchronize()
-    assert tpl.tpl_get_status() == 0
+    status = tpl.tpl_get_status()
+    if status != 0:
+        raise SystemExit(f"device status 0x{status:x} after the warm-up steps")
     # one CUDA graph per C-ABI call: replays cost the host a few microseconds, so
     # the events below see GPU time, not Python launch overhead
     graphs = []
-    for c in calls:
+    for _, c in st.calls:
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
             c()
         graphs.append(g)
     torch.cuda.synchronize()
+    nc = len(graphs)
 
     def step(ev=None):
         for i, g in enumerate(graphs):
@@ -254,14 +545,14 @@ def run_tpl(args):
                 ev[i].record(stream)
             g.replay()
         if ev is not None:
-            ev[4].record(stream)
+            ev[nc].record(stream)
 
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
         step()
     torch.cuda.synchronize()
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nc + 1)] for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -275,61 +566,49 @@ def run_tpl(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    per = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(4)] for k in range(args.steps)])
-    step_ms = per.sum(axis=1)
-    total_ms = float(step_ms.sum())
+    per = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(nc)] for k in range(args.steps)])
+    total_ms = float(per.sum())
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    residues = int(lengths.sum())
-    value = residues * world * args.steps / (total_ms * 1e-3)
+    value = st.units * world * args.steps / (total_ms * 1e-3)
 
-    # algorithmic bytes per launch (per-unit figures x units per launch)
-    n_atoms = int(na.sum().item())
-    alg = {
-        "fullatom_forward": residues * (28 + 1) + 12 * n_atoms,
-        "lrmsd_forward": 24 * n_atoms,
-        "lrmsd_backward": 36 * n_atoms,
-        "fullatom_backward": residues * (28 + 1 + 28) + 12 * n_atoms,
-    }
+    # roofline of the dominant call (per-unit bytes x units per launch / mean event time)
     mean_ms = per.mean(axis=0)
-    dom = int(np.argmax(mean_ms))
+    dom = names[int(np.argmax(mean_ms))]
     peaks = {}
     try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
     except (OSError, ValueError):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    achieved = alg[names[dom]] / (mean_ms[dom] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+    achieved = st.alg[dom] / (mean_ms[names.index(dom)] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "+".join(st.kernels[dom]), "call": dom,
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": TRAFFIC.get(args.workload),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "alg_bytes": alg[names[dom]]}
-    step_bytes = sum(alg.values())
+                "alg_bytes": st.alg[dom]}
+    step_bytes = sum(st.alg.values())
 
-    # end to end: pinned host inputs -> device, the step, loss -> host
-    pa = torch.from_numpy(a).pin_memory()
-    ps = torch.from_numpy(seq).pin_memory()
-    pl = torch.from_numpy(lengths).pin_memory()
-    tgt_host = target.cpu().pin_memory()
-    loss_host = torch.empty((B,), dtype=torch.float32).pin_memory()
-    h2d = pa.numel() * 4 + ps.numel() + pl.numel() * 4 + tgt_host.numel() * 4
-    d2h = loss_host.numel() * 4
+    # end to end: pinned host inputs -> device, the step, result -> host
+    h2d = sum(h.numel() * h.element_size() for _, h in st.h2d)
+    host_out, dev_out = st.d2h
+    d2h = host_out.numel() * host_out.element_size()
 
     def e2e_step():
-        A.copy_(pa, non_blocking=True)
-        S.copy_(ps, non_blocking=True)
-        Ln.copy_(pl, non_blocking=True)
-        target.copy_(tgt_host, non_blocking=True)
+        for dv, h in st.h2d:
+            dv.copy_(h, non_blocking=True)
         step()
-        loss_host.copy_(lr, non_blocking=True)
+        host_out.copy_(dev_out, non_blocking=True)
 
     for _ in range(2):
         e2e_step()
     torch.cuda.synchronize()
+    n_e2e = min(args.steps, 200)
     e_ms = 0.0
-    for _ in range(min(args.steps, 200)):
+    for _ in range(n_e2e):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -342,80 +621,39 @@ def run_tpl(args):
         t = torch.tensor([e_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e_ms = float(t.item())
-    e2e_value = residues * world * min(args.steps, 200) / (e_ms * 1e-3)
+    e2e_value = st.units * world * n_e2e / (e_ms * 1e-3)
 
+    # the e2e loop rewrote the inputs with the same values: the FP32 outputs the
+    # FP64 comparison reads are those of the last step
     extra = {}
     if rank == 0 and not args.no_fp64:
-        extra = fp64_comparison(tpl, torch, dev, a, seq, lengths, Amax, coords, gang, ta)
+        extra = st.fp64()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(a, seq, lengths, ta)
+        cpu = cpu_baseline(args, d, unit)
     if rank == 0:
+        config.update({"parallelism": f"replicas x{world}",
+                       "l2": "flushed (512 MiB write) before every step"})
+        config.update(st.extra_config)
         line = {
-            "metric": METRIC, "value": value, "unit": "residues/s", "n_gpus": world,
+            "metric": metric, "value": value, "unit": unit, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": f"full-atom training step, {B} chains x {L} residues per GPU, "
-                                   "uniform residue types, phi/psi/chi ~ U[-pi,pi], omega = pi; "
-                                   "forward -> LRMSD to N(0,0.1 rad)-perturbed targets -> backward",
-                       "global_batch": B * world, "seq_len": L, "parallelism": f"replicas x{world}",
-                       "atoms_per_gpu": n_atoms, "l2": "flushed (512 MiB write) before every step",
-                       "threads": args.threads or "default", "fullatom_backward": args.bwd},
+            "data": "synthetic", "config": config,
             "breakdown_ms": dict(zip(names, [float(x) for x in mean_ms])),
             "step_alg_bytes": step_bytes,
             "step_gbs": step_bytes / (total_ms / args.steps * 1e-3) / 1e9,
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "residues/s", "h2d_bytes_per_step": int(h2d),
+            "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": sum(launches.values()) * args.steps,
+            "gpu_launches": sum(st.launches.values()) * args.steps,
             "clocks": clk,
         }
         line.update(extra)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
-
-
-def fp64_comparison(tpl, torch, dev, a, seq, lengths, Amax, coords32, gang32, ta):
-    """Errors of the FP32 step against the plain FP64 per-chain GPU form, and that
-    form's own throughput on the same workload."""
-    B, _, Lmax = a.shape
-    A64 = torch.from_numpy(a.astype(np.float64)).to(dev)
-    S = torch.from_numpy(seq).to(dev)
-    Ln = torch.from_numpy(lengths).to(dev)
-    c64 = torch.zeros((B, Amax, 3), dtype=torch.float64, device=dev)
-    t64 = torch.zeros_like(c64)
-    na = torch.zeros((B,), dtype=torch.int32, device=dev)
-    lr = torch.zeros((B,), dtype=torch.float64, device=dev)
-    st = torch.zeros((B, 16), dtype=torch.float64, device=dev)
-    gc = torch.zeros_like(c64)
-    ga = torch.zeros_like(A64)
-    w = torch.full((B,), 1.0 / B, dtype=torch.float64, device=dev)
-    tpl.tpl_fullatom_forward_ref64(torch.from_numpy(ta.astype(np.float64)).to(dev), S, Ln, t64, na)
-
-    def step64():
-        tpl.tpl_fullatom_forward_ref64(A64, S, Ln, c64, na)
-        tpl.tpl_lrmsd_forward_ref64(c64, t64, na, lr, st)
-        tpl.tpl_lrmsd_backward_ref64(w, c64, t64, na, st, gc)
-        tpl.tpl_fullatom_backward_ref64(A64, S, Ln, c64, gc, ga)
-
-    step64()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    step64()
-    e1.record()
-    e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    coord_err = float((coords32.double() - c64).abs().max().item())
-    g32 = gang32.double().reshape(B, -1)
-    g64 = ga.reshape(B, -1)
-    grad_rel = float(((g32 - g64).norm(dim=1) / g64.norm(dim=1).clamp_min(1e-300)).max().item())
-    return {"fp64_gpu_form": {"value": int(lengths.sum()) / (ms * 1e-3), "unit": "residues/s",
-                              "ms_per_step": ms},
-            "errors_vs_fp64_gpu": {"coord_max_abs_A": coord_err, "grad_rel_max": grad_rel}}
 
 
 def main():

@@ -151,9 +151,11 @@ __global__ void __launch_bounds__(NT) bb_fwd_kernel(const float* __restrict__ an
         int ce, ctot;
         block_scan_rigid_count<NT>(A, 0, s_rig, s_cnt, E, ce, Tot, ctot);
         if (threadIdx.x == NT - 32) publish_prefix_agg(ws, slot0 + t, Tot, 0);
-        const int requested = request_tile(ws.hdr + kHdrFwdNext);
         int pc;
         const Rigid P = gather_prefix(ws, slot0, t, pc);  // every warp gathers it
+        // the next tile is requested only now: a CTA that holds a tile it has
+        // not started never waits, so no wait can chain through held tiles
+        const int requested = request_tile(ws.hdr + kHdrFwdNext);
         if (threadIdx.x == 0) store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, 0);
         E = rigid_mul(P, E);
         float vv[9 * K];
@@ -284,8 +286,8 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
             Sum6 after, total;
             block_suffix_sum6<NT>(own, s6, after, total);
             if (threadIdx.x == NT - 32) publish_suffix_agg(ws, slot0 + t, total);
-            requested = request_tile(counter);
             const Sum6 later = gather_suffix(ws, slot0, t, T);  // every warp gathers it
+            requested = request_tile(counter);  // after the last wait of this tile
             // pass 2: gradients, atoms ascending with S = sum over atoms >= current
             Sum6 S = sum6_add(sum6_add(after, later), own);
             M = E;
@@ -325,8 +327,8 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
             Sum6 after, total;
             block_suffix_sum6<NT>(own, s6, after, total);
             if (threadIdx.x == NT - 32) publish_suffix_agg(ws, slot0 + t, total);
-            requested = request_tile(counter);
             const Sum6 later = gather_suffix(ws, slot0, t, T);  // every warp gathers it
+            requested = request_tile(counter);  // after the last wait of this tile
             Sum6 S = sum6_add(sum6_add(after, later), own);
 #pragma unroll
             for (int k = 0; k < K; ++k) {

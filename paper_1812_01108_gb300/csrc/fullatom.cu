@@ -268,6 +268,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT>()) fa_fwd_kernel(
         // frame at the tile start (every warp gathers it), applied in place
         int pc;
         const Rigid P = gather_prefix(ws, slot0, t, pc);
+        const int requested = request_tile(ws.hdr + kHdrFwdNext);  // after the last wait of this tile
         if (threadIdx.x == 0) store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, pc, tile_atoms);
         const int end_atom = pc + tile_atoms;
         const int nout = max(0, min(end_atom, Amax) - pc);
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT>()) fa_fwd_kernel(
             if (threadIdx.x == 0) num_atoms[b] = end_atom;
             zero_range<NT>(out, 3 * min(end_atom, Amax), 3 * Amax);
         }
-        v = next_tile(request_tile(ws.hdr + kHdrFwdNext), &s_v);
+        v = next_tile(requested, &s_v);
     }
 }
 
@@ -447,8 +448,8 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT>() > 2 ? fa_min_blocks<NT
         Sum6 after, total;
         block_suffix_sum6<NT>(own, s6, after, total);
         if (threadIdx.x == NT - 32) publish_suffix_agg(ws, slot0 + t, total);
-        const int requested = request_tile(counter);
         after = sum6_add(after, gather_suffix(ws, slot0, t, T));  // every warp gathers it
+        const int requested = request_tile(counter);  // after the last wait of this tile
         if (j < Lmax) {
             float gphi = 0.f, gpsi = 0.f, gomg = 0.f;
             if (in_range) {
@@ -602,8 +603,8 @@ __global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ an
         Sum6 after, total;
         block_suffix_sum6<NT>(own, s6, after, total);
         if (threadIdx.x == NT - 32) publish_suffix_agg(ws, slot0 + t, total);
-        const int requested = request_tile(counter);
         after = sum6_add(after, gather_suffix(ws, slot0, t, T));  // every warp gathers it
+        const int requested = request_tile(counter);  // after the last wait of this tile
         if (j < Lmax) {
             float gphi = 0.f, gpsi = 0.f, gomg = 0.f;
             if (in_range) {

@@ -255,10 +255,11 @@ __device__ __forceinline__ Sum6 gather_suffix(const ChainWs& ws, int slot0, int 
 }
 
 // Work-list entries for a persistent CTA.  take_tile() is called once at the
-// start; during a tile thread 0 requests the next entry late (request_tile),
-// after the tile's aggregate is published, and next_tile() hands it to the CTA.
-// A taken tile therefore starts right away, so a tile waiting on it never
-// waits on work that has not begun.
+// start; during a tile thread 0 requests the next entry (request_tile) once its
+// warp has finished the tile's look-back, and next_tile() hands it to the CTA
+// after the tile's stores.  Between the two the CTA waits on nothing, so a
+// tile held but not yet started never delays a tile that waits on it by more
+// than one tile's stores: waits cannot chain through held tiles.
 __device__ __forceinline__ int take_tile(int* counter, int* s_v) {
     if (threadIdx.x == 0) *s_v = atomicAdd(counter, 1);
     __syncthreads();
