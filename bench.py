@@ -40,14 +40,22 @@ METRIC_LRMSD = "atoms/s LRMSD fwd+bwd vs plain FP64 GPU form; HBM roofline %"
 
 DEFAULT_BATCH = {"training_step": 256, "backbone_uneven": 4096, "lrmsd_batch": 16384}
 
-# DRAM bytes per launch of the dominant kernel from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload, with the
-# profile summary that holds the capture.  None when the kernel changed after
-# the capture.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a C-ABI
+# call's kernels from one ncu capture, per unit processed (residue or atom),
+# keyed by (workload, call), with the profile summary that holds the capture.
+# An entry is removed when one of its kernels changes after the capture.
 TRAFFIC = {
-    "training_step": None,
-    "backbone_uneven": None,
-    "lrmsd_batch": None,
+    # fa_bwd_coords_kernel<256>: 36.29 MB for 1496321 atoms
+    ("training_step", "fullatom_backward"): (36.2916e6 / 1496321, "atom",
+                                             "profiles/fa_bwd_coords_kernel_training_step_256x700.md"),
+    # moments 256.66 MB + solve 1.99 MB + residual 256.82 MB for 10499521 atoms (4096 pairs)
+    ("lrmsd_batch", "lrmsd_forward"): (515.47e6 / 10499521, "atom",
+                                       "profiles/lrmsd_kernels_lrmsd_batch_4096.md"),
+    # grad: 449.87 MB for 10499521 atoms (4096 pairs)
+    ("lrmsd_batch", "lrmsd_backward"): (449.87e6 / 10499521, "atom",
+                                        "profiles/lrmsd_kernels_lrmsd_batch_4096.md"),
+    ("backbone_uneven", "lrmsd_forward"): (515.47e6 / 10499521, "atom",
+                                           "profiles/lrmsd_kernels_lrmsd_batch_4096.md"),
 }
 
 
@@ -316,6 +324,7 @@ def setup_training_step(args, tpl, torch, dev, d):
         "fullatom_backward": res * (28 + 1 + 28) + 12 * n_atoms,
     }
     st.units = res
+    st.atoms = n_atoms
     st.extra_config = {"atoms_per_gpu": n_atoms, "threads": args.threads or "default",
                        "fullatom_backward": args.bwd}
     tgt_host = target.cpu().pin_memory()
@@ -387,6 +396,7 @@ def setup_backbone_uneven(args, tpl, torch, dev, d):
     st.alg = {"backbone_forward": 48 * res, "lrmsd_forward": 24 * n_atoms,
               "lrmsd_backward": 36 * n_atoms, "backbone_backward": 60 * res}
     st.units = res
+    st.atoms = n_atoms
     st.extra_config = {"atoms_per_gpu": n_atoms, "threads": args.threads or "default",
                        "res_per_thread": args.res_per_thread or "default", "backbone_backward": args.bwd}
     st.h2d = [(A, torch.from_numpy(a).pin_memory()), (Ln, torch.from_numpy(lengths).pin_memory()),
@@ -437,6 +447,7 @@ def setup_lrmsd_batch(args, tpl, torch, dev, d):
     st.launches = {k: len(v) for k, v in st.kernels.items()}
     st.alg = {"lrmsd_forward": 24 * n_atoms, "lrmsd_backward": 36 * n_atoms}
     st.units = n_atoms
+    st.atoms = n_atoms
     st.extra_config = {"atoms_per_gpu": n_atoms, "Nmax": Nmax}
     st.h2d = [(X, torch.from_numpy(x).pin_memory()), (Y, torch.from_numpy(y).pin_memory()),
               (NA, torch.from_numpy(n).pin_memory())]
@@ -585,9 +596,13 @@ def run_tpl(args):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = st.alg[dom] / (mean_ms[names.index(dom)] * 1e-3) / 1e9
+    tr = TRAFFIC.get((args.workload, dom))
+    traffic = None
+    if tr is not None:
+        traffic = tr[0] * (st.atoms if tr[1] == "atom" else st.units)
     roofline = {"bound": "hbm", "kernel": "+".join(st.kernels[dom]), "call": dom,
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": TRAFFIC.get(args.workload),
+                "traffic": traffic, "traffic_source": tr[2] if tr else None,
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "alg_bytes": st.alg[dom]}
     step_bytes = sum(st.alg.values())

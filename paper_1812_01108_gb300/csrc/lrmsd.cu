@@ -324,22 +324,24 @@ __global__ void __launch_bounds__(32) lrmsd_solve_kernel(
             default: adj_row<3>(A, q); break;
         }
         const double nn = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
-        float q0 = 1.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+        double q0 = 1.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
         if (nn > 0.0) {
             double s = (double)rsqrtf((float)nn);
-            s = s * fma(-0.5 * nn * s, s, 1.5);  // one Newton step for 1/sqrt(nn)
-            q0 = (float)(q[0] * s); q1 = (float)(q[1] * s); q2 = (float)(q[2] * s); q3 = (float)(q[3] * s);
+            s = s * fma(-0.5 * nn * s, s, 1.5);  // Newton steps for 1/sqrt(nn)
+            s = s * fma(-0.5 * nn * s, s, 1.5);
+            q0 = q[0] * s; q1 = q[1] * s; q2 = q[2] * s; q3 = q[3] * s;
         }
-        // U(q) of Section 4
-        U[0] = q0 * q0 + q1 * q1 - q2 * q2 - q3 * q3;
-        U[1] = 2.f * (q1 * q2 - q0 * q3);
-        U[2] = 2.f * (q1 * q3 + q0 * q2);
-        U[3] = 2.f * (q1 * q2 + q0 * q3);
-        U[4] = q0 * q0 - q1 * q1 + q2 * q2 - q3 * q3;
-        U[5] = 2.f * (q2 * q3 - q0 * q1);
-        U[6] = 2.f * (q1 * q3 - q0 * q2);
-        U[7] = 2.f * (q2 * q3 + q0 * q1);
-        U[8] = q0 * q0 - q1 * q1 - q2 * q2 + q3 * q3;
+        // U(q) of Section 4, formed in FP64 and rounded once: the gradient
+        // y' - U x' is a small difference of ~|x'|-sized terms
+        U[0] = (float)(q0 * q0 + q1 * q1 - q2 * q2 - q3 * q3);
+        U[1] = (float)(2.0 * (q1 * q2 - q0 * q3));
+        U[2] = (float)(2.0 * (q1 * q3 + q0 * q2));
+        U[3] = (float)(2.0 * (q1 * q2 + q0 * q3));
+        U[4] = (float)(q0 * q0 - q1 * q1 + q2 * q2 - q3 * q3);
+        U[5] = (float)(2.0 * (q2 * q3 - q0 * q1));
+        U[6] = (float)(2.0 * (q1 * q3 - q0 * q2));
+        U[7] = (float)(2.0 * (q2 * q3 + q0 * q1));
+        U[8] = (float)(q0 * q0 - q1 * q1 - q2 * q2 + q3 * q3);
         }
     }
 store:

@@ -101,3 +101,52 @@ def test_autograd_lrmsd():
     l = tpl.lrmsd(X, dev(y, d), dev(n, d))
     l.sum().backward()
     assert rel_err(host(X.grad), oracle.lrmsd_backward(np.ones(2), x, y, n)) <= GRAD_TOL
+
+
+def test_precision_small_clouds_far_from_origin():
+    """The moments are shifted by each pair's first atom and summed in
+    double-float, so a cloud far from the origin costs no precision."""
+    x, y, n = _clouds([100] * 12 + [5000] * 4, 5)
+    off = np.array([300.0, -200.0, 150.0], np.float32)
+    mask = (np.arange(x.shape[1])[None, :] < n[:, None])[:, :, None]
+    x = ((x + off) * mask).astype(np.float32)
+    y = ((y - 2 * off) * mask).astype(np.float32)
+    w = np.ones(len(n), np.float32)
+    l32, g32 = _run(x, y, n, w)
+    assert np.abs(l32 - oracle.lrmsd_forward(x, y, n)).max() <= LRMSD_TOL
+    assert rel_err(g32, oracle.lrmsd_backward(w, x, y, n)) <= GRAD_TOL
+
+
+def test_precision_close_fit():
+    """LRMSD near 0.1 A.  The value keeps the 1e-5 A bound.  The gradient is
+    the residual y' - U x', a difference of FP32 terms of size |x'| (about 26 A
+    here) that ends near LRMSD: its relative error is a few units of
+    eps_32 |x'| / LRMSD (eps_32 = 2^-24 relative rounding, |x'| / LRMSD ~ 300),
+    so the bound for this case is 10 eps_32 |x'|_rms / min LRMSD."""
+    x, y, n = _clouds([100] * 12 + [2000] * 4, 6, noise=0.05)
+    w = np.ones(len(n), np.float32)
+    l32, g32 = _run(x, y, n, w)
+    l64 = oracle.lrmsd_forward(x, y, n)
+    assert l64.max() < 0.15
+    assert np.abs(l32 - l64).max() <= LRMSD_TOL
+    xr = max(float(np.sqrt(((x[p, :k] - x[p, :k].mean(0)) ** 2).sum(1)).mean()) for p, k in enumerate(n))
+    bound = 10 * 2.0 ** -24 * xr / float(l64.min())
+    assert 1e-4 < bound < 1e-3
+    assert rel_err(g32, oracle.lrmsd_backward(w, x, y, n)) <= bound
+
+
+def test_protein_shaped_pairs():
+    """Full-atom chains built from the origin against angle-perturbed copies
+    (the training-step pairing), on identical FP32 coordinates."""
+    rng = workloads.rng_for(4, salt=11)
+    lengths = np.array([700, 350, 128, 64], np.int32)
+    a, seq = workloads.fullatom_inputs(lengths, rng)
+    ta = workloads.perturb_angles(a, lengths, rng, rows=(0, 1, 3, 4, 5, 6))
+    Amax = workloads.pad_to(oracle.max_atoms(seq, lengths))
+    c, n = oracle.fullatom_forward(a, seq, lengths, Amax)
+    t, _ = oracle.fullatom_forward(ta, seq, lengths, Amax)
+    x, y = t.astype(np.float32), c.astype(np.float32)
+    w = np.full(len(n), 0.25, np.float32)
+    l32, g32 = _run(x, y, n.astype(np.int32), w)
+    assert np.abs(l32 - oracle.lrmsd_forward(x, y, n)).max() <= LRMSD_TOL
+    assert rel_err(g32, oracle.lrmsd_backward(w, x, y, n)) <= GRAD_TOL
