@@ -11,6 +11,9 @@ Workloads (``--workload``):
                   Unit: residues/s.
   lrmsd_batch     16384 coordinate-set pairs of U{100..5000} atoms: LRMSD
                   forward + backward.  Unit: atoms/s (atoms of the input side).
+  backbone_stress precision stress, 64 backbone chains x 10000 residues, the
+                  same step as backbone_uneven; reports the coordinate drift and
+                  gradient error against the FP64 per-chain form.
 
 ``--impl reference`` times the FP64 CPU oracle, as it stands, on a bounded
 sample of the same workload instead.
@@ -38,7 +41,8 @@ sys.path.insert(0, ROOT)
 METRIC = "residues/s fwd+bwd at FP32 err≤2e-3 Å vs plain FP64 GPU form; HBM roofline %"
 METRIC_LRMSD = "atoms/s LRMSD fwd+bwd vs plain FP64 GPU form; HBM roofline %"
 
-DEFAULT_BATCH = {"training_step": 256, "backbone_uneven": 4096, "lrmsd_batch": 16384}
+DEFAULT_BATCH = {"training_step": 256, "backbone_uneven": 4096, "lrmsd_batch": 16384,
+                 "backbone_stress": 64}
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a C-ABI
 # call's kernels from one ncu capture, per unit processed (residue or atom),
@@ -87,6 +91,25 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, device, world):
+    """The largest value of x over all ranks (the job's elapsed time).  The
+    replicas exchange nothing else: there is no data-path collective."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_step, world, steps, max_ms):
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (weak scaling: each rank has a batch of its own)."""
+    return units_per_rank_step * world * steps / (max_ms * 1e-3)
+
+
 # ----------------------------------------------------------------------------- host inputs
 def make_inputs(args, rank):
     """Seeded host arrays of the workload (one batch per rank)."""
@@ -102,6 +125,12 @@ def make_inputs(args, rank):
         rng = workloads.rng_for(2, salt=rank)
         lengths = workloads.lengths_loguniform(args.batch, 50, 1000, rng)
         a = workloads.backbone_angles(lengths, rng, Lmax=workloads.pad_to(1000))
+        ta = workloads.perturb_angles(a, lengths, rng)
+        return {"angles": a, "lengths": lengths, "target_angles": ta}
+    if args.workload == "backbone_stress":
+        rng = workloads.rng_for(5, salt=rank)
+        lengths = np.full(args.batch, 10000, np.int32)
+        a = workloads.backbone_angles(lengths, rng)
         ta = workloads.perturb_angles(a, lengths, rng)
         return {"angles": a, "lengths": lengths, "target_angles": ta}
     rng = workloads.rng_for(3, salt=rank)
@@ -123,6 +152,12 @@ def describe(args, world):
                         "phi/psi ~ U[-pi,pi], omega = pi; forward -> LRMSD to "
                         "N(0,0.1 rad)-perturbed targets -> backward",
             "global_batch": B * world, "seq_len": "logU[50,1000]"})
+    if args.workload == "backbone_stress":
+        return (METRIC, "residues/s", {
+            "workload": f"backbone precision stress, {B} chains x 10000 residues per GPU, "
+                        "phi/psi ~ U[-pi,pi], omega = pi; forward -> LRMSD to "
+                        "N(0,0.1 rad)-perturbed targets -> backward",
+            "global_batch": B * world, "seq_len": 10000})
     return (METRIC_LRMSD, "atoms/s", {
         "workload": f"LRMSD batch, {B} pairs per GPU, atoms U{{100..5000}}, N(0,15 A) clouds, "
                     "target = rotated + N(0,10 A) shift + N(0,0.5 A) noise; forward + backward",
@@ -193,7 +228,7 @@ def oracle_step(args, d, n):
         g = oracle.lrmsd_backward(np.full(n, 1.0 / n), c, tgt, na)
         oracle.fullatom_backward(a, seq, L, g)
         return time.perf_counter() - t0, int(L.sum())
-    if args.workload == "backbone_uneven":
+    if args.workload in ("backbone_uneven", "backbone_stress"):
         a, L, ta = d["angles"][s], d["lengths"][s], d["target_angles"][s]
         t0 = time.perf_counter()
         tgt = oracle.backbone_forward(ta, L)
@@ -421,7 +456,8 @@ def setup_backbone_uneven(args, tpl, torch, dev, d):
 
         ms = time_once(torch, step64)
         return {"fp64_gpu_form": {"value": res / (ms * 1e-3), "unit": "residues/s", "ms_per_step": ms},
-                "errors_vs_fp64_gpu": errors(torch, coords, c64, gang, ga, lr, lr64)}
+                "errors_vs_fp64_gpu": errors(torch, coords, c64, gang, ga, lr, lr64,
+                                             prefix_atoms=3000 if Lmax > 1000 else None)}
 
     st.fp64 = fp64
     return st
@@ -487,19 +523,25 @@ def time_once(torch, fn):
     return e0.elapsed_time(e1)
 
 
-def errors(torch, c32, c64, g32, g64, lr32, lr64):
+def errors(torch, c32, c64, g32, g64, lr32, lr64, prefix_atoms=None):
     """Max-abs coordinate error, per-chain relative angle-gradient error (max over
-    chains) and max-abs LRMSD error of the FP32 step against the FP64 form."""
+    chains) and max-abs LRMSD error of the FP32 step against the FP64 form.
+    With prefix_atoms, also the coordinate error over the first prefix_atoms
+    atoms of every chain (the drift along long chains)."""
     B = c32.shape[0]
     a = g32.double().reshape(B, -1)
     b = g64.reshape(B, -1)
-    return {"coord_max_abs_A": float((c32.double() - c64).abs().max().item()),
-            "grad_rel_max": float(((a - b).norm(dim=1) / b.norm(dim=1).clamp_min(1e-300)).max().item()),
-            "lrmsd_max_abs_A": float((lr32.double() - lr64).abs().max().item())}
+    dc = (c32.double() - c64).abs()
+    out = {"coord_max_abs_A": float(dc.max().item()),
+           "grad_rel_max": float(((a - b).norm(dim=1) / b.norm(dim=1).clamp_min(1e-300)).max().item()),
+           "lrmsd_max_abs_A": float((lr32.double() - lr64).abs().max().item())}
+    if prefix_atoms is not None:
+        out[f"coord_max_abs_first_{prefix_atoms}_atoms_A"] = float(dc[:, :prefix_atoms].max().item())
+    return out
 
 
 SETUP = {"training_step": setup_training_step, "backbone_uneven": setup_backbone_uneven,
-         "lrmsd_batch": setup_lrmsd_batch}
+         "backbone_stress": setup_backbone_uneven, "lrmsd_batch": setup_lrmsd_batch}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -578,12 +620,8 @@ def run_tpl(args):
         dist.barrier()
     clk = clocks.stop()
     per = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(nc)] for k in range(args.steps)])
-    total_ms = float(per.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = st.units * world * args.steps / (total_ms * 1e-3)
+    total_ms = max_over_ranks(float(per.sum()), dev, world)
+    value = job_throughput(st.units, world, args.steps, total_ms)
 
     # roofline of the dominant call (per-unit bytes x units per launch / mean event time)
     mean_ms = per.mean(axis=0)
@@ -632,11 +670,8 @@ def run_tpl(args):
         e1.record(stream)
         e1.synchronize()
         e_ms += e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_ms = float(t.item())
-    e2e_value = st.units * world * n_e2e / (e_ms * 1e-3)
+    e_ms = max_over_ranks(e_ms, dev, world)
+    e2e_value = job_throughput(st.units, world, n_e2e, e_ms)
 
     # the e2e loop rewrote the inputs with the same values: the FP32 outputs the
     # FP64 comparison reads are those of the last step

@@ -260,6 +260,16 @@ int tpl_fullatom_max_atoms(const uint8_t* seq_host, const int32_t* lengths_host,
  * enqueues the read on `stream` and waits for that stream.  Not capturable. */
 tpl_status tpl_get_status(tpl_stream stream, int* device_status);
 
+/* Diagnostic (the paper has no counterpart): runs, in one thread of a
+ * one-CTA launch on `stream`, the bounded wait that the chain kernels use
+ * between CTAs, on the int at device address `flag`.  The caller keeps the
+ * int at 0 (nothing sets it), so the wait gives up after its poll limit
+ * (well under a second to a few seconds), sets TPL_STATUS_TIMEOUT and
+ * returns; the context stays usable.  It shows that a lost cross-CTA signal
+ * becomes a status bit, not a hang.  `flag` must be 4-byte aligned device
+ * memory owned by the caller. */
+tpl_status tpl_selftest_wait_timeout(const int* flag, tpl_stream stream);
+
 /* Message of the last error returned on this thread ("" if none). */
 const char* tpl_last_error(void);
 

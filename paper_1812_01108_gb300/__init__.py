@@ -28,7 +28,8 @@ __all__ = [
     "tpl_lrmsd_forward", "tpl_lrmsd_backward", "tpl_lrmsd_forward_noalloc",
     "tpl_backbone_forward_ref64",
     "tpl_backbone_backward_ref64", "tpl_fullatom_forward_ref64", "tpl_fullatom_backward_ref64",
-    "tpl_lrmsd_forward_ref64", "tpl_lrmsd_backward_ref64", "tpl_get_status", "backbone",
+    "tpl_lrmsd_forward_ref64", "tpl_lrmsd_backward_ref64", "tpl_get_status",
+    "tpl_selftest_wait_timeout", "backbone",
     "fullatom", "lrmsd", "residue_table", "fullatom_max_atoms", "BWD_RECOMPUTE",
     "BWD_FROM_COORDS", "SCHED_LONGEST_FIRST", "SCHED_BATCH_ORDER",
 ]
@@ -98,6 +99,7 @@ def load_library():
             "tpl_fullatom_chain_atoms": ([P, I], I),
             "tpl_fullatom_max_atoms": ([P, P, I, I], I),
             "tpl_get_status": ([P, P], I),
+            "tpl_selftest_wait_timeout": ([P, P], I),
             "tpl_last_error": ([], ctypes.c_char_p),
             "tpl_version": ([], ctypes.c_char_p),
         }
@@ -275,6 +277,15 @@ def tpl_lrmsd_backward_ref64(grad_lrmsd, input, target, num_atoms, state, grad_i
         _ptr(_cuda(num_atoms, torch.int32, "num_atoms")), P, Nmax,
         _ptr(_cuda(state, torch.float64, "state")),
         _ptr(_cuda(grad_input, torch.float64, "grad_input")), _stream(input, stream)))
+
+
+def tpl_selftest_wait_timeout(flag, stream=None):
+    """Bounded wait on ``flag`` (an int32 CUDA tensor the caller keeps at 0):
+    gives up after the poll limit and sets TPL_STATUS_TIMEOUT."""
+    import torch
+
+    _check("tpl_selftest_wait_timeout", load_library().tpl_selftest_wait_timeout(
+        _ptr(_cuda(flag, torch.int32, "flag")), _stream(flag, stream)))
 
 
 def tpl_get_status(device=None):

@@ -157,7 +157,7 @@ tpl_status check_opts(const tpl_opts& o) {
 LaunchCfg backbone_cfg(const tpl_opts& o) {
     LaunchCfg c;
     c.threads = o.threads ? o.threads : 128;
-    c.res_per_thread = o.res_per_thread ? o.res_per_thread : 2;
+    c.res_per_thread = o.res_per_thread ? o.res_per_thread : 4;
     return c;
 }
 
@@ -190,6 +190,11 @@ tpl_status check_ws(void* ws, size_t have, size_t need) {
 }  // namespace
 
 size_t chain_ws_bytes(int B, int Lmax) { return chain_ws_layout(nullptr, B, Lmax, nullptr); }
+
+// One thread waits on `flag` with the chain kernels' bounded wait.
+__global__ void selftest_wait_kernel(const int* flag) {
+    if (threadIdx.x == 0) wait_flag(flag);
+}
 
 cudaError_t launch_schedule(const int32_t* lengths, int B, int Lmax, int tile, bool longest_first,
                             const ChainWs& ws, cudaStream_t s) {
@@ -537,6 +542,16 @@ int tpl_fullatom_max_atoms(const uint8_t* seq_host, const int32_t* lengths_host,
         if (n > best) best = n;
     }
     return best;
+}
+
+tpl_status tpl_selftest_wait_timeout(const int* flag, tpl_stream stream) {
+    if (!flag || (reinterpret_cast<uintptr_t>(flag) & 3u))
+        return fail(TPL_ERR_INVALID_ARG, "flag is NULL or not 4-byte aligned");
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return fail(TPL_ERR_NO_DEVICE, "no CUDA device");
+    selftest_wait_kernel<<<1, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(flag);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ok() : cuda_fail(e, "selftest_wait_timeout");
 }
 
 tpl_status tpl_get_status(tpl_stream stream, int* device_status) {
