@@ -76,6 +76,8 @@ def parse():
     p.add_argument("--res-per-thread", type=int, default=0, help="backbone residues per thread (0 = default)")
     p.add_argument("--bwd", default="coords", choices=["coords", "recompute"],
                    help="chain backward: read the forward's coordinates or rebuild frames")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="use the library's default launch shape instead of the autotuner's pick")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 per-chain comparison")
     a = p.parse_args()
@@ -337,6 +339,12 @@ def setup_training_step(args, tpl, torch, dev, d):
     tpl.tpl_fullatom_forward(TA, S, Ln, target, na_t, fa_ws, opts)  # target structures
     torch.cuda.synchronize()
     n_atoms = int(na_t.sum().item())
+    tuned = None
+    if not args.no_autotune and not args.threads:
+        gtune = torch.randn((B, Amax, 3), device=dev)
+        opts, tms = tpl.tpl_fullatom_autotune(A, S, Ln, coords, na, gtune, gang, fa_ws,
+                                              bwd_mode=opts.bwd_mode)
+        tuned = {"threads": opts.threads, "schedule": opts.schedule, "fwd_bwd_ms": tms}
 
     st = Step()
     st.calls = [
@@ -360,8 +368,8 @@ def setup_training_step(args, tpl, torch, dev, d):
     }
     st.units = res
     st.atoms = n_atoms
-    st.extra_config = {"atoms_per_gpu": n_atoms, "threads": args.threads or "default",
-                       "fullatom_backward": args.bwd}
+    st.extra_config = {"atoms_per_gpu": n_atoms, "threads": opts.threads or "default",
+                       "fullatom_backward": args.bwd, "autotuned": tuned}
     tgt_host = target.cpu().pin_memory()
     st.h2d = [(A, torch.from_numpy(a).pin_memory()), (S, torch.from_numpy(seq).pin_memory()),
               (Ln, torch.from_numpy(lengths).pin_memory()), (target, tgt_host)]
@@ -413,6 +421,12 @@ def setup_backbone_uneven(args, tpl, torch, dev, d):
     lr_ws = torch.empty(tpl.tpl_lrmsd_workspace_size(B, 3 * Lmax), dtype=torch.uint8, device=dev)
     tpl.tpl_backbone_forward(torch.from_numpy(ta).to(dev), Ln, target, bb_ws, opts)
     torch.cuda.synchronize()
+    tuned = None
+    if not args.no_autotune and not args.threads and not args.res_per_thread:
+        gtune = torch.randn((B, 3 * Lmax, 3), device=dev)
+        opts, tms = tpl.tpl_backbone_autotune(A, Ln, coords, gtune, gang, bb_ws, bwd_mode=opts.bwd_mode)
+        tuned = {"threads": opts.threads, "res_per_thread": opts.res_per_thread,
+                 "schedule": opts.schedule, "fwd_bwd_ms": tms}
     n_atoms = int(na_host.sum())
     res = int(lengths.sum())
 
@@ -432,8 +446,9 @@ def setup_backbone_uneven(args, tpl, torch, dev, d):
               "lrmsd_backward": 36 * n_atoms, "backbone_backward": 60 * res}
     st.units = res
     st.atoms = n_atoms
-    st.extra_config = {"atoms_per_gpu": n_atoms, "threads": args.threads or "default",
-                       "res_per_thread": args.res_per_thread or "default", "backbone_backward": args.bwd}
+    st.extra_config = {"atoms_per_gpu": n_atoms, "threads": opts.threads or "default",
+                       "res_per_thread": opts.res_per_thread or "default", "backbone_backward": args.bwd,
+                       "autotuned": tuned}
     st.h2d = [(A, torch.from_numpy(a).pin_memory()), (Ln, torch.from_numpy(lengths).pin_memory()),
               (na, torch.from_numpy(na_host).pin_memory()), (target, target.cpu().pin_memory())]
     st.d2h = (torch.empty((B,), dtype=torch.float32).pin_memory(), lr)

@@ -81,9 +81,12 @@ typedef struct CUstream_st* tpl_stream; /* same type as cudaStream_t */
 #define TPL_BWD_RECOMPUTE 1   /* rebuild frames from the angles (fewest HBM bytes) */
 #define TPL_BWD_FROM_COORDS 2 /* read the forward's coordinates instead */
 
-#define TPL_SCHED_AUTO 0
+#define TPL_SCHED_AUTO 0          /* backbone: PACKED; full atom: BATCH_ORDER */
 #define TPL_SCHED_LONGEST_FIRST 1 /* chains sorted by length, longest first */
 #define TPL_SCHED_BATCH_ORDER 2   /* chains in batch order */
+#define TPL_SCHED_PACKED 3        /* longest first, and chains of at most one tile packed
+                                     several per tile (backbone; the full-atom calls
+                                     treat it as LONGEST_FIRST) */
 
 /* Launch options; a NULL pointer means all zeros (everything automatic). */
 typedef struct tpl_opts {
@@ -259,6 +262,26 @@ int tpl_fullatom_max_atoms(const uint8_t* seq_host, const int32_t* lengths_host,
 /* Reads and clears the current device's status word (TPL_STATUS_* bits):
  * enqueues the read on `stream` and waits for that stream.  Not capturable. */
 tpl_status tpl_get_status(tpl_stream stream, int* device_status);
+
+/* Autotuner (the paper has no counterpart): runs forward + backward on the
+ * caller's batch for every supported launch shape and schedule -- backbone:
+ * threads 64..512 x residues per thread 1, 2, 4 x {PACKED, LONGEST_FIRST};
+ * full atom: threads 64..512 x {BATCH_ORDER, LONGEST_FIRST} -- times each with
+ * CUDA events on `stream` (one untimed pass, best of three), and writes the
+ * fastest options to *best (and its time in ms to *best_ms if not NULL).
+ * `bwd_mode` is kept in every candidate.  The arguments are those of the
+ * forward and backward calls; coords, num_atoms and grad_angles are
+ * overwritten.  It synchronizes `stream` and must not run while the stream is
+ * being captured (TPL_ERR_INVALID_ARG).  Pass *best to later calls. */
+tpl_status tpl_backbone_autotune(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                 float* coords, const float* grad_coords, float* grad_angles,
+                                 void* workspace, size_t workspace_bytes, int bwd_mode, tpl_opts* best,
+                                 float* best_ms, tpl_stream stream);
+tpl_status tpl_fullatom_autotune(const float* angles, const uint8_t* seq, const int32_t* lengths, int B,
+                                 int Lmax, int Amax, float* coords, int32_t* num_atoms,
+                                 const float* grad_coords, float* grad_angles, void* workspace,
+                                 size_t workspace_bytes, int bwd_mode, tpl_opts* best, float* best_ms,
+                                 tpl_stream stream);
 
 /* Diagnostic (the paper has no counterpart): runs, in one thread of a
  * one-CTA launch on `stream`, the bounded wait that the chain kernels use

@@ -29,9 +29,9 @@ __all__ = [
     "tpl_backbone_forward_ref64",
     "tpl_backbone_backward_ref64", "tpl_fullatom_forward_ref64", "tpl_fullatom_backward_ref64",
     "tpl_lrmsd_forward_ref64", "tpl_lrmsd_backward_ref64", "tpl_get_status",
-    "tpl_selftest_wait_timeout", "backbone",
+    "tpl_selftest_wait_timeout", "tpl_backbone_autotune", "tpl_fullatom_autotune", "backbone",
     "fullatom", "lrmsd", "residue_table", "fullatom_max_atoms", "BWD_RECOMPUTE",
-    "BWD_FROM_COORDS", "SCHED_LONGEST_FIRST", "SCHED_BATCH_ORDER",
+    "BWD_FROM_COORDS", "SCHED_LONGEST_FIRST", "SCHED_BATCH_ORDER", "SCHED_PACKED",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -40,7 +40,7 @@ _lib = None
 _lock = threading.Lock()
 
 BWD_AUTO, BWD_RECOMPUTE, BWD_FROM_COORDS = 0, 1, 2
-SCHED_AUTO, SCHED_LONGEST_FIRST, SCHED_BATCH_ORDER = 0, 1, 2
+SCHED_AUTO, SCHED_LONGEST_FIRST, SCHED_BATCH_ORDER, SCHED_PACKED = 0, 1, 2, 3
 STATUS_BAD_RESIDUE, STATUS_BAD_LENGTH, STATUS_TOO_MANY_ATOMS, STATUS_ZERO_LRMSD = 1, 2, 4, 8
 STATUS_TIMEOUT, STATUS_BAD_WORKSPACE = 16, 32
 
@@ -77,6 +77,7 @@ def load_library():
         lib = ctypes.CDLL(_LIB_PATH)
         P, I, Z = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
         O = ctypes.POINTER(Opts)
+        F = ctypes.POINTER(ctypes.c_float)
         sig = {
             "tpl_backbone_workspace_size": ([I, I], Z),
             "tpl_fullatom_workspace_size": ([I, I], Z),
@@ -100,6 +101,8 @@ def load_library():
             "tpl_fullatom_max_atoms": ([P, P, I, I], I),
             "tpl_get_status": ([P, P], I),
             "tpl_selftest_wait_timeout": ([P, P], I),
+            "tpl_backbone_autotune": ([P, P, I, I, P, P, P, P, Z, I, O, F, P], I),
+            "tpl_fullatom_autotune": ([P, P, P, I, I, I, P, P, P, P, P, Z, I, O, F, P], I),
             "tpl_last_error": ([], ctypes.c_char_p),
             "tpl_version": ([], ctypes.c_char_p),
         }
@@ -195,6 +198,43 @@ def tpl_fullatom_backward(angles, seq, lengths, coords, grad_coords, grad_angles
         _ptr(_cuda(grad_coords, torch.float32, "grad_coords")),
         _ptr(_cuda(grad_angles, torch.float32, "grad_angles")), _ptr(workspace),
         workspace.numel() * workspace.element_size(), _opts(opts), _stream(angles, stream)))
+
+
+def tpl_backbone_autotune(angles, lengths, coords, grad_coords, grad_angles, workspace,
+                          bwd_mode=0, stream=None):
+    """Times forward + backward for every launch shape and schedule on this
+    batch; returns (fastest Opts, its milliseconds).  Overwrites coords and
+    grad_angles.  Not capturable."""
+    B, _, Lmax = angles.shape
+    best = Opts()
+    ms = ctypes.c_float(0.0)
+    _check("tpl_backbone_autotune", load_library().tpl_backbone_autotune(
+        _ptr(_cuda(angles, torch.float32, "angles")), _ptr(_cuda(lengths, torch.int32, "lengths")),
+        B, Lmax, _ptr(_cuda(coords, torch.float32, "coords")),
+        _ptr(_cuda(grad_coords, torch.float32, "grad_coords")),
+        _ptr(_cuda(grad_angles, torch.float32, "grad_angles")), _ptr(workspace),
+        workspace.numel() * workspace.element_size(), int(bwd_mode), ctypes.byref(best),
+        ctypes.byref(ms), _stream(angles, stream)))
+    return best, ms.value
+
+
+def tpl_fullatom_autotune(angles, seq, lengths, coords, num_atoms, grad_coords, grad_angles,
+                          workspace, bwd_mode=0, stream=None):
+    """As tpl_backbone_autotune for the full-atom calls; overwrites coords,
+    num_atoms and grad_angles."""
+    B, _, Lmax = angles.shape
+    Amax = coords.shape[1]
+    best = Opts()
+    ms = ctypes.c_float(0.0)
+    _check("tpl_fullatom_autotune", load_library().tpl_fullatom_autotune(
+        _ptr(_cuda(angles, torch.float32, "angles")), _ptr(_cuda(seq, torch.uint8, "seq")),
+        _ptr(_cuda(lengths, torch.int32, "lengths")), B, Lmax, Amax,
+        _ptr(_cuda(coords, torch.float32, "coords")), _ptr(_cuda(num_atoms, torch.int32, "num_atoms")),
+        _ptr(_cuda(grad_coords, torch.float32, "grad_coords")),
+        _ptr(_cuda(grad_angles, torch.float32, "grad_angles")), _ptr(workspace),
+        workspace.numel() * workspace.element_size(), int(bwd_mode), ctypes.byref(best),
+        ctypes.byref(ms), _stream(angles, stream)))
+    return best, ms.value
 
 
 def tpl_lrmsd_forward(input, target, num_atoms, lrmsd_out, workspace, stream=None):

@@ -46,39 +46,54 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 
 // ---------------------------------------------------------------------------
-// K8: the tile list.  One CTA: chain order (batch order, or longest first by a
-// 64-bucket counting sort), tiles per chain, exclusive scan, list entries; it
-// also zeroes the forward look-back flags and work counter.
+// K8: the work list.  One CTA.  Chain order: batch order, or longest first by
+// a counting sort on 64 length buckets.  In packed mode a chain of at most one
+// tile goes instead to the class m = min(8, tile / slots), the number of such
+// chains that fit one tile (slots = length rounded up to the granule); the
+// classes follow the long chains, m ascending, and every m consecutive chains
+// of a class form one packed entry.  Then the entries per thread, an
+// exclusive scan, and the entries.  It also zeroes the forward look-back
+// flags and work counter.
 // ---------------------------------------------------------------------------
 constexpr int kBuckets = 64;
+constexpr int kKeys = kBuckets + kMaxPack;
 constexpr int kSchedThreads = 1024;
 
 __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* __restrict__ lengths,
-                                                                 int B, int Lmax, int tile,
-                                                                 int longest_first, ChainWs ws) {
-    __shared__ int hist[kBuckets];
+                                                                 int B, int Lmax, int tile, int mode,
+                                                                 int granule, ChainWs ws) {
+    __shared__ int hist[kKeys];
+    __shared__ int s_start[kKeys + 1];
     __shared__ int s_part[33];
-    int* order = reinterpret_cast<int*>(ws.bagg);  // scratch: the backward's area is free here
+    int* order = ws.order;
     for (int i = threadIdx.x; i < B * ws.tmax; i += kSchedThreads) ws.fflag[i] = 0;
     auto len = [&](int b) {
         const int L = lengths[b];
         return L < 0 ? 0 : (L > Lmax ? Lmax : L);
     };
-    if (longest_first) {
-        if (threadIdx.x < kBuckets) hist[threadIdx.x] = 0;
+    auto is_short = [&](int b) { return mode == kSchedPacked && len(b) <= tile; };
+    auto pack_class = [&](int b) {  // chains per packed tile, 1..kMaxPack
+        const int slots = (len(b) + granule - 1) / granule * granule;
+        return slots == 0 ? kMaxPack : min(kMaxPack, tile / slots);
+    };
+    auto key = [&](int b) {
+        if (is_short(b)) return kBuckets + pack_class(b) - 1;
+        return kBuckets - 1 - (int)(((long long)len(b) * kBuckets) / ((long long)Lmax + 1));
+    };
+    if (mode != kSchedBatch) {
+        if (threadIdx.x < kKeys) hist[threadIdx.x] = 0;
         __syncthreads();
-        auto key = [&](int b) {
-            return kBuckets - 1 - (int)(((long long)len(b) * kBuckets) / ((long long)Lmax + 1));
-        };
         for (int b = threadIdx.x; b < B; b += kSchedThreads) atomicAdd(&hist[key(b)], 1);
         __syncthreads();
         if (threadIdx.x == 0) {
             int run = 0;
-            for (int k = 0; k < kBuckets; ++k) {
+            for (int k = 0; k < kKeys; ++k) {
                 const int c = hist[k];
                 hist[k] = run;
+                s_start[k] = run;
                 run += c;
             }
+            s_start[kKeys] = run;
         }
         __syncthreads();
         for (int b = threadIdx.x; b < B; b += kSchedThreads) order[atomicAdd(&hist[key(b)], 1)] = b;
@@ -93,8 +108,16 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
         const int L = len(b);
         return L > 0 ? (L + tile - 1) / tile : 1;  // an empty chain still gets one tile (zero fill)
     };
+    // entries that start at order position i: a long chain's tiles, or one
+    // packed entry at every m-th chain of a class
+    auto entries = [&](int i) {
+        const int b = order[i];
+        if (!is_short(b)) return ntiles(b);
+        const int m = pack_class(b);
+        return ((i - s_start[kBuckets + m - 1]) % m) == 0 ? 1 : 0;
+    };
     int mine = 0;
-    for (int i = i0; i < i1; ++i) mine += ntiles(order[i]);
+    for (int i = i0; i < i1; ++i) mine += entries(i);
     // block-wide exclusive scan of `mine`: warp shuffles, then the warp totals
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int inc = mine;
@@ -120,9 +143,15 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
     int base = s_part[warp] + inc - mine;
     for (int i = i0; i < i1; ++i) {
         const int b = order[i];
-        const int n = ntiles(b);
-        for (int k = 0; k < n; ++k) ws.tiles[base + k] = make_int2(b, k);
-        base += n;
+        if (is_short(b)) {
+            const int m = pack_class(b);
+            const int k = kBuckets + m - 1;
+            if (((i - s_start[k]) % m) == 0) ws.tiles[base++] = make_int2(-1 - i, min(m, s_start[k + 1] - i));
+        } else {
+            const int n = ntiles(b);
+            for (int k = 0; k < n; ++k) ws.tiles[base + k] = make_int2(b, k);
+            base += n;
+        }
     }
     if (threadIdx.x == 0) {
         ws.hdr[kHdrTiles] = s_part[32];
@@ -141,19 +170,28 @@ tpl_opts resolve(const tpl_opts* o) {
     return r;
 }
 
-bool longest_first(const tpl_opts& o) { return o.schedule == TPL_SCHED_LONGEST_FIRST; }
+// Schedule mode of a chain call (kSched* of sched.cuh); packing is a
+// backbone feature.
+int sched_mode(const tpl_opts& o, bool can_pack) {
+    switch (o.schedule) {
+        case TPL_SCHED_LONGEST_FIRST: return kSchedLongest;
+        case TPL_SCHED_BATCH_ORDER: return kSchedBatch;
+        case TPL_SCHED_PACKED: return can_pack ? kSchedPacked : kSchedLongest;
+        default: return can_pack ? kSchedPacked : kSchedBatch;
+    }
+}
 
 tpl_status check_opts(const tpl_opts& o) {
     if (o.bwd_mode < TPL_BWD_AUTO || o.bwd_mode > TPL_BWD_FROM_COORDS)
         return fail(TPL_ERR_INVALID_ARG, "bwd_mode %d unknown", o.bwd_mode);
-    if (o.schedule < TPL_SCHED_AUTO || o.schedule > TPL_SCHED_BATCH_ORDER)
+    if (o.schedule < TPL_SCHED_AUTO || o.schedule > TPL_SCHED_PACKED)
         return fail(TPL_ERR_INVALID_ARG, "schedule %d unknown", o.schedule);
     if (o.threads < 0 || o.res_per_thread < 0)
         return fail(TPL_ERR_INVALID_ARG, "negative launch option");
     return TPL_OK;
 }
 
-// Backbone defaults: 128 threads x 2 residues (tile 256 residues).
+// Backbone defaults: 128 threads x 4 residues (tile 512 residues).
 LaunchCfg backbone_cfg(const tpl_opts& o) {
     LaunchCfg c;
     c.threads = o.threads ? o.threads : 128;
@@ -196,9 +234,9 @@ __global__ void selftest_wait_kernel(const int* flag) {
     if (threadIdx.x == 0) wait_flag(flag);
 }
 
-cudaError_t launch_schedule(const int32_t* lengths, int B, int Lmax, int tile, bool longest_first,
+cudaError_t launch_schedule(const int32_t* lengths, int B, int Lmax, int tile, int mode, int granule,
                             const ChainWs& ws, cudaStream_t s) {
-    schedule_kernel<<<1, kSchedThreads, 0, s>>>(lengths, B, Lmax, tile, longest_first ? 1 : 0, ws);
+    schedule_kernel<<<1, kSchedThreads, 0, s>>>(lengths, B, Lmax, tile, mode, granule, ws);
     return cudaGetLastError();
 }
 
@@ -245,6 +283,60 @@ cudaError_t read_and_clear_status(cudaStream_t s, int* out) {
 
 using namespace tpl;
 
+namespace {
+
+// ---------------------------------------------------------------------------
+// Autotuner: times forward + backward for every supported launch shape and
+// schedule on the caller's own batch (CUDA events on `stream`; one untimed
+// pass, then the best of `kTuneReps`) and returns the fastest options.
+// ---------------------------------------------------------------------------
+constexpr int kTuneReps = 3;
+
+template <class Step>
+tpl_status tune(const tpl_opts* cands, int n, cudaStream_t s, const Step& step, tpl_opts* best,
+                       float* best_ms) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+        return fail(TPL_ERR_INVALID_ARG, "autotune cannot run while the stream is being captured");
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "autotune");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError(), "autotune");
+    }
+    float best_t = -1.f;
+    tpl_status st = TPL_OK;
+    for (int c = 0; c < n && st == TPL_OK; ++c) {
+        if (step(cands[c]) != TPL_OK) continue;  // a shape this call rejects
+        float t_min = -1.f;
+        for (int r = 0; r < kTuneReps; ++r) {
+            cudaEventRecord(e0, s);
+            if ((st = step(cands[c])) != TPL_OK) break;
+            cudaEventRecord(e1, s);
+            const cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                st = cuda_fail(e, "autotune");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (t_min < 0.f || ms < t_min) t_min = ms;
+        }
+        if (st == TPL_OK && t_min >= 0.f && (best_t < 0.f || t_min < best_t)) {
+            best_t = t_min;
+            *best = cands[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != TPL_OK) return st;
+    if (best_t < 0.f) return fail(TPL_ERR_INVALID_ARG, "autotune: no launch shape accepted these arguments");
+    if (best_ms) *best_ms = best_t;
+    return ok();
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* tpl_version(void) { return "0.1.0"; }
@@ -275,7 +367,7 @@ tpl_status tpl_backbone_forward(const float* angles, const int32_t* lengths, int
         return fail(TPL_ERR_INVALID_ARG, "unsupported backbone launch %d x %d", cfg.threads, cfg.res_per_thread);
     if ((st = check_ws(workspace, workspace_bytes, tpl_backbone_workspace_size(B, Lmax)))) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_backbone_forward(angles, lengths, B, Lmax, coords, longest_first(o),
+    cudaError_t e = launch_backbone_forward(angles, lengths, B, Lmax, coords, sched_mode(o, true),
                                             workspace, cfg, s);
     if (e != cudaSuccess) return cuda_fail(e, "backbone_forward");
     return ok();
@@ -321,7 +413,7 @@ tpl_status tpl_fullatom_forward(const float* angles, const uint8_t* seq, const i
     if ((st = check_ws(workspace, workspace_bytes, tpl_fullatom_workspace_size(B, Lmax)))) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = launch_fullatom_forward(angles, seq, lengths, B, Lmax, Amax, coords, num_atoms,
-                                            longest_first(o), workspace, cfg, s);
+                                            sched_mode(o, false), workspace, cfg, s);
     if (e != cudaSuccess) return cuda_fail(e, "fullatom_forward");
     return ok();
 }
@@ -354,7 +446,8 @@ tpl_status tpl_fullatom_backward(const float* angles, const uint8_t* seq, const 
 static tpl_status check_pair_args(int P, int Nmax, const void* const* ptrs, int nptr) {
     if (P < 0 || Nmax < 0) return fail(TPL_ERR_INVALID_ARG, "P=%d Nmax=%d must be >= 0", P, Nmax);
     if (Nmax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Nmax=%d must be a multiple of 4", Nmax);
-    if (P > 65535 * 64) return fail(TPL_ERR_BAD_SHAPE, "P=%d too large", P);
+    if ((long long)P * ((Nmax + 2047) / 2048 + 1) > 0x7fffffffLL)
+        return fail(TPL_ERR_BAD_SHAPE, "P=%d x Nmax=%d too large for one call", P, Nmax);
     if (P == 0) return TPL_OK;
     for (int i = 0; i < nptr; ++i) {
         if (!ptrs[i]) return fail(TPL_ERR_INVALID_ARG, "pointer argument %d is NULL", i);
@@ -370,7 +463,6 @@ tpl_status tpl_lrmsd_forward(const float* input, const float* target, const int3
     tpl_status st = check_pair_args(P, Nmax, ptrs, 4);
     if (st) return st;
     if (P == 0) return ok();
-    if (P > 65535) return fail(TPL_ERR_BAD_SHAPE, "P=%d exceeds 65535 pairs per call", P);
     if ((st = check_ws(workspace, workspace_bytes, tpl_lrmsd_workspace_size(P, Nmax)))) return st;
     cudaError_t e = launch_lrmsd_forward(input, target, num_atoms, P, Nmax, lrmsd, workspace,
                                          reinterpret_cast<cudaStream_t>(stream));
@@ -385,7 +477,6 @@ tpl_status tpl_lrmsd_backward(const float* grad_lrmsd, const float* input, const
     tpl_status st = check_pair_args(P, Nmax, ptrs, 5);
     if (st) return st;
     if (P == 0) return ok();
-    if (P > 65535) return fail(TPL_ERR_BAD_SHAPE, "P=%d exceeds 65535 pairs per call", P);
     if ((st = check_ws(const_cast<void*>(workspace), workspace_bytes, tpl_lrmsd_workspace_size(P, Nmax))))
         return st;
     cudaError_t e = launch_lrmsd_backward(grad_lrmsd, input, target, num_atoms, P, Nmax, grad_input,
@@ -542,6 +633,61 @@ int tpl_fullatom_max_atoms(const uint8_t* seq_host, const int32_t* lengths_host,
         if (n > best) best = n;
     }
     return best;
+}
+
+tpl_status tpl_backbone_autotune(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                 float* coords, const float* grad_coords, float* grad_angles,
+                                 void* workspace, size_t workspace_bytes, int bwd_mode, tpl_opts* best,
+                                 float* best_ms, tpl_stream stream) {
+    if (!best) return fail(TPL_ERR_INVALID_ARG, "best is NULL");
+    tpl_opts cands[32];
+    int n = 0;
+    const int threads[4] = {64, 128, 256, 512}, ks[3] = {1, 2, 4}, sch[2] = {TPL_SCHED_PACKED, TPL_SCHED_LONGEST_FIRST};
+    for (int si = 0; si < 2; ++si)
+        for (int ti = 0; ti < 4; ++ti)
+            for (int ki = 0; ki < 3; ++ki) {
+                if (!backbone_cfg_supported(threads[ti], ks[ki]) || (threads[ti] == 512 && ks[ki] == 4)) continue;
+                tpl_opts o;
+                memset(&o, 0, sizeof(o));
+                o.bwd_mode = bwd_mode;
+                o.threads = threads[ti];
+                o.res_per_thread = ks[ki];
+                o.schedule = sch[si];
+                cands[n++] = o;
+            }
+    return tune(cands, n, reinterpret_cast<cudaStream_t>(stream), [&](const tpl_opts& o) {
+        tpl_status st = tpl_backbone_forward(angles, lengths, B, Lmax, coords, workspace, workspace_bytes, &o, stream);
+        if (st) return st;
+        return tpl_backbone_backward(angles, lengths, B, Lmax, coords, grad_coords, grad_angles, workspace,
+                                     workspace_bytes, &o, stream);
+    }, best, best_ms);
+}
+
+tpl_status tpl_fullatom_autotune(const float* angles, const uint8_t* seq, const int32_t* lengths, int B,
+                                 int Lmax, int Amax, float* coords, int32_t* num_atoms,
+                                 const float* grad_coords, float* grad_angles, void* workspace,
+                                 size_t workspace_bytes, int bwd_mode, tpl_opts* best, float* best_ms,
+                                 tpl_stream stream) {
+    if (!best) return fail(TPL_ERR_INVALID_ARG, "best is NULL");
+    tpl_opts cands[8];
+    int n = 0;
+    const int threads[4] = {64, 128, 256, 512}, sch[2] = {TPL_SCHED_BATCH_ORDER, TPL_SCHED_LONGEST_FIRST};
+    for (int si = 0; si < 2; ++si)
+        for (int ti = 0; ti < 4; ++ti) {
+            tpl_opts o;
+            memset(&o, 0, sizeof(o));
+            o.bwd_mode = bwd_mode;
+            o.threads = threads[ti];
+            o.schedule = sch[si];
+            cands[n++] = o;
+        }
+    return tune(cands, n, reinterpret_cast<cudaStream_t>(stream), [&](const tpl_opts& o) {
+        tpl_status st = tpl_fullatom_forward(angles, seq, lengths, B, Lmax, Amax, coords, num_atoms, workspace,
+                                             workspace_bytes, &o, stream);
+        if (st) return st;
+        return tpl_fullatom_backward(angles, seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles,
+                                     workspace, workspace_bytes, &o, stream);
+    }, best, best_ms);
 }
 
 tpl_status tpl_selftest_wait_timeout(const int* flag, tpl_stream stream) {

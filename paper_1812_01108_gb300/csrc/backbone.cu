@@ -101,6 +101,32 @@ __device__ __forceinline__ void store_stage(float* s, const float (&v)[9 * K]) {
 // CA <- phi (0), C <- psi (1).
 __device__ __forceinline__ constexpr int row_of(int k) { return k == 0 ? 2 : (k == 1 ? 0 : 1); }
 
+// Product of the 3K transforms of a thread's residues j0 .. j0+K-1 (R_0 = I;
+// residues past L are identities) and the local atom positions it places.
+template <int K>
+__device__ __forceinline__ Rigid thread_product(const float* __restrict__ ang, int j0, int L, int Lmax,
+                                                const BackboneConst& bc, float3 (&pos)[3 * K]) {
+    float a[3][K];
+    load_row<K>(ang, j0, Lmax, a[0]);
+    load_row<K>(ang + Lmax, j0, Lmax, a[1]);
+    load_row<K>(ang + 2 * Lmax, j0, Lmax, a[2]);
+    Rigid A = rigid_identity();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int j = j0 + k;
+#pragma unroll
+        for (int at = 0; at < 3; ++at) {
+            if (j < L && (j > 0 || at > 0)) {
+                float s, c;
+                sincosf(a[row_of(at)][k], &s, &c);
+                rigid_mul_R(A, c, s, bc.ct[at], bc.st[at], bc.d[at]);
+            }
+            pos[3 * k + at] = A.t;
+        }
+    }
+    return A;
+}
+
 // ---------------------------------------------------------------------------
 // K1: forward.  One tile (NT*K residues) per step of a persistent CTA.
 // ---------------------------------------------------------------------------
@@ -115,11 +141,64 @@ __global__ void __launch_bounds__(NT) bb_fwd_kernel(const float* __restrict__ an
     __shared__ int s_cnt[NW + 1];
     __shared__ int s_v;
     __shared__ __align__(16) float s_out[TILE * 9];
+    __shared__ PackS s_pack;
 
     const int ntiles = ws.hdr[kHdrTiles];
     int v = take_tile(ws.hdr + kHdrFwdNext, &s_v);
     while (v < ntiles) {
         const int2 ct = ws.tiles[v];
+        if (ct.x < 0) {
+            // a pack of whole short chains: segmented scan, no look-back
+            const int m = ct.y;
+            load_pack<K>(ws, lengths, Lmax, -1 - ct.x, m, s_pack);
+            const int slot = threadIdx.x * K;
+            const int ci = pack_member(s_pack, m, slot);
+            const int b = ci >= 0 ? s_pack.b[ci] : 0;
+            const int L = ci >= 0 ? s_pack.len[ci] : 0;
+            const int j0 = ci >= 0 ? slot - s_pack.off[ci] : Lmax;  // Lmax: nothing to load
+            float3 pos[3 * K];
+            const Rigid A = thread_product<K>(angles + (size_t)b * 3 * Lmax, j0, L, Lmax, bc, pos);
+            const Rigid E = block_seg_scan_rigid<NT>(A, ci < 0 || j0 == 0, s_rig, s_cnt);
+            const int requested = request_tile(ws.hdr + kHdrFwdNext);
+            float vv[9 * K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+#pragma unroll
+                for (int at = 0; at < 3; ++at) {
+                    const float3 r = point_apply(E, pos[3 * k + at]);
+                    vv[9 * k + 3 * at + 0] = r.x;
+                    vv[9 * k + 3 * at + 1] = r.y;
+                    vv[9 * k + 3 * at + 2] = r.z;
+                }
+            }
+            store_stage<K>(s_out + threadIdx.x * 9 * K, vv);
+            __syncthreads();
+            // each chain's whole row: its atoms from the stage (16-byte copies when
+            // the stage offset allows), the float4 that straddles the end, zeros
+            for (int i = 0; i < m; ++i) {
+                const int n9 = 9 * s_pack.len[i], o9 = 9 * s_pack.off[i];
+                float4* dst = reinterpret_cast<float4*>(coords + (size_t)s_pack.b[i] * 9 * Lmax);
+                const int full = n9 >> 2;
+                if ((o9 & 3) == 0) {
+                    const float4* src = reinterpret_cast<const float4*>(s_out + o9);
+                    for (int q = threadIdx.x; q < full; q += NT) dst[q] = src[q];
+                } else {
+                    for (int q = threadIdx.x; q < full; q += NT) {
+                        const float* e = s_out + o9 + 4 * q;
+                        dst[q] = make_float4(e[0], e[1], e[2], e[3]);
+                    }
+                }
+                if ((n9 & 3) && threadIdx.x == 0) {
+                    const int e = 4 * full;
+                    dst[full] = make_float4(s_out[o9 + e], e + 1 < n9 ? s_out[o9 + e + 1] : 0.f,
+                                            e + 2 < n9 ? s_out[o9 + e + 2] : 0.f, 0.f);
+                }
+                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int q = ((n9 + 3) >> 2) + threadIdx.x; q < 9 * Lmax / 4; q += NT) dst[q] = z;
+            }
+            v = next_tile(requested, &s_v);
+            continue;
+        }
         const int b = ct.x, t = ct.y;
         const int L = clamp_length(lengths, b, Lmax);
         const int T = L > 0 ? (L + TILE - 1) / TILE : 1;
@@ -128,25 +207,8 @@ __global__ void __launch_bounds__(NT) bb_fwd_kernel(const float* __restrict__ an
         float* out = coords + (size_t)b * 9 * Lmax;
         const int tile0 = t * TILE;
         const int j0 = tile0 + threadIdx.x * K;
-        float a[3][K];
-        load_row<K>(ang, j0, Lmax, a[0]);
-        load_row<K>(ang + Lmax, j0, Lmax, a[1]);
-        load_row<K>(ang + 2 * Lmax, j0, Lmax, a[2]);
-        Rigid A = rigid_identity();
         float3 pos[3 * K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const int j = j0 + k;
-#pragma unroll
-            for (int at = 0; at < 3; ++at) {
-                if (j < L && (j > 0 || at > 0)) {
-                    float s, c;
-                    sincosf(a[row_of(at)][k], &s, &c);
-                    rigid_mul_R(A, c, s, bc.ct[at], bc.st[at], bc.d[at]);
-                }
-                pos[3 * k + at] = A.t;
-            }
-        }
+        const Rigid A = thread_product<K>(ang, j0, L, Lmax, bc, pos);
         Rigid E, Tot;
         int ce, ctot;
         block_scan_rigid_count<NT>(A, 0, s_rig, s_cnt, E, ce, Tot, ctot);
@@ -231,6 +293,7 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
     __shared__ int s_cnt[NW + 1];
     __shared__ float s6[6 * (NW + 1)];
     __shared__ int s_v;
+    __shared__ PackS s_pack;
 
     const bool ok = ws_matches(ws, TILE, B, Lmax);
     if (!ok) {
@@ -244,29 +307,65 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
     int v = take_tile(counter, &s_v);
     while (v < ntiles) {
         const int2 ct = ws.tiles[v];
-        const int b = ct.x;
-        const int L = clamp_length(lengths, b, Lmax);
-        const int T = L > 0 ? (L + TILE - 1) / TILE : 1;
-        const int t = T - 1 - ct.y;  // last tile first
+        // a pack of whole short chains (segmented scans, no look-back) or one
+        // tile of a chain, the chain's tiles taken last to first
+        const bool pack = ct.x < 0;
+        int b, L, j0, t = 0, T = 1, m = 0;
+        bool head = false, tail = false;
+        if (pack) {
+            m = ct.y;
+            load_pack<K>(ws, lengths, Lmax, -1 - ct.x, m, s_pack);
+            const int slot = threadIdx.x * K;
+            const int ci = pack_member(s_pack, m, slot);
+            b = ci >= 0 ? s_pack.b[ci] : 0;
+            L = ci >= 0 ? s_pack.len[ci] : 0;
+            j0 = ci >= 0 ? slot - s_pack.off[ci] : Lmax;  // Lmax: nothing to load or store
+            head = ci < 0 || j0 == 0;
+            tail = ci < 0 || slot + K >= s_pack.off[ci + 1];
+        } else {
+            b = ct.x;
+            L = clamp_length(lengths, b, Lmax);
+            T = L > 0 ? (L + TILE - 1) / TILE : 1;
+            t = T - 1 - ct.y;
+            j0 = t * TILE + threadIdx.x * K;
+        }
         const int slot0 = b * ws.tmax;
         const float* ang = angles + (size_t)b * 3 * Lmax;
         const float* g_in = grad_coords + (size_t)b * 9 * Lmax;
         int requested = 0;
         float* ga = grad_angles + (size_t)b * 3 * Lmax;
-        const int j0 = t * TILE + threadIdx.x * K;
 
         float g[9 * K];
-        load_atoms<K>(g_in + 9 * (size_t)j0, j0 < Lmax, g);
+        load_atoms<K>(g_in + 9 * (size_t)min(j0, Lmax - K), j0 < Lmax, g);
         Sum6 own = sum6_zero();
         float gr[3][K];
+        // (sum r x g, sum g) over the later atoms of the chain, from the block
+        // suffix scan and, for a tile, the look-back over the chain's later tiles
+        auto later_sums = [&](const Sum6& x) {
+            Sum6 after, total;
+            if (pack) {
+                after = block_seg_suffix_sum6<NT>(x, tail, s6, s_cnt);
+            } else {
+                block_suffix_sum6<NT>(x, s6, after, total);
+                if (threadIdx.x == NT - 32) publish_suffix_agg(ws, slot0 + t, total);
+                after = sum6_add(after, gather_suffix(ws, slot0, t, T));  // every warp gathers it
+            }
+            requested = request_tile(counter);  // after the last wait of this tile
+            return after;
+        };
         if constexpr (!FROM_COORDS) {
             float sn[3 * K], cs[3 * K];
             Rigid A = local_product<K>(ang, j0, L, Lmax, bc, sn, cs);
-            Rigid E, Tot;
-            int ce, ctot;
-            block_scan_rigid_count<NT>(A, 0, s_rig, s_cnt, E, ce, Tot, ctot);
-            int pc;
-            E = rigid_mul(load_rigid_prev(ws.start + 4 * (size_t)(slot0 + t), pc), E);
+            Rigid E;
+            if (pack) {
+                E = block_seg_scan_rigid<NT>(A, head, s_rig, s_cnt);
+            } else {
+                Rigid Tot;
+                int ce, ctot;
+                block_scan_rigid_count<NT>(A, 0, s_rig, s_cnt, E, ce, Tot, ctot);
+                int pc;
+                E = rigid_mul(load_rigid_prev(ws.start + 4 * (size_t)(slot0 + t), pc), E);
+            }
             // pass 1: per-thread totals of (r x g, g)
             Rigid M = E;
 #pragma unroll
@@ -283,13 +382,8 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
                     }
                 }
             }
-            Sum6 after, total;
-            block_suffix_sum6<NT>(own, s6, after, total);
-            if (threadIdx.x == NT - 32) publish_suffix_agg(ws, slot0 + t, total);
-            const Sum6 later = gather_suffix(ws, slot0, t, T);  // every warp gathers it
-            requested = request_tile(counter);  // after the last wait of this tile
             // pass 2: gradients, atoms ascending with S = sum over atoms >= current
-            Sum6 S = sum6_add(sum6_add(after, later), own);
+            Sum6 S = sum6_add(later_sums(own), own);
             M = E;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -312,7 +406,7 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
         } else {
             const float* r_in = coords + (size_t)b * 9 * Lmax;
             float r[9 * K];
-            load_atoms<K>(r_in + 9 * (size_t)j0, j0 < Lmax, r);
+            load_atoms<K>(r_in + 9 * (size_t)min(j0, Lmax - K), j0 < Lmax, r);
             float3 prev = make_float3(0.f, 0.f, 0.f);
             if (j0 > 0 && j0 < Lmax) prev = make_float3(r_in[9 * j0 - 3], r_in[9 * j0 - 2], r_in[9 * j0 - 1]);
 #pragma unroll
@@ -324,12 +418,7 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
                     own.g = f3_add(own.g, gi);
                 }
             }
-            Sum6 after, total;
-            block_suffix_sum6<NT>(own, s6, after, total);
-            if (threadIdx.x == NT - 32) publish_suffix_agg(ws, slot0 + t, total);
-            const Sum6 later = gather_suffix(ws, slot0, t, T);  // every warp gathers it
-            requested = request_tile(counter);  // after the last wait of this tile
-            Sum6 S = sum6_add(sum6_add(after, later), own);
+            Sum6 S = sum6_add(later_sums(own), own);
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const int j = j0 + k;
@@ -356,7 +445,16 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
         store_row<K>(ga, j0, Lmax, gr[0]);
         store_row<K>(ga + Lmax, j0, Lmax, gr[1]);
         store_row<K>(ga + 2 * Lmax, j0, Lmax, gr[2]);
-        if (t == T - 1) {
+        if (pack) {  // rows past each chain's slots
+            for (int i = 0; i < m; ++i) {
+                float* gi = grad_angles + (size_t)s_pack.b[i] * 3 * Lmax;
+                for (int j = s_pack.off[i + 1] - s_pack.off[i] + threadIdx.x; j < Lmax; j += NT) {
+                    gi[j] = 0.f;
+                    gi[Lmax + j] = 0.f;
+                    gi[2 * Lmax + j] = 0.f;
+                }
+            }
+        } else if (t == T - 1) {
             for (int i = min(Lmax, T * TILE) + threadIdx.x; i < Lmax; i += NT) {
                 ga[i] = 0.f;
                 ga[Lmax + i] = 0.f;
@@ -487,12 +585,13 @@ bool backbone_cfg_supported(int threads, int k) {
     }
 
 cudaError_t launch_backbone_forward(const float* angles, const int32_t* lengths, int B, int Lmax,
-                                    float* coords, bool longest_first, void* workspace,
+                                    float* coords, int sched_mode, void* workspace,
                                     LaunchCfg cfg, cudaStream_t s) {
     if (B == 0) return cudaSuccess;
     ChainWs ws;
     chain_ws_layout(workspace, B, Lmax, &ws);
-    cudaError_t e = launch_schedule(lengths, B, Lmax, cfg.threads * cfg.res_per_thread, longest_first, ws, s);
+    cudaError_t e = launch_schedule(lengths, B, Lmax, cfg.threads * cfg.res_per_thread, sched_mode,
+                                    cfg.res_per_thread, ws, s);
     if (e != cudaSuccess) return e;
     TPL_BB_DISPATCH(fwd_t, angles, lengths, B, Lmax, coords, ws, s)
 }

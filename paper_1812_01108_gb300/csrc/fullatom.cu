@@ -173,6 +173,13 @@ __host__ __device__ constexpr int fa_min_blocks() {
     return NT >= 512 ? 1 : (NT >= 256 ? 3 : 6);
 }
 
+// The coordinate-reading backward stages two tiles (coordinates and their
+// gradients), so shared memory holds fewer of its CTAs per SM.
+template <int NT>
+__host__ __device__ constexpr int fa_bwd_min_blocks() {
+    return NT >= 512 ? 1 : (NT >= 256 ? 2 : 5);
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT, fa_min_blocks<NT>()) fa_fwd_kernel(
     const float* __restrict__ angles, const uint8_t* __restrict__ seq,
@@ -331,7 +338,7 @@ __host__ __device__ constexpr size_t fa_bwd_coords_smem() {
 __device__ __forceinline__ float3 unit3(float3 v) { return f3_scale(rsqrtf(f3_dot(v, v)), v); }
 
 template <int NT>
-__global__ void __launch_bounds__(NT, fa_min_blocks<NT>() > 2 ? fa_min_blocks<NT>() - 1 : 1) fa_bwd_coords_kernel(
+__global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_kernel(
     const uint8_t* __restrict__ seq, const int32_t* __restrict__ lengths, int B, int Lmax, int Amax,
     const float* __restrict__ coords, const float* __restrict__ grad_coords,
     float* __restrict__ grad_angles, ChainWs ws, const __grid_constant__ FaTable tab) {
@@ -874,12 +881,12 @@ bool fullatom_cfg_supported(int threads) {
 
 cudaError_t launch_fullatom_forward(const float* angles, const uint8_t* seq,
                                     const int32_t* lengths, int B, int Lmax, int Amax,
-                                    float* coords, int32_t* num_atoms, bool longest_first,
+                                    float* coords, int32_t* num_atoms, int sched_mode,
                                     void* workspace, LaunchCfg cfg, cudaStream_t s) {
     if (B == 0) return cudaSuccess;
     ChainWs ws;
     chain_ws_layout(workspace, B, Lmax, &ws);
-    cudaError_t e = launch_schedule(lengths, B, Lmax, cfg.threads, longest_first, ws, s);
+    cudaError_t e = launch_schedule(lengths, B, Lmax, cfg.threads, sched_mode, 1, ws, s);
     if (e != cudaSuccess) return e;
     switch (cfg.threads) {
         case 64: return fa_fwd_t<64>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s);

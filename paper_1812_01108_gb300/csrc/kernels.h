@@ -20,7 +20,7 @@ size_t chain_ws_bytes(int B, int Lmax);
 // K1 / K2: backbone FP32 scan kernels.
 bool backbone_cfg_supported(int threads, int res_per_thread);
 cudaError_t launch_backbone_forward(const float* angles, const int32_t* lengths, int B, int Lmax,
-                                    float* coords, bool longest_first, void* workspace,
+                                    float* coords, int sched_mode, void* workspace,
                                     LaunchCfg cfg, cudaStream_t s);
 cudaError_t launch_backbone_backward(const float* angles, const int32_t* lengths, int B, int Lmax,
                                      const float* coords, const float* grad_coords,
@@ -31,7 +31,7 @@ cudaError_t launch_backbone_backward(const float* angles, const int32_t* lengths
 bool fullatom_cfg_supported(int threads);
 cudaError_t launch_fullatom_forward(const float* angles, const uint8_t* seq,
                                     const int32_t* lengths, int B, int Lmax, int Amax,
-                                    float* coords, int32_t* num_atoms, bool longest_first,
+                                    float* coords, int32_t* num_atoms, int sched_mode,
                                     void* workspace, LaunchCfg cfg, cudaStream_t s);
 cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
                                      const int32_t* lengths, int B, int Lmax, int Amax,

@@ -1,7 +1,7 @@
 // LRMSD of the paper (Section 4) on sm_103a.
 //
 // Forward, three launches:
-//  K5a lrmsd_moments: grid (chunks, pairs), 2048 atoms per chunk.  Each CTA
+//  K5a lrmsd_moments: one CTA per (pair, chunk), 2048 atoms per chunk.  Each CTA
 //      streams its chunk once (16-byte loads) and reduces, in FP32, the
 //      moments shifted by the pair's first atom: sum dx, sum dy, sum dx dy^T
 //      (x = target, y = input, as in the paper's R = sum x y^T).
@@ -11,7 +11,7 @@
 //      quaternion-characteristic-polynomial approach of Theobald, Acta Cryst.
 //      A61 (2005) 478, then an adjugate column) and solves it in FP64
 //      (Rayleigh quotient of T, adjugate of T - lambda I), then U(q).
-//  K5c lrmsd_residual: grid (chunks, pairs).  LRMSD^2 = (sum |x'|^2 + |y'|^2 -
+//  K5c lrmsd_residual: one CTA per (pair, chunk).  LRMSD^2 = (sum |x'|^2 + |y'|^2 -
 //      2 lambda)/N equals sum |y'_i - U x'_i|^2 / N at the optimum; the
 //      residual form has no cancellation, so it is summed in FP32 per chunk and
 //      the chunk partials in FP64 by the last CTA of the pair.
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kNT) lrmsd_moments_kernel(const float* __restr
                                                             int P, int Nmax, float* __restrict__ part1,
                                                             int nch_max) {
     __shared__ float s_red[kNT / 32][kMom];
-    const int p = blockIdx.y, c = blockIdx.x;
+    const int p = blockIdx.x / nch_max, c = blockIdx.x % nch_max;
     const int n = pair_atoms(num_atoms, p, Nmax);
     if (c >= num_chunks(n)) return;
     const float* x = target + (size_t)p * Nmax * 3;
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(kNT) lrmsd_residual_kernel(
     float* __restrict__ lrmsd, int nch_max) {
     __shared__ float s_red[kNT / 32];
     __shared__ int s_last;
-    const int p = blockIdx.y, c = blockIdx.x;
+    const int p = blockIdx.x / nch_max, c = blockIdx.x % nch_max;
     const int n = pair_atoms(num_atoms, p, Nmax);
     const int nch = num_chunks(n);
     if (c >= nch) return;
@@ -448,8 +448,8 @@ __global__ void __launch_bounds__(kNT) lrmsd_grad_kernel(const float* __restrict
                                                          const float* __restrict__ target,
                                                          const int32_t* __restrict__ num_atoms,
                                                          int P, int Nmax, const float* __restrict__ state,
-                                                         float* __restrict__ grad_input) {
-    const int p = blockIdx.y, c = blockIdx.x;
+                                                         float* __restrict__ grad_input, int nch_max) {
+    const int p = blockIdx.x / nch_max, c = blockIdx.x % nch_max;
     const int n = pair_atoms(num_atoms, p, Nmax);
     const float* x = target + (size_t)p * Nmax * 3;
     const float* y = input + (size_t)p * Nmax * 3;
@@ -643,7 +643,7 @@ cudaError_t launch_lrmsd_forward(const float* input, const float* target, const 
     float* state = reinterpret_cast<float*>(base + L.state);
     double* lr64 = reinterpret_cast<double*>(base + L.lr64);
     int* counter = reinterpret_cast<int*>(base + L.counter);
-    const dim3 grid(L.nch, P);
+    const unsigned grid = (unsigned)P * (unsigned)L.nch;  // block = pair * nch + chunk
     lrmsd_moments_kernel<<<grid, kNT, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.nch);
     lrmsd_solve_kernel<<<(P + 31) / 32, 32, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.nch,
                                                     state, counter);
@@ -658,9 +658,9 @@ cudaError_t launch_lrmsd_backward(const float* grad_lrmsd, const float* input, c
     if (P == 0) return cudaSuccess;
     const WsLayout L = ws_layout(P, Nmax);
     const float* state = reinterpret_cast<const float*>(static_cast<const char*>(ws) + L.state);
-    const dim3 grid(L.nch, P);
+    const unsigned grid = (unsigned)P * (unsigned)L.nch;  // block = pair * nch + chunk
     lrmsd_grad_kernel<<<grid, kNT, 0, s>>>(grad_lrmsd, input, target, num_atoms, P, Nmax, state,
-                                           grad_input);
+                                           grad_input, L.nch);
     return cudaGetLastError();
 }
 

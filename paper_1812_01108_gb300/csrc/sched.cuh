@@ -37,9 +37,16 @@ enum {
     kHdrLmax = 5,
 };
 
+// A list entry is (chain, tile) for a tile of one chain, or, for a pack of
+// short chains that share one tile (chains per CTA > 1), (-1 - start, count):
+// the chains order[start .. start + count), each a whole chain, in slots
+// padded to the granule of the kernel (residues per thread).
+constexpr int kMaxPack = 8;
+
 struct ChainWs {
     int* hdr;        // 64 ints
-    int2* tiles;     // [B * tmax] (chain, tile)
+    int2* tiles;     // [B * tmax] list entries
+    int* order;      // [B] chains in schedule order (packs index into it)
     int* fflag;      // [B * tmax] forward aggregate flags
     float4* fagg;    // [B * tmax][4] forward aggregate: rigid (12 floats) + atom count
     float4* start;   // [B * tmax][4] frame at the tile start + first atom index
@@ -63,6 +70,7 @@ __host__ __device__ inline size_t chain_ws_layout(void* base, int B, int Lmax, C
     size_t o = 0;
     const size_t hdr = o; o = ws_align(o + 64 * sizeof(int));
     const size_t tiles = o; o = ws_align(o + slots * sizeof(int2));
+    const size_t order = o; o = ws_align(o + (size_t)(B > 0 ? B : 1) * sizeof(int));
     const size_t fflag = o; o = ws_align(o + slots * sizeof(int));
     const size_t fagg = o; o = ws_align(o + slots * 4 * sizeof(float4));
     const size_t start = o; o = ws_align(o + slots * 4 * sizeof(float4));
@@ -72,6 +80,7 @@ __host__ __device__ inline size_t chain_ws_layout(void* base, int B, int Lmax, C
         char* c = static_cast<char*>(base);
         w->hdr = reinterpret_cast<int*>(c + hdr);
         w->tiles = reinterpret_cast<int2*>(c + tiles);
+        w->order = reinterpret_cast<int*>(c + order);
         w->fflag = reinterpret_cast<int*>(c + fflag);
         w->fagg = reinterpret_cast<float4*>(c + fagg);
         w->start = reinterpret_cast<float4*>(c + start);
@@ -254,6 +263,50 @@ __device__ __forceinline__ Sum6 gather_suffix(const ChainWs& ws, int slot0, int 
     return r;
 }
 
+// Chains of a packed list entry, in shared memory: chain id, length and first
+// slot (slots of G residues; off[count] = slots used).
+struct PackS {
+    int b[kMaxPack];
+    int len[kMaxPack];
+    int off[kMaxPack + 1];
+};
+
+// Fills `s` for the pack (start, m) with warp 0; all threads must call it.
+template <int G>
+__device__ __forceinline__ void load_pack(const ChainWs& ws, const int32_t* lengths, int Lmax,
+                                          int start, int m, PackS& s) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int b = 0, L = 0;
+        if (lane < m) {
+            b = ws.order[start + lane];
+            L = clamp_length(lengths, b, Lmax);
+        }
+        const int lp = (L + G - 1) / G * G;
+        int inc = lp;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += y;
+        }
+        if (lane < m) {
+            s.b[lane] = b;
+            s.len[lane] = L;
+            s.off[lane] = inc - lp;
+            if (lane == m - 1) s.off[m] = inc;
+        }
+    }
+    __syncthreads();
+}
+
+// Member of the pack whose slots hold residue slot `slot`, or -1 (unused slot).
+__device__ __forceinline__ int pack_member(const PackS& s, int m, int slot) {
+    int ci = -1;
+    for (int i = 0; i < m; ++i)
+        if (s.off[i] <= slot && slot < s.off[i + 1]) ci = i;
+    return ci;
+}
+
 // Work-list entries for a persistent CTA.  take_tile() is called once at the
 // start; during a tile thread 0 requests the next entry (request_tile) once its
 // warp has finished the tile's look-back, and next_tile() hands it to the CTA
@@ -276,7 +329,11 @@ __device__ __forceinline__ int next_tile(int requested, int* s_v) {
 }
 
 // Host side: schedule kernel (api.cu) and the persistent grid size.
-cudaError_t launch_schedule(const int32_t* lengths, int B, int Lmax, int tile, bool longest_first,
+// Chain order of the schedule: batch order, longest first, or longest first
+// with the chains of at most one tile packed several per tile (granule =
+// residues per thread, the unit a chain's slots are padded to).
+enum SchedMode { kSchedBatch = 0, kSchedLongest = 1, kSchedPacked = 2 };
+cudaError_t launch_schedule(const int32_t* lengths, int B, int Lmax, int tile, int mode, int granule,
                             const ChainWs& ws, cudaStream_t s);
 cudaError_t reset_backward_flags(const ChainWs& ws, cudaStream_t s);
 int persistent_grid(const void* kernel, int threads, size_t smem);

@@ -225,6 +225,61 @@ __device__ __forceinline__ void block_scan_rigid_count(const Rigid& x, int cnt, 
 }
 
 // ---------------------------------------------------------------------------
+// Segmented block-wide exclusive scan of rigid transforms: a thread with
+// `head` set starts a new segment (its result is the identity); otherwise the
+// result is the product of the earlier threads back to the segment's head.
+// Two __syncthreads; s_rig / s_flag hold NW+1 entries.
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ Rigid block_seg_scan_rigid(const Rigid& x, bool head, RigidS* s_rig,
+                                                      int* s_flag) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    Rigid inc = x;
+    int fl = head ? 1 : 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const Rigid y = shfl_up_rigid(inc, off);
+        const int fy = __shfl_up_sync(0xffffffffu, fl, off);
+        if (lane >= off) {
+            if (!fl) inc = rigid_mul(y, inc);
+            fl |= fy;
+        }
+    }
+    if (lane == 31) {
+        store_rigid(s_rig[warp], inc);
+        s_flag[warp] = fl;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        Rigid w = (lane < NW) ? load_rigid(s_rig[lane]) : rigid_identity();
+        int wf = (lane < NW) ? s_flag[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < NW; off <<= 1) {
+            const Rigid y = shfl_up_rigid(w, off);
+            const int fy = __shfl_up_sync(0xffffffffu, wf, off);
+            if (lane >= off) {
+                if (!wf) w = rigid_mul(y, w);
+                wf |= fy;
+            }
+        }
+        Rigid wex = shfl_up_rigid(w, 1);
+        if (lane == 0) wex = rigid_identity();
+        if (lane < NW) store_rigid(s_rig[lane], wex);
+    }
+    __syncthreads();
+    Rigid lex = shfl_up_rigid(inc, 1);
+    int lexf = __shfl_up_sync(0xffffffffu, fl, 1);
+    if (lane == 0) {
+        lex = rigid_identity();
+        lexf = 0;
+    }
+    if (head) return rigid_identity();
+    return lexf ? lex : rigid_mul(load_rigid(s_rig[warp]), lex);
+}
+
+// ---------------------------------------------------------------------------
 // Block-wide exclusive REVERSE (suffix) scan of a 6-float sum (r x g, g):
 // `after` = sum over threads with a larger index; `total` = sum over all
 // threads.  scratch: NW+1 float[6].  Two __syncthreads.
@@ -314,6 +369,76 @@ __device__ __forceinline__ void block_suffix_sum6(const Sum6& x, float* s6, Sum6
     const float* q = s6 + 6 * NW;
     total.c = make_float3(q[0], q[1], q[2]);
     total.g = make_float3(q[3], q[4], q[5]);
+}
+
+// Segmented form: a thread with `tail` set ends its segment, so its result
+// is zero; otherwise the result sums the later threads up to and including
+// the segment's tail.  Two __syncthreads; s6 holds NW+1 float[6], s_flag NW+1.
+template <int NT>
+__device__ __forceinline__ Sum6 block_seg_suffix_sum6(const Sum6& x, bool tail, float* s6,
+                                                      int* s_flag) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    Sum6 inc = x;
+    int fl = tail ? 1 : 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const Sum6 y = shfl_down_sum6(inc, off);
+        const int fy = __shfl_down_sync(0xffffffffu, fl, off);
+        if (lane + off < 32) {
+            if (!fl) inc = sum6_add(inc, y);
+            fl |= fy;
+        }
+    }
+    if (lane == 0) {
+        float* p = s6 + 6 * warp;
+        p[0] = inc.c.x; p[1] = inc.c.y; p[2] = inc.c.z;
+        p[3] = inc.g.x; p[4] = inc.g.y; p[5] = inc.g.z;
+        s_flag[warp] = fl;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        Sum6 w = sum6_zero();
+        int wf = 0;
+        if (lane < NW) {
+            const float* p = s6 + 6 * lane;
+            w.c = make_float3(p[0], p[1], p[2]);
+            w.g = make_float3(p[3], p[4], p[5]);
+            wf = s_flag[lane];
+        }
+#pragma unroll
+        for (int off = 1; off < NW; off <<= 1) {
+            const Sum6 y = shfl_down_sum6(w, off);
+            const int fy = __shfl_down_sync(0xffffffffu, wf, off);
+            if (lane + off < 32) {
+                if (!wf) w = sum6_add(w, y);
+                wf |= fy;
+            }
+        }
+        Sum6 wex = shfl_down_sum6(w, 1);  // segment sum starting at the next warp
+        if (lane >= NW - 1) wex = sum6_zero();
+        __syncwarp();
+        if (lane < NW) {
+            float* p = s6 + 6 * lane;
+            p[0] = wex.c.x; p[1] = wex.c.y; p[2] = wex.c.z;
+            p[3] = wex.g.x; p[4] = wex.g.y; p[5] = wex.g.z;
+        }
+    }
+    __syncthreads();
+    Sum6 lex = shfl_down_sum6(inc, 1);
+    int lexf = __shfl_down_sync(0xffffffffu, fl, 1);
+    if (lane == 31) {
+        lex = sum6_zero();
+        lexf = 0;
+    }
+    if (tail) return sum6_zero();
+    if (lexf) return lex;
+    const float* p = s6 + 6 * warp;
+    Sum6 wv;
+    wv.c = make_float3(p[0], p[1], p[2]);
+    wv.g = make_float3(p[3], p[4], p[5]);
+    return sum6_add(lex, wv);
 }
 
 __device__ __forceinline__ int clamp_length(const int32_t* lengths, int b, int Lmax) {

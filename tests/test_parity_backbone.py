@@ -66,13 +66,46 @@ def test_fp32_scan_matches_oracle(reference, threads, k):
     assert np.all(ga32[:, 2, 0] == 0)  # omega_0 carries no gradient
 
 
-@pytest.mark.parametrize("sched", [tpl.SCHED_LONGEST_FIRST, tpl.SCHED_BATCH_ORDER])
-def test_schedules_and_from_coords_mode(reference, sched):
+@pytest.mark.parametrize("sched", [tpl.SCHED_LONGEST_FIRST, tpl.SCHED_BATCH_ORDER, tpl.SCHED_PACKED])
+@pytest.mark.parametrize("bwd", [tpl.BWD_FROM_COORDS, tpl.BWD_RECOMPUTE])
+def test_schedules_and_backward_modes(reference, sched, bwd):
     a, g, c64, g64 = reference
-    c32, ga32 = _run_fp32(a, LENGTHS, g, {"schedule": sched},
-                          {"schedule": sched, "bwd_mode": tpl.BWD_FROM_COORDS})
+    c32, ga32 = _run_fp32(a, LENGTHS, g, {"schedule": sched}, {"schedule": sched, "bwd_mode": bwd})
     assert np.abs(c32 - c64).max() <= COORD_TOL
     assert rel_err(ga32, g64) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("threads,k", [(128, 4), (64, 1), (256, 2), (512, 1)])
+@pytest.mark.parametrize("bwd", [tpl.BWD_FROM_COORDS, tpl.BWD_RECOMPUTE])
+def test_packed_short_chains(threads, k, bwd):
+    """Many chains of at most one tile: up to 8 whole chains share a tile
+    (segmented scans), with empty chains and lengths not a multiple of the
+    residues per thread."""
+    rng = np.random.default_rng(41)
+    lengths = rng.integers(0, 41, size=300).astype(np.int32)
+    lengths[:7] = [0, 1, 2, 3, 4, 5, 64]
+    a, g = _inputs(lengths, 42, Lmax=64)
+    opts = {"threads": threads, "res_per_thread": k, "schedule": tpl.SCHED_PACKED}
+    c32, ga32 = _run_fp32(a, lengths, g, opts, dict(opts, bwd_mode=bwd))
+    assert np.abs(c32 - oracle.backbone_forward(a, lengths)).max() <= COORD_TOL
+    g64 = oracle.backbone_backward(a, lengths, g)
+    for b, L in enumerate(lengths):
+        assert np.all(c32[b, 3 * L:] == 0) and np.all(ga32[b, :, L:] == 0)
+        if L > 1:
+            assert rel_err(ga32[b][None], g64[b][None]) <= GRAD_TOL
+
+
+def test_packed_and_tiled_chains_in_one_batch():
+    """Log-uniform lengths: chains longer than a tile use tiles and the
+    look-back, the rest are packed."""
+    rng = np.random.default_rng(43)
+    lengths = workloads.lengths_loguniform(96, 1, 1000, rng)
+    a, g = _inputs(lengths, 44, Lmax=1000)
+    for bwd in (tpl.BWD_FROM_COORDS, tpl.BWD_RECOMPUTE):
+        opts = {"threads": 128, "res_per_thread": 2, "schedule": tpl.SCHED_PACKED}
+        c32, ga32 = _run_fp32(a, lengths, g, opts, dict(opts, bwd_mode=bwd))
+        assert np.abs(c32 - oracle.backbone_forward(a, lengths)).max() <= COORD_TOL
+        assert rel_err(ga32, oracle.backbone_backward(a, lengths, g)) <= GRAD_TOL
 
 
 def test_results_do_not_depend_on_the_schedule(reference):
@@ -144,3 +177,21 @@ def test_backward_without_forward_workspace_flags_and_zeroes():
     tpl.tpl_backbone_backward(A, Ln, None, dev(g, d), ga, ws)
     assert tpl.tpl_get_status() & tpl.STATUS_BAD_WORKSPACE
     assert torch.all(ga == 0)
+
+
+def test_autotuner_picks_a_valid_shape_and_its_results_match():
+    d = require_gpu()
+    rng = np.random.default_rng(45)
+    lengths = workloads.lengths_loguniform(64, 20, 600, rng)
+    a, g = _inputs(lengths, 46, Lmax=600)
+    A, Ln, G = dev(a, d), dev(lengths, d), dev(g, d)
+    B, _, Lmax = a.shape
+    coords = torch.empty((B, 3 * Lmax, 3), device=d)
+    ga = torch.empty_like(A)
+    ws = torch.empty(tpl.tpl_backbone_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    best, ms = tpl.tpl_backbone_autotune(A, Ln, coords, G, ga, ws, bwd_mode=tpl.BWD_FROM_COORDS)
+    assert ms > 0 and best.threads in (64, 128, 256, 512) and best.res_per_thread in (1, 2, 4)
+    assert best.schedule in (tpl.SCHED_PACKED, tpl.SCHED_LONGEST_FIRST)
+    c32, ga32 = _run_fp32(a, lengths, g, best)
+    assert np.abs(c32 - oracle.backbone_forward(a, lengths)).max() <= COORD_TOL
+    assert rel_err(ga32, oracle.backbone_backward(a, lengths, g)) <= GRAD_TOL

@@ -129,3 +129,21 @@ def test_bad_residue_and_too_many_atoms_set_status():
     c32, na32, _ = _run_fp32(a, seq, lengths, g, 12)  # Amax far too small
     assert tpl.tpl_get_status() & tpl.STATUS_TOO_MANY_ATOMS
     assert np.all(np.isfinite(c32))
+
+
+def test_autotuner_picks_a_valid_shape_and_its_results_match(reference):
+    d = require_gpu()
+    a, seq, g, Amax, c64, na64, g64 = reference
+    A, S, Ln, G = dev(a, d), dev(seq, d), dev(LENGTHS, d), dev(g, d)
+    B, _, Lmax = a.shape
+    coords = torch.empty((B, Amax, 3), device=d)
+    na = torch.empty((B,), dtype=torch.int32, device=d)
+    ga = torch.empty_like(A)
+    ws = torch.empty(tpl.tpl_fullatom_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    best, ms = tpl.tpl_fullatom_autotune(A, S, Ln, coords, na, G, ga, ws, bwd_mode=tpl.BWD_FROM_COORDS)
+    assert ms > 0 and best.threads in (64, 128, 256, 512)
+    assert best.schedule in (tpl.SCHED_BATCH_ORDER, tpl.SCHED_LONGEST_FIRST)
+    c32, n32, ga32 = _run_fp32(a, seq, LENGTHS, g, Amax, best, from_coords=True)
+    assert np.array_equal(n32, na64)
+    assert np.abs(c32 - c64).max() <= COORD_TOL
+    assert rel_err(ga32, g64) <= GRAD_TOL
