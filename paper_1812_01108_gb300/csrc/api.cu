@@ -227,7 +227,9 @@ tpl_status check_ws(void* ws, size_t have, size_t need) {
 
 }  // namespace
 
-size_t chain_ws_bytes(int B, int Lmax) { return chain_ws_layout(nullptr, B, Lmax, nullptr); }
+size_t chain_ws_bytes(int B, int Lmax, bool per_residue) {
+    return chain_ws_layout(nullptr, B, Lmax, nullptr, per_residue);
+}
 
 // One thread waits on `flag` with the chain kernels' bounded wait.
 __global__ void selftest_wait_kernel(const int* flag) {
@@ -343,9 +345,9 @@ const char* tpl_version(void) { return "0.1.0"; }
 
 const char* tpl_last_error(void) { return t_last_error.c_str(); }
 
-size_t tpl_backbone_workspace_size(int B, int Lmax) { return chain_ws_bytes(B, Lmax); }
+size_t tpl_backbone_workspace_size(int B, int Lmax) { return chain_ws_bytes(B, Lmax, false); }
 
-size_t tpl_fullatom_workspace_size(int B, int Lmax) { return chain_ws_bytes(B, Lmax); }
+size_t tpl_fullatom_workspace_size(int B, int Lmax) { return chain_ws_bytes(B, Lmax, true); }
 
 size_t tpl_lrmsd_workspace_size(int P, int Nmax) {
     if (P <= 0 || Nmax < 0) return 256;

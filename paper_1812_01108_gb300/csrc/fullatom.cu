@@ -108,32 +108,9 @@ __device__ __forceinline__ void store_range(float* __restrict__ glob, const floa
     for (int i = tail + threadIdx.x; i < g1; i += NT) glob[i] = stage[i - g0];
 }
 
-// Asynchronous copy (cp.async, no register round trip) of the float range
-// [g0, g1) of global memory into stage[off + i - g0], off = g0 mod 4: 16-byte
-// copies for the aligned middle, 4-byte copies for the ragged ends.  The caller
-// commits and waits (cp_async_wait_all) before a barrier.
-__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-                 "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-                 "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
-template <int NT>
-__device__ __forceinline__ void async_copy_range(const float* __restrict__ glob, float* __restrict__ stage,
-                                                 int g0, int g1) {
-    if (g1 <= g0) return;
-    const int off = g0 & 3;
-    const int head = min(g1, (g0 + 3) & ~3);
-    const int tail = max(head, g1 & ~3);
-    for (int i = g0 + threadIdx.x; i < head; i += NT) cp_async4(stage + off + i - g0, glob + i);
-    for (int q = head / 4 + threadIdx.x; q < tail / 4; q += NT) cp_async16(stage + off + 4 * q - g0, glob + 4 * q);
-    for (int i = tail + threadIdx.x; i < g1; i += NT) cp_async4(stage + off + i - g0, glob + i);
+// Fetch the 128-byte line at p into L2 (a hint; nothing waits on it).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 template <int NT>
@@ -177,7 +154,7 @@ __host__ __device__ constexpr int fa_min_blocks() {
 // gradients), so shared memory holds fewer of its CTAs per SM.
 template <int NT>
 __host__ __device__ constexpr int fa_bwd_min_blocks() {
-    return NT >= 512 ? 1 : (NT >= 256 ? 2 : 5);
+    return NT >= 512 ? 2 : (NT >= 256 ? 4 : 8);
 }
 
 template <int NT>
@@ -189,7 +166,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT>()) fa_fwd_kernel(
     __shared__ FaTable s_tab;
     __shared__ RigidS s_rig[NW + 1];
     __shared__ int s_cnt[NW + 1];
-    __shared__ int s_v;
+    __shared__ int s_v, s_next;
     extern __shared__ float4 s_dyn[];
     float* stage = reinterpret_cast<float*>(s_dyn);  // tile-local atoms, 3 floats each
 
@@ -276,7 +253,9 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT>()) fa_fwd_kernel(
         int pc;
         const Rigid P = gather_prefix(ws, slot0, t, pc);
         const int requested = request_tile(ws.hdr + kHdrFwdNext);  // after the last wait of this tile
+        if (threadIdx.x == 0) s_next = requested;
         if (threadIdx.x == 0) store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, pc, tile_atoms);
+        if (valid) ws.ratom[(size_t)b * Lmax + j] = pc + a0;  // the backward reads its atoms directly
         const int end_atom = pc + tile_atoms;
         const int nout = max(0, min(end_atom, Amax) - pc);
         for (int a = threadIdx.x; a < nout; a += NT) {
@@ -286,6 +265,21 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT>()) fa_fwd_kernel(
             stage[3 * a + 2] = r.z;
         }
         __syncthreads();
+        {
+            // the next tile's angle rows and sequence into L2 while this tile is stored
+            const int vn = s_next;
+            if (vn < ntiles && threadIdx.x < 64) {
+                const int2 cn = ws.tiles[vn];
+                const int row = threadIdx.x >> 3, part = threadIdx.x & 7;  // 8 rows x 8 parts of NT residues
+                const int jn = cn.y * NT + part * (NT / 8);
+                if (cn.x >= 0 && jn < Lmax) {
+                    const char* base = row < 7 ? reinterpret_cast<const char*>(angles + ((size_t)cn.x * 7 + row) * Lmax + jn)
+                                               : reinterpret_cast<const char*>(seq + (size_t)cn.x * Lmax + jn);
+                    const int bytes = (row < 7 ? 4 : 1) * min(NT / 8, Lmax - jn);
+                    for (int o = 0; o < bytes; o += 128) prefetch_l2(base + o);
+                }
+            }
+        }
         if (end_atom > Amax && threadIdx.x == 0) flag_status(TPL_STATUS_TOO_MANY_ATOMS);
         store_range<NT>(out, stage, 3 * pc, 3 * (pc + nout));
         if (t == T - 1) {
@@ -330,12 +324,9 @@ __device__ __forceinline__ int block_scan_int(int x, int* s_cnt, int& total) {
 // group k-1 -> origin of group k); the tile's atoms and their upstream
 // gradients are staged in shared memory with 16-byte loads.
 // ---------------------------------------------------------------------------
-template <int NT>
-__host__ __device__ constexpr size_t fa_bwd_coords_smem() {
-    return 2 * (size_t)(4 + NT * kMaxAtoms * 3) * 4;
-}
 
 __device__ __forceinline__ float3 unit3(float3 v) { return f3_scale(rsqrtf(f3_dot(v, v)), v); }
+
 
 template <int NT>
 __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_kernel(
@@ -343,16 +334,9 @@ __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_ker
     const float* __restrict__ coords, const float* __restrict__ grad_coords,
     float* __restrict__ grad_angles, ChainWs ws, const __grid_constant__ FaTable tab) {
     constexpr int NW = NT / 32;
-    constexpr int STAGE = 4 + NT * kMaxAtoms * 3;
     __shared__ FaTable s_tab;
-    __shared__ int s_cnt[NW + 1];
     __shared__ float s6[6 * (NW + 1)];
-    __shared__ float s_prevc[3];
     __shared__ int s_v;
-    __shared__ uint8_t s_type[NT];
-    extern __shared__ float4 s_dyn[];
-    float* st_r = reinterpret_cast<float*>(s_dyn);
-    float* st_g = st_r + STAGE;
 
     if (!ws_matches(ws, NT, B, Lmax)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) flag_status(TPL_STATUS_BAD_WORKSPACE);
@@ -376,40 +360,25 @@ __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_ker
         const float* g_in = grad_coords + (size_t)b * Amax * 3;
         float* ga = grad_angles + (size_t)b * 7 * Lmax;
 
-        // the forward recorded the tile's first atom and atom count: start the
-        // staging copies right away, then scan the counts while they fly
-        const float4 sd = ws.start[4 * (size_t)(slot0 + t) + 3];
-        const int pc = __float_as_int(sd.x);
-        const int soff = (3 * pc) & 3;
-        const int g1 = 3 * min(pc + __float_as_int(sd.y), Amax);
-        async_copy_range<NT>(r_in, st_r, 3 * pc, g1);
-        async_copy_range<NT>(g_in, st_g, 3 * pc, g1);
+        // each thread reads its residue's atoms directly (the forward recorded
+        // every residue's first atom); the per-thread runs are contiguous, so
+        // a warp's loads stay within a few kilobytes and hit L1 after the first
         const int j = t * NT + threadIdx.x;
         const bool valid = j < L;
         const int type = residue_type(sq, j, valid);
         const int nat = valid ? s_tab.n_atoms[type] : 0;
-        s_type[threadIdx.x] = (uint8_t)type;
-        int tile_atoms;
-        const int a0 = block_scan_int<NT>(nat, s_cnt, tile_atoms);
-        if (threadIdx.x == 0 && t > 0) {  // C of the residue before the tile
-            const int jp = t * NT - 1;
-            const int ip = pc - s_tab.n_atoms[residue_type(sq, jp, true)] + 2;
-            s_prevc[0] = r_in[3 * ip];
-            s_prevc[1] = r_in[3 * ip + 1];
-            s_prevc[2] = r_in[3 * ip + 2];
-        }
-        cp_async_wait_all();
-        __syncthreads();
+        const int a0 = valid ? __ldg(ws.ratom + (size_t)b * Lmax + j) : 0;
+        const int ap = (valid && j > 0) ? __ldg(ws.ratom + (size_t)b * Lmax + j - 1) : 0;
 
+        const bool in_range = valid && a0 >= 0 && a0 + nat <= Amax;
         float gchi[kMaxGroups] = {0.f, 0.f, 0.f, 0.f};
         Sum6 all = sum6_zero(), nsum = sum6_zero(), csum = sum6_zero();
         float3 rN = make_float3(0.f, 0.f, 0.f), rCA = rN, rC = rN, rCprev = rN;
-        const bool in_range = valid && pc + a0 + nat <= Amax;
         if (in_range) {
-            const float* sr = st_r + soff + 3 * a0;
-            const float* sg = st_g + soff + 3 * a0;
-            auto R = [&](int k) { return make_float3(sr[3 * k], sr[3 * k + 1], sr[3 * k + 2]); };
-            auto G = [&](int k) { return make_float3(sg[3 * k], sg[3 * k + 1], sg[3 * k + 2]); };
+            const float* sr = r_in + 3 * (size_t)a0;
+            const float* sg = g_in + 3 * (size_t)a0;
+            auto R = [&](int k) { return make_float3(__ldg(sr + 3 * k), __ldg(sr + 3 * k + 1), __ldg(sr + 3 * k + 2)); };
+            auto G = [&](int k) { return make_float3(__ldg(sg + 3 * k), __ldg(sg + 3 * k + 1), __ldg(sg + 3 * k + 2)); };
             auto add = [&](Sum6& s, int k) {
                 const float3 g = G(k);
                 s.c = f3_add(s.c, f3_cross(R(k), g));
@@ -418,6 +387,10 @@ __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_ker
             rN = R(0);
             rCA = R(1);
             rC = R(2);
+            if (j > 0) {  // C of the previous residue
+                const float* pr = r_in + 3 * (size_t)(ap + 2);
+                rCprev = make_float3(__ldg(pr), __ldg(pr + 1), __ldg(pr + 2));
+            }
             add(nsum, 0);
             add(all, 1);
             add(csum, 2);
@@ -441,15 +414,6 @@ __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_ker
                 }
             }
             all = sum6_add(sum6_add(all, suf), csum);
-            if (j > 0) {
-                if (threadIdx.x == 0) {
-                    rCprev = make_float3(s_prevc[0], s_prevc[1], s_prevc[2]);
-                } else {
-                    const int np = s_tab.n_atoms[s_type[threadIdx.x - 1]];
-                    const float* pr = sr - 3 * np + 6;
-                    rCprev = make_float3(pr[0], pr[1], pr[2]);
-                }
-            }
         }
         const Sum6 own = sum6_add(all, nsum);
         Sum6 after, total;
@@ -849,12 +813,8 @@ template <int NT>
 cudaError_t fa_bwd_coords_t(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
                             const float* coords, const float* grad_coords, float* grad_angles,
                             const ChainWs& ws, cudaStream_t s) {
-    const size_t smem = fa_bwd_coords_smem<NT>();
-    static bool done[64] = {false};
-    cudaError_t e = smem_attr_once(fa_bwd_coords_kernel<NT>, (int)smem, done);
-    if (e != cudaSuccess) return e;
-    const int grid = persistent_grid((const void*)fa_bwd_coords_kernel<NT>, NT, smem);
-    fa_bwd_coords_kernel<NT><<<grid, NT, smem, s>>>(seq, lengths, B, Lmax, Amax, coords, grad_coords,
+    const int grid = persistent_grid((const void*)fa_bwd_coords_kernel<NT>, NT, 0);
+    fa_bwd_coords_kernel<NT><<<grid, NT, 0, s>>>(seq, lengths, B, Lmax, Amax, coords, grad_coords,
                                                     grad_angles, ws, fa_table());
     return cudaGetLastError();
 }
@@ -885,7 +845,7 @@ cudaError_t launch_fullatom_forward(const float* angles, const uint8_t* seq,
                                     void* workspace, LaunchCfg cfg, cudaStream_t s) {
     if (B == 0) return cudaSuccess;
     ChainWs ws;
-    chain_ws_layout(workspace, B, Lmax, &ws);
+    chain_ws_layout(workspace, B, Lmax, &ws, true);
     cudaError_t e = launch_schedule(lengths, B, Lmax, cfg.threads, sched_mode, 1, ws, s);
     if (e != cudaSuccess) return e;
     switch (cfg.threads) {
@@ -904,7 +864,7 @@ cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
                                      LaunchCfg cfg, cudaStream_t s) {
     if (B == 0) return cudaSuccess;
     ChainWs ws;
-    chain_ws_layout(workspace, B, Lmax, &ws);
+    chain_ws_layout(workspace, B, Lmax, &ws, true);
     cudaError_t e = reset_backward_flags(ws, s);
     if (e != cudaSuccess) return e;
     if (from_coords) {

@@ -14,8 +14,9 @@ struct LaunchCfg {
 };
 
 // Bytes of the chain workspace (tile list, look-back flags and aggregates,
-// tile-start frames) for B chains of at most Lmax residues.
-size_t chain_ws_bytes(int B, int Lmax);
+// tile-start frames; with per_residue, each residue's first atom) for B chains
+// of at most Lmax residues.
+size_t chain_ws_bytes(int B, int Lmax, bool per_residue);
 
 // K1 / K2: backbone FP32 scan kernels.
 bool backbone_cfg_supported(int threads, int res_per_thread);

@@ -52,6 +52,7 @@ struct ChainWs {
     float4* start;   // [B * tmax][4] frame at the tile start + first atom index
     int* bflag;      // [B * tmax + 4]: backward flags; word B * tmax is the backward work counter
     float4* bagg;    // [B * tmax][2] backward aggregate (c, g)
+    int* ratom;      // [B * Lmax] first atom of each residue (full atom only; else null)
     int tmax;        // tiles per chain for the smallest tile
     int slots;       // B * tmax
 };
@@ -64,7 +65,8 @@ __host__ __device__ inline int ws_tmax(int Lmax) {
 }
 
 // Offsets of the regions; `base` may be null to only size the workspace.
-__host__ __device__ inline size_t chain_ws_layout(void* base, int B, int Lmax, ChainWs* w) {
+__host__ __device__ inline size_t chain_ws_layout(void* base, int B, int Lmax, ChainWs* w,
+                                                  bool per_residue = false) {
     const int tmax = ws_tmax(Lmax);
     const size_t slots = (size_t)(B > 0 ? B : 1) * tmax;
     size_t o = 0;
@@ -76,6 +78,8 @@ __host__ __device__ inline size_t chain_ws_layout(void* base, int B, int Lmax, C
     const size_t start = o; o = ws_align(o + slots * 4 * sizeof(float4));
     const size_t bflag = o; o = ws_align(o + (slots + 4) * sizeof(int));
     const size_t bagg = o; o = ws_align(o + slots * 2 * sizeof(float4));
+    const size_t ratom = o;
+    if (per_residue) o = ws_align(o + (size_t)(B > 0 ? B : 1) * (Lmax > 0 ? Lmax : 1) * sizeof(int));
     if (w) {
         char* c = static_cast<char*>(base);
         w->hdr = reinterpret_cast<int*>(c + hdr);
@@ -86,6 +90,7 @@ __host__ __device__ inline size_t chain_ws_layout(void* base, int B, int Lmax, C
         w->start = reinterpret_cast<float4*>(c + start);
         w->bflag = reinterpret_cast<int*>(c + bflag);
         w->bagg = reinterpret_cast<float4*>(c + bagg);
+        w->ratom = per_residue ? reinterpret_cast<int*>(c + ratom) : nullptr;
         w->tmax = tmax;
         w->slots = (int)slots;
     }
