@@ -18,9 +18,11 @@ Workloads (``--workload``):
 ``--impl reference`` times the FP64 CPU oracle, as it stands, on a bounded
 sample of the same workload instead.
 
-Timing: W warm-up steps, then K timed steps; every C-ABI call of a step is a
-CUDA graph replayed between CUDA events on the launching stream, and L2 is
-flushed (a 512 MiB write, outside the events) before every step.  Under
+Timing: W warm-up steps, then K timed steps; a step (all its C-ABI calls) is
+one CUDA graph replayed between CUDA events on the launching stream, and L2 is
+flushed (a 512 MiB write, outside the events) before every step.  Per-call
+times (breakdown, roofline) come from a second graph of the same calls with
+event-record nodes between them.  Under
 torchrun each rank runs its own batch (weak scaling, no data-path collective);
 the elapsed time is the max over ranks.
 """
@@ -596,31 +598,34 @@ def run_tpl(args):
     status = tpl.tpl_get_status()
     if status != 0:
         raise SystemExit(f"device status 0x{status:x} after the warm-up steps")
-    # one CUDA graph per C-ABI call: replays cost the host a few microseconds, so
-    # the events below see GPU time, not Python launch overhead
-    graphs = []
-    for _, c in st.calls:
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
+    # the whole step is one CUDA graph (forward -> LRMSD -> backward), replayed
+    # between CUDA events; a second graph with event-record nodes between the
+    # calls gives the per-call times (its extra nodes make it a little slower,
+    # so it is used for the breakdown and the roofline, not for the value)
+    nc = len(st.calls)
+    step_graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(step_graph):
+        for _, c in st.calls:
             c()
-        graphs.append(g)
+    split_ev = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(nc + 1)]
+    split_graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(split_graph):
+        for i, (_, c) in enumerate(st.calls):
+            split_ev[i].record()
+            c()
+        split_ev[nc].record()
     torch.cuda.synchronize()
-    nc = len(graphs)
 
-    def step(ev=None):
-        for i, g in enumerate(graphs):
-            if ev is not None:
-                ev[i].record(stream)
-            g.replay()
-        if ev is not None:
-            ev[nc].record(stream)
+    def step():
+        step_graph.replay()
 
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
         step()
     torch.cuda.synchronize()
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nc + 1)] for _ in range(args.steps)]
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -629,14 +634,25 @@ def run_tpl(args):
     torch.cuda.synchronize()
     for k in range(args.steps):
         flush.zero_()
-        step(evs[k])
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    per = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(nc)] for k in range(args.steps)])
-    total_ms = max_over_ranks(float(per.sum()), dev, world)
+    step_ms = np.array([e0.elapsed_time(e1) for e0, e1 in evs])
+    total_ms = max_over_ranks(float(step_ms.sum()), dev, world)
     value = job_throughput(st.units, world, args.steps, total_ms)
+
+    # per-call times from the split graph (same inputs, L2 flushed before each step)
+    n_split = min(args.steps, 500)
+    per = np.zeros((n_split, nc))
+    for k in range(n_split):
+        flush.zero_()
+        split_graph.replay()
+        split_ev[nc].synchronize()
+        per[k] = [split_ev[i].elapsed_time(split_ev[i + 1]) for i in range(nc)]
 
     # roofline of the dominant call (per-unit bytes x units per launch / mean event time)
     mean_ms = per.mean(axis=0)
@@ -706,6 +722,7 @@ def run_tpl(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": config,
             "breakdown_ms": dict(zip(names, [float(x) for x in mean_ms])),
+            "breakdown_source": "graph of the step with event nodes between the calls",
             "step_alg_bytes": step_bytes,
             "step_gbs": step_bytes / (total_ms / args.steps * 1e-3) / 1e9,
             "roofline": roofline,

@@ -31,6 +31,7 @@ constexpr int kAPT = 8;      // atoms per thread (two groups of 4)
 constexpr int kChunk = kNT * kAPT;
 constexpr int kMom = 17;     // sum dx (3), sum dy (3), sum dx dy^T (9), sum |dx|^2, sum |dy|^2
 constexpr int kSlot = 20;    // floats per chunk partial (5 float4)
+constexpr int kQuadSolveMaxPairs = 8192;  // up to here four lanes share a pair's eigen-solve
 
 struct WsLayout {
     size_t part1, part2, state, lr64, counter, total;
@@ -182,6 +183,210 @@ __device__ __forceinline__ void adj_row(const double (&A)[4][4], double (&q)[4])
     q[1] = cofactor<R, 1>(A);
     q[2] = cofactor<R, 2>(A);
     q[3] = cofactor<R, 3>(A);
+}
+
+// FP32 estimate of the largest eigenpair of T(R) for R scaled to |R|_F = 1
+// (T, lambda and the adjugate are O(1); the eigenvectors do not depend on the
+// scale): Newton's method on the characteristic polynomial l^4 + c2 l^2 +
+// c1 l + c0 (c2 = -2, c1 = -8 det R, c0 = det T) from the upper bound E0/2
+// (e0s = E0 |R|^-1), then the column of adj(T - l I) with the largest
+// diagonal entry, scaled by it.  jb is that column.
+__device__ __forceinline__ void fp32_eigen_estimate(const float (&r)[9], float e0s, float& lam,
+                                                    float (&qf)[4], int& jb) {
+    const float t00 = r[0] + r[4] + r[8], t01 = r[5] - r[7], t02 = r[6] - r[2], t03 = r[1] - r[3];
+    const float t11 = r[0] - r[4] - r[8], t12 = r[1] + r[3], t13 = r[2] + r[6];
+    const float t22 = -r[0] + r[4] - r[8], t23 = r[5] + r[7], t33 = -r[0] - r[4] + r[8];
+    const float detR = r[0] * (r[4] * r[8] - r[5] * r[7]) - r[1] * (r[3] * r[8] - r[5] * r[6]) +
+                       r[2] * (r[3] * r[7] - r[4] * r[6]);
+    float m[16];
+    const float c0 = adjugate4f(t00, t01, t02, t03, t11, t12, t13, t22, t23, t33, m);
+    const float c2 = -2.f, c1 = -8.f * detR;
+    lam = fminf(2.f, 0.5f * e0s * (1.f + 1e-5f));
+    for (int it = 0; it < 24; ++it) {
+        const float l2 = lam * lam;
+        const float pv = (l2 + c2) * l2 + c1 * lam + c0;
+        const float dp = (4.f * l2 + 2.f * c2) * lam + c1;
+        if (!(fabsf(dp) > 0.f)) break;
+        const float step = __fdividef(pv, dp);
+        lam -= step;
+        if (fabsf(step) <= 1e-6f * fabsf(lam)) break;
+    }
+    adjugate4f(t00 - lam, t01, t02, t03, t11 - lam, t12, t13, t22 - lam, t23, t33 - lam, m);
+    jb = 0;
+    float best = m[0];
+    qf[0] = m[0]; qf[1] = m[4]; qf[2] = m[8]; qf[3] = m[12];
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+        if (fabsf(m[5 * k]) > fabsf(best)) {
+            best = m[5 * k];
+            jb = k;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) qf[i] = m[4 * i + k];
+        }
+    if (fabsf(best) > 0.f) {
+        const float ib = 1.f / fabsf(best);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) qf[i] *= ib;
+    } else {
+        qf[0] = 1.f; qf[1] = qf[2] = qf[3] = 0.f;
+        jb = 0;
+    }
+}
+
+__device__ __forceinline__ double pick4(int i, double a, double b, double c, double d) {
+    return i == 0 ? a : (i == 1 ? b : (i == 2 ? c : d));
+}
+
+// Quad form of the eigen-solve for small batches: four lanes per pair split
+// the FP64 refinement -- lane i forms row i of T q for the Rayleigh quotient,
+// cofactor (jb, i) of the adjugate row and row i of U -- so the dependent
+// FP64 chain is about a quarter as long; the FP32 estimate runs in all four
+// lanes alike.  No lane leaves early, so the quad shuffles see every lane.
+__global__ void __launch_bounds__(32) lrmsd_solve_quad_kernel(
+    const float* __restrict__ input, const float* __restrict__ target,
+    const int32_t* __restrict__ num_atoms, int P, int Nmax, const float* __restrict__ part1,
+    int nch_max, float* __restrict__ state, int* __restrict__ counter) {
+    const unsigned full = 0xffffffffu;
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sub = gid & 3, lane = threadIdx.x & 31;
+    const bool active = (gid >> 2) < P;
+    const int p = active ? (gid >> 2) : P - 1;
+    const int n = pair_atoms(num_atoms, p, Nmax);
+    if (active && sub == 0) counter[p] = 0;
+    float S[kSlot];
+#pragma unroll
+    for (int k = 0; k < kSlot; ++k) S[k] = 0.f;
+    const int nch = num_chunks(n);
+    for (int c = 0; c < nch; ++c) {
+        const float4* q = reinterpret_cast<const float4*>(part1 + ((size_t)p * nch_max + c) * kSlot);
+#pragma unroll
+        for (int k = 0; k < kSlot / 4; ++k) {
+            const float4 v = q[k];
+            S[4 * k] += v.x; S[4 * k + 1] += v.y; S[4 * k + 2] += v.z; S[4 * k + 3] += v.w;
+        }
+    }
+    float xc[3] = {0.f, 0.f, 0.f}, yc[3] = {0.f, 0.f, 0.f}, r[9], e0 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) r[k] = 0.f;
+    if (n > 0) {
+        const float* x = target + (size_t)p * Nmax * 3;
+        const float* y = input + (size_t)p * Nmax * 3;
+        const float inv = 1.f / n;
+        float mx[3], my[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            mx[a] = S[a] * inv;
+            my[a] = S[3 + a] * inv;
+            xc[a] = x[a] + mx[a];
+            yc[a] = y[a] + my[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r[3 * a + c] = S[6 + 3 * a + c] - n * mx[a] * my[c];
+        e0 = S[15] + S[16] - n * (mx[0] * mx[0] + mx[1] * mx[1] + mx[2] * mx[2] +
+                                  my[0] * my[0] + my[1] * my[1] + my[2] * my[2]);
+    }
+    float fro = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) fro = fmaf(r[k], r[k], fro);
+    const bool solve = n > 0 && fro > 0.f;  // else U = I (one atom, or all atoms coincide)
+    const float sc = solve ? rsqrtf(fro) : 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) r[k] *= sc;
+    float lam = 0.f, qf[4] = {1.f, 0.f, 0.f, 0.f};
+    int jb = 0;
+    if (solve) fp32_eigen_estimate(r, e0 * sc, lam, qf, jb);
+    // ---- FP64, every lane of the warp together from here on
+    double R[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[k] = (double)r[k];
+    double T[4][4];
+    T[0][0] = R[0] + R[4] + R[8];
+    T[0][1] = T[1][0] = R[5] - R[7];
+    T[0][2] = T[2][0] = R[6] - R[2];
+    T[0][3] = T[3][0] = R[1] - R[3];
+    T[1][1] = R[0] - R[4] - R[8];
+    T[1][2] = T[2][1] = R[1] + R[3];
+    T[1][3] = T[3][1] = R[2] + R[6];
+    T[2][2] = -R[0] + R[4] - R[8];
+    T[2][3] = T[3][2] = R[5] + R[7];
+    T[3][3] = -R[0] - R[4] + R[8];
+    const double qa0 = qf[0], qa1 = qf[1], qa2 = qf[2], qa3 = qf[3];
+    // Rayleigh quotient: lane sub forms (T q)_sub
+    double w = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w = fma(pick4(sub, T[0][k], T[1][k], T[2][k], T[3][k]), pick4(k, qa0, qa1, qa2, qa3), w);
+    double num = pick4(sub, qa0, qa1, qa2, qa3) * w;
+    num += __shfl_xor_sync(full, num, 1);
+    num += __shfl_xor_sync(full, num, 2);
+    const double den = qa0 * qa0 + qa1 * qa1 + qa2 * qa2 + qa3 * qa3;
+    double l64 = 0.0;
+    if (den > 0.0) {
+        const double rd = (double)(1.f / (float)den);
+        l64 = num * rd;
+        l64 = fma(rd, fma(-l64, den, num), l64);  // one correction of num / den
+    }
+    // cofactor (jb, sub) of A = T - lambda I: rows other than jb, columns other than sub
+#pragma unroll
+    for (int i = 0; i < 4; ++i) T[i][i] -= l64;
+    double M[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double row[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            // row k of the minor: A row (k < jb ? k : k + 1)
+            row[c] = k == 0 ? (jb == 0 ? T[1][c] : T[0][c]) : (k == 1 ? (jb <= 1 ? T[2][c] : T[1][c]) : (jb <= 2 ? T[3][c] : T[2][c]));
+        }
+        M[k][0] = sub == 0 ? row[1] : row[0];
+        M[k][1] = sub <= 1 ? row[2] : row[1];
+        M[k][2] = sub <= 2 ? row[3] : row[2];
+    }
+    double qc = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    if ((jb + sub) & 1) qc = -qc;
+    double nn = qc * qc;
+    nn += __shfl_xor_sync(full, nn, 1);
+    nn += __shfl_xor_sync(full, nn, 2);
+    double s = 0.0;
+    if (nn > 0.0) {
+        s = (double)rsqrtf((float)nn);
+        s = s * fma(-0.5 * nn * s, s, 1.5);  // Newton steps for 1/sqrt(nn)
+        s = s * fma(-0.5 * nn * s, s, 1.5);
+    }
+    const double qn = qc * s;
+    const int base = lane & ~3;
+    double q0 = __shfl_sync(full, qn, base), q1 = __shfl_sync(full, qn, base + 1);
+    double q2 = __shfl_sync(full, qn, base + 2), q3 = __shfl_sync(full, qn, base + 3);
+    if (!(solve && nn > 0.0)) {
+        q0 = 1.0; q1 = q2 = q3 = 0.0;
+    }
+    // row sub of U(q) (Section 4), formed in FP64 and rounded once
+    const double a = q0 * q0, b = q1 * q1, c = q2 * q2, d = q3 * q3;
+    double u0, u1, u2;
+    if (sub == 0) {
+        u0 = a + b - c - d; u1 = 2.0 * (q1 * q2 - q0 * q3); u2 = 2.0 * (q1 * q3 + q0 * q2);
+    } else if (sub == 1) {
+        u0 = 2.0 * (q1 * q2 + q0 * q3); u1 = a - b + c - d; u2 = 2.0 * (q2 * q3 - q0 * q1);
+    } else {
+        u0 = 2.0 * (q1 * q3 - q0 * q2); u1 = 2.0 * (q2 * q3 + q0 * q1); u2 = a - b - c + d;
+    }
+    if (active) {
+        float* st = state + 16 * (size_t)p;
+        if (sub < 3) {
+            st[3 * sub] = (float)u0;
+            st[3 * sub + 1] = (float)u1;
+            st[3 * sub + 2] = (float)u2;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                st[9 + k] = xc[k];
+                st[12 + k] = yc[k];
+            }
+            st[15] = 0.f;
+        }
+    }
 }
 
 // Eigen-solve of T (one thread per pair).  FP64 issue is scarce on this GPU
@@ -645,7 +850,11 @@ cudaError_t launch_lrmsd_forward(const float* input, const float* target, const 
     int* counter = reinterpret_cast<int*>(base + L.counter);
     const unsigned grid = (unsigned)P * (unsigned)L.nch;  // block = pair * nch + chunk
     lrmsd_moments_kernel<<<grid, kNT, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.nch);
-    lrmsd_solve_kernel<<<(P + 31) / 32, 32, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.nch,
+    if (P <= kQuadSolveMaxPairs)
+        lrmsd_solve_quad_kernel<<<(4 * P + 31) / 32, 32, 0, s>>>(input, target, num_atoms, P, Nmax, part1,
+                                                                L.nch, state, counter);
+    else
+        lrmsd_solve_kernel<<<(P + 31) / 32, 32, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.nch,
                                                     state, counter);
     lrmsd_residual_kernel<<<grid, kNT, 0, s>>>(input, target, num_atoms, P, Nmax, part2, state, lr64,
                                                counter, lrmsd, L.nch);

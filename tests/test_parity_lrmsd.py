@@ -150,3 +150,15 @@ def test_protein_shaped_pairs():
     l32, g32 = _run(x, y, n.astype(np.int32), w)
     assert np.abs(l32 - oracle.lrmsd_forward(x, y, n)).max() <= LRMSD_TOL
     assert rel_err(g32, oracle.lrmsd_backward(w, x, y, n)) <= GRAD_TOL
+
+
+def test_large_batch_takes_the_one_lane_solve():
+    """Above 8192 pairs the eigen-solve runs one lane per pair (below, four
+    lanes share a pair): both forms must agree with the oracle."""
+    rng = np.random.default_rng(9)
+    P = 8300
+    x, y, n = workloads.lrmsd_clouds(P, 3, 40, rng)
+    w = rng.normal(size=P).astype(np.float32)
+    l32, g32 = _run(x, y, n, w)
+    assert np.abs(l32 - oracle.lrmsd_forward(x, y, n)).max() <= LRMSD_TOL
+    assert rel_err(g32, oracle.lrmsd_backward(w, x, y, n)) <= GRAD_TOL
