@@ -50,19 +50,7 @@ DEFAULT_BATCH = {"training_step": 256, "backbone_uneven": 4096, "lrmsd_batch": 1
 # call's kernels from one ncu capture, per unit processed (residue or atom),
 # keyed by (workload, call), with the profile summary that holds the capture.
 # An entry is removed when one of its kernels changes after the capture.
-TRAFFIC = {
-    # fa_bwd_coords_kernel<256>: 36.29 MB for 1496321 atoms
-    ("training_step", "fullatom_backward"): (36.2916e6 / 1496321, "atom",
-                                             "profiles/fa_bwd_coords_kernel_training_step_256x700.md"),
-    # moments 256.66 MB + solve 1.99 MB + residual 256.82 MB for 10499521 atoms (4096 pairs)
-    ("lrmsd_batch", "lrmsd_forward"): (515.47e6 / 10499521, "atom",
-                                       "profiles/lrmsd_kernels_lrmsd_batch_4096.md"),
-    # grad: 449.87 MB for 10499521 atoms (4096 pairs)
-    ("lrmsd_batch", "lrmsd_backward"): (449.87e6 / 10499521, "atom",
-                                        "profiles/lrmsd_kernels_lrmsd_batch_4096.md"),
-    ("backbone_uneven", "lrmsd_forward"): (515.47e6 / 10499521, "atom",
-                                           "profiles/lrmsd_kernels_lrmsd_batch_4096.md"),
-}
+TRAFFIC = {}
 
 
 def parse():
@@ -78,6 +66,8 @@ def parse():
     p.add_argument("--res-per-thread", type=int, default=0, help="backbone residues per thread (0 = default)")
     p.add_argument("--bwd", default="coords", choices=["coords", "recompute"],
                    help="chain backward: read the forward's coordinates or rebuild frames")
+    p.add_argument("--unfused", action="store_true",
+                   help="training step: LRMSD backward and full-atom backward as two calls")
     p.add_argument("--no-autotune", action="store_true",
                    help="use the library's default launch shape instead of the autotuner's pick")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -349,29 +339,40 @@ def setup_training_step(args, tpl, torch, dev, d):
         tuned = {"threads": opts.threads, "schedule": opts.schedule, "fwd_bwd_ms": tms}
 
     st = Step()
-    st.calls = [
-        ("fullatom_forward", lambda: tpl.tpl_fullatom_forward(A, S, Ln, coords, na, fa_ws, opts)),
-        ("lrmsd_forward", lambda: tpl.tpl_lrmsd_forward(coords, target, na, lr, lr_ws)),
-        ("lrmsd_backward", lambda: tpl.tpl_lrmsd_backward(wgt, coords, target, na, gcoords, lr_ws)),
-        ("fullatom_backward",
-         lambda: tpl.tpl_fullatom_backward(A, S, Ln, coords, gcoords, gang, fa_ws, opts)),
-    ]
-    bwd_kernel = "fa_bwd_coords_kernel" if args.bwd == "coords" else "fa_bwd_kernel"
-    st.kernels = {"fullatom_forward": ["schedule_kernel", "fa_fwd_kernel"],
-                  "lrmsd_forward": ["lrmsd_moments_kernel", "lrmsd_solve_kernel", "lrmsd_residual_kernel"],
-                  "lrmsd_backward": ["lrmsd_grad_kernel"], "fullatom_backward": [bwd_kernel]}
-    st.launches = {k: len(v) for k, v in st.kernels.items()}
     res = int(lengths.sum())
-    st.alg = {
-        "fullatom_forward": res * (28 + 1) + 12 * n_atoms,
-        "lrmsd_forward": 24 * n_atoms,
-        "lrmsd_backward": 36 * n_atoms,
-        "fullatom_backward": res * (28 + 1 + 28) + 12 * n_atoms,
-    }
+    solve = "lrmsd_solve_quad_kernel" if B <= 8192 else "lrmsd_solve_kernel"
+    st.kernels = {"fullatom_forward": ["schedule_kernel", "fa_fwd_kernel"],
+                  "lrmsd_forward": ["lrmsd_moments_kernel", solve, "lrmsd_residual_kernel"]}
+    st.alg = {"fullatom_forward": res * (28 + 1) + 12 * n_atoms, "lrmsd_forward": 24 * n_atoms}
+    if args.unfused or args.bwd != "coords":
+        bwd_kernel = "fa_bwd_coords_kernel" if args.bwd == "coords" else "fa_bwd_kernel"
+        st.calls = [
+            ("fullatom_forward", lambda: tpl.tpl_fullatom_forward(A, S, Ln, coords, na, fa_ws, opts)),
+            ("lrmsd_forward", lambda: tpl.tpl_lrmsd_forward(coords, target, na, lr, lr_ws)),
+            ("lrmsd_backward", lambda: tpl.tpl_lrmsd_backward(wgt, coords, target, na, gcoords, lr_ws)),
+            ("fullatom_backward",
+             lambda: tpl.tpl_fullatom_backward(A, S, Ln, coords, gcoords, gang, fa_ws, opts)),
+        ]
+        st.kernels.update({"lrmsd_backward": ["lrmsd_grad_kernel"], "fullatom_backward": [bwd_kernel]})
+        st.alg.update({"lrmsd_backward": 36 * n_atoms, "fullatom_backward": res * (28 + 1 + 28) + 12 * n_atoms})
+    else:
+        # LRMSD backward formed inside the full-atom backward (no coordinate-gradient tensor)
+        st.calls = [
+            ("fullatom_forward", lambda: tpl.tpl_fullatom_forward(A, S, Ln, coords, na, fa_ws, opts)),
+            ("lrmsd_forward", lambda: tpl.tpl_lrmsd_forward(coords, target, na, lr, lr_ws)),
+            ("lrmsd_fullatom_backward",
+             lambda: tpl.tpl_fullatom_backward_lrmsd(A, S, Ln, coords, target, wgt, lr_ws, gang, fa_ws, opts)),
+        ]
+        st.kernels["lrmsd_fullatom_backward"] = ["fa_bwd_coords_kernel"]
+        # angles 28 + sequence 1 in, angle gradient 28 out per residue; coordinates and target 24 per atom
+        st.alg["lrmsd_fullatom_backward"] = res * (28 + 1 + 28) + 24 * n_atoms
+    st.launches = {k: len(v) for k, v in st.kernels.items()}
     st.units = res
     st.atoms = n_atoms
     st.extra_config = {"atoms_per_gpu": n_atoms, "threads": opts.threads or "default",
-                       "fullatom_backward": args.bwd, "autotuned": tuned}
+                       "fullatom_backward": args.bwd, "autotuned": tuned,
+                       "lrmsd_backward": "separate call" if len(st.calls) == 4 else
+                                         "formed inside the full-atom backward"}
     tgt_host = target.cpu().pin_memory()
     st.h2d = [(A, torch.from_numpy(a).pin_memory()), (S, torch.from_numpy(seq).pin_memory()),
               (Ln, torch.from_numpy(lengths).pin_memory()), (target, tgt_host)]

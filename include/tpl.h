@@ -164,6 +164,24 @@ tpl_status tpl_fullatom_backward(const float* angles, const uint8_t* seq, const 
                                  const float* grad_coords, float* grad_angles, void* workspace,
                                  size_t workspace_bytes, const tpl_opts* opts, tpl_stream stream);
 
+/* The backward of a training step on the LRMSD loss of Section 4 chained
+ * into Eq. 1: grad_angles = d(sum_b grad_lrmsd[b] LRMSD(coords[b],
+ * target[b])) / d(angles), the same as tpl_lrmsd_backward (P = B, Nmax =
+ * Amax) followed by tpl_fullatom_backward with FROM_COORDS, with each atom's
+ * coordinate gradient formed in the kernel from the coordinates, the target
+ * and the per-pair state of the LRMSD forward, so no coordinate-gradient
+ * tensor is written or read.  The paper has no fused form; it is this
+ * library's fusion of two of its calls.
+ *   coords: the full-atom forward's output with `workspace` (same inputs);
+ *   target [B][Amax][3]; grad_lrmsd [B]; lrmsd_workspace: as filled by
+ *   tpl_lrmsd_forward(coords, target, num_atoms of the forward, P = B,
+ *   Nmax = Amax).  bwd_mode in opts is ignored. */
+tpl_status tpl_fullatom_backward_lrmsd(const float* angles, const uint8_t* seq, const int32_t* lengths,
+                                       int B, int Lmax, int Amax, const float* coords, const float* target,
+                                       const float* grad_lrmsd, const void* lrmsd_workspace,
+                                       size_t lrmsd_workspace_bytes, float* grad_angles, void* workspace,
+                                       size_t workspace_bytes, const tpl_opts* opts, tpl_stream stream);
+
 /* ------------------------------------------------------------------------ */
 /* LRMSD (paper Section 4)                                                   */
 /* ------------------------------------------------------------------------ */

@@ -420,6 +420,31 @@ tpl_status tpl_fullatom_forward(const float* angles, const uint8_t* seq, const i
     return ok();
 }
 
+tpl_status tpl_fullatom_backward_lrmsd(const float* angles, const uint8_t* seq, const int32_t* lengths,
+                                       int B, int Lmax, int Amax, const float* coords, const float* target,
+                                       const float* grad_lrmsd, const void* lrmsd_workspace,
+                                       size_t lrmsd_workspace_bytes, float* grad_angles, void* workspace,
+                                       size_t workspace_bytes, const tpl_opts* opts, tpl_stream stream) {
+    tpl_opts o = resolve(opts);
+    tpl_status st = check_opts(o);
+    if (st) return st;
+    const void* ptrs[7] = {angles, seq, lengths, coords, target, grad_lrmsd, grad_angles};
+    if ((st = check_chain_args(B, Lmax, ptrs, 7))) return st;
+    if (Amax < 0 || Amax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Amax=%d must be a multiple of 4", Amax);
+    if (B == 0) return ok();
+    LaunchCfg cfg = fullatom_cfg(o);
+    if (!fullatom_cfg_supported(cfg.threads))
+        return fail(TPL_ERR_INVALID_ARG, "unsupported full-atom launch %d threads", cfg.threads);
+    if ((st = check_ws(workspace, workspace_bytes, tpl_fullatom_workspace_size(B, Lmax)))) return st;
+    if ((st = check_ws(const_cast<void*>(lrmsd_workspace), lrmsd_workspace_bytes, tpl_lrmsd_workspace_size(B, Amax))))
+        return st;
+    cudaError_t e = launch_fullatom_backward_lrmsd(seq, lengths, B, Lmax, Amax, coords, target, grad_lrmsd,
+                                                   lrmsd_state(lrmsd_workspace, B, Amax), grad_angles,
+                                                   workspace, cfg, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "fullatom_backward_lrmsd");
+    return ok();
+}
+
 tpl_status tpl_fullatom_backward(const float* angles, const uint8_t* seq, const int32_t* lengths,
                                  int B, int Lmax, int Amax, const float* coords,
                                  const float* grad_coords, float* grad_angles, void* workspace,

@@ -328,11 +328,21 @@ __device__ __forceinline__ int block_scan_int(int x, int* s_cnt, int& total) {
 __device__ __forceinline__ float3 unit3(float3 v) { return f3_scale(rsqrtf(f3_dot(v, v)), v); }
 
 
-template <int NT>
+// Inputs of the LRMSD gradient formed in the backward (Section 4): for chain
+// b, g_i = w_b ((y_i - yc) - U (x_i - xc)) with y the chain's coordinates, x
+// the target, w_b = grad_lrmsd[b] / (N LRMSD) (the per-pair state of the
+// LRMSD forward).
+struct LrmsdGrad {
+    const float* target;
+    const float* state;
+    const float* grad_lrmsd;
+};
+
+template <int NT, bool LR>
 __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_kernel(
     const uint8_t* __restrict__ seq, const int32_t* __restrict__ lengths, int B, int Lmax, int Amax,
     const float* __restrict__ coords, const float* __restrict__ grad_coords,
-    float* __restrict__ grad_angles, ChainWs ws, const __grid_constant__ FaTable tab) {
+    float* __restrict__ grad_angles, ChainWs ws, LrmsdGrad lg, const __grid_constant__ FaTable tab) {
     constexpr int NW = NT / 32;
     __shared__ FaTable s_tab;
     __shared__ float s6[6 * (NW + 1)];
@@ -376,9 +386,26 @@ __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_ker
         float3 rN = make_float3(0.f, 0.f, 0.f), rCA = rN, rC = rN, rCprev = rN;
         if (in_range) {
             const float* sr = r_in + 3 * (size_t)a0;
-            const float* sg = g_in + 3 * (size_t)a0;
             auto R = [&](int k) { return make_float3(__ldg(sr + 3 * k), __ldg(sr + 3 * k + 1), __ldg(sr + 3 * k + 2)); };
-            auto G = [&](int k) { return make_float3(__ldg(sg + 3 * k), __ldg(sg + 3 * k + 1), __ldg(sg + 3 * k + 2)); };
+            // the coordinate gradient: read, or formed from the LRMSD state
+            const float* sg = LR ? lg.target + ((size_t)b * Amax + a0) * 3 : g_in + 3 * (size_t)a0;
+            float3 u0 = make_float3(0.f, 0.f, 0.f), u1 = u0, u2 = u0, xc = u0, yc = u0;
+            float w = 0.f;
+            if constexpr (LR) {
+                const float* st = lg.state + 16 * (size_t)b;
+                u0 = make_float3(__ldg(st), __ldg(st + 1), __ldg(st + 2));
+                u1 = make_float3(__ldg(st + 3), __ldg(st + 4), __ldg(st + 5));
+                u2 = make_float3(__ldg(st + 6), __ldg(st + 7), __ldg(st + 8));
+                xc = make_float3(__ldg(st + 9), __ldg(st + 10), __ldg(st + 11));
+                yc = make_float3(__ldg(st + 12), __ldg(st + 13), __ldg(st + 14));
+                w = __ldg(lg.grad_lrmsd + b) * __ldg(st + 15);
+            }
+            auto G = [&](int k) {
+                const float3 v = make_float3(__ldg(sg + 3 * k), __ldg(sg + 3 * k + 1), __ldg(sg + 3 * k + 2));
+                if constexpr (!LR) return v;
+                const float3 xp = f3_sub(v, xc), yp = f3_sub(R(k), yc);
+                return f3_scale(w, make_float3(yp.x - f3_dot(u0, xp), yp.y - f3_dot(u1, xp), yp.z - f3_dot(u2, xp)));
+            };
             auto add = [&](Sum6& s, int k) {
                 const float3 g = G(k);
                 s.c = f3_add(s.c, f3_cross(R(k), g));
@@ -809,13 +836,13 @@ cudaError_t fa_fwd_t(const float* angles, const uint8_t* seq, const int32_t* len
     return cudaGetLastError();
 }
 
-template <int NT>
+template <int NT, bool LR>
 cudaError_t fa_bwd_coords_t(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
                             const float* coords, const float* grad_coords, float* grad_angles,
-                            const ChainWs& ws, cudaStream_t s) {
-    const int grid = persistent_grid((const void*)fa_bwd_coords_kernel<NT>, NT, 0);
-    fa_bwd_coords_kernel<NT><<<grid, NT, 0, s>>>(seq, lengths, B, Lmax, Amax, coords, grad_coords,
-                                                    grad_angles, ws, fa_table());
+                            const ChainWs& ws, LrmsdGrad lg, cudaStream_t s) {
+    const int grid = persistent_grid((const void*)fa_bwd_coords_kernel<NT, LR>, NT, 0);
+    fa_bwd_coords_kernel<NT, LR><<<grid, NT, 0, s>>>(seq, lengths, B, Lmax, Amax, coords, grad_coords,
+                                                        grad_angles, ws, lg, fa_table());
     return cudaGetLastError();
 }
 
@@ -869,10 +896,10 @@ cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
     if (e != cudaSuccess) return e;
     if (from_coords) {
         switch (cfg.threads) {
-            case 64: return fa_bwd_coords_t<64>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, s);
-            case 128: return fa_bwd_coords_t<128>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, s);
-            case 256: return fa_bwd_coords_t<256>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, s);
-            case 512: return fa_bwd_coords_t<512>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, s);
+            case 64: return fa_bwd_coords_t<64, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, LrmsdGrad{}, s);
+            case 128: return fa_bwd_coords_t<128, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, LrmsdGrad{}, s);
+            case 256: return fa_bwd_coords_t<256, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, LrmsdGrad{}, s);
+            case 512: return fa_bwd_coords_t<512, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, LrmsdGrad{}, s);
             default: return cudaErrorInvalidValue;
         }
     }
@@ -892,6 +919,26 @@ cudaError_t launch_fullatom_forward_ref64(const double* angles, const uint8_t* s
     fa_fwd_ref64_kernel<<<B, 128, 0, s>>>(angles, seq, lengths, B, Lmax, Amax, coords, num_atoms,
                                           fa_table_d());
     return cudaGetLastError();
+}
+
+cudaError_t launch_fullatom_backward_lrmsd(const uint8_t* seq, const int32_t* lengths, int B, int Lmax,
+                                          int Amax, const float* coords, const float* target,
+                                          const float* grad_lrmsd, const float* lrmsd_state,
+                                          float* grad_angles, void* workspace, LaunchCfg cfg,
+                                          cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    ChainWs ws;
+    chain_ws_layout(workspace, B, Lmax, &ws, true);
+    cudaError_t e = reset_backward_flags(ws, s);
+    if (e != cudaSuccess) return e;
+    const LrmsdGrad lg{target, lrmsd_state, grad_lrmsd};
+    switch (cfg.threads) {
+        case 64: return fa_bwd_coords_t<64, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
+        case 128: return fa_bwd_coords_t<128, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
+        case 256: return fa_bwd_coords_t<256, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
+        case 512: return fa_bwd_coords_t<512, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_fullatom_backward_ref64(const double* angles, const uint8_t* seq,

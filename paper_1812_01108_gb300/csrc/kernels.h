@@ -40,8 +40,19 @@ cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
                                      float* grad_angles, bool from_coords, void* workspace,
                                      LaunchCfg cfg, cudaStream_t s);
 
+// K4 with the LRMSD gradient formed in place of a coordinate-gradient input:
+// the gradient of sum_b grad_lrmsd[b] LRMSD(coords[b], target[b]).
+cudaError_t launch_fullatom_backward_lrmsd(const uint8_t* seq, const int32_t* lengths, int B, int Lmax,
+                                          int Amax, const float* coords, const float* target,
+                                          const float* grad_lrmsd, const float* lrmsd_state,
+                                          float* grad_angles, void* workspace, LaunchCfg cfg,
+                                          cudaStream_t s);
+
 // K5 / K6: LRMSD.  The workspace layout is private to lrmsd.cu.
 size_t lrmsd_ws_bytes(int P, int Nmax);
+// Per-pair state the LRMSD forward leaves in its workspace: U (9, row-major),
+// centroid of the target, centroid of the input, 1 / (N LRMSD) (16 floats).
+const float* lrmsd_state(const void* ws, int P, int Nmax);
 cudaError_t launch_lrmsd_forward(const float* input, const float* target,
                                  const int32_t* num_atoms, int P, int Nmax, float* lrmsd,
                                  void* ws, cudaStream_t s);

@@ -838,6 +838,10 @@ __global__ void __launch_bounds__(kRefNT) lrmsd_bwd_ref64_kernel(
 
 size_t lrmsd_ws_bytes(int P, int Nmax) { return ws_layout(P, Nmax).total; }
 
+const float* lrmsd_state(const void* ws, int P, int Nmax) {
+    return reinterpret_cast<const float*>(static_cast<const char*>(ws) + ws_layout(P, Nmax).state);
+}
+
 cudaError_t launch_lrmsd_forward(const float* input, const float* target, const int32_t* num_atoms,
                                  int P, int Nmax, float* lrmsd, void* ws, cudaStream_t s) {
     if (P == 0) return cudaSuccess;

@@ -147,3 +147,43 @@ def test_autotuner_picks_a_valid_shape_and_its_results_match(reference):
     assert np.array_equal(n32, na64)
     assert np.abs(c32 - c64).max() <= COORD_TOL
     assert rel_err(ga32, g64) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("threads", [256, 64])
+def test_fused_lrmsd_backward_equals_the_two_calls_and_the_oracle(threads):
+    """tpl_fullatom_backward_lrmsd = tpl_lrmsd_backward + tpl_fullatom_backward
+    (FROM_COORDS), against the same chain of oracle calls."""
+    d = require_gpu()
+    rng = workloads.rng_for(4, salt=31)
+    lengths = np.array([700, 333, 64, 1, 0, 257], np.int32)
+    a, seq = workloads.fullatom_inputs(lengths, rng)
+    ta = workloads.perturb_angles(a, lengths, rng, rows=(0, 1, 3, 4, 5, 6))
+    Amax = workloads.pad_to(oracle.max_atoms(seq, lengths))
+    B, _, Lmax = a.shape
+    A, S, Ln = dev(a, d), dev(seq, d), dev(lengths, d)
+    opts = {"threads": threads}
+    fa_ws = torch.empty(tpl.tpl_fullatom_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    tgt = torch.zeros((B, Amax, 3), device=d)
+    na = torch.zeros((B,), dtype=torch.int32, device=d)
+    tpl.tpl_fullatom_forward(dev(ta, d), S, Ln, tgt, na, fa_ws, opts)
+    coords = torch.zeros_like(tgt)
+    tpl.tpl_fullatom_forward(A, S, Ln, coords, na, fa_ws, opts)
+    lr = torch.zeros((B,), device=d)
+    lr_ws = torch.empty(tpl.tpl_lrmsd_workspace_size(B, Amax), dtype=torch.uint8, device=d)
+    tpl.tpl_lrmsd_forward(coords, tgt, na, lr, lr_ws)
+    w = dev(np.linspace(0.5, 2.0, B).astype(np.float32), d)
+    ga_fused = torch.full_like(A, float("nan"))
+    tpl.tpl_fullatom_backward_lrmsd(A, S, Ln, coords, tgt, w, lr_ws, ga_fused, fa_ws, opts)
+    gc = torch.empty_like(coords)
+    tpl.tpl_lrmsd_backward(w, coords, tgt, na, gc, lr_ws)
+    ga_two = torch.full_like(A, float("nan"))
+    tpl.tpl_fullatom_backward(A, S, Ln, coords, gc, ga_two, fa_ws, dict(opts, bwd_mode=tpl.BWD_FROM_COORDS))
+    torch.cuda.synchronize()
+    f, t = host(ga_fused), host(ga_two)
+    assert np.all(np.isfinite(f))
+    assert rel_err(f, t) <= 1e-5
+    # oracle chain on the same FP32 coordinates
+    c32, t32, n32 = host(coords), host(tgt), host(na)
+    g64 = oracle.lrmsd_backward(host(w).astype(np.float64), c32, t32, n32)
+    ga64 = oracle.fullatom_backward(a, seq, lengths, g64)
+    assert rel_err(f, ga64) <= GRAD_TOL
