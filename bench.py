@@ -434,24 +434,38 @@ def setup_backbone_uneven(args, tpl, torch, dev, d):
     res = int(lengths.sum())
 
     st = Step()
-    st.calls = [
-        ("backbone_forward", lambda: tpl.tpl_backbone_forward(A, Ln, coords, bb_ws, opts)),
-        ("lrmsd_forward", lambda: tpl.tpl_lrmsd_forward(coords, target, na, lr, lr_ws)),
-        ("lrmsd_backward", lambda: tpl.tpl_lrmsd_backward(wgt, coords, target, na, gcoords, lr_ws)),
-        ("backbone_backward",
-         lambda: tpl.tpl_backbone_backward(A, Ln, coords, gcoords, gang, bb_ws, opts)),
-    ]
+    solve = "lrmsd_solve_quad_kernel" if B <= 8192 else "lrmsd_solve_kernel"
     st.kernels = {"backbone_forward": ["schedule_kernel", "bb_fwd_kernel"],
-                  "lrmsd_forward": ["lrmsd_moments_kernel", "lrmsd_solve_kernel", "lrmsd_residual_kernel"],
-                  "lrmsd_backward": ["lrmsd_grad_kernel"], "backbone_backward": ["bb_bwd_kernel"]}
+                  "lrmsd_forward": ["lrmsd_moments_kernel", solve, "lrmsd_residual_kernel"]}
+    st.alg = {"backbone_forward": 48 * res, "lrmsd_forward": 24 * n_atoms}
+    if args.unfused or args.bwd != "coords":
+        st.calls = [
+            ("backbone_forward", lambda: tpl.tpl_backbone_forward(A, Ln, coords, bb_ws, opts)),
+            ("lrmsd_forward", lambda: tpl.tpl_lrmsd_forward(coords, target, na, lr, lr_ws)),
+            ("lrmsd_backward", lambda: tpl.tpl_lrmsd_backward(wgt, coords, target, na, gcoords, lr_ws)),
+            ("backbone_backward",
+             lambda: tpl.tpl_backbone_backward(A, Ln, coords, gcoords, gang, bb_ws, opts)),
+        ]
+        st.kernels.update({"lrmsd_backward": ["lrmsd_grad_kernel"], "backbone_backward": ["bb_bwd_kernel"]})
+        st.alg.update({"lrmsd_backward": 36 * n_atoms, "backbone_backward": 60 * res})
+    else:
+        st.calls = [
+            ("backbone_forward", lambda: tpl.tpl_backbone_forward(A, Ln, coords, bb_ws, opts)),
+            ("lrmsd_forward", lambda: tpl.tpl_lrmsd_forward(coords, target, na, lr, lr_ws)),
+            ("lrmsd_backbone_backward",
+             lambda: tpl.tpl_backbone_backward_lrmsd(A, Ln, coords, target, wgt, lr_ws, gang, bb_ws, opts)),
+        ]
+        st.kernels["lrmsd_backbone_backward"] = ["bb_bwd_kernel"]
+        # angles 12 in, gradient 12 out per residue; coordinates and target 24 per atom
+        st.alg["lrmsd_backbone_backward"] = 24 * res + 24 * n_atoms
     st.launches = {k: len(v) for k, v in st.kernels.items()}
-    st.alg = {"backbone_forward": 48 * res, "lrmsd_forward": 24 * n_atoms,
-              "lrmsd_backward": 36 * n_atoms, "backbone_backward": 60 * res}
     st.units = res
     st.atoms = n_atoms
     st.extra_config = {"atoms_per_gpu": n_atoms, "threads": opts.threads or "default",
                        "res_per_thread": opts.res_per_thread or "default", "backbone_backward": args.bwd,
-                       "autotuned": tuned}
+                       "autotuned": tuned,
+                       "lrmsd_backward": "separate call" if len(st.calls) == 4 else
+                                         "formed inside the backbone backward"}
     st.h2d = [(A, torch.from_numpy(a).pin_memory()), (Ln, torch.from_numpy(lengths).pin_memory()),
               (na, torch.from_numpy(na_host).pin_memory()), (target, target.cpu().pin_memory())]
     st.d2h = (torch.empty((B,), dtype=torch.float32).pin_memory(), lr)

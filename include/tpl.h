@@ -164,6 +164,20 @@ tpl_status tpl_fullatom_backward(const float* angles, const uint8_t* seq, const 
                                  const float* grad_coords, float* grad_angles, void* workspace,
                                  size_t workspace_bytes, const tpl_opts* opts, tpl_stream stream);
 
+/* Backbone form of tpl_fullatom_backward_lrmsd below (Eq. 2 instead of
+ * Eq. 1): grad_angles = d(sum_b grad_lrmsd[b] LRMSD(coords[b], target[b])) /
+ * d(angles), equal to tpl_lrmsd_backward (P = B, Nmax = 3 Lmax, num_atoms =
+ * 3 lengths) followed by tpl_backbone_backward with FROM_COORDS.
+ *   coords: the backbone forward's output with `workspace`; target
+ *   [B][3 Lmax][3]; lrmsd_workspace: as filled by tpl_lrmsd_forward on
+ *   (coords, target, 3 lengths, P = B, Nmax = 3 Lmax).  The paper has no
+ *   fused form. */
+tpl_status tpl_backbone_backward_lrmsd(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                       const float* coords, const float* target, const float* grad_lrmsd,
+                                       const void* lrmsd_workspace, size_t lrmsd_workspace_bytes,
+                                       float* grad_angles, void* workspace, size_t workspace_bytes,
+                                       const tpl_opts* opts, tpl_stream stream);
+
 /* The backward of a training step on the LRMSD loss of Section 4 chained
  * into Eq. 1: grad_angles = d(sum_b grad_lrmsd[b] LRMSD(coords[b],
  * target[b])) / d(angles), the same as tpl_lrmsd_backward (P = B, Nmax =

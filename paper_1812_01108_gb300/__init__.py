@@ -30,7 +30,7 @@ __all__ = [
     "tpl_backbone_backward_ref64", "tpl_fullatom_forward_ref64", "tpl_fullatom_backward_ref64",
     "tpl_lrmsd_forward_ref64", "tpl_lrmsd_backward_ref64", "tpl_get_status",
     "tpl_selftest_wait_timeout", "tpl_backbone_autotune", "tpl_fullatom_autotune",
-    "tpl_fullatom_backward_lrmsd", "backbone",
+    "tpl_fullatom_backward_lrmsd", "tpl_backbone_backward_lrmsd", "backbone",
     "fullatom", "lrmsd", "residue_table", "fullatom_max_atoms", "BWD_RECOMPUTE",
     "BWD_FROM_COORDS", "SCHED_LONGEST_FIRST", "SCHED_BATCH_ORDER", "SCHED_PACKED",
 ]
@@ -88,6 +88,7 @@ def load_library():
             "tpl_fullatom_forward": ([P, P, P, I, I, I, P, P, P, Z, O, P], I),
             "tpl_fullatom_backward": ([P, P, P, I, I, I, P, P, P, P, Z, O, P], I),
             "tpl_fullatom_backward_lrmsd": ([P, P, P, I, I, I, P, P, P, P, Z, P, P, Z, O, P], I),
+            "tpl_backbone_backward_lrmsd": ([P, P, I, I, P, P, P, P, Z, P, P, Z, O, P], I),
             "tpl_lrmsd_forward": ([P, P, P, I, I, P, P, Z, P], I),
             "tpl_lrmsd_backward": ([P, P, P, P, I, I, P, P, Z, P], I),
             "tpl_lrmsd_forward_noalloc": ([P, P, P, I, I, P, P], I),
@@ -237,6 +238,20 @@ def tpl_fullatom_autotune(angles, seq, lengths, coords, num_atoms, grad_coords, 
         workspace.numel() * workspace.element_size(), int(bwd_mode), ctypes.byref(best),
         ctypes.byref(ms), _stream(angles, stream)))
     return best, ms.value
+
+
+def tpl_backbone_backward_lrmsd(angles, lengths, coords, target, grad_lrmsd, lrmsd_workspace,
+                                grad_angles, workspace, opts=None, stream=None):
+    """Backward of sum_b grad_lrmsd[b] * LRMSD(coords[b], target[b]) to the backbone
+    angles in one call."""
+    B, _, Lmax = angles.shape
+    _check("tpl_backbone_backward_lrmsd", load_library().tpl_backbone_backward_lrmsd(
+        _ptr(_cuda(angles, torch.float32, "angles")), _ptr(_cuda(lengths, torch.int32, "lengths")),
+        B, Lmax, _ptr(_cuda(coords, torch.float32, "coords")), _ptr(_cuda(target, torch.float32, "target")),
+        _ptr(_cuda(grad_lrmsd, torch.float32, "grad_lrmsd")), _ptr(lrmsd_workspace),
+        lrmsd_workspace.numel() * lrmsd_workspace.element_size(),
+        _ptr(_cuda(grad_angles, torch.float32, "grad_angles")), _ptr(workspace),
+        workspace.numel() * workspace.element_size(), _opts(opts), _stream(angles, stream)))
 
 
 def tpl_fullatom_backward_lrmsd(angles, seq, lengths, coords, target, grad_lrmsd, lrmsd_workspace,

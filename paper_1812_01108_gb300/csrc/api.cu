@@ -420,6 +420,32 @@ tpl_status tpl_fullatom_forward(const float* angles, const uint8_t* seq, const i
     return ok();
 }
 
+tpl_status tpl_backbone_backward_lrmsd(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                       const float* coords, const float* target, const float* grad_lrmsd,
+                                       const void* lrmsd_workspace, size_t lrmsd_workspace_bytes,
+                                       float* grad_angles, void* workspace, size_t workspace_bytes,
+                                       const tpl_opts* opts, tpl_stream stream) {
+    tpl_opts o = resolve(opts);
+    tpl_status st = check_opts(o);
+    if (st) return st;
+    const void* ptrs[6] = {angles, lengths, coords, target, grad_lrmsd, grad_angles};
+    if ((st = check_chain_args(B, Lmax, ptrs, 6))) return st;
+    if (B == 0) return ok();
+    LaunchCfg cfg = backbone_cfg(o);
+    if (!backbone_cfg_supported(cfg.threads, cfg.res_per_thread) ||
+        (cfg.threads == 512 && cfg.res_per_thread == 4))
+        return fail(TPL_ERR_INVALID_ARG, "unsupported backbone launch %d x %d", cfg.threads, cfg.res_per_thread);
+    if ((st = check_ws(workspace, workspace_bytes, tpl_backbone_workspace_size(B, Lmax)))) return st;
+    if ((st = check_ws(const_cast<void*>(lrmsd_workspace), lrmsd_workspace_bytes,
+                       tpl_lrmsd_workspace_size(B, 3 * Lmax))))
+        return st;
+    cudaError_t e = launch_backbone_backward_lrmsd(angles, lengths, B, Lmax, coords, target, grad_lrmsd,
+                                                   lrmsd_state(lrmsd_workspace, B, 3 * Lmax), grad_angles,
+                                                   workspace, cfg, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "backbone_backward_lrmsd");
+    return ok();
+}
+
 tpl_status tpl_fullatom_backward_lrmsd(const float* angles, const uint8_t* seq, const int32_t* lengths,
                                        int B, int Lmax, int Amax, const float* coords, const float* target,
                                        const float* grad_lrmsd, const void* lrmsd_workspace,

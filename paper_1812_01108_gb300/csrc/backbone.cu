@@ -280,13 +280,16 @@ __device__ __forceinline__ bool ws_matches(const ChainWs& ws, int tile, int B, i
 // from the angles and the forward's tile-start frames (RECOMPUTE) or read from
 // the forward's coordinates (FROM_COORDS).
 // ---------------------------------------------------------------------------
-template <int NT, int K, bool FROM_COORDS>
+// LR (with FROM_COORDS): the coordinate gradient is the LRMSD gradient,
+// formed from the coordinates, the target and the LRMSD state.
+template <int NT, int K, bool FROM_COORDS, bool LR>
 __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ angles,
                                                     const int32_t* __restrict__ lengths, int B,
                                                     int Lmax, const float* __restrict__ coords,
                                                     const float* __restrict__ grad_coords,
                                                     float* __restrict__ grad_angles, ChainWs ws,
-                                                    BackboneConst bc) {
+                                                    LrmsdGrad lg, BackboneConst bc) {
+    static_assert(FROM_COORDS || !LR, "the LRMSD gradient needs the coordinates");
     constexpr int NW = NT / 32;
     constexpr int TILE = NT * K;
     __shared__ RigidS s_rig[NW + 1];
@@ -336,7 +339,29 @@ __global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ an
         float* ga = grad_angles + (size_t)b * 3 * Lmax;
 
         float g[9 * K];
-        load_atoms<K>(g_in + 9 * (size_t)min(j0, Lmax - K), j0 < Lmax, g);
+        if constexpr (LR) {
+            float x[9 * K], y[9 * K];
+            const size_t o = (size_t)b * 9 * Lmax + 9 * (size_t)min(j0, Lmax - K);
+            load_atoms<K>(lg.target + o, j0 < Lmax, x);
+            load_atoms<K>(coords + o, j0 < Lmax, y);
+            const float* st = lg.state + 16 * (size_t)b;
+            const float3 u0 = make_float3(__ldg(st), __ldg(st + 1), __ldg(st + 2));
+            const float3 u1 = make_float3(__ldg(st + 3), __ldg(st + 4), __ldg(st + 5));
+            const float3 u2 = make_float3(__ldg(st + 6), __ldg(st + 7), __ldg(st + 8));
+            const float3 xc = make_float3(__ldg(st + 9), __ldg(st + 10), __ldg(st + 11));
+            const float3 yc = make_float3(__ldg(st + 12), __ldg(st + 13), __ldg(st + 14));
+            const float w = __ldg(lg.grad_lrmsd + b) * __ldg(st + 15);
+#pragma unroll
+            for (int q = 0; q < 3 * K; ++q) {
+                const float3 xp = f3_sub(make_float3(x[3 * q], x[3 * q + 1], x[3 * q + 2]), xc);
+                const float3 yp = f3_sub(make_float3(y[3 * q], y[3 * q + 1], y[3 * q + 2]), yc);
+                g[3 * q] = w * (yp.x - f3_dot(u0, xp));
+                g[3 * q + 1] = w * (yp.y - f3_dot(u1, xp));
+                g[3 * q + 2] = w * (yp.z - f3_dot(u2, xp));
+            }
+        } else {
+            load_atoms<K>(g_in + 9 * (size_t)min(j0, Lmax - K), j0 < Lmax, g);
+        }
         Sum6 own = sum6_zero();
         float gr[3][K];
         // (sum r x g, sum g) over the later atoms of the chain, from the block
@@ -548,15 +573,19 @@ cudaError_t fwd_t(const float* angles, const int32_t* lengths, int B, int Lmax, 
 template <int NT, int K>
 cudaError_t bwd_t(const float* angles, const int32_t* lengths, int B, int Lmax,
                   const float* coords, const float* grad_coords, float* grad_angles,
-                  bool from_coords, const ChainWs& ws, cudaStream_t s) {
-    if (from_coords) {
-        const int grid = persistent_grid((const void*)bb_bwd_kernel<NT, K, true>, NT, 0);
-        bb_bwd_kernel<NT, K, true><<<grid, NT, 0, s>>>(angles, lengths, B, Lmax, coords, grad_coords,
-                                                        grad_angles, ws, backbone_const());
+                  bool from_coords, const ChainWs& ws, const LrmsdGrad& lg, cudaStream_t s) {
+    if (lg.target) {
+        const int grid = persistent_grid((const void*)bb_bwd_kernel<NT, K, true, true>, NT, 0);
+        bb_bwd_kernel<NT, K, true, true><<<grid, NT, 0, s>>>(angles, lengths, B, Lmax, coords, grad_coords,
+                                                              grad_angles, ws, lg, backbone_const());
+    } else if (from_coords) {
+        const int grid = persistent_grid((const void*)bb_bwd_kernel<NT, K, true, false>, NT, 0);
+        bb_bwd_kernel<NT, K, true, false><<<grid, NT, 0, s>>>(angles, lengths, B, Lmax, coords, grad_coords,
+                                                               grad_angles, ws, lg, backbone_const());
     } else {
-        const int grid = persistent_grid((const void*)bb_bwd_kernel<NT, K, false>, NT, 0);
-        bb_bwd_kernel<NT, K, false><<<grid, NT, 0, s>>>(angles, lengths, B, Lmax, coords, grad_coords,
-                                                         grad_angles, ws, backbone_const());
+        const int grid = persistent_grid((const void*)bb_bwd_kernel<NT, K, false, false>, NT, 0);
+        bb_bwd_kernel<NT, K, false, false><<<grid, NT, 0, s>>>(angles, lengths, B, Lmax, coords, grad_coords,
+                                                                grad_angles, ws, lg, backbone_const());
     }
     return cudaGetLastError();
 }
@@ -605,7 +634,22 @@ cudaError_t launch_backbone_backward(const float* angles, const int32_t* lengths
     chain_ws_layout(workspace, B, Lmax, &ws);
     cudaError_t e = reset_backward_flags(ws, s);
     if (e != cudaSuccess) return e;
-    TPL_BB_DISPATCH(bwd_t, angles, lengths, B, Lmax, coords, grad_coords, grad_angles, from_coords, ws, s)
+    const LrmsdGrad none{nullptr, nullptr, nullptr};
+    TPL_BB_DISPATCH(bwd_t, angles, lengths, B, Lmax, coords, grad_coords, grad_angles, from_coords, ws, none, s)
+}
+
+cudaError_t launch_backbone_backward_lrmsd(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                           const float* coords, const float* target,
+                                           const float* grad_lrmsd, const float* lrmsd_state,
+                                           float* grad_angles, void* workspace, LaunchCfg cfg,
+                                           cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    ChainWs ws;
+    chain_ws_layout(workspace, B, Lmax, &ws);
+    cudaError_t e = reset_backward_flags(ws, s);
+    if (e != cudaSuccess) return e;
+    const LrmsdGrad lg{target, lrmsd_state, grad_lrmsd};
+    TPL_BB_DISPATCH(bwd_t, angles, lengths, B, Lmax, coords, nullptr, grad_angles, true, ws, lg, s)
 }
 
 cudaError_t launch_backbone_forward_ref64(const double* angles, const int32_t* lengths, int B,

@@ -328,16 +328,6 @@ __device__ __forceinline__ int block_scan_int(int x, int* s_cnt, int& total) {
 __device__ __forceinline__ float3 unit3(float3 v) { return f3_scale(rsqrtf(f3_dot(v, v)), v); }
 
 
-// Inputs of the LRMSD gradient formed in the backward (Section 4): for chain
-// b, g_i = w_b ((y_i - yc) - U (x_i - xc)) with y the chain's coordinates, x
-// the target, w_b = grad_lrmsd[b] / (N LRMSD) (the per-pair state of the
-// LRMSD forward).
-struct LrmsdGrad {
-    const float* target;
-    const float* state;
-    const float* grad_lrmsd;
-};
-
 template <int NT, bool LR>
 __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_kernel(
     const uint8_t* __restrict__ seq, const int32_t* __restrict__ lengths, int B, int Lmax, int Amax,

@@ -28,6 +28,14 @@ cudaError_t launch_backbone_backward(const float* angles, const int32_t* lengths
                                      float* grad_angles, bool from_coords, void* workspace,
                                      LaunchCfg cfg, cudaStream_t s);
 
+// K2 with the LRMSD gradient formed in place of a coordinate-gradient input
+// (P = B pairs of Nmax = 3 Lmax atoms).
+cudaError_t launch_backbone_backward_lrmsd(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                           const float* coords, const float* target,
+                                           const float* grad_lrmsd, const float* lrmsd_state,
+                                           float* grad_angles, void* workspace, LaunchCfg cfg,
+                                           cudaStream_t s);
+
 // K3 / K4: full-atom FP32 scan kernels.
 bool fullatom_cfg_supported(int threads);
 cudaError_t launch_fullatom_forward(const float* angles, const uint8_t* seq,

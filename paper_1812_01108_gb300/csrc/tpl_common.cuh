@@ -441,6 +441,16 @@ __device__ __forceinline__ Sum6 block_seg_suffix_sum6(const Sum6& x, bool tail, 
     return sum6_add(lex, wv);
 }
 
+// Inputs of an LRMSD gradient formed inside a chain backward (Section 4): for
+// chain b, g_i = w_b ((y_i - yc) - U (x_i - xc)) with y the chain's
+// coordinates, x the target and w_b = grad_lrmsd[b] / (N LRMSD), from the
+// per-pair state of the LRMSD forward (U row-major, xc, yc, 1 / (N LRMSD)).
+struct LrmsdGrad {
+    const float* target;
+    const float* state;
+    const float* grad_lrmsd;
+};
+
 __device__ __forceinline__ int clamp_length(const int32_t* lengths, int b, int Lmax) {
     int L = lengths[b];
     if (L < 0 || L > Lmax) {

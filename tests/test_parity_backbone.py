@@ -195,3 +195,47 @@ def test_autotuner_picks_a_valid_shape_and_its_results_match():
     c32, ga32 = _run_fp32(a, lengths, g, best)
     assert np.abs(c32 - oracle.backbone_forward(a, lengths)).max() <= COORD_TOL
     assert rel_err(ga32, oracle.backbone_backward(a, lengths, g)) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("threads,k,sched", [(128, 4, tpl.SCHED_PACKED), (256, 2, tpl.SCHED_LONGEST_FIRST),
+                                              (64, 1, tpl.SCHED_PACKED)])
+def test_fused_lrmsd_backward_equals_the_two_calls_and_the_oracle(threads, k, sched):
+    """tpl_backbone_backward_lrmsd = tpl_lrmsd_backward + tpl_backbone_backward
+    (FROM_COORDS), packed and tiled chains, against the oracle chain."""
+    d = require_gpu()
+    rng = np.random.default_rng(47)
+    lengths = workloads.lengths_loguniform(40, 1, 900, rng)
+    lengths[:3] = [0, 1, 900]
+    a, _ = _inputs(lengths, 48, Lmax=900)
+    ta = workloads.perturb_angles(a, lengths, rng)
+    B, _, Lmax = a.shape
+    A, Ln = dev(a, d), dev(lengths, d)
+    opts = {"threads": threads, "res_per_thread": k, "schedule": sched}
+    ws = torch.empty(tpl.tpl_backbone_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    tgt = torch.zeros((B, 3 * Lmax, 3), device=d)
+    tpl.tpl_backbone_forward(dev(ta, d), Ln, tgt, ws, opts)
+    coords = torch.zeros_like(tgt)
+    tpl.tpl_backbone_forward(A, Ln, coords, ws, opts)
+    na = dev((3 * lengths).astype(np.int32), d)
+    lr = torch.zeros((B,), device=d)
+    lr_ws = torch.empty(tpl.tpl_lrmsd_workspace_size(B, 3 * Lmax), dtype=torch.uint8, device=d)
+    tpl.tpl_lrmsd_forward(coords, tgt, na, lr, lr_ws)
+    w = dev(np.linspace(-1.0, 2.0, B).astype(np.float32), d)
+    ga_fused = torch.full_like(A, float("nan"))
+    tpl.tpl_backbone_backward_lrmsd(A, Ln, coords, tgt, w, lr_ws, ga_fused, ws, opts)
+    gc = torch.empty_like(coords)
+    tpl.tpl_lrmsd_backward(w, coords, tgt, na, gc, lr_ws)
+    ga_two = torch.full_like(A, float("nan"))
+    tpl.tpl_backbone_backward(A, Ln, coords, gc, ga_two, ws, dict(opts, bwd_mode=tpl.BWD_FROM_COORDS))
+    torch.cuda.synchronize()
+    f = host(ga_fused)
+    assert np.all(np.isfinite(f))
+    assert rel_err(f, host(ga_two)) <= 1e-5
+    g64 = oracle.lrmsd_backward(host(w).astype(np.float64), host(coords), host(tgt), 3 * lengths)
+    ga64 = oracle.backbone_backward(a, lengths, g64)
+    # a one-residue chain is a rigid N-CA-C triangle: input and target are
+    # congruent, LRMSD is zero up to rounding and its gradient is undefined
+    m = lengths >= 2
+    assert rel_err(f[m], ga64[m]) <= GRAD_TOL
+    for b, L in enumerate(lengths):
+        assert np.all(f[b, :, L:] == 0)
