@@ -50,7 +50,21 @@ DEFAULT_BATCH = {"training_step": 256, "backbone_uneven": 4096, "lrmsd_batch": 1
 # call's kernels from one ncu capture, per unit processed (residue or atom),
 # keyed by (workload, call), with the profile summary that holds the capture.
 # An entry is removed when one of its kernels changes after the capture.
-TRAFFIC = {}
+TRAFFIC = {
+    # fa_bwd_coords_kernel<256, 1> (LRMSD gradient formed in the kernel), cold cache
+    ("training_step", "lrmsd_fullatom_backward"): (24.7444, "atom",
+                                                   "profiles/fa_kernels_training_step_256x700.md"),
+    # bb_fwd_kernel<256, 4> (the schedule kernel's few bytes not counted)
+    ("backbone_uneven", "backbone_forward"): (80.3405, "residue",
+                                              "profiles/backbone_kernels_backbone_uneven_4096.md"),
+    # bb_bwd_kernel<256, 4, 1, 1>
+    ("backbone_uneven", "lrmsd_backbone_backward"): (82.6204, "residue",
+                                                     "profiles/backbone_kernels_backbone_uneven_4096.md"),
+    # moments + solve + residual, 4096-pair capture scaled by atoms
+    ("lrmsd_batch", "lrmsd_forward"): (49.1460, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md"),
+    # grad, 4096-pair capture scaled by atoms
+    ("lrmsd_batch", "lrmsd_backward"): (42.8179, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md"),
+}
 
 
 def parse():
