@@ -67,7 +67,7 @@ TRAFFIC = {
 }
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=2000)
@@ -86,7 +86,7 @@ def parse():
                    help="use the library's default launch shape instead of the autotuner's pick")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 per-chain comparison")
-    a = p.parse_args()
+    a = p.parse_args(argv)
     if a.batch <= 0:
         a.batch = DEFAULT_BATCH[a.workload]
     return a
@@ -390,6 +390,8 @@ def setup_training_step(args, tpl, torch, dev, d):
     tgt_host = target.cpu().pin_memory()
     st.h2d = [(A, torch.from_numpy(a).pin_memory()), (S, torch.from_numpy(seq).pin_memory()),
               (Ln, torch.from_numpy(lengths).pin_memory()), (target, tgt_host)]
+    st.outputs = {"coords": coords, "target": target, "num_atoms": na, "lrmsd": lr, "grad_angles": gang,
+                  "weights": wgt}
     st.d2h = (torch.empty((B,), dtype=torch.float32).pin_memory(), lr)
 
     def fp64():
@@ -482,6 +484,7 @@ def setup_backbone_uneven(args, tpl, torch, dev, d):
                                          "formed inside the backbone backward"}
     st.h2d = [(A, torch.from_numpy(a).pin_memory()), (Ln, torch.from_numpy(lengths).pin_memory()),
               (na, torch.from_numpy(na_host).pin_memory()), (target, target.cpu().pin_memory())]
+    st.outputs = {"coords": coords, "target": target, "lrmsd": lr, "grad_angles": gang, "weights": wgt}
     st.d2h = (torch.empty((B,), dtype=torch.float32).pin_memory(), lr)
 
     def fp64():
@@ -533,6 +536,7 @@ def setup_lrmsd_batch(args, tpl, torch, dev, d):
     st.extra_config = {"atoms_per_gpu": n_atoms, "Nmax": Nmax}
     st.h2d = [(X, torch.from_numpy(x).pin_memory()), (Y, torch.from_numpy(y).pin_memory()),
               (NA, torch.from_numpy(n).pin_memory())]
+    st.outputs = {"lrmsd": lr, "grad_input": gx, "weights": up}
     st.d2h = (torch.empty((P,), dtype=torch.float32).pin_memory(), lr)
 
     def fp64():
