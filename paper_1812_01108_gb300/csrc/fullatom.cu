@@ -113,6 +113,34 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// Asynchronous copy (cp.async, no register round trip) of the float range
+// [g0, g1) of global memory into stage[off + i - g0], off = g0 mod 4: 16-byte
+// copies for the aligned middle, 4-byte copies for the ragged ends.  The caller
+// commits and waits (cp_async_wait_all) before a barrier.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+template <int NT>
+__device__ __forceinline__ void async_copy_range(const float* __restrict__ glob, float* __restrict__ stage,
+                                                 int g0, int g1) {
+    if (g1 <= g0) return;
+    const int off = g0 & 3;
+    const int head = min(g1, (g0 + 3) & ~3);
+    const int tail = max(head, g1 & ~3);
+    for (int i = g0 + threadIdx.x; i < head; i += NT) cp_async4(stage + off + i - g0, glob + i);
+    for (int q = head / 4 + threadIdx.x; q < tail / 4; q += NT) cp_async16(stage + off + 4 * q - g0, glob + 4 * q);
+    for (int i = tail + threadIdx.x; i < g1; i += NT) cp_async4(stage + off + i - g0, glob + i);
+}
+
 template <int NT>
 __device__ __forceinline__ void zero_range(float* __restrict__ glob, int g0, int g1) {
     if (g1 <= g0) return;
@@ -337,6 +365,8 @@ __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_ker
     __shared__ FaTable s_tab;
     __shared__ float s6[6 * (NW + 1)];
     __shared__ int s_v;
+    extern __shared__ float4 s_dyn[];
+    float* st_r = reinterpret_cast<float*>(s_dyn);  // the tile's coordinates
 
     if (!ws_matches(ws, NT, B, Lmax)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) flag_status(TPL_STATUS_BAD_WORKSPACE);
@@ -360,9 +390,14 @@ __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_ker
         const float* g_in = grad_coords + (size_t)b * Amax * 3;
         float* ga = grad_angles + (size_t)b * 7 * Lmax;
 
-        // each thread reads its residue's atoms directly (the forward recorded
-        // every residue's first atom); the per-thread runs are contiguous, so
-        // a warp's loads stay within a few kilobytes and hit L1 after the first
+        // the tile's coordinates are staged with coalesced asynchronous copies
+        // (the forward recorded the tile's first atom and atom count, and
+        // every residue's first atom); each thread reads the gradient or
+        // target of its own atoms directly
+        const float4 sd = ws.start[4 * (size_t)(slot0 + t) + 3];
+        const int pc = __float_as_int(sd.x);
+        const int soff = (3 * pc) & 3;
+        async_copy_range<NT>(r_in, st_r, 3 * pc, 3 * min(pc + __float_as_int(sd.y), Amax));
         const int j = t * NT + threadIdx.x;
         const bool valid = j < L;
         const int type = residue_type(sq, j, valid);
@@ -370,13 +405,15 @@ __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_ker
         const int a0 = valid ? __ldg(ws.ratom + (size_t)b * Lmax + j) : 0;
         const int ap = (valid && j > 0) ? __ldg(ws.ratom + (size_t)b * Lmax + j - 1) : 0;
 
-        const bool in_range = valid && a0 >= 0 && a0 + nat <= Amax;
+        const bool in_range = valid && a0 >= pc && a0 + nat <= Amax && a0 - pc + nat <= NT * kMaxAtoms;
+        cp_async_wait_all();
+        __syncthreads();
         float gchi[kMaxGroups] = {0.f, 0.f, 0.f, 0.f};
         Sum6 all = sum6_zero(), nsum = sum6_zero(), csum = sum6_zero();
         float3 rN = make_float3(0.f, 0.f, 0.f), rCA = rN, rC = rN, rCprev = rN;
         if (in_range) {
-            const float* sr = r_in + 3 * (size_t)a0;
-            auto R = [&](int k) { return make_float3(__ldg(sr + 3 * k), __ldg(sr + 3 * k + 1), __ldg(sr + 3 * k + 2)); };
+            const float* sr = st_r + soff + 3 * (a0 - pc);
+            auto R = [&](int k) { return make_float3(sr[3 * k], sr[3 * k + 1], sr[3 * k + 2]); };
             // the coordinate gradient: read, or formed from the LRMSD state
             const float* sg = LR ? lg.target + ((size_t)b * Amax + a0) * 3 : g_in + 3 * (size_t)a0;
             float3 u0 = make_float3(0.f, 0.f, 0.f), u1 = u0, u2 = u0, xc = u0, yc = u0;
@@ -404,9 +441,9 @@ __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_ker
             rN = R(0);
             rCA = R(1);
             rC = R(2);
-            if (j > 0) {  // C of the previous residue
-                const float* pr = r_in + 3 * (size_t)(ap + 2);
-                rCprev = make_float3(__ldg(pr), __ldg(pr + 1), __ldg(pr + 2));
+            if (j > 0) {  // C of the previous residue (the tile before holds it for the first)
+                const float* pr = ap >= pc ? st_r + soff + 3 * (ap + 2 - pc) : r_in + 3 * (size_t)(ap + 2);
+                rCprev = make_float3(pr[0], pr[1], pr[2]);
             }
             add(nsum, 0);
             add(all, 1);
@@ -830,9 +867,13 @@ template <int NT, bool LR>
 cudaError_t fa_bwd_coords_t(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
                             const float* coords, const float* grad_coords, float* grad_angles,
                             const ChainWs& ws, LrmsdGrad lg, cudaStream_t s) {
-    const int grid = persistent_grid((const void*)fa_bwd_coords_kernel<NT, LR>, NT, 0);
-    fa_bwd_coords_kernel<NT, LR><<<grid, NT, 0, s>>>(seq, lengths, B, Lmax, Amax, coords, grad_coords,
-                                                        grad_angles, ws, lg, fa_table());
+    const size_t smem = (size_t)(4 + NT * kMaxAtoms * 3) * sizeof(float);
+    static bool done[64] = {false};
+    cudaError_t e = smem_attr_once(fa_bwd_coords_kernel<NT, LR>, (int)smem, done);
+    if (e != cudaSuccess) return e;
+    const int grid = persistent_grid((const void*)fa_bwd_coords_kernel<NT, LR>, NT, smem);
+    fa_bwd_coords_kernel<NT, LR><<<grid, NT, smem, s>>>(seq, lengths, B, Lmax, Amax, coords, grad_coords,
+                                                           grad_angles, ws, lg, fa_table());
     return cudaGetLastError();
 }
 
