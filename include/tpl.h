@@ -298,7 +298,7 @@ tpl_status tpl_get_status(tpl_stream stream, int* device_status);
 /* Autotuner (the paper has no counterpart): runs forward + backward on the
  * caller's batch for every supported launch shape and schedule -- backbone:
  * threads 64..512 x residues per thread 1, 2, 4 x {PACKED, LONGEST_FIRST};
- * full atom: threads 64..512 x {BATCH_ORDER, LONGEST_FIRST} -- times each with
+ * full atom: threads 64, 128, 192, 256, 384, 512 x {BATCH_ORDER, LONGEST_FIRST} -- times each with
  * CUDA events on `stream` (one untimed pass, best of three), and writes the
  * fastest options to *best (and its time in ms to *best_ms if not NULL).
  * `bwd_mode` is kept in every candidate.  The arguments are those of the

@@ -722,11 +722,12 @@ tpl_status tpl_fullatom_autotune(const float* angles, const uint8_t* seq, const 
                                  size_t workspace_bytes, int bwd_mode, tpl_opts* best, float* best_ms,
                                  tpl_stream stream) {
     if (!best) return fail(TPL_ERR_INVALID_ARG, "best is NULL");
-    tpl_opts cands[8];
+    tpl_opts cands[12];
     int n = 0;
-    const int threads[4] = {64, 128, 256, 512}, sch[2] = {TPL_SCHED_BATCH_ORDER, TPL_SCHED_LONGEST_FIRST};
+    const int threads[6] = {64, 128, 192, 256, 384, 512};
+    const int sch[2] = {TPL_SCHED_BATCH_ORDER, TPL_SCHED_LONGEST_FIRST};
     for (int si = 0; si < 2; ++si)
-        for (int ti = 0; ti < 4; ++ti) {
+        for (int ti = 0; ti < 6; ++ti) {
             tpl_opts o;
             memset(&o, 0, sizeof(o));
             o.bwd_mode = bwd_mode;

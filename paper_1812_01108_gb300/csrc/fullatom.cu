@@ -175,14 +175,14 @@ __host__ __device__ constexpr size_t fa_fwd_smem() {
 // CTAs per SM the forward and backward kernels are compiled for (register cap)
 template <int NT>
 __host__ __device__ constexpr int fa_min_blocks() {
-    return NT >= 512 ? 1 : (NT >= 256 ? 3 : 6);
+    return NT >= 512 ? 1 : (NT >= 384 ? 2 : (NT >= 256 ? 3 : (NT >= 192 ? 4 : 6)));
 }
 
 // The coordinate-reading backward stages two tiles (coordinates and their
 // gradients), so shared memory holds fewer of its CTAs per SM.
 template <int NT>
 __host__ __device__ constexpr int fa_bwd_min_blocks() {
-    return NT >= 512 ? 2 : (NT >= 256 ? 4 : 8);
+    return NT >= 384 ? 2 : (NT >= 256 ? 4 : (NT >= 192 ? 5 : 8));
 }
 
 template <int NT>
@@ -894,7 +894,8 @@ cudaError_t fa_bwd_t(const float* angles, const uint8_t* seq, const int32_t* len
 }  // namespace
 
 bool fullatom_cfg_supported(int threads) {
-    return threads == 64 || threads == 128 || threads == 256 || threads == 512;
+    return threads == 64 || threads == 128 || threads == 192 || threads == 256 || threads == 384 ||
+           threads == 512;
 }
 
 cudaError_t launch_fullatom_forward(const float* angles, const uint8_t* seq,
@@ -909,7 +910,9 @@ cudaError_t launch_fullatom_forward(const float* angles, const uint8_t* seq,
     switch (cfg.threads) {
         case 64: return fa_fwd_t<64>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s);
         case 128: return fa_fwd_t<128>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s);
+        case 192: return fa_fwd_t<192>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s);
         case 256: return fa_fwd_t<256>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s);
+        case 384: return fa_fwd_t<384>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s);
         case 512: return fa_fwd_t<512>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s);
         default: return cudaErrorInvalidValue;
     }
@@ -929,7 +932,9 @@ cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
         switch (cfg.threads) {
             case 64: return fa_bwd_coords_t<64, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, LrmsdGrad{}, s);
             case 128: return fa_bwd_coords_t<128, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, LrmsdGrad{}, s);
+            case 192: return fa_bwd_coords_t<192, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, LrmsdGrad{}, s);
             case 256: return fa_bwd_coords_t<256, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, LrmsdGrad{}, s);
+            case 384: return fa_bwd_coords_t<384, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, LrmsdGrad{}, s);
             case 512: return fa_bwd_coords_t<512, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, LrmsdGrad{}, s);
             default: return cudaErrorInvalidValue;
         }
@@ -937,7 +942,9 @@ cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
     switch (cfg.threads) {
         case 64: return fa_bwd_t<64>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);
         case 128: return fa_bwd_t<128>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);
+        case 192: return fa_bwd_t<192>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);
         case 256: return fa_bwd_t<256>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);
+        case 384: return fa_bwd_t<384>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);
         case 512: return fa_bwd_t<512>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);
         default: return cudaErrorInvalidValue;
     }
@@ -966,7 +973,9 @@ cudaError_t launch_fullatom_backward_lrmsd(const uint8_t* seq, const int32_t* le
     switch (cfg.threads) {
         case 64: return fa_bwd_coords_t<64, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
         case 128: return fa_bwd_coords_t<128, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
+        case 192: return fa_bwd_coords_t<192, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
         case 256: return fa_bwd_coords_t<256, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
+        case 384: return fa_bwd_coords_t<384, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
         case 512: return fa_bwd_coords_t<512, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
         default: return cudaErrorInvalidValue;
     }

@@ -54,7 +54,7 @@ def reference():
 
 
 @pytest.mark.parametrize("from_coords", [False, True])
-@pytest.mark.parametrize("threads", [256, 64, 128, 512])
+@pytest.mark.parametrize("threads", [256, 64, 128, 192, 384, 512])
 def test_fp32_scan_matches_oracle(reference, threads, from_coords):
     a, seq, g, Amax, c64, na64, g64 = reference
     c32, na32, ga32 = _run_fp32(a, seq, LENGTHS, g, Amax, {"threads": threads}, from_coords)
