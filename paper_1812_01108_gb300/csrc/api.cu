@@ -58,15 +58,23 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 constexpr int kBuckets = 64;
 constexpr int kKeys = kBuckets + kMaxPack;
 constexpr int kSchedThreads = 1024;
+constexpr int kSchedWarps = kSchedThreads / 32;
 
 __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* __restrict__ lengths,
                                                                  int B, int Lmax, int tile, int mode,
                                                                  int granule, ChainWs ws) {
     __shared__ int hist[kKeys];
     __shared__ int s_start[kKeys + 1];
+    __shared__ int s_run[kKeys];
+    __shared__ int s_wcnt[kSchedWarps][kKeys];
     __shared__ int s_part[33];
     int* order = ws.order;
-    for (int i = threadIdx.x; i < B * ws.tmax; i += kSchedThreads) ws.fflag[i] = 0;
+    {  // zero the forward flags, 16 bytes at a time (the region is 256-byte aligned)
+        const int n = B * ws.tmax;
+        int4* f4 = reinterpret_cast<int4*>(ws.fflag);
+        for (int i = threadIdx.x; i < n / 4; i += kSchedThreads) f4[i] = make_int4(0, 0, 0, 0);
+        for (int i = (n & ~3) + threadIdx.x; i < n; i += kSchedThreads) ws.fflag[i] = 0;
+    }
     auto len = [&](int b) {
         const int L = lengths[b];
         return L < 0 ? 0 : (L > Lmax ? Lmax : L);
@@ -81,22 +89,74 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
         return kBuckets - 1 - (int)(((long long)len(b) * kBuckets) / ((long long)Lmax + 1));
     };
     if (mode != kSchedBatch) {
-        if (threadIdx.x < kKeys) hist[threadIdx.x] = 0;
-        __syncthreads();
-        for (int b = threadIdx.x; b < B; b += kSchedThreads) atomicAdd(&hist[key(b)], 1);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int run = 0;
-            for (int k = 0; k < kKeys; ++k) {
-                const int c = hist[k];
-                hist[k] = run;
-                s_start[k] = run;
-                run += c;
-            }
-            s_start[kKeys] = run;
+        // stable counting sort by key: chains of equal key keep batch order, so
+        // the schedule (and the packs) do not depend on timing
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const unsigned lt = (1u << lane) - 1u;
+        if (threadIdx.x < kKeys) {
+            hist[threadIdx.x] = 0;
+            s_run[threadIdx.x] = 0;
         }
         __syncthreads();
-        for (int b = threadIdx.x; b < B; b += kSchedThreads) order[atomicAdd(&hist[key(b)], 1)] = b;
+        // key counts: one atomic per distinct key of a warp
+        for (int b0 = 0; b0 < B; b0 += kSchedThreads) {
+            const int b = b0 + threadIdx.x;
+            const int k = b < B ? key(b) : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, k);
+            if (k >= 0 && (peers & lt) == 0) atomicAdd(&hist[k], __popc(peers));
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {  // exclusive scan of the key counts, kKeys <= 128: 4 per lane
+            static_assert(kKeys <= 128, "key scan covers 128 keys");
+            int c[4], sum = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = 4 * lane + q;
+                c[q] = k < kKeys ? hist[k] : 0;
+                sum += c[q];
+            }
+            int inc = sum;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, off);
+                if (lane >= off) inc += y;
+            }
+            int run = inc - sum;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = 4 * lane + q;
+                if (k < kKeys) s_start[k] = run;
+                run += c[q];
+            }
+            if (lane == 31) s_start[kKeys] = inc;
+        }
+        __syncthreads();
+        // positions, 1024 chains at a time: rank among equal keys = chains of
+        // that key in earlier rounds + in earlier warps of this round + in
+        // earlier lanes of this warp
+        for (int b0 = 0; b0 < B; b0 += kSchedThreads) {
+            const int b = b0 + threadIdx.x;
+            const int k = b < B ? key(b) : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, k);
+            for (int i = threadIdx.x; i < kSchedWarps * kKeys; i += kSchedThreads) (&s_wcnt[0][0])[i] = 0;
+            __syncthreads();
+            if (k >= 0 && (peers & lt) == 0) s_wcnt[warp][k] = __popc(peers);
+            __syncthreads();
+            if (threadIdx.x < kKeys) {  // exclusive prefix over the warps, per key
+                int run = 0;
+                for (int w = 0; w < kSchedWarps; ++w) {
+                    const int c = s_wcnt[w][threadIdx.x];
+                    s_wcnt[w][threadIdx.x] = run;
+                    run += c;
+                }
+                hist[threadIdx.x] = run;  // this round's count of the key
+            }
+            __syncthreads();
+            if (k >= 0) order[s_start[k] + s_run[k] + s_wcnt[warp][k] + __popc(peers & lt)] = b;
+            __syncthreads();
+            if (threadIdx.x < kKeys) s_run[threadIdx.x] += hist[threadIdx.x];
+            __syncthreads();
+        }
     } else {
         for (int b = threadIdx.x; b < B; b += kSchedThreads) order[b] = b;
     }

@@ -239,3 +239,16 @@ def test_fused_lrmsd_backward_equals_the_two_calls_and_the_oracle(threads, k, sc
     assert rel_err(f[m], ga64[m]) <= GRAD_TOL
     for b, L in enumerate(lengths):
         assert np.all(f[b, :, L:] == 0)
+
+
+def test_packed_schedule_is_deterministic():
+    """The packs come from a stable sort (no atomics decide the order), so the
+    packed results are bit-identical from run to run."""
+    rng = np.random.default_rng(49)
+    lengths = workloads.lengths_loguniform(3000, 1, 800, rng)
+    a, g = _inputs(lengths, 50, Lmax=800)
+    opts = {"threads": 128, "res_per_thread": 4, "schedule": tpl.SCHED_PACKED}
+    c1, g1 = _run_fp32(a, lengths, g, opts, dict(opts, bwd_mode=tpl.BWD_FROM_COORDS))
+    _run_fp32(a[:7], lengths[:7], g[:7], opts)  # something else in between
+    c2, g2 = _run_fp32(a, lengths, g, opts, dict(opts, bwd_mode=tpl.BWD_FROM_COORDS))
+    assert np.array_equal(c1, c2) and np.array_equal(g1, g2)
