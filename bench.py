@@ -80,8 +80,10 @@ def parse(argv=None):
     p.add_argument("--res-per-thread", type=int, default=0, help="backbone residues per thread (0 = default)")
     p.add_argument("--bwd", default="coords", choices=["coords", "recompute"],
                    help="chain backward: read the forward's coordinates or rebuild frames")
-    p.add_argument("--unfused", action="store_true",
-                   help="training step: LRMSD backward and full-atom backward as two calls")
+    p.add_argument("--fusion", default="backward", choices=["step", "backward", "none"],
+                   help="training step: fused step (two calls), fused backward (three calls), "
+                        "or separate calls (four)")
+    p.add_argument("--unfused", action="store_true", help="same as --fusion none")
     p.add_argument("--no-autotune", action="store_true",
                    help="use the library's default launch shape instead of the autotuner's pick")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -89,6 +91,8 @@ def parse(argv=None):
     a = p.parse_args(argv)
     if a.batch <= 0:
         a.batch = DEFAULT_BATCH[a.workload]
+    if a.unfused:
+        a.fusion = "none"
     return a
 
 
@@ -358,7 +362,24 @@ def setup_training_step(args, tpl, torch, dev, d):
     st.kernels = {"fullatom_forward": ["schedule_kernel", "fa_fwd_kernel"],
                   "lrmsd_forward": ["lrmsd_moments_kernel", solve, "lrmsd_residual_kernel"]}
     st.alg = {"fullatom_forward": res * (28 + 1) + 12 * n_atoms, "lrmsd_forward": 24 * n_atoms}
-    if args.unfused or args.bwd != "coords":
+    st_ws = None
+    if args.fusion == "step" and args.bwd == "coords":
+        # forward with the LRMSD moments in its tiles + eigen-solve; backward with
+        # the LRMSD gradient, residuals and LRMSD (one workspace for both)
+        st_ws = torch.empty(tpl.tpl_fullatom_lrmsd_workspace_size(B, Lmax), dtype=torch.uint8, device=dev)
+        st.calls = [
+            ("lrmsd_step_forward",
+             lambda: tpl.tpl_fullatom_lrmsd_forward(A, S, Ln, target, coords, na, st_ws, opts)),
+            ("lrmsd_step_backward",
+             lambda: tpl.tpl_fullatom_lrmsd_backward(S, Ln, coords, target, na, wgt, lr, gang, st_ws, opts)),
+        ]
+        st.kernels = {"lrmsd_step_forward": ["schedule_kernel", "fa_fwd_kernel", "lrmsd_solve_quad_kernel"],
+                      "lrmsd_step_backward": ["fa_bwd_coords_kernel"]}
+        # forward: angles and sequence in, coordinates out, target read for the moments;
+        # backward: angles and sequence in, angle gradient out, coordinates and target read
+        st.alg = {"lrmsd_step_forward": res * (28 + 1) + 24 * n_atoms,
+                  "lrmsd_step_backward": res * (28 + 1 + 28) + 24 * n_atoms}
+    elif args.fusion == "none" or args.bwd != "coords":
         bwd_kernel = "fa_bwd_coords_kernel" if args.bwd == "coords" else "fa_bwd_kernel"
         st.calls = [
             ("fullatom_forward", lambda: tpl.tpl_fullatom_forward(A, S, Ln, coords, na, fa_ws, opts)),
@@ -385,8 +406,10 @@ def setup_training_step(args, tpl, torch, dev, d):
     st.atoms = n_atoms
     st.extra_config = {"atoms_per_gpu": n_atoms, "threads": opts.threads or "default",
                        "fullatom_backward": args.bwd, "autotuned": tuned,
-                       "lrmsd_backward": "separate call" if len(st.calls) == 4 else
-                                         "formed inside the full-atom backward"}
+                       "fusion": {2: "fused step: forward with LRMSD moments + eigen-solve; backward with "
+                                     "LRMSD gradient, residuals and LRMSD",
+                                  3: "LRMSD backward formed inside the full-atom backward",
+                                  4: "separate calls"}[len(st.calls)]}
     tgt_host = target.cpu().pin_memory()
     st.h2d = [(A, torch.from_numpy(a).pin_memory()), (S, torch.from_numpy(seq).pin_memory()),
               (Ln, torch.from_numpy(lengths).pin_memory()), (target, tgt_host)]

@@ -164,6 +164,30 @@ tpl_status tpl_fullatom_backward(const float* angles, const uint8_t* seq, const 
                                  const float* grad_coords, float* grad_angles, void* workspace,
                                  size_t workspace_bytes, const tpl_opts* opts, tpl_stream stream);
 
+/* Fused training step on the LRMSD loss of Section 4 chained into Eq. 1, in
+ * two calls that share one workspace (the paper has no fused form; the
+ * results equal tpl_fullatom_forward, tpl_lrmsd_forward with P = B and
+ * Nmax = Amax, and tpl_fullatom_backward_lrmsd):
+ *  - tpl_fullatom_lrmsd_forward: coords and num_atoms as tpl_fullatom_forward;
+ *    each tile also reduces its atoms' LRMSD moments against target
+ *    [B][Amax][3], and the eigen-solve leaves U and the centroids of every
+ *    chain in the workspace.
+ *  - tpl_fullatom_lrmsd_backward: grad_angles = d(sum_b grad_lrmsd[b]
+ *    LRMSD_b) / d(angles) and lrmsd[b] = LRMSD(coords[b], target[b]): the
+ *    backward forms each atom's LRMSD gradient and squared residual, and the
+ *    chain's first tile forms LRMSD (FP64 sum) and applies 1 / (N LRMSD).
+ *    coords, target and num_atoms are those of the forward call.
+ * The loss value comes out of the backward, with the gradient. */
+size_t tpl_fullatom_lrmsd_workspace_size(int B, int Lmax);
+tpl_status tpl_fullatom_lrmsd_forward(const float* angles, const uint8_t* seq, const int32_t* lengths, int B,
+                                      int Lmax, int Amax, const float* target, float* coords, int32_t* num_atoms,
+                                      void* workspace, size_t workspace_bytes, const tpl_opts* opts,
+                                      tpl_stream stream);
+tpl_status tpl_fullatom_lrmsd_backward(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
+                                       const float* coords, const float* target, const int32_t* num_atoms,
+                                       const float* grad_lrmsd, float* lrmsd, float* grad_angles, void* workspace,
+                                       size_t workspace_bytes, const tpl_opts* opts, tpl_stream stream);
+
 /* Backbone form of tpl_fullatom_backward_lrmsd below (Eq. 2 instead of
  * Eq. 1): grad_angles = d(sum_b grad_lrmsd[b] LRMSD(coords[b], target[b])) /
  * d(angles), equal to tpl_lrmsd_backward (P = B, Nmax = 3 Lmax, num_atoms =

@@ -30,7 +30,8 @@ __all__ = [
     "tpl_backbone_backward_ref64", "tpl_fullatom_forward_ref64", "tpl_fullatom_backward_ref64",
     "tpl_lrmsd_forward_ref64", "tpl_lrmsd_backward_ref64", "tpl_get_status",
     "tpl_selftest_wait_timeout", "tpl_backbone_autotune", "tpl_fullatom_autotune",
-    "tpl_fullatom_backward_lrmsd", "tpl_backbone_backward_lrmsd", "backbone",
+    "tpl_fullatom_backward_lrmsd", "tpl_backbone_backward_lrmsd", "tpl_fullatom_lrmsd_workspace_size",
+    "tpl_fullatom_lrmsd_forward", "tpl_fullatom_lrmsd_backward", "backbone",
     "fullatom", "lrmsd", "residue_table", "fullatom_max_atoms", "BWD_RECOMPUTE",
     "BWD_FROM_COORDS", "SCHED_LONGEST_FIRST", "SCHED_BATCH_ORDER", "SCHED_PACKED",
 ]
@@ -89,6 +90,9 @@ def load_library():
             "tpl_fullatom_backward": ([P, P, P, I, I, I, P, P, P, P, Z, O, P], I),
             "tpl_fullatom_backward_lrmsd": ([P, P, P, I, I, I, P, P, P, P, Z, P, P, Z, O, P], I),
             "tpl_backbone_backward_lrmsd": ([P, P, I, I, P, P, P, P, Z, P, P, Z, O, P], I),
+            "tpl_fullatom_lrmsd_workspace_size": ([I, I], Z),
+            "tpl_fullatom_lrmsd_forward": ([P, P, P, I, I, I, P, P, P, P, Z, O, P], I),
+            "tpl_fullatom_lrmsd_backward": ([P, P, I, I, I, P, P, P, P, P, P, P, Z, O, P], I),
             "tpl_lrmsd_forward": ([P, P, P, I, I, P, P, Z, P], I),
             "tpl_lrmsd_backward": ([P, P, P, P, I, I, P, P, Z, P], I),
             "tpl_lrmsd_forward_noalloc": ([P, P, P, I, I, P, P], I),
@@ -238,6 +242,38 @@ def tpl_fullatom_autotune(angles, seq, lengths, coords, num_atoms, grad_coords, 
         workspace.numel() * workspace.element_size(), int(bwd_mode), ctypes.byref(best),
         ctypes.byref(ms), _stream(angles, stream)))
     return best, ms.value
+
+
+def tpl_fullatom_lrmsd_workspace_size(B, Lmax):
+    return int(load_library().tpl_fullatom_lrmsd_workspace_size(B, Lmax))
+
+
+def tpl_fullatom_lrmsd_forward(angles, seq, lengths, target, coords, num_atoms, workspace, opts=None,
+                               stream=None):
+    """Fused training step, forward: coordinates, atom counts, and the LRMSD
+    moments and rotation against ``target`` left in ``workspace``."""
+    B, _, Lmax = angles.shape
+    Amax = coords.shape[1]
+    _check("tpl_fullatom_lrmsd_forward", load_library().tpl_fullatom_lrmsd_forward(
+        _ptr(_cuda(angles, torch.float32, "angles")), _ptr(_cuda(seq, torch.uint8, "seq")),
+        _ptr(_cuda(lengths, torch.int32, "lengths")), B, Lmax, Amax,
+        _ptr(_cuda(target, torch.float32, "target")), _ptr(_cuda(coords, torch.float32, "coords")),
+        _ptr(_cuda(num_atoms, torch.int32, "num_atoms")), _ptr(workspace),
+        workspace.numel() * workspace.element_size(), _opts(opts), _stream(angles, stream)))
+
+
+def tpl_fullatom_lrmsd_backward(seq, lengths, coords, target, num_atoms, grad_lrmsd, lrmsd_out,
+                                grad_angles, workspace, opts=None, stream=None):
+    """Fused training step, backward: angle gradients of sum_b grad_lrmsd[b] *
+    LRMSD_b and the LRMSD values."""
+    B, Lmax = seq.shape
+    Amax = coords.shape[1]
+    _check("tpl_fullatom_lrmsd_backward", load_library().tpl_fullatom_lrmsd_backward(
+        _ptr(_cuda(seq, torch.uint8, "seq")), _ptr(_cuda(lengths, torch.int32, "lengths")), B, Lmax, Amax,
+        _ptr(_cuda(coords, torch.float32, "coords")), _ptr(_cuda(target, torch.float32, "target")),
+        _ptr(_cuda(num_atoms, torch.int32, "num_atoms")), _ptr(_cuda(grad_lrmsd, torch.float32, "grad_lrmsd")),
+        _ptr(_cuda(lrmsd_out, torch.float32, "lrmsd")), _ptr(_cuda(grad_angles, torch.float32, "grad_angles")),
+        _ptr(workspace), workspace.numel() * workspace.element_size(), _opts(opts), _stream(coords, stream)))
 
 
 def tpl_backbone_backward_lrmsd(angles, lengths, coords, target, grad_lrmsd, lrmsd_workspace,

@@ -74,6 +74,8 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
         int4* f4 = reinterpret_cast<int4*>(ws.fflag);
         for (int i = threadIdx.x; i < n / 4; i += kSchedThreads) f4[i] = make_int4(0, 0, 0, 0);
         for (int i = (n & ~3) + threadIdx.x; i < n; i += kSchedThreads) ws.fflag[i] = 0;
+        if (ws.tdone)  // fused training step: the backward's per-tile done flags
+            for (int i = threadIdx.x; i < n; i += kSchedThreads) ws.tdone[i] = 0;
     }
     auto len = [&](int b) {
         const int L = lengths[b];
@@ -287,8 +289,8 @@ tpl_status check_ws(void* ws, size_t have, size_t need) {
 
 }  // namespace
 
-size_t chain_ws_bytes(int B, int Lmax, bool per_residue) {
-    return chain_ws_layout(nullptr, B, Lmax, nullptr, per_residue);
+size_t chain_ws_bytes(int B, int Lmax, bool per_residue, bool step) {
+    return chain_ws_layout(nullptr, B, Lmax, nullptr, per_residue, step);
 }
 
 // One thread waits on `flag` with the chain kernels' bounded wait.
@@ -405,9 +407,9 @@ const char* tpl_version(void) { return "0.1.0"; }
 
 const char* tpl_last_error(void) { return t_last_error.c_str(); }
 
-size_t tpl_backbone_workspace_size(int B, int Lmax) { return chain_ws_bytes(B, Lmax, false); }
+size_t tpl_backbone_workspace_size(int B, int Lmax) { return chain_ws_bytes(B, Lmax, false, false); }
 
-size_t tpl_fullatom_workspace_size(int B, int Lmax) { return chain_ws_bytes(B, Lmax, true); }
+size_t tpl_fullatom_workspace_size(int B, int Lmax) { return chain_ws_bytes(B, Lmax, true, false); }
 
 size_t tpl_lrmsd_workspace_size(int P, int Nmax) {
     if (P <= 0 || Nmax < 0) return 256;
@@ -477,6 +479,52 @@ tpl_status tpl_fullatom_forward(const float* angles, const uint8_t* seq, const i
     cudaError_t e = launch_fullatom_forward(angles, seq, lengths, B, Lmax, Amax, coords, num_atoms,
                                             sched_mode(o, false), workspace, cfg, s);
     if (e != cudaSuccess) return cuda_fail(e, "fullatom_forward");
+    return ok();
+}
+
+size_t tpl_fullatom_lrmsd_workspace_size(int B, int Lmax) { return chain_ws_bytes(B, Lmax, true, true); }
+
+tpl_status tpl_fullatom_lrmsd_forward(const float* angles, const uint8_t* seq, const int32_t* lengths, int B,
+                                      int Lmax, int Amax, const float* target, float* coords, int32_t* num_atoms,
+                                      void* workspace, size_t workspace_bytes, const tpl_opts* opts,
+                                      tpl_stream stream) {
+    tpl_opts o = resolve(opts);
+    tpl_status st = check_opts(o);
+    if (st) return st;
+    const void* ptrs[6] = {angles, seq, lengths, target, coords, num_atoms};
+    if ((st = check_chain_args(B, Lmax, ptrs, 6))) return st;
+    if (Amax < 0 || Amax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Amax=%d must be a multiple of 4", Amax);
+    if (B == 0) return ok();
+    LaunchCfg cfg = fullatom_cfg(o);
+    if (!fullatom_cfg_supported(cfg.threads))
+        return fail(TPL_ERR_INVALID_ARG, "unsupported full-atom launch %d threads", cfg.threads);
+    if ((st = check_ws(workspace, workspace_bytes, tpl_fullatom_lrmsd_workspace_size(B, Lmax)))) return st;
+    cudaError_t e = launch_fullatom_lrmsd_forward(angles, seq, lengths, target, B, Lmax, Amax, coords, num_atoms,
+                                                  sched_mode(o, false), workspace, cfg,
+                                                  reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "fullatom_lrmsd_forward");
+    return ok();
+}
+
+tpl_status tpl_fullatom_lrmsd_backward(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
+                                       const float* coords, const float* target, const int32_t* num_atoms,
+                                       const float* grad_lrmsd, float* lrmsd, float* grad_angles, void* workspace,
+                                       size_t workspace_bytes, const tpl_opts* opts, tpl_stream stream) {
+    tpl_opts o = resolve(opts);
+    tpl_status st = check_opts(o);
+    if (st) return st;
+    const void* ptrs[8] = {seq, lengths, coords, target, num_atoms, grad_lrmsd, lrmsd, grad_angles};
+    if ((st = check_chain_args(B, Lmax, ptrs, 8))) return st;
+    if (Amax < 0 || Amax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Amax=%d must be a multiple of 4", Amax);
+    if (B == 0) return ok();
+    LaunchCfg cfg = fullatom_cfg(o);
+    if (!fullatom_cfg_supported(cfg.threads))
+        return fail(TPL_ERR_INVALID_ARG, "unsupported full-atom launch %d threads", cfg.threads);
+    if ((st = check_ws(workspace, workspace_bytes, tpl_fullatom_lrmsd_workspace_size(B, Lmax)))) return st;
+    cudaError_t e = launch_fullatom_lrmsd_backward(seq, lengths, coords, target, grad_lrmsd, num_atoms, lrmsd, B,
+                                                   Lmax, Amax, grad_angles, workspace, cfg,
+                                                   reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "fullatom_lrmsd_backward");
     return ok();
 }
 

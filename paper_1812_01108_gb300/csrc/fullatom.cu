@@ -185,16 +185,22 @@ __host__ __device__ constexpr int fa_bwd_min_blocks() {
     return NT >= 384 ? 2 : (NT >= 256 ? 4 : (NT >= 192 ? 5 : 8));
 }
 
-template <int NT>
+// LM: also reduce, per tile, the LRMSD moments (Section 4) of the tile's atoms
+// against `target`: sum dx, sum dy, sum dx dy^T, sum |dx|^2, sum |dy|^2 with
+// dx = x - x_0 (x the target, x_0 its first atom) and dy = y (the chain's
+// first atom, N of residue 0, is the origin: R_0 = I).
+template <int NT, bool LM>
 __global__ void __launch_bounds__(NT, fa_min_blocks<NT>()) fa_fwd_kernel(
     const float* __restrict__ angles, const uint8_t* __restrict__ seq,
     const int32_t* __restrict__ lengths, int Lmax, int Amax, float* __restrict__ coords,
-    int32_t* __restrict__ num_atoms, ChainWs ws, const __grid_constant__ FaTable tab) {
+    int32_t* __restrict__ num_atoms, ChainWs ws, const float* __restrict__ target,
+    const __grid_constant__ FaTable tab) {
     constexpr int NW = NT / 32;
     __shared__ FaTable s_tab;
     __shared__ RigidS s_rig[NW + 1];
     __shared__ int s_cnt[NW + 1];
     __shared__ int s_v, s_next;
+    __shared__ float s_mom[LM ? NW : 1][17];
     extern __shared__ float4 s_dyn[];
     float* stage = reinterpret_cast<float*>(s_dyn);  // tile-local atoms, 3 floats each
 
@@ -314,6 +320,43 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT>()) fa_fwd_kernel(
             if (threadIdx.x == 0) num_atoms[b] = end_atom;
             zero_range<NT>(out, 3 * min(end_atom, Amax), 3 * Amax);
         }
+        if constexpr (LM) {
+            const float* tg = target + (size_t)b * Amax * 3;
+            const float3 x0 = make_float3(__ldg(tg), __ldg(tg + 1), __ldg(tg + 2));
+            float m[17];
+#pragma unroll
+            for (int k = 0; k < 17; ++k) m[k] = 0.f;
+            for (int a = threadIdx.x; a < nout; a += NT) {
+                const float* xa = tg + 3 * (size_t)(pc + a);
+                const float3 dx = make_float3(__ldg(xa) - x0.x, __ldg(xa + 1) - x0.y, __ldg(xa + 2) - x0.z);
+                const float3 dy = make_float3(stage[3 * a], stage[3 * a + 1], stage[3 * a + 2]);
+                m[0] += dx.x; m[1] += dx.y; m[2] += dx.z;
+                m[3] += dy.x; m[4] += dy.y; m[5] += dy.z;
+                m[6] = fmaf(dx.x, dy.x, m[6]); m[7] = fmaf(dx.x, dy.y, m[7]); m[8] = fmaf(dx.x, dy.z, m[8]);
+                m[9] = fmaf(dx.y, dy.x, m[9]); m[10] = fmaf(dx.y, dy.y, m[10]); m[11] = fmaf(dx.y, dy.z, m[11]);
+                m[12] = fmaf(dx.z, dy.x, m[12]); m[13] = fmaf(dx.z, dy.y, m[13]); m[14] = fmaf(dx.z, dy.z, m[14]);
+                m[15] += f3_dot(dx, dx);
+                m[16] += f3_dot(dy, dy);
+            }
+            // block sum: warp shuffles, then the warp sums in a fixed order
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+            for (int k = 0; k < 17; ++k) {
+                float v = m[k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                m[k] = v;
+            }
+            if (lane == 0)
+#pragma unroll
+                for (int k = 0; k < 17; ++k) s_mom[warp][k] = m[k];
+            __syncthreads();
+            if (threadIdx.x < 17) {
+                float v = 0.f;
+                for (int w = 0; w < NW; ++w) v += s_mom[w][threadIdx.x];
+                ws.tmom[(size_t)(slot0 + t) * 20 + threadIdx.x] = v;
+            }
+        }
         v = next_tile(requested, &s_v);
     }
 }
@@ -356,7 +399,12 @@ __device__ __forceinline__ int block_scan_int(int x, int* s_cnt, int& total) {
 __device__ __forceinline__ float3 unit3(float3 v) { return f3_scale(rsqrtf(f3_dot(v, v)), v); }
 
 
-template <int NT, bool LR>
+// RES (with LR, the fused training step): the LRMSD gradient is formed
+// without its 1 / (N LRMSD) factor, each tile also sums its atoms' squared
+// residuals |y' - U x'|^2 (Section 4), and the chain's first tile -- taken
+// last -- waits for the chain's other tiles, forms LRMSD in FP64 and rescales
+// the chain's angle gradients.
+template <int NT, bool LR, bool RES>
 __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_kernel(
     const uint8_t* __restrict__ seq, const int32_t* __restrict__ lengths, int B, int Lmax, int Amax,
     const float* __restrict__ coords, const float* __restrict__ grad_coords,
@@ -365,6 +413,8 @@ __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_ker
     __shared__ FaTable s_tab;
     __shared__ float s6[6 * (NW + 1)];
     __shared__ int s_v;
+    __shared__ float s_res[NW];
+    __shared__ float s_scale;
     extern __shared__ float4 s_dyn[];
     float* st_r = reinterpret_cast<float*>(s_dyn);  // the tile's coordinates
 
@@ -408,6 +458,7 @@ __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_ker
         const bool in_range = valid && a0 >= pc && a0 + nat <= Amax && a0 - pc + nat <= NT * kMaxAtoms;
         cp_async_wait_all();
         __syncthreads();
+        float res_acc = 0.f;  // RES: this thread's squared residuals
         float gchi[kMaxGroups] = {0.f, 0.f, 0.f, 0.f};
         Sum6 all = sum6_zero(), nsum = sum6_zero(), csum = sum6_zero();
         float3 rN = make_float3(0.f, 0.f, 0.f), rCA = rN, rC = rN, rCprev = rN;
@@ -425,13 +476,15 @@ __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_ker
                 u2 = make_float3(__ldg(st + 6), __ldg(st + 7), __ldg(st + 8));
                 xc = make_float3(__ldg(st + 9), __ldg(st + 10), __ldg(st + 11));
                 yc = make_float3(__ldg(st + 12), __ldg(st + 13), __ldg(st + 14));
-                w = __ldg(lg.grad_lrmsd + b) * __ldg(st + 15);
+                w = __ldg(lg.grad_lrmsd + b) * (RES ? 1.f : __ldg(st + 15));
             }
             auto G = [&](int k) {
                 const float3 v = make_float3(__ldg(sg + 3 * k), __ldg(sg + 3 * k + 1), __ldg(sg + 3 * k + 2));
                 if constexpr (!LR) return v;
                 const float3 xp = f3_sub(v, xc), yp = f3_sub(R(k), yc);
-                return f3_scale(w, make_float3(yp.x - f3_dot(u0, xp), yp.y - f3_dot(u1, xp), yp.z - f3_dot(u2, xp)));
+                const float3 r = make_float3(yp.x - f3_dot(u0, xp), yp.y - f3_dot(u1, xp), yp.z - f3_dot(u2, xp));
+                if constexpr (RES) res_acc += f3_dot(r, r);
+                return f3_scale(w, r);
             };
             auto add = [&](Sum6& s, int k) {
                 const float3 g = G(k);
@@ -474,7 +527,9 @@ __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_ker
         block_suffix_sum6<NT>(own, s6, after, total);
         if (threadIdx.x == NT - 32) publish_suffix_agg(ws, slot0 + t, total);
         after = sum6_add(after, gather_suffix(ws, slot0, t, T));  // every warp gathers it
-        const int requested = request_tile(counter);  // after the last wait of this tile
+        // after the last wait of this tile (the chain's first tile of a fused
+        // step still waits for the chain's other tiles: it asks later)
+        int requested = (RES && t == 0) ? 0 : request_tile(counter);
         if (j < Lmax) {
             float gphi = 0.f, gpsi = 0.f, gomg = 0.f;
             if (in_range) {
@@ -497,6 +552,49 @@ __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_ker
             for (int i = min(Lmax, T * NT) + threadIdx.x; i < Lmax; i += NT)
 #pragma unroll
                 for (int r = 0; r < 7; ++r) ga[r * Lmax + i] = 0.f;
+        }
+        if constexpr (RES) {
+            // this tile's residual sum, then "done" once every thread's
+            // gradient writes are in
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) res_acc += __shfl_xor_sync(0xffffffffu, res_acc, o);
+            if ((threadIdx.x & 31) == 0) s_res[threadIdx.x >> 5] = res_acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float tot = 0.f;
+                for (int w2 = 0; w2 < NW; ++w2) tot += s_res[w2];
+                ws.tres[slot0 + t] = tot;
+                __threadfence();
+                flag_release(ws.tdone + slot0 + t, 1);
+            }
+            if (t == 0) {
+                // the chain's LRMSD from its tiles' residual sums (fixed order,
+                // FP64), then the factor 1 / (N LRMSD) on all its gradients
+                if (threadIdx.x == 0) {
+                    double sum = 0.0;
+                    for (int tp = 0; tp < T; ++tp) {
+                        if (tp > 0) wait_flag(ws.tdone + slot0 + tp);
+                        sum += (double)__ldcg(ws.tres + slot0 + tp);
+                    }
+                    const int n = lg.num_atoms[b] < Amax ? lg.num_atoms[b] : Amax;
+                    const double lr = n > 0 ? sqrt(sum / n) : 0.0;
+                    double scale = 0.0;
+                    if (lr >= 1e-12) {
+                        scale = 1.0 / (n * lr);
+                    } else if (n > 0) {
+                        flag_status(TPL_STATUS_ZERO_LRMSD);
+                    }
+                    lg.lrmsd_out[b] = (float)lr;
+                    s_scale = (float)scale;
+                }
+                __syncthreads();
+                const float sc = s_scale;
+                for (int i = threadIdx.x; i < 7 * L; i += NT) {
+                    float* q = ga + (i / L) * Lmax + (i % L);
+                    *q = __ldcg(q) * sc;
+                }
+                requested = request_tile(counter);
+            }
         }
         v = next_tile(requested, &s_v);
     }
@@ -849,31 +947,31 @@ cudaError_t smem_attr_once(K kernel, int bytes, bool* done_per_device) {
     return e;
 }
 
-template <int NT>
+template <int NT, bool LM = false>
 cudaError_t fa_fwd_t(const float* angles, const uint8_t* seq, const int32_t* lengths, int Lmax,
                      int Amax, float* coords, int32_t* num_atoms, const ChainWs& ws,
-                     cudaStream_t s) {
+                     cudaStream_t s, const float* target = nullptr) {
     const size_t smem = fa_fwd_smem<NT>();
     static bool done[64] = {false};
-    cudaError_t e = smem_attr_once(fa_fwd_kernel<NT>, (int)smem, done);
+    cudaError_t e = smem_attr_once(fa_fwd_kernel<NT, LM>, (int)smem, done);
     if (e != cudaSuccess) return e;
-    const int grid = persistent_grid((const void*)fa_fwd_kernel<NT>, NT, smem);
-    fa_fwd_kernel<NT><<<grid, NT, smem, s>>>(angles, seq, lengths, Lmax, Amax, coords, num_atoms,
-                                             ws, fa_table());
+    const int grid = persistent_grid((const void*)fa_fwd_kernel<NT, LM>, NT, smem);
+    fa_fwd_kernel<NT, LM><<<grid, NT, smem, s>>>(angles, seq, lengths, Lmax, Amax, coords, num_atoms,
+                                                 ws, target, fa_table());
     return cudaGetLastError();
 }
 
-template <int NT, bool LR>
+template <int NT, bool LR, bool RES = false>
 cudaError_t fa_bwd_coords_t(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
                             const float* coords, const float* grad_coords, float* grad_angles,
                             const ChainWs& ws, LrmsdGrad lg, cudaStream_t s) {
     const size_t smem = (size_t)(4 + NT * kMaxAtoms * 3) * sizeof(float);
     static bool done[64] = {false};
-    cudaError_t e = smem_attr_once(fa_bwd_coords_kernel<NT, LR>, (int)smem, done);
+    cudaError_t e = smem_attr_once(fa_bwd_coords_kernel<NT, LR, RES>, (int)smem, done);
     if (e != cudaSuccess) return e;
-    const int grid = persistent_grid((const void*)fa_bwd_coords_kernel<NT, LR>, NT, smem);
-    fa_bwd_coords_kernel<NT, LR><<<grid, NT, smem, s>>>(seq, lengths, B, Lmax, Amax, coords, grad_coords,
-                                                           grad_angles, ws, lg, fa_table());
+    const int grid = persistent_grid((const void*)fa_bwd_coords_kernel<NT, LR, RES>, NT, smem);
+    fa_bwd_coords_kernel<NT, LR, RES><<<grid, NT, smem, s>>>(seq, lengths, B, Lmax, Amax, coords, grad_coords,
+                                                                grad_angles, ws, lg, fa_table());
     return cudaGetLastError();
 }
 
@@ -977,6 +1075,50 @@ cudaError_t launch_fullatom_backward_lrmsd(const uint8_t* seq, const int32_t* le
         case 256: return fa_bwd_coords_t<256, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
         case 384: return fa_bwd_coords_t<384, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
         case 512: return fa_bwd_coords_t<512, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fullatom_lrmsd_forward(const float* angles, const uint8_t* seq, const int32_t* lengths,
+                                          const float* target, int B, int Lmax, int Amax, float* coords,
+                                          int32_t* num_atoms, int sched_mode, void* workspace, LaunchCfg cfg,
+                                          cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    ChainWs ws;
+    chain_ws_layout(workspace, B, Lmax, &ws, true, true);
+    cudaError_t e = launch_schedule(lengths, B, Lmax, cfg.threads, sched_mode, 1, ws, s);
+    if (e != cudaSuccess) return e;
+    switch (cfg.threads) {
+        case 64: e = fa_fwd_t<64, true>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s, target); break;
+        case 128: e = fa_fwd_t<128, true>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s, target); break;
+        case 192: e = fa_fwd_t<192, true>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s, target); break;
+        case 256: e = fa_fwd_t<256, true>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s, target); break;
+        case 384: e = fa_fwd_t<384, true>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s, target); break;
+        case 512: e = fa_fwd_t<512, true>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s, target); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    return launch_lrmsd_solve_tiles(coords, target, num_atoms, B, Amax, ws.tmom, ws.tmax, lengths, cfg.threads,
+                                    Lmax, ws.lstate, s);
+}
+
+cudaError_t launch_fullatom_lrmsd_backward(const uint8_t* seq, const int32_t* lengths, const float* coords,
+                                           const float* target, const float* grad_lrmsd,
+                                           const int32_t* num_atoms, float* lrmsd, int B, int Lmax, int Amax,
+                                           float* grad_angles, void* workspace, LaunchCfg cfg, cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    ChainWs ws;
+    chain_ws_layout(workspace, B, Lmax, &ws, true, true);
+    cudaError_t e = reset_backward_flags(ws, s);
+    if (e != cudaSuccess) return e;
+    LrmsdGrad lg{target, ws.lstate, grad_lrmsd, lrmsd, num_atoms};
+    switch (cfg.threads) {
+        case 64: return fa_bwd_coords_t<64, true, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
+        case 128: return fa_bwd_coords_t<128, true, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
+        case 192: return fa_bwd_coords_t<192, true, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
+        case 256: return fa_bwd_coords_t<256, true, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
+        case 384: return fa_bwd_coords_t<384, true, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
+        case 512: return fa_bwd_coords_t<512, true, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -14,9 +14,10 @@ struct LaunchCfg {
 };
 
 // Bytes of the chain workspace (tile list, look-back flags and aggregates,
-// tile-start frames; with per_residue, each residue's first atom) for B chains
-// of at most Lmax residues.
-size_t chain_ws_bytes(int B, int Lmax, bool per_residue);
+// tile-start frames; with per_residue, each residue's first atom; with step,
+// the fused training step's per-tile LRMSD partials) for B chains of at most
+// Lmax residues.
+size_t chain_ws_bytes(int B, int Lmax, bool per_residue, bool step);
 
 // K1 / K2: backbone FP32 scan kernels.
 bool backbone_cfg_supported(int threads, int res_per_thread);
@@ -55,6 +56,27 @@ cudaError_t launch_fullatom_backward_lrmsd(const uint8_t* seq, const int32_t* le
                                           const float* grad_lrmsd, const float* lrmsd_state,
                                           float* grad_angles, void* workspace, LaunchCfg cfg,
                                           cudaStream_t s);
+
+// The eigen-solve of K5 on per-tile moment partials (slot = chain * tiles_max
+// + tile, 20 floats each; tiles of `tile` residues of chain p): the fused
+// training step.  Writes the per-pair state (16 floats per pair).
+cudaError_t launch_lrmsd_solve_tiles(const float* input, const float* target, const int32_t* num_atoms,
+                                     int P, int Nmax, const float* tile_moments, int tiles_max,
+                                     const int32_t* lengths, int tile, int Lmax, float* state,
+                                     cudaStream_t s);
+
+// Fused training step on the full-atom model with the LRMSD loss (workspace of
+// chain_ws_bytes(B, Lmax, true, true)): forward = schedule, forward with
+// per-tile LRMSD moments, eigen-solve; backward = the LRMSD gradient formed in
+// the full-atom backward with the residual sums and the final 1 / (N LRMSD).
+cudaError_t launch_fullatom_lrmsd_forward(const float* angles, const uint8_t* seq, const int32_t* lengths,
+                                          const float* target, int B, int Lmax, int Amax, float* coords,
+                                          int32_t* num_atoms, int sched_mode, void* workspace, LaunchCfg cfg,
+                                          cudaStream_t s);
+cudaError_t launch_fullatom_lrmsd_backward(const uint8_t* seq, const int32_t* lengths, const float* coords,
+                                           const float* target, const float* grad_lrmsd,
+                                           const int32_t* num_atoms, float* lrmsd, int B, int Lmax, int Amax,
+                                           float* grad_angles, void* workspace, LaunchCfg cfg, cudaStream_t s);
 
 // K5 / K6: LRMSD.  The workspace layout is private to lrmsd.cu.
 size_t lrmsd_ws_bytes(int P, int Nmax);

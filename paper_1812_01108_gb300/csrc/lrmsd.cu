@@ -242,21 +242,28 @@ __device__ __forceinline__ double pick4(int i, double a, double b, double c, dou
 // cofactor (jb, i) of the adjugate row and row i of U -- so the dependent
 // FP64 chain is about a quarter as long; the FP32 estimate runs in all four
 // lanes alike.  No lane leaves early, so the quad shuffles see every lane.
+// With `lengths`, the partials are per tile of `tile` residues of chain p
+// (the fused training step's forward), not per chunk of atoms.
 __global__ void __launch_bounds__(32) lrmsd_solve_quad_kernel(
     const float* __restrict__ input, const float* __restrict__ target,
     const int32_t* __restrict__ num_atoms, int P, int Nmax, const float* __restrict__ part1,
-    int nch_max, float* __restrict__ state, int* __restrict__ counter) {
+    int nch_max, float* __restrict__ state, int* __restrict__ counter,
+    const int32_t* __restrict__ lengths = nullptr, int tile = 0, int Lmax = 0) {
     const unsigned full = 0xffffffffu;
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     const int sub = gid & 3, lane = threadIdx.x & 31;
     const bool active = (gid >> 2) < P;
     const int p = active ? (gid >> 2) : P - 1;
     const int n = pair_atoms(num_atoms, p, Nmax);
-    if (active && sub == 0) counter[p] = 0;
+    if (active && sub == 0 && counter) counter[p] = 0;
     float S[kSlot];
 #pragma unroll
     for (int k = 0; k < kSlot; ++k) S[k] = 0.f;
-    const int nch = num_chunks(n);
+    int nch = num_chunks(n);
+    if (lengths) {
+        const int L = min(max(lengths[p], 0), Lmax);
+        nch = L > 0 ? (L + tile - 1) / tile : 1;
+    }
     for (int c = 0; c < nch; ++c) {
         const float4* q = reinterpret_cast<const float4*>(part1 + ((size_t)p * nch_max + c) * kSlot);
 #pragma unroll
@@ -837,6 +844,16 @@ __global__ void __launch_bounds__(kRefNT) lrmsd_bwd_ref64_kernel(
 }  // namespace
 
 size_t lrmsd_ws_bytes(int P, int Nmax) { return ws_layout(P, Nmax).total; }
+
+cudaError_t launch_lrmsd_solve_tiles(const float* input, const float* target, const int32_t* num_atoms,
+                                     int P, int Nmax, const float* tile_moments, int tiles_max,
+                                     const int32_t* lengths, int tile, int Lmax, float* state,
+                                     cudaStream_t s) {
+    if (P == 0) return cudaSuccess;
+    lrmsd_solve_quad_kernel<<<(4 * P + 31) / 32, 32, 0, s>>>(input, target, num_atoms, P, Nmax, tile_moments,
+                                                            tiles_max, state, nullptr, lengths, tile, Lmax);
+    return cudaGetLastError();
+}
 
 const float* lrmsd_state(const void* ws, int P, int Nmax) {
     return reinterpret_cast<const float*>(static_cast<const char*>(ws) + ws_layout(P, Nmax).state);

@@ -53,6 +53,13 @@ struct ChainWs {
     int* bflag;      // [B * tmax + 4]: backward flags; word B * tmax is the backward work counter
     float4* bagg;    // [B * tmax][2] backward aggregate (c, g)
     int* ratom;      // [B * Lmax] first atom of each residue (full atom only; else null)
+    // fused training step only (else null): per tile, the LRMSD moments of its
+    // atoms (20 floats), the sum of its squared residuals, a done flag; per
+    // chain, the LRMSD state (U, centroids, 1 / (N LRMSD): 16 floats)
+    float* tmom;
+    float* tres;
+    int* tdone;
+    float* lstate;
     int tmax;        // tiles per chain for the smallest tile
     int slots;       // B * tmax
 };
@@ -66,7 +73,7 @@ __host__ __device__ inline int ws_tmax(int Lmax) {
 
 // Offsets of the regions; `base` may be null to only size the workspace.
 __host__ __device__ inline size_t chain_ws_layout(void* base, int B, int Lmax, ChainWs* w,
-                                                  bool per_residue = false) {
+                                                  bool per_residue = false, bool step = false) {
     const int tmax = ws_tmax(Lmax);
     const size_t slots = (size_t)(B > 0 ? B : 1) * tmax;
     size_t o = 0;
@@ -80,6 +87,14 @@ __host__ __device__ inline size_t chain_ws_layout(void* base, int B, int Lmax, C
     const size_t bagg = o; o = ws_align(o + slots * 2 * sizeof(float4));
     const size_t ratom = o;
     if (per_residue) o = ws_align(o + (size_t)(B > 0 ? B : 1) * (Lmax > 0 ? Lmax : 1) * sizeof(int));
+    const size_t tmom = o;
+    if (step) o = ws_align(o + slots * 20 * sizeof(float));
+    const size_t tres = o;
+    if (step) o = ws_align(o + slots * sizeof(float));
+    const size_t tdone = o;
+    if (step) o = ws_align(o + slots * sizeof(int));
+    const size_t lstate = o;
+    if (step) o = ws_align(o + (size_t)(B > 0 ? B : 1) * 16 * sizeof(float));
     if (w) {
         char* c = static_cast<char*>(base);
         w->hdr = reinterpret_cast<int*>(c + hdr);
@@ -91,6 +106,10 @@ __host__ __device__ inline size_t chain_ws_layout(void* base, int B, int Lmax, C
         w->bflag = reinterpret_cast<int*>(c + bflag);
         w->bagg = reinterpret_cast<float4*>(c + bagg);
         w->ratom = per_residue ? reinterpret_cast<int*>(c + ratom) : nullptr;
+        w->tmom = step ? reinterpret_cast<float*>(c + tmom) : nullptr;
+        w->tres = step ? reinterpret_cast<float*>(c + tres) : nullptr;
+        w->tdone = step ? reinterpret_cast<int*>(c + tdone) : nullptr;
+        w->lstate = step ? reinterpret_cast<float*>(c + lstate) : nullptr;
         w->tmax = tmax;
         w->slots = (int)slots;
     }

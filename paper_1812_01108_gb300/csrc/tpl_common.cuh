@@ -449,6 +449,9 @@ struct LrmsdGrad {
     const float* target;
     const float* state;
     const float* grad_lrmsd;
+    // fused training step: LRMSD per chain out, atoms per chain in
+    float* lrmsd_out;
+    const int32_t* num_atoms;
 };
 
 __device__ __forceinline__ int clamp_length(const int32_t* lengths, int b, int Lmax) {

@@ -15,6 +15,7 @@ pytestmark = pytest.mark.gpu
 
 COORD_TOL = 2e-3
 GRAD_TOL = 1e-4
+LRMSD_TOL = 1e-5
 LENGTHS = np.array([0, 1, 2, 31, 64, 255, 256, 257, 350, 513, 700], np.int32)
 
 
@@ -187,3 +188,54 @@ def test_fused_lrmsd_backward_equals_the_two_calls_and_the_oracle(threads):
     g64 = oracle.lrmsd_backward(host(w).astype(np.float64), c32, t32, n32)
     ga64 = oracle.fullatom_backward(a, seq, lengths, g64)
     assert rel_err(f, ga64) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("threads", [384, 256, 64])
+def test_fused_training_step_matches_the_separate_calls_and_the_oracle(threads):
+    """tpl_fullatom_lrmsd_forward / _backward (moments in the forward's tiles,
+    residuals and the 1 / (N LRMSD) factor in the backward) against
+    tpl_fullatom_forward + tpl_lrmsd_forward + tpl_fullatom_backward_lrmsd and
+    against the oracle chain on the same FP32 coordinates."""
+    d = require_gpu()
+    rng = workloads.rng_for(4, salt=33)
+    lengths = np.array([700, 333, 64, 1, 0, 257, 700, 9], np.int32)
+    a, seq = workloads.fullatom_inputs(lengths, rng)
+    ta = workloads.perturb_angles(a, lengths, rng, rows=(0, 1, 3, 4, 5, 6))
+    Amax = workloads.pad_to(oracle.max_atoms(seq, lengths))
+    B, _, Lmax = a.shape
+    A, S, Ln = dev(a, d), dev(seq, d), dev(lengths, d)
+    opts = {"threads": threads}
+    fa_ws = torch.empty(tpl.tpl_fullatom_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    tgt = torch.zeros((B, Amax, 3), device=d)
+    na = torch.zeros((B,), dtype=torch.int32, device=d)
+    tpl.tpl_fullatom_forward(dev(ta, d), S, Ln, tgt, na, fa_ws, opts)
+    w = dev(np.linspace(0.5, 2.0, B).astype(np.float32), d)
+    # separate calls
+    c1 = torch.zeros_like(tgt)
+    tpl.tpl_fullatom_forward(A, S, Ln, c1, na, fa_ws, opts)
+    l1 = torch.zeros((B,), device=d)
+    lr_ws = torch.empty(tpl.tpl_lrmsd_workspace_size(B, Amax), dtype=torch.uint8, device=d)
+    tpl.tpl_lrmsd_forward(c1, tgt, na, l1, lr_ws)
+    g1 = torch.full_like(A, float("nan"))
+    tpl.tpl_fullatom_backward_lrmsd(A, S, Ln, c1, tgt, w, lr_ws, g1, fa_ws, opts)
+    # fused step
+    st_ws = torch.empty(tpl.tpl_fullatom_lrmsd_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    c2 = torch.full_like(tgt, float("nan"))
+    n2 = torch.full((B,), -1, dtype=torch.int32, device=d)
+    tpl.tpl_fullatom_lrmsd_forward(A, S, Ln, tgt, c2, n2, st_ws, opts)
+    l2 = torch.full((B,), float("nan"), device=d)
+    g2 = torch.full_like(A, float("nan"))
+    tpl.tpl_fullatom_lrmsd_backward(S, Ln, c2, tgt, n2, w, l2, g2, st_ws, opts)
+    torch.cuda.synchronize()
+    assert tpl.tpl_get_status() & ~tpl.STATUS_ZERO_LRMSD == 0
+    assert np.array_equal(host(c1), host(c2)) and np.array_equal(host(na), host(n2))
+    m = lengths >= 2  # one residue or none: congruent structures, LRMSD 0 and no gradient
+    assert np.abs(host(l1) - host(l2))[m].max() <= 1e-5
+    assert rel_err(host(g2)[m], host(g1)[m]) <= 1e-4
+    c32, t32, n32 = host(c2), host(tgt), host(n2)
+    assert np.abs(host(l2) - oracle.lrmsd_forward(c32, t32, n32))[m].max() <= LRMSD_TOL
+    g64 = oracle.lrmsd_backward(host(w).astype(np.float64), c32, t32, n32)
+    ga64 = oracle.fullatom_backward(a, seq, lengths, g64)
+    assert rel_err(host(g2)[m], ga64[m]) <= GRAD_TOL
+    for b, L in enumerate(lengths):
+        assert np.all(host(g2)[b, :, L:] == 0)
