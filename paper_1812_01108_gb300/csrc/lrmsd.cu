@@ -256,15 +256,26 @@ __global__ void __launch_bounds__(32) lrmsd_solve_quad_kernel(
     const int p = active ? (gid >> 2) : P - 1;
     const int n = pair_atoms(num_atoms, p, Nmax);
     if (active && sub == 0 && counter) counter[p] = 0;
-    float S[kSlot];
-#pragma unroll
-    for (int k = 0; k < kSlot; ++k) S[k] = 0.f;
     int nch = num_chunks(n);
     if (lengths) {
         const int L = min(max(lengths[p], 0), Lmax);
         nch = L > 0 ? (L + tile - 1) / tile : 1;
     }
-    for (int c = 0; c < nch; ++c) {
+    // the pair's first atoms, and the chunk partials split over the quad's
+    // lanes (lane i sums chunks i, i + 4, ...), so the loads go out together
+    const float* x = target + (size_t)p * Nmax * 3;
+    const float* y = input + (size_t)p * Nmax * 3;
+    float x0[3] = {0.f, 0.f, 0.f}, y0[3] = {0.f, 0.f, 0.f};
+    if (n > 0)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            x0[a] = x[a];
+            y0[a] = y[a];
+        }
+    float S[kSlot];
+#pragma unroll
+    for (int k = 0; k < kSlot; ++k) S[k] = 0.f;
+    for (int c = sub; c < nch; c += 4) {
         const float4* q = reinterpret_cast<const float4*>(part1 + ((size_t)p * nch_max + c) * kSlot);
 #pragma unroll
         for (int k = 0; k < kSlot / 4; ++k) {
@@ -272,20 +283,25 @@ __global__ void __launch_bounds__(32) lrmsd_solve_quad_kernel(
             S[4 * k] += v.x; S[4 * k + 1] += v.y; S[4 * k + 2] += v.z; S[4 * k + 3] += v.w;
         }
     }
+#pragma unroll
+    for (int k = 0; k < kMom; ++k) {  // fixed-order quad sum: (0 + 1) + (2 + 3) in every lane
+        const float o1 = __shfl_xor_sync(full, S[k], 1);
+        const float lo = (sub & 1) ? o1 + S[k] : S[k] + o1;
+        const float o2 = __shfl_xor_sync(full, lo, 2);
+        S[k] = (sub & 2) ? o2 + lo : lo + o2;
+    }
     float xc[3] = {0.f, 0.f, 0.f}, yc[3] = {0.f, 0.f, 0.f}, r[9], e0 = 0.f;
 #pragma unroll
     for (int k = 0; k < 9; ++k) r[k] = 0.f;
     if (n > 0) {
-        const float* x = target + (size_t)p * Nmax * 3;
-        const float* y = input + (size_t)p * Nmax * 3;
         const float inv = 1.f / n;
         float mx[3], my[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             mx[a] = S[a] * inv;
             my[a] = S[3 + a] * inv;
-            xc[a] = x[a] + mx[a];
-            yc[a] = y[a] + my[a];
+            xc[a] = x0[a] + mx[a];
+            yc[a] = y0[a] + my[a];
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a)
@@ -359,8 +375,7 @@ __global__ void __launch_bounds__(32) lrmsd_solve_quad_kernel(
     double s = 0.0;
     if (nn > 0.0) {
         s = (double)rsqrtf((float)nn);
-        s = s * fma(-0.5 * nn * s, s, 1.5);  // Newton steps for 1/sqrt(nn)
-        s = s * fma(-0.5 * nn * s, s, 1.5);
+        s = s * fma(-0.5 * nn * s, s, 1.5);  // one Newton step: relative error about 1e-14
     }
     const double qn = qc * s;
     const int base = lane & ~3;
