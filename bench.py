@@ -358,9 +358,8 @@ def setup_training_step(args, tpl, torch, dev, d):
 
     st = Step()
     res = int(lengths.sum())
-    solve = "lrmsd_solve_quad_kernel" if B <= 8192 else "lrmsd_solve_kernel"
     st.kernels = {"fullatom_forward": ["schedule_kernel", "fa_fwd_kernel"],
-                  "lrmsd_forward": ["lrmsd_moments_kernel", solve, "lrmsd_residual_kernel"]}
+                  "lrmsd_forward": ["lrmsd_moments_kernel", "lrmsd_residual_kernel"]}
     st.alg = {"fullatom_forward": res * (28 + 1) + 12 * n_atoms, "lrmsd_forward": 24 * n_atoms}
     st_ws = None
     if args.fusion == "step" and args.bwd == "coords":
@@ -373,7 +372,7 @@ def setup_training_step(args, tpl, torch, dev, d):
             ("lrmsd_step_backward",
              lambda: tpl.tpl_fullatom_lrmsd_backward(S, Ln, coords, target, na, wgt, lr, gang, st_ws, opts)),
         ]
-        st.kernels = {"lrmsd_step_forward": ["schedule_kernel", "fa_fwd_kernel", "lrmsd_solve_quad_kernel"],
+        st.kernels = {"lrmsd_step_forward": ["schedule_kernel", "fa_fwd_kernel", "lrmsd_solve_tiles_kernel"],
                       "lrmsd_step_backward": ["fa_bwd_coords_kernel"]}
         # forward: angles and sequence in, coordinates out, target read for the moments;
         # backward: angles and sequence in, angle gradient out, coordinates and target read
@@ -473,9 +472,8 @@ def setup_backbone_uneven(args, tpl, torch, dev, d):
     res = int(lengths.sum())
 
     st = Step()
-    solve = "lrmsd_solve_quad_kernel" if B <= 8192 else "lrmsd_solve_kernel"
     st.kernels = {"backbone_forward": ["schedule_kernel", "bb_fwd_kernel"],
-                  "lrmsd_forward": ["lrmsd_moments_kernel", solve, "lrmsd_residual_kernel"]}
+                  "lrmsd_forward": ["lrmsd_moments_kernel", "lrmsd_residual_kernel"]}
     st.alg = {"backbone_forward": 48 * res, "lrmsd_forward": 24 * n_atoms}
     if args.unfused or args.bwd != "coords":
         st.calls = [
@@ -550,7 +548,7 @@ def setup_lrmsd_batch(args, tpl, torch, dev, d):
     st = Step()
     st.calls = [("lrmsd_forward", lambda: tpl.tpl_lrmsd_forward(X, Y, NA, lr, ws)),
                 ("lrmsd_backward", lambda: tpl.tpl_lrmsd_backward(up, X, Y, NA, gx, ws))]
-    st.kernels = {"lrmsd_forward": ["lrmsd_moments_kernel", "lrmsd_solve_kernel", "lrmsd_residual_kernel"],
+    st.kernels = {"lrmsd_forward": ["lrmsd_moments_kernel", "lrmsd_residual_kernel"],
                   "lrmsd_backward": ["lrmsd_grad_kernel"]}
     st.launches = {k: len(v) for k, v in st.kernels.items()}
     st.alg = {"lrmsd_forward": 24 * n_atoms, "lrmsd_backward": 36 * n_atoms}

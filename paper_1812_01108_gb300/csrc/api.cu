@@ -607,7 +607,7 @@ tpl_status tpl_fullatom_backward(const float* angles, const uint8_t* seq, const 
 static tpl_status check_pair_args(int P, int Nmax, const void* const* ptrs, int nptr) {
     if (P < 0 || Nmax < 0) return fail(TPL_ERR_INVALID_ARG, "P=%d Nmax=%d must be >= 0", P, Nmax);
     if (Nmax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Nmax=%d must be a multiple of 4", Nmax);
-    if ((long long)P * ((Nmax + 2047) / 2048 + 1) > 0x7fffffffLL)
+    if ((long long)P * ((Nmax + 255) / 256 + 1) > 0x7fffffffLL)
         return fail(TPL_ERR_BAD_SHAPE, "P=%d x Nmax=%d too large for one call", P, Nmax);
     if (P == 0) return TPL_OK;
     for (int i = 0; i < nptr; ++i) {

@@ -19,6 +19,10 @@ struct LaunchCfg {
 // Lmax residues.
 size_t chain_ws_bytes(int B, int Lmax, bool per_residue, bool step);
 
+// CTAs of a persistent launch of `kernel`: SMs x resident CTAs per SM (cached
+// per kernel and device).
+int persistent_grid(const void* kernel, int threads, size_t smem);
+
 // K1 / K2: backbone FP32 scan kernels.
 bool backbone_cfg_supported(int threads, int res_per_thread);
 cudaError_t launch_backbone_forward(const float* angles, const int32_t* lengths, int B, int Lmax,

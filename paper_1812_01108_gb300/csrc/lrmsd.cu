@@ -1,22 +1,30 @@
 // LRMSD of the paper (Section 4) on sm_103a.
 //
-// Forward, three launches:
-//  K5a lrmsd_moments: one CTA per (pair, chunk), 2048 atoms per chunk.  Each CTA
-//      streams its chunk once (16-byte loads) and reduces, in FP32, the
-//      moments shifted by the pair's first atom: sum dx, sum dy, sum dx dy^T
-//      (x = target, y = input, as in the paper's R = sum x y^T).
-//  K5b lrmsd_solve: one thread per pair.  Sums the chunk partials, centres R,
-//      builds the 4x4 matrix T(R), estimates its largest eigenpair in FP32
-//      (Newton's method on the characteristic polynomial, as in the
-//      quaternion-characteristic-polynomial approach of Theobald, Acta Cryst.
-//      A61 (2005) 478, then an adjugate column) and solves it in FP64
-//      (Rayleigh quotient of T, adjugate of T - lambda I), then U(q).
-//  K5c lrmsd_residual: one CTA per (pair, chunk).  LRMSD^2 = (sum |x'|^2 + |y'|^2 -
-//      2 lambda)/N equals sum |y'_i - U x'_i|^2 / N at the optimum; the
-//      residual form has no cancellation, so it is summed in FP32 per chunk and
-//      the chunk partials in FP64 by the last CTA of the pair.
+// The atoms of a pair are cut into chunks of 256 (eight atoms per lane of one
+// warp).  The streaming kernels give each pair `wpp` warps (chosen from the
+// batch size so that the GPU is full: one warp per pair for large batches,
+// up to one per chunk for a few long pairs); warp r of a pair takes chunks
+// r, r + wpp, ... and stores one partial, so no warp waits on another.
+//
+// Forward, four launches:
+//  K5a lrmsd_moments: per warp, the moments shifted by the pair's first atom
+//      in FP32 -- sum dx, sum dy, sum dx dy^T, sum |dx|^2, sum |dy|^2 (x =
+//      target, y = input, as in the paper's R = sum x y^T).
+//  K5b lrmsd_solve: four lanes per pair sum its partials, centre R, estimate
+//      the largest eigenpair of the 4x4 matrix T(R) in FP32 (Newton's method
+//      on the characteristic polynomial, as in the quaternion-characteristic-
+//      polynomial approach of Theobald, Acta Cryst. A61 (2005) 478, then an
+//      adjugate column) and solve it in FP64 (Rayleigh quotient of T,
+//      adjugate of T - lambda I), then U(q).
+//  K5c lrmsd_residual: LRMSD^2 = (sum |x'|^2 + |y'|^2 - 2 lambda)/N equals
+//      sum |y'_i - U x'_i|^2 / N at the optimum; the residual form has no
+//      cancellation, so it is summed in FP32 per chunk and in FP64 over the
+//      warp's chunks.
+//  K5d lrmsd_finalize: four lanes per pair sum the warps' partials in FP64:
+//      LRMSD and the gradient scale 1 / (N LRMSD).
 // Backward:
 //  K6 lrmsd_grad: grad_y_i = w (y'_i - U x'_i) / (N LRMSD).
+// Every sum runs in a fixed order, so the results are the same from run to run.
 #include <mutex>
 
 #include "kernels.h"
@@ -26,15 +34,15 @@ namespace tpl {
 
 namespace {
 
-constexpr int kNT = 256;     // threads per CTA
-constexpr int kAPT = 8;      // atoms per thread (two groups of 4)
-constexpr int kChunk = kNT * kAPT;
+constexpr int kWNT = 128;    // threads per CTA: four independent warp workers
+constexpr int kWarps = kWNT / 32;
+constexpr int kWC = 256;     // atoms per chunk: one warp, two groups of 4 atoms per lane
 constexpr int kMom = 17;     // sum dx (3), sum dy (3), sum dx dy^T (9), sum |dx|^2, sum |dy|^2
 constexpr int kSlot = 20;    // floats per chunk partial (5 float4)
-constexpr int kQuadSolveMaxPairs = 8192;  // up to here four lanes share a pair's eigen-solve
+constexpr unsigned kFull = 0xffffffffu;
 
 struct WsLayout {
-    size_t part1, part2, state, lr64, counter, total;
+    size_t part1, part2, state, total;
     int nch;
 };
 
@@ -42,20 +50,17 @@ __host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) & ~si
 
 __host__ __device__ constexpr WsLayout ws_layout(int P, int Nmax) {
     WsLayout w{};
-    w.nch = (Nmax + kChunk - 1) / kChunk;
+    w.nch = (Nmax + kWC - 1) / kWC;
     if (w.nch < 1) w.nch = 1;
-    size_t o = 0;
+    size_t o = 0;  // partials: room for one warp per chunk
     w.part1 = o; o = align256(o + (size_t)P * w.nch * kSlot * sizeof(float));
-    w.part2 = o; o = align256(o + (size_t)P * w.nch * sizeof(float));
+    w.part2 = o; o = align256(o + (size_t)P * w.nch * sizeof(double));
     w.state = o; o = align256(o + (size_t)P * 16 * sizeof(float));  // U(9) xc(3) yc(3) scale
-    w.lr64 = o; o = align256(o + (size_t)P * sizeof(double));
-    w.counter = o; o = align256(o + (size_t)P * sizeof(int));
     w.total = o;
     return w;
 }
 
-__device__ __forceinline__ int pair_atoms(const int32_t* num_atoms, int p, int Nmax) {
-    int n = num_atoms[p];
+__device__ __forceinline__ int checked_atoms(int n, int Nmax) {
     if (n < 0 || n > Nmax) {
         flag_status(TPL_STATUS_BAD_LENGTH);
         n = n < 0 ? 0 : Nmax;
@@ -63,7 +68,15 @@ __device__ __forceinline__ int pair_atoms(const int32_t* num_atoms, int p, int N
     return n;
 }
 
-__device__ __forceinline__ int num_chunks(int n) { return n <= 0 ? 1 : (n + kChunk - 1) / kChunk; }
+__device__ __forceinline__ int pair_atoms(const int32_t* num_atoms, int p, int Nmax) {
+    return checked_atoms(num_atoms[p], Nmax);
+}
+
+__device__ __forceinline__ int num_chunks(int n) { return n <= 0 ? 1 : (n + kWC - 1) / kWC; }
+
+// Partials of a pair: one per warp that has a chunk.
+__device__ __forceinline__ int num_parts(int n, int wpp) { return min(wpp, num_chunks(n)); }
+
 
 // Four consecutive atoms (12 floats, 16-byte aligned) into xyz[4].
 __device__ __forceinline__ void load4(const float* __restrict__ p, float3 (&v)[4]) {
@@ -75,73 +88,24 @@ __device__ __forceinline__ void load4(const float* __restrict__ p, float3 (&v)[4
     v[3] = make_float3(c.y, c.z, c.w);
 }
 
+// Butterfly sum: every lane ends with the same total.
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
 
-// ---------------------------------------------------------------------------
-// K5a
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kNT) lrmsd_moments_kernel(const float* __restrict__ input,
-                                                            const float* __restrict__ target,
-                                                            const int32_t* __restrict__ num_atoms,
-                                                            int P, int Nmax, float* __restrict__ part1,
-                                                            int nch_max) {
-    __shared__ float s_red[kNT / 32][kMom];
-    const int p = blockIdx.x / nch_max, c = blockIdx.x % nch_max;
-    const int n = pair_atoms(num_atoms, p, Nmax);
-    if (c >= num_chunks(n)) return;
-    const float* x = target + (size_t)p * Nmax * 3;
-    const float* y = input + (size_t)p * Nmax * 3;
-    float3 sx = make_float3(0.f, 0.f, 0.f), sy = sx;
-    if (n > 0) {
-        sx = make_float3(__ldg(x), __ldg(x + 1), __ldg(x + 2));
-        sy = make_float3(__ldg(y), __ldg(y + 1), __ldg(y + 2));
-    }
-    float m[kMom];
-#pragma unroll
-    for (int k = 0; k < kMom; ++k) m[k] = 0.f;
-#pragma unroll
-    for (int s = 0; s < kAPT / 4; ++s) {
-        const int i0 = c * kChunk + 4 * (threadIdx.x + kNT * s);
-        if (i0 < n) {
-            float3 xv[4], yv[4];
-            load4(x + 3 * (size_t)i0, xv);
-            load4(y + 3 * (size_t)i0, yv);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (i0 + q < n) {
-                    const float3 dx = f3_sub(xv[q], sx), dy = f3_sub(yv[q], sy);
-                    m[0] += dx.x; m[1] += dx.y; m[2] += dx.z;
-                    m[3] += dy.x; m[4] += dy.y; m[5] += dy.z;
-                    m[6] = fmaf(dx.x, dy.x, m[6]); m[7] = fmaf(dx.x, dy.y, m[7]); m[8] = fmaf(dx.x, dy.z, m[8]);
-                    m[9] = fmaf(dx.y, dy.x, m[9]); m[10] = fmaf(dx.y, dy.y, m[10]); m[11] = fmaf(dx.y, dy.z, m[11]);
-                    m[12] = fmaf(dx.z, dy.x, m[12]); m[13] = fmaf(dx.z, dy.y, m[13]); m[14] = fmaf(dx.z, dy.z, m[14]);
-                    m[15] += f3_dot(dx, dx);
-                    m[16] += f3_dot(dy, dy);
-                }
-            }
-        }
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < kMom; ++k) {
-        const float v = warp_sum(m[k]);
-        if (lane == 0) s_red[warp][k] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < kMom) {
-        float v = 0.f;
-#pragma unroll
-        for (int w = 0; w < kNT / 32; ++w) v += s_red[w][threadIdx.x];
-        part1[((size_t)p * nch_max + c) * kSlot + threadIdx.x] = v;
-    }
+// Fixed-order sum over the four lanes of a quad, (0 + 1) + (2 + 3) in every lane.
+template <typename T>
+__device__ __forceinline__ T quad_sum(T v, int sub) {
+    const T o1 = __shfl_xor_sync(kFull, v, 1);
+    const T lo = (sub & 1) ? o1 + v : v + o1;
+    const T o2 = __shfl_xor_sync(kFull, lo, 2);
+    return (sub & 2) ? o2 + lo : lo + o2;
 }
 
 // ---------------------------------------------------------------------------
-// K5b
+// Eigen-solve of T(R) (part of K5a)
 // ---------------------------------------------------------------------------
 // Adjugate of a symmetric 4x4 (float): the same Laplace expansion in FP32,
 // used only for the starting eigenvector.
@@ -165,24 +129,6 @@ __device__ __forceinline__ float adjugate4f(float a00, float a01, float a02, flo
     m[15] = a20 * s3 - a21 * s1 + a22 * s0;
     m[1] = m[4]; m[2] = m[8]; m[3] = m[12]; m[6] = m[9]; m[7] = m[13]; m[11] = m[14];
     return s0 * c5 - s1 * c4 + s2 * c3 + s3 * c2 - s4 * c1 + s5 * c0;
-}
-
-// Cofactor (R, C) of a 4x4 matrix: signed determinant of the 3x3 minor.
-template <int R, int C>
-__device__ __forceinline__ double cofactor(const double (&A)[4][4]) {
-    constexpr int r0 = R == 0 ? 1 : 0, r1 = R <= 1 ? 2 : 1, r2 = R <= 2 ? 3 : 2;
-    constexpr int c0 = C == 0 ? 1 : 0, c1 = C <= 1 ? 2 : 1, c2 = C <= 2 ? 3 : 2;
-    const double d = A[r0][c0] * (A[r1][c1] * A[r2][c2] - A[r1][c2] * A[r2][c1]) -
-                     A[r0][c1] * (A[r1][c0] * A[r2][c2] - A[r1][c2] * A[r2][c0]) +
-                     A[r0][c2] * (A[r1][c0] * A[r2][c1] - A[r1][c1] * A[r2][c0]);
-    return ((R + C) & 1) ? -d : d;
-}
-template <int R>
-__device__ __forceinline__ void adj_row(const double (&A)[4][4], double (&q)[4]) {
-    q[0] = cofactor<R, 0>(A);
-    q[1] = cofactor<R, 1>(A);
-    q[2] = cofactor<R, 2>(A);
-    q[3] = cofactor<R, 3>(A);
 }
 
 // FP32 estimate of the largest eigenpair of T(R) for R scaled to |R|_F = 1
@@ -237,59 +183,15 @@ __device__ __forceinline__ double pick4(int i, double a, double b, double c, dou
     return i == 0 ? a : (i == 1 ? b : (i == 2 ? c : d));
 }
 
-// Quad form of the eigen-solve for small batches: four lanes per pair split
-// the FP64 refinement -- lane i forms row i of T q for the Rayleigh quotient,
-// cofactor (jb, i) of the adjugate row and row i of U -- so the dependent
-// FP64 chain is about a quarter as long; the FP32 estimate runs in all four
-// lanes alike.  No lane leaves early, so the quad shuffles see every lane.
-// With `lengths`, the partials are per tile of `tile` residues of chain p
-// (the fused training step's forward), not per chunk of atoms.
-__global__ void __launch_bounds__(32) lrmsd_solve_quad_kernel(
-    const float* __restrict__ input, const float* __restrict__ target,
-    const int32_t* __restrict__ num_atoms, int P, int Nmax, const float* __restrict__ part1,
-    int nch_max, float* __restrict__ state, int* __restrict__ counter,
-    const int32_t* __restrict__ lengths = nullptr, int tile = 0, int Lmax = 0) {
-    const unsigned full = 0xffffffffu;
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int sub = gid & 3, lane = threadIdx.x & 31;
-    const bool active = (gid >> 2) < P;
-    const int p = active ? (gid >> 2) : P - 1;
-    const int n = pair_atoms(num_atoms, p, Nmax);
-    if (active && sub == 0 && counter) counter[p] = 0;
-    int nch = num_chunks(n);
-    if (lengths) {
-        const int L = min(max(lengths[p], 0), Lmax);
-        nch = L > 0 ? (L + tile - 1) / tile : 1;
-    }
-    // the pair's first atoms, and the chunk partials split over the quad's
-    // lanes (lane i sums chunks i, i + 4, ...), so the loads go out together
-    const float* x = target + (size_t)p * Nmax * 3;
-    const float* y = input + (size_t)p * Nmax * 3;
-    float x0[3] = {0.f, 0.f, 0.f}, y0[3] = {0.f, 0.f, 0.f};
-    if (n > 0)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            x0[a] = x[a];
-            y0[a] = y[a];
-        }
-    float S[kSlot];
-#pragma unroll
-    for (int k = 0; k < kSlot; ++k) S[k] = 0.f;
-    for (int c = sub; c < nch; c += 4) {
-        const float4* q = reinterpret_cast<const float4*>(part1 + ((size_t)p * nch_max + c) * kSlot);
-#pragma unroll
-        for (int k = 0; k < kSlot / 4; ++k) {
-            const float4 v = q[k];
-            S[4 * k] += v.x; S[4 * k + 1] += v.y; S[4 * k + 2] += v.z; S[4 * k + 3] += v.w;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < kMom; ++k) {  // fixed-order quad sum: (0 + 1) + (2 + 3) in every lane
-        const float o1 = __shfl_xor_sync(full, S[k], 1);
-        const float lo = (sub & 1) ? o1 + S[k] : S[k] + o1;
-        const float o2 = __shfl_xor_sync(full, lo, 2);
-        S[k] = (sub & 2) ? o2 + lo : lo + o2;
-    }
+// Eigen-solve of one pair by the four lanes of a quad (sub = lane & 3), from
+// the summed moments S: lane i forms row i of T q for the Rayleigh quotient,
+// cofactor (jb, i) of the adjugate row and row i of U, so the dependent FP64
+// chain is about a quarter as long; the FP32 estimate runs in all four lanes
+// alike.  Every lane of the warp must call it (quad shuffles); only lanes with
+// `store` write the pair's state st: U (9), xc (3), yc (3), 0.
+__device__ __forceinline__ void quad_eigen_solve(const float (&S)[kSlot], const float (&x0)[3],
+                                                 const float (&y0)[3], int n, int sub, int lane,
+                                                 bool store, float* __restrict__ st) {
     float xc[3] = {0.f, 0.f, 0.f}, yc[3] = {0.f, 0.f, 0.f}, r[9], e0 = 0.f;
 #pragma unroll
     for (int k = 0; k < 9; ++k) r[k] = 0.f;
@@ -303,6 +205,7 @@ __global__ void __launch_bounds__(32) lrmsd_solve_quad_kernel(
             xc[a] = x0[a] + mx[a];
             yc[a] = y0[a] + my[a];
         }
+        // centred correlation R_ab = sum x'_a y'_b and E0 = sum |x'|^2 + |y'|^2
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -341,8 +244,8 @@ __global__ void __launch_bounds__(32) lrmsd_solve_quad_kernel(
 #pragma unroll
     for (int k = 0; k < 4; ++k) w = fma(pick4(sub, T[0][k], T[1][k], T[2][k], T[3][k]), pick4(k, qa0, qa1, qa2, qa3), w);
     double num = pick4(sub, qa0, qa1, qa2, qa3) * w;
-    num += __shfl_xor_sync(full, num, 1);
-    num += __shfl_xor_sync(full, num, 2);
+    num += __shfl_xor_sync(kFull, num, 1);
+    num += __shfl_xor_sync(kFull, num, 2);
     const double den = qa0 * qa0 + qa1 * qa1 + qa2 * qa2 + qa3 * qa3;
     double l64 = 0.0;
     if (den > 0.0) {
@@ -370,8 +273,8 @@ __global__ void __launch_bounds__(32) lrmsd_solve_quad_kernel(
                 M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
     if ((jb + sub) & 1) qc = -qc;
     double nn = qc * qc;
-    nn += __shfl_xor_sync(full, nn, 1);
-    nn += __shfl_xor_sync(full, nn, 2);
+    nn += __shfl_xor_sync(kFull, nn, 1);
+    nn += __shfl_xor_sync(kFull, nn, 2);
     double s = 0.0;
     if (nn > 0.0) {
         s = (double)rsqrtf((float)nn);
@@ -379,8 +282,8 @@ __global__ void __launch_bounds__(32) lrmsd_solve_quad_kernel(
     }
     const double qn = qc * s;
     const int base = lane & ~3;
-    double q0 = __shfl_sync(full, qn, base), q1 = __shfl_sync(full, qn, base + 1);
-    double q2 = __shfl_sync(full, qn, base + 2), q3 = __shfl_sync(full, qn, base + 3);
+    double q0 = __shfl_sync(kFull, qn, base), q1 = __shfl_sync(kFull, qn, base + 1);
+    double q2 = __shfl_sync(kFull, qn, base + 2), q3 = __shfl_sync(kFull, qn, base + 3);
     if (!(solve && nn > 0.0)) {
         q0 = 1.0; q1 = q2 = q3 = 0.0;
     }
@@ -394,8 +297,7 @@ __global__ void __launch_bounds__(32) lrmsd_solve_quad_kernel(
     } else {
         u0 = 2.0 * (q1 * q3 - q0 * q2); u1 = 2.0 * (q2 * q3 + q0 * q1); u2 = a - b - c + d;
     }
-    if (active) {
-        float* st = state + 16 * (size_t)p;
+    if (store) {
         if (sub < 3) {
             st[3 * sub] = (float)u0;
             st[3 * sub + 1] = (float)u1;
@@ -411,175 +313,54 @@ __global__ void __launch_bounds__(32) lrmsd_solve_quad_kernel(
     }
 }
 
-// Eigen-solve of T (one thread per pair).  FP64 issue is scarce on this GPU
-// (about 34 ns per dependent FP64 instruction per warp), so the largest
-// eigenpair is first estimated in FP32 -- Newton's method on the characteristic
-// polynomial l^4 + c2 l^2 + c1 l + c0 (c2 = -2|R|^2, c1 = -8 det R, c0 = det T)
-// from the upper bound E0/2, then the largest column of adj(T - l I) -- and
-// then solved in FP64: T is formed in FP64, the eigenvalue is the Rayleigh
-// quotient of T at the estimate (error quadratic in the estimate's), and the
-// eigenvector is a column of adj(T - lambda I) computed in FP64.
-__global__ void __launch_bounds__(32) lrmsd_solve_kernel(
-    const float* __restrict__ input, const float* __restrict__ target,
-    const int32_t* __restrict__ num_atoms, int P, int Nmax, const float* __restrict__ part1,
-    int nch_max, float* __restrict__ state, int* __restrict__ counter) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
-    const int n = pair_atoms(num_atoms, p, Nmax);
-    counter[p] = 0;
-    float* st = state + 16 * (size_t)p;
-    float S[kSlot];
+// Quad-lane sum of a pair's nch partials (slot stride kSlot floats): lane
+// sub sums partials sub, sub + 4, ... in order, then the fixed-order quad
+// sum; L2 loads (the partials are written by other SMs in the same kernel).
+__device__ __forceinline__ void quad_sum_partials(const float* __restrict__ part, int nch, int sub,
+                                                  float (&S)[kSlot]) {
 #pragma unroll
     for (int k = 0; k < kSlot; ++k) S[k] = 0.f;
-    const int nch = num_chunks(n);
-    for (int c = 0; c < nch; ++c) {
-        const float4* q = reinterpret_cast<const float4*>(part1 + ((size_t)p * nch_max + c) * kSlot);
+#pragma unroll 4
+    for (int c = sub; c < nch; c += 4) {
+        const float4* q = reinterpret_cast<const float4*>(part + (size_t)c * kSlot);
 #pragma unroll
         for (int k = 0; k < kSlot / 4; ++k) {
-            const float4 v = q[k];
+            const float4 v = __ldcg(q + k);
             S[4 * k] += v.x; S[4 * k + 1] += v.y; S[4 * k + 2] += v.z; S[4 * k + 3] += v.w;
         }
     }
-    float U[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
-    float xc[3] = {0.f, 0.f, 0.f}, yc[3] = {0.f, 0.f, 0.f};
-    if (n > 0) {
-        const float* x = target + (size_t)p * Nmax * 3;
-        const float* y = input + (size_t)p * Nmax * 3;
-        const float inv = 1.f / n;
-        float mx[3], my[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            mx[a] = S[a] * inv;
-            my[a] = S[3 + a] * inv;
-            xc[a] = x[a] + mx[a];
-            yc[a] = y[a] + my[a];
-        }
-        // centred correlation R_ab = sum x'_a y'_b and E0 = sum |x'|^2 + |y'|^2 (FP32 reductions)
-        float r[9];
+    for (int k = 0; k < kMom; ++k) S[k] = quad_sum(S[k], sub);
+}
+
+__device__ __forceinline__ void first_atoms(const float* __restrict__ x, const float* __restrict__ y, int n,
+                                            float (&x0)[3], float (&y0)[3]) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) r[3 * a + c] = S[6 + 3 * a + c] - n * mx[a] * my[c];
-        const float e0 = S[15] + S[16] - n * (mx[0] * mx[0] + mx[1] * mx[1] + mx[2] * mx[2] +
-                                              my[0] * my[0] + my[1] * my[1] + my[2] * my[2]);
-        // ---- FP32 estimate on R / |R| (T, lambda and the adjugate are O(1);
-        // the eigenvectors do not depend on the scale)
-        float fro = 0.f;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) fro = fmaf(r[k], r[k], fro);
-        if (!(fro > 0.f)) goto store;  // R = 0 (one atom, or all atoms coincide): U = I
-        {
-        const float sc = rsqrtf(fro);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) r[k] *= sc;
-        const float t00 = r[0] + r[4] + r[8], t01 = r[5] - r[7], t02 = r[6] - r[2], t03 = r[1] - r[3];
-        const float t11 = r[0] - r[4] - r[8], t12 = r[1] + r[3], t13 = r[2] + r[6];
-        const float t22 = -r[0] + r[4] - r[8], t23 = r[5] + r[7], t33 = -r[0] - r[4] + r[8];
-        const float detR = r[0] * (r[4] * r[8] - r[5] * r[7]) - r[1] * (r[3] * r[8] - r[5] * r[6]) +
-                           r[2] * (r[3] * r[7] - r[4] * r[6]);
-        float m[16];
-        const float c0 = adjugate4f(t00, t01, t02, t03, t11, t12, t13, t22, t23, t33, m);
-        const float c2 = -2.f, c1 = -8.f * detR;  // |R| = 1 after scaling
-        float lam = fminf(2.f, 0.5f * e0 * sc * (1.f + 1e-5f));
-        for (int it = 0; it < 24; ++it) {
-            const float l2 = lam * lam;
-            const float pv = (l2 + c2) * l2 + c1 * lam + c0;
-            const float dp = (4.f * l2 + 2.f * c2) * lam + c1;
-            if (!(fabsf(dp) > 0.f)) break;
-            const float step = __fdividef(pv, dp);
-            lam -= step;
-            if (fabsf(step) <= 1e-6f * fabsf(lam)) break;
-        }
-        adjugate4f(t00 - lam, t01, t02, t03, t11 - lam, t12, t13, t22 - lam, t23, t33 - lam, m);
-        int jb = 0;
-        float best = m[0];
-        float qf[4] = {m[0], m[4], m[8], m[12]};
-#pragma unroll
-        for (int k = 1; k < 4; ++k)
-            if (fabsf(m[5 * k]) > fabsf(best)) {
-                best = m[5 * k];
-                jb = k;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) qf[i] = m[4 * i + k];
-            }
-        if (fabsf(best) > 0.f) {
-            const float ib = 1.f / fabsf(best);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) qf[i] *= ib;
-        } else {
-            qf[0] = 1.f; qf[1] = qf[2] = qf[3] = 0.f;
-            jb = 0;
-        }
-        // ---- FP64 solve: T in FP64, Rayleigh quotient, adjugate column
-        double R[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) R[k] = (double)r[k];
-        double T[4][4];
-        T[0][0] = R[0] + R[4] + R[8];
-        T[0][1] = T[1][0] = R[5] - R[7];
-        T[0][2] = T[2][0] = R[6] - R[2];
-        T[0][3] = T[3][0] = R[1] - R[3];
-        T[1][1] = R[0] - R[4] - R[8];
-        T[1][2] = T[2][1] = R[1] + R[3];
-        T[1][3] = T[3][1] = R[2] + R[6];
-        T[2][2] = -R[0] + R[4] - R[8];
-        T[2][3] = T[3][2] = R[5] + R[7];
-        T[3][3] = -R[0] - R[4] + R[8];
-        double q[4], w[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) q[i] = (double)qf[i];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) w[i] = T[i][0] * q[0] + T[i][1] * q[1] + T[i][2] * q[2] + T[i][3] * q[3];
-        const double num = q[0] * w[0] + q[1] * w[1] + q[2] * w[2] + q[3] * w[3];
-        const double den = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
-        double l64 = 0.0;
-        if (den > 0.0) {
-            const double rd = (double)(1.f / (float)den);
-            l64 = num * rd;
-            l64 = fma(rd, fma(-l64, den, num), l64);  // one Newton correction of num / den
-        }
-        // eigenvector: row jb of adj(T - lambda I) (symmetric, so also column jb)
-        double A[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) A[i][k] = T[i][k] - (i == k ? l64 : 0.0);
-        switch (jb) {
-            case 0: adj_row<0>(A, q); break;
-            case 1: adj_row<1>(A, q); break;
-            case 2: adj_row<2>(A, q); break;
-            default: adj_row<3>(A, q); break;
-        }
-        const double nn = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
-        double q0 = 1.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;
-        if (nn > 0.0) {
-            double s = (double)rsqrtf((float)nn);
-            s = s * fma(-0.5 * nn * s, s, 1.5);  // Newton steps for 1/sqrt(nn)
-            s = s * fma(-0.5 * nn * s, s, 1.5);
-            q0 = q[0] * s; q1 = q[1] * s; q2 = q[2] * s; q3 = q[3] * s;
-        }
-        // U(q) of Section 4, formed in FP64 and rounded once: the gradient
-        // y' - U x' is a small difference of ~|x'|-sized terms
-        U[0] = (float)(q0 * q0 + q1 * q1 - q2 * q2 - q3 * q3);
-        U[1] = (float)(2.0 * (q1 * q2 - q0 * q3));
-        U[2] = (float)(2.0 * (q1 * q3 + q0 * q2));
-        U[3] = (float)(2.0 * (q1 * q2 + q0 * q3));
-        U[4] = (float)(q0 * q0 - q1 * q1 + q2 * q2 - q3 * q3);
-        U[5] = (float)(2.0 * (q2 * q3 - q0 * q1));
-        U[6] = (float)(2.0 * (q1 * q3 - q0 * q2));
-        U[7] = (float)(2.0 * (q2 * q3 + q0 * q1));
-        U[8] = (float)(q0 * q0 - q1 * q1 - q2 * q2 + q3 * q3);
-        }
+    for (int a = 0; a < 3; ++a) {
+        x0[a] = n > 0 ? x[a] : 0.f;
+        y0[a] = n > 0 ? y[a] : 0.f;
     }
-store:
-#pragma unroll
-    for (int k = 0; k < 9; ++k) st[k] = U[k];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        st[9 + k] = xc[k];
-        st[12 + k] = yc[k];
-    }
-    st[15] = 0.f;
+}
+
+// Eigen-solve of the fused training step: the partials are per tile of `tile`
+// residues of chain p (the full-atom forward's tile moments), eight pairs per
+// warp.
+__global__ void __launch_bounds__(32) lrmsd_solve_tiles_kernel(
+    const float* __restrict__ input, const float* __restrict__ target,
+    const int32_t* __restrict__ num_atoms, int P, int Nmax, const float* __restrict__ part1,
+    int tiles_max, float* __restrict__ state, const int32_t* __restrict__ lengths, int tile, int Lmax) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sub = gid & 3, lane = threadIdx.x & 31;
+    const bool active = (gid >> 2) < P;
+    const int p = active ? (gid >> 2) : P - 1;
+    const int n = pair_atoms(num_atoms, p, Nmax);
+    const int L = min(max(lengths[p], 0), Lmax);
+    const int nch = L > 0 ? (L + tile - 1) / tile : 1;
+    float x0[3], y0[3];
+    first_atoms(target + (size_t)p * Nmax * 3, input + (size_t)p * Nmax * 3, n, x0, y0);
+    float S[kSlot];
+    quad_sum_partials(part1 + (size_t)p * tiles_max * kSlot, nch, sub, S);
+    quad_eigen_solve(S, x0, y0, n, sub, lane, active, state + 16 * (size_t)p);
 }
 
 // U x + loads of the per-pair state
@@ -589,14 +370,28 @@ struct PairState {
     float scale;
 };
 
+// The state is written by an earlier kernel: read-only loads, four float4.
 __device__ __forceinline__ PairState load_state(const float* st) {
+    const float4* q = reinterpret_cast<const float4*>(st);
+    const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
+    PairState s;
+    s.u0 = make_float3(a.x, a.y, a.z);
+    s.u1 = make_float3(a.w, b.x, b.y);
+    s.u2 = make_float3(b.z, b.w, c.x);
+    s.xc = make_float3(c.y, c.z, c.w);
+    s.yc = make_float3(d.x, d.y, d.z);
+    s.scale = d.w;
+    return s;
+}
+
+__device__ __forceinline__ PairState load_state_shared(const float* st) {
     PairState s;
     s.u0 = make_float3(st[0], st[1], st[2]);
     s.u1 = make_float3(st[3], st[4], st[5]);
     s.u2 = make_float3(st[6], st[7], st[8]);
     s.xc = make_float3(st[9], st[10], st[11]);
     s.yc = make_float3(st[12], st[13], st[14]);
-    s.scale = st[15];
+    s.scale = 0.f;
     return s;
 }
 
@@ -606,54 +401,240 @@ __device__ __forceinline__ float3 residual(const PairState& s, float3 x, float3 
 }
 
 // ---------------------------------------------------------------------------
-// K5c
+// K5: the whole forward of a pair in one CTA, for batches that fit the GPU
+// in one wave (a few long pairs): moments, eigen-solve by one quad of warp 0,
+// residual sum and LRMSD, with block barriers instead of launches between
+// the steps.  Same arithmetic as K5a-K5d; the sums run over the CTA's warps.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kNT) lrmsd_residual_kernel(
+constexpr int kPNT = 256;
+
+__global__ void __launch_bounds__(kPNT, 2) lrmsd_pair_kernel(
     const float* __restrict__ input, const float* __restrict__ target,
-    const int32_t* __restrict__ num_atoms, int P, int Nmax, float* __restrict__ part2,
-    float* __restrict__ state, double* __restrict__ lr64, int* __restrict__ counter,
-    float* __restrict__ lrmsd, int nch_max) {
-    __shared__ float s_red[kNT / 32];
-    __shared__ int s_last;
-    const int p = blockIdx.x / nch_max, c = blockIdx.x % nch_max;
+    const int32_t* __restrict__ num_atoms, int P, int Nmax, float* __restrict__ state,
+    float* __restrict__ lrmsd) {
+    constexpr int NW = kPNT / 32;
+    __shared__ float s_mom[NW][kMom + 1];
+    __shared__ double s_res[NW];
+    __shared__ __align__(16) float s_st[16];
+    const int p = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = pair_atoms(num_atoms, p, Nmax);
+    const float* x = target + (size_t)p * Nmax * 3;
+    const float* y = input + (size_t)p * Nmax * 3;
+    float x0[3], y0[3];
+    first_atoms(x, y, n, x0, y0);
+    const float3 sx = make_float3(x0[0], x0[1], x0[2]), sy = make_float3(y0[0], y0[1], y0[2]);
+    float m[kMom];
+#pragma unroll
+    for (int k = 0; k < kMom; ++k) m[k] = 0.f;
+    for (int base = 0; base < n; base += 8 * kPNT)  // two groups of 4 atoms per thread in flight
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int i0 = base + 4 * (threadIdx.x + kPNT * s);
+        if (i0 >= n) continue;
+        float3 xv[4], yv[4];
+        load4(x + 3 * (size_t)i0, xv);
+        load4(y + 3 * (size_t)i0, yv);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (i0 + q < n) {
+                const float3 dx = f3_sub(xv[q], sx), dy = f3_sub(yv[q], sy);
+                m[0] += dx.x; m[1] += dx.y; m[2] += dx.z;
+                m[3] += dy.x; m[4] += dy.y; m[5] += dy.z;
+                m[6] = fmaf(dx.x, dy.x, m[6]); m[7] = fmaf(dx.x, dy.y, m[7]); m[8] = fmaf(dx.x, dy.z, m[8]);
+                m[9] = fmaf(dx.y, dy.x, m[9]); m[10] = fmaf(dx.y, dy.y, m[10]); m[11] = fmaf(dx.y, dy.z, m[11]);
+                m[12] = fmaf(dx.z, dy.x, m[12]); m[13] = fmaf(dx.z, dy.y, m[13]); m[14] = fmaf(dx.z, dy.z, m[14]);
+                m[15] += f3_dot(dx, dx);
+                m[16] += f3_dot(dy, dy);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kMom; ++k) {
+        const float v = warp_sum(m[k]);
+        if (lane == 0) s_mom[warp][k] = v;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float S[kSlot];
+#pragma unroll
+        for (int k = 0; k < kSlot; ++k) S[k] = 0.f;
+#pragma unroll
+        for (int w = 0; w < NW; ++w)
+#pragma unroll
+            for (int k = 0; k < kMom; ++k) S[k] += s_mom[w][k];
+        quad_eigen_solve(S, x0, y0, n, lane & 3, lane, lane < 4, s_st);
+    }
+    __syncthreads();
+    const PairState ps = load_state_shared(s_st);
+    float acc = 0.f;
+    for (int base = 0; base < n; base += 8 * kPNT)
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int i0 = base + 4 * (threadIdx.x + kPNT * s);
+        if (i0 >= n) continue;
+        float3 xv[4], yv[4];
+        load4(x + 3 * (size_t)i0, xv);
+        load4(y + 3 * (size_t)i0, yv);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (i0 + q < n) {
+                const float3 d = residual(ps, xv[q], yv[q]);
+                acc += f3_dot(d, d);
+            }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) s_res[warp] = (double)acc;
+    __syncthreads();
+    if (threadIdx.x < 16) {
+        double sum = 0.0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) sum += s_res[w];
+        const double lr = n > 0 ? sqrt(sum / n) : 0.0;
+        double scale = 0.0;
+        if (lr >= 1e-12) {
+            scale = 1.0 / (n * lr);
+        } else if (n > 0 && threadIdx.x == 0) {
+            flag_status(TPL_STATUS_ZERO_LRMSD);
+        }
+        state[16 * (size_t)p + threadIdx.x] = threadIdx.x < 15 ? s_st[threadIdx.x] : (float)scale;
+        if (threadIdx.x == 0) lrmsd[p] = (float)lr;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K5a: moments, one partial per warp
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kWNT) lrmsd_moments_kernel(
+    const float* __restrict__ input, const float* __restrict__ target,
+    const int32_t* __restrict__ num_atoms, int P, int Nmax, float* __restrict__ part1, int nch_max,
+    int wpp) {
+    const int lane = threadIdx.x & 31;
+    const long long w = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    if (w >= (long long)P * wpp) return;
+    const int p = (int)(w / wpp), r = (int)(w % wpp);
     const int n = pair_atoms(num_atoms, p, Nmax);
     const int nch = num_chunks(n);
-    if (c >= nch) return;
+    if (r >= nch) return;
+    const float* x = target + (size_t)p * Nmax * 3;
+    const float* y = input + (size_t)p * Nmax * 3;
+    float3 sx = make_float3(0.f, 0.f, 0.f), sy = sx;
+    if (n > 0) {
+        sx = make_float3(__ldg(x), __ldg(x + 1), __ldg(x + 2));
+        sy = make_float3(__ldg(y), __ldg(y + 1), __ldg(y + 2));
+    }
+    float m[kMom];
+#pragma unroll
+    for (int k = 0; k < kMom; ++k) m[k] = 0.f;
+    for (int c = r; c < nch; c += wpp) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const int i0 = c * kWC + 4 * (lane + 32 * s);
+            if (i0 < n) {
+                float3 xv[4], yv[4];
+                load4(x + 3 * (size_t)i0, xv);
+                load4(y + 3 * (size_t)i0, yv);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (i0 + q < n) {
+                        const float3 dx = f3_sub(xv[q], sx), dy = f3_sub(yv[q], sy);
+                        m[0] += dx.x; m[1] += dx.y; m[2] += dx.z;
+                        m[3] += dy.x; m[4] += dy.y; m[5] += dy.z;
+                        m[6] = fmaf(dx.x, dy.x, m[6]); m[7] = fmaf(dx.x, dy.y, m[7]); m[8] = fmaf(dx.x, dy.z, m[8]);
+                        m[9] = fmaf(dx.y, dy.x, m[9]); m[10] = fmaf(dx.y, dy.y, m[10]); m[11] = fmaf(dx.y, dy.z, m[11]);
+                        m[12] = fmaf(dx.z, dy.x, m[12]); m[13] = fmaf(dx.z, dy.y, m[13]); m[14] = fmaf(dx.z, dy.z, m[14]);
+                        m[15] += f3_dot(dx, dx);
+                        m[16] += f3_dot(dy, dy);
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kMom; ++k) m[k] = warp_sum(m[k]);
+    float4* slot = reinterpret_cast<float4*>(part1 + ((size_t)p * nch_max + r) * kSlot);
+#pragma unroll
+    for (int k = 0; k < kSlot / 4; ++k)
+        if (lane == k)
+            slot[k] = make_float4(m[4 * k], 4 * k + 1 < kMom ? m[4 * k + 1] : 0.f,
+                                  4 * k + 2 < kMom ? m[4 * k + 2] : 0.f, 4 * k + 3 < kMom ? m[4 * k + 3] : 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// K5b: eigen-solve, four lanes per pair
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(32) lrmsd_solve_kernel(
+    const float* __restrict__ input, const float* __restrict__ target,
+    const int32_t* __restrict__ num_atoms, int P, int Nmax, const float* __restrict__ part1, int nch_max,
+    int wpp, float* __restrict__ state) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sub = gid & 3, lane = threadIdx.x & 31;
+    const bool active = (gid >> 2) < P;
+    const int p = active ? (gid >> 2) : P - 1;
+    const int n = pair_atoms(num_atoms, p, Nmax);
+    float x0[3], y0[3];
+    first_atoms(target + (size_t)p * Nmax * 3, input + (size_t)p * Nmax * 3, n, x0, y0);
+    float S[kSlot];
+    quad_sum_partials(part1 + (size_t)p * nch_max * kSlot, num_parts(n, wpp), sub, S);
+    quad_eigen_solve(S, x0, y0, n, sub, lane, active, state + 16 * (size_t)p);
+}
+
+// ---------------------------------------------------------------------------
+// K5c: residual sums, one FP64 partial per warp
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kWNT) lrmsd_residual_kernel(
+    const float* __restrict__ input, const float* __restrict__ target,
+    const int32_t* __restrict__ num_atoms, int P, int Nmax, double* __restrict__ part2, int nch_max,
+    int wpp, const float* __restrict__ state) {
+    const int lane = threadIdx.x & 31;
+    const long long w = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    if (w >= (long long)P * wpp) return;
+    const int p = (int)(w / wpp), r = (int)(w % wpp);
+    const int n = pair_atoms(num_atoms, p, Nmax);
+    const int nch = num_chunks(n);
+    if (r >= nch) return;
     const float* x = target + (size_t)p * Nmax * 3;
     const float* y = input + (size_t)p * Nmax * 3;
     const PairState ps = load_state(state + 16 * (size_t)p);
-    float acc = 0.f;
+    double tot = 0.0;
+    for (int c = r; c < nch; c += wpp) {
+        float acc = 0.f;
 #pragma unroll
-    for (int s = 0; s < kAPT / 4; ++s) {
-        const int i0 = c * kChunk + 4 * (threadIdx.x + kNT * s);
-        if (i0 < n) {
-            float3 xv[4], yv[4];
-            load4(x + 3 * (size_t)i0, xv);
-            load4(y + 3 * (size_t)i0, yv);
+        for (int s = 0; s < 2; ++s) {
+            const int i0 = c * kWC + 4 * (lane + 32 * s);
+            if (i0 < n) {
+                float3 xv[4], yv[4];
+                load4(x + 3 * (size_t)i0, xv);
+                load4(y + 3 * (size_t)i0, yv);
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (i0 + q < n) {
-                    const float3 r = residual(ps, xv[q], yv[q]);
-                    acc += f3_dot(r, r);
-                }
+                for (int q = 0; q < 4; ++q)
+                    if (i0 + q < n) {
+                        const float3 d = residual(ps, xv[q], yv[q]);
+                        acc += f3_dot(d, d);
+                    }
+            }
         }
+        tot += (double)warp_sum(acc);
     }
-    acc = warp_sum(acc);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_red[warp] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float v = 0.f;
-        for (int w = 0; w < kNT / 32; ++w) v += s_red[w];
-        part2[(size_t)p * nch_max + c] = v;
-        __threadfence();
-        s_last = (atomicAdd(counter + p, 1) == nch - 1);
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        __threadfence();
-        double sum = 0.0;
-        for (int k = 0; k < nch; ++k) sum += (double)__ldcg(part2 + (size_t)p * nch_max + k);
+    if (lane == 0) part2[(size_t)p * nch_max + r] = tot;
+}
+
+// ---------------------------------------------------------------------------
+// K5d: LRMSD and gradient scale, four lanes per pair
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(32) lrmsd_finalize_kernel(
+    const int32_t* __restrict__ num_atoms, int P, int Nmax, const double* __restrict__ part2, int nch_max,
+    int wpp, float* __restrict__ state, float* __restrict__ lrmsd) {
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sub = gid & 3;
+    const bool active = (gid >> 2) < P;
+    const int p = active ? (gid >> 2) : P - 1;
+    const int n = pair_atoms(num_atoms, p, Nmax);
+    const int np = num_parts(n, wpp);
+    double sum = 0.0;
+    for (int k = sub; k < np; k += 4) sum += part2[(size_t)p * nch_max + k];
+    sum = quad_sum(sum, sub);
+    if (active && sub == 0) {
         const double lr = n > 0 ? sqrt(sum / n) : 0.0;
         double scale = 0.0;
         if (lr >= 1e-12) {
@@ -661,21 +642,24 @@ __global__ void __launch_bounds__(kNT) lrmsd_residual_kernel(
         } else if (n > 0) {
             flag_status(TPL_STATUS_ZERO_LRMSD);
         }
-        lr64[p] = lr;
         lrmsd[p] = (float)lr;
         state[16 * (size_t)p + 15] = (float)scale;
     }
 }
 
 // ---------------------------------------------------------------------------
-// K6
+// K6: one CTA per 2048 atoms of a pair (a write stream: large CTAs keep the
+// stores of a pair together)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kNT) lrmsd_grad_kernel(const float* __restrict__ grad_lrmsd,
-                                                         const float* __restrict__ input,
-                                                         const float* __restrict__ target,
-                                                         const int32_t* __restrict__ num_atoms,
-                                                         int P, int Nmax, const float* __restrict__ state,
-                                                         float* __restrict__ grad_input, int nch_max) {
+constexpr int kGNT = 256;
+constexpr int kGChunk = kGNT * 8;  // two groups of 4 atoms per thread
+
+__global__ void __launch_bounds__(kGNT) lrmsd_grad_kernel(const float* __restrict__ grad_lrmsd,
+                                                          const float* __restrict__ input,
+                                                          const float* __restrict__ target,
+                                                          const int32_t* __restrict__ num_atoms,
+                                                          int P, int Nmax, const float* __restrict__ state,
+                                                          float* __restrict__ grad_input, int nch_max) {
     const int p = blockIdx.x / nch_max, c = blockIdx.x % nch_max;
     const int n = pair_atoms(num_atoms, p, Nmax);
     const float* x = target + (size_t)p * Nmax * 3;
@@ -684,8 +668,8 @@ __global__ void __launch_bounds__(kNT) lrmsd_grad_kernel(const float* __restrict
     const PairState ps = load_state(state + 16 * (size_t)p);
     const float w = __ldg(grad_lrmsd + p) * ps.scale;
 #pragma unroll
-    for (int s = 0; s < kAPT / 4; ++s) {
-        const int i0 = c * kChunk + 4 * (threadIdx.x + kNT * s);
+    for (int s = 0; s < 2; ++s) {
+        const int i0 = c * kGChunk + 4 * (threadIdx.x + kGNT * s);
         if (i0 >= Nmax) continue;
         float g[12];
 #pragma unroll
@@ -858,6 +842,7 @@ __global__ void __launch_bounds__(kRefNT) lrmsd_bwd_ref64_kernel(
 
 }  // namespace
 
+
 size_t lrmsd_ws_bytes(int P, int Nmax) { return ws_layout(P, Nmax).total; }
 
 cudaError_t launch_lrmsd_solve_tiles(const float* input, const float* target, const int32_t* num_atoms,
@@ -865,13 +850,22 @@ cudaError_t launch_lrmsd_solve_tiles(const float* input, const float* target, co
                                      const int32_t* lengths, int tile, int Lmax, float* state,
                                      cudaStream_t s) {
     if (P == 0) return cudaSuccess;
-    lrmsd_solve_quad_kernel<<<(4 * P + 31) / 32, 32, 0, s>>>(input, target, num_atoms, P, Nmax, tile_moments,
-                                                            tiles_max, state, nullptr, lengths, tile, Lmax);
+    lrmsd_solve_tiles_kernel<<<(4 * P + 31) / 32, 32, 0, s>>>(input, target, num_atoms, P, Nmax, tile_moments,
+                                                             tiles_max, state, lengths, tile, Lmax);
     return cudaGetLastError();
 }
 
 const float* lrmsd_state(const void* ws, int P, int Nmax) {
     return reinterpret_cast<const float*>(static_cast<const char*>(ws) + ws_layout(P, Nmax).state);
+}
+
+// Warps per pair of the streaming kernels: enough for about two rounds of the
+// GPU's resident warps, at most one per chunk.
+static int warps_per_pair(int P, int nch) {
+    const long long resident = (long long)persistent_grid((const void*)lrmsd_moments_kernel, kWNT, 0) * kWarps;
+    long long w = (2 * resident + P - 1) / P;
+    if (w > nch) w = nch;
+    return w < 1 ? 1 : (int)w;
 }
 
 cudaError_t launch_lrmsd_forward(const float* input, const float* target, const int32_t* num_atoms,
@@ -880,20 +874,19 @@ cudaError_t launch_lrmsd_forward(const float* input, const float* target, const 
     const WsLayout L = ws_layout(P, Nmax);
     char* base = static_cast<char*>(ws);
     float* part1 = reinterpret_cast<float*>(base + L.part1);
-    float* part2 = reinterpret_cast<float*>(base + L.part2);
+    double* part2 = reinterpret_cast<double*>(base + L.part2);
     float* state = reinterpret_cast<float*>(base + L.state);
-    double* lr64 = reinterpret_cast<double*>(base + L.lr64);
-    int* counter = reinterpret_cast<int*>(base + L.counter);
-    const unsigned grid = (unsigned)P * (unsigned)L.nch;  // block = pair * nch + chunk
-    lrmsd_moments_kernel<<<grid, kNT, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.nch);
-    if (P <= kQuadSolveMaxPairs)
-        lrmsd_solve_quad_kernel<<<(4 * P + 31) / 32, 32, 0, s>>>(input, target, num_atoms, P, Nmax, part1,
-                                                                L.nch, state, counter);
-    else
-        lrmsd_solve_kernel<<<(P + 31) / 32, 32, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.nch,
-                                                    state, counter);
-    lrmsd_residual_kernel<<<grid, kNT, 0, s>>>(input, target, num_atoms, P, Nmax, part2, state, lr64,
-                                               counter, lrmsd, L.nch);
+    if (P <= persistent_grid((const void*)lrmsd_pair_kernel, kPNT, 0)) {
+        lrmsd_pair_kernel<<<P, kPNT, 0, s>>>(input, target, num_atoms, P, Nmax, state, lrmsd);
+        return cudaGetLastError();
+    }
+    const int wpp = warps_per_pair(P, L.nch);
+    const unsigned grid = (unsigned)(((long long)P * wpp + kWarps - 1) / kWarps);
+    const unsigned quads = (unsigned)((4LL * P + 31) / 32);
+    lrmsd_moments_kernel<<<grid, kWNT, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.nch, wpp);
+    lrmsd_solve_kernel<<<quads, 32, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.nch, wpp, state);
+    lrmsd_residual_kernel<<<grid, kWNT, 0, s>>>(input, target, num_atoms, P, Nmax, part2, L.nch, wpp, state);
+    lrmsd_finalize_kernel<<<quads, 32, 0, s>>>(num_atoms, P, Nmax, part2, L.nch, wpp, state, lrmsd);
     return cudaGetLastError();
 }
 
@@ -903,9 +896,10 @@ cudaError_t launch_lrmsd_backward(const float* grad_lrmsd, const float* input, c
     if (P == 0) return cudaSuccess;
     const WsLayout L = ws_layout(P, Nmax);
     const float* state = reinterpret_cast<const float*>(static_cast<const char*>(ws) + L.state);
-    const unsigned grid = (unsigned)P * (unsigned)L.nch;  // block = pair * nch + chunk
-    lrmsd_grad_kernel<<<grid, kNT, 0, s>>>(grad_lrmsd, input, target, num_atoms, P, Nmax, state,
-                                           grad_input, L.nch);
+    const int nch = (Nmax + kGChunk - 1) / kGChunk > 0 ? (Nmax + kGChunk - 1) / kGChunk : 1;
+    const unsigned grid = (unsigned)P * (unsigned)nch;  // block = pair * nch + chunk
+    lrmsd_grad_kernel<<<grid, kGNT, 0, s>>>(grad_lrmsd, input, target, num_atoms, P, Nmax, state, grad_input,
+                                            nch);
     return cudaGetLastError();
 }
 
@@ -977,9 +971,8 @@ cudaError_t launch_lrmsd_forward_noalloc(const float* input, const float* target
     void* scratch = nullptr;
     cudaError_t e = noalloc_scratch_address(&scratch);
     if (e != cudaSuccess) return e;
-    // Nothing in the scratch has to start at zero: every chunk partial that is
-    // read is written first in the same call, and the per-pair completion
-    // counters are reset by the solve kernel before the residual kernel counts.
+    // Nothing in the scratch has to start at zero: every partial that is read
+    // is written first in the same call.
     return launch_lrmsd_forward(input, target, num_atoms, P, Nmax, lrmsd, scratch, s);
 }
 

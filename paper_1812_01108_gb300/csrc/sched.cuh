@@ -352,7 +352,7 @@ __device__ __forceinline__ int next_tile(int requested, int* s_v) {
     return *s_v;
 }
 
-// Host side: schedule kernel (api.cu) and the persistent grid size.
+// Host side: schedule kernel (api.cu).
 // Chain order of the schedule: batch order, longest first, or longest first
 // with the chains of at most one tile packed several per tile (granule =
 // residues per thread, the unit a chain's slots are padded to).
@@ -360,6 +360,5 @@ enum SchedMode { kSchedBatch = 0, kSchedLongest = 1, kSchedPacked = 2 };
 cudaError_t launch_schedule(const int32_t* lengths, int B, int Lmax, int tile, int mode, int granule,
                             const ChainWs& ws, cudaStream_t s);
 cudaError_t reset_backward_flags(const ChainWs& ws, cudaStream_t s);
-int persistent_grid(const void* kernel, int threads, size_t smem);
 
 }  // namespace tpl

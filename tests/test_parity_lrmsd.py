@@ -152,9 +152,8 @@ def test_protein_shaped_pairs():
     assert rel_err(g32, oracle.lrmsd_backward(w, x, y, n)) <= GRAD_TOL
 
 
-def test_large_batch_takes_the_one_lane_solve():
-    """Above 8192 pairs the eigen-solve runs one lane per pair (below, four
-    lanes share a pair): both forms must agree with the oracle."""
+def test_large_batch_of_small_pairs():
+    """Many pairs of a few atoms: one warp per pair in the streaming kernels."""
     rng = np.random.default_rng(9)
     P = 8300
     x, y, n = workloads.lrmsd_clouds(P, 3, 40, rng)
@@ -162,3 +161,23 @@ def test_large_batch_takes_the_one_lane_solve():
     l32, g32 = _run(x, y, n, w)
     assert np.abs(l32 - oracle.lrmsd_forward(x, y, n)).max() <= LRMSD_TOL
     assert rel_err(g32, oracle.lrmsd_backward(w, x, y, n)) <= GRAD_TOL
+
+
+# sizes around the 256-atom chunks of the streaming kernels
+CHUNK_SIZES = [0, 1, 2, 3, 4, 255, 256, 257, 511, 512, 513, 1023, 1024, 1025, 2999, 3000]
+
+
+@pytest.mark.parametrize("P", [600, 2000])
+def test_batches_that_spread_pairs_over_warps(P):
+    """Batches too large for one CTA per pair: the streaming kernels give each
+    pair several warps (each with one or more chunks of 256 atoms), so the
+    partials of a pair come from several warps."""
+    sizes = [CHUNK_SIZES[i % len(CHUNK_SIZES)] for i in range(P)]
+    x, y, n = _clouds(sizes, 11 + P)
+    w = np.random.default_rng(P).normal(size=P).astype(np.float32)
+    l32, g32 = _run(x, y, n, w)
+    assert np.abs(l32 - oracle.lrmsd_forward(x, y, n)).max() <= LRMSD_TOL
+    unique = n >= 3
+    assert rel_err(g32[unique], oracle.lrmsd_backward(w, x, y, n)[unique]) <= GRAD_TOL
+    for p, k in enumerate(n):
+        assert np.all(g32[p, k:] == 0)
