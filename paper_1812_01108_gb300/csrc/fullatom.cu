@@ -577,15 +577,10 @@ __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_ker
                         sum += (double)__ldcg(ws.tres + slot0 + tp);
                     }
                     const int n = lg.num_atoms[b] < Amax ? lg.num_atoms[b] : Amax;
-                    const double lr = n > 0 ? sqrt(sum / n) : 0.0;
-                    double scale = 0.0;
-                    if (lr >= 1e-12) {
-                        scale = 1.0 / (n * lr);
-                    } else if (n > 0) {
-                        flag_status(TPL_STATUS_ZERO_LRMSD);
-                    }
-                    lg.lrmsd_out[b] = (float)lr;
-                    s_scale = (float)scale;
+                    float lr, scale;
+                    lrmsd_from_sum(sum, n, lr, scale);
+                    lg.lrmsd_out[b] = lr;
+                    s_scale = scale;
                 }
                 __syncthreads();
                 const float sc = s_scale;

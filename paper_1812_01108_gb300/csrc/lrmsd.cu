@@ -413,39 +413,53 @@ __global__ void __launch_bounds__(kPNT, 2) lrmsd_pair_kernel(
     const int32_t* __restrict__ num_atoms, int P, int Nmax, float* __restrict__ state,
     float* __restrict__ lrmsd) {
     constexpr int NW = kPNT / 32;
+    constexpr int G = 4;  // groups of 4 atoms per thread in flight
+    constexpr int kBatch = 4 * G * kPNT;
     __shared__ float s_mom[NW][kMom + 1];
     __shared__ double s_res[NW];
     __shared__ __align__(16) float s_st[16];
     const int p = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int n = pair_atoms(num_atoms, p, Nmax);
     const float* x = target + (size_t)p * Nmax * 3;
     const float* y = input + (size_t)p * Nmax * 3;
-    float x0[3], y0[3];
-    first_atoms(x, y, n, x0, y0);
-    const float3 sx = make_float3(x0[0], x0[1], x0[2]), sy = make_float3(y0[0], y0[1], y0[2]);
+    // The first batch and the first atoms are read up to Nmax (inside the
+    // padded rows) so that their loads do not wait for the atom count.
+    float3 sx = make_float3(0.f, 0.f, 0.f), sy = sx;
+    if (Nmax > 0) {
+        sx = make_float3(__ldg(x), __ldg(x + 1), __ldg(x + 2));
+        sy = make_float3(__ldg(y), __ldg(y + 1), __ldg(y + 2));
+    }
+    const int n = pair_atoms(num_atoms, p, Nmax);
+    if (n == 0) sx = sy = make_float3(0.f, 0.f, 0.f);
     float m[kMom];
 #pragma unroll
     for (int k = 0; k < kMom; ++k) m[k] = 0.f;
-    for (int base = 0; base < n; base += 8 * kPNT)  // two groups of 4 atoms per thread in flight
+    for (int base = 0; base < (base == 0 ? Nmax : n); base += kBatch) {
+        const int bound = base == 0 ? Nmax : n;
+        float3 xv[G][4], yv[G][4];
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        const int i0 = base + 4 * (threadIdx.x + kPNT * s);
-        if (i0 >= n) continue;
-        float3 xv[4], yv[4];
-        load4(x + 3 * (size_t)i0, xv);
-        load4(y + 3 * (size_t)i0, yv);
+        for (int s = 0; s < G; ++s) {
+            const int i0 = base + 4 * (threadIdx.x + kPNT * s);
+            if (i0 < bound) {
+                load4(x + 3 * (size_t)i0, xv[s]);
+                load4(y + 3 * (size_t)i0, yv[s]);
+            }
+        }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (i0 + q < n) {
-                const float3 dx = f3_sub(xv[q], sx), dy = f3_sub(yv[q], sy);
-                m[0] += dx.x; m[1] += dx.y; m[2] += dx.z;
-                m[3] += dy.x; m[4] += dy.y; m[5] += dy.z;
-                m[6] = fmaf(dx.x, dy.x, m[6]); m[7] = fmaf(dx.x, dy.y, m[7]); m[8] = fmaf(dx.x, dy.z, m[8]);
-                m[9] = fmaf(dx.y, dy.x, m[9]); m[10] = fmaf(dx.y, dy.y, m[10]); m[11] = fmaf(dx.y, dy.z, m[11]);
-                m[12] = fmaf(dx.z, dy.x, m[12]); m[13] = fmaf(dx.z, dy.y, m[13]); m[14] = fmaf(dx.z, dy.z, m[14]);
-                m[15] += f3_dot(dx, dx);
-                m[16] += f3_dot(dy, dy);
+        for (int s = 0; s < G; ++s) {
+            const int i0 = base + 4 * (threadIdx.x + kPNT * s);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (i0 + q < n) {
+                    const float3 dx = f3_sub(xv[s][q], sx), dy = f3_sub(yv[s][q], sy);
+                    m[0] += dx.x; m[1] += dx.y; m[2] += dx.z;
+                    m[3] += dy.x; m[4] += dy.y; m[5] += dy.z;
+                    m[6] = fmaf(dx.x, dy.x, m[6]); m[7] = fmaf(dx.x, dy.y, m[7]); m[8] = fmaf(dx.x, dy.z, m[8]);
+                    m[9] = fmaf(dx.y, dy.x, m[9]); m[10] = fmaf(dx.y, dy.y, m[10]); m[11] = fmaf(dx.y, dy.z, m[11]);
+                    m[12] = fmaf(dx.z, dy.x, m[12]); m[13] = fmaf(dx.z, dy.y, m[13]); m[14] = fmaf(dx.z, dy.z, m[14]);
+                    m[15] += f3_dot(dx, dx);
+                    m[16] += f3_dot(dy, dy);
+                }
             }
         }
     }
@@ -456,49 +470,54 @@ __global__ void __launch_bounds__(kPNT, 2) lrmsd_pair_kernel(
     }
     __syncthreads();
     if (warp == 0) {
+        // lane k < kMom sums moment k over the warps (fixed order), then every
+        // lane takes all of them
+        float v = 0.f;
+        if (lane < kMom)
+#pragma unroll
+            for (int w = 0; w < NW; ++w) v += s_mom[w][lane];
         float S[kSlot];
 #pragma unroll
-        for (int k = 0; k < kSlot; ++k) S[k] = 0.f;
-#pragma unroll
-        for (int w = 0; w < NW; ++w)
-#pragma unroll
-            for (int k = 0; k < kMom; ++k) S[k] += s_mom[w][k];
+        for (int k = 0; k < kSlot; ++k) S[k] = k < kMom ? __shfl_sync(kFull, v, k) : 0.f;
+        const float x0[3] = {sx.x, sx.y, sx.z}, y0[3] = {sy.x, sy.y, sy.z};
         quad_eigen_solve(S, x0, y0, n, lane & 3, lane, lane < 4, s_st);
     }
     __syncthreads();
     const PairState ps = load_state_shared(s_st);
     float acc = 0.f;
-    for (int base = 0; base < n; base += 8 * kPNT)
+    for (int base = 0; base < n; base += kBatch) {
+        float3 xv[G][4], yv[G][4];
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        const int i0 = base + 4 * (threadIdx.x + kPNT * s);
-        if (i0 >= n) continue;
-        float3 xv[4], yv[4];
-        load4(x + 3 * (size_t)i0, xv);
-        load4(y + 3 * (size_t)i0, yv);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (i0 + q < n) {
-                const float3 d = residual(ps, xv[q], yv[q]);
-                acc += f3_dot(d, d);
+        for (int s = 0; s < G; ++s) {
+            const int i0 = base + 4 * (threadIdx.x + kPNT * s);
+            if (i0 < n) {
+                load4(x + 3 * (size_t)i0, xv[s]);
+                load4(y + 3 * (size_t)i0, yv[s]);
             }
+        }
+#pragma unroll
+        for (int s = 0; s < G; ++s) {
+            const int i0 = base + 4 * (threadIdx.x + kPNT * s);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (i0 + q < n) {
+                    const float3 d = residual(ps, xv[s][q], yv[s][q]);
+                    acc += f3_dot(d, d);
+                }
+        }
     }
     acc = warp_sum(acc);
     if (lane == 0) s_res[warp] = (double)acc;
     __syncthreads();
-    if (threadIdx.x < 16) {
+    if (threadIdx.x < 15) state[16 * (size_t)p + threadIdx.x] = s_st[threadIdx.x];
+    if (threadIdx.x == 0) {
         double sum = 0.0;
 #pragma unroll
         for (int w = 0; w < NW; ++w) sum += s_res[w];
-        const double lr = n > 0 ? sqrt(sum / n) : 0.0;
-        double scale = 0.0;
-        if (lr >= 1e-12) {
-            scale = 1.0 / (n * lr);
-        } else if (n > 0 && threadIdx.x == 0) {
-            flag_status(TPL_STATUS_ZERO_LRMSD);
-        }
-        state[16 * (size_t)p + threadIdx.x] = threadIdx.x < 15 ? s_st[threadIdx.x] : (float)scale;
-        if (threadIdx.x == 0) lrmsd[p] = (float)lr;
+        float lr, scale;
+        lrmsd_from_sum(sum, n, lr, scale);
+        state[16 * (size_t)p + 15] = scale;
+        lrmsd[p] = lr;
     }
 }
 
@@ -635,15 +654,10 @@ __global__ void __launch_bounds__(32) lrmsd_finalize_kernel(
     for (int k = sub; k < np; k += 4) sum += part2[(size_t)p * nch_max + k];
     sum = quad_sum(sum, sub);
     if (active && sub == 0) {
-        const double lr = n > 0 ? sqrt(sum / n) : 0.0;
-        double scale = 0.0;
-        if (lr >= 1e-12) {
-            scale = 1.0 / (n * lr);
-        } else if (n > 0) {
-            flag_status(TPL_STATUS_ZERO_LRMSD);
-        }
-        lrmsd[p] = (float)lr;
-        state[16 * (size_t)p + 15] = (float)scale;
+        float lr, scale;
+        lrmsd_from_sum(sum, n, lr, scale);
+        lrmsd[p] = lr;
+        state[16 * (size_t)p + 15] = scale;
     }
 }
 

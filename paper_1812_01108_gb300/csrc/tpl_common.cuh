@@ -441,6 +441,23 @@ __device__ __forceinline__ Sum6 block_seg_suffix_sum6(const Sum6& x, bool tail, 
     return sum6_add(lex, wv);
 }
 
+// LRMSD = sqrt(sum / n) and the gradient factor 1 / (n LRMSD) from the FP64
+// residual sum of n atoms.  Both are stored as float, so they are formed in
+// FP32 (within an ulp or two of the FP64 forms, without FP64's long sqrt and
+// divide sequences).  An LRMSD below 1e-12 has no gradient: factor 0, status
+// TPL_STATUS_ZERO_LRMSD.
+__device__ __forceinline__ void lrmsd_from_sum(double sum, int n, float& lr, float& scale) {
+    lr = 0.f;
+    scale = 0.f;
+    if (n <= 0) return;
+    const float ms = (float)sum / (float)n;
+    lr = ms > 0.f ? sqrtf(ms) : 0.f;
+    if (lr >= 1e-12f)
+        scale = 1.f / ((float)n * lr);
+    else
+        flag_status(TPL_STATUS_ZERO_LRMSD);
+}
+
 // Inputs of an LRMSD gradient formed inside a chain backward (Section 4): for
 // chain b, g_i = w_b ((y_i - yc) - U (x_i - xc)) with y the chain's
 // coordinates, x the target and w_b = grad_lrmsd[b] / (N LRMSD), from the
