@@ -51,19 +51,26 @@ DEFAULT_BATCH = {"training_step": 256, "backbone_uneven": 4096, "lrmsd_batch": 1
 # keyed by (workload, call), with the profile summary that holds the capture.
 # An entry is removed when one of its kernels changes after the capture.
 TRAFFIC = {
-    # fa_bwd_coords_kernel<256, 1> (LRMSD gradient formed in the kernel), cold cache
-    ("training_step", "lrmsd_fullatom_backward"): (24.7444, "atom",
-                                                   "profiles/fa_kernels_training_step_256x700.md"),
+    # (per-unit DRAM bytes, unit, profile, launch shape of the capture or None if the
+    # kernels take none); cold-cache captures of one launch
+    # fa_bwd_coords_kernel<384, 1, 0> (LRMSD gradient formed in the kernel)
+    ("training_step", "lrmsd_fullatom_backward"): (24.7286, "atom", "profiles/fa_kernels_training_step_256x700.md",
+                                                   "threads=384"),
+    # lrmsd_pair_kernel
+    ("training_step", "lrmsd_forward"): (24.0737, "atom", "profiles/lrmsd_kernels_training_step_256x700.md", None),
     # bb_fwd_kernel<256, 4> (the schedule kernel's few bytes not counted)
-    ("backbone_uneven", "backbone_forward"): (80.3405, "residue",
-                                              "profiles/backbone_kernels_backbone_uneven_4096.md"),
+    ("backbone_uneven", "backbone_forward"): (80.0168, "residue", "profiles/backbone_kernels_backbone_uneven_4096.md",
+                                              "threads=256,res_per_thread=4"),
     # bb_bwd_kernel<256, 4, 1, 1>
-    ("backbone_uneven", "lrmsd_backbone_backward"): (82.6204, "residue",
-                                                     "profiles/backbone_kernels_backbone_uneven_4096.md"),
-    # moments + solve + residual, 4096-pair capture scaled by atoms
-    ("lrmsd_batch", "lrmsd_forward"): (49.1460, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md"),
+    ("backbone_uneven", "lrmsd_backbone_backward"): (82.9732, "residue",
+                                                     "profiles/backbone_kernels_backbone_uneven_4096.md",
+                                                     "threads=256,res_per_thread=4"),
+    # moments + solve + residual + finalize
+    ("backbone_uneven", "lrmsd_forward"): (50.5826, "atom", "profiles/lrmsd_kernels_backbone_uneven_4096.md", None),
+    # moments + solve + residual + finalize, 4096-pair capture scaled by atoms
+    ("lrmsd_batch", "lrmsd_forward"): (49.2543, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md", None),
     # grad, 4096-pair capture scaled by atoms
-    ("lrmsd_batch", "lrmsd_backward"): (42.8179, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md"),
+    ("lrmsd_batch", "lrmsd_backward"): (42.8071, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md", None),
 }
 
 
@@ -313,6 +320,8 @@ def run_reference(args):
 class Step:
     """The C-ABI calls of one step with their bookkeeping.
 
+    shape    launch shape of the chain kernels ("threads=.." [",res_per_thread=.."])
+
     calls    [(name, fn)] in launch order
     launches {name: kernels of ours per call}
     kernels  {name: [kernel names]}
@@ -351,12 +360,18 @@ def setup_training_step(args, tpl, torch, dev, d):
     n_atoms = int(na_t.sum().item())
     tuned = None
     if not args.no_autotune and not args.threads:
-        gtune = torch.randn((B, Amax, 3), device=dev)
-        opts, tms = tpl.tpl_fullatom_autotune(A, S, Ln, coords, na, gtune, gang, fa_ws,
-                                              bwd_mode=opts.bwd_mode)
-        tuned = {"threads": opts.threads, "schedule": opts.schedule, "fwd_bwd_ms": tms}
+        if args.bwd == "coords" and args.fusion == "backward":
+            # the three calls of the timed step
+            opts, tms = tpl.tpl_fullatom_lrmsd_autotune(A, S, Ln, coords, na, target, wgt, lr, lr_ws, gang, fa_ws)
+            tuned = {"threads": opts.threads, "schedule": opts.schedule, "step_ms": tms}
+        else:
+            gtune = torch.randn((B, Amax, 3), device=dev)
+            opts, tms = tpl.tpl_fullatom_autotune(A, S, Ln, coords, na, gtune, gang, fa_ws,
+                                                  bwd_mode=opts.bwd_mode)
+            tuned = {"threads": opts.threads, "schedule": opts.schedule, "fwd_bwd_ms": tms}
 
     st = Step()
+    st.shape = f"threads={opts.threads or 256}"
     res = int(lengths.sum())
     st.kernels = {"fullatom_forward": ["schedule_kernel", "fa_fwd_kernel"],
                   "lrmsd_forward": ["lrmsd_moments_kernel", "lrmsd_residual_kernel"]}
@@ -464,14 +479,21 @@ def setup_backbone_uneven(args, tpl, torch, dev, d):
     torch.cuda.synchronize()
     tuned = None
     if not args.no_autotune and not args.threads and not args.res_per_thread:
-        gtune = torch.randn((B, 3 * Lmax, 3), device=dev)
-        opts, tms = tpl.tpl_backbone_autotune(A, Ln, coords, gtune, gang, bb_ws, bwd_mode=opts.bwd_mode)
-        tuned = {"threads": opts.threads, "res_per_thread": opts.res_per_thread,
-                 "schedule": opts.schedule, "fwd_bwd_ms": tms}
+        if args.bwd == "coords" and not args.unfused:
+            # the three calls of the timed step
+            opts, tms = tpl.tpl_backbone_lrmsd_autotune(A, Ln, coords, target, na, wgt, lr, lr_ws, gang, bb_ws)
+            tuned = {"threads": opts.threads, "res_per_thread": opts.res_per_thread,
+                     "schedule": opts.schedule, "step_ms": tms}
+        else:
+            gtune = torch.randn((B, 3 * Lmax, 3), device=dev)
+            opts, tms = tpl.tpl_backbone_autotune(A, Ln, coords, gtune, gang, bb_ws, bwd_mode=opts.bwd_mode)
+            tuned = {"threads": opts.threads, "res_per_thread": opts.res_per_thread,
+                     "schedule": opts.schedule, "fwd_bwd_ms": tms}
     n_atoms = int(na_host.sum())
     res = int(lengths.sum())
 
     st = Step()
+    st.shape = f"threads={opts.threads or 128},res_per_thread={opts.res_per_thread or 4}"
     st.kernels = {"backbone_forward": ["schedule_kernel", "bb_fwd_kernel"],
                   "lrmsd_forward": ["lrmsd_moments_kernel", "lrmsd_residual_kernel"]}
     st.alg = {"backbone_forward": 48 * res, "lrmsd_forward": 24 * n_atoms}
@@ -546,6 +568,7 @@ def setup_lrmsd_batch(args, tpl, torch, dev, d):
     n_atoms = int(n.sum())
 
     st = Step()
+    st.shape = None
     st.calls = [("lrmsd_forward", lambda: tpl.tpl_lrmsd_forward(X, Y, NA, lr, ws)),
                 ("lrmsd_backward", lambda: tpl.tpl_lrmsd_backward(up, X, Y, NA, gx, ws))]
     st.kernels = {"lrmsd_forward": ["lrmsd_moments_kernel", "lrmsd_residual_kernel"],
@@ -720,6 +743,8 @@ def run_tpl(args):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = st.alg[dom] / (mean_ms[names.index(dom)] * 1e-3) / 1e9
     tr = TRAFFIC.get((args.workload, dom))
+    if tr is not None and tr[3] is not None and tr[3] != st.shape:
+        tr = None  # captured at another launch shape
     traffic = None
     if tr is not None:
         traffic = tr[0] * (st.atoms if tr[1] == "atom" else st.units)

@@ -323,7 +323,7 @@ tpl_status tpl_get_status(tpl_stream stream, int* device_status);
  * caller's batch for every supported launch shape and schedule -- backbone:
  * threads 64..512 x residues per thread 1, 2, 4 x {PACKED, LONGEST_FIRST};
  * full atom: threads 64, 128, 192, 256, 384, 512 x {BATCH_ORDER, LONGEST_FIRST} -- times each with
- * CUDA events on `stream` (one untimed pass, best of three), and writes the
+ * CUDA events on `stream` (one untimed pass, best of five), and writes the
  * fastest options to *best (and its time in ms to *best_ms if not NULL).
  * `bwd_mode` is kept in every candidate.  The arguments are those of the
  * forward and backward calls; coords, num_atoms and grad_angles are
@@ -338,6 +338,24 @@ tpl_status tpl_fullatom_autotune(const float* angles, const uint8_t* seq, const 
                                  const float* grad_coords, float* grad_angles, void* workspace,
                                  size_t workspace_bytes, int bwd_mode, tpl_opts* best, float* best_ms,
                                  tpl_stream stream);
+
+/* Autotuners of a training step on the LRMSD loss: as above, but each
+ * candidate is timed on the three calls such a step makes -- the forward,
+ * tpl_lrmsd_forward(coords, target, num_atoms, P = B, Nmax = 3 Lmax or Amax)
+ * and the fused backward tpl_*_backward_lrmsd with grad_lrmsd [B] -- with
+ * bwd_mode FROM_COORDS.  coords, lrmsd [B], lrmsd_workspace, grad_angles
+ * (and num_atoms for the full atom) are overwritten; for the backbone,
+ * num_atoms [B] = 3 lengths is an input. */
+tpl_status tpl_backbone_lrmsd_autotune(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                       float* coords, const float* target, const int32_t* num_atoms,
+                                       const float* grad_lrmsd, float* lrmsd, void* lrmsd_workspace,
+                                       size_t lrmsd_workspace_bytes, float* grad_angles, void* workspace,
+                                       size_t workspace_bytes, tpl_opts* best, float* best_ms, tpl_stream stream);
+tpl_status tpl_fullatom_lrmsd_autotune(const float* angles, const uint8_t* seq, const int32_t* lengths, int B,
+                                       int Lmax, int Amax, float* coords, int32_t* num_atoms, const float* target,
+                                       const float* grad_lrmsd, float* lrmsd, void* lrmsd_workspace,
+                                       size_t lrmsd_workspace_bytes, float* grad_angles, void* workspace,
+                                       size_t workspace_bytes, tpl_opts* best, float* best_ms, tpl_stream stream);
 
 /* Diagnostic (the paper has no counterpart): runs, in one thread of a
  * one-CTA launch on `stream`, the bounded wait that the chain kernels use

@@ -30,6 +30,7 @@ __all__ = [
     "tpl_backbone_backward_ref64", "tpl_fullatom_forward_ref64", "tpl_fullatom_backward_ref64",
     "tpl_lrmsd_forward_ref64", "tpl_lrmsd_backward_ref64", "tpl_get_status",
     "tpl_selftest_wait_timeout", "tpl_backbone_autotune", "tpl_fullatom_autotune",
+    "tpl_backbone_lrmsd_autotune", "tpl_fullatom_lrmsd_autotune",
     "tpl_fullatom_backward_lrmsd", "tpl_backbone_backward_lrmsd", "tpl_fullatom_lrmsd_workspace_size",
     "tpl_fullatom_lrmsd_forward", "tpl_fullatom_lrmsd_backward", "backbone",
     "fullatom", "lrmsd", "residue_table", "fullatom_max_atoms", "BWD_RECOMPUTE",
@@ -110,6 +111,8 @@ def load_library():
             "tpl_selftest_wait_timeout": ([P, P], I),
             "tpl_backbone_autotune": ([P, P, I, I, P, P, P, P, Z, I, O, F, P], I),
             "tpl_fullatom_autotune": ([P, P, P, I, I, I, P, P, P, P, P, Z, I, O, F, P], I),
+            "tpl_backbone_lrmsd_autotune": ([P, P, I, I, P, P, P, P, P, P, Z, P, P, Z, O, F, P], I),
+            "tpl_fullatom_lrmsd_autotune": ([P, P, P, I, I, I, P, P, P, P, P, P, Z, P, P, Z, O, F, P], I),
             "tpl_last_error": ([], ctypes.c_char_p),
             "tpl_version": ([], ctypes.c_char_p),
         }
@@ -241,6 +244,47 @@ def tpl_fullatom_autotune(angles, seq, lengths, coords, num_atoms, grad_coords, 
         _ptr(_cuda(grad_angles, torch.float32, "grad_angles")), _ptr(workspace),
         workspace.numel() * workspace.element_size(), int(bwd_mode), ctypes.byref(best),
         ctypes.byref(ms), _stream(angles, stream)))
+    return best, ms.value
+
+
+def tpl_backbone_lrmsd_autotune(angles, lengths, coords, target, num_atoms, grad_lrmsd, lrmsd,
+                                lrmsd_workspace, grad_angles, workspace, stream=None):
+    """Times the LRMSD training step (forward, tpl_lrmsd_forward, fused backward)
+    for every launch shape and schedule; returns (fastest Opts, its milliseconds).
+    Overwrites coords, lrmsd, lrmsd_workspace and grad_angles.  Not capturable."""
+    B, _, Lmax = angles.shape
+    best = Opts()
+    ms = ctypes.c_float(0.0)
+    _check("tpl_backbone_lrmsd_autotune", load_library().tpl_backbone_lrmsd_autotune(
+        _ptr(_cuda(angles, torch.float32, "angles")), _ptr(_cuda(lengths, torch.int32, "lengths")),
+        B, Lmax, _ptr(_cuda(coords, torch.float32, "coords")), _ptr(_cuda(target, torch.float32, "target")),
+        _ptr(_cuda(num_atoms, torch.int32, "num_atoms")), _ptr(_cuda(grad_lrmsd, torch.float32, "grad_lrmsd")),
+        _ptr(_cuda(lrmsd, torch.float32, "lrmsd")), _ptr(lrmsd_workspace),
+        lrmsd_workspace.numel() * lrmsd_workspace.element_size(),
+        _ptr(_cuda(grad_angles, torch.float32, "grad_angles")), _ptr(workspace),
+        workspace.numel() * workspace.element_size(), ctypes.byref(best), ctypes.byref(ms),
+        _stream(angles, stream)))
+    return best, ms.value
+
+
+def tpl_fullatom_lrmsd_autotune(angles, seq, lengths, coords, num_atoms, target, grad_lrmsd, lrmsd,
+                                lrmsd_workspace, grad_angles, workspace, stream=None):
+    """As tpl_backbone_lrmsd_autotune for the full-atom calls; also overwrites
+    num_atoms."""
+    B, _, Lmax = angles.shape
+    Amax = coords.shape[1]
+    best = Opts()
+    ms = ctypes.c_float(0.0)
+    _check("tpl_fullatom_lrmsd_autotune", load_library().tpl_fullatom_lrmsd_autotune(
+        _ptr(_cuda(angles, torch.float32, "angles")), _ptr(_cuda(seq, torch.uint8, "seq")),
+        _ptr(_cuda(lengths, torch.int32, "lengths")), B, Lmax, Amax,
+        _ptr(_cuda(coords, torch.float32, "coords")), _ptr(_cuda(num_atoms, torch.int32, "num_atoms")),
+        _ptr(_cuda(target, torch.float32, "target")), _ptr(_cuda(grad_lrmsd, torch.float32, "grad_lrmsd")),
+        _ptr(_cuda(lrmsd, torch.float32, "lrmsd")), _ptr(lrmsd_workspace),
+        lrmsd_workspace.numel() * lrmsd_workspace.element_size(),
+        _ptr(_cuda(grad_angles, torch.float32, "grad_angles")), _ptr(workspace),
+        workspace.numel() * workspace.element_size(), ctypes.byref(best), ctypes.byref(ms),
+        _stream(angles, stream)))
     return best, ms.value
 
 

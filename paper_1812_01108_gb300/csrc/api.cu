@@ -354,7 +354,7 @@ namespace {
 // schedule on the caller's own batch (CUDA events on `stream`; one untimed
 // pass, then the best of `kTuneReps`) and returns the fastest options.
 // ---------------------------------------------------------------------------
-constexpr int kTuneReps = 3;
+constexpr int kTuneReps = 5;
 
 template <class Step>
 tpl_status tune(const tpl_opts* cands, int n, cudaStream_t s, const Step& step, tpl_opts* best,
@@ -796,12 +796,7 @@ int tpl_fullatom_max_atoms(const uint8_t* seq_host, const int32_t* lengths_host,
     return best;
 }
 
-tpl_status tpl_backbone_autotune(const float* angles, const int32_t* lengths, int B, int Lmax,
-                                 float* coords, const float* grad_coords, float* grad_angles,
-                                 void* workspace, size_t workspace_bytes, int bwd_mode, tpl_opts* best,
-                                 float* best_ms, tpl_stream stream) {
-    if (!best) return fail(TPL_ERR_INVALID_ARG, "best is NULL");
-    tpl_opts cands[32];
+int backbone_candidates(int bwd_mode, tpl_opts* cands) {
     int n = 0;
     const int threads[4] = {64, 128, 256, 512}, ks[3] = {1, 2, 4}, sch[2] = {TPL_SCHED_PACKED, TPL_SCHED_LONGEST_FIRST};
     for (int si = 0; si < 2; ++si)
@@ -816,21 +811,10 @@ tpl_status tpl_backbone_autotune(const float* angles, const int32_t* lengths, in
                 o.schedule = sch[si];
                 cands[n++] = o;
             }
-    return tune(cands, n, reinterpret_cast<cudaStream_t>(stream), [&](const tpl_opts& o) {
-        tpl_status st = tpl_backbone_forward(angles, lengths, B, Lmax, coords, workspace, workspace_bytes, &o, stream);
-        if (st) return st;
-        return tpl_backbone_backward(angles, lengths, B, Lmax, coords, grad_coords, grad_angles, workspace,
-                                     workspace_bytes, &o, stream);
-    }, best, best_ms);
+    return n;
 }
 
-tpl_status tpl_fullatom_autotune(const float* angles, const uint8_t* seq, const int32_t* lengths, int B,
-                                 int Lmax, int Amax, float* coords, int32_t* num_atoms,
-                                 const float* grad_coords, float* grad_angles, void* workspace,
-                                 size_t workspace_bytes, int bwd_mode, tpl_opts* best, float* best_ms,
-                                 tpl_stream stream) {
-    if (!best) return fail(TPL_ERR_INVALID_ARG, "best is NULL");
-    tpl_opts cands[12];
+int fullatom_candidates(int bwd_mode, tpl_opts* cands) {
     int n = 0;
     const int threads[6] = {64, 128, 192, 256, 384, 512};
     const int sch[2] = {TPL_SCHED_BATCH_ORDER, TPL_SCHED_LONGEST_FIRST};
@@ -843,12 +827,79 @@ tpl_status tpl_fullatom_autotune(const float* angles, const uint8_t* seq, const 
             o.schedule = sch[si];
             cands[n++] = o;
         }
+    return n;
+}
+
+tpl_status tpl_backbone_autotune(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                 float* coords, const float* grad_coords, float* grad_angles,
+                                 void* workspace, size_t workspace_bytes, int bwd_mode, tpl_opts* best,
+                                 float* best_ms, tpl_stream stream) {
+    if (!best) return fail(TPL_ERR_INVALID_ARG, "best is NULL");
+    tpl_opts cands[32];
+    const int n = backbone_candidates(bwd_mode, cands);
+    return tune(cands, n, reinterpret_cast<cudaStream_t>(stream), [&](const tpl_opts& o) {
+        tpl_status st = tpl_backbone_forward(angles, lengths, B, Lmax, coords, workspace, workspace_bytes, &o, stream);
+        if (st) return st;
+        return tpl_backbone_backward(angles, lengths, B, Lmax, coords, grad_coords, grad_angles, workspace,
+                                     workspace_bytes, &o, stream);
+    }, best, best_ms);
+}
+
+tpl_status tpl_backbone_lrmsd_autotune(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                       float* coords, const float* target, const int32_t* num_atoms,
+                                       const float* grad_lrmsd, float* lrmsd, void* lrmsd_workspace,
+                                       size_t lrmsd_workspace_bytes, float* grad_angles, void* workspace,
+                                       size_t workspace_bytes, tpl_opts* best, float* best_ms, tpl_stream stream) {
+    if (!best) return fail(TPL_ERR_INVALID_ARG, "best is NULL");
+    tpl_opts cands[32];
+    const int n = backbone_candidates(TPL_BWD_FROM_COORDS, cands);
+    return tune(cands, n, reinterpret_cast<cudaStream_t>(stream), [&](const tpl_opts& o) {
+        tpl_status st = tpl_backbone_forward(angles, lengths, B, Lmax, coords, workspace, workspace_bytes, &o, stream);
+        if (st) return st;
+        st = tpl_lrmsd_forward(coords, target, num_atoms, B, 3 * Lmax, lrmsd, lrmsd_workspace, lrmsd_workspace_bytes,
+                               stream);
+        if (st) return st;
+        return tpl_backbone_backward_lrmsd(angles, lengths, B, Lmax, coords, target, grad_lrmsd, lrmsd_workspace,
+                                           lrmsd_workspace_bytes, grad_angles, workspace, workspace_bytes, &o,
+                                           stream);
+    }, best, best_ms);
+}
+
+tpl_status tpl_fullatom_autotune(const float* angles, const uint8_t* seq, const int32_t* lengths, int B,
+                                 int Lmax, int Amax, float* coords, int32_t* num_atoms,
+                                 const float* grad_coords, float* grad_angles, void* workspace,
+                                 size_t workspace_bytes, int bwd_mode, tpl_opts* best, float* best_ms,
+                                 tpl_stream stream) {
+    if (!best) return fail(TPL_ERR_INVALID_ARG, "best is NULL");
+    tpl_opts cands[12];
+    const int n = fullatom_candidates(bwd_mode, cands);
     return tune(cands, n, reinterpret_cast<cudaStream_t>(stream), [&](const tpl_opts& o) {
         tpl_status st = tpl_fullatom_forward(angles, seq, lengths, B, Lmax, Amax, coords, num_atoms, workspace,
                                              workspace_bytes, &o, stream);
         if (st) return st;
         return tpl_fullatom_backward(angles, seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles,
                                      workspace, workspace_bytes, &o, stream);
+    }, best, best_ms);
+}
+
+tpl_status tpl_fullatom_lrmsd_autotune(const float* angles, const uint8_t* seq, const int32_t* lengths, int B,
+                                       int Lmax, int Amax, float* coords, int32_t* num_atoms, const float* target,
+                                       const float* grad_lrmsd, float* lrmsd, void* lrmsd_workspace,
+                                       size_t lrmsd_workspace_bytes, float* grad_angles, void* workspace,
+                                       size_t workspace_bytes, tpl_opts* best, float* best_ms, tpl_stream stream) {
+    if (!best) return fail(TPL_ERR_INVALID_ARG, "best is NULL");
+    tpl_opts cands[12];
+    const int n = fullatom_candidates(TPL_BWD_FROM_COORDS, cands);
+    return tune(cands, n, reinterpret_cast<cudaStream_t>(stream), [&](const tpl_opts& o) {
+        tpl_status st = tpl_fullatom_forward(angles, seq, lengths, B, Lmax, Amax, coords, num_atoms, workspace,
+                                             workspace_bytes, &o, stream);
+        if (st) return st;
+        st = tpl_lrmsd_forward(coords, target, num_atoms, B, Amax, lrmsd, lrmsd_workspace, lrmsd_workspace_bytes,
+                               stream);
+        if (st) return st;
+        return tpl_fullatom_backward_lrmsd(angles, seq, lengths, B, Lmax, Amax, coords, target, grad_lrmsd,
+                                           lrmsd_workspace, lrmsd_workspace_bytes, grad_angles, workspace,
+                                           workspace_bytes, &o, stream);
     }, best, best_ms);
 }
 

@@ -197,6 +197,41 @@ def test_autotuner_picks_a_valid_shape_and_its_results_match():
     assert rel_err(ga32, oracle.backbone_backward(a, lengths, g)) <= GRAD_TOL
 
 
+def test_lrmsd_step_autotuner_picks_a_valid_shape_and_its_step_matches_the_oracle():
+    """tpl_backbone_lrmsd_autotune times forward, LRMSD forward and the fused
+    backward per candidate; the step with its pick agrees with the oracle."""
+    d = require_gpu()
+    rng = np.random.default_rng(49)
+    lengths = workloads.lengths_loguniform(64, 20, 600, rng)
+    a, _ = _inputs(lengths, 50, Lmax=600)
+    ta = workloads.perturb_angles(a, lengths, rng)
+    B, _, Lmax = a.shape
+    A, Ln = dev(a, d), dev(lengths, d)
+    ws = torch.empty(tpl.tpl_backbone_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    tgt = torch.zeros((B, 3 * Lmax, 3), device=d)
+    tpl.tpl_backbone_forward(dev(ta, d), Ln, tgt, ws)
+    coords = torch.zeros_like(tgt)
+    na = dev((3 * lengths).astype(np.int32), d)
+    lr = torch.zeros((B,), device=d)
+    lr_ws = torch.empty(tpl.tpl_lrmsd_workspace_size(B, 3 * Lmax), dtype=torch.uint8, device=d)
+    w = dev(np.linspace(-1.0, 2.0, B).astype(np.float32), d)
+    ga = torch.empty_like(A)
+    best, ms = tpl.tpl_backbone_lrmsd_autotune(A, Ln, coords, tgt, na, w, lr, lr_ws, ga, ws)
+    assert ms > 0 and best.threads in (64, 128, 256, 512) and best.res_per_thread in (1, 2, 4)
+    assert best.schedule in (tpl.SCHED_PACKED, tpl.SCHED_LONGEST_FIRST)
+    assert best.bwd_mode == tpl.BWD_FROM_COORDS
+    ga.fill_(float("nan"))
+    lr.fill_(float("nan"))
+    tpl.tpl_backbone_forward(A, Ln, coords, ws, best)
+    tpl.tpl_lrmsd_forward(coords, tgt, na, lr, lr_ws)
+    tpl.tpl_backbone_backward_lrmsd(A, Ln, coords, tgt, w, lr_ws, ga, ws, best)
+    torch.cuda.synchronize()
+    c32, t32 = host(coords), host(tgt)
+    assert np.abs(host(lr) - oracle.lrmsd_forward(c32, t32, 3 * lengths)).max() <= 1e-5
+    g64 = oracle.lrmsd_backward(host(w).astype(np.float64), c32, t32, 3 * lengths)
+    assert rel_err(host(ga), oracle.backbone_backward(a, lengths, g64)) <= GRAD_TOL
+
+
 @pytest.mark.parametrize("threads,k,sched", [(128, 4, tpl.SCHED_PACKED), (256, 2, tpl.SCHED_LONGEST_FIRST),
                                               (64, 1, tpl.SCHED_PACKED)])
 def test_fused_lrmsd_backward_equals_the_two_calls_and_the_oracle(threads, k, sched):

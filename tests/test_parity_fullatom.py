@@ -150,6 +150,42 @@ def test_autotuner_picks_a_valid_shape_and_its_results_match(reference):
     assert rel_err(ga32, g64) <= GRAD_TOL
 
 
+def test_lrmsd_step_autotuner_picks_a_valid_shape_and_its_step_matches_the_oracle():
+    """tpl_fullatom_lrmsd_autotune times forward, LRMSD forward and the fused
+    backward per candidate; the step with its pick agrees with the oracle."""
+    d = require_gpu()
+    rng = workloads.rng_for(4, salt=37)
+    lengths = np.array([700, 333, 64, 1, 0, 257, 512, 129], np.int32)
+    a, seq = workloads.fullatom_inputs(lengths, rng)
+    ta = workloads.perturb_angles(a, lengths, rng, rows=(0, 1, 3, 4, 5, 6))
+    Amax = workloads.pad_to(oracle.max_atoms(seq, lengths))
+    B, _, Lmax = a.shape
+    A, S, Ln = dev(a, d), dev(seq, d), dev(lengths, d)
+    fa_ws = torch.empty(tpl.tpl_fullatom_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    tgt = torch.zeros((B, Amax, 3), device=d)
+    na = torch.zeros((B,), dtype=torch.int32, device=d)
+    tpl.tpl_fullatom_forward(dev(ta, d), S, Ln, tgt, na, fa_ws)
+    coords = torch.zeros_like(tgt)
+    lr = torch.zeros((B,), device=d)
+    lr_ws = torch.empty(tpl.tpl_lrmsd_workspace_size(B, Amax), dtype=torch.uint8, device=d)
+    w = dev(np.linspace(0.5, 2.0, B).astype(np.float32), d)
+    ga = torch.empty_like(A)
+    best, ms = tpl.tpl_fullatom_lrmsd_autotune(A, S, Ln, coords, na, tgt, w, lr, lr_ws, ga, fa_ws)
+    assert ms > 0 and best.threads in (64, 128, 192, 256, 384, 512)
+    assert best.schedule in (tpl.SCHED_BATCH_ORDER, tpl.SCHED_LONGEST_FIRST)
+    assert best.bwd_mode == tpl.BWD_FROM_COORDS
+    ga.fill_(float("nan"))
+    lr.fill_(float("nan"))
+    tpl.tpl_fullatom_forward(A, S, Ln, coords, na, fa_ws, best)
+    tpl.tpl_lrmsd_forward(coords, tgt, na, lr, lr_ws)
+    tpl.tpl_fullatom_backward_lrmsd(A, S, Ln, coords, tgt, w, lr_ws, ga, fa_ws, best)
+    torch.cuda.synchronize()
+    c32, t32, n32 = host(coords), host(tgt), host(na)
+    assert np.abs(host(lr) - oracle.lrmsd_forward(c32, t32, n32)).max() <= 1e-5
+    g64 = oracle.lrmsd_backward(host(w).astype(np.float64), c32, t32, n32)
+    assert rel_err(host(ga), oracle.fullatom_backward(a, seq, lengths, g64)) <= GRAD_TOL
+
+
 @pytest.mark.parametrize("threads", [256, 64])
 def test_fused_lrmsd_backward_equals_the_two_calls_and_the_oracle(threads):
     """tpl_fullatom_backward_lrmsd = tpl_lrmsd_backward + tpl_fullatom_backward
