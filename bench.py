@@ -59,10 +59,10 @@ TRAFFIC = {
     # lrmsd_pair_kernel
     ("training_step", "lrmsd_forward"): (24.0737, "atom", "profiles/lrmsd_kernels_training_step_256x700.md", None),
     # bb_fwd_kernel<256, 4> (the schedule kernel's few bytes not counted)
-    ("backbone_uneven", "backbone_forward"): (80.0168, "residue", "profiles/backbone_kernels_backbone_uneven_4096.md",
+    ("backbone_uneven", "backbone_forward"): (80.8140, "residue", "profiles/backbone_kernels_backbone_uneven_4096.md",
                                               "threads=256,res_per_thread=4"),
     # bb_bwd_kernel<256, 4, 1, 1>
-    ("backbone_uneven", "lrmsd_backbone_backward"): (82.9732, "residue",
+    ("backbone_uneven", "lrmsd_backbone_backward"): (81.9417, "residue",
                                                      "profiles/backbone_kernels_backbone_uneven_4096.md",
                                                      "threads=256,res_per_thread=4"),
     # moments + solve + residual + finalize
@@ -317,6 +317,13 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU workloads
+def lrmsd_forward_kernels(tpl, P):
+    """Kernels of tpl_lrmsd_forward for P pairs on this device (the library's plan)."""
+    if tpl.tpl_lrmsd_forward_launches(P) == 1:
+        return ["lrmsd_pair_kernel"]
+    return ["lrmsd_moments_kernel", "lrmsd_solve_kernel", "lrmsd_residual_kernel", "lrmsd_finalize_kernel"]
+
+
 class Step:
     """The C-ABI calls of one step with their bookkeeping.
 
@@ -374,7 +381,7 @@ def setup_training_step(args, tpl, torch, dev, d):
     st.shape = f"threads={opts.threads or 256}"
     res = int(lengths.sum())
     st.kernels = {"fullatom_forward": ["schedule_kernel", "fa_fwd_kernel"],
-                  "lrmsd_forward": ["lrmsd_moments_kernel", "lrmsd_residual_kernel"]}
+                  "lrmsd_forward": lrmsd_forward_kernels(tpl, B)}
     st.alg = {"fullatom_forward": res * (28 + 1) + 12 * n_atoms, "lrmsd_forward": 24 * n_atoms}
     st_ws = None
     if args.fusion == "step" and args.bwd == "coords":
@@ -495,7 +502,7 @@ def setup_backbone_uneven(args, tpl, torch, dev, d):
     st = Step()
     st.shape = f"threads={opts.threads or 128},res_per_thread={opts.res_per_thread or 4}"
     st.kernels = {"backbone_forward": ["schedule_kernel", "bb_fwd_kernel"],
-                  "lrmsd_forward": ["lrmsd_moments_kernel", "lrmsd_residual_kernel"]}
+                  "lrmsd_forward": lrmsd_forward_kernels(tpl, B)}
     st.alg = {"backbone_forward": 48 * res, "lrmsd_forward": 24 * n_atoms}
     if args.unfused or args.bwd != "coords":
         st.calls = [
@@ -571,7 +578,7 @@ def setup_lrmsd_batch(args, tpl, torch, dev, d):
     st.shape = None
     st.calls = [("lrmsd_forward", lambda: tpl.tpl_lrmsd_forward(X, Y, NA, lr, ws)),
                 ("lrmsd_backward", lambda: tpl.tpl_lrmsd_backward(up, X, Y, NA, gx, ws))]
-    st.kernels = {"lrmsd_forward": ["lrmsd_moments_kernel", "lrmsd_residual_kernel"],
+    st.kernels = {"lrmsd_forward": lrmsd_forward_kernels(tpl, P),
                   "lrmsd_backward": ["lrmsd_grad_kernel"]}
     st.launches = {k: len(v) for k, v in st.kernels.items()}
     st.alg = {"lrmsd_forward": 24 * n_atoms, "lrmsd_backward": 36 * n_atoms}

@@ -239,6 +239,12 @@ tpl_status tpl_lrmsd_forward(const float* input, const float* target, const int3
                              int P, int Nmax, float* lrmsd, void* workspace,
                              size_t workspace_bytes, tpl_stream stream);
 
+/* Kernels tpl_lrmsd_forward launches for P pairs on the current device: 1
+ * when the batch fits the GPU in one wave of one CTA per pair (moments,
+ * eigen-solve and residuals in one kernel), else 4 (moments, eigen-solve,
+ * residuals, LRMSD); 0 for P <= 0.  Needs no workspace; launches nothing. */
+int tpl_lrmsd_forward_launches(int P);
+
 /* Section 4: grad_input_i = grad_lrmsd[p] (y'_i - U x'_i) / (N LRMSD); 0 when
  * LRMSD < 1e-12 (status bit TPL_STATUS_ZERO_LRMSD).
  *   grad_lrmsd [P] in, grad_input [P][Nmax][3] out; `workspace` as filled by

@@ -30,7 +30,7 @@ __all__ = [
     "tpl_backbone_backward_ref64", "tpl_fullatom_forward_ref64", "tpl_fullatom_backward_ref64",
     "tpl_lrmsd_forward_ref64", "tpl_lrmsd_backward_ref64", "tpl_get_status",
     "tpl_selftest_wait_timeout", "tpl_backbone_autotune", "tpl_fullatom_autotune",
-    "tpl_backbone_lrmsd_autotune", "tpl_fullatom_lrmsd_autotune",
+    "tpl_backbone_lrmsd_autotune", "tpl_fullatom_lrmsd_autotune", "tpl_lrmsd_forward_launches",
     "tpl_fullatom_backward_lrmsd", "tpl_backbone_backward_lrmsd", "tpl_fullatom_lrmsd_workspace_size",
     "tpl_fullatom_lrmsd_forward", "tpl_fullatom_lrmsd_backward", "backbone",
     "fullatom", "lrmsd", "residue_table", "fullatom_max_atoms", "BWD_RECOMPUTE",
@@ -111,6 +111,7 @@ def load_library():
             "tpl_selftest_wait_timeout": ([P, P], I),
             "tpl_backbone_autotune": ([P, P, I, I, P, P, P, P, Z, I, O, F, P], I),
             "tpl_fullatom_autotune": ([P, P, P, I, I, I, P, P, P, P, P, Z, I, O, F, P], I),
+            "tpl_lrmsd_forward_launches": ([I], I),
             "tpl_backbone_lrmsd_autotune": ([P, P, I, I, P, P, P, P, P, P, Z, P, P, Z, O, F, P], I),
             "tpl_fullatom_lrmsd_autotune": ([P, P, P, I, I, I, P, P, P, P, P, P, Z, P, P, Z, O, F, P], I),
             "tpl_last_error": ([], ctypes.c_char_p),
@@ -245,6 +246,11 @@ def tpl_fullatom_autotune(angles, seq, lengths, coords, num_atoms, grad_coords, 
         workspace.numel() * workspace.element_size(), int(bwd_mode), ctypes.byref(best),
         ctypes.byref(ms), _stream(angles, stream)))
     return best, ms.value
+
+
+def tpl_lrmsd_forward_launches(P):
+    """Kernels tpl_lrmsd_forward launches for P pairs on the current device."""
+    return int(load_library().tpl_lrmsd_forward_launches(int(P)))
 
 
 def tpl_backbone_lrmsd_autotune(angles, lengths, coords, target, num_atoms, grad_lrmsd, lrmsd,

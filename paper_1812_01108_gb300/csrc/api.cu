@@ -416,6 +416,8 @@ size_t tpl_lrmsd_workspace_size(int P, int Nmax) {
     return lrmsd_ws_bytes(P, Nmax);
 }
 
+int tpl_lrmsd_forward_launches(int P) { return lrmsd_forward_launches(P); }
+
 tpl_status tpl_backbone_forward(const float* angles, const int32_t* lengths, int B, int Lmax,
                                 float* coords, void* workspace, size_t workspace_bytes,
                                 const tpl_opts* opts, tpl_stream stream) {

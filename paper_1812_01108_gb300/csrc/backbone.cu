@@ -131,7 +131,7 @@ __device__ __forceinline__ Rigid thread_product(const float* __restrict__ ang, i
 // K1: forward.  One tile (NT*K residues) per step of a persistent CTA.
 // ---------------------------------------------------------------------------
 template <int NT, int K>
-__global__ void __launch_bounds__(NT) bb_fwd_kernel(const float* __restrict__ angles,
+__global__ void __launch_bounds__(NT, 768 / NT) bb_fwd_kernel(const float* __restrict__ angles,
                                                     const int32_t* __restrict__ lengths, int Lmax,
                                                     float* __restrict__ coords, ChainWs ws,
                                                     BackboneConst bc) {
@@ -283,7 +283,7 @@ __device__ __forceinline__ bool ws_matches(const ChainWs& ws, int tile, int B, i
 // LR (with FROM_COORDS): the coordinate gradient is the LRMSD gradient,
 // formed from the coordinates, the target and the LRMSD state.
 template <int NT, int K, bool FROM_COORDS, bool LR>
-__global__ void __launch_bounds__(NT) bb_bwd_kernel(const float* __restrict__ angles,
+__global__ void __launch_bounds__(NT, 512 / NT) bb_bwd_kernel(const float* __restrict__ angles,
                                                     const int32_t* __restrict__ lengths, int B,
                                                     int Lmax, const float* __restrict__ coords,
                                                     const float* __restrict__ grad_coords,

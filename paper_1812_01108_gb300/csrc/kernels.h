@@ -87,6 +87,8 @@ size_t lrmsd_ws_bytes(int P, int Nmax);
 // Per-pair state the LRMSD forward leaves in its workspace: U (9, row-major),
 // centroid of the target, centroid of the input, 1 / (N LRMSD) (16 floats).
 const float* lrmsd_state(const void* ws, int P, int Nmax);
+// Kernels tpl_lrmsd_forward launches for P pairs on the current device.
+int lrmsd_forward_launches(int P);
 cudaError_t launch_lrmsd_forward(const float* input, const float* target,
                                  const int32_t* num_atoms, int P, int Nmax, float* lrmsd,
                                  void* ws, cudaStream_t s);

@@ -37,24 +37,26 @@ namespace {
 constexpr int kWNT = 128;    // threads per CTA: four independent warp workers
 constexpr int kWarps = kWNT / 32;
 constexpr int kWC = 256;     // atoms per chunk: one warp, two groups of 4 atoms per lane
+constexpr int kMaxWpp = 8;   // most warps per pair in the streaming kernels
 constexpr int kMom = 17;     // sum dx (3), sum dy (3), sum dx dy^T (9), sum |dx|^2, sum |dy|^2
 constexpr int kSlot = 20;    // floats per chunk partial (5 float4)
 constexpr unsigned kFull = 0xffffffffu;
 
 struct WsLayout {
     size_t part1, part2, state, total;
-    int nch;
+    int parts;  // partial slots per pair: the most warps a pair can get
 };
 
 __host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 __host__ __device__ constexpr WsLayout ws_layout(int P, int Nmax) {
     WsLayout w{};
-    w.nch = (Nmax + kWC - 1) / kWC;
-    if (w.nch < 1) w.nch = 1;
-    size_t o = 0;  // partials: room for one warp per chunk
-    w.part1 = o; o = align256(o + (size_t)P * w.nch * kSlot * sizeof(float));
-    w.part2 = o; o = align256(o + (size_t)P * w.nch * sizeof(double));
+    w.parts = (Nmax + kWC - 1) / kWC;
+    if (w.parts > kMaxWpp) w.parts = kMaxWpp;
+    if (w.parts < 1) w.parts = 1;
+    size_t o = 0;
+    w.part1 = o; o = align256(o + (size_t)P * w.parts * kSlot * sizeof(float));
+    w.part2 = o; o = align256(o + (size_t)P * w.parts * sizeof(double));
     w.state = o; o = align256(o + (size_t)P * 16 * sizeof(float));  // U(9) xc(3) yc(3) scale
     w.total = o;
     return w;
@@ -526,7 +528,7 @@ __global__ void __launch_bounds__(kPNT, 2) lrmsd_pair_kernel(
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kWNT) lrmsd_moments_kernel(
     const float* __restrict__ input, const float* __restrict__ target,
-    const int32_t* __restrict__ num_atoms, int P, int Nmax, float* __restrict__ part1, int nch_max,
+    const int32_t* __restrict__ num_atoms, int P, int Nmax, float* __restrict__ part1, int pstride,
     int wpp) {
     const int lane = threadIdx.x & 31;
     const long long w = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -571,7 +573,7 @@ __global__ void __launch_bounds__(kWNT) lrmsd_moments_kernel(
     }
 #pragma unroll
     for (int k = 0; k < kMom; ++k) m[k] = warp_sum(m[k]);
-    float4* slot = reinterpret_cast<float4*>(part1 + ((size_t)p * nch_max + r) * kSlot);
+    float4* slot = reinterpret_cast<float4*>(part1 + ((size_t)p * pstride + r) * kSlot);
 #pragma unroll
     for (int k = 0; k < kSlot / 4; ++k)
         if (lane == k)
@@ -584,7 +586,7 @@ __global__ void __launch_bounds__(kWNT) lrmsd_moments_kernel(
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(32) lrmsd_solve_kernel(
     const float* __restrict__ input, const float* __restrict__ target,
-    const int32_t* __restrict__ num_atoms, int P, int Nmax, const float* __restrict__ part1, int nch_max,
+    const int32_t* __restrict__ num_atoms, int P, int Nmax, const float* __restrict__ part1, int pstride,
     int wpp, float* __restrict__ state) {
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     const int sub = gid & 3, lane = threadIdx.x & 31;
@@ -594,7 +596,7 @@ __global__ void __launch_bounds__(32) lrmsd_solve_kernel(
     float x0[3], y0[3];
     first_atoms(target + (size_t)p * Nmax * 3, input + (size_t)p * Nmax * 3, n, x0, y0);
     float S[kSlot];
-    quad_sum_partials(part1 + (size_t)p * nch_max * kSlot, num_parts(n, wpp), sub, S);
+    quad_sum_partials(part1 + (size_t)p * pstride * kSlot, num_parts(n, wpp), sub, S);
     quad_eigen_solve(S, x0, y0, n, sub, lane, active, state + 16 * (size_t)p);
 }
 
@@ -603,7 +605,7 @@ __global__ void __launch_bounds__(32) lrmsd_solve_kernel(
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kWNT) lrmsd_residual_kernel(
     const float* __restrict__ input, const float* __restrict__ target,
-    const int32_t* __restrict__ num_atoms, int P, int Nmax, double* __restrict__ part2, int nch_max,
+    const int32_t* __restrict__ num_atoms, int P, int Nmax, double* __restrict__ part2, int pstride,
     int wpp, const float* __restrict__ state) {
     const int lane = threadIdx.x & 31;
     const long long w = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -635,14 +637,14 @@ __global__ void __launch_bounds__(kWNT) lrmsd_residual_kernel(
         }
         tot += (double)warp_sum(acc);
     }
-    if (lane == 0) part2[(size_t)p * nch_max + r] = tot;
+    if (lane == 0) part2[(size_t)p * pstride + r] = tot;
 }
 
 // ---------------------------------------------------------------------------
 // K5d: LRMSD and gradient scale, four lanes per pair
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(32) lrmsd_finalize_kernel(
-    const int32_t* __restrict__ num_atoms, int P, int Nmax, const double* __restrict__ part2, int nch_max,
+    const int32_t* __restrict__ num_atoms, int P, int Nmax, const double* __restrict__ part2, int pstride,
     int wpp, float* __restrict__ state, float* __restrict__ lrmsd) {
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     const int sub = gid & 3;
@@ -651,7 +653,7 @@ __global__ void __launch_bounds__(32) lrmsd_finalize_kernel(
     const int n = pair_atoms(num_atoms, p, Nmax);
     const int np = num_parts(n, wpp);
     double sum = 0.0;
-    for (int k = sub; k < np; k += 4) sum += part2[(size_t)p * nch_max + k];
+    for (int k = sub; k < np; k += 4) sum += part2[(size_t)p * pstride + k];
     sum = quad_sum(sum, sub);
     if (active && sub == 0) {
         float lr, scale;
@@ -874,13 +876,18 @@ const float* lrmsd_state(const void* ws, int P, int Nmax) {
 }
 
 // Warps per pair of the streaming kernels: enough for about two rounds of the
-// GPU's resident warps, at most one per chunk.
-static int warps_per_pair(int P, int nch) {
+// GPU's resident warps, at most one per chunk and kMaxWpp (the partial slots).
+static int warps_per_pair(int P, int parts) {
     const long long resident = (long long)persistent_grid((const void*)lrmsd_moments_kernel, kWNT, 0) * kWarps;
     long long w = (2 * resident + P - 1) / P;
-    if (w > nch) w = nch;
+    if (w > parts) w = parts;
     return w < 1 ? 1 : (int)w;
 }
+
+// One CTA per pair when the batch fits the GPU in one wave of such CTAs.
+static bool pair_path(int P) { return P <= persistent_grid((const void*)lrmsd_pair_kernel, kPNT, 0); }
+
+int lrmsd_forward_launches(int P) { return P <= 0 ? 0 : (pair_path(P) ? 1 : 4); }
 
 cudaError_t launch_lrmsd_forward(const float* input, const float* target, const int32_t* num_atoms,
                                  int P, int Nmax, float* lrmsd, void* ws, cudaStream_t s) {
@@ -890,17 +897,17 @@ cudaError_t launch_lrmsd_forward(const float* input, const float* target, const 
     float* part1 = reinterpret_cast<float*>(base + L.part1);
     double* part2 = reinterpret_cast<double*>(base + L.part2);
     float* state = reinterpret_cast<float*>(base + L.state);
-    if (P <= persistent_grid((const void*)lrmsd_pair_kernel, kPNT, 0)) {
+    if (pair_path(P)) {
         lrmsd_pair_kernel<<<P, kPNT, 0, s>>>(input, target, num_atoms, P, Nmax, state, lrmsd);
         return cudaGetLastError();
     }
-    const int wpp = warps_per_pair(P, L.nch);
+    const int wpp = warps_per_pair(P, L.parts);
     const unsigned grid = (unsigned)(((long long)P * wpp + kWarps - 1) / kWarps);
     const unsigned quads = (unsigned)((4LL * P + 31) / 32);
-    lrmsd_moments_kernel<<<grid, kWNT, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.nch, wpp);
-    lrmsd_solve_kernel<<<quads, 32, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.nch, wpp, state);
-    lrmsd_residual_kernel<<<grid, kWNT, 0, s>>>(input, target, num_atoms, P, Nmax, part2, L.nch, wpp, state);
-    lrmsd_finalize_kernel<<<quads, 32, 0, s>>>(num_atoms, P, Nmax, part2, L.nch, wpp, state, lrmsd);
+    lrmsd_moments_kernel<<<grid, kWNT, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.parts, wpp);
+    lrmsd_solve_kernel<<<quads, 32, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.parts, wpp, state);
+    lrmsd_residual_kernel<<<grid, kWNT, 0, s>>>(input, target, num_atoms, P, Nmax, part2, L.parts, wpp, state);
+    lrmsd_finalize_kernel<<<quads, 32, 0, s>>>(num_atoms, P, Nmax, part2, L.parts, wpp, state, lrmsd);
     return cudaGetLastError();
 }
 
