@@ -24,7 +24,8 @@
 namespace tpl {
 
 constexpr int kMinTile = 64;          // smallest tile of any launch shape (sizes the workspace)
-constexpr int kSpinLimit = 1 << 20;   // polls of one flag (x 100 ns sleep) before giving up
+constexpr int kSpinLimit = 1 << 20;   // polls of one flag before giving up
+constexpr int kSpinFast = 64;         // polls back to back before each later poll sleeps 100 ns
 constexpr int kWsMagic = 0x54504c31;  // written by the schedule kernel, checked by the backward
 
 // Header words.
@@ -129,11 +130,13 @@ __device__ __forceinline__ int flag_acquire(const int* p) {
 }
 
 // Bounded wait for a nonzero flag.  Returns false (and flags the status word)
-// on timeout.
+// on timeout.  The first polls run back to back: a short wait (a neighbour
+// tile publishing moments later) is the common case, and a sleep requested
+// here lasts microseconds on this GPU, far longer than asked.
 __device__ __forceinline__ bool wait_flag(const int* p) {
     for (int it = 0; it < kSpinLimit; ++it) {
         if (flag_acquire(p) != 0) return true;
-        __nanosleep(100);
+        if (it >= kSpinFast) __nanosleep(100);
     }
     flag_status(TPL_STATUS_TIMEOUT);
     return false;
