@@ -53,16 +53,19 @@ DEFAULT_BATCH = {"training_step": 256, "backbone_uneven": 4096, "lrmsd_batch": 1
 TRAFFIC = {
     # (per-unit DRAM bytes, unit, profile, launch shape of the capture or None if the
     # kernels take none); cold-cache captures of one launch
+    # fa_fwd_kernel<384, 0> (the coordinates it writes stay in L2 during the capture)
+    ("training_step", "fullatom_forward"): (3.5172, "atom", "profiles/fa_kernels_training_step_256x700.md",
+                                            "threads=384"),
     # fa_bwd_coords_kernel<384, 1, 0> (LRMSD gradient formed in the kernel)
-    ("training_step", "lrmsd_fullatom_backward"): (24.7286, "atom", "profiles/fa_kernels_training_step_256x700.md",
+    ("training_step", "lrmsd_fullatom_backward"): (24.7292, "atom", "profiles/fa_kernels_training_step_256x700.md",
                                                    "threads=384"),
     # lrmsd_pair_kernel
     ("training_step", "lrmsd_forward"): (24.0737, "atom", "profiles/lrmsd_kernels_training_step_256x700.md", None),
     # bb_fwd_kernel<256, 4> (the schedule kernel's few bytes not counted)
-    ("backbone_uneven", "backbone_forward"): (80.8140, "residue", "profiles/backbone_kernels_backbone_uneven_4096.md",
+    ("backbone_uneven", "backbone_forward"): (80.9907, "residue", "profiles/backbone_kernels_backbone_uneven_4096.md",
                                               "threads=256,res_per_thread=4"),
     # bb_bwd_kernel<256, 4, 1, 1>
-    ("backbone_uneven", "lrmsd_backbone_backward"): (81.9417, "residue",
+    ("backbone_uneven", "lrmsd_backbone_backward"): (81.9533, "residue",
                                                      "profiles/backbone_kernels_backbone_uneven_4096.md",
                                                      "threads=256,res_per_thread=4"),
     # moments + solve + residual + finalize
