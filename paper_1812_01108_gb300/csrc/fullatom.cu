@@ -175,7 +175,7 @@ __host__ __device__ constexpr size_t fa_fwd_smem() {
 // CTAs per SM the forward and backward kernels are compiled for (register cap)
 template <int NT>
 __host__ __device__ constexpr int fa_min_blocks() {
-    return NT >= 512 ? 1 : (NT >= 384 ? 2 : (NT >= 256 ? 3 : (NT >= 192 ? 4 : 6)));
+    return NT >= 512 ? 1 : (NT >= 384 ? 2 : (NT >= 256 ? 4 : (NT >= 192 ? 5 : 8)));
 }
 
 // The coordinate-reading backward stages two tiles (coordinates and their

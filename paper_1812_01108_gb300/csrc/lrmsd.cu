@@ -14,8 +14,8 @@
 //      the largest eigenpair of the 4x4 matrix T(R) in FP32 (Newton's method
 //      on the characteristic polynomial, as in the quaternion-characteristic-
 //      polynomial approach of Theobald, Acta Cryst. A61 (2005) 478, then an
-//      adjugate column) and solve it in FP64 (Rayleigh quotient of T,
-//      adjugate of T - lambda I), then U(q).
+//      adjugate column) and refine it in double-float FP32 arithmetic, about
+//      48 bits (Rayleigh quotient of T, adjugate of T - lambda I), then U(q).
 //  K5c lrmsd_residual: LRMSD^2 = (sum |x'|^2 + |y'|^2 - 2 lambda)/N equals
 //      sum |y'_i - U x'_i|^2 / N at the optimum; the residual form has no
 //      cancellation, so it is summed in FP32 per chunk and in FP64 over the
@@ -181,15 +181,106 @@ __device__ __forceinline__ void fp32_eigen_estimate(const float (&r)[9], float e
     }
 }
 
-__device__ __forceinline__ double pick4(int i, double a, double b, double c, double d) {
+// ---------------------------------------------------------------------------
+// Double-float ("double-word") arithmetic on the FP32 pipe: a value is the
+// unevaluated sum hi + lo of two floats, |lo| <= ulp(hi) / 2, about 48
+// significant bits.  The building blocks are the classical error-free
+// transformations -- Knuth's TwoSum, the FMA form of Dekker's TwoProduct,
+// Dekker's Fast2Sum -- combined into the double-word sum, product and
+// quotient analysed by Joldes, Muller and Popescu (ACM TOMS 44 (2017) 1).
+// The round-to-nearest intrinsics keep the compiler from contracting or
+// reordering them.  FP64 issues at a small fraction of the FP32 rate on this
+// GPU, so the eigen-solve refines in this form instead.
+// ---------------------------------------------------------------------------
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_zero() { return DF{0.f, 0.f}; }
+
+// exact a + b (Knuth)
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return DF{s, e};
+}
+
+// exact a + b for |a| >= |b| (Dekker)
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// exact a * b (FMA)
+__device__ __forceinline__ DF two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return DF{p, fmaf(a, b, -p)};
+}
+
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+    DF s = two_sum(x.hi, y.hi);
+    const DF t = two_sum(x.lo, y.lo);
+    s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+
+__device__ __forceinline__ DF df_neg(DF x) { return DF{-x.hi, -x.lo}; }
+__device__ __forceinline__ DF df_sub(DF x, DF y) { return df_add(x, df_neg(y)); }
+__device__ __forceinline__ DF df_twice(DF x) { return DF{__fmul_rn(2.f, x.hi), __fmul_rn(2.f, x.lo)}; }
+
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+    const DF p = two_prod(x.hi, y.hi);
+    const float e = fmaf(x.lo, y.lo, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo)));
+    return fast_two_sum(p.hi, e);
+}
+
+__device__ __forceinline__ DF df_mul_f(DF x, float y) {
+    const DF p = two_prod(x.hi, y);
+    return fast_two_sum(p.hi, fmaf(x.lo, y, p.lo));
+}
+
+// x / y: FP32 quotient, then one correction with the double-float remainder
+__device__ __forceinline__ DF df_div(DF x, DF y) {
+    const float q1 = __fdiv_rn(x.hi, y.hi);
+    const DF r = df_sub(x, df_mul_f(y, q1));
+    const float q2 = __fdiv_rn(r.hi, y.hi);
+    return fast_two_sum(q1, q2);
+}
+
+// 1 / sqrt(x) for x > 0: FP32 estimate, one Newton step s (3 - x s^2) / 2 with
+// the residual 1 - x s^2 in double-float
+__device__ __forceinline__ DF df_rsqrt(DF x) {
+    const float s0 = rsqrtf(x.hi);
+    const DF e = df_sub(DF{1.f, 0.f}, df_mul_f(df_mul_f(x, s0), s0));
+    return fast_two_sum(s0, __fmul_rn(__fmul_rn(0.5f, s0), e.hi));
+}
+
+// a + b + c to double-float accuracy
+__device__ __forceinline__ DF df_sum3(float a, float b, float c) { return df_add(two_sum(a, b), DF{c, 0.f}); }
+
+__device__ __forceinline__ float df_round(DF x) { return __fadd_rn(x.hi, x.lo); }
+
+__device__ __forceinline__ DF df_shfl_xor(DF x, int m) {
+    return DF{__shfl_xor_sync(0xffffffffu, x.hi, m), __shfl_xor_sync(0xffffffffu, x.lo, m)};
+}
+__device__ __forceinline__ DF df_shfl(DF x, int src) {
+    return DF{__shfl_sync(0xffffffffu, x.hi, src), __shfl_sync(0xffffffffu, x.lo, src)};
+}
+
+__device__ __forceinline__ DF pick4(int i, DF a, DF b, DF c, DF d) {
+    return i == 0 ? a : (i == 1 ? b : (i == 2 ? c : d));
+}
+__device__ __forceinline__ float pick4f(int i, float a, float b, float c, float d) {
     return i == 0 ? a : (i == 1 ? b : (i == 2 ? c : d));
 }
 
+
 // Eigen-solve of one pair by the four lanes of a quad (sub = lane & 3), from
 // the summed moments S: lane i forms row i of T q for the Rayleigh quotient,
-// cofactor (jb, i) of the adjugate row and row i of U, so the dependent FP64
-// chain is about a quarter as long; the FP32 estimate runs in all four lanes
-// alike.  Every lane of the warp must call it (quad shuffles); only lanes with
+// cofactor (jb, i) of the adjugate row and row i of U, so the dependent
+// double-float chain is about a quarter as long; the FP32 estimate runs in
+// all four lanes alike.  Every lane of the warp must call it (quad shuffles); only lanes with
 // `store` write the pair's state st: U (9), xc (3), yc (3), 0.
 __device__ __forceinline__ void quad_eigen_solve(const float (&S)[kSlot], const float (&x0)[3],
                                                  const float (&y0)[3], int n, int sub, int lane,
@@ -225,43 +316,37 @@ __device__ __forceinline__ void quad_eigen_solve(const float (&S)[kSlot], const 
     float lam = 0.f, qf[4] = {1.f, 0.f, 0.f, 0.f};
     int jb = 0;
     if (solve) fp32_eigen_estimate(r, e0 * sc, lam, qf, jb);
-    // ---- FP64, every lane of the warp together from here on
-    double R[9];
+    // ---- refinement in double-float arithmetic (about 48 significant bits),
+    // every lane of the warp together from here on
+    DF T[4][4];
+    T[0][0] = df_sum3(r[0], r[4], r[8]);
+    T[0][1] = T[1][0] = two_sum(r[5], -r[7]);
+    T[0][2] = T[2][0] = two_sum(r[6], -r[2]);
+    T[0][3] = T[3][0] = two_sum(r[1], -r[3]);
+    T[1][1] = df_sum3(r[0], -r[4], -r[8]);
+    T[1][2] = T[2][1] = two_sum(r[1], r[3]);
+    T[1][3] = T[3][1] = two_sum(r[2], r[6]);
+    T[2][2] = df_sum3(-r[0], r[4], -r[8]);
+    T[2][3] = T[3][2] = two_sum(r[5], r[7]);
+    T[3][3] = df_sum3(-r[0], -r[4], r[8]);
+    // Rayleigh quotient at the FP32 estimate: lane sub forms (T q)_sub
+    DF w = df_zero();
 #pragma unroll
-    for (int k = 0; k < 9; ++k) R[k] = (double)r[k];
-    double T[4][4];
-    T[0][0] = R[0] + R[4] + R[8];
-    T[0][1] = T[1][0] = R[5] - R[7];
-    T[0][2] = T[2][0] = R[6] - R[2];
-    T[0][3] = T[3][0] = R[1] - R[3];
-    T[1][1] = R[0] - R[4] - R[8];
-    T[1][2] = T[2][1] = R[1] + R[3];
-    T[1][3] = T[3][1] = R[2] + R[6];
-    T[2][2] = -R[0] + R[4] - R[8];
-    T[2][3] = T[3][2] = R[5] + R[7];
-    T[3][3] = -R[0] - R[4] + R[8];
-    const double qa0 = qf[0], qa1 = qf[1], qa2 = qf[2], qa3 = qf[3];
-    // Rayleigh quotient: lane sub forms (T q)_sub
-    double w = 0.0;
+    for (int k = 0; k < 4; ++k) w = df_add(w, df_mul_f(pick4(sub, T[0][k], T[1][k], T[2][k], T[3][k]), qf[k]));
+    DF num = df_mul_f(w, pick4f(sub, qf[0], qf[1], qf[2], qf[3]));
+    num = df_add(num, df_shfl_xor(num, 1));
+    num = df_add(num, df_shfl_xor(num, 2));
+    DF den = two_prod(qf[0], qf[0]);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) w = fma(pick4(sub, T[0][k], T[1][k], T[2][k], T[3][k]), pick4(k, qa0, qa1, qa2, qa3), w);
-    double num = pick4(sub, qa0, qa1, qa2, qa3) * w;
-    num += __shfl_xor_sync(kFull, num, 1);
-    num += __shfl_xor_sync(kFull, num, 2);
-    const double den = qa0 * qa0 + qa1 * qa1 + qa2 * qa2 + qa3 * qa3;
-    double l64 = 0.0;
-    if (den > 0.0) {
-        const double rd = (double)(1.f / (float)den);
-        l64 = num * rd;
-        l64 = fma(rd, fma(-l64, den, num), l64);  // one correction of num / den
-    }
+    for (int k = 1; k < 4; ++k) den = df_add(den, two_prod(qf[k], qf[k]));
+    const DF l64 = den.hi > 0.f ? df_div(num, den) : df_zero();
     // cofactor (jb, sub) of A = T - lambda I: rows other than jb, columns other than sub
 #pragma unroll
-    for (int i = 0; i < 4; ++i) T[i][i] -= l64;
-    double M[3][3];
+    for (int i = 0; i < 4; ++i) T[i][i] = df_sub(T[i][i], l64);
+    DF M[3][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        double row[4];
+        DF row[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             // row k of the minor: A row (k < jb ? k : k + 1)
@@ -271,39 +356,42 @@ __device__ __forceinline__ void quad_eigen_solve(const float (&S)[kSlot], const 
         M[k][1] = sub <= 1 ? row[2] : row[1];
         M[k][2] = sub <= 2 ? row[3] : row[2];
     }
-    double qc = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
-                M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
-    if ((jb + sub) & 1) qc = -qc;
-    double nn = qc * qc;
-    nn += __shfl_xor_sync(kFull, nn, 1);
-    nn += __shfl_xor_sync(kFull, nn, 2);
-    double s = 0.0;
-    if (nn > 0.0) {
-        s = (double)rsqrtf((float)nn);
-        s = s * fma(-0.5 * nn * s, s, 1.5);  // one Newton step: relative error about 1e-14
-    }
-    const double qn = qc * s;
+    DF qc = df_sub(df_mul(M[0][0], df_sub(df_mul(M[1][1], M[2][2]), df_mul(M[1][2], M[2][1]))),
+                   df_mul(M[0][1], df_sub(df_mul(M[1][0], M[2][2]), df_mul(M[1][2], M[2][0]))));
+    qc = df_add(qc, df_mul(M[0][2], df_sub(df_mul(M[1][0], M[2][1]), df_mul(M[1][1], M[2][0]))));
+    if ((jb + sub) & 1) qc = df_neg(qc);
+    DF nn = df_mul(qc, qc);
+    nn = df_add(nn, df_shfl_xor(nn, 1));
+    nn = df_add(nn, df_shfl_xor(nn, 2));
+    const bool ok = solve && nn.hi > 0.f;
+    const DF qn = ok ? df_mul(qc, df_rsqrt(nn)) : df_zero();
     const int base = lane & ~3;
-    double q0 = __shfl_sync(kFull, qn, base), q1 = __shfl_sync(kFull, qn, base + 1);
-    double q2 = __shfl_sync(kFull, qn, base + 2), q3 = __shfl_sync(kFull, qn, base + 3);
-    if (!(solve && nn > 0.0)) {
-        q0 = 1.0; q1 = q2 = q3 = 0.0;
+    DF q0 = df_shfl(qn, base), q1 = df_shfl(qn, base + 1), q2 = df_shfl(qn, base + 2), q3 = df_shfl(qn, base + 3);
+    if (!ok) {
+        q0 = DF{1.f, 0.f};
+        q1 = q2 = q3 = df_zero();
     }
-    // row sub of U(q) (Section 4), formed in FP64 and rounded once
-    const double a = q0 * q0, b = q1 * q1, c = q2 * q2, d = q3 * q3;
-    double u0, u1, u2;
+    // row sub of U(q) (Section 4), formed in double-float and rounded once
+    const DF a = df_mul(q0, q0), bq = df_mul(q1, q1), c = df_mul(q2, q2), d = df_mul(q3, q3);
+    DF u0, u1, u2;
     if (sub == 0) {
-        u0 = a + b - c - d; u1 = 2.0 * (q1 * q2 - q0 * q3); u2 = 2.0 * (q1 * q3 + q0 * q2);
+        u0 = df_sub(df_add(a, bq), df_add(c, d));
+        u1 = df_twice(df_sub(df_mul(q1, q2), df_mul(q0, q3)));
+        u2 = df_twice(df_add(df_mul(q1, q3), df_mul(q0, q2)));
     } else if (sub == 1) {
-        u0 = 2.0 * (q1 * q2 + q0 * q3); u1 = a - b + c - d; u2 = 2.0 * (q2 * q3 - q0 * q1);
+        u0 = df_twice(df_add(df_mul(q1, q2), df_mul(q0, q3)));
+        u1 = df_sub(df_add(a, c), df_add(bq, d));
+        u2 = df_twice(df_sub(df_mul(q2, q3), df_mul(q0, q1)));
     } else {
-        u0 = 2.0 * (q1 * q3 - q0 * q2); u1 = 2.0 * (q2 * q3 + q0 * q1); u2 = a - b - c + d;
+        u0 = df_twice(df_sub(df_mul(q1, q3), df_mul(q0, q2)));
+        u1 = df_twice(df_add(df_mul(q2, q3), df_mul(q0, q1)));
+        u2 = df_sub(df_add(a, d), df_add(bq, c));
     }
     if (store) {
         if (sub < 3) {
-            st[3 * sub] = (float)u0;
-            st[3 * sub + 1] = (float)u1;
-            st[3 * sub + 2] = (float)u2;
+            st[3 * sub] = df_round(u0);
+            st[3 * sub + 1] = df_round(u1);
+            st[3 * sub + 2] = df_round(u2);
         } else {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
