@@ -219,12 +219,16 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT>()) fa_fwd_kernel(
         const int j = t * NT + threadIdx.x;
         const bool valid = j < L;
         int type = kGlyCode;
-        float a_phi = 0.f, a_psi = 0.f, a_om = 0.f;
+        float a_phi = 0.f, a_psi = 0.f, a_om = 0.f, a_chi[kMaxGroups] = {0.f, 0.f, 0.f, 0.f};
         if (valid) {
+            // every angle row up front (the chi rows too, used or not), so no
+            // load waits inside the side-chain loop
             type = residue_type(seq + (size_t)b * Lmax, j, true);
             a_phi = __ldg(ang + j);
             a_psi = __ldg(ang + Lmax + j);
             if (j + 1 < L) a_om = __ldg(ang + 2 * Lmax + j + 1);
+#pragma unroll
+            for (int c = 0; c < kMaxGroups; ++c) a_chi[c] = __ldg(ang + (3 + c) * Lmax + j);
         }
         const int nat = valid ? s_tab.n_atoms[type] : 0;
         float sp = 0.f, cp = 1.f, ss = 0.f, cs = 1.f;
@@ -263,12 +267,14 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT>()) fa_fwd_kernel(
             rigid_mul_Rx(S, s_tab.rp_c, s_tab.rp_s);
             const int ng = s_tab.n_groups[type], nchi = s_tab.n_chi[type];
             int e = 0;
-            for (int k = 0; k < ng; ++k) {
+#pragma unroll
+            for (int k = 0; k < kMaxGroups; ++k) {
+                if (k >= ng) break;
                 float sc, cc;
                 if (k < nchi) {
                     // chi moves only its own side chain (no error propagates along
                     // the chain): the SFU sine/cosine is accurate enough here
-                    __sincosf(__ldg(ang + (3 + k) * Lmax + j), &sc, &cc);
+                    __sincosf(a_chi[k], &sc, &cc);
                 } else {
                     cc = s_tab.fixchi[type][k].x;
                     sc = s_tab.fixchi[type][k].y;
@@ -292,11 +298,13 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT>()) fa_fwd_kernel(
         if (valid) ws.ratom[(size_t)b * Lmax + j] = pc + a0;  // the backward reads its atoms directly
         const int end_atom = pc + tile_atoms;
         const int nout = max(0, min(end_atom, Amax) - pc);
-        for (int a = threadIdx.x; a < nout; a += NT) {
-            const float3 r = point_apply(P, make_float3(stage[3 * a], stage[3 * a + 1], stage[3 * a + 2]));
-            stage[3 * a] = r.x;
-            stage[3 * a + 1] = r.y;
-            stage[3 * a + 2] = r.z;
+        if (t > 0) {  // the chain's first tile starts at the identity frame (R_0 = I)
+            for (int a = threadIdx.x; a < nout; a += NT) {
+                const float3 r = point_apply(P, make_float3(stage[3 * a], stage[3 * a + 1], stage[3 * a + 2]));
+                stage[3 * a] = r.x;
+                stage[3 * a + 1] = r.y;
+                stage[3 * a + 2] = r.z;
+            }
         }
         __syncthreads();
         {
