@@ -41,6 +41,8 @@ constexpr int kMaxWpp = 8;   // most warps per pair in the streaming kernels
 constexpr int kMom = 17;     // sum dx (3), sum dy (3), sum dx dy^T (9), sum |dx|^2, sum |dy|^2
 constexpr int kSlot = 20;    // floats per chunk partial (5 float4)
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kRqPasses = 4;          // most Rayleigh-quotient passes of the eigen-solve
+constexpr float kNearDouble = 1e-4f;  // |adjugate column|^2 below which another pass runs
 
 struct WsLayout {
     size_t part1, part2, state, total;
@@ -271,9 +273,6 @@ __device__ __forceinline__ DF df_shfl(DF x, int src) {
 __device__ __forceinline__ DF pick4(int i, DF a, DF b, DF c, DF d) {
     return i == 0 ? a : (i == 1 ? b : (i == 2 ? c : d));
 }
-__device__ __forceinline__ float pick4f(int i, float a, float b, float c, float d) {
-    return i == 0 ? a : (i == 1 ? b : (i == 2 ? c : d));
-}
 
 
 // Eigen-solve of one pair by the four lanes of a quad (sub = lane & 3), from
@@ -329,44 +328,71 @@ __device__ __forceinline__ void quad_eigen_solve(const float (&S)[kSlot], const 
     T[2][2] = df_sum3(-r[0], r[4], -r[8]);
     T[2][3] = T[3][2] = two_sum(r[5], r[7]);
     T[3][3] = df_sum3(-r[0], -r[4], r[8]);
-    // Rayleigh quotient at the FP32 estimate: lane sub forms (T q)_sub
-    DF w = df_zero();
-#pragma unroll
-    for (int k = 0; k < 4; ++k) w = df_add(w, df_mul_f(pick4(sub, T[0][k], T[1][k], T[2][k], T[3][k]), qf[k]));
-    DF num = df_mul_f(w, pick4f(sub, qf[0], qf[1], qf[2], qf[3]));
-    num = df_add(num, df_shfl_xor(num, 1));
-    num = df_add(num, df_shfl_xor(num, 2));
-    DF den = two_prod(qf[0], qf[0]);
-#pragma unroll
-    for (int k = 1; k < 4; ++k) den = df_add(den, two_prod(qf[k], qf[k]));
-    const DF l64 = den.hi > 0.f ? df_div(num, den) : df_zero();
-    // cofactor (jb, sub) of A = T - lambda I: rows other than jb, columns other than sub
-#pragma unroll
-    for (int i = 0; i < 4; ++i) T[i][i] = df_sub(T[i][i], l64);
-    DF M[3][3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        DF row[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            // row k of the minor: A row (k < jb ? k : k + 1)
-            row[c] = k == 0 ? (jb == 0 ? T[1][c] : T[0][c]) : (k == 1 ? (jb <= 1 ? T[2][c] : T[1][c]) : (jb <= 2 ? T[3][c] : T[2][c]));
-        }
-        M[k][0] = sub == 0 ? row[1] : row[0];
-        M[k][1] = sub <= 1 ? row[2] : row[1];
-        M[k][2] = sub <= 2 ? row[3] : row[2];
-    }
-    DF qc = df_sub(df_mul(M[0][0], df_sub(df_mul(M[1][1], M[2][2]), df_mul(M[1][2], M[2][1]))),
-                   df_mul(M[0][1], df_sub(df_mul(M[1][0], M[2][2]), df_mul(M[1][2], M[2][0]))));
-    qc = df_add(qc, df_mul(M[0][2], df_sub(df_mul(M[1][0], M[2][1]), df_mul(M[1][1], M[2][0]))));
-    if ((jb + sub) & 1) qc = df_neg(qc);
-    DF nn = df_mul(qc, qc);
-    nn = df_add(nn, df_shfl_xor(nn, 1));
-    nn = df_add(nn, df_shfl_xor(nn, 2));
-    const bool ok = solve && nn.hi > 0.f;
-    const DF qn = ok ? df_mul(qc, df_rsqrt(nn)) : df_zero();
+    // Rayleigh-quotient passes: lambda = q.T q / q.q at the current estimate,
+    // then q = row jb of adj(T - lambda I) (lane sub forms its entry).  One pass
+    // is exact to rounding when the largest eigenvalue is well separated (the
+    // adjugate column is then of order one, |R|_F being 1).  When it is (nearly)
+    // double -- collinear clouds, where any turn about the line fits as well --
+    // the FP32 estimate can lean towards the other eigenvectors, and each further
+    // pass squares that error; passes repeat while the column stays small.
+    // Every lane runs every pass (full-warp shuffles); a quad keeps the pass
+    // results only while it still needs them.
+    DF qv[4] = {DF{qf[0], 0.f}, DF{qf[1], 0.f}, DF{qf[2], 0.f}, DF{qf[3], 0.f}};
+    int jv = jb;
+    bool need = true, ok = false;
     const int base = lane & ~3;
-    DF q0 = df_shfl(qn, base), q1 = df_shfl(qn, base + 1), q2 = df_shfl(qn, base + 2), q3 = df_shfl(qn, base + 3);
+    for (int pass = 0; pass < kRqPasses; ++pass) {
+        if (!__any_sync(kFull, need)) break;
+        DF w = df_zero();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w = df_add(w, df_mul(pick4(sub, T[0][k], T[1][k], T[2][k], T[3][k]), qv[k]));
+        DF num = df_mul(w, pick4(sub, qv[0], qv[1], qv[2], qv[3]));
+        num = df_add(num, df_shfl_xor(num, 1));
+        num = df_add(num, df_shfl_xor(num, 2));
+        DF den = df_mul(qv[0], qv[0]);
+#pragma unroll
+        for (int k = 1; k < 4; ++k) den = df_add(den, df_mul(qv[k], qv[k]));
+        const DF lam2 = den.hi > 0.f ? df_div(num, den) : df_zero();
+        // cofactor (jv, sub) of A = T - lambda I: rows other than jv, columns other than sub
+        DF M[3][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int ri = k < jv ? k : k + 1;
+            DF row[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                row[c] = pick4(ri, T[0][c], T[1][c], T[2][c], T[3][c]);
+                if (c == ri) row[c] = df_sub(row[c], lam2);
+            }
+            M[k][0] = sub == 0 ? row[1] : row[0];
+            M[k][1] = sub <= 1 ? row[2] : row[1];
+            M[k][2] = sub <= 2 ? row[3] : row[2];
+        }
+        DF qc = df_sub(df_mul(M[0][0], df_sub(df_mul(M[1][1], M[2][2]), df_mul(M[1][2], M[2][1]))),
+                       df_mul(M[0][1], df_sub(df_mul(M[1][0], M[2][2]), df_mul(M[1][2], M[2][0]))));
+        qc = df_add(qc, df_mul(M[0][2], df_sub(df_mul(M[1][0], M[2][1]), df_mul(M[1][1], M[2][0]))));
+        if ((jv + sub) & 1) qc = df_neg(qc);
+        DF nn = df_mul(qc, qc);
+        nn = df_add(nn, df_shfl_xor(nn, 1));
+        nn = df_add(nn, df_shfl_xor(nn, 2));
+        const bool ok_p = solve && nn.hi > 0.f;
+        const DF qn = ok_p ? df_mul(qc, df_rsqrt(nn)) : df_zero();
+        DF qg[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qg[k] = df_shfl(qn, base + k);
+        if (need) {
+            ok = ok_p;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) qv[k] = qg[k];
+            need = ok_p && nn.hi < kNearDouble;
+            // next cofactor row: the largest entry of the estimate
+            jv = 0;
+#pragma unroll
+            for (int k = 1; k < 4; ++k)
+                if (fabsf(qv[k].hi) > fabsf(pick4(jv, qv[0], qv[1], qv[2], qv[3]).hi)) jv = k;
+        }
+    }
+    DF q0 = qv[0], q1 = qv[1], q2 = qv[2], q3 = qv[3];
     if (!ok) {
         q0 = DF{1.f, 0.f};
         q1 = q2 = q3 = df_zero();

@@ -181,3 +181,59 @@ def test_batches_that_spread_pairs_over_warps(P):
     assert rel_err(g32[unique], oracle.lrmsd_backward(w, x, y, n)[unique]) <= GRAD_TOL
     for p, k in enumerate(n):
         assert np.all(g32[p, k:] == 0)
+
+
+def _rot(q):
+    q = np.asarray(q, np.float64)
+    a, b, c, d = q / np.linalg.norm(q)
+    return np.array([[a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c)],
+                     [2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)],
+                     [2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d]])
+
+
+def _degenerate_clouds(P, rng, Nmax, extent):
+    """Pairs whose optimal rotation is not unique: collinear atoms (any turn
+    about the line fits as well: the largest eigenvalue of T is double), evenly
+    or unevenly spaced over `extent` A, as exact rigid copies; plus two-fold
+    symmetric clouds, as exact copies and with 0.3 A noise."""
+    x = np.zeros((P, Nmax, 3), np.float64)
+    y = np.zeros_like(x)
+    n = np.zeros(P, np.int32)
+    for p in range(P):
+        k = int(rng.integers(4, Nmax + 1))
+        kind = p % 4
+        if kind < 2:
+            d = rng.normal(size=3)
+            d /= np.linalg.norm(d)
+            t = np.linspace(-0.5, 0.5, k) if kind == 0 else np.sort(rng.uniform(-0.5, 0.5, k))
+            pts = np.outer(t * extent, d) + rng.normal(size=3) * 5
+        else:
+            k -= k % 2
+            half = rng.normal(scale=12.0, size=(k // 2, 3))
+            axis = rng.normal(size=3)
+            axis /= np.linalg.norm(axis)
+            pts = np.concatenate([half, half @ (2 * np.outer(axis, axis) - np.eye(3)).T]) + rng.normal(size=3) * 3
+        moved = pts @ _rot(rng.normal(size=4)).T + rng.normal(size=3) * 10
+        if kind == 3:
+            moved = moved + rng.normal(scale=0.3, size=moved.shape)
+        x[p, :k], y[p, :k], n[p] = pts, moved, k
+    return x.astype(np.float32), y.astype(np.float32), n
+
+
+@pytest.mark.parametrize("P,extent", [(16, 60.0), (600, 60.0), (64, 770.0)])
+def test_degenerate_largest_eigenvalue(P, extent):
+    """Collinear pairs (a double largest eigenvalue) and two-fold symmetric
+    pairs: the LRMSD is unique even where the rotation is not, and must match
+    the oracle.  P = 600 takes the streaming kernels, P = 16 and 64 one CTA per
+    pair.  The exact copies have an LRMSD of rounding size, where the FP32
+    rounding of U and of the coordinates alone moves the value by a few units
+    of 2^-24 |x'|: the bound is 10 * 2^-24 * max |x' - centroid| of each pair
+    (about 1.8e-5 A for the 60 A lines), and never below 1e-5 A."""
+    rng = np.random.default_rng(71 + P)
+    x, y, n = _degenerate_clouds(P, rng, 512, extent)
+    l32, _ = _run(x, y, n, np.ones(P, np.float32))
+    l64 = oracle.lrmsd_forward(x, y, n)
+    for p in range(P):
+        pts = y[p, :n[p]].astype(np.float64)
+        bound = max(LRMSD_TOL, 10 * 2.0 ** -24 * np.linalg.norm(pts - pts.mean(0), axis=1).max())
+        assert abs(l32[p] - l64[p]) <= bound, (p, l32[p], l64[p], bound)
