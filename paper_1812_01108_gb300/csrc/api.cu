@@ -1,5 +1,6 @@
 // C ABI of the library (include/tpl.h): argument checks, workspace layout,
-// scheduling (longest-first chain order) and dispatch to the kernels.
+// the schedule kernel (work lists of tiles and packed short chains), the
+// autotuners and dispatch to the kernels.
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>

@@ -1,20 +1,27 @@
 // Full-atom model of the paper (Section 2) on sm_103a.
 //
-// K3 fa_fwd_kernel: one CTA per chain (longest first), one residue per
-// thread.  The residue-to-residue transform T_j = R_1(phi_j) R_3(psi_j)
-// R_4(omega_{j+1}) is scanned across the CTA (exclusive prefix = M_0 of
-// residue j, the frame of its N), together with an exclusive scan of the
-// per-residue atom counts (the residue's first output atom).  Each thread then
-// builds M_1, M_3 and the side-chain frames M_1 R' R(chi_1) R(chi_2) ... and
-// places its atoms r = M_g r0 into a shared-memory tile that the CTA writes
-// out with coalesced stores.  The residue tables live in shared memory.
+// Chains are cut into tiles of NT residues (one residue per thread) that
+// persistent CTAs take from the schedule's work list; the tiles of a chain
+// meet through the aggregate look-back of sched.cuh.
 //
-// K4 fa_bwd_kernel: Eq. 1 as suffix sums.  For a frame with x axis u and
-// origin p, dL/dalpha = u . sum_{k downstream} (r_k - p) x g_k.  chi_k
-// gradients are local to the residue (suffix over its side-chain groups);
-// phi, psi and omega add the sum over all later residues, a reverse
-// suffix scan of (sum r x g, sum g) across the CTA.  Frames are recomputed
-// from the angles; long chains use tile carries from a first pass.
+// K3 fa_fwd_kernel: the residue-to-residue transform T_j = R_1(phi_j)
+// R_3(psi_j) R_4(omega_{j+1}) is scanned across the tile (exclusive prefix =
+// M_0 of residue j, the frame of its N, relative to the tile start), together
+// with an exclusive scan of the per-residue atom counts (the residue's first
+// output atom).  Each thread then builds M_1, M_3 and the side-chain frames
+// M_1 R' R(chi_1) R(chi_2) ... and places its atoms r = M_g r0 into a
+// shared-memory stage; once the look-back has given the tile's start frame it
+// is applied in place and the CTA writes the stage out with 16-byte stores.
+// The residue tables live in shared memory.
+//
+// K4 fa_bwd_coords_kernel / fa_bwd_kernel: Eq. 1 as suffix sums.  For a frame
+// with x axis u and origin p, dL/dalpha = u . sum_{k downstream} (r_k - p) x
+// g_k.  chi_k gradients are local to the residue (suffix over its side-chain
+// groups); phi, psi and omega add the sum over all later residues, a reverse
+// suffix scan of (sum r x g, sum g) across the tile plus the suffix of the
+// later tiles (look-back, tiles of a chain taken last to first).  Axes and
+// origins come from the forward's coordinates (fa_bwd_coords_kernel) or from
+// frames recomputed from the angles and the tile-start frames (fa_bwd_kernel).
 #include "kernels.h"
 #include "sched.cuh"
 #include "tables.h"
@@ -158,14 +165,15 @@ __device__ __forceinline__ bool ws_matches(const ChainWs& ws, int tile, int B, i
 }
 
 // ---------------------------------------------------------------------------
-// K3: forward.  One tile of NT residues per step of a persistent CTA.
-//  1. residue-parallel: angles and type loaded up front; T_j built and
-//     scanned; look-back gives the tile's start frame; each thread builds
-//     M_1, M_3 and the four side-chain group frames (branch-free), places N,
-//     CA, C and O, and leaves its group frames in shared memory;
-//  2. atom-parallel: every thread places side-chain atoms of the tile (no
-//     divergence between residue types);
-//  3. the staged tile is written out with 16-byte stores.
+// K3: forward.  One tile of NT residues per step of a persistent CTA:
+//  1. every angle row and the type of each thread's residue are loaded up
+//     front; T_j is built and scanned across the tile with the atom counts,
+//     and the tile's aggregate is published for the look-back;
+//  2. each thread places its residue's atoms (N, CA, C, O, then the side
+//     chain group by group) in tile-local coordinates in the stage;
+//  3. the look-back gives the tile's start frame, which is applied to the
+//     stage in place (not for a chain's first tile: R_0 = I);
+//  4. the stage is written out with 16-byte stores.
 // ---------------------------------------------------------------------------
 template <int NT>
 __host__ __device__ constexpr size_t fa_fwd_smem() {

@@ -1,8 +1,9 @@
 // Tile scheduling shared by the chain kernels (backbone and full atom).
 //
 // A chain of L residues is cut into tiles of TILE residues.  A schedule kernel
-// writes the list of (chain, tile) pairs, chains longest first, and zeroes the
-// forward flags and work counter.  The chain kernels are persistent: each CTA
+// writes the list of (chain, tile) entries -- chains in batch order, longest
+// first, or longest first with the chains of at most one tile packed several
+// per entry -- and zeroes the forward flags and work counter.  The chain kernels are persistent: each CTA
 // takes the next list entry from an atomic counter, so every tile a CTA waits
 // for was taken earlier by a CTA that is running and never waits on a later
 // one (no deadlock, whatever order the hardware starts CTAs in).
