@@ -124,3 +124,26 @@ def test_degenerate_sizes():
     assert np.all(oracle.lrmsd_forward(y, x, n) == 0.0)
     g = oracle.lrmsd_backward(np.ones(3), y, x, n)
     assert np.all(g == 0.0)
+
+
+def test_collinear_pairs_match_kabsch():
+    """Collinear atoms leave the turn about the line free: the largest
+    eigenvalue of T is double.  The LRMSD is still unique: zero for a rigid
+    copy, and equal to the Kabsch value (numpy SVD) when the second line is
+    stretched, which no rotation can undo."""
+    rng = np.random.default_rng(19)
+    for k in (3, 7, 40):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        t = np.sort(rng.uniform(-20, 20, k))
+        x = np.outer(t, d) + rng.normal(size=3)
+        rot = Rotation.from_quat(rng.normal(size=4)).as_matrix()
+        y = x @ rot.T + rng.normal(size=3) * 5
+        n = np.array([k], np.int32)
+        # the closed form sqrt((E0 - 2 lambda) / N) cancels: at a zero LRMSD it
+        # leaves about sqrt(few ulp * E0 / N)
+        e0n = (((x - x.mean(0)) ** 2).sum() + ((y - y.mean(0)) ** 2).sum()) / k
+        assert oracle.lrmsd_forward(y[None], x[None], n)[0] <= np.sqrt(64 * 2.0 ** -52 * e0n)
+        ys = 1.1 * y  # stretched copy
+        ref = _kabsch(ys, x)
+        assert abs(oracle.lrmsd_forward(ys[None], x[None], n)[0] - ref) < 1e-9
