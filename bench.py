@@ -54,13 +54,13 @@ TRAFFIC = {
     # (per-unit DRAM bytes, unit, profile, launch shape of the capture or None if the
     # kernels take none); cold-cache captures of one launch
     # fa_fwd_kernel<384, 0> (the coordinates it writes stay in L2 during the capture)
-    ("training_step", "fullatom_forward"): (3.5307, "atom", "profiles/fa_kernels_training_step_256x700.md",
+    ("training_step", "fullatom_forward"): (3.5305, "atom", "profiles/fa_kernels_training_step_256x700.md",
                                             "threads=384"),
     # fa_bwd_coords_kernel<384, 1, 0> (LRMSD gradient formed in the kernel)
-    ("training_step", "lrmsd_fullatom_backward"): (24.7293, "atom", "profiles/fa_kernels_training_step_256x700.md",
+    ("training_step", "lrmsd_fullatom_backward"): (24.7285, "atom", "profiles/fa_kernels_training_step_256x700.md",
                                                    "threads=384"),
     # lrmsd_pair_kernel
-    ("training_step", "lrmsd_forward"): (24.0818, "atom", "profiles/lrmsd_kernels_training_step_256x700.md", None),
+    ("training_step", "lrmsd_forward"): (24.0843, "atom", "profiles/lrmsd_kernels_training_step_256x700.md", None),
     # bb_fwd_kernel<256, 4> (the schedule kernel's few bytes not counted)
     ("backbone_uneven", "backbone_forward"): (80.9907, "residue", "profiles/backbone_kernels_backbone_uneven_4096.md",
                                               "threads=256,res_per_thread=4"),
@@ -69,11 +69,11 @@ TRAFFIC = {
                                                      "profiles/backbone_kernels_backbone_uneven_4096.md",
                                                      "threads=256,res_per_thread=4"),
     # moments + solve + residual + finalize
-    ("backbone_uneven", "lrmsd_forward"): (50.5103, "atom", "profiles/lrmsd_kernels_backbone_uneven_4096.md", None),
+    ("backbone_uneven", "lrmsd_forward"): (50.4512, "atom", "profiles/lrmsd_kernels_backbone_uneven_4096.md", None),
     # moments + solve + residual + finalize, 4096-pair capture scaled by atoms
-    ("lrmsd_batch", "lrmsd_forward"): (49.1959, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md", None),
+    ("lrmsd_batch", "lrmsd_forward"): (49.1724, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md", None),
     # grad, 4096-pair capture scaled by atoms
-    ("lrmsd_batch", "lrmsd_backward"): (42.8496, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md", None),
+    ("lrmsd_batch", "lrmsd_backward"): (42.8211, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md", None),
 }
 
 
