@@ -259,7 +259,7 @@ tpl_status tpl_lrmsd_backward(const float* grad_lrmsd, const float* input, const
  * memory is all owned by another runtime's allocator, or an interface without
  * a scratch argument).  The paper has no counterpart; this is an interface
  * convenience.  The scratch is a fixed array inside the library: every GPU
- * that loads the library holds it (about 3.2 MB) until the process exits.
+ * that loads the library holds it (about 3.1 MB) until the process exits.
  *   Limits: P <= 4096 pairs, Nmax <= 8192 atoms; larger sizes return
  *   TPL_ERR_BAD_SHAPE and launch nothing.  Inputs and outputs as in
  *   tpl_lrmsd_forward; no allocation, no workspace.
