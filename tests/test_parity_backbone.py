@@ -287,3 +287,32 @@ def test_packed_schedule_is_deterministic():
     _run_fp32(a[:7], lengths[:7], g[:7], opts)  # something else in between
     c2, g2 = _run_fp32(a, lengths, g, opts, dict(opts, bwd_mode=tpl.BWD_FROM_COORDS))
     assert np.array_equal(c1, c2) and np.array_equal(g1, g2)
+
+
+def _free_omega(a, lengths, rng):
+    """omega per residue: trans (pi +- 0.1), cis (0 +- 0.1) or uniform, in thirds."""
+    B, _, Lmax = a.shape
+    kind = rng.integers(0, 3, size=(B, Lmax))
+    om = np.where(kind == 0, np.pi + rng.normal(0, 0.1, (B, Lmax)),
+                  np.where(kind == 1, rng.normal(0, 0.1, (B, Lmax)), rng.uniform(-np.pi, np.pi, (B, Lmax))))
+    a = a.copy()
+    a[:, 2] = (om * (np.arange(Lmax)[None, :] < lengths[:, None])).astype(np.float32)
+    return a
+
+
+@pytest.mark.parametrize("bwd", [tpl.BWD_FROM_COORDS, tpl.BWD_RECOMPUTE])
+def test_free_omega_cis_and_trans(bwd):
+    """omega is an input (reading 3), not fixed at pi: with cis, trans and
+    arbitrary peptide bonds the coordinates, all angle gradients and the omega
+    row of the gradient on its own match the oracle."""
+    rng = np.random.default_rng(57)
+    a, g = _inputs(LENGTHS, 58)
+    a = _free_omega(a, LENGTHS, rng)
+    c64 = oracle.backbone_forward(a, LENGTHS)
+    g64 = oracle.backbone_backward(a, LENGTHS, g)
+    c32, ga32 = _run_fp32(a, LENGTHS, g, {"threads": 128, "res_per_thread": 4},
+                          {"threads": 128, "res_per_thread": 4, "bwd_mode": bwd})
+    assert np.abs(c32 - c64).max() <= COORD_TOL
+    assert rel_err(ga32, g64) <= GRAD_TOL
+    assert rel_err(ga32[:, 2], g64[:, 2]) <= GRAD_TOL
+    assert np.all(ga32[:, 2, 0] == 0)

@@ -275,3 +275,25 @@ def test_fused_training_step_matches_the_separate_calls_and_the_oracle(threads):
     assert rel_err(host(g2)[m], ga64[m]) <= GRAD_TOL
     for b, L in enumerate(lengths):
         assert np.all(host(g2)[b, :, L:] == 0)
+
+
+@pytest.mark.parametrize("from_coords", [False, True])
+def test_free_omega_cis_and_trans(from_coords):
+    """omega per residue trans (pi +- 0.1), cis (0 +- 0.1) or uniform: the
+    coordinates, all angle gradients and the omega row on its own match the
+    oracle (omega is an input, reading 3)."""
+    rng = np.random.default_rng(59)
+    a, seq, g, Amax = _inputs(LENGTHS, 60)
+    B, _, Lmax = a.shape
+    kind = rng.integers(0, 3, size=(B, Lmax))
+    om = np.where(kind == 0, np.pi + rng.normal(0, 0.1, (B, Lmax)),
+                  np.where(kind == 1, rng.normal(0, 0.1, (B, Lmax)), rng.uniform(-np.pi, np.pi, (B, Lmax))))
+    a[:, 2] = (om * (np.arange(Lmax)[None, :] < LENGTHS[:, None])).astype(np.float32)
+    c64, na64 = oracle.fullatom_forward(a, seq, LENGTHS, Amax)
+    g = (g * (np.arange(Amax)[None, :] < na64[:, None])[:, :, None]).astype(np.float32)
+    g64 = oracle.fullatom_backward(a, seq, LENGTHS, g)
+    c32, na32, ga32 = _run_fp32(a, seq, LENGTHS, g, Amax, {"threads": 256}, from_coords)
+    assert np.array_equal(na32, na64)
+    assert np.abs(c32 - c64).max() <= COORD_TOL
+    assert rel_err(ga32, g64) <= GRAD_TOL
+    assert rel_err(ga32[:, 2], g64[:, 2]) <= GRAD_TOL
