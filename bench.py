@@ -88,8 +88,9 @@ def parse(argv=None):
     p.add_argument("--length", type=int, default=700, help="residues per chain (training_step)")
     p.add_argument("--threads", type=int, default=0, help="CTA size of the chain kernels (0 = default)")
     p.add_argument("--res-per-thread", type=int, default=0, help="backbone residues per thread (0 = default)")
-    p.add_argument("--bwd", default="coords", choices=["coords", "recompute"],
-                   help="chain backward: read the forward's coordinates or rebuild frames")
+    p.add_argument("--bwd", default="coords", choices=["coords", "recompute", "quadratic"],
+                   help="chain backward: read the forward's coordinates, rebuild frames, or (backbone) "
+                        "the paper's O(L^2) sums from the coordinates")
     p.add_argument("--fusion", default="backward", choices=["step", "backward", "none"],
                    help="training step: fused step (two calls), fused backward (three calls), "
                         "or separate calls (four)")
@@ -103,6 +104,8 @@ def parse(argv=None):
         a.batch = DEFAULT_BATCH[a.workload]
     if a.unfused:
         a.fusion = "none"
+    if a.bwd == "quadratic" and a.workload not in ("backbone_uneven", "backbone_stress"):
+        p.error("--bwd quadratic is the backbone comparator (backbone workloads only)")
     return a
 
 
@@ -521,6 +524,11 @@ def setup_backbone_uneven(args, tpl, torch, dev, d):
         ]
         st.kernels.update({"lrmsd_backward": ["lrmsd_grad_kernel"], "backbone_backward": ["bb_bwd_kernel"]})
         st.alg.update({"lrmsd_backward": 36 * n_atoms, "backbone_backward": 60 * res})
+        if args.bwd == "quadratic":
+            # the paper's O(L^2) sums of Eq. 2, one thread per atom (comparator)
+            st.calls[3] = ("backbone_backward",
+                           lambda: tpl.tpl_backbone_backward_quadratic(Ln, coords, gcoords, gang))
+            st.kernels["backbone_backward"] = ["bb_bwd_quadratic_kernel"]
     else:
         st.calls = [
             ("backbone_forward", lambda: tpl.tpl_backbone_forward(A, Ln, coords, bb_ws, opts)),

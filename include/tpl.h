@@ -137,6 +137,17 @@ tpl_status tpl_backbone_backward(const float* angles, const int32_t* lengths, in
 /* Full-atom model (paper Section 2)                                         */
 /* ------------------------------------------------------------------------ */
 
+/* The paper's own O(L^2) evaluation of Eq. 2 (Section 3): every (angle,
+ * atom) term dL/dalpha_q = g_k . (M_{q-1} dR_q M_q^{-1} r_k), k >= q, summed
+ * directly -- written as u_q . sum_{k >= q} (r_k - r_q) x g_k with u_q the unit
+ * bond into atom q -- with no suffix scan: a comparator for
+ * tpl_backbone_backward (same result to rounding, O(L^2) work per chain).
+ *   coords: the backbone forward's output [B][3 Lmax][3]; grad_coords the
+ *   same shape; grad_angles [B][3][Lmax] out (zeros at padding and for
+ *   omega_0).  B <= 65535.  Needs no workspace. */
+tpl_status tpl_backbone_backward_quadratic(const int32_t* lengths, int B, int Lmax, const float* coords,
+                                           const float* grad_coords, float* grad_angles, tpl_stream stream);
+
 /* Workspace of the full-atom calls; the same contract as the backbone's (the
  * backward reuses the forward's schedule and tile-start frames). */
 size_t tpl_fullatom_workspace_size(int B, int Lmax);

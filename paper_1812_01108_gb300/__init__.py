@@ -31,6 +31,7 @@ __all__ = [
     "tpl_lrmsd_forward_ref64", "tpl_lrmsd_backward_ref64", "tpl_get_status",
     "tpl_selftest_wait_timeout", "tpl_backbone_autotune", "tpl_fullatom_autotune",
     "tpl_backbone_lrmsd_autotune", "tpl_fullatom_lrmsd_autotune", "tpl_lrmsd_forward_launches",
+    "tpl_backbone_backward_quadratic",
     "tpl_fullatom_backward_lrmsd", "tpl_backbone_backward_lrmsd", "tpl_fullatom_lrmsd_workspace_size",
     "tpl_fullatom_lrmsd_forward", "tpl_fullatom_lrmsd_backward", "backbone",
     "fullatom", "lrmsd", "residue_table", "fullatom_max_atoms", "BWD_RECOMPUTE",
@@ -112,6 +113,7 @@ def load_library():
             "tpl_backbone_autotune": ([P, P, I, I, P, P, P, P, Z, I, O, F, P], I),
             "tpl_fullatom_autotune": ([P, P, P, I, I, I, P, P, P, P, P, Z, I, O, F, P], I),
             "tpl_lrmsd_forward_launches": ([I], I),
+            "tpl_backbone_backward_quadratic": ([P, I, I, P, P, P, P], I),
             "tpl_backbone_lrmsd_autotune": ([P, P, I, I, P, P, P, P, P, P, Z, P, P, Z, O, F, P], I),
             "tpl_fullatom_lrmsd_autotune": ([P, P, P, I, I, I, P, P, P, P, P, P, Z, P, P, Z, O, F, P], I),
             "tpl_last_error": ([], ctypes.c_char_p),
@@ -324,6 +326,16 @@ def tpl_fullatom_lrmsd_backward(seq, lengths, coords, target, num_atoms, grad_lr
         _ptr(_cuda(num_atoms, torch.int32, "num_atoms")), _ptr(_cuda(grad_lrmsd, torch.float32, "grad_lrmsd")),
         _ptr(_cuda(lrmsd_out, torch.float32, "lrmsd")), _ptr(_cuda(grad_angles, torch.float32, "grad_angles")),
         _ptr(workspace), workspace.numel() * workspace.element_size(), _opts(opts), _stream(coords, stream)))
+
+
+def tpl_backbone_backward_quadratic(lengths, coords, grad_coords, grad_angles, stream=None):
+    """The paper's O(L^2) form of the backbone backward (every angle-atom term
+    summed directly), a comparator for tpl_backbone_backward."""
+    B, _, Lmax = grad_angles.shape
+    _check("tpl_backbone_backward_quadratic", load_library().tpl_backbone_backward_quadratic(
+        _ptr(_cuda(lengths, torch.int32, "lengths")), B, Lmax, _ptr(_cuda(coords, torch.float32, "coords")),
+        _ptr(_cuda(grad_coords, torch.float32, "grad_coords")),
+        _ptr(_cuda(grad_angles, torch.float32, "grad_angles")), _stream(grad_angles, stream)))
 
 
 def tpl_backbone_backward_lrmsd(angles, lengths, coords, target, grad_lrmsd, lrmsd_workspace,

@@ -463,6 +463,19 @@ tpl_status tpl_backbone_backward(const float* angles, const int32_t* lengths, in
     return ok();
 }
 
+tpl_status tpl_backbone_backward_quadratic(const int32_t* lengths, int B, int Lmax, const float* coords,
+                                           const float* grad_coords, float* grad_angles, tpl_stream stream) {
+    const void* ptrs[4] = {lengths, coords, grad_coords, grad_angles};
+    tpl_status st = check_chain_args(B, Lmax, ptrs, 4);
+    if (st) return st;
+    if (B == 0) return ok();
+    if (B > 65535) return fail(TPL_ERR_BAD_SHAPE, "B=%d above 65535 chains per call", B);
+    cudaError_t e = launch_backbone_backward_quadratic(lengths, B, Lmax, coords, grad_coords, grad_angles,
+                                                       reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "backbone_backward_quadratic");
+    return ok();
+}
+
 tpl_status tpl_fullatom_forward(const float* angles, const uint8_t* seq, const int32_t* lengths,
                                 int B, int Lmax, int Amax, float* coords, int32_t* num_atoms,
                                 void* workspace, size_t workspace_bytes, const tpl_opts* opts,

@@ -491,6 +491,57 @@ __global__ void __launch_bounds__(NT, 512 / NT) bb_bwd_kernel(const float* __res
 }
 
 // ---------------------------------------------------------------------------
+// K2q: the paper's O(L^2) evaluation of Eq. 2 -- every (angle, atom) term
+// summed directly, no suffix scan -- as a GPU comparator for K2.  The angle
+// at atom q (q >= 1: omega at N, phi at CA, psi at C) turns the atoms k >= q
+// about the unit bond u_q = (r_q - r_{q-1}) / |.| through p_q = r_q, so
+//   dL/dalpha_q = sum_{k >= q} g_k . (u_q x (r_k - p_q)) = u_q . sum_{k >= q} (r_k - p_q) x g_k.
+// One thread per atom q of a chain (grid y = chain); the CTA stages tiles of
+// the chain's coordinates and gradients in shared memory and every thread
+// sums the tile's atoms k >= q, like a tiled all-pairs sum.
+// ---------------------------------------------------------------------------
+constexpr int kQNT = 128;
+
+__global__ void __launch_bounds__(kQNT) bb_bwd_quadratic_kernel(const int32_t* __restrict__ lengths, int Lmax,
+                                                              const float* __restrict__ coords,
+                                                              const float* __restrict__ grad_coords,
+                                                              float* __restrict__ grad_angles) {
+    __shared__ float3 s_r[kQNT], s_g[kQNT];
+    const int b = blockIdx.y;
+    const int L = clamp_length(lengths, b, Lmax);
+    const int na = 3 * L;
+    const int q0 = blockIdx.x * kQNT, q = q0 + threadIdx.x;
+    const float* r_in = coords + (size_t)b * 9 * Lmax;
+    const float* g_in = grad_coords + (size_t)b * 9 * Lmax;
+    float3 rq = make_float3(0.f, 0.f, 0.f), u = rq;
+    if (q < na) {
+        rq = make_float3(r_in[3 * q], r_in[3 * q + 1], r_in[3 * q + 2]);
+        if (q > 0) {
+            u = f3_sub(rq, make_float3(r_in[3 * q - 3], r_in[3 * q - 2], r_in[3 * q - 1]));
+            u = f3_scale(rsqrtf(f3_dot(u, u)), u);
+        }
+    }
+    float3 c = make_float3(0.f, 0.f, 0.f);  // sum_{k >= q} (r_k - p_q) x g_k
+    for (int k0 = q0; k0 < na; k0 += kQNT) {
+        const int k = k0 + threadIdx.x;
+        __syncthreads();
+        s_r[threadIdx.x] = k < na ? make_float3(r_in[3 * k], r_in[3 * k + 1], r_in[3 * k + 2]) : rq;
+        s_g[threadIdx.x] = k < na ? make_float3(g_in[3 * k], g_in[3 * k + 1], g_in[3 * k + 2])
+                                  : make_float3(0.f, 0.f, 0.f);
+        __syncthreads();
+        const int kend = min(kQNT, na - k0);
+        for (int t = 0; t < kend; ++t)
+            if (k0 + t >= q) c = f3_add(c, f3_cross(f3_sub(s_r[t], rq), s_g[t]));
+    }
+    if (q < 3 * Lmax) {
+        // atom q = 3 j + at carries omega_j (at 0), phi_j (at 1) or psi_j (at 2)
+        const int j = q / 3, at = q % 3;
+        const float val = (q > 0 && q < na) ? f3_dot(u, c) : 0.f;
+        grad_angles[(size_t)b * 3 * Lmax + row_of(at) * Lmax + j] = val;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // K7: plain FP64 per-chain forms (one CTA per chain, thread 0 serial).
 // ---------------------------------------------------------------------------
 __global__ void bb_fwd_ref64_kernel(const double* __restrict__ angles,
@@ -623,6 +674,14 @@ cudaError_t launch_backbone_forward(const float* angles, const int32_t* lengths,
                                     cfg.res_per_thread, ws, s);
     if (e != cudaSuccess) return e;
     TPL_BB_DISPATCH(fwd_t, angles, lengths, B, Lmax, coords, ws, s)
+}
+
+cudaError_t launch_backbone_backward_quadratic(const int32_t* lengths, int B, int Lmax, const float* coords,
+                                              const float* grad_coords, float* grad_angles, cudaStream_t s) {
+    if (B == 0 || Lmax == 0) return cudaSuccess;
+    const dim3 grid((3 * Lmax + kQNT - 1) / kQNT, B);
+    bb_bwd_quadratic_kernel<<<grid, kQNT, 0, s>>>(lengths, Lmax, coords, grad_coords, grad_angles);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_backbone_backward(const float* angles, const int32_t* lengths, int B, int Lmax,

@@ -28,6 +28,9 @@ bool backbone_cfg_supported(int threads, int res_per_thread);
 cudaError_t launch_backbone_forward(const float* angles, const int32_t* lengths, int B, int Lmax,
                                     float* coords, int sched_mode, void* workspace,
                                     LaunchCfg cfg, cudaStream_t s);
+// K2q: the paper's O(L^2) form of Eq. 2 from the forward's coordinates (comparator).
+cudaError_t launch_backbone_backward_quadratic(const int32_t* lengths, int B, int Lmax, const float* coords,
+                                              const float* grad_coords, float* grad_angles, cudaStream_t s);
 cudaError_t launch_backbone_backward(const float* angles, const int32_t* lengths, int B, int Lmax,
                                      const float* coords, const float* grad_coords,
                                      float* grad_angles, bool from_coords, void* workspace,

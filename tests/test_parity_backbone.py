@@ -316,3 +316,23 @@ def test_free_omega_cis_and_trans(bwd):
     assert rel_err(ga32, g64) <= GRAD_TOL
     assert rel_err(ga32[:, 2], g64[:, 2]) <= GRAD_TOL
     assert np.all(ga32[:, 2, 0] == 0)
+
+
+def test_quadratic_comparator_matches_the_scan_and_the_oracle(reference):
+    """tpl_backbone_backward_quadratic (the paper's O(L^2) sums of Eq. 2 on the
+    GPU) agrees with the oracle and with the suffix-scan backward on the same
+    FP32 coordinates; padding and omega_0 are zero."""
+    a, g, c64, g64 = reference
+    d = require_gpu()
+    c32, ga_scan = _run_fp32(a, LENGTHS, g, None, {"bwd_mode": tpl.BWD_FROM_COORDS})
+    B, _, Lmax = a.shape
+    ga_q = torch.full((B, 3, Lmax), float("nan"), device=d)
+    tpl.tpl_backbone_backward_quadratic(dev(LENGTHS, d), dev(c32, d), dev(g, d), ga_q)
+    torch.cuda.synchronize()
+    gq = host(ga_q)
+    assert np.all(np.isfinite(gq))
+    assert rel_err(gq, g64) <= GRAD_TOL
+    assert rel_err(gq, ga_scan) <= 1e-5
+    for b, L in enumerate(LENGTHS):
+        assert np.all(gq[b, :, L:] == 0)
+    assert np.all(gq[:, 2, 0] == 0)
