@@ -124,6 +124,7 @@ __device__ __forceinline__ Rigid thread_product(const float* __restrict__ ang, i
             pos[3 * k + at] = A.t;
         }
     }
+    if (j0 < L) rigid_reortho(A);  // the scan composes orthonormal operands
     return A;
 }
 
@@ -267,6 +268,7 @@ __device__ __forceinline__ Rigid local_product(const float* ang, int j0, int L, 
                 rigid_mul_R(A, cs[3 * k + at], sn[3 * k + at], bc.ct[at], bc.st[at], bc.d[at]);
         }
     }
+    if (j0 < L) rigid_reortho(A);  // as in the forward: identical frames
     return A;
 }
 

@@ -159,6 +159,13 @@ __device__ __forceinline__ Rigid load_rigid(const RigidS& s) {
 // x_0 * ... * x_{tid-1}, `cnt_excl` the sum of earlier counts, and `total` /
 // `cnt_total` include every thread.  All threads of the CTA must call it (two
 // __syncthreads); the caller composes a carry in front.
+//
+// Every product of warp totals is re-orthonormalised before it is composed
+// further: in FP32 the loss of orthogonality of composed rotations, not the
+// rounding of the rotation angle, is what drifts along a long chain, and a
+// scaled rotation also scales the translations it is later composed with, so
+// operands are corrected before use (a correction of the result afterwards
+// leaves the translations already built from it).
 // ---------------------------------------------------------------------------
 template <int NT>
 __device__ __forceinline__ void block_scan_rigid_count(const Rigid& x, int cnt, RigidS* s_rig,
@@ -192,6 +199,7 @@ __device__ __forceinline__ void block_scan_rigid_count(const Rigid& x, int cnt, 
             int cy = __shfl_up_sync(0xffffffffu, cw, off);
             if (lane >= off) {
                 w = rigid_mul(y, w);
+                rigid_reortho(w);
                 cw += cy;
             }
         }
@@ -260,7 +268,10 @@ __device__ __forceinline__ Rigid block_seg_scan_rigid(const Rigid& x, bool head,
             const Rigid y = shfl_up_rigid(w, off);
             const int fy = __shfl_up_sync(0xffffffffu, wf, off);
             if (lane >= off) {
-                if (!wf) w = rigid_mul(y, w);
+                if (!wf) {
+                    w = rigid_mul(y, w);
+                    rigid_reortho(w);
+                }
                 wf |= fy;
             }
         }
