@@ -19,8 +19,8 @@ Paper sections followed (Derevyanko & Lamoureux 2018, "TorchProteinLibrary"):
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 (closed forms, geometry invariants, finite differences, library and brute-force
 cross-checks).  The full-atom side-chain geometry is authored (the paper prints
-none), so its pins are self-consistency pins: measured internal coordinates
-reproduce the authored table.
+none); every bond and angle of it is pinned against the Engh & Huber (1991)
+values typed into tests/golden/sidechain_geometry.txt.
 """
 from __future__ import annotations
 
@@ -32,8 +32,11 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "tpl_oracle.c")
-_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# The source and library paths can be redirected (TPL_ORACLE_SRC / TPL_ORACLE_LIB)
+# so that a test can build a copy of the oracle with a planted mistake and
+# check that the pins catch it.
+_SRC = os.environ.get("TPL_ORACLE_SRC", os.path.join(_HERE, "tpl_oracle.c"))
+_LIB_PATH = os.environ.get("TPL_ORACLE_LIB", os.path.join(_HERE, "liboracle.so"))
 _lock = threading.Lock()
 _lib = None
 
@@ -46,7 +49,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "tpl_oracle.h"))):
         tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-        subprocess.run(["gcc", "-O2", "-std=c99", "-Wall", "-shared", "-fPIC", "-o", tmp,
+        subprocess.run(["gcc", "-O2", "-std=c99", "-Wall", "-shared", "-fPIC", "-I", _HERE, "-o", tmp,
                         _SRC, "-lm"], check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH

@@ -25,8 +25,11 @@
  *     at CA; in the paper's R_x convention that is R_x(-122.686 deg);
  *   - the rigid-group geometry (theta_i, d_i, r0) of the side chains is not
  *     printed in the paper; the internal coordinates below are authored from
- *     ideal stereochemistry (values rounded from Engh & Huber, Acta Cryst.
+ *     ideal stereochemistry (bond lengths and angles of Engh & Huber, Acta Cryst.
  *     A47 (1991) 392-400), backbone entries equal the Section 3 constants;
+ *     the HIS ring angles at ND1 and CD2 and the proline ring's fixed chi1
+ *     and CD dihedral are fitted so that those rings close at the Engh &
+ *     Huber closure bond and angles;
  *   - the LRMSD gradient is the exact derivative of the stated LRMSD with
  *     respect to the input y, (y'_i - U x'_i)/(N LRMSD).
  */
@@ -256,15 +259,15 @@ typedef struct {
  * bonded to group k-1's origin (CA for k = 1). */
 static const residue_def RES[NRES] = {
     {"ALA", 0, 1, {0.0}, 1, {
-        {"CB", 1, "CA", "N", "C", 1.530, 110.5, 0.0, 0}}},
+        {"CB", 1, "CA", "N", "C", 1.521, 110.4, 0.0, 0}}},
     {"ARG", 4, 4, {0}, 7, {
         {"CB", 1, "CA", "N", "C", 1.530, 110.5, 0.0, 0},
         {"CG", 2, "CB", "CA", "N", 1.520, 114.1, 0.0, 1},
         {"CD", 3, "CG", "CB", "CA", 1.520, 111.3, 0.0, 1},
         {"NE", 4, "CD", "CG", "CB", 1.460, 112.0, 0.0, 1},
-        {"CZ", 4, "NE", "CD", "CG", 1.330, 124.2, 0.0, 1},
+        {"CZ", 4, "NE", "CD", "CG", 1.329, 124.2, 0.0, 1},
         {"NH1", 4, "CZ", "NE", "CD", 1.326, 120.0, 0.0, 0},
-        {"NH2", 4, "CZ", "NE", "CD", 1.326, 119.7, 180.0, 0}}},
+        {"NH2", 4, "CZ", "NE", "CD", 1.326, 120.0, 180.0, 0}}},
     {"ASN", 2, 2, {0}, 4, {
         {"CB", 1, "CA", "N", "C", 1.530, 110.5, 0.0, 0},
         {"CG", 2, "CB", "CA", "N", 1.516, 112.6, 0.0, 1},
@@ -277,7 +280,7 @@ static const residue_def RES[NRES] = {
         {"OD2", 2, "CG", "CB", "CA", 1.249, 118.4, 180.0, 1}}},
     {"CYS", 1, 1, {0}, 2, {
         {"CB", 1, "CA", "N", "C", 1.530, 110.5, 0.0, 0},
-        {"SG", 1, "CB", "CA", "N", 1.808, 114.0, 0.0, 1}}},
+        {"SG", 1, "CB", "CA", "N", 1.808, 114.4, 0.0, 1}}},
     {"GLN", 3, 3, {0}, 5, {
         {"CB", 1, "CA", "N", "C", 1.530, 110.5, 0.0, 0},
         {"CG", 2, "CB", "CA", "N", 1.520, 114.1, 0.0, 1},
@@ -296,10 +299,10 @@ static const residue_def RES[NRES] = {
         {"CG", 2, "CB", "CA", "N", 1.497, 113.8, 0.0, 1},
         {"ND1", 2, "CG", "CB", "CA", 1.378, 122.7, 0.0, 1},
         {"CD2", 2, "CG", "CB", "CA", 1.354, 131.0, 180.0, 1},
-        {"CE1", 2, "ND1", "CG", "CB", 1.321, 109.0, 180.0, 0},
-        {"NE2", 2, "CD2", "CG", "CB", 1.374, 107.0, 180.0, 0}}},
+        {"CE1", 2, "ND1", "CG", "CB", 1.345, 106.9, 180.0, 0},
+        {"NE2", 2, "CD2", "CG", "CB", 1.382, 109.6, 180.0, 0}}},
     {"ILE", 2, 2, {0}, 4, {
-        {"CB", 1, "CA", "N", "C", 1.530, 110.5, 0.0, 0},
+        {"CB", 1, "CA", "N", "C", 1.540, 111.5, 0.0, 0},
         {"CG1", 2, "CB", "CA", "N", 1.530, 110.4, 0.0, 1},
         {"CG2", 1, "CB", "CA", "N", 1.521, 110.5, -122.6, 1},
         {"CD1", 2, "CG1", "CB", "CA", 1.513, 113.8, 0.0, 1}}},
@@ -317,7 +320,7 @@ static const residue_def RES[NRES] = {
     {"MET", 3, 3, {0}, 4, {
         {"CB", 1, "CA", "N", "C", 1.530, 110.5, 0.0, 0},
         {"CG", 2, "CB", "CA", "N", 1.520, 114.1, 0.0, 1},
-        {"SD", 3, "CG", "CB", "CA", 1.807, 112.7, 0.0, 1},
+        {"SD", 3, "CG", "CB", "CA", 1.803, 112.7, 0.0, 1},
         {"CE", 3, "SD", "CG", "CB", 1.791, 100.9, 0.0, 1}}},
     {"PHE", 2, 2, {0}, 7, {
         {"CB", 1, "CA", "N", "C", 1.530, 110.5, 0.0, 0},
@@ -327,17 +330,17 @@ static const residue_def RES[NRES] = {
         {"CE1", 2, "CD1", "CG", "CB", 1.382, 120.7, 180.0, 0},
         {"CE2", 2, "CD2", "CG", "CB", 1.382, 120.7, 180.0, 0},
         {"CZ", 2, "CE1", "CD1", "CG", 1.382, 120.0, 0.0, 0}}},
-    {"PRO", 0, 1, {-19.0}, 3, {
-        {"CB", 1, "CA", "N", "C", 1.530, 110.5, 0.0, 0},
-        {"CG", 1, "CB", "CA", "N", 1.495, 104.5, 0.0, 1},
-        {"CD", 1, "CG", "CB", "CA", 1.507, 105.5, 17.0, 0}}},
+    {"PRO", 0, 1, {-28.0}, 3, {
+        {"CB", 1, "CA", "N", "C", 1.530, 103.0, 0.0, 0},
+        {"CG", 1, "CB", "CA", "N", 1.492, 104.5, 0.0, 1},
+        {"CD", 1, "CG", "CB", "CA", 1.503, 106.1, 33.0, 0}}},
     {"SER", 1, 1, {0}, 2, {
         {"CB", 1, "CA", "N", "C", 1.530, 110.5, 0.0, 0},
         {"OG", 1, "CB", "CA", "N", 1.417, 111.1, 0.0, 1}}},
     {"THR", 1, 1, {0}, 3, {
-        {"CB", 1, "CA", "N", "C", 1.530, 110.5, 0.0, 0},
-        {"OG1", 1, "CB", "CA", "N", 1.433, 109.2, 0.0, 1},
-        {"CG2", 1, "CB", "CA", "N", 1.521, 111.1, -120.0, 1}}},
+        {"CB", 1, "CA", "N", "C", 1.540, 111.5, 0.0, 0},
+        {"OG1", 1, "CB", "CA", "N", 1.433, 109.6, 0.0, 1},
+        {"CG2", 1, "CB", "CA", "N", 1.521, 110.5, -120.0, 1}}},
     {"TRP", 2, 2, {0}, 10, {
         {"CB", 1, "CA", "N", "C", 1.530, 110.5, 0.0, 0},
         {"CG", 2, "CB", "CA", "N", 1.498, 113.6, 0.0, 1},
@@ -359,13 +362,13 @@ static const residue_def RES[NRES] = {
         {"CZ", 2, "CE1", "CD1", "CG", 1.378, 119.6, 0.0, 0},
         {"OH", 2, "CZ", "CE1", "CD1", 1.376, 119.9, 180.0, 0}}},
     {"VAL", 1, 1, {0}, 3, {
-        {"CB", 1, "CA", "N", "C", 1.530, 110.5, 0.0, 0},
+        {"CB", 1, "CA", "N", "C", 1.540, 111.5, 0.0, 0},
         {"CG1", 1, "CB", "CA", "N", 1.521, 110.5, 0.0, 1},
         {"CG2", 1, "CB", "CA", "N", 1.521, 110.5, -122.9, 1}}},
 };
 
 /* Backbone O in the M_3 frame: bonded to C, angle CA-C-O, dihedral N-CA-C-O = psi + 180. */
-static const double O_BOND = 1.231, O_ANGLE_DEG = 120.5, O_DIHEDRAL_OFFSET_DEG = 180.0;
+static const double O_BOND = 1.231, O_ANGLE_DEG = 120.1, O_DIHEDRAL_OFFSET_DEG = 180.0;
 /* R' of Section 2, about x, in the R_x convention of Section 3 (L chirality). */
 static const double RPRIME_DEG = -122.686;
 

@@ -5,8 +5,10 @@
 // through R' and R(chi), M_3 = M_1 R_3(psi), M_4 = M_3 R_4(omega)), the angle
 // of R' (122.686 degrees) and the backbone constants, but no side-chain
 // geometry.  The internal coordinates below are authored from ideal
-// stereochemistry (values rounded from Engh & Huber, Acta Cryst. A47 (1991)
-// 392-400).  Each side-chain atom is (group, bonded atom p, angle atom q,
+// stereochemistry (bond lengths and angles of Engh & Huber, Acta Cryst. A47 (1991)
+// 392-400); the HIS ring angles at ND1 and CD2 and the proline ring's fixed
+// chi1 and CD dihedral are fitted so that those rings close at the Engh &
+// Huber closure values.  Each side-chain atom is (group, bonded atom p, angle atom q,
 // dihedral atom r, bond, angle, dihedral); indices count N=0, CA=1, C=2, O=3,
 // then the side chain in output order.  A dihedral marked on_chi is an offset
 // added to its group's chi.  The first atom of each group is the group's
@@ -41,15 +43,15 @@ struct ResDef {
 };
 
 const ResDef kRes[kNumTypes] = {
-    {"ALA", 0, 1, {0.0}, 1, {{"CB", 1, 1, 0, 2, 1.530, 110.5, 0.0, 0}}},
+    {"ALA", 0, 1, {0.0}, 1, {{"CB", 1, 1, 0, 2, 1.521, 110.4, 0.0, 0}}},
     {"ARG", 4, 4, {0}, 7,
      {{"CB", 1, 1, 0, 2, 1.530, 110.5, 0.0, 0},
       {"CG", 2, 4, 1, 0, 1.520, 114.1, 0.0, 1},
       {"CD", 3, 5, 4, 1, 1.520, 111.3, 0.0, 1},
       {"NE", 4, 6, 5, 4, 1.460, 112.0, 0.0, 1},
-      {"CZ", 4, 7, 6, 5, 1.330, 124.2, 0.0, 1},
+      {"CZ", 4, 7, 6, 5, 1.329, 124.2, 0.0, 1},
       {"NH1", 4, 8, 7, 6, 1.326, 120.0, 0.0, 0},
-      {"NH2", 4, 8, 7, 6, 1.326, 119.7, 180.0, 0}}},
+      {"NH2", 4, 8, 7, 6, 1.326, 120.0, 180.0, 0}}},
     {"ASN", 2, 2, {0}, 4,
      {{"CB", 1, 1, 0, 2, 1.530, 110.5, 0.0, 0},
       {"CG", 2, 4, 1, 0, 1.516, 112.6, 0.0, 1},
@@ -62,7 +64,7 @@ const ResDef kRes[kNumTypes] = {
       {"OD2", 2, 5, 4, 1, 1.249, 118.4, 180.0, 1}}},
     {"CYS", 1, 1, {0}, 2,
      {{"CB", 1, 1, 0, 2, 1.530, 110.5, 0.0, 0},
-      {"SG", 1, 4, 1, 0, 1.808, 114.0, 0.0, 1}}},
+      {"SG", 1, 4, 1, 0, 1.808, 114.4, 0.0, 1}}},
     {"GLN", 3, 3, {0}, 5,
      {{"CB", 1, 1, 0, 2, 1.530, 110.5, 0.0, 0},
       {"CG", 2, 4, 1, 0, 1.520, 114.1, 0.0, 1},
@@ -81,10 +83,10 @@ const ResDef kRes[kNumTypes] = {
       {"CG", 2, 4, 1, 0, 1.497, 113.8, 0.0, 1},
       {"ND1", 2, 5, 4, 1, 1.378, 122.7, 0.0, 1},
       {"CD2", 2, 5, 4, 1, 1.354, 131.0, 180.0, 1},
-      {"CE1", 2, 6, 5, 4, 1.321, 109.0, 180.0, 0},
-      {"NE2", 2, 7, 5, 4, 1.374, 107.0, 180.0, 0}}},
+      {"CE1", 2, 6, 5, 4, 1.345, 106.9, 180.0, 0},
+      {"NE2", 2, 7, 5, 4, 1.382, 109.6, 180.0, 0}}},
     {"ILE", 2, 2, {0}, 4,
-     {{"CB", 1, 1, 0, 2, 1.530, 110.5, 0.0, 0},
+     {{"CB", 1, 1, 0, 2, 1.540, 111.5, 0.0, 0},
       {"CG1", 2, 4, 1, 0, 1.530, 110.4, 0.0, 1},
       {"CG2", 1, 4, 1, 0, 1.521, 110.5, -122.6, 1},
       {"CD1", 2, 5, 4, 1, 1.513, 113.8, 0.0, 1}}},
@@ -102,7 +104,7 @@ const ResDef kRes[kNumTypes] = {
     {"MET", 3, 3, {0}, 4,
      {{"CB", 1, 1, 0, 2, 1.530, 110.5, 0.0, 0},
       {"CG", 2, 4, 1, 0, 1.520, 114.1, 0.0, 1},
-      {"SD", 3, 5, 4, 1, 1.807, 112.7, 0.0, 1},
+      {"SD", 3, 5, 4, 1, 1.803, 112.7, 0.0, 1},
       {"CE", 3, 6, 5, 4, 1.791, 100.9, 0.0, 1}}},
     {"PHE", 2, 2, {0}, 7,
      {{"CB", 1, 1, 0, 2, 1.530, 110.5, 0.0, 0},
@@ -112,17 +114,17 @@ const ResDef kRes[kNumTypes] = {
       {"CE1", 2, 6, 5, 4, 1.382, 120.7, 180.0, 0},
       {"CE2", 2, 7, 5, 4, 1.382, 120.7, 180.0, 0},
       {"CZ", 2, 8, 6, 5, 1.382, 120.0, 0.0, 0}}},
-    {"PRO", 0, 1, {-19.0}, 3,
-     {{"CB", 1, 1, 0, 2, 1.530, 110.5, 0.0, 0},
-      {"CG", 1, 4, 1, 0, 1.495, 104.5, 0.0, 1},
-      {"CD", 1, 5, 4, 1, 1.507, 105.5, 17.0, 0}}},
+    {"PRO", 0, 1, {-28.0}, 3,
+     {{"CB", 1, 1, 0, 2, 1.530, 103.0, 0.0, 0},
+      {"CG", 1, 4, 1, 0, 1.492, 104.5, 0.0, 1},
+      {"CD", 1, 5, 4, 1, 1.503, 106.1, 33.0, 0}}},
     {"SER", 1, 1, {0}, 2,
      {{"CB", 1, 1, 0, 2, 1.530, 110.5, 0.0, 0},
       {"OG", 1, 4, 1, 0, 1.417, 111.1, 0.0, 1}}},
     {"THR", 1, 1, {0}, 3,
-     {{"CB", 1, 1, 0, 2, 1.530, 110.5, 0.0, 0},
-      {"OG1", 1, 4, 1, 0, 1.433, 109.2, 0.0, 1},
-      {"CG2", 1, 4, 1, 0, 1.521, 111.1, -120.0, 1}}},
+     {{"CB", 1, 1, 0, 2, 1.540, 111.5, 0.0, 0},
+      {"OG1", 1, 4, 1, 0, 1.433, 109.6, 0.0, 1},
+      {"CG2", 1, 4, 1, 0, 1.521, 110.5, -120.0, 1}}},
     {"TRP", 2, 2, {0}, 10,
      {{"CB", 1, 1, 0, 2, 1.530, 110.5, 0.0, 0},
       {"CG", 2, 4, 1, 0, 1.498, 113.6, 0.0, 1},
@@ -144,7 +146,7 @@ const ResDef kRes[kNumTypes] = {
       {"CZ", 2, 8, 6, 5, 1.378, 119.6, 0.0, 0},
       {"OH", 2, 10, 8, 6, 1.376, 119.9, 180.0, 0}}},
     {"VAL", 1, 1, {0}, 3,
-     {{"CB", 1, 1, 0, 2, 1.530, 110.5, 0.0, 0},
+     {{"CB", 1, 1, 0, 2, 1.540, 111.5, 0.0, 0},
       {"CG1", 1, 4, 1, 0, 1.521, 110.5, 0.0, 1},
       {"CG2", 1, 4, 1, 0, 1.521, 110.5, -122.9, 1}}},
 };
@@ -155,8 +157,8 @@ const char* kBackboneNames[4] = {"N", "CA", "C", "O"};
 // for the transforms placing N (omega), CA (phi), C (psi).
 const double kBbAngle[3] = {2.1186, 1.9391, 2.0610};
 const double kBbBond[3] = {1.330, 1.460, 1.525};
-// Backbone O: bonded to C, angle CA-C-O 120.5 deg, dihedral N-CA-C-O = psi + 180.
-const double kOBond = 1.231, kOAngle = 120.5, kODih = 180.0;
+// Backbone O: bonded to C, angle CA-C-O 120.1 deg, dihedral N-CA-C-O = psi + 180.
+const double kOBond = 1.231, kOAngle = 120.1, kODih = 180.0;
 // R' about x by -122.686 deg in the R_x convention of Section 3 (L chirality).
 const double kRprime = -122.686;
 
