@@ -15,6 +15,10 @@ Workloads (``--workload``):
                   same step as backbone_uneven; reports the coordinate drift and
                   gradient error against the FP64 per-chain form.
 
+The default run (training_step) also times backbone_uneven and lrmsd_batch
+with the same protocol and reports them under "workloads" (``--no-extra``
+skips them).
+
 ``--impl reference`` times the FP64 CPU oracle, as it stands, on a bounded
 sample of the same workload instead.
 
@@ -99,6 +103,8 @@ def parse(argv=None):
                    help="use the library's default launch shape instead of the autotuner's pick")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 per-chain comparison")
+    p.add_argument("--no-extra", action="store_true",
+                   help="training step only: skip the uneven backbone and LRMSD batch workloads")
     a = p.parse_args(argv)
     if a.batch <= 0:
         a.batch = DEFAULT_BATCH[a.workload]
@@ -662,32 +668,16 @@ SETUP = {"training_step": setup_training_step, "backbone_uneven": setup_backbone
 
 
 # ----------------------------------------------------------------------------- GPU arm
-def run_tpl(args):
-    import torch
-
-    import paper_1812_01108_gb300 as tpl
-    from paper_1812_01108_gb300 import build as tpl_build
-
-    rank, world, local = dist_env()
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py needs a CUDA GPU (there is no CPU path)")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=dev)
-    if rank == 0:
-        tpl_build.build()
-    if world > 1:
-        dist.barrier()
-    tpl.load_library()
-
-    d = make_inputs(args, rank)
-    st = SETUP[args.workload](args, tpl, torch, dev, d)
-    metric, unit, config = describe(args, world)
+def measure(args, workload, tpl, torch, dev, rank, world, local, flush):
+    """Times one workload's step (a CUDA graph of its C-ABI calls) and its
+    end-to-end form; returns the fields of its JSON line."""
+    sub = argparse.Namespace(**vars(args))
+    if workload != args.workload:  # an extra workload of the default run: its own defaults
+        sub.workload, sub.batch, sub.threads, sub.res_per_thread = workload, DEFAULT_BATCH[workload], 0, 0
+    d = make_inputs(sub, rank)
+    st = SETUP[workload](sub, tpl, torch, dev, d)
+    metric, unit, config = describe(sub, world)
     names = [n for n, _ in st.calls]
-    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     for _ in range(max(args.warmup, 3)):
@@ -697,7 +687,7 @@ def run_tpl(args):
     torch.cuda.synchronize()
     status = tpl.tpl_get_status()
     if status != 0:
-        raise SystemExit(f"device status 0x{status:x} after the warm-up steps")
+        raise SystemExit(f"device status 0x{status:x} after the warm-up steps ({workload})")
     # the whole step is one CUDA graph (forward -> LRMSD -> backward), replayed
     # between CUDA events; a second graph with event-record nodes between the
     # calls gives the per-call times (its extra nodes make it a little slower,
@@ -730,6 +720,8 @@ def run_tpl(args):
     clocks.start()
     time.sleep(0.3)
     if world > 1:
+        import torch.distributed as dist
+
         dist.barrier()
     torch.cuda.synchronize()
     for k in range(args.steps):
@@ -765,7 +757,7 @@ def run_tpl(args):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = st.alg[dom] / (mean_ms[names.index(dom)] * 1e-3) / 1e9
-    tr = TRAFFIC.get((args.workload, dom))
+    tr = TRAFFIC.get((workload, dom))
     if tr is not None and tr[3] is not None and tr[3] != st.shape:
         tr = None  # captured at another launch shape
     traffic = None
@@ -837,30 +829,73 @@ def run_tpl(args):
     extra = {}
     if rank == 0 and not args.no_fp64:
         extra = st.fp64()
+    config.update({"parallelism": f"replicas x{world}", "l2": "flushed (512 MiB write) before every step"})
+    config.update(st.extra_config)
+    out = {
+        "metric": metric, "value": value, "unit": unit, "ms_per_step": total_ms / args.steps,
+        "config": config,
+        "breakdown_ms": dict(zip(names, [float(x) for x in mean_ms])),
+        "breakdown_source": "graph of the step with event nodes between the calls",
+        "step_alg_bytes": step_bytes,
+        "step_gbs": step_bytes / (total_ms / args.steps * 1e-3) / 1e9,
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": sum(st.launches.values()) * args.steps,
+        "clocks": clk,
+    }
+    out.update(extra)
+    return out, d, unit
+
+
+# The default run (the training step) also times these workloads, each with
+# the same protocol, and reports them under "workloads".
+EXTRA_WORKLOADS = ("backbone_uneven", "lrmsd_batch")
+
+
+def run_tpl(args):
+    import torch
+
+    import paper_1812_01108_gb300 as tpl
+    from paper_1812_01108_gb300 import build as tpl_build
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (there is no CPU path)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        tpl_build.build()
+    if world > 1:
+        dist.barrier()
+    tpl.load_library()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    main_out, d, unit = measure(args, args.workload, tpl, torch, dev, rank, world, local, flush)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, d, unit)
+    extras = {}
+    if args.workload == "training_step" and not args.no_extra:
+        for w in EXTRA_WORKLOADS:
+            torch.cuda.empty_cache()
+            out, _, _ = measure(args, w, tpl, torch, dev, rank, world, local, flush)
+            extras[w] = out
     if rank == 0:
-        config.update({"parallelism": f"replicas x{world}",
-                       "l2": "flushed (512 MiB write) before every step"})
-        config.update(st.extra_config)
         line = {
-            "metric": metric, "value": value, "unit": unit, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": config,
-            "breakdown_ms": dict(zip(names, [float(x) for x in mean_ms])),
-            "breakdown_source": "graph of the step with event nodes between the calls",
-            "step_alg_bytes": step_bytes,
-            "step_gbs": step_bytes / (total_ms / args.steps * 1e-3) / 1e9,
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": unit, "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": sum(st.launches.values()) * args.steps,
-            "clocks": clk,
+            "metric": main_out["metric"], "value": main_out["value"], "unit": main_out["unit"],
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": main_out["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         }
-        line.update(extra)
+        line.update({k: v for k, v in main_out.items() if k not in line})
+        line["cpu_baseline"] = cpu
+        if extras:
+            line["workloads"] = extras
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

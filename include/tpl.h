@@ -274,7 +274,9 @@ tpl_status tpl_lrmsd_backward(const float* grad_lrmsd, const float* input, const
  *   Limits: P <= 4096 pairs, Nmax <= 8192 atoms; larger sizes return
  *   TPL_ERR_BAD_SHAPE and launch nothing.  Inputs and outputs as in
  *   tpl_lrmsd_forward; no allocation, no workspace.
- *   The first call on a device looks up the scratch array's device address
+ *   The scratch used is the CURRENT device's: make the device that holds
+ *   the pointers current before the call (the Python binding does).  The
+ *   first call on a device looks up the scratch array's device address
  *   (once per device); make that first call before any stream capture.
  *   All calls share the one array and it keeps the last call's contents, so
  *   calls that overlap on the GPU (different streams without ordering between

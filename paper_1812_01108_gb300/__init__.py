@@ -378,12 +378,15 @@ def tpl_lrmsd_forward(input, target, num_atoms, lrmsd_out, workspace, stream=Non
 
 
 def tpl_lrmsd_forward_noalloc(input, target, num_atoms, lrmsd_out, stream=None):
-    """LRMSD forward with the library's fixed internal scratch (no workspace)."""
+    """LRMSD forward with the library's fixed internal scratch (no workspace).
+    The C call uses the scratch array of the current device, so the tensors'
+    device is made current for it."""
     P, Nmax, _ = input.shape
-    _check("tpl_lrmsd_forward_noalloc", load_library().tpl_lrmsd_forward_noalloc(
-        _ptr(_cuda(input, torch.float32, "input")), _ptr(_cuda(target, torch.float32, "target")),
-        _ptr(_cuda(num_atoms, torch.int32, "num_atoms")), P, Nmax,
-        _ptr(_cuda(lrmsd_out, torch.float32, "lrmsd")), _stream(input, stream)))
+    with torch.cuda.device(_cuda(input, torch.float32, "input").device):
+        _check("tpl_lrmsd_forward_noalloc", load_library().tpl_lrmsd_forward_noalloc(
+            _ptr(input), _ptr(_cuda(target, torch.float32, "target")),
+            _ptr(_cuda(num_atoms, torch.int32, "num_atoms")), P, Nmax,
+            _ptr(_cuda(lrmsd_out, torch.float32, "lrmsd")), _stream(input, stream)))
 
 
 def tpl_lrmsd_backward(grad_lrmsd, input, target, num_atoms, grad_input, workspace, stream=None):

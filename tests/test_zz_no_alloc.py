@@ -2,11 +2,15 @@
 
 Some callers can neither allocate device memory nor pass a workspace, so this
 entry point keeps its scratch in a fixed array inside the library.  The test
-calls it through the C ABI twice in a row (the array keeps the previous call's
-contents) and checks each result against the workspace-based
-tpl_lrmsd_forward, within the LRMSD tolerance of the other tests.  It collects
-last so a failure here leaves every other test already run, and it passes
-alone in a fresh process as well as after the others.
+calls it through the C ABI several times in a row (the array keeps the
+previous call's contents) and checks each result against the workspace-based
+tpl_lrmsd_forward: both paths run the same deterministic kernels, so the
+results must be identical.  The calls cover both plans of the forward: the
+one-CTA-per-pair kernel (a batch that fits one wave) and the streaming
+kernels, whose per-pair partial slots fill most of the array, at the
+documented limit (4096 pairs of 8192 atoms).  It collects last so a failure
+here leaves every other test already run, and it passes alone in a fresh
+process as well as after the others.
 """
 import numpy as np
 import pytest
@@ -18,7 +22,7 @@ from tests.gpu_util import dev, host, require_gpu
 
 pytestmark = pytest.mark.gpu
 
-LRMSD_TOL = 1e-5  # the LRMSD tolerance of tests/test_parity_lrmsd.py
+MAX_PAIRS, MAX_ATOMS = 4096, 8192  # the limits include/tpl.h states
 
 
 def _with_workspace(X, Y, N):
@@ -35,24 +39,41 @@ def _no_alloc(X, Y, N):
     return out
 
 
-def test_no_alloc_forward_matches_workspace_forward_on_two_calls():
+def test_no_alloc_forward_matches_workspace_forward_on_consecutive_calls():
     d = require_gpu()
     rng = np.random.default_rng(20240)
-    cases = [workloads.lrmsd_clouds(300, 100, 5000, rng), workloads.lrmsd_clouds(57, 3, 900, rng)]
-    for x, y, n in cases:  # two calls in a row, different shapes
+    big = workloads.lrmsd_clouds(MAX_PAIRS, 100, MAX_ATOMS, rng, Nmax=MAX_ATOMS)
+    small = workloads.lrmsd_clouds(57, 3, 900, rng)
+    big2 = workloads.lrmsd_clouds(MAX_PAIRS, 3, 2000, rng)
+    assert tpl.tpl_lrmsd_forward_launches(MAX_PAIRS) == 4  # streaming kernels
+    assert tpl.tpl_lrmsd_forward_launches(57) == 1         # one CTA per pair
+    # streaming at the limit, then one CTA per pair, then streaming again over
+    # the array the first call left behind
+    for x, y, n in (big, small, big2):
         X, Y, N = dev(x, d), dev(y, d), dev(n, d)
         got = host(_no_alloc(X, Y, N))
         ref = host(_with_workspace(X, Y, N))
         torch.cuda.synchronize()
         assert np.all(np.isfinite(got))
-        assert np.abs(got - ref).max() <= LRMSD_TOL
+        assert np.array_equal(got, ref)
+        del X, Y, N
 
 
 def test_no_alloc_forward_rejects_sizes_beyond_its_limits():
     d = require_gpu()
-    x = torch.zeros((2, 8196, 3), device=d)
-    n = torch.full((2,), 8196, dtype=torch.int32, device=d)
-    out = torch.zeros((2,), device=d)
+    # too many atoms per pair
+    x = torch.zeros((2, MAX_ATOMS + 4, 3), device=d)
+    n = torch.full((2,), MAX_ATOMS + 4, dtype=torch.int32, device=d)
+    out = torch.full((2,), 7.0, device=d)
     with pytest.raises(tpl.TplError) as err:
         tpl.tpl_lrmsd_forward_noalloc(x, x, n, out)
     assert err.value.code == 2  # TPL_ERR_BAD_SHAPE
+    # too many pairs
+    x = torch.zeros((MAX_PAIRS + 1, 8, 3), device=d)
+    n = torch.full((MAX_PAIRS + 1,), 8, dtype=torch.int32, device=d)
+    out = torch.full((MAX_PAIRS + 1,), 7.0, device=d)
+    with pytest.raises(tpl.TplError) as err:
+        tpl.tpl_lrmsd_forward_noalloc(x, x, n, out)
+    assert err.value.code == 2
+    torch.cuda.synchronize()
+    assert torch.all(out == 7.0)  # nothing was launched
