@@ -92,9 +92,17 @@ typedef struct CUstream_st* tpl_stream; /* same type as cudaStream_t */
 typedef struct tpl_opts {
     int bwd_mode;       /* TPL_BWD_* */
     int threads;        /* threads per CTA of the chain kernels, 0 = tuned default */
-    int res_per_thread; /* backbone residues per thread (1, 2 or 4), 0 = tuned default */
+    int res_per_thread; /* consecutive residues per thread (1, 2 or 4), 0 = tuned default
+                           (with `threads` given: the fewest that form a supported shape) */
     int schedule;       /* TPL_SCHED_* */
 } tpl_opts;
+/* Launch shapes (threads x residues per thread; a tile is their product):
+ *  - backbone: threads 64, 128, 256, 512 x 1, 2, 4 (not 512 x 4); default 128 x 4;
+ *  - full atom: 128, 256, 384 x 1; 128, 192 x 2; 64, 192 x 4; default 384 x 1.  A full-atom chain is cut into balanced tiles of at most
+ *    threads x residues - 1 residues.  Rebuilding frames from the angles in
+ *    the full-atom backward (TPL_BWD_RECOMPUTE, or TPL_BWD_AUTO without
+ *    coordinates) needs one residue per thread: 128, 256 or 384 x 1 in both
+ *    calls (TPL_ERR_INVALID_ARG otherwise). */
 
 /* ------------------------------------------------------------------------ */
 /* Backbone model (paper Section 3)                                          */
@@ -167,9 +175,11 @@ tpl_status tpl_fullatom_forward(const float* angles, const uint8_t* seq, const i
  * p_i x sum g_k) with a suffix scan over residues for phi/psi/omega and a
  * suffix over the side-chain groups for chi.
  *   grad_coords [B][Amax][3] in, grad_angles [B][7][Lmax] out (0 at padding,
- *   unused chi rows and omega_0).  Frames are rebuilt from the angles and the
- *   forward's tile-start frames (`workspace` as filled by the forward);
- *   `coords` is unused and may be NULL (TPL_BWD_FROM_COORDS is rejected). */
+ *   unused chi rows and omega_0).  `workspace` is the one the forward filled,
+ *   with the same options.  Axes and origins come from the forward's `coords`
+ *   (TPL_BWD_FROM_COORDS, or TPL_BWD_AUTO with coords given), or frames are
+ *   rebuilt from the angles and the forward's tile-start frames
+ *   (TPL_BWD_RECOMPUTE, or AUTO with coords NULL: one residue per thread). */
 tpl_status tpl_fullatom_backward(const float* angles, const uint8_t* seq, const int32_t* lengths,
                                  int B, int Lmax, int Amax, const float* coords,
                                  const float* grad_coords, float* grad_angles, void* workspace,
@@ -342,8 +352,10 @@ tpl_status tpl_get_status(tpl_stream stream, int* device_status);
 /* Autotuner (the paper has no counterpart): runs forward + backward on the
  * caller's batch for every supported launch shape and schedule -- backbone:
  * threads 64..512 x residues per thread 1, 2, 4 x {PACKED, LONGEST_FIRST};
- * full atom: threads 64, 128, 192, 256, 384, 512 x {BATCH_ORDER, LONGEST_FIRST} -- times each with
- * CUDA events on `stream` (one untimed pass, best of five), and writes the
+ * full atom: the seven shapes above (the one-residue ones for RECOMPUTE) x
+ * {BATCH_ORDER, LONGEST_FIRST} -- times each as a CUDA graph of its calls
+ * replayed between CUDA events on `stream` (one direct untimed pass, one
+ * untimed replay, best of five), and writes the
  * fastest options to *best (and its time in ms to *best_ms if not NULL).
  * `bwd_mode` is kept in every candidate.  The arguments are those of the
  * forward and backward calls; coords, num_atoms and grad_angles are

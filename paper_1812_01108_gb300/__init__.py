@@ -538,16 +538,18 @@ class FullAtomFn(torch.autograd.Function):
         num_atoms = torch.empty((B,), dtype=torch.int32, device=angles.device)
         ws = _workspace(tpl_fullatom_workspace_size(B, Lmax), angles.device)
         tpl_fullatom_forward(angles, seq, lengths, coords, num_atoms, ws, opts)
-        ctx.save_for_backward(angles, seq, lengths, ws)
+        # the backward reads the forward's coordinates (axes and origins of
+        # every frame) and its workspace (schedule, each residue's first atom)
+        ctx.save_for_backward(angles, seq, lengths, coords, ws)
         ctx.opts = opts
         ctx.mark_non_differentiable(num_atoms)
         return coords, num_atoms
 
     @staticmethod
     def backward(ctx, grad_coords, _grad_num):
-        angles, seq, lengths, ws = ctx.saved_tensors
+        angles, seq, lengths, coords, ws = ctx.saved_tensors
         ga = torch.empty_like(angles)
-        tpl_fullatom_backward(angles, seq, lengths, None, grad_coords.contiguous(), ga, ws, ctx.opts)
+        tpl_fullatom_backward(angles, seq, lengths, coords, grad_coords.contiguous(), ga, ws, ctx.opts)
         return ga, None, None, None, None
 
 

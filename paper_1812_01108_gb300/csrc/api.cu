@@ -63,7 +63,7 @@ constexpr int kSchedWarps = kSchedThreads / 32;
 
 __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* __restrict__ lengths,
                                                                  int B, int Lmax, int tile, int mode,
-                                                                 int granule, ChainWs ws) {
+                                                                 int granule, bool balanced, ChainWs ws) {
     __shared__ int hist[kKeys];
     __shared__ int s_start[kKeys + 1];
     __shared__ int s_run[kKeys];
@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
     const int i0 = threadIdx.x * per, i1 = min(B, i0 + per);
     auto ntiles = [&](int b) {
         const int L = len(b);
+        if (balanced) return fa_num_tiles(L, tile);
         return L > 0 ? (L + tile - 1) / tile : 1;  // an empty chain still gets one tile (zero fill)
     };
     // entries that start at order position i: a long chain's tiles, or one
@@ -262,11 +263,31 @@ LaunchCfg backbone_cfg(const tpl_opts& o) {
     return c;
 }
 
+// Full-atom defaults: 384 threads x 1 residue (tiles of up to 383 residues);
+// threads without residues per thread take the fewest residues per thread that
+// form a supported shape.
 LaunchCfg fullatom_cfg(const tpl_opts& o) {
     LaunchCfg c;
-    c.threads = o.threads ? o.threads : 256;
-    c.res_per_thread = 1;
+    c.threads = o.threads ? o.threads : 384;
+    c.res_per_thread = o.res_per_thread ? o.res_per_thread : 1;
+    if (o.threads && !o.res_per_thread)
+        for (int k : {1, 2, 4})
+            if (fullatom_cfg_supported(c.threads, k)) {
+                c.res_per_thread = k;
+                break;
+            }
     return c;
+}
+
+bool fullatom_cfg_supported_recompute(const LaunchCfg& c) {
+    return c.res_per_thread == 1 && (c.threads == 128 || c.threads == 256 || c.threads == 384);
+}
+
+tpl_status check_fullatom_cfg(const LaunchCfg& c) {
+    if (!fullatom_cfg_supported(c.threads, c.res_per_thread))
+        return fail(TPL_ERR_INVALID_ARG, "unsupported full-atom launch %d threads x %d residues", c.threads,
+                    c.res_per_thread);
+    return TPL_OK;
 }
 
 tpl_status check_chain_args(int B, int Lmax, const void* const* ptrs, int nptr) {
@@ -300,8 +321,8 @@ __global__ void selftest_wait_kernel(const int* flag) {
 }
 
 cudaError_t launch_schedule(const int32_t* lengths, int B, int Lmax, int tile, int mode, int granule,
-                            const ChainWs& ws, cudaStream_t s) {
-    schedule_kernel<<<1, kSchedThreads, 0, s>>>(lengths, B, Lmax, tile, mode, granule, ws);
+                            const ChainWs& ws, cudaStream_t s, bool balanced) {
+    schedule_kernel<<<1, kSchedThreads, 0, s>>>(lengths, B, Lmax, tile, mode, granule, balanced, ws);
     return cudaGetLastError();
 }
 
@@ -352,8 +373,11 @@ namespace {
 
 // ---------------------------------------------------------------------------
 // Autotuner: times forward + backward for every supported launch shape and
-// schedule on the caller's own batch (CUDA events on `stream`; one untimed
-// pass, then the best of `kTuneReps`) and returns the fastest options.
+// schedule on the caller's own batch and returns the fastest options.  Each
+// candidate's calls are captured once into a CUDA graph (the form a training
+// loop replays; launched one by one, the calls rank shapes differently) after
+// one direct, untimed pass; the graph is replayed once untimed, then the best
+// of `kTuneReps` replays between CUDA events on `stream` counts.
 // ---------------------------------------------------------------------------
 constexpr int kTuneReps = 5;
 
@@ -363,37 +387,71 @@ tpl_status tune(const tpl_opts* cands, int n, cudaStream_t s, const Step& step, 
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
         return fail(TPL_ERR_INVALID_ARG, "autotune cannot run while the stream is being captured");
+    // the candidates run on a stream of the tuner's own (the caller's stream
+    // may be the legacy default stream, which cannot be captured), after the
+    // work already queued on the caller's stream
+    cudaStream_t ts = nullptr;
+    if (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "autotune");
+    cudaError_t es = cudaStreamSynchronize(s);
+    if (es != cudaSuccess) {
+        cudaStreamDestroy(ts);
+        return cuda_fail(es, "autotune");
+    }
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "autotune");
-    if (cudaEventCreate(&e1) != cudaSuccess) {
-        cudaEventDestroy(e0);
+    if (cudaEventCreate(&e0) != cudaSuccess) {
+        cudaStreamDestroy(ts);
         return cuda_fail(cudaGetLastError(), "autotune");
     }
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaStreamDestroy(ts);
+        return cuda_fail(cudaGetLastError(), "autotune");
+    }
+    const tpl_stream tstream = reinterpret_cast<tpl_stream>(ts);
     float best_t = -1.f;
     tpl_status st = TPL_OK;
     for (int c = 0; c < n && st == TPL_OK; ++c) {
-        if (step(cands[c]) != TPL_OK) continue;  // a shape this call rejects
-        float t_min = -1.f;
-        for (int r = 0; r < kTuneReps; ++r) {
-            cudaEventRecord(e0, s);
-            if ((st = step(cands[c])) != TPL_OK) break;
-            cudaEventRecord(e1, s);
-            const cudaError_t e = cudaEventSynchronize(e1);
-            if (e != cudaSuccess) {
-                st = cuda_fail(e, "autotune");
+        if (step(cands[c], tstream) != TPL_OK) continue;  // a shape this call rejects
+        cudaError_t e = cudaStreamSynchronize(ts);
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const tpl_status sc = step(cands[c], tstream);
+            e = cudaStreamEndCapture(ts, &graph);
+            if (sc != TPL_OK) {
+                st = sc;
+                if (graph) cudaGraphDestroy(graph);
                 break;
             }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (t_min < 0.f || ms < t_min) t_min = ms;
         }
-        if (st == TPL_OK && t_min >= 0.f && (best_t < 0.f || t_min < best_t)) {
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        float t_min = -1.f;
+        for (int r = -1; r < kTuneReps && e == cudaSuccess; ++r) {
+            cudaEventRecord(e0, ts);
+            e = cudaGraphLaunch(exec, ts);
+            cudaEventRecord(e1, ts);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e == cudaSuccess && r >= 0 && (t_min < 0.f || ms < t_min)) t_min = ms;
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "autotune");
+            break;
+        }
+        if (t_min >= 0.f && (best_t < 0.f || t_min < best_t)) {
             best_t = t_min;
             *best = cands[c];
         }
     }
+    cudaStreamSynchronize(ts);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaStreamDestroy(ts);
     if (st != TPL_OK) return st;
     if (best_t < 0.f) return fail(TPL_ERR_INVALID_ARG, "autotune: no launch shape accepted these arguments");
     if (best_ms) *best_ms = best_t;
@@ -488,8 +546,7 @@ tpl_status tpl_fullatom_forward(const float* angles, const uint8_t* seq, const i
     if (Amax < 0 || Amax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Amax=%d must be a multiple of 4", Amax);
     if (B == 0) return ok();
     LaunchCfg cfg = fullatom_cfg(o);
-    if (!fullatom_cfg_supported(cfg.threads))
-        return fail(TPL_ERR_INVALID_ARG, "unsupported full-atom launch %d threads", cfg.threads);
+    if ((st = check_fullatom_cfg(cfg))) return st;
     if ((st = check_ws(workspace, workspace_bytes, tpl_fullatom_workspace_size(B, Lmax)))) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = launch_fullatom_forward(angles, seq, lengths, B, Lmax, Amax, coords, num_atoms,
@@ -512,8 +569,7 @@ tpl_status tpl_fullatom_lrmsd_forward(const float* angles, const uint8_t* seq, c
     if (Amax < 0 || Amax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Amax=%d must be a multiple of 4", Amax);
     if (B == 0) return ok();
     LaunchCfg cfg = fullatom_cfg(o);
-    if (!fullatom_cfg_supported(cfg.threads))
-        return fail(TPL_ERR_INVALID_ARG, "unsupported full-atom launch %d threads", cfg.threads);
+    if ((st = check_fullatom_cfg(cfg))) return st;
     if ((st = check_ws(workspace, workspace_bytes, tpl_fullatom_lrmsd_workspace_size(B, Lmax)))) return st;
     cudaError_t e = launch_fullatom_lrmsd_forward(angles, seq, lengths, target, B, Lmax, Amax, coords, num_atoms,
                                                   sched_mode(o, false), workspace, cfg,
@@ -534,8 +590,7 @@ tpl_status tpl_fullatom_lrmsd_backward(const uint8_t* seq, const int32_t* length
     if (Amax < 0 || Amax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Amax=%d must be a multiple of 4", Amax);
     if (B == 0) return ok();
     LaunchCfg cfg = fullatom_cfg(o);
-    if (!fullatom_cfg_supported(cfg.threads))
-        return fail(TPL_ERR_INVALID_ARG, "unsupported full-atom launch %d threads", cfg.threads);
+    if ((st = check_fullatom_cfg(cfg))) return st;
     if ((st = check_ws(workspace, workspace_bytes, tpl_fullatom_lrmsd_workspace_size(B, Lmax)))) return st;
     cudaError_t e = launch_fullatom_lrmsd_backward(seq, lengths, coords, target, grad_lrmsd, num_atoms, lrmsd, B,
                                                    Lmax, Amax, grad_angles, workspace, cfg,
@@ -583,8 +638,7 @@ tpl_status tpl_fullatom_backward_lrmsd(const float* angles, const uint8_t* seq, 
     if (Amax < 0 || Amax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Amax=%d must be a multiple of 4", Amax);
     if (B == 0) return ok();
     LaunchCfg cfg = fullatom_cfg(o);
-    if (!fullatom_cfg_supported(cfg.threads))
-        return fail(TPL_ERR_INVALID_ARG, "unsupported full-atom launch %d threads", cfg.threads);
+    if ((st = check_fullatom_cfg(cfg))) return st;
     if ((st = check_ws(workspace, workspace_bytes, tpl_fullatom_workspace_size(B, Lmax)))) return st;
     if ((st = check_ws(const_cast<void*>(lrmsd_workspace), lrmsd_workspace_bytes, tpl_lrmsd_workspace_size(B, Amax))))
         return st;
@@ -610,8 +664,11 @@ tpl_status tpl_fullatom_backward(const float* angles, const uint8_t* seq, const 
     if (Amax < 0 || Amax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Amax=%d must be a multiple of 4", Amax);
     if (B == 0) return ok();
     LaunchCfg cfg = fullatom_cfg(o);
-    if (!fullatom_cfg_supported(cfg.threads))
-        return fail(TPL_ERR_INVALID_ARG, "unsupported full-atom launch %d threads", cfg.threads);
+    if ((st = check_fullatom_cfg(cfg))) return st;
+    if (!from_coords && !fullatom_cfg_supported_recompute(cfg))
+        return fail(TPL_ERR_INVALID_ARG,
+                    "rebuilding frames from the angles needs one residue per thread and 128, 256 or 384 threads "
+                    "(got %d x %d); pass the forward's coordinates", cfg.threads, cfg.res_per_thread);
     if ((st = check_ws(workspace, workspace_bytes, tpl_fullatom_workspace_size(B, Lmax)))) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = launch_fullatom_backward(angles, seq, lengths, B, Lmax, Amax, coords, grad_coords,
@@ -832,15 +889,19 @@ int backbone_candidates(int bwd_mode, tpl_opts* cands) {
 
 int fullatom_candidates(int bwd_mode, tpl_opts* cands) {
     int n = 0;
-    const int threads[6] = {64, 128, 192, 256, 384, 512};
+    const int shapes[7][2] = {{128, 1}, {256, 1}, {384, 1}, {128, 2}, {192, 2}, {64, 4}, {192, 4}};
     const int sch[2] = {TPL_SCHED_BATCH_ORDER, TPL_SCHED_LONGEST_FIRST};
     for (int si = 0; si < 2; ++si)
-        for (int ti = 0; ti < 6; ++ti) {
+        for (int ti = 0; ti < 7; ++ti) {
             tpl_opts o;
             memset(&o, 0, sizeof(o));
             o.bwd_mode = bwd_mode;
-            o.threads = threads[ti];
+            o.threads = shapes[ti][0];
+            o.res_per_thread = shapes[ti][1];
             o.schedule = sch[si];
+            // rebuilding frames from the angles takes one residue per thread
+            if (bwd_mode == TPL_BWD_RECOMPUTE && !fullatom_cfg_supported_recompute(LaunchCfg{o.threads, o.res_per_thread}))
+                continue;
             cands[n++] = o;
         }
     return n;
@@ -853,11 +914,11 @@ tpl_status tpl_backbone_autotune(const float* angles, const int32_t* lengths, in
     if (!best) return fail(TPL_ERR_INVALID_ARG, "best is NULL");
     tpl_opts cands[32];
     const int n = backbone_candidates(bwd_mode, cands);
-    return tune(cands, n, reinterpret_cast<cudaStream_t>(stream), [&](const tpl_opts& o) {
-        tpl_status st = tpl_backbone_forward(angles, lengths, B, Lmax, coords, workspace, workspace_bytes, &o, stream);
+    return tune(cands, n, reinterpret_cast<cudaStream_t>(stream), [&](const tpl_opts& o, tpl_stream ts) {
+        tpl_status st = tpl_backbone_forward(angles, lengths, B, Lmax, coords, workspace, workspace_bytes, &o, ts);
         if (st) return st;
         return tpl_backbone_backward(angles, lengths, B, Lmax, coords, grad_coords, grad_angles, workspace,
-                                     workspace_bytes, &o, stream);
+                                     workspace_bytes, &o, ts);
     }, best, best_ms);
 }
 
@@ -869,15 +930,15 @@ tpl_status tpl_backbone_lrmsd_autotune(const float* angles, const int32_t* lengt
     if (!best) return fail(TPL_ERR_INVALID_ARG, "best is NULL");
     tpl_opts cands[32];
     const int n = backbone_candidates(TPL_BWD_FROM_COORDS, cands);
-    return tune(cands, n, reinterpret_cast<cudaStream_t>(stream), [&](const tpl_opts& o) {
-        tpl_status st = tpl_backbone_forward(angles, lengths, B, Lmax, coords, workspace, workspace_bytes, &o, stream);
+    return tune(cands, n, reinterpret_cast<cudaStream_t>(stream), [&](const tpl_opts& o, tpl_stream ts) {
+        tpl_status st = tpl_backbone_forward(angles, lengths, B, Lmax, coords, workspace, workspace_bytes, &o, ts);
         if (st) return st;
         st = tpl_lrmsd_forward(coords, target, num_atoms, B, 3 * Lmax, lrmsd, lrmsd_workspace, lrmsd_workspace_bytes,
-                               stream);
+                               ts);
         if (st) return st;
         return tpl_backbone_backward_lrmsd(angles, lengths, B, Lmax, coords, target, grad_lrmsd, lrmsd_workspace,
                                            lrmsd_workspace_bytes, grad_angles, workspace, workspace_bytes, &o,
-                                           stream);
+                                           ts);
     }, best, best_ms);
 }
 
@@ -887,14 +948,14 @@ tpl_status tpl_fullatom_autotune(const float* angles, const uint8_t* seq, const 
                                  size_t workspace_bytes, int bwd_mode, tpl_opts* best, float* best_ms,
                                  tpl_stream stream) {
     if (!best) return fail(TPL_ERR_INVALID_ARG, "best is NULL");
-    tpl_opts cands[12];
+    tpl_opts cands[20];
     const int n = fullatom_candidates(bwd_mode, cands);
-    return tune(cands, n, reinterpret_cast<cudaStream_t>(stream), [&](const tpl_opts& o) {
+    return tune(cands, n, reinterpret_cast<cudaStream_t>(stream), [&](const tpl_opts& o, tpl_stream ts) {
         tpl_status st = tpl_fullatom_forward(angles, seq, lengths, B, Lmax, Amax, coords, num_atoms, workspace,
-                                             workspace_bytes, &o, stream);
+                                             workspace_bytes, &o, ts);
         if (st) return st;
         return tpl_fullatom_backward(angles, seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles,
-                                     workspace, workspace_bytes, &o, stream);
+                                     workspace, workspace_bytes, &o, ts);
     }, best, best_ms);
 }
 
@@ -904,18 +965,18 @@ tpl_status tpl_fullatom_lrmsd_autotune(const float* angles, const uint8_t* seq, 
                                        size_t lrmsd_workspace_bytes, float* grad_angles, void* workspace,
                                        size_t workspace_bytes, tpl_opts* best, float* best_ms, tpl_stream stream) {
     if (!best) return fail(TPL_ERR_INVALID_ARG, "best is NULL");
-    tpl_opts cands[12];
+    tpl_opts cands[20];
     const int n = fullatom_candidates(TPL_BWD_FROM_COORDS, cands);
-    return tune(cands, n, reinterpret_cast<cudaStream_t>(stream), [&](const tpl_opts& o) {
+    return tune(cands, n, reinterpret_cast<cudaStream_t>(stream), [&](const tpl_opts& o, tpl_stream ts) {
         tpl_status st = tpl_fullatom_forward(angles, seq, lengths, B, Lmax, Amax, coords, num_atoms, workspace,
-                                             workspace_bytes, &o, stream);
+                                             workspace_bytes, &o, ts);
         if (st) return st;
         st = tpl_lrmsd_forward(coords, target, num_atoms, B, Amax, lrmsd, lrmsd_workspace, lrmsd_workspace_bytes,
-                               stream);
+                               ts);
         if (st) return st;
         return tpl_fullatom_backward_lrmsd(angles, seq, lengths, B, Lmax, Amax, coords, target, grad_lrmsd,
                                            lrmsd_workspace, lrmsd_workspace_bytes, grad_angles, workspace,
-                                           workspace_bytes, &o, stream);
+                                           workspace_bytes, &o, ts);
     }, best, best_ms);
 }
 

@@ -38,6 +38,41 @@ __device__ __forceinline__ void copy_table(FaTable& dst, const FaTable& src) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = s[i];
 }
 
+// The residue table reaches the kernels as a kernel parameter.  Copying its
+// 6 KB from parameter space into shared memory serialises on the constant
+// cache (several microseconds per CTA), so the first CTA that runs on a device
+// also leaves a copy in global memory and sets g_fa_tab_ready; later CTAs copy
+// that one with 16-byte loads.  Every launch passes the same table, so a CTA
+// that finds the flag unset copies the parameter instead and the result is
+// the same either way.
+static_assert(sizeof(FaTable) % 16 == 0, "the table is copied in 16-byte pieces");
+__device__ FaTable g_fa_tab;
+__device__ int g_fa_tab_ready;
+
+__device__ __forceinline__ void load_table(FaTable& dst, const FaTable& param) {
+    __shared__ int s_ready;
+    if (threadIdx.x == 0) s_ready = flag_acquire(&g_fa_tab_ready);
+    __syncthreads();
+    constexpr int n4 = (int)(sizeof(FaTable) / 16);
+    int4* d = reinterpret_cast<int4*>(&dst);
+    if (s_ready) {
+        const int4* src = reinterpret_cast<const int4*>(&g_fa_tab);
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) d[i] = __ldcg(src + i);
+    } else {
+        copy_table(dst, param);
+        if (blockIdx.x == 0) {
+            __syncthreads();
+            int4* g = reinterpret_cast<int4*>(&g_fa_tab);
+            for (int i = threadIdx.x; i < n4; i += blockDim.x) g[i] = d[i];
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) flag_release(&g_fa_tab_ready, 1);
+        }
+    }
+    __syncthreads();
+}
+
+
 __device__ __forceinline__ int residue_type(const uint8_t* __restrict__ sq, int j, bool valid) {
     if (!valid) return kGlyCode;
     int t = sq[j];
@@ -165,173 +200,307 @@ __device__ __forceinline__ bool ws_matches(const ChainWs& ws, int tile, int B, i
 }
 
 // ---------------------------------------------------------------------------
-// K3: forward.  One tile of NT residues per step of a persistent CTA:
-//  1. every angle row and the type of each thread's residue are loaded up
-//     front; T_j is built and scanned across the tile with the atom counts,
-//     and the tile's aggregate is published for the look-back;
-//  2. each thread places its residue's atoms (N, CA, C, O, then the side
-//     chain group by group) in tile-local coordinates in the stage;
-//  3. the look-back gives the tile's start frame, which is applied to the
-//     stage in place (not for a chain's first tile: R_0 = I);
-//  4. the stage is written out with 16-byte stores.
+// Launch shapes.  A CTA has NT threads; each thread owns K consecutive
+// residues, so a tile holds at most NT * K - 1 residues (balanced tiles,
+// fa_num_tiles).  The stage holds a tile's atoms (12 bytes each) so that the
+// forward writes and the backward reads them with coalesced 16-byte accesses;
+// it has room for kStageAtoms atoms per residue slot on average.  A residue
+// has at most 14 atoms: a tile whose atoms do not fit (a long run of the
+// largest types) bypasses the stage and its atoms go to (come from) global
+// memory directly.
 // ---------------------------------------------------------------------------
-template <int NT>
-__host__ __device__ constexpr size_t fa_fwd_smem() {
-    return (size_t)(4 + NT * kMaxAtoms * 3) * 4;
+constexpr int kStageAtoms = 10;
+
+template <int NT, int K>
+__host__ __device__ constexpr int fa_stage_atoms() {
+    return NT * K * kStageAtoms;
+}
+template <int NT, int K>
+__host__ __device__ constexpr size_t fa_smem() {
+    return (size_t)(4 + 3 * fa_stage_atoms<NT, K>()) * sizeof(float);
 }
 
-// CTAs per SM the forward and backward kernels are compiled for (register cap)
-template <int NT>
+// CTAs per SM the kernels are compiled for: what shared memory allows (227 KB
+// per SM; the residue table and the scan scratch take about 7 KB per CTA),
+// capped by a register budget per thread that grows with K.
+template <int K>
+__host__ __device__ constexpr int fa_reg_budget() {
+    return K == 1 ? 80 : (K == 2 ? 96 : 160);
+}
+template <int NT, int K>
 __host__ __device__ constexpr int fa_min_blocks() {
-    return NT >= 512 ? 1 : (NT >= 384 ? 2 : (NT >= 256 ? 4 : (NT >= 192 ? 5 : 8)));
+    return (227 * 1024 / (int)(fa_smem<NT, K>() + 7 * 1024)) < (65536 / (NT * fa_reg_budget<K>()))
+               ? (227 * 1024 / (int)(fa_smem<NT, K>() + 7 * 1024))
+               : (65536 / (NT * fa_reg_budget<K>()));
 }
 
-// The coordinate-reading backward stages two tiles (coordinates and their
-// gradients), so shared memory holds fewer of its CTAs per SM.
-template <int NT>
-__host__ __device__ constexpr int fa_bwd_min_blocks() {
-    return NT >= 384 ? 2 : (NT >= 256 ? 4 : (NT >= 192 ? 5 : 8));
+// K consecutive floats (bytes) at p, 4K-byte (K-byte) aligned.
+template <int K>
+__device__ __forceinline__ void load_k(const float* __restrict__ p, float (&v)[K]) {
+    if constexpr (K == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else if constexpr (K == 2) {
+        const float2 q = __ldg(reinterpret_cast<const float2*>(p));
+        v[0] = q.x; v[1] = q.y;
+    } else {
+        v[0] = __ldg(p);
+    }
+}
+template <int K>
+__device__ __forceinline__ void load_k(const uint8_t* __restrict__ p, int (&v)[K]) {
+    if constexpr (K == 4) {
+        const uchar4 q = __ldg(reinterpret_cast<const uchar4*>(p));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else if constexpr (K == 2) {
+        const uchar2 q = __ldg(reinterpret_cast<const uchar2*>(p));
+        v[0] = q.x; v[1] = q.y;
+    } else {
+        v[0] = __ldg(p);
+    }
 }
 
+template <int K>
+__device__ __forceinline__ void load_k(const int* __restrict__ p, int (&v)[K]) {
+    if constexpr (K == 4) {
+        const int4 q = __ldg(reinterpret_cast<const int4*>(p));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else if constexpr (K == 2) {
+        const int2 q = __ldg(reinterpret_cast<const int2*>(p));
+        v[0] = q.x; v[1] = q.y;
+    } else {
+        v[0] = __ldg(p);
+    }
+}
+
+// K consecutive floats (ints) to p, 4K-byte aligned.
+template <int K>
+__device__ __forceinline__ void store_k(float* p, const float (&v)[K]) {
+    if constexpr (K == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else if constexpr (K == 2) *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    else p[0] = v[0];
+}
+template <int K>
+__device__ __forceinline__ void store_k(int* p, const int (&v)[K]) {
+    if constexpr (K == 4) *reinterpret_cast<int4*>(p) = make_int4(v[0], v[1], v[2], v[3]);
+    else if constexpr (K == 2) *reinterpret_cast<int2*>(p) = make_int2(v[0], v[1]);
+    else p[0] = v[0];
+}
+
+// The tile-start record of the forward, for the backward: frame at the tile
+// start, the tile's first atom and its atom count.
+__device__ __forceinline__ void tile_record(const ChainWs& ws, int slot, int& first, int& count) {
+    const float4 d = ws.start[4 * (size_t)slot + 3];
+    first = __float_as_int(d.x);
+    count = __float_as_int(d.y);
+}
+
+// ---------------------------------------------------------------------------
+// K3: forward.  One tile per step of a persistent CTA:
+//  1. each thread loads the angle rows and types of its K residues (vector
+//     loads), builds the residue transforms T_j = R_1(phi_j) R_3(psi_j)
+//     R_4(omega_{j+1}) and their product;
+//  2. the CTA scans the products and the atom counts (tile-local frame of
+//     each thread's first residue, its first atom) and publishes the tile's
+//     aggregate for the chain's later tiles;
+//  3. one warp gathers the earlier tiles' aggregates (the frame at the tile
+//     start; the identity for a chain's first tile, R_0 = I);
+//  4. each thread walks its residues in the chain's frame: N = M_0 0, CA =
+//     M_1 0, C and O from M_3, the side-chain groups S_0 = M_1 R', S_k =
+//     S_{k-1} R(chi_k), placing every atom r = M_g r0 into the stage;
+//  5. the stage goes out with 16-byte stores.
+// The residue tables live in shared memory.
 // LM: also reduce, per tile, the LRMSD moments (Section 4) of the tile's atoms
 // against `target`: sum dx, sum dy, sum dx dy^T, sum |dx|^2, sum |dy|^2 with
 // dx = x - x_0 (x the target, x_0 its first atom) and dy = y (the chain's
 // first atom, N of residue 0, is the origin: R_0 = I).
-template <int NT, bool LM>
-__global__ void __launch_bounds__(NT, fa_min_blocks<NT>()) fa_fwd_kernel(
+// ---------------------------------------------------------------------------
+template <int NT, int K, bool LM>
+__global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
     const float* __restrict__ angles, const uint8_t* __restrict__ seq,
     const int32_t* __restrict__ lengths, int Lmax, int Amax, float* __restrict__ coords,
     int32_t* __restrict__ num_atoms, ChainWs ws, const float* __restrict__ target,
     const __grid_constant__ FaTable tab) {
     constexpr int NW = NT / 32;
+    constexpr int TILE = NT * K;
+    constexpr int CAP = fa_stage_atoms<NT, K>();
     __shared__ FaTable s_tab;
     __shared__ RigidS s_rig[NW + 1];
     __shared__ int s_cnt[NW + 1];
     __shared__ int s_v, s_next;
+    __shared__ float4 s_start[4];  // tile-start frame and its first atom
     __shared__ float s_mom[LM ? NW : 1][17];
     extern __shared__ float4 s_dyn[];
-    float* stage = reinterpret_cast<float*>(s_dyn);  // tile-local atoms, 3 floats each
+    float* stage = reinterpret_cast<float*>(s_dyn);  // the tile's atoms, 3 floats each
 
-    copy_table(s_tab, tab);
+    load_table(s_tab, tab);
     const int ntiles = ws.hdr[kHdrTiles];
     int v = take_tile(ws.hdr + kHdrFwdNext, &s_v);
     while (v < ntiles) {
         const int2 ct = ws.tiles[v];
         const int b = ct.x, t = ct.y;
         const int L = clamp_length(lengths, b, Lmax);
-        const int T = L > 0 ? (L + NT - 1) / NT : 1;
+        const int T = fa_num_tiles(L, TILE);
+        const int s0 = fa_tile_start(L, T, t), s1 = fa_tile_start(L, T, t + 1);
         const int slot0 = b * ws.tmax;
         const float* ang = angles + (size_t)b * 7 * Lmax;
         float* out = coords + (size_t)b * Amax * 3;
+        const int j0 = s0 + threadIdx.x * K;
 
-        const int j = t * NT + threadIdx.x;
-        const bool valid = j < L;
-        int type = kGlyCode;
-        float a_phi = 0.f, a_psi = 0.f, a_om = 0.f, a_chi[kMaxGroups] = {0.f, 0.f, 0.f, 0.f};
-        if (valid) {
-            // every angle row up front (the chi rows too, used or not), so no
-            // load waits inside the side-chain loop
-            type = residue_type(seq + (size_t)b * Lmax, j, true);
-            a_phi = __ldg(ang + j);
-            a_psi = __ldg(ang + Lmax + j);
-            if (j + 1 < L) a_om = __ldg(ang + 2 * Lmax + j + 1);
+        // 1. inputs of the thread's residues, every angle row up front
+        int type[K];
+        float phi[K], psi[K], om[K], chi[kMaxGroups][K];
+        float om_next = 0.f;
+        if (j0 < s1) {
+            load_k<K>(seq + (size_t)b * Lmax + j0, type);
+            load_k<K>(ang + j0, phi);
+            load_k<K>(ang + Lmax + j0, psi);
+            load_k<K>(ang + 2 * Lmax + j0, om);
 #pragma unroll
-            for (int c = 0; c < kMaxGroups; ++c) a_chi[c] = __ldg(ang + (3 + c) * Lmax + j);
+            for (int c = 0; c < kMaxGroups; ++c) load_k<K>(ang + (3 + c) * Lmax + j0, chi[c]);
+            if (j0 + K < L) om_next = __ldg(ang + 2 * Lmax + j0 + K);
         }
-        const int nat = valid ? s_tab.n_atoms[type] : 0;
-        float sp = 0.f, cp = 1.f, ss = 0.f, cs = 1.f;
+        float sp[K], cp[K], ss[K], cs[K], so[K], co[K];
         Rigid A = rigid_identity();
-        if (valid) {
-            sincosf(a_phi, &sp, &cp);
-            sincosf(a_psi, &ss, &cs);
-            A = rigid_R(cp, sp, s_tab.bb.ct[1], s_tab.bb.st[1], s_tab.bb.d[1]);
-            rigid_mul_R(A, cs, ss, s_tab.bb.ct[2], s_tab.bb.st[2], s_tab.bb.d[2]);
-            if (j + 1 < L) {
-                float so, co;
-                sincosf(a_om, &so, &co);
-                rigid_mul_R(A, co, so, s_tab.bb.ct[0], s_tab.bb.st[0], s_tab.bb.d[0]);
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int j = j0 + k;
+            sp[k] = ss[k] = so[k] = 0.f;
+            cp[k] = cs[k] = co[k] = 1.f;
+            if (j < s1) {
+                int ty = type[k];
+                if (ty >= kNumTypes) {
+                    flag_status(TPL_STATUS_BAD_RESIDUE);
+                    ty = kGlyCode;
+                }
+                type[k] = ty;
+                cnt += s_tab.n_atoms[ty];
+                sincosf(phi[k], &sp[k], &cp[k]);
+                sincosf(psi[k], &ss[k], &cs[k]);
+                if (k == 0) A = rigid_R(cp[k], sp[k], s_tab.bb.ct[1], s_tab.bb.st[1], s_tab.bb.d[1]);
+                else rigid_mul_R(A, cp[k], sp[k], s_tab.bb.ct[1], s_tab.bb.st[1], s_tab.bb.d[1]);
+                rigid_mul_R(A, cs[k], ss[k], s_tab.bb.ct[2], s_tab.bb.st[2], s_tab.bb.d[2]);
+                if (j + 1 < L) {  // R_4(omega_{j+1}) places the next residue's N
+                    sincosf(k + 1 < K ? om[k + 1] : om_next, &so[k], &co[k]);
+                    rigid_mul_R(A, co[k], so[k], s_tab.bb.ct[0], s_tab.bb.st[0], s_tab.bb.d[0]);
+                }
             }
         }
-        Rigid E, Tot;
+        if (j0 < s1) rigid_reortho(A);  // the scan composes orthonormal operands
+
+        // 2. tile-local frame of the first residue and its first atom
+        Rigid X, Tot;
         int a0, tile_atoms;
-        block_scan_rigid_count<NT>(A, nat, s_rig, s_cnt, E, a0, Tot, tile_atoms);
-        // publish the tile's aggregate now (successors need it); every warp
-        // gathers the prefix later, so no warp waits on another for it
-        if (threadIdx.x == NT - 32) publish_prefix_agg(ws, slot0 + t, Tot, tile_atoms);
-        // residue atoms in tile-local coordinates (E is relative to the tile start)
-        if (valid) {
-            float* st = stage + 3 * a0;
-            stage_atom(st, 0, E.t);  // N = M_0 0
-            Rigid M1 = E;
-            rigid_mul_R(M1, cp, sp, s_tab.bb.ct[1], s_tab.bb.st[1], s_tab.bb.d[1]);
-            stage_atom(st, 1, M1.t);  // CA = M_1 0
-            Rigid M3 = M1;
-            rigid_mul_R(M3, cs, ss, s_tab.bb.ct[2], s_tab.bb.st[2], s_tab.bb.d[2]);
-            stage_atom(st, 2, M3.t);  // C = M_3 0
-            const float4 o = s_tab.o_r0;
-            stage_atom(st, 3, point_apply(M3, make_float3(o.x, o.y, o.z)));
-            // side-chain groups: S_k = S_{k-1} R(chi_k), S_0 = M_1 R'; atoms r = S_k r0
-            Rigid S = M1;
-            rigid_mul_Rx(S, s_tab.rp_c, s_tab.rp_s);
-            const int ng = s_tab.n_groups[type], nchi = s_tab.n_chi[type];
-            int e = 0;
-#pragma unroll
-            for (int k = 0; k < kMaxGroups; ++k) {
-                if (k >= ng) break;
-                float sc, cc;
-                if (k < nchi) {
-                    // chi moves only its own side chain (no error propagates along
-                    // the chain): the SFU sine/cosine is accurate enough here
-                    __sincosf(a_chi[k], &sc, &cc);
-                } else {
-                    cc = s_tab.fixchi[type][k].x;
-                    sc = s_tab.fixchi[type][k].y;
-                }
-                const float4 gk = s_tab.grp[type][k];
-                rigid_mul_R(S, cc, sc, gk.x, gk.y, gk.z);
-                const int end = s_tab.grp_end[type][k];
-                for (; e < end; ++e) {
-                    const float4 r0 = s_tab.side[type][e];
-                    stage_atom(st, (int)r0.w & 15, point_apply(S, make_float3(r0.x, r0.y, r0.z)));
-                }
+        block_scan_rigid_count<NT>(A, cnt, s_rig, s_cnt, X, a0, Tot, tile_atoms);
+        if (threadIdx.x == NT - 32 && t + 1 < T) publish_prefix_agg(ws, slot0 + t, Tot, tile_atoms);
+
+        // 3. frame at the tile start and its first atom (one warp)
+        if (threadIdx.x < 32) {
+            int pc = 0;
+            const Rigid P = gather_prefix(ws, slot0, t, pc);
+            if (threadIdx.x == 0) {
+                s_next = request_tile(ws.hdr + kHdrFwdNext);  // after the last wait of this tile
+                store_rigid_g(s_start, P, pc, tile_atoms);
+                store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, pc, tile_atoms);
             }
         }
         __syncthreads();
-        // frame at the tile start (every warp gathers it), applied in place
         int pc;
-        const Rigid P = gather_prefix(ws, slot0, t, pc);
-        const int requested = request_tile(ws.hdr + kHdrFwdNext);  // after the last wait of this tile
-        if (threadIdx.x == 0) s_next = requested;
-        if (threadIdx.x == 0) store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, pc, tile_atoms);
-        if (valid) ws.ratom[(size_t)b * Lmax + j] = pc + a0;  // the backward reads its atoms directly
+        const Rigid P = load_rigid_prev(s_start, pc);
+        const int requested = s_next;
         const int end_atom = pc + tile_atoms;
         const int nout = max(0, min(end_atom, Amax) - pc);
-        if (t > 0) {  // the chain's first tile starts at the identity frame (R_0 = I)
-            for (int a = threadIdx.x; a < nout; a += NT) {
-                const float3 r = point_apply(P, make_float3(stage[3 * a], stage[3 * a + 1], stage[3 * a + 2]));
-                stage[3 * a] = r.x;
-                stage[3 * a + 1] = r.y;
-                stage[3 * a + 2] = r.z;
+        // the tile's atoms go through the stage unless they do not fit in it
+        const bool staged = tile_atoms <= CAP;
+        float* dst = staged ? stage : out + 3 * (size_t)pc;
+        const int lim = staged ? CAP : Amax - pc;  // tile atoms at or past it are not written
+
+        // 4. atoms in the chain's frame
+        if (j0 < s1) {
+            Rigid M0 = t > 0 ? rigid_mul(P, X) : X;
+            int a = a0;
+            int ra[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int j = j0 + k;
+                if (j >= s1) break;
+                const int ty = type[k];
+                ra[k] = pc + a;
+                float* st = dst + 3 * a;
+                const int room = lim - a;  // atoms of this residue that may be written
+                auto put = [&](int idx, float3 r) {
+                    if (idx < room) stage_atom(st, idx, r);
+                };
+                Rigid M1 = M0;
+                rigid_mul_R(M1, cp[k], sp[k], s_tab.bb.ct[1], s_tab.bb.st[1], s_tab.bb.d[1]);
+                Rigid M3 = M1;
+                rigid_mul_R(M3, cs[k], ss[k], s_tab.bb.ct[2], s_tab.bb.st[2], s_tab.bb.d[2]);
+                put(0, M0.t);  // N = M_0 0
+                put(1, M1.t);  // CA = M_1 0
+                put(2, M3.t);  // C = M_3 0
+                const float4 o = s_tab.o_r0;
+                put(3, point_apply(M3, make_float3(o.x, o.y, o.z)));
+                // side-chain groups: S_k = S_{k-1} R(chi_k), S_0 = M_1 R'; atoms r = S_k r0
+                Rigid S = M1;
+                rigid_mul_Rx(S, s_tab.rp_c, s_tab.rp_s);
+                const int ng = s_tab.n_groups[ty], nchi = s_tab.n_chi[ty];
+                int e = 0;
+#pragma unroll
+                for (int g = 0; g < kMaxGroups; ++g) {
+                    if (g >= ng) break;
+                    float sc, cc;
+                    if (g < nchi) {
+                        // chi moves only its own side chain (no error propagates along
+                        // the chain): the SFU sine/cosine is accurate enough here
+                        __sincosf(chi[g][k], &sc, &cc);
+                    } else {
+                        cc = s_tab.fixchi[ty][g].x;
+                        sc = s_tab.fixchi[ty][g].y;
+                    }
+                    const float4 gk = s_tab.grp[ty][g];
+                    rigid_mul_R(S, cc, sc, gk.x, gk.y, gk.z);
+                    const int end = s_tab.grp_end[ty][g];
+                    for (; e < end; ++e) {
+                        const float4 r0 = s_tab.side[ty][e];
+                        put((int)r0.w & 15, point_apply(S, make_float3(r0.x, r0.y, r0.z)));
+                    }
+                }
+                a += s_tab.n_atoms[ty];
+                if (k + 1 < K && j + 1 < L) {  // the next residue's frame
+                    M0 = M3;
+                    rigid_mul_R(M0, co[k], so[k], s_tab.bb.ct[0], s_tab.bb.st[0], s_tab.bb.d[0]);
+                }
             }
+            // each residue's first atom, which the backward reads its atoms by
+            // (a thread's K residues lie in one tile: tile starts are multiples
+            // of 4; past the chain's end the entries are unused)
+            store_k<K>(ws.ratom + (size_t)b * Lmax + j0, ra);
         }
         __syncthreads();
         {
             // the next tile's angle rows and sequence into L2 while this tile is stored
-            const int vn = s_next;
-            if (vn < ntiles && threadIdx.x < 64) {
-                const int2 cn = ws.tiles[vn];
-                const int row = threadIdx.x >> 3, part = threadIdx.x & 7;  // 8 rows x 8 parts of NT residues
-                const int jn = cn.y * NT + part * (NT / 8);
-                if (cn.x >= 0 && jn < Lmax) {
-                    const char* base = row < 7 ? reinterpret_cast<const char*>(angles + ((size_t)cn.x * 7 + row) * Lmax + jn)
-                                               : reinterpret_cast<const char*>(seq + (size_t)cn.x * Lmax + jn);
-                    const int bytes = (row < 7 ? 4 : 1) * min(NT / 8, Lmax - jn);
-                    for (int o = 0; o < bytes; o += 128) prefetch_l2(base + o);
+            if (requested < ntiles && threadIdx.x < 64) {
+                const int2 cn = ws.tiles[requested];
+                const int row = threadIdx.x >> 3, part = threadIdx.x & 7;  // 8 rows x 8 parts of the tile
+                if (cn.x >= 0) {
+                    const int Ln = clamp_length(lengths, cn.x, Lmax);
+                    const int Tn = fa_num_tiles(Ln, TILE);
+                    const int sn = fa_tile_start(Ln, Tn, cn.y), en = fa_tile_start(Ln, Tn, cn.y + 1);
+                    const int per = (en - sn + 7) / 8;
+                    const int jn = sn + part * per;
+                    if (jn < en) {
+                        const char* base = row < 7 ? reinterpret_cast<const char*>(angles + ((size_t)cn.x * 7 + row) * Lmax + jn)
+                                                   : reinterpret_cast<const char*>(seq + (size_t)cn.x * Lmax + jn);
+                        const int bytes = (row < 7 ? 4 : 1) * min(per, en - jn);
+                        for (int o = 0; o < bytes; o += 128) prefetch_l2(base + o);
+                    }
                 }
             }
         }
         if (end_atom > Amax && threadIdx.x == 0) flag_status(TPL_STATUS_TOO_MANY_ATOMS);
-        store_range<NT>(out, stage, 3 * pc, 3 * (pc + nout));
+        // 5. the stage out
+        if (staged) store_range<NT>(out, stage, 3 * pc, 3 * (pc + nout));
         if (t == T - 1) {
             if (threadIdx.x == 0) num_atoms[b] = end_atom;
             zero_range<NT>(out, 3 * min(end_atom, Amax), 3 * Amax);
@@ -339,13 +508,16 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT>()) fa_fwd_kernel(
         if constexpr (LM) {
             const float* tg = target + (size_t)b * Amax * 3;
             const float3 x0 = make_float3(__ldg(tg), __ldg(tg + 1), __ldg(tg + 2));
+            // the tile's coordinates: the stage, or (tiles that bypass it) this
+            // CTA's own global writes, visible after the barrier above
+            const float* ys = staged ? stage : out + 3 * (size_t)pc;
             float m[17];
 #pragma unroll
-            for (int k = 0; k < 17; ++k) m[k] = 0.f;
+            for (int q = 0; q < 17; ++q) m[q] = 0.f;
             for (int a = threadIdx.x; a < nout; a += NT) {
                 const float* xa = tg + 3 * (size_t)(pc + a);
                 const float3 dx = make_float3(__ldg(xa) - x0.x, __ldg(xa + 1) - x0.y, __ldg(xa + 2) - x0.z);
-                const float3 dy = make_float3(stage[3 * a], stage[3 * a + 1], stage[3 * a + 2]);
+                const float3 dy = make_float3(ys[3 * a], ys[3 * a + 1], ys[3 * a + 2]);
                 m[0] += dx.x; m[1] += dx.y; m[2] += dx.z;
                 m[3] += dy.x; m[4] += dy.y; m[5] += dy.z;
                 m[6] = fmaf(dx.x, dy.x, m[6]); m[7] = fmaf(dx.x, dy.y, m[7]); m[8] = fmaf(dx.x, dy.z, m[8]);
@@ -357,90 +529,77 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT>()) fa_fwd_kernel(
             // block sum: warp shuffles, then the warp sums in a fixed order
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-            for (int k = 0; k < 17; ++k) {
-                float v = m[k];
+            for (int q = 0; q < 17; ++q) {
+                float x = m[q];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                m[k] = v;
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                m[q] = x;
             }
             if (lane == 0)
 #pragma unroll
-                for (int k = 0; k < 17; ++k) s_mom[warp][k] = m[k];
+                for (int q = 0; q < 17; ++q) s_mom[warp][q] = m[q];
             __syncthreads();
             if (threadIdx.x < 17) {
-                float v = 0.f;
-                for (int w = 0; w < NW; ++w) v += s_mom[w][threadIdx.x];
-                ws.tmom[(size_t)(slot0 + t) * 20 + threadIdx.x] = v;
+                float x = 0.f;
+                for (int w = 0; w < NW; ++w) x += s_mom[w][threadIdx.x];
+                ws.tmom[(size_t)(slot0 + t) * 20 + threadIdx.x] = x;
             }
         }
         v = next_tile(requested, &s_v);
     }
 }
 
-// Block-wide exclusive scan of an int (tile atom offsets); two __syncthreads.
-template <int NT>
-__device__ __forceinline__ int block_scan_int(int x, int* s_cnt, int& total) {
-    constexpr int NW = NT / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int inc = x;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, inc, off);
-        if (lane >= off) inc += y;
-    }
-    if (lane == 31) s_cnt[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        int w = lane < NW ? s_cnt[lane] : 0;
-#pragma unroll
-        for (int off = 1; off < NW; off <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, w, off);
-            if (lane >= off) w += y;
-        }
-        if (lane < NW) s_cnt[lane] = w - (lane < NW ? s_cnt[lane] : 0);
-        if (lane == NW - 1) s_cnt[NW] = w;
-    }
-    __syncthreads();
-    total = s_cnt[NW];
-    return s_cnt[warp] + inc - x;
-}
-
-// ---------------------------------------------------------------------------
-// K4': backward from the forward's coordinates.  Axes and origins come from
-// atom positions (phi: N->CA, psi: CA->C, omega: C_{j-1}->N_j, chi_k: origin of
-// group k-1 -> origin of group k); the tile's atoms and their upstream
-// gradients are staged in shared memory with 16-byte loads.
-// ---------------------------------------------------------------------------
 
 __device__ __forceinline__ float3 unit3(float3 v) { return f3_scale(rsqrtf(f3_dot(v, v)), v); }
 
-
+// ---------------------------------------------------------------------------
+// K4': backward from the forward's coordinates.  For a frame with x axis u and
+// origin p, dL/dalpha = u . sum_{k downstream} (r_k - p) x g_k; axes and
+// origins come from atom positions (phi: N->CA, psi: CA->C, omega: C_{j-1}->N_j,
+// chi_k: origin of group k-1 -> origin of group k).  One tile per step of a
+// persistent CTA, the tiles of a chain taken last to first:
+//  1. the tile's coordinates are staged with coalesced asynchronous copies
+//     (the forward recorded each tile's first atom and atom count, and every
+//     residue's first atom);
+//  2. each thread walks its K residues: every atom's gradient (read, or the
+//     LRMSD gradient formed from the coordinates, the target and the LRMSD
+//     state), the residue's (sum r x g, sum g), and the chi gradients from the
+//     suffix over its side-chain groups;
+//  3. a block suffix scan of the threads' sums and one warp's look-back over
+//     the chain's later tiles give, for every thread, the sums over all later
+//     atoms of the chain;
+//  4. each thread walks its residues back, adding each residue's sums, and
+//     forms phi, psi and omega from them and from its N, C and O terms.
 // RES (with LR, the fused training step): the LRMSD gradient is formed
 // without its 1 / (N LRMSD) factor, each tile also sums its atoms' squared
 // residuals |y' - U x'|^2 (Section 4), and the chain's first tile -- taken
 // last -- waits for the chain's other tiles, forms LRMSD in FP64 and rescales
 // the chain's angle gradients.
-template <int NT, bool LR, bool RES>
-__global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_kernel(
+// ---------------------------------------------------------------------------
+template <int NT, int K, bool LR, bool RES>
+__global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kernel(
     const uint8_t* __restrict__ seq, const int32_t* __restrict__ lengths, int B, int Lmax, int Amax,
     const float* __restrict__ coords, const float* __restrict__ grad_coords,
     float* __restrict__ grad_angles, ChainWs ws, LrmsdGrad lg, const __grid_constant__ FaTable tab) {
     constexpr int NW = NT / 32;
+    constexpr int TILE = NT * K;
+    constexpr int CAP = fa_stage_atoms<NT, K>();
     __shared__ FaTable s_tab;
     __shared__ float s6[6 * (NW + 1)];
-    __shared__ int s_v;
+    __shared__ float s_later[6];
+    __shared__ int s_v, s_next;
     __shared__ float s_res[NW];
     __shared__ float s_scale;
     extern __shared__ float4 s_dyn[];
     float* st_r = reinterpret_cast<float*>(s_dyn);  // the tile's coordinates
 
-    if (!ws_matches(ws, NT, B, Lmax)) {
+    if (!ws_matches(ws, TILE, B, Lmax)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) flag_status(TPL_STATUS_BAD_WORKSPACE);
         for (size_t i = blockIdx.x * (size_t)NT + threadIdx.x; i < (size_t)B * 7 * Lmax; i += (size_t)gridDim.x * NT)
             grad_angles[i] = 0.f;
         return;
     }
-    copy_table(s_tab, tab);
+    load_table(s_tab, tab);
     const int ntiles = ws.hdr[kHdrTiles];
     int* counter = ws.bflag + ws.slots;
     int v = take_tile(counter, &s_v);
@@ -448,124 +607,213 @@ __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_ker
         const int2 ct = ws.tiles[v];
         const int b = ct.x;
         const int L = clamp_length(lengths, b, Lmax);
-        const int T = L > 0 ? (L + NT - 1) / NT : 1;
+        const int T = fa_num_tiles(L, TILE);
         const int t = T - 1 - ct.y;  // last tile first
+        const int s0 = fa_tile_start(L, T, t), s1 = fa_tile_start(L, T, t + 1);
         const int slot0 = b * ws.tmax;
-        const uint8_t* sq = seq + (size_t)b * Lmax;
         const float* r_in = coords + (size_t)b * Amax * 3;
-        const float* g_in = grad_coords + (size_t)b * Amax * 3;
         float* ga = grad_angles + (size_t)b * 7 * Lmax;
 
-        // the tile's coordinates are staged with coalesced asynchronous copies
-        // (the forward recorded the tile's first atom and atom count, and
-        // every residue's first atom); each thread reads the gradient or
-        // target of its own atoms directly
-        const float4 sd = ws.start[4 * (size_t)(slot0 + t) + 3];
-        const int pc = __float_as_int(sd.x);
-        const int soff = (3 * pc) & 3;
-        async_copy_range<NT>(r_in, st_r, 3 * pc, 3 * min(pc + __float_as_int(sd.y), Amax));
-        const int j = t * NT + threadIdx.x;
-        const bool valid = j < L;
-        const int type = residue_type(sq, j, valid);
-        const int nat = valid ? s_tab.n_atoms[type] : 0;
-        const int a0 = valid ? __ldg(ws.ratom + (size_t)b * Lmax + j) : 0;
-        const int ap = (valid && j > 0) ? __ldg(ws.ratom + (size_t)b * Lmax + j - 1) : 0;
-
-        const bool in_range = valid && a0 >= pc && a0 + nat <= Amax && a0 - pc + nat <= NT * kMaxAtoms;
+        // 1. the tile's coordinates into the stage (unless they do not fit)
+        int pc, n;
+        tile_record(ws, slot0 + t, pc, n);
+        const int a_end = min(pc + n, Amax);  // the tile's atoms present in the output
+        const bool staged = n <= CAP;
+        if (staged) async_copy_range<NT>(r_in, st_r, 3 * pc, 3 * a_end);
+        // atom a is at rb[rofs + 3 a]
+        const float* rb = staged ? st_r : r_in;
+        const int rofs = staged ? ((3 * pc) & 3) - 3 * pc : 0;
+        const int j0 = s0 + threadIdx.x * K;
+        int type[K], a0[K];
+        if (j0 < s1) {
+            load_k<K>(seq + (size_t)b * Lmax + j0, type);
+            load_k<K>(ws.ratom + (size_t)b * Lmax + j0, a0);
+        }
+        int aprev = 0;  // first atom of the residue before the thread's first one
+        if (j0 < s1 && j0 > 0) aprev = __ldg(ws.ratom + (size_t)b * Lmax + j0 - 1);
+        float3 u0 = make_float3(0.f, 0.f, 0.f), u1 = u0, u2 = u0, xc = u0, yc = u0;
+        float w = 0.f;
+        if constexpr (LR) {
+            const float* st = lg.state + 16 * (size_t)b;
+            u0 = make_float3(__ldg(st), __ldg(st + 1), __ldg(st + 2));
+            u1 = make_float3(__ldg(st + 3), __ldg(st + 4), __ldg(st + 5));
+            u2 = make_float3(__ldg(st + 6), __ldg(st + 7), __ldg(st + 8));
+            xc = make_float3(__ldg(st + 9), __ldg(st + 10), __ldg(st + 11));
+            yc = make_float3(__ldg(st + 12), __ldg(st + 13), __ldg(st + 14));
+            w = __ldg(lg.grad_lrmsd + b) * (RES ? 1.f : __ldg(st + 15));
+        }
+        auto Rp = [&](int a) { return make_float3(rb[rofs + 3 * a], rb[rofs + 3 * a + 1], rb[rofs + 3 * a + 2]); };
+        // the coordinate gradient of atom a at position r: read, or formed from
+        // the LRMSD state (and, for RES, its squared residual added to *res)
+        auto G = [&](int a, float3 r, float* res) {
+            const float* src = LR ? lg.target + ((size_t)b * Amax + a) * 3 : grad_coords + ((size_t)b * Amax + a) * 3;
+            const float3 v3 = make_float3(__ldg(src), __ldg(src + 1), __ldg(src + 2));
+            if constexpr (!LR) return v3;
+            const float3 xp = f3_sub(v3, xc), yp = f3_sub(r, yc);
+            const float3 d = make_float3(yp.x - f3_dot(u0, xp), yp.y - f3_dot(u1, xp), yp.z - f3_dot(u2, xp));
+            if (RES && res) *res += f3_dot(d, d);
+            return f3_scale(w, d);
+        };
+        auto add = [](Sum6& s, float3 r, float3 g) {
+            s.c = f3_add(s.c, f3_cross(r, g));
+            s.g = f3_add(s.g, g);
+        };
         cp_async_wait_all();
         __syncthreads();
+
+        // 2. residue sums and chi gradients; with up to two residues per thread
+        // the N and C, O sums and the axis atoms are kept for step 4, with more
+        // they are formed again there
+        constexpr bool KEEP = K <= 2;
         float res_acc = 0.f;  // RES: this thread's squared residuals
-        float gchi[kMaxGroups] = {0.f, 0.f, 0.f, 0.f};
-        Sum6 all = sum6_zero(), nsum = sum6_zero(), csum = sum6_zero();
-        float3 rN = make_float3(0.f, 0.f, 0.f), rCA = rN, rC = rN, rCprev = rN;
-        if (in_range) {
-            const float* sr = st_r + soff + 3 * (a0 - pc);
-            auto R = [&](int k) { return make_float3(sr[3 * k], sr[3 * k + 1], sr[3 * k + 2]); };
-            // the coordinate gradient: read, or formed from the LRMSD state
-            const float* sg = LR ? lg.target + ((size_t)b * Amax + a0) * 3 : g_in + 3 * (size_t)a0;
-            float3 u0 = make_float3(0.f, 0.f, 0.f), u1 = u0, u2 = u0, xc = u0, yc = u0;
-            float w = 0.f;
-            if constexpr (LR) {
-                const float* st = lg.state + 16 * (size_t)b;
-                u0 = make_float3(__ldg(st), __ldg(st + 1), __ldg(st + 2));
-                u1 = make_float3(__ldg(st + 3), __ldg(st + 4), __ldg(st + 5));
-                u2 = make_float3(__ldg(st + 6), __ldg(st + 7), __ldg(st + 8));
-                xc = make_float3(__ldg(st + 9), __ldg(st + 10), __ldg(st + 11));
-                yc = make_float3(__ldg(st + 12), __ldg(st + 13), __ldg(st + 14));
-                w = __ldg(lg.grad_lrmsd + b) * (RES ? 1.f : __ldg(st + 15));
-            }
-            auto G = [&](int k) {
-                const float3 v = make_float3(__ldg(sg + 3 * k), __ldg(sg + 3 * k + 1), __ldg(sg + 3 * k + 2));
-                if constexpr (!LR) return v;
-                const float3 xp = f3_sub(v, xc), yp = f3_sub(R(k), yc);
-                const float3 r = make_float3(yp.x - f3_dot(u0, xp), yp.y - f3_dot(u1, xp), yp.z - f3_dot(u2, xp));
-                if constexpr (RES) res_acc += f3_dot(r, r);
-                return f3_scale(w, r);
-            };
-            auto add = [&](Sum6& s, int k) {
-                const float3 g = G(k);
-                s.c = f3_add(s.c, f3_cross(R(k), g));
-                s.g = f3_add(s.g, g);
-            };
-            rN = R(0);
-            rCA = R(1);
-            rC = R(2);
-            if (j > 0) {  // C of the previous residue (the tile before holds it for the first)
-                const float* pr = ap >= pc ? st_r + soff + 3 * (ap + 2 - pc) : r_in + 3 * (size_t)(ap + 2);
-                rCprev = make_float3(pr[0], pr[1], pr[2]);
-            }
-            add(nsum, 0);
-            add(all, 1);
-            add(csum, 2);
-            add(csum, 3);
-            // side chain, entries in decreasing group order: suffix over groups
-            const int nchi = s_tab.n_chi[type];
-            Sum6 suf = sum6_zero();
-            for (int e = nat - 5; e >= 0; --e) {
-                const int w = (int)s_tab.side[type][e].w;
-                const int grp = w >> 4;
-                add(suf, w & 15);
-                const bool last_of_group = (e == 0) || (((int)s_tab.side[type][e - 1].w >> 4) != grp);
-                if (last_of_group && grp <= nchi) {
-                    const int o1 = s_tab.origin[type][grp - 1];
-                    const int o0 = grp >= 2 ? s_tab.origin[type][grp - 2] : 1;
-                    const float3 p = R(o1);
-                    const float val = f3_dot(unit3(f3_sub(p, R(o0))), f3_sub(suf.c, f3_cross(p, suf.g)));
+        Sum6 own[K];
+        Sum6 tsum = sum6_zero();
+        bool in_range[K];
+        float gchi[kMaxGroups][K];
+        Sum6 nkeep[KEEP ? K : 1], cokeep[KEEP ? K : 1];
+        float3 rkeep[KEEP ? K : 1][3];
 #pragma unroll
-                    for (int k = 0; k < kMaxGroups; ++k)
-                        if (k == grp - 1) gchi[k] = val;
-                }
+        for (int k = 0; k < K; ++k) {
+            const int j = j0 + k;
+            own[k] = sum6_zero();
+            in_range[k] = false;
+#pragma unroll
+            for (int c = 0; c < kMaxGroups; ++c) gchi[c][k] = 0.f;
+            if (j >= s1) continue;
+            int ty = type[k];
+            if (ty >= kNumTypes) {
+                flag_status(TPL_STATUS_BAD_RESIDUE);
+                ty = kGlyCode;
             }
-            all = sum6_add(sum6_add(all, suf), csum);
+            type[k] = ty;
+            const int nat = s_tab.n_atoms[ty];
+            const int a = a0[k];
+            in_range[k] = a >= pc && a + nat <= a_end;
+            if (in_range[k]) {
+                Sum6 s = sum6_zero();
+                if constexpr (KEEP) {
+                    Sum6 ns = sum6_zero(), co = sum6_zero(), ca = sum6_zero();
+                    const float3 rN = Rp(a), rCA = Rp(a + 1), rC = Rp(a + 2), rO = Rp(a + 3);
+                    add(ns, rN, G(a, rN, &res_acc));
+                    add(ca, rCA, G(a + 1, rCA, &res_acc));
+                    add(co, rC, G(a + 2, rC, &res_acc));
+                    add(co, rO, G(a + 3, rO, &res_acc));
+                    s = sum6_add(sum6_add(ns, ca), co);
+                    nkeep[k] = ns;
+                    cokeep[k] = co;
+                    rkeep[k][0] = rN;
+                    rkeep[k][1] = rCA;
+                    rkeep[k][2] = rC;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {  // N, CA, C, O
+                        const float3 r = Rp(a + q);
+                        add(s, r, G(a + q, r, &res_acc));
+                    }
+                }
+                // side chain, entries in decreasing group order: suffix over groups
+                const int nchi = s_tab.n_chi[ty];
+                Sum6 suf = sum6_zero();
+                for (int e = nat - 5; e >= 0; --e) {
+                    const int wv = (int)s_tab.side[ty][e].w;
+                    const int grp = wv >> 4;
+                    const float3 r = Rp(a + (wv & 15));
+                    add(suf, r, G(a + (wv & 15), r, &res_acc));
+                    const bool last_of_group = (e == 0) || (((int)s_tab.side[ty][e - 1].w >> 4) != grp);
+                    if (last_of_group && grp <= nchi) {
+                        const int o1 = s_tab.origin[ty][grp - 1];
+                        const int o0 = grp >= 2 ? s_tab.origin[ty][grp - 2] : 1;
+                        const float3 p = Rp(a + o1);
+                        const float val = f3_dot(unit3(f3_sub(p, Rp(a + o0))), f3_sub(suf.c, f3_cross(p, suf.g)));
+#pragma unroll
+                        for (int c = 0; c < kMaxGroups; ++c)
+                            if (c == grp - 1) gchi[c][k] = val;
+                    }
+                }
+                own[k] = sum6_add(s, suf);
+                tsum = sum6_add(tsum, own[k]);
+            }
         }
-        const Sum6 own = sum6_add(all, nsum);
+        // A thread's K residues lie in one tile (tile starts are multiples of 4),
+        // except past the chain's end, where the last tile writes zeros anyway.
+        if (j0 < s1) {
+#pragma unroll
+            for (int c = 0; c < kMaxGroups; ++c) store_k<K>(ga + (3 + c) * Lmax + j0, gchi[c]);
+        }
+
+        // 3. sums over the later threads of the tile and the chain's later tiles
         Sum6 after, total;
-        block_suffix_sum6<NT>(own, s6, after, total);
-        if (threadIdx.x == NT - 32) publish_suffix_agg(ws, slot0 + t, total);
-        after = sum6_add(after, gather_suffix(ws, slot0, t, T));  // every warp gathers it
-        // after the last wait of this tile (the chain's first tile of a fused
-        // step still waits for the chain's other tiles: it asks later)
-        int requested = (RES && t == 0) ? 0 : request_tile(counter);
-        if (j < Lmax) {
-            float gphi = 0.f, gpsi = 0.f, gomg = 0.f;
-            if (in_range) {
-                Sum6 x = sum6_add(csum, after);
-                gpsi = f3_dot(unit3(f3_sub(rC, rCA)), f3_sub(x.c, f3_cross(rC, x.g)));
-                x = sum6_add(all, after);
-                gphi = f3_dot(unit3(f3_sub(rCA, rN)), f3_sub(x.c, f3_cross(rCA, x.g)));
-                if (j > 0) {
-                    x = sum6_add(own, after);
-                    gomg = f3_dot(unit3(f3_sub(rN, rCprev)), f3_sub(x.c, f3_cross(rN, x.g)));
+        block_suffix_sum6<NT>(tsum, s6, after, total);
+        if (threadIdx.x == NT - 32 && t > 0) publish_suffix_agg(ws, slot0 + t, total);
+        if (threadIdx.x < 32) {
+            const Sum6 later = gather_suffix(ws, slot0, t, T);
+            if (threadIdx.x == 0) {
+                s_later[0] = later.c.x; s_later[1] = later.c.y; s_later[2] = later.c.z;
+                s_later[3] = later.g.x; s_later[4] = later.g.y; s_later[5] = later.g.z;
+                // after the last wait of this tile (the chain's first tile of a
+                // fused step still waits for the chain's other tiles: it asks later)
+                s_next = (RES && t == 0) ? 0 : request_tile(counter);
+            }
+        }
+        __syncthreads();
+        int requested = s_next;
+        Sum6 A;
+        A.c = f3_add(after.c, make_float3(s_later[0], s_later[1], s_later[2]));
+        A.g = f3_add(after.g, make_float3(s_later[3], s_later[4], s_later[5]));
+
+        // 4. phi, psi, omega, residues last to first
+        float gphi[K], gpsi[K], gomg[K];
+#pragma unroll
+        for (int k = K - 1; k >= 0; --k) {
+            const int j = j0 + k;
+            gphi[k] = gpsi[k] = gomg[k] = 0.f;
+            if (j >= s1) continue;
+            if (in_range[k]) {
+                const int a = a0[k];
+                float3 rN, rCA, rC;
+                Sum6 nsum, co;
+                if constexpr (KEEP) {
+                    rN = rkeep[k][0];
+                    rCA = rkeep[k][1];
+                    rC = rkeep[k][2];
+                    nsum = nkeep[k];
+                    co = cokeep[k];
+                } else {
+                    rN = Rp(a);
+                    rCA = Rp(a + 1);
+                    rC = Rp(a + 2);
+                    const float3 rO = Rp(a + 3);
+                    nsum = sum6_zero();
+                    co = sum6_zero();
+                    add(nsum, rN, G(a, rN, nullptr));
+                    add(co, rC, G(a + 2, rC, nullptr));
+                    add(co, rO, G(a + 3, rO, nullptr));
+                }
+                Sum6 x = sum6_add(co, A);
+                gpsi[k] = f3_dot(unit3(f3_sub(rC, rCA)), f3_sub(x.c, f3_cross(rC, x.g)));
+                Sum6 rest;  // every atom of the residue but N, and everything after it
+                rest.c = f3_sub(own[k].c, nsum.c);
+                rest.g = f3_sub(own[k].g, nsum.g);
+                x = sum6_add(rest, A);
+                gphi[k] = f3_dot(unit3(f3_sub(rCA, rN)), f3_sub(x.c, f3_cross(rCA, x.g)));
+                if (j > 0) {  // C of the previous residue
+                    const int ap = (k > 0 ? a0[k - 1] : aprev) + 2;
+                    const float3 rCp = (staged && ap >= pc) ? Rp(ap) : make_float3(__ldg(r_in + 3 * (size_t)ap),
+                                                                                    __ldg(r_in + 3 * (size_t)ap + 1),
+                                                                                    __ldg(r_in + 3 * (size_t)ap + 2));
+                    x = sum6_add(own[k], A);
+                    gomg[k] = f3_dot(unit3(f3_sub(rN, rCp)), f3_sub(x.c, f3_cross(rN, x.g)));
                 }
             }
-            ga[j] = gphi;
-            ga[Lmax + j] = gpsi;
-            ga[2 * Lmax + j] = gomg;
-#pragma unroll
-            for (int k = 0; k < kMaxGroups; ++k) ga[(3 + k) * Lmax + j] = gchi[k];
+            A = sum6_add(A, own[k]);
         }
-        if (t == T - 1) {
-            for (int i = min(Lmax, T * NT) + threadIdx.x; i < Lmax; i += NT)
+        if (j0 < s1) {
+            store_k<K>(ga + j0, gphi);
+            store_k<K>(ga + Lmax + j0, gpsi);
+            store_k<K>(ga + 2 * Lmax + j0, gomg);
+        }
+        if (t == T - 1) {  // rows past the chain's last residue
+            for (int i = L + threadIdx.x; i < Lmax; i += NT)
 #pragma unroll
                 for (int r = 0; r < 7; ++r) ga[r * Lmax + i] = 0.f;
         }
@@ -592,9 +840,9 @@ __global__ void __launch_bounds__(NT, fa_bwd_min_blocks<NT>()) fa_bwd_coords_ker
                         if (tp > 0) wait_flag(ws.tdone + slot0 + tp);
                         sum += (double)__ldcg(ws.tres + slot0 + tp);
                     }
-                    const int n = lg.num_atoms[b] < Amax ? lg.num_atoms[b] : Amax;
+                    const int na = lg.num_atoms[b] < Amax ? lg.num_atoms[b] : Amax;
                     float lr, scale;
-                    lrmsd_from_sum(sum, n, lr, scale);
+                    lrmsd_from_sum(sum, na, lr, scale);
                     lg.lrmsd_out[b] = lr;
                     s_scale = scale;
                 }
@@ -638,7 +886,7 @@ __global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ an
             grad_angles[i] = 0.f;
         return;
     }
-    copy_table(s_tab, tab);
+    load_table(s_tab, tab);
     const int ntiles = ws.hdr[kHdrTiles];
     int* counter = ws.bflag + ws.slots;
     int v = take_tile(counter, &s_v);
@@ -646,19 +894,25 @@ __global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ an
         const int2 ct = ws.tiles[v];
         const int b = ct.x;
         const int L = clamp_length(lengths, b, Lmax);
-        const int T = L > 0 ? (L + NT - 1) / NT : 1;
+        const int T = fa_num_tiles(L, NT);
         const int t = T - 1 - ct.y;  // last tile first
+        const int s0 = fa_tile_start(L, T, t), s1 = fa_tile_start(L, T, t + 1);
         const int slot0 = b * ws.tmax;
         const float* ang = angles + (size_t)b * 7 * Lmax;
         const uint8_t* sq = seq + (size_t)b * Lmax;
         const float* g_in = grad_coords + (size_t)b * Amax * 3;
         float* ga = grad_angles + (size_t)b * 7 * Lmax;
 
-        const int j = t * NT + threadIdx.x;
-        const bool valid = j < L;
+        const int j = s0 + threadIdx.x;
+        const bool valid = j < s1;
         const int type = residue_type(sq, j, valid);
         float sp = 0.f, cp = 1.f, ss = 0.f, cs = 1.f;
-        const Rigid A = residue_transform(s_tab, ang, Lmax, j, L, sp, cp, ss, cs);
+        // the forward's frames exactly: the same residue transform, re-orthonormalised
+        Rigid A = rigid_identity();
+        if (valid) {
+            A = residue_transform(s_tab, ang, Lmax, j, L, sp, cp, ss, cs);
+            rigid_reortho(A);
+        }
         Rigid E, Tot;
         int a0, ctot;
         block_scan_rigid_count<NT>(A, valid ? s_tab.n_atoms[type] : 0, s_rig, s_cnt, E, a0, Tot, ctot);
@@ -739,7 +993,7 @@ __global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ an
         if (threadIdx.x == NT - 32) publish_suffix_agg(ws, slot0 + t, total);
         after = sum6_add(after, gather_suffix(ws, slot0, t, T));  // every warp gathers it
         const int requested = request_tile(counter);  // after the last wait of this tile
-        if (j < Lmax) {
+        if (valid) {
             float gphi = 0.f, gpsi = 0.f, gomg = 0.f;
             if (in_range) {
                 Sum6 x = sum6_add(csum, after);
@@ -757,8 +1011,8 @@ __global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ an
 #pragma unroll
             for (int k = 0; k < kMaxGroups; ++k) ga[(3 + k) * Lmax + j] = gchi[k];
         }
-        if (t == T - 1) {
-            for (int i = min(Lmax, T * NT) + threadIdx.x; i < Lmax; i += NT)
+        if (t == T - 1) {  // rows past the chain's last residue
+            for (int i = L + threadIdx.x; i < Lmax; i += NT)
 #pragma unroll
                 for (int r = 0; r < 7; ++r) ga[r * Lmax + i] = 0.f;
         }
@@ -958,31 +1212,31 @@ cudaError_t smem_attr_once(K kernel, int bytes, bool* done_per_device) {
     return e;
 }
 
-template <int NT, bool LM = false>
+template <int NT, int K, bool LM>
 cudaError_t fa_fwd_t(const float* angles, const uint8_t* seq, const int32_t* lengths, int Lmax,
                      int Amax, float* coords, int32_t* num_atoms, const ChainWs& ws,
-                     cudaStream_t s, const float* target = nullptr) {
-    const size_t smem = fa_fwd_smem<NT>();
+                     cudaStream_t s, const float* target) {
+    const size_t smem = fa_smem<NT, K>();
     static bool done[64] = {false};
-    cudaError_t e = smem_attr_once(fa_fwd_kernel<NT, LM>, (int)smem, done);
+    cudaError_t e = smem_attr_once(fa_fwd_kernel<NT, K, LM>, (int)smem, done);
     if (e != cudaSuccess) return e;
-    const int grid = persistent_grid((const void*)fa_fwd_kernel<NT, LM>, NT, smem);
-    fa_fwd_kernel<NT, LM><<<grid, NT, smem, s>>>(angles, seq, lengths, Lmax, Amax, coords, num_atoms,
-                                                 ws, target, fa_table());
+    const int grid = persistent_grid((const void*)fa_fwd_kernel<NT, K, LM>, NT, smem);
+    fa_fwd_kernel<NT, K, LM><<<grid, NT, smem, s>>>(angles, seq, lengths, Lmax, Amax, coords, num_atoms,
+                                                    ws, target, fa_table());
     return cudaGetLastError();
 }
 
-template <int NT, bool LR, bool RES = false>
+template <int NT, int K, bool LR, bool RES>
 cudaError_t fa_bwd_coords_t(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
                             const float* coords, const float* grad_coords, float* grad_angles,
                             const ChainWs& ws, LrmsdGrad lg, cudaStream_t s) {
-    const size_t smem = (size_t)(4 + NT * kMaxAtoms * 3) * sizeof(float);
+    const size_t smem = fa_smem<NT, K>();
     static bool done[64] = {false};
-    cudaError_t e = smem_attr_once(fa_bwd_coords_kernel<NT, LR, RES>, (int)smem, done);
+    cudaError_t e = smem_attr_once(fa_bwd_coords_kernel<NT, K, LR, RES>, (int)smem, done);
     if (e != cudaSuccess) return e;
-    const int grid = persistent_grid((const void*)fa_bwd_coords_kernel<NT, LR, RES>, NT, smem);
-    fa_bwd_coords_kernel<NT, LR, RES><<<grid, NT, smem, s>>>(seq, lengths, B, Lmax, Amax, coords, grad_coords,
-                                                                grad_angles, ws, lg, fa_table());
+    const int grid = persistent_grid((const void*)fa_bwd_coords_kernel<NT, K, LR, RES>, NT, smem);
+    fa_bwd_coords_kernel<NT, K, LR, RES><<<grid, NT, smem, s>>>(seq, lengths, B, Lmax, Amax, coords, grad_coords,
+                                                                   grad_angles, ws, lg, fa_table());
     return cudaGetLastError();
 }
 
@@ -1002,10 +1256,46 @@ cudaError_t fa_bwd_t(const float* angles, const uint8_t* seq, const int32_t* len
 
 }  // namespace
 
-bool fullatom_cfg_supported(int threads) {
-    return threads == 64 || threads == 128 || threads == 192 || threads == 256 || threads == 384 ||
-           threads == 512;
+// Launch shapes (threads x residues per thread) of the full-atom kernels.
+#define TPL_FA_SHAPES(X) \
+    X(128, 1) X(256, 1) X(384, 1) X(128, 2) X(192, 2) X(64, 4) X(192, 4)
+
+bool fullatom_cfg_supported(int threads, int k) {
+#define TPL_FA_SUPPORTED(NT, K) \
+    if (threads == NT && k == K) return true;
+    TPL_FA_SHAPES(TPL_FA_SUPPORTED)
+#undef TPL_FA_SUPPORTED
+    return false;
 }
+
+#define TPL_FA_CASE_FWD(NT, K) case NT * 8 + K: e = fa_fwd_t<NT, K, LMV>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s, target); break;
+#define TPL_FA_CASE_BWD(NT, K) case NT * 8 + K: return fa_bwd_coords_t<NT, K, LRV, RESV>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, lg, s);
+
+namespace {
+
+template <bool LMV>
+cudaError_t fa_forward_shape(const float* angles, const uint8_t* seq, const int32_t* lengths, int Lmax, int Amax,
+                             float* coords, int32_t* num_atoms, const ChainWs& ws, LaunchCfg cfg, cudaStream_t s,
+                             const float* target) {
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (cfg.threads * 8 + cfg.res_per_thread) {
+        TPL_FA_SHAPES(TPL_FA_CASE_FWD)
+        default: return cudaErrorInvalidValue;
+    }
+    return e;
+}
+
+template <bool LRV, bool RESV>
+cudaError_t fa_backward_shape(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
+                              const float* coords, const float* grad_coords, float* grad_angles,
+                              const ChainWs& ws, LrmsdGrad lg, LaunchCfg cfg, cudaStream_t s) {
+    switch (cfg.threads * 8 + cfg.res_per_thread) {
+        TPL_FA_SHAPES(TPL_FA_CASE_BWD)
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
 
 cudaError_t launch_fullatom_forward(const float* angles, const uint8_t* seq,
                                     const int32_t* lengths, int B, int Lmax, int Amax,
@@ -1014,17 +1304,9 @@ cudaError_t launch_fullatom_forward(const float* angles, const uint8_t* seq,
     if (B == 0) return cudaSuccess;
     ChainWs ws;
     chain_ws_layout(workspace, B, Lmax, &ws, true);
-    cudaError_t e = launch_schedule(lengths, B, Lmax, cfg.threads, sched_mode, 1, ws, s);
+    cudaError_t e = launch_schedule(lengths, B, Lmax, cfg.threads * cfg.res_per_thread, sched_mode, 1, ws, s, true);
     if (e != cudaSuccess) return e;
-    switch (cfg.threads) {
-        case 64: return fa_fwd_t<64>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s);
-        case 128: return fa_fwd_t<128>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s);
-        case 192: return fa_fwd_t<192>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s);
-        case 256: return fa_fwd_t<256>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s);
-        case 384: return fa_fwd_t<384>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s);
-        case 512: return fa_fwd_t<512>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s);
-        default: return cudaErrorInvalidValue;
-    }
+    return fa_forward_shape<false>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, cfg, s, nullptr);
 }
 
 cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
@@ -1037,24 +1319,15 @@ cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
     chain_ws_layout(workspace, B, Lmax, &ws, true);
     cudaError_t e = reset_backward_flags(ws, s);
     if (e != cudaSuccess) return e;
-    if (from_coords) {
-        switch (cfg.threads) {
-            case 64: return fa_bwd_coords_t<64, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, LrmsdGrad{}, s);
-            case 128: return fa_bwd_coords_t<128, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, LrmsdGrad{}, s);
-            case 192: return fa_bwd_coords_t<192, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, LrmsdGrad{}, s);
-            case 256: return fa_bwd_coords_t<256, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, LrmsdGrad{}, s);
-            case 384: return fa_bwd_coords_t<384, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, LrmsdGrad{}, s);
-            case 512: return fa_bwd_coords_t<512, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, LrmsdGrad{}, s);
-            default: return cudaErrorInvalidValue;
-        }
-    }
+    if (from_coords)
+        return fa_backward_shape<false, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws,
+                                               LrmsdGrad{}, cfg, s);
+    // frames rebuilt from the angles: one residue per thread
+    if (cfg.res_per_thread != 1) return cudaErrorInvalidValue;
     switch (cfg.threads) {
-        case 64: return fa_bwd_t<64>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);
         case 128: return fa_bwd_t<128>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);
-        case 192: return fa_bwd_t<192>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);
         case 256: return fa_bwd_t<256>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);
         case 384: return fa_bwd_t<384>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);
-        case 512: return fa_bwd_t<512>(angles, seq, lengths, B, Lmax, Amax, grad_coords, grad_angles, ws, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1079,15 +1352,7 @@ cudaError_t launch_fullatom_backward_lrmsd(const uint8_t* seq, const int32_t* le
     cudaError_t e = reset_backward_flags(ws, s);
     if (e != cudaSuccess) return e;
     const LrmsdGrad lg{target, lrmsd_state, grad_lrmsd};
-    switch (cfg.threads) {
-        case 64: return fa_bwd_coords_t<64, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
-        case 128: return fa_bwd_coords_t<128, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
-        case 192: return fa_bwd_coords_t<192, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
-        case 256: return fa_bwd_coords_t<256, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
-        case 384: return fa_bwd_coords_t<384, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
-        case 512: return fa_bwd_coords_t<512, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
-        default: return cudaErrorInvalidValue;
-    }
+    return fa_backward_shape<true, false>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, cfg, s);
 }
 
 cudaError_t launch_fullatom_lrmsd_forward(const float* angles, const uint8_t* seq, const int32_t* lengths,
@@ -1097,19 +1362,12 @@ cudaError_t launch_fullatom_lrmsd_forward(const float* angles, const uint8_t* se
     if (B == 0) return cudaSuccess;
     ChainWs ws;
     chain_ws_layout(workspace, B, Lmax, &ws, true, true);
-    cudaError_t e = launch_schedule(lengths, B, Lmax, cfg.threads, sched_mode, 1, ws, s);
+    const int tile = cfg.threads * cfg.res_per_thread;
+    cudaError_t e = launch_schedule(lengths, B, Lmax, tile, sched_mode, 1, ws, s, true);
     if (e != cudaSuccess) return e;
-    switch (cfg.threads) {
-        case 64: e = fa_fwd_t<64, true>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s, target); break;
-        case 128: e = fa_fwd_t<128, true>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s, target); break;
-        case 192: e = fa_fwd_t<192, true>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s, target); break;
-        case 256: e = fa_fwd_t<256, true>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s, target); break;
-        case 384: e = fa_fwd_t<384, true>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s, target); break;
-        case 512: e = fa_fwd_t<512, true>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s, target); break;
-        default: return cudaErrorInvalidValue;
-    }
+    e = fa_forward_shape<true>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, cfg, s, target);
     if (e != cudaSuccess) return e;
-    return launch_lrmsd_solve_tiles(coords, target, num_atoms, B, Amax, ws.tmom, ws.tmax, lengths, cfg.threads,
+    return launch_lrmsd_solve_tiles(coords, target, num_atoms, B, Amax, ws.tmom, ws.tmax, lengths, tile,
                                     Lmax, ws.lstate, s);
 }
 
@@ -1123,15 +1381,7 @@ cudaError_t launch_fullatom_lrmsd_backward(const uint8_t* seq, const int32_t* le
     cudaError_t e = reset_backward_flags(ws, s);
     if (e != cudaSuccess) return e;
     LrmsdGrad lg{target, ws.lstate, grad_lrmsd, lrmsd, num_atoms};
-    switch (cfg.threads) {
-        case 64: return fa_bwd_coords_t<64, true, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
-        case 128: return fa_bwd_coords_t<128, true, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
-        case 192: return fa_bwd_coords_t<192, true, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
-        case 256: return fa_bwd_coords_t<256, true, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
-        case 384: return fa_bwd_coords_t<384, true, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
-        case 512: return fa_bwd_coords_t<512, true, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, s);
-        default: return cudaErrorInvalidValue;
-    }
+    return fa_backward_shape<true, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, cfg, s);
 }
 
 cudaError_t launch_fullatom_backward_ref64(const double* angles, const uint8_t* seq,

@@ -9,8 +9,8 @@
 namespace tpl {
 
 struct LaunchCfg {
-    int threads;        // CTA size (= residues per tile of the full-atom kernels)
-    int res_per_thread; // backbone only (tile = threads * res_per_thread)
+    int threads;        // CTA size
+    int res_per_thread; // consecutive residues per thread (tile = threads * res_per_thread)
 };
 
 // Bytes of the chain workspace (tile list, look-back flags and aggregates,
@@ -45,7 +45,7 @@ cudaError_t launch_backbone_backward_lrmsd(const float* angles, const int32_t* l
                                            cudaStream_t s);
 
 // K3 / K4: full-atom FP32 scan kernels.
-bool fullatom_cfg_supported(int threads);
+bool fullatom_cfg_supported(int threads, int res_per_thread);
 cudaError_t launch_fullatom_forward(const float* angles, const uint8_t* seq,
                                     const int32_t* lengths, int B, int Lmax, int Amax,
                                     float* coords, int32_t* num_atoms, int sched_mode,

@@ -28,6 +28,7 @@
 #include <mutex>
 
 #include "kernels.h"
+#include "sched.cuh"
 #include "tpl_common.cuh"
 
 namespace tpl {
@@ -471,7 +472,7 @@ __global__ void __launch_bounds__(32) lrmsd_solve_tiles_kernel(
     const int p = active ? (gid >> 2) : P - 1;
     const int n = pair_atoms(num_atoms, p, Nmax);
     const int L = min(max(lengths[p], 0), Lmax);
-    const int nch = L > 0 ? (L + tile - 1) / tile : 1;
+    const int nch = fa_num_tiles(L, tile);
     float x0[3], y0[3];
     first_atoms(target + (size_t)p * Nmax * 3, input + (size_t)p * Nmax * 3, n, x0, y0);
     float S[kSlot];

@@ -68,9 +68,23 @@ struct ChainWs {
 
 __host__ __device__ inline size_t ws_align(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Tiles per chain the workspace provides: enough for the smallest tile, also
+// when a full-atom chain is split into balanced tiles (fa_num_tiles).
 __host__ __device__ inline int ws_tmax(int Lmax) {
-    int t = (Lmax + kMinTile - 1) / kMinTile;
+    int t = (Lmax + kMinTile - 5) / (kMinTile - 4);
     return t < 1 ? 1 : t;
+}
+
+// Full-atom tiles are balanced: a chain of L residues becomes T = ceil(L /
+// (tile - 4)) tiles of nearly equal length whose starts are multiples of 4
+// (so a thread's residues start 16-byte aligned), each at most tile - 1
+// residues.  Tile t covers residues [fa_tile_start(L, T, t), fa_tile_start(L,
+// T, t + 1)).  An empty chain has one (empty) tile.
+__host__ __device__ inline int fa_num_tiles(int L, int tile) {
+    return L > 0 ? (L + tile - 5) / (tile - 4) : 1;
+}
+__host__ __device__ inline int fa_tile_start(int L, int T, int t) {
+    return t >= T ? L : (int)(((long long)t * L / T) & ~3LL);
 }
 
 // Offsets of the regions; `base` may be null to only size the workspace.
@@ -361,8 +375,9 @@ __device__ __forceinline__ int next_tile(int requested, int* s_v) {
 // with the chains of at most one tile packed several per tile (granule =
 // residues per thread, the unit a chain's slots are padded to).
 enum SchedMode { kSchedBatch = 0, kSchedLongest = 1, kSchedPacked = 2 };
+// balanced: full-atom tiles (fa_num_tiles per chain) instead of ceil(L / tile).
 cudaError_t launch_schedule(const int32_t* lengths, int B, int Lmax, int tile, int mode, int granule,
-                            const ChainWs& ws, cudaStream_t s);
+                            const ChainWs& ws, cudaStream_t s, bool balanced = false);
 cudaError_t reset_backward_flags(const ChainWs& ws, cudaStream_t s);
 
 }  // namespace tpl

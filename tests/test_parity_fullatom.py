@@ -17,6 +17,9 @@ COORD_TOL = 2e-3
 GRAD_TOL = 1e-4
 LRMSD_TOL = 1e-5
 LENGTHS = np.array([0, 1, 2, 31, 64, 255, 256, 257, 350, 513, 700], np.int32)
+# launch shapes (threads, residues per thread) of the full-atom kernels
+SHAPES = [(128, 1), (256, 1), (384, 1), (128, 2), (192, 2), (64, 4), (192, 4)]
+RECOMPUTE_SHAPES = [(128, 1), (256, 1), (384, 1)]  # frames rebuilt from the angles: one residue per thread
 
 
 def _inputs(lengths, seed, omega_noise=0.0):
@@ -54,11 +57,11 @@ def reference():
     return a, seq, g.astype(np.float32), Amax, c64, na64, g64
 
 
-@pytest.mark.parametrize("from_coords", [False, True])
-@pytest.mark.parametrize("threads", [256, 64, 128, 192, 384, 512])
-def test_fp32_scan_matches_oracle(reference, threads, from_coords):
+@pytest.mark.parametrize("shape,from_coords", [(s, True) for s in SHAPES] + [(s, False) for s in RECOMPUTE_SHAPES])
+def test_fp32_scan_matches_oracle(reference, shape, from_coords):
     a, seq, g, Amax, c64, na64, g64 = reference
-    c32, na32, ga32 = _run_fp32(a, seq, LENGTHS, g, Amax, {"threads": threads}, from_coords)
+    opts = {"threads": shape[0], "res_per_thread": shape[1]}
+    c32, na32, ga32 = _run_fp32(a, seq, LENGTHS, g, Amax, opts, from_coords)
     assert np.array_equal(na32, na64)  # atom counts bit-exact
     assert np.abs(c32 - c64).max() <= COORD_TOL
     assert rel_err(ga32, g64) <= GRAD_TOL
@@ -74,12 +77,13 @@ def test_fp32_scan_matches_oracle(reference, threads, from_coords):
             assert ga32[b, 2, 0] == 0
 
 
-@pytest.mark.parametrize("from_coords", [False, True])
-def test_schedule_independent_and_deterministic(reference, from_coords):
+@pytest.mark.parametrize("shape,from_coords", [((192, 2), True), ((64, 4), True), ((256, 1), False)])
+def test_schedule_independent_and_deterministic(reference, shape, from_coords):
     a, seq, g, Amax, *_ = reference
-    r1 = _run_fp32(a, seq, LENGTHS, g, Amax, {"schedule": tpl.SCHED_LONGEST_FIRST}, from_coords)
-    r2 = _run_fp32(a, seq, LENGTHS, g, Amax, {"schedule": tpl.SCHED_BATCH_ORDER}, from_coords)
-    r3 = _run_fp32(a, seq, LENGTHS, g, Amax, {"schedule": tpl.SCHED_BATCH_ORDER}, from_coords)
+    o = {"threads": shape[0], "res_per_thread": shape[1]}
+    r1 = _run_fp32(a, seq, LENGTHS, g, Amax, dict(o, schedule=tpl.SCHED_LONGEST_FIRST), from_coords)
+    r2 = _run_fp32(a, seq, LENGTHS, g, Amax, dict(o, schedule=tpl.SCHED_BATCH_ORDER), from_coords)
+    r3 = _run_fp32(a, seq, LENGTHS, g, Amax, dict(o, schedule=tpl.SCHED_BATCH_ORDER), from_coords)
     for x, y, z in zip(r1, r2, r3):
         assert np.array_equal(x, y) and np.array_equal(y, z)
 
@@ -107,7 +111,7 @@ def test_backbone_atoms_equal_backbone_kernel():
     d = require_gpu()
     lengths = np.array([300, 120], np.int32)
     a, seq, g, Amax = _inputs(lengths, 4)
-    c32, na32, _ = _run_fp32(a, seq, lengths, g, Amax)
+    c32, na32, _ = _run_fp32(a, seq, lengths, g, Amax, from_coords=True)
     bb = tpl.backbone(dev(np.ascontiguousarray(a[:, :3]), d), dev(lengths, d))
     bb = host(bb)
     for b, L in enumerate(lengths):
@@ -124,12 +128,45 @@ def test_bad_residue_and_too_many_atoms_set_status():
     a, seq, g, Amax = _inputs(lengths, 6)
     seq = seq.copy()
     seq[0, 3] = 31
-    _run_fp32(a, seq, lengths, g, Amax)
+    _run_fp32(a, seq, lengths, g, Amax, from_coords=True)
     assert tpl.tpl_get_status() & tpl.STATUS_BAD_RESIDUE
     seq[0, 3] = 1
-    c32, na32, _ = _run_fp32(a, seq, lengths, g, 12)  # Amax far too small
+    c32, na32, ga32 = _run_fp32(a, seq, lengths, g[:, :12], 12, from_coords=True)  # Amax far too small
     assert tpl.tpl_get_status() & tpl.STATUS_TOO_MANY_ATOMS
-    assert np.all(np.isfinite(c32))
+    assert np.all(np.isfinite(c32)) and np.all(np.isfinite(ga32))
+
+
+def test_tiles_whose_atoms_overflow_the_stage_match_the_oracle():
+    """Chains of TRP (14 atoms per residue, more than the stage holds per
+    residue slot on average) and mixes around it: those tiles write (and the
+    backward reads) their atoms without the stage; all tiles match the oracle."""
+    rng = np.random.default_rng(71)
+    lengths = np.array([700, 383, 200, 129], np.int32)
+    a, seq, g, Amax = _inputs(lengths, 72)
+    seq = seq.copy()
+    seq[0, :] = 17                      # TRP only: every tile overflows
+    seq[1, :200] = 17                   # half TRP
+    seq[2, ::2] = 17                    # every other residue
+    Amax = workloads.pad_to(oracle.max_atoms(seq, lengths))
+    g = workloads.upstream_grad((len(lengths), Amax, 3), rng)
+    c64, na64 = oracle.fullatom_forward(a, seq, lengths, Amax)
+    g = (g * (np.arange(Amax)[None, :] < na64[:, None])[:, :, None]).astype(np.float32)
+    g64 = oracle.fullatom_backward(a, seq, lengths, g)
+    for shape in [(192, 2), (64, 4), (256, 1)]:
+        opts = {"threads": shape[0], "res_per_thread": shape[1]}
+        c32, na32, ga32 = _run_fp32(a, seq, lengths, g, Amax, opts, from_coords=True)
+        assert np.array_equal(na32, na64)
+        assert np.abs(c32 - c64).max() <= COORD_TOL
+        assert rel_err(ga32, g64) <= GRAD_TOL
+
+
+def test_recompute_needs_one_residue_per_thread():
+    d = require_gpu()
+    lengths = np.array([40], np.int32)
+    a, seq, g, Amax = _inputs(lengths, 8)
+    with pytest.raises(tpl.TplError) as err:
+        _run_fp32(a, seq, lengths, g, Amax, {"threads": 192, "res_per_thread": 2}, from_coords=False)
+    assert err.value.code == 1  # TPL_ERR_INVALID_ARG
 
 
 def test_autotuner_picks_a_valid_shape_and_its_results_match(reference):
@@ -142,7 +179,7 @@ def test_autotuner_picks_a_valid_shape_and_its_results_match(reference):
     ga = torch.empty_like(A)
     ws = torch.empty(tpl.tpl_fullatom_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
     best, ms = tpl.tpl_fullatom_autotune(A, S, Ln, coords, na, G, ga, ws, bwd_mode=tpl.BWD_FROM_COORDS)
-    assert ms > 0 and best.threads in (64, 128, 192, 256, 384, 512)
+    assert ms > 0 and (best.threads, best.res_per_thread) in SHAPES
     assert best.schedule in (tpl.SCHED_BATCH_ORDER, tpl.SCHED_LONGEST_FIRST)
     c32, n32, ga32 = _run_fp32(a, seq, LENGTHS, g, Amax, best, from_coords=True)
     assert np.array_equal(n32, na64)
@@ -171,7 +208,7 @@ def test_lrmsd_step_autotuner_picks_a_valid_shape_and_its_step_matches_the_oracl
     w = dev(np.linspace(0.5, 2.0, B).astype(np.float32), d)
     ga = torch.empty_like(A)
     best, ms = tpl.tpl_fullatom_lrmsd_autotune(A, S, Ln, coords, na, tgt, w, lr, lr_ws, ga, fa_ws)
-    assert ms > 0 and best.threads in (64, 128, 192, 256, 384, 512)
+    assert ms > 0 and (best.threads, best.res_per_thread) in SHAPES
     assert best.schedule in (tpl.SCHED_BATCH_ORDER, tpl.SCHED_LONGEST_FIRST)
     assert best.bwd_mode == tpl.BWD_FROM_COORDS
     ga.fill_(float("nan"))
@@ -186,8 +223,8 @@ def test_lrmsd_step_autotuner_picks_a_valid_shape_and_its_step_matches_the_oracl
     assert rel_err(host(ga), oracle.fullatom_backward(a, seq, lengths, g64)) <= GRAD_TOL
 
 
-@pytest.mark.parametrize("threads", [256, 64])
-def test_fused_lrmsd_backward_equals_the_two_calls_and_the_oracle(threads):
+@pytest.mark.parametrize("shape", [(256, 1), (192, 2), (64, 4)])
+def test_fused_lrmsd_backward_equals_the_two_calls_and_the_oracle(shape):
     """tpl_fullatom_backward_lrmsd = tpl_lrmsd_backward + tpl_fullatom_backward
     (FROM_COORDS), against the same chain of oracle calls."""
     d = require_gpu()
@@ -198,7 +235,7 @@ def test_fused_lrmsd_backward_equals_the_two_calls_and_the_oracle(threads):
     Amax = workloads.pad_to(oracle.max_atoms(seq, lengths))
     B, _, Lmax = a.shape
     A, S, Ln = dev(a, d), dev(seq, d), dev(lengths, d)
-    opts = {"threads": threads}
+    opts = {"threads": shape[0], "res_per_thread": shape[1]}
     fa_ws = torch.empty(tpl.tpl_fullatom_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
     tgt = torch.zeros((B, Amax, 3), device=d)
     na = torch.zeros((B,), dtype=torch.int32, device=d)
@@ -226,8 +263,8 @@ def test_fused_lrmsd_backward_equals_the_two_calls_and_the_oracle(threads):
     assert rel_err(f, ga64) <= GRAD_TOL
 
 
-@pytest.mark.parametrize("threads", [384, 256, 64])
-def test_fused_training_step_matches_the_separate_calls_and_the_oracle(threads):
+@pytest.mark.parametrize("shape", [(384, 1), (192, 2), (64, 4)])
+def test_fused_training_step_matches_the_separate_calls_and_the_oracle(shape):
     """tpl_fullatom_lrmsd_forward / _backward (moments in the forward's tiles,
     residuals and the 1 / (N LRMSD) factor in the backward) against
     tpl_fullatom_forward + tpl_lrmsd_forward + tpl_fullatom_backward_lrmsd and
@@ -240,7 +277,7 @@ def test_fused_training_step_matches_the_separate_calls_and_the_oracle(threads):
     Amax = workloads.pad_to(oracle.max_atoms(seq, lengths))
     B, _, Lmax = a.shape
     A, S, Ln = dev(a, d), dev(seq, d), dev(lengths, d)
-    opts = {"threads": threads}
+    opts = {"threads": shape[0], "res_per_thread": shape[1]}
     fa_ws = torch.empty(tpl.tpl_fullatom_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
     tgt = torch.zeros((B, Amax, 3), device=d)
     na = torch.zeros((B,), dtype=torch.int32, device=d)
