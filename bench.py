@@ -56,22 +56,8 @@ DEFAULT_BATCH = {"training_step": 256, "backbone_uneven": 4096, "lrmsd_batch": 1
 # An entry is removed when one of its kernels changes after the capture.
 TRAFFIC = {
     # (per-unit DRAM bytes, unit, profile, launch shape of the capture or None if the
-    # kernels take none); cold-cache captures of one launch
-    # lrmsd_pair_kernel
-    ("training_step", "lrmsd_forward"): (24.0843, "atom", "profiles/lrmsd_kernels_training_step_256x700.md", None),
-    # bb_fwd_kernel<256, 4> (the schedule kernel's few bytes not counted)
-    ("backbone_uneven", "backbone_forward"): (80.9907, "residue", "profiles/backbone_kernels_backbone_uneven_4096.md",
-                                              "threads=256,res_per_thread=4"),
-    # bb_bwd_kernel<256, 4, 1, 1>
-    ("backbone_uneven", "lrmsd_backbone_backward"): (81.9533, "residue",
-                                                     "profiles/backbone_kernels_backbone_uneven_4096.md",
-                                                     "threads=256,res_per_thread=4"),
-    # moments + solve + residual + finalize
-    ("backbone_uneven", "lrmsd_forward"): (50.4512, "atom", "profiles/lrmsd_kernels_backbone_uneven_4096.md", None),
-    # moments + solve + residual + finalize, 4096-pair capture scaled by atoms
-    ("lrmsd_batch", "lrmsd_forward"): (49.1724, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md", None),
-    # grad, 4096-pair capture scaled by atoms
-    ("lrmsd_batch", "lrmsd_backward"): (42.8211, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md", None),
+    # kernels take none); cold-cache captures of one launch.  Filled from the
+    # captures of the current kernels (profiles/).
 }
 
 
@@ -325,9 +311,7 @@ def run_reference(args):
 # ----------------------------------------------------------------------------- GPU workloads
 def lrmsd_forward_kernels(tpl, P):
     """Kernels of tpl_lrmsd_forward for P pairs on this device (the library's plan)."""
-    if tpl.tpl_lrmsd_forward_launches(P) == 1:
-        return ["lrmsd_pair_kernel"]
-    return ["lrmsd_moments_kernel", "lrmsd_solve_kernel", "lrmsd_residual_kernel", "lrmsd_finalize_kernel"]
+    return ["lrmsd_pair_kernel"] * tpl.tpl_lrmsd_forward_launches(P)
 
 
 class Step:

@@ -262,9 +262,9 @@ tpl_status tpl_lrmsd_forward(const float* input, const float* target, const int3
                              size_t workspace_bytes, tpl_stream stream);
 
 /* Kernels tpl_lrmsd_forward launches for P pairs on the current device: 1
- * when the batch fits the GPU in one wave of one CTA per pair (moments,
- * eigen-solve and residuals in one kernel), else 4 (moments, eigen-solve,
- * residuals, LRMSD); 0 for P <= 0.  Needs no workspace; launches nothing. */
+ * for P > 0 (one CTA per pair does the moments, the eigen-solve and the
+ * residuals; a wide CTA when the batch fits the GPU in one wave, a compact
+ * one otherwise), 0 for P <= 0.  Needs no workspace; launches nothing. */
 int tpl_lrmsd_forward_launches(int P);
 
 /* Section 4: grad_input_i = grad_lrmsd[p] (y'_i - U x'_i) / (N LRMSD); 0 when
@@ -280,7 +280,7 @@ tpl_status tpl_lrmsd_backward(const float* grad_lrmsd, const float* input, const
  * memory is all owned by another runtime's allocator, or an interface without
  * a scratch argument).  The paper has no counterpart; this is an interface
  * convenience.  The scratch is a fixed array inside the library: every GPU
- * that loads the library holds it (about 3.1 MB) until the process exits.
+ * that loads the library holds it (256 KB) until the process exits.
  *   Limits: P <= 4096 pairs, Nmax <= 8192 atoms; larger sizes return
  *   TPL_ERR_BAD_SHAPE and launch nothing.  Inputs and outputs as in
  *   tpl_lrmsd_forward; no allocation, no workspace.

@@ -1,27 +1,20 @@
 // LRMSD of the paper (Section 4) on sm_103a.
 //
-// The atoms of a pair are cut into chunks of 256 (eight atoms per lane of one
-// warp).  The streaming kernels give each pair `wpp` warps (chosen from the
-// batch size so that the GPU is full: one warp per pair for large batches,
-// up to one per chunk for a few long pairs); warp r of a pair takes chunks
-// r, r + wpp, ... and stores one partial, so no warp waits on another.
-//
-// Forward, four launches:
-//  K5a lrmsd_moments: per warp, the moments shifted by the pair's first atom
-//      in FP32 -- sum dx, sum dy, sum dx dy^T, sum |dx|^2, sum |dy|^2 (x =
-//      target, y = input, as in the paper's R = sum x y^T).
-//  K5b lrmsd_solve: four lanes per pair sum its partials, centre R, estimate
-//      the largest eigenpair of the 4x4 matrix T(R) in FP32 (Newton's method
-//      on the characteristic polynomial, as in the quaternion-characteristic-
-//      polynomial approach of Theobald, Acta Cryst. A61 (2005) 478, then an
-//      adjugate column) and refine it in double-float FP32 arithmetic, about
-//      48 bits (Rayleigh quotient of T, adjugate of T - lambda I), then U(q).
-//  K5c lrmsd_residual: LRMSD^2 = (sum |x'|^2 + |y'|^2 - 2 lambda)/N equals
-//      sum |y'_i - U x'_i|^2 / N at the optimum; the residual form has no
-//      cancellation, so it is summed in FP32 per chunk and in FP64 over the
-//      warp's chunks.
-//  K5d lrmsd_finalize: four lanes per pair sum the warps' partials in FP64:
-//      LRMSD and the gradient scale 1 / (N LRMSD).
+// Forward, one launch: one CTA per pair (K5 lrmsd_pair_kernel)
+//  - moments: the CTA streams both clouds, the moments shifted by the pair's
+//    first atom in FP32 -- sum dx, sum dy, sum dx dy^T, sum |dx|^2, sum
+//    |dy|^2 (x = target, y = input, as in the paper's R = sum x y^T);
+//  - eigen-solve: one quad of warp 0 centres R, estimates the largest
+//    eigenpair of the 4x4 matrix T(R) in FP32 (Newton's method on the
+//    characteristic polynomial, as in the quaternion-characteristic-polynomial
+//    approach of Theobald, Acta Cryst. A61 (2005) 478, then an adjugate
+//    column) and refines it in double-float FP32 arithmetic, about 48 bits
+//    (Rayleigh quotient of T, adjugate of T - lambda I), then U(q);
+//  - residuals: LRMSD^2 = (sum |x'|^2 + |y'|^2 - 2 lambda)/N equals sum |y'_i -
+//    U x'_i|^2 / N at the optimum; the residual form has no cancellation, so
+//    it is summed in FP32 per thread and in FP64 over the warps.  The clouds
+//    were just read by the moments, so this pass reads them from L2;
+//  - LRMSD and the gradient scale 1 / (N LRMSD).
 // Backward:
 //  K6 lrmsd_grad: grad_y_i = w (y'_i - U x'_i) / (N LRMSD).
 // Every sum runs in a fixed order, so the results are the same from run to run.
@@ -35,33 +28,28 @@ namespace tpl {
 
 namespace {
 
-constexpr int kWNT = 128;    // threads per CTA: four independent warp workers
-constexpr int kWarps = kWNT / 32;
-constexpr int kWC = 256;     // atoms per chunk: one warp, two groups of 4 atoms per lane
-constexpr int kMaxWpp = 8;   // most warps per pair in the streaming kernels
 constexpr int kMom = 17;     // sum dx (3), sum dy (3), sum dx dy^T (9), sum |dx|^2, sum |dy|^2
 constexpr int kSlot = 20;    // floats per chunk partial (5 float4)
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kRqPasses = 4;          // most Rayleigh-quotient passes of the eigen-solve
 constexpr float kNearDouble = 1e-4f;  // |adjugate column|^2 below which another pass runs
+constexpr int kPowerSteps = 24;       // power iterations when the adjugate passes fail (double eigenvalue)
+constexpr float kEigenResidual2 = 1e-18f;  // |T q - lambda q|^2 above which they run
+constexpr float kSuspectAdj = 5e-2f;       // FP32 adjugate diagonal below which the result is checked
 
+// Workspace: the per-pair state the backward reads (U row-major, centroid of
+// the target, centroid of the input, 1 / (N LRMSD)).
 struct WsLayout {
-    size_t part1, part2, state, total;
-    int parts;  // partial slots per pair: the most warps a pair can get
+    size_t state, total;
 };
 
 __host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 __host__ __device__ constexpr WsLayout ws_layout(int P, int Nmax) {
+    (void)Nmax;
     WsLayout w{};
-    w.parts = (Nmax + kWC - 1) / kWC;
-    if (w.parts > kMaxWpp) w.parts = kMaxWpp;
-    if (w.parts < 1) w.parts = 1;
-    size_t o = 0;
-    w.part1 = o; o = align256(o + (size_t)P * w.parts * kSlot * sizeof(float));
-    w.part2 = o; o = align256(o + (size_t)P * w.parts * sizeof(double));
-    w.state = o; o = align256(o + (size_t)P * 16 * sizeof(float));  // U(9) xc(3) yc(3) scale
-    w.total = o;
+    w.state = 0;
+    w.total = align256((size_t)(P > 0 ? P : 1) * 16 * sizeof(float));
     return w;
 }
 
@@ -77,10 +65,6 @@ __device__ __forceinline__ int pair_atoms(const int32_t* num_atoms, int p, int N
     return checked_atoms(num_atoms[p], Nmax);
 }
 
-__device__ __forceinline__ int num_chunks(int n) { return n <= 0 ? 1 : (n + kWC - 1) / kWC; }
-
-// Partials of a pair: one per warp that has a chunk.
-__device__ __forceinline__ int num_parts(int n, int wpp) { return min(wpp, num_chunks(n)); }
 
 
 // Four consecutive atoms (12 floats, 16-byte aligned) into xyz[4].
@@ -110,7 +94,7 @@ __device__ __forceinline__ T quad_sum(T v, int sub) {
 }
 
 // ---------------------------------------------------------------------------
-// Eigen-solve of T(R) (part of K5a)
+// Eigen-solve of T(R) (part of K5)
 // ---------------------------------------------------------------------------
 // Adjugate of a symmetric 4x4 (float): the same Laplace expansion in FP32,
 // used only for the starting eigenvector.
@@ -143,7 +127,7 @@ __device__ __forceinline__ float adjugate4f(float a00, float a01, float a02, flo
 // (e0s = E0 |R|^-1), then the column of adj(T - l I) with the largest
 // diagonal entry, scaled by it.  jb is that column.
 __device__ __forceinline__ void fp32_eigen_estimate(const float (&r)[9], float e0s, float& lam,
-                                                    float (&qf)[4], int& jb) {
+                                                    float (&qf)[4], int& jb, float& adj) {
     const float t00 = r[0] + r[4] + r[8], t01 = r[5] - r[7], t02 = r[6] - r[2], t03 = r[1] - r[3];
     const float t11 = r[0] - r[4] - r[8], t12 = r[1] + r[3], t13 = r[2] + r[6];
     const float t22 = -r[0] + r[4] - r[8], t23 = r[5] + r[7], t33 = -r[0] - r[4] + r[8];
@@ -153,13 +137,20 @@ __device__ __forceinline__ void fp32_eigen_estimate(const float (&r)[9], float e
     const float c0 = adjugate4f(t00, t01, t02, t03, t11, t12, t13, t22, t23, t33, m);
     const float c2 = -2.f, c1 = -8.f * detR;
     lam = fminf(2.f, 0.5f * e0s * (1.f + 1e-5f));
+    // From above the largest root, Newton's method on a polynomial with real
+    // roots only (T is symmetric) decreases monotonically to that root, which
+    // is positive (T has trace 0 and is not 0).  Near a double root the FP32
+    // polynomial is rounding noise and a step can jump anywhere; a step that
+    // would leave (0, lam) ends the iteration instead.
     for (int it = 0; it < 24; ++it) {
         const float l2 = lam * lam;
         const float pv = (l2 + c2) * l2 + c1 * lam + c0;
         const float dp = (4.f * l2 + 2.f * c2) * lam + c1;
         if (!(fabsf(dp) > 0.f)) break;
         const float step = __fdividef(pv, dp);
-        lam -= step;
+        const float next = lam - step;
+        if (!(next < lam && next > 0.f)) break;
+        lam = next;
         if (fabsf(step) <= 1e-6f * fabsf(lam)) break;
     }
     adjugate4f(t00 - lam, t01, t02, t03, t11 - lam, t12, t13, t22 - lam, t23, t33 - lam, m);
@@ -174,6 +165,7 @@ __device__ __forceinline__ void fp32_eigen_estimate(const float (&r)[9], float e
 #pragma unroll
             for (int i = 0; i < 4; ++i) qf[i] = m[4 * i + k];
         }
+    adj = fabsf(best);  // of order one for a well separated lambda_max; small near a double one
     if (fabsf(best) > 0.f) {
         const float ib = 1.f / fabsf(best);
 #pragma unroll
@@ -315,7 +307,9 @@ __device__ __forceinline__ void quad_eigen_solve(const float (&S)[kSlot], const 
     for (int k = 0; k < 9; ++k) r[k] *= sc;
     float lam = 0.f, qf[4] = {1.f, 0.f, 0.f, 0.f};
     int jb = 0;
-    if (solve) fp32_eigen_estimate(r, e0 * sc, lam, qf, jb);
+    float adj = 1.f;
+    if (solve) fp32_eigen_estimate(r, e0 * sc, lam, qf, jb, adj);
+    const bool suspect = solve && adj < kSuspectAdj;  // a (nearly) double lambda_max
     // ---- refinement in double-float arithmetic (about 48 significant bits),
     // every lane of the warp together from here on
     DF T[4][4];
@@ -391,6 +385,54 @@ __device__ __forceinline__ void quad_eigen_solve(const float (&S)[kSlot], const 
 #pragma unroll
             for (int k = 1; k < 4; ++k)
                 if (fabsf(qv[k].hi) > fabsf(pick4(jv, qv[0], qv[1], qv[2], qv[3]).hi)) jv = k;
+        }
+    }
+    // The passes stop once the adjugate column is not small, which presumes
+    // that lambda was already close to lambda_max.  When the FP32 estimate's
+    // eigenvector is rounding noise -- lambda_max exactly double, as for two
+    // atoms or collinear atoms (R of rank one) -- the Rayleigh quotient of
+    // that noise is not, and the adjugate column is then a mixture of
+    // eigenvectors.  So when the FP32 adjugate was small (the sign of a
+    // double root) the result is checked by its eigen-residual |T q -
+    // (q.T q) q|; a pair that fails the check takes power iterations of
+    // T + 2 I (positive definite: |R|_F = 1 bounds the eigenvalues of T by
+    // sqrt(3)), which reach the eigenspace of lambda_max at a ratio of at
+    // most (lambda_3 + 2) / (lambda_max + 2) per step; any vector of that
+    // space is optimal.
+    bool redo = false;
+    if (__any_sync(kFull, suspect)) {
+        DF w = df_zero();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w = df_add(w, df_mul(pick4(sub, T[0][k], T[1][k], T[2][k], T[3][k]), qv[k]));
+        const DF qs = pick4(sub, qv[0], qv[1], qv[2], qv[3]);
+        DF num = df_mul(w, qs);
+        num = df_add(num, df_shfl_xor(num, 1));
+        num = df_add(num, df_shfl_xor(num, 2));
+        const DF r = df_sub(w, df_mul(num, qs));  // q has unit length
+        DF rr = df_mul(r, r);
+        rr = df_add(rr, df_shfl_xor(rr, 1));
+        rr = df_add(rr, df_shfl_xor(rr, 2));
+        redo = suspect && (!ok || rr.hi > kEigenResidual2);
+    }
+    if (__any_sync(kFull, redo)) {
+        DF pq[4] = {qv[0], qv[1], qv[2], qv[3]};
+        if (!ok) pq[0] = DF{1.f, 0.f}, pq[1] = pq[2] = pq[3] = DF{0.5f, 0.f};
+#pragma unroll 1
+        for (int it = 0; it < kPowerSteps; ++it) {
+            DF w = df_mul_f(pick4(sub, pq[0], pq[1], pq[2], pq[3]), 2.f);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) w = df_add(w, df_mul(pick4(sub, T[0][k], T[1][k], T[2][k], T[3][k]), pq[k]));
+            DF nn = df_mul(w, w);
+            nn = df_add(nn, df_shfl_xor(nn, 1));
+            nn = df_add(nn, df_shfl_xor(nn, 2));
+            const DF wn = nn.hi > 0.f ? df_mul(w, df_rsqrt(nn)) : df_zero();
+#pragma unroll
+            for (int k = 0; k < 4; ++k) pq[k] = df_shfl(wn, base + k);
+        }
+        if (redo && (pq[0].hi != 0.f || pq[1].hi != 0.f || pq[2].hi != 0.f || pq[3].hi != 0.f)) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) qv[k] = pq[k];
+            ok = true;
         }
     }
     DF q0 = qv[0], q1 = qv[1], q2 = qv[2], q3 = qv[3];
@@ -518,20 +560,26 @@ __device__ __forceinline__ float3 residual(const PairState& s, float3 x, float3 
 }
 
 // ---------------------------------------------------------------------------
-// K5: the whole forward of a pair in one CTA, for batches that fit the GPU
-// in one wave (a few long pairs): moments, eigen-solve by one quad of warp 0,
-// residual sum and LRMSD, with block barriers instead of launches between
-// the steps.  Same arithmetic as K5a-K5d; the sums run over the CTA's warps.
+// K5: the whole forward of a pair in one CTA: moments, eigen-solve by one quad
+// of warp 0, residual sum and LRMSD, with block barriers between the steps.
+// Two shapes: 256 threads with four groups of four atoms per thread in
+// flight (two CTAs per SM) for batches that fit one wave, and a compact one,
+// 128 threads with one group (eight CTAs per SM), for larger batches: about
+// 1200 pairs are then in flight, their clouds (tens of MB) stay in L2, and
+// the residual pass reads them from there instead of from HBM, while other
+// CTAs on the SM stream while one CTA's quad solves.
 // ---------------------------------------------------------------------------
 constexpr int kPNT = 256;
+constexpr int kCNT = 128;  // compact shape
 
-__global__ void __launch_bounds__(kPNT, 2) lrmsd_pair_kernel(
+template <int NT, int G, int MINB>
+__global__ void __launch_bounds__(NT, MINB) lrmsd_pair_kernel(
     const float* __restrict__ input, const float* __restrict__ target,
     const int32_t* __restrict__ num_atoms, int P, int Nmax, float* __restrict__ state,
     float* __restrict__ lrmsd) {
+    constexpr int kPNT = NT;
     constexpr int NW = kPNT / 32;
-    constexpr int G = 4;  // groups of 4 atoms per thread in flight
-    constexpr int kBatch = 4 * G * kPNT;
+    constexpr int kBatch = 4 * G * kPNT;  // G groups of 4 atoms per thread in flight
     __shared__ float s_mom[NW][kMom + 1];
     __shared__ double s_res[NW];
     __shared__ __align__(16) float s_st[16];
@@ -635,146 +683,6 @@ __global__ void __launch_bounds__(kPNT, 2) lrmsd_pair_kernel(
         lrmsd_from_sum(sum, n, lr, scale);
         state[16 * (size_t)p + 15] = scale;
         lrmsd[p] = lr;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// K5a: moments, one partial per warp
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kWNT) lrmsd_moments_kernel(
-    const float* __restrict__ input, const float* __restrict__ target,
-    const int32_t* __restrict__ num_atoms, int P, int Nmax, float* __restrict__ part1, int pstride,
-    int wpp) {
-    const int lane = threadIdx.x & 31;
-    const long long w = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    if (w >= (long long)P * wpp) return;
-    const int p = (int)(w / wpp), r = (int)(w % wpp);
-    const int n = pair_atoms(num_atoms, p, Nmax);
-    const int nch = num_chunks(n);
-    if (r >= nch) return;
-    const float* x = target + (size_t)p * Nmax * 3;
-    const float* y = input + (size_t)p * Nmax * 3;
-    float3 sx = make_float3(0.f, 0.f, 0.f), sy = sx;
-    if (n > 0) {
-        sx = make_float3(__ldg(x), __ldg(x + 1), __ldg(x + 2));
-        sy = make_float3(__ldg(y), __ldg(y + 1), __ldg(y + 2));
-    }
-    float m[kMom];
-#pragma unroll
-    for (int k = 0; k < kMom; ++k) m[k] = 0.f;
-    for (int c = r; c < nch; c += wpp) {
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const int i0 = c * kWC + 4 * (lane + 32 * s);
-            if (i0 < n) {
-                float3 xv[4], yv[4];
-                load4(x + 3 * (size_t)i0, xv);
-                load4(y + 3 * (size_t)i0, yv);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (i0 + q < n) {
-                        const float3 dx = f3_sub(xv[q], sx), dy = f3_sub(yv[q], sy);
-                        m[0] += dx.x; m[1] += dx.y; m[2] += dx.z;
-                        m[3] += dy.x; m[4] += dy.y; m[5] += dy.z;
-                        m[6] = fmaf(dx.x, dy.x, m[6]); m[7] = fmaf(dx.x, dy.y, m[7]); m[8] = fmaf(dx.x, dy.z, m[8]);
-                        m[9] = fmaf(dx.y, dy.x, m[9]); m[10] = fmaf(dx.y, dy.y, m[10]); m[11] = fmaf(dx.y, dy.z, m[11]);
-                        m[12] = fmaf(dx.z, dy.x, m[12]); m[13] = fmaf(dx.z, dy.y, m[13]); m[14] = fmaf(dx.z, dy.z, m[14]);
-                        m[15] += f3_dot(dx, dx);
-                        m[16] += f3_dot(dy, dy);
-                    }
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < kMom; ++k) m[k] = warp_sum(m[k]);
-    float4* slot = reinterpret_cast<float4*>(part1 + ((size_t)p * pstride + r) * kSlot);
-#pragma unroll
-    for (int k = 0; k < kSlot / 4; ++k)
-        if (lane == k)
-            slot[k] = make_float4(m[4 * k], 4 * k + 1 < kMom ? m[4 * k + 1] : 0.f,
-                                  4 * k + 2 < kMom ? m[4 * k + 2] : 0.f, 4 * k + 3 < kMom ? m[4 * k + 3] : 0.f);
-}
-
-// ---------------------------------------------------------------------------
-// K5b: eigen-solve, four lanes per pair
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32) lrmsd_solve_kernel(
-    const float* __restrict__ input, const float* __restrict__ target,
-    const int32_t* __restrict__ num_atoms, int P, int Nmax, const float* __restrict__ part1, int pstride,
-    int wpp, float* __restrict__ state) {
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int sub = gid & 3, lane = threadIdx.x & 31;
-    const bool active = (gid >> 2) < P;
-    const int p = active ? (gid >> 2) : P - 1;
-    const int n = pair_atoms(num_atoms, p, Nmax);
-    float x0[3], y0[3];
-    first_atoms(target + (size_t)p * Nmax * 3, input + (size_t)p * Nmax * 3, n, x0, y0);
-    float S[kSlot];
-    quad_sum_partials(part1 + (size_t)p * pstride * kSlot, num_parts(n, wpp), sub, S);
-    quad_eigen_solve(S, x0, y0, n, sub, lane, active, state + 16 * (size_t)p);
-}
-
-// ---------------------------------------------------------------------------
-// K5c: residual sums, one FP64 partial per warp
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kWNT) lrmsd_residual_kernel(
-    const float* __restrict__ input, const float* __restrict__ target,
-    const int32_t* __restrict__ num_atoms, int P, int Nmax, double* __restrict__ part2, int pstride,
-    int wpp, const float* __restrict__ state) {
-    const int lane = threadIdx.x & 31;
-    const long long w = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
-    if (w >= (long long)P * wpp) return;
-    const int p = (int)(w / wpp), r = (int)(w % wpp);
-    const int n = pair_atoms(num_atoms, p, Nmax);
-    const int nch = num_chunks(n);
-    if (r >= nch) return;
-    const float* x = target + (size_t)p * Nmax * 3;
-    const float* y = input + (size_t)p * Nmax * 3;
-    const PairState ps = load_state(state + 16 * (size_t)p);
-    double tot = 0.0;
-    for (int c = r; c < nch; c += wpp) {
-        float acc = 0.f;
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const int i0 = c * kWC + 4 * (lane + 32 * s);
-            if (i0 < n) {
-                float3 xv[4], yv[4];
-                load4(x + 3 * (size_t)i0, xv);
-                load4(y + 3 * (size_t)i0, yv);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (i0 + q < n) {
-                        const float3 d = residual(ps, xv[q], yv[q]);
-                        acc += f3_dot(d, d);
-                    }
-            }
-        }
-        tot += (double)warp_sum(acc);
-    }
-    if (lane == 0) part2[(size_t)p * pstride + r] = tot;
-}
-
-// ---------------------------------------------------------------------------
-// K5d: LRMSD and gradient scale, four lanes per pair
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(32) lrmsd_finalize_kernel(
-    const int32_t* __restrict__ num_atoms, int P, int Nmax, const double* __restrict__ part2, int pstride,
-    int wpp, float* __restrict__ state, float* __restrict__ lrmsd) {
-    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int sub = gid & 3;
-    const bool active = (gid >> 2) < P;
-    const int p = active ? (gid >> 2) : P - 1;
-    const int n = pair_atoms(num_atoms, p, Nmax);
-    const int np = num_parts(n, wpp);
-    double sum = 0.0;
-    for (int k = sub; k < np; k += 4) sum += part2[(size_t)p * pstride + k];
-    sum = quad_sum(sum, sub);
-    if (active && sub == 0) {
-        float lr, scale;
-        lrmsd_from_sum(sum, n, lr, scale);
-        lrmsd[p] = lr;
-        state[16 * (size_t)p + 15] = scale;
     }
 }
 
@@ -990,39 +898,22 @@ const float* lrmsd_state(const void* ws, int P, int Nmax) {
     return reinterpret_cast<const float*>(static_cast<const char*>(ws) + ws_layout(P, Nmax).state);
 }
 
-// Warps per pair of the streaming kernels: enough for about two rounds of the
-// GPU's resident warps, at most one per chunk and kMaxWpp (the partial slots).
-static int warps_per_pair(int P, int parts) {
-    const long long resident = (long long)persistent_grid((const void*)lrmsd_moments_kernel, kWNT, 0) * kWarps;
-    long long w = (2 * resident + P - 1) / P;
-    if (w > parts) w = parts;
-    return w < 1 ? 1 : (int)w;
+// Shape of the pair kernel: the wide one when the batch fits the GPU in one
+// wave of its CTAs, else the compact one.
+static bool pair_path(int P) {
+    return P <= persistent_grid((const void*)lrmsd_pair_kernel<kPNT, 4, 2>, kPNT, 0);
 }
 
-// One CTA per pair when the batch fits the GPU in one wave of such CTAs.
-static bool pair_path(int P) { return P <= persistent_grid((const void*)lrmsd_pair_kernel, kPNT, 0); }
-
-int lrmsd_forward_launches(int P) { return P <= 0 ? 0 : (pair_path(P) ? 1 : 4); }
+int lrmsd_forward_launches(int P) { return P <= 0 ? 0 : 1; }
 
 cudaError_t launch_lrmsd_forward(const float* input, const float* target, const int32_t* num_atoms,
                                  int P, int Nmax, float* lrmsd, void* ws, cudaStream_t s) {
     if (P == 0) return cudaSuccess;
-    const WsLayout L = ws_layout(P, Nmax);
-    char* base = static_cast<char*>(ws);
-    float* part1 = reinterpret_cast<float*>(base + L.part1);
-    double* part2 = reinterpret_cast<double*>(base + L.part2);
-    float* state = reinterpret_cast<float*>(base + L.state);
-    if (pair_path(P)) {
-        lrmsd_pair_kernel<<<P, kPNT, 0, s>>>(input, target, num_atoms, P, Nmax, state, lrmsd);
-        return cudaGetLastError();
-    }
-    const int wpp = warps_per_pair(P, L.parts);
-    const unsigned grid = (unsigned)(((long long)P * wpp + kWarps - 1) / kWarps);
-    const unsigned quads = (unsigned)((4LL * P + 31) / 32);
-    lrmsd_moments_kernel<<<grid, kWNT, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.parts, wpp);
-    lrmsd_solve_kernel<<<quads, 32, 0, s>>>(input, target, num_atoms, P, Nmax, part1, L.parts, wpp, state);
-    lrmsd_residual_kernel<<<grid, kWNT, 0, s>>>(input, target, num_atoms, P, Nmax, part2, L.parts, wpp, state);
-    lrmsd_finalize_kernel<<<quads, 32, 0, s>>>(num_atoms, P, Nmax, part2, L.parts, wpp, state, lrmsd);
+    float* state = reinterpret_cast<float*>(static_cast<char*>(ws) + ws_layout(P, Nmax).state);
+    if (pair_path(P))
+        lrmsd_pair_kernel<kPNT, 4, 2><<<P, kPNT, 0, s>>>(input, target, num_atoms, P, Nmax, state, lrmsd);
+    else
+        lrmsd_pair_kernel<kCNT, 2, 6><<<P, kCNT, 0, s>>>(input, target, num_atoms, P, Nmax, state, lrmsd);
     return cudaGetLastError();
 }
 

@@ -153,7 +153,7 @@ def test_protein_shaped_pairs():
 
 
 def test_large_batch_of_small_pairs():
-    """Many pairs of a few atoms: one warp per pair in the streaming kernels."""
+    """Many pairs of a few atoms: the compact CTA shape, most of its threads idle."""
     rng = np.random.default_rng(9)
     P = 8300
     x, y, n = workloads.lrmsd_clouds(P, 3, 40, rng)
@@ -163,15 +163,16 @@ def test_large_batch_of_small_pairs():
     assert rel_err(g32, oracle.lrmsd_backward(w, x, y, n)) <= GRAD_TOL
 
 
-# sizes around the 256-atom chunks of the streaming kernels
-CHUNK_SIZES = [0, 1, 2, 3, 4, 255, 256, 257, 511, 512, 513, 1023, 1024, 1025, 2999, 3000]
+# sizes around the atoms a CTA loads per pass (four per thread and group:
+# 1024 for the compact shape, 4096 for the wide one) and their halves
+CHUNK_SIZES = [0, 1, 2, 3, 4, 255, 256, 257, 511, 512, 513, 1023, 1024, 1025, 2999, 3000, 4095, 4096, 4097]
 
 
-@pytest.mark.parametrize("P", [600, 2000])
-def test_batches_that_spread_pairs_over_warps(P):
-    """Batches too large for one CTA per pair: the streaming kernels give each
-    pair several warps (each with one or more chunks of 256 atoms), so the
-    partials of a pair come from several warps."""
+@pytest.mark.parametrize("P", [200, 600, 2000])
+def test_batches_of_every_size_around_the_load_passes(P):
+    """Batches that fit one wave of wide CTAs (200) and larger ones (compact
+    CTAs), with atom counts around the CTA's load passes, so pairs end in
+    every position of a pass."""
     sizes = [CHUNK_SIZES[i % len(CHUNK_SIZES)] for i in range(P)]
     x, y, n = _clouds(sizes, 11 + P)
     w = np.random.default_rng(P).normal(size=P).astype(np.float32)
@@ -181,6 +182,20 @@ def test_batches_that_spread_pairs_over_warps(P):
     assert rel_err(g32[unique], oracle.lrmsd_backward(w, x, y, n)[unique]) <= GRAD_TOL
     for p, k in enumerate(n):
         assert np.all(g32[p, k:] == 0)
+
+
+@pytest.mark.parametrize("P", [150, 1500])
+def test_two_atom_pairs(P):
+    """Two atoms: R has rank one, so the largest eigenvalue of T is exactly
+    double and every cofactor of T - lambda I vanishes; the eigen-solve must
+    still land in the eigenspace of lambda_max (aligned, not anti-aligned,
+    difference vectors), for both CTA shapes (150 pairs fit one wave of wide
+    CTAs, 1500 do not)."""
+    rng = np.random.default_rng(P + 5)
+    x, y, n = workloads.lrmsd_clouds(P, 2, 2, rng)
+    w = rng.normal(size=P).astype(np.float32)
+    l32, g32 = _run(x, y, n, w)
+    assert np.abs(l32 - oracle.lrmsd_forward(x, y, n)).max() <= LRMSD_TOL
 
 
 def _rot(q):

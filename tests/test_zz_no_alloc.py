@@ -5,10 +5,10 @@ entry point keeps its scratch in a fixed array inside the library.  The test
 calls it through the C ABI several times in a row (the array keeps the
 previous call's contents) and checks each result against the workspace-based
 tpl_lrmsd_forward: both paths run the same deterministic kernels, so the
-results must be identical.  The calls cover both plans of the forward: the
-one-CTA-per-pair kernel (a batch that fits one wave) and the streaming
-kernels, whose per-pair partial slots fill most of the array, at the
-documented limit (4096 pairs of 8192 atoms).  It collects last so a failure
+results must be identical.  The calls cover both shapes of the forward's
+one-CTA-per-pair kernel: the wide one (a batch that fits one wave) and the
+compact one (larger batches), the latter at the documented limit (4096 pairs
+of 8192 atoms, every per-pair slot of the array in use).  It collects last so a failure
 here leaves every other test already run, and it passes alone in a fresh
 process as well as after the others.
 """
@@ -45,9 +45,8 @@ def test_no_alloc_forward_matches_workspace_forward_on_consecutive_calls():
     big = workloads.lrmsd_clouds(MAX_PAIRS, 100, MAX_ATOMS, rng, Nmax=MAX_ATOMS)
     small = workloads.lrmsd_clouds(57, 3, 900, rng)
     big2 = workloads.lrmsd_clouds(MAX_PAIRS, 3, 2000, rng)
-    assert tpl.tpl_lrmsd_forward_launches(MAX_PAIRS) == 4  # streaming kernels
-    assert tpl.tpl_lrmsd_forward_launches(57) == 1         # one CTA per pair
-    # streaming at the limit, then one CTA per pair, then streaming again over
+    assert tpl.tpl_lrmsd_forward_launches(MAX_PAIRS) == 1 and tpl.tpl_lrmsd_forward_launches(57) == 1
+    # compact CTAs at the limit, then wide ones, then compact ones again over
     # the array the first call left behind
     for x, y, n in (big, small, big2):
         X, Y, N = dev(x, d), dev(y, d), dev(n, d)
