@@ -83,6 +83,9 @@ def parse(argv=None):
                    help="use the library's default launch shape instead of the autotuner's pick")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 per-chain comparison")
+    p.add_argument("--write-padding", action="store_true",
+                   help="chain calls write their outputs' padding every call (default: the bench "
+                        "zeroes the output buffers once and passes TPL_FLAG_PADDING_ZEROED)")
     p.add_argument("--no-extra", action="store_true",
                    help="training step only: skip the uneven backbone and LRMSD batch workloads")
     a = p.parse_args(argv)
@@ -415,6 +418,11 @@ def setup_training_step(args, tpl, torch, dev, d):
             if args.bwd == "coords" and args.fusion == "backward" else [
             lambda: tpl.tpl_fullatom_forward(A, S, Ln, coords, na, fa_ws, o),
             lambda: tpl.tpl_fullatom_backward(A, S, Ln, coords, gtune, gang, fa_ws, o)])
+    if not args.write_padding:
+        # buffers live across steps: zeroed once here, the calls skip their padding
+        opts.flags = tpl.FLAG_PADDING_ZEROED
+        coords.zero_()
+        gang.zero_()
     st = Step()
     st.shape = f"threads={opts.threads or 384},res_per_thread={opts.res_per_thread or 1}"
     res = int(lengths.sum())
@@ -465,6 +473,7 @@ def setup_training_step(args, tpl, torch, dev, d):
     st.atoms = n_atoms
     st.extra_config = {"atoms_per_gpu": n_atoms, "threads": opts.threads or "default",
                        "res_per_thread": opts.res_per_thread or "default",
+                       "output_padding": "written every call" if args.write_padding else "zeroed once",
                        "fullatom_backward": args.bwd, "autotuned": tuned,
                        "fusion": {2: "fused step: forward with LRMSD moments + eigen-solve; backward with "
                                      "LRMSD gradient, residuals and LRMSD",
@@ -540,6 +549,10 @@ def setup_backbone_uneven(args, tpl, torch, dev, d):
     n_atoms = int(na_host.sum())
     res = int(lengths.sum())
 
+    if not args.write_padding:
+        opts.flags = tpl.FLAG_PADDING_ZEROED
+        coords.zero_()
+        gang.zero_()
     st = Step()
     st.shape = f"threads={opts.threads or 128},res_per_thread={opts.res_per_thread or 4}"
     st.kernels = {"backbone_forward": ["schedule_kernel", "bb_fwd_kernel"],
@@ -574,7 +587,9 @@ def setup_backbone_uneven(args, tpl, torch, dev, d):
     st.units = res
     st.atoms = n_atoms
     st.extra_config = {"atoms_per_gpu": n_atoms, "threads": opts.threads or "default",
-                       "res_per_thread": opts.res_per_thread or "default", "backbone_backward": args.bwd,
+                       "res_per_thread": opts.res_per_thread or "default",
+                       "output_padding": "written every call" if args.write_padding else "zeroed once",
+                       "backbone_backward": args.bwd,
                        "autotuned": tuned,
                        "lrmsd_backward": "separate call" if len(st.calls) == 4 else
                                          "formed inside the backbone backward"}

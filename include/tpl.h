@@ -23,7 +23,8 @@
  *    entry points require 16-byte aligned base pointers and Lmax, Amax, Nmax
  *    multiples of 4 (TPL_ERR_MISALIGNED / TPL_ERR_BAD_SHAPE otherwise).
  *  - Padding (residue >= length, atom >= num_atoms) is ignored on input and
- *    written as 0 on output.
+ *    written as 0 on output; with TPL_FLAG_PADDING_ZEROED in the options the
+ *    chain calls may leave output padding unwritten (the caller keeps it 0).
  *
  * Layouts
  *  - backbone angles  [B][3][Lmax]  rows phi, psi, omega (radians)
@@ -89,12 +90,17 @@ typedef struct CUstream_st* tpl_stream; /* same type as cudaStream_t */
                                      treat it as LONGEST_FIRST) */
 
 /* Launch options; a NULL pointer means all zeros (everything automatic). */
+/* tpl_opts.flags */
+#define TPL_FLAG_PADDING_ZEROED 0x1 /* the caller keeps the padding of the outputs zero (it zeroed
+                                       them once): the chain calls need not write it again */
+
 typedef struct tpl_opts {
     int bwd_mode;       /* TPL_BWD_* */
     int threads;        /* threads per CTA of the chain kernels, 0 = tuned default */
     int res_per_thread; /* consecutive residues per thread (1, 2 or 4), 0 = tuned default
                            (with `threads` given: the fewest that form a supported shape) */
     int schedule;       /* TPL_SCHED_* */
+    int flags;          /* TPL_FLAG_* */
 } tpl_opts;
 /* Launch shapes (threads x residues per thread; a tile is their product):
  *  - backbone: threads 64, 128, 256, 512 x 1, 2, 4 (not 512 x 4); default 128 x 4;

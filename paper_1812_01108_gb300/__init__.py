@@ -47,6 +47,7 @@ BWD_AUTO, BWD_RECOMPUTE, BWD_FROM_COORDS = 0, 1, 2
 SCHED_AUTO, SCHED_LONGEST_FIRST, SCHED_BATCH_ORDER, SCHED_PACKED = 0, 1, 2, 3
 STATUS_BAD_RESIDUE, STATUS_BAD_LENGTH, STATUS_TOO_MANY_ATOMS, STATUS_ZERO_LRMSD = 1, 2, 4, 8
 STATUS_TIMEOUT, STATUS_BAD_WORKSPACE = 16, 32
+FLAG_PADDING_ZEROED = 0x1
 
 
 class TplError(RuntimeError):
@@ -61,7 +62,8 @@ class Opts(ctypes.Structure):
     """``tpl_opts``: zero fields mean automatic."""
 
     _fields_ = [("bwd_mode", ctypes.c_int), ("threads", ctypes.c_int),
-                ("res_per_thread", ctypes.c_int), ("schedule", ctypes.c_int)]
+                ("res_per_thread", ctypes.c_int), ("schedule", ctypes.c_int),
+                ("flags", ctypes.c_int)]
 
 
 def library_path() -> str:

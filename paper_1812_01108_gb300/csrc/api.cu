@@ -60,6 +60,10 @@ constexpr int kBuckets = 64;
 constexpr int kKeys = kBuckets + kMaxPack;
 constexpr int kSchedThreads = 1024;
 constexpr int kSchedWarps = kSchedThreads / 32;
+// The first kSchedCache chains' lengths and order entries are kept in shared
+// memory: the per-thread passes over the ordered chains read them in a
+// dependent sequence, which from global memory costs a round trip each.
+constexpr int kSchedCache = 8192;
 
 __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* __restrict__ lengths,
                                                                  int B, int Lmax, int tile, int mode,
@@ -69,7 +73,15 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
     __shared__ int s_run[kKeys];
     __shared__ int s_wcnt[kSchedWarps][kKeys];
     __shared__ int s_part[33];
+    extern __shared__ int s_cache[];  // [ncache] lengths, [ncache] order entries
+    const int ncache = B < kSchedCache ? B : kSchedCache;
+    int* s_len = s_cache;
+    int* s_ord = s_cache + ncache;
     int* order = ws.order;
+    for (int b = threadIdx.x; b < ncache; b += kSchedThreads) {
+        const int L = lengths[b];
+        s_len[b] = L < 0 ? 0 : (L > Lmax ? Lmax : L);
+    }
     {  // zero the forward flags, 16 bytes at a time (the region is 256-byte aligned)
         const int n = B * ws.tmax;
         int4* f4 = reinterpret_cast<int4*>(ws.fflag);
@@ -78,10 +90,17 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
         if (ws.tdone)  // fused training step: the backward's per-tile done flags
             for (int i = threadIdx.x; i < n; i += kSchedThreads) ws.tdone[i] = 0;
     }
+    __syncthreads();
     auto len = [&](int b) {
+        if (b < ncache) return s_len[b];
         const int L = lengths[b];
         return L < 0 ? 0 : (L > Lmax ? Lmax : L);
     };
+    auto set_order = [&](int i, int b) {
+        order[i] = b;
+        if (i < ncache) s_ord[i] = b;
+    };
+    auto ord = [&](int i) { return i < ncache ? s_ord[i] : order[i]; };
     auto is_short = [&](int b) { return mode == kSchedPacked && len(b) <= tile; };
     auto pack_class = [&](int b) {  // chains per packed tile, 1..kMaxPack
         const int slots = (len(b) + granule - 1) / granule * granule;
@@ -155,13 +174,13 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
                 hist[threadIdx.x] = run;  // this round's count of the key
             }
             __syncthreads();
-            if (k >= 0) order[s_start[k] + s_run[k] + s_wcnt[warp][k] + __popc(peers & lt)] = b;
+            if (k >= 0) set_order(s_start[k] + s_run[k] + s_wcnt[warp][k] + __popc(peers & lt), b);
             __syncthreads();
             if (threadIdx.x < kKeys) s_run[threadIdx.x] += hist[threadIdx.x];
             __syncthreads();
         }
     } else {
-        for (int b = threadIdx.x; b < B; b += kSchedThreads) order[b] = b;
+        for (int b = threadIdx.x; b < B; b += kSchedThreads) set_order(b, b);
     }
     __syncthreads();
     // each thread owns a contiguous run of the ordered chains
@@ -175,7 +194,7 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
     // entries that start at order position i: a long chain's tiles, or one
     // packed entry at every m-th chain of a class
     auto entries = [&](int i) {
-        const int b = order[i];
+        const int b = ord(i);
         if (!is_short(b)) return ntiles(b);
         const int m = pack_class(b);
         return ((i - s_start[kBuckets + m - 1]) % m) == 0 ? 1 : 0;
@@ -206,7 +225,7 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
     __syncthreads();
     int base = s_part[warp] + inc - mine;
     for (int i = i0; i < i1; ++i) {
-        const int b = order[i];
+        const int b = ord(i);
         if (is_short(b)) {
             const int m = pack_class(b);
             const int k = kBuckets + m - 1;
@@ -252,6 +271,7 @@ tpl_status check_opts(const tpl_opts& o) {
         return fail(TPL_ERR_INVALID_ARG, "schedule %d unknown", o.schedule);
     if (o.threads < 0 || o.res_per_thread < 0)
         return fail(TPL_ERR_INVALID_ARG, "negative launch option");
+    if (o.flags & ~TPL_FLAG_PADDING_ZEROED) return fail(TPL_ERR_INVALID_ARG, "unknown flags 0x%x", o.flags);
     return TPL_OK;
 }
 
@@ -260,6 +280,7 @@ LaunchCfg backbone_cfg(const tpl_opts& o) {
     LaunchCfg c;
     c.threads = o.threads ? o.threads : 128;
     c.res_per_thread = o.res_per_thread ? o.res_per_thread : 4;
+    c.flags = o.flags;
     return c;
 }
 
@@ -276,6 +297,7 @@ LaunchCfg fullatom_cfg(const tpl_opts& o) {
                 c.res_per_thread = k;
                 break;
             }
+    c.flags = o.flags;
     return c;
 }
 
@@ -322,7 +344,20 @@ __global__ void selftest_wait_kernel(const int* flag) {
 
 cudaError_t launch_schedule(const int32_t* lengths, int B, int Lmax, int tile, int mode, int granule,
                             const ChainWs& ws, cudaStream_t s, bool balanced) {
-    schedule_kernel<<<1, kSchedThreads, 0, s>>>(lengths, B, Lmax, tile, mode, granule, balanced, ws);
+    // the shared-memory limit is raised once per device (not during a capture after the first call)
+    static bool raised[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!raised[dev]) {
+        e = cudaFuncSetAttribute(schedule_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 2 * kSchedCache * (int)sizeof(int));
+        if (e != cudaSuccess) return e;
+        raised[dev] = true;
+    }
+    const size_t smem = 2 * (size_t)(B < kSchedCache ? B : kSchedCache) * sizeof(int);
+    schedule_kernel<<<1, kSchedThreads, smem, s>>>(lengths, B, Lmax, tile, mode, granule, balanced, ws);
     return cudaGetLastError();
 }
 

@@ -195,7 +195,8 @@ __global__ void __launch_bounds__(NT, 768 / NT) bb_fwd_kernel(const float* __res
                                             e + 2 < n9 ? s_out[o9 + e + 2] : 0.f, 0.f);
                 }
                 const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int q = ((n9 + 3) >> 2) + threadIdx.x; q < 9 * Lmax / 4; q += NT) dst[q] = z;
+                if (!(ws.flags & TPL_FLAG_PADDING_ZEROED))
+                    for (int q = ((n9 + 3) >> 2) + threadIdx.x; q < 9 * Lmax / 4; q += NT) dst[q] = z;
             }
             v = next_tile(requested, &s_v);
             continue;
@@ -235,11 +236,15 @@ __global__ void __launch_bounds__(NT, 768 / NT) bb_fwd_kernel(const float* __res
         }
         store_stage<K>(s_out + threadIdx.x * 9 * K, vv);
         __syncthreads();
-        const int nres = min(TILE, Lmax - tile0);  // multiple of 4
+        // with the padding kept zero by the caller, the stores stop at the
+        // chain's last residue (rounded up to 4 residues: the stage holds
+        // zeros past it)
+        const int nres = (ws.flags & TPL_FLAG_PADDING_ZEROED) ? min(TILE, (L - tile0 + 3) & ~3)
+                                                             : min(TILE, Lmax - tile0);  // multiple of 4
         float4* dst = reinterpret_cast<float4*>(out + 9 * (size_t)tile0);
         const float4* src = reinterpret_cast<const float4*>(s_out);
         for (int i = threadIdx.x; i < nres * 9 / 4; i += NT) dst[i] = src[i];
-        if (t == T - 1) {  // zero the residues past the last tile
+        if (t == T - 1 && !(ws.flags & TPL_FLAG_PADDING_ZEROED)) {  // zero the residues past the last tile
             float4* o4 = reinterpret_cast<float4*>(out);
             for (int i = min(Lmax, T * TILE) * 9 / 4 + threadIdx.x; i < Lmax * 9 / 4; i += NT)
                 o4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -472,7 +477,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) bb_bwd_kernel(const float* __res
         store_row<K>(ga, j0, Lmax, gr[0]);
         store_row<K>(ga + Lmax, j0, Lmax, gr[1]);
         store_row<K>(ga + 2 * Lmax, j0, Lmax, gr[2]);
-        if (pack) {  // rows past each chain's slots
+        if (ws.flags & TPL_FLAG_PADDING_ZEROED) {
+            // the caller keeps the rows past each chain zero
+        } else if (pack) {  // rows past each chain's slots
             for (int i = 0; i < m; ++i) {
                 float* gi = grad_angles + (size_t)s_pack.b[i] * 3 * Lmax;
                 for (int j = s_pack.off[i + 1] - s_pack.off[i] + threadIdx.x; j < Lmax; j += NT) {
@@ -672,6 +679,7 @@ cudaError_t launch_backbone_forward(const float* angles, const int32_t* lengths,
     if (B == 0) return cudaSuccess;
     ChainWs ws;
     chain_ws_layout(workspace, B, Lmax, &ws);
+    ws.flags = cfg.flags;
     cudaError_t e = launch_schedule(lengths, B, Lmax, cfg.threads * cfg.res_per_thread, sched_mode,
                                     cfg.res_per_thread, ws, s);
     if (e != cudaSuccess) return e;
@@ -693,6 +701,7 @@ cudaError_t launch_backbone_backward(const float* angles, const int32_t* lengths
     if (B == 0) return cudaSuccess;
     ChainWs ws;
     chain_ws_layout(workspace, B, Lmax, &ws);
+    ws.flags = cfg.flags;
     cudaError_t e = reset_backward_flags(ws, s);
     if (e != cudaSuccess) return e;
     const LrmsdGrad none{nullptr, nullptr, nullptr};
@@ -707,6 +716,7 @@ cudaError_t launch_backbone_backward_lrmsd(const float* angles, const int32_t* l
     if (B == 0) return cudaSuccess;
     ChainWs ws;
     chain_ws_layout(workspace, B, Lmax, &ws);
+    ws.flags = cfg.flags;
     cudaError_t e = reset_backward_flags(ws, s);
     if (e != cudaSuccess) return e;
     const LrmsdGrad lg{target, lrmsd_state, grad_lrmsd};

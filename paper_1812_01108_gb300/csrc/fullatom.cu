@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
         if (staged) store_range<NT>(out, stage, 3 * pc, 3 * (pc + nout));
         if (t == T - 1) {
             if (threadIdx.x == 0) num_atoms[b] = end_atom;
-            zero_range<NT>(out, 3 * min(end_atom, Amax), 3 * Amax);
+            if (!(ws.flags & TPL_FLAG_PADDING_ZEROED)) zero_range<NT>(out, 3 * min(end_atom, Amax), 3 * Amax);
         }
         if constexpr (LM) {
             const float* tg = target + (size_t)b * Amax * 3;
@@ -812,7 +812,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
             store_k<K>(ga + Lmax + j0, gpsi);
             store_k<K>(ga + 2 * Lmax + j0, gomg);
         }
-        if (t == T - 1) {  // rows past the chain's last residue
+        if (t == T - 1 && !(ws.flags & TPL_FLAG_PADDING_ZEROED)) {  // rows past the chain's last residue
             for (int i = L + threadIdx.x; i < Lmax; i += NT)
 #pragma unroll
                 for (int r = 0; r < 7; ++r) ga[r * Lmax + i] = 0.f;
@@ -1011,7 +1011,7 @@ __global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ an
 #pragma unroll
             for (int k = 0; k < kMaxGroups; ++k) ga[(3 + k) * Lmax + j] = gchi[k];
         }
-        if (t == T - 1) {  // rows past the chain's last residue
+        if (t == T - 1 && !(ws.flags & TPL_FLAG_PADDING_ZEROED)) {  // rows past the chain's last residue
             for (int i = L + threadIdx.x; i < Lmax; i += NT)
 #pragma unroll
                 for (int r = 0; r < 7; ++r) ga[r * Lmax + i] = 0.f;
@@ -1304,6 +1304,7 @@ cudaError_t launch_fullatom_forward(const float* angles, const uint8_t* seq,
     if (B == 0) return cudaSuccess;
     ChainWs ws;
     chain_ws_layout(workspace, B, Lmax, &ws, true);
+    ws.flags = cfg.flags;
     cudaError_t e = launch_schedule(lengths, B, Lmax, cfg.threads * cfg.res_per_thread, sched_mode, 1, ws, s, true);
     if (e != cudaSuccess) return e;
     return fa_forward_shape<false>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, cfg, s, nullptr);
@@ -1317,6 +1318,7 @@ cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
     if (B == 0) return cudaSuccess;
     ChainWs ws;
     chain_ws_layout(workspace, B, Lmax, &ws, true);
+    ws.flags = cfg.flags;
     cudaError_t e = reset_backward_flags(ws, s);
     if (e != cudaSuccess) return e;
     if (from_coords)
@@ -1349,6 +1351,7 @@ cudaError_t launch_fullatom_backward_lrmsd(const uint8_t* seq, const int32_t* le
     if (B == 0) return cudaSuccess;
     ChainWs ws;
     chain_ws_layout(workspace, B, Lmax, &ws, true);
+    ws.flags = cfg.flags;
     cudaError_t e = reset_backward_flags(ws, s);
     if (e != cudaSuccess) return e;
     const LrmsdGrad lg{target, lrmsd_state, grad_lrmsd};
@@ -1362,6 +1365,7 @@ cudaError_t launch_fullatom_lrmsd_forward(const float* angles, const uint8_t* se
     if (B == 0) return cudaSuccess;
     ChainWs ws;
     chain_ws_layout(workspace, B, Lmax, &ws, true, true);
+    ws.flags = cfg.flags;
     const int tile = cfg.threads * cfg.res_per_thread;
     cudaError_t e = launch_schedule(lengths, B, Lmax, tile, sched_mode, 1, ws, s, true);
     if (e != cudaSuccess) return e;
@@ -1378,6 +1382,7 @@ cudaError_t launch_fullatom_lrmsd_backward(const uint8_t* seq, const int32_t* le
     if (B == 0) return cudaSuccess;
     ChainWs ws;
     chain_ws_layout(workspace, B, Lmax, &ws, true, true);
+    ws.flags = cfg.flags;
     cudaError_t e = reset_backward_flags(ws, s);
     if (e != cudaSuccess) return e;
     LrmsdGrad lg{target, ws.lstate, grad_lrmsd, lrmsd, num_atoms};

@@ -6,11 +6,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/tpl.h"  // TPL_FLAG_*
+
 namespace tpl {
 
 struct LaunchCfg {
     int threads;        // CTA size
     int res_per_thread; // consecutive residues per thread (tile = threads * res_per_thread)
+    int flags = 0;      // TPL_FLAG_*
 };
 
 // Bytes of the chain workspace (tile list, look-back flags and aggregates,

@@ -64,6 +64,7 @@ struct ChainWs {
     float* lstate;
     int tmax;        // tiles per chain for the smallest tile
     int slots;       // B * tmax
+    int flags;       // TPL_FLAG_* of the call (set by the launcher)
 };
 
 __host__ __device__ inline size_t ws_align(size_t x) { return (x + 255) & ~size_t(255); }
@@ -88,6 +89,7 @@ __host__ __device__ inline int fa_tile_start(int L, int T, int t) {
 }
 
 // Offsets of the regions; `base` may be null to only size the workspace.
+// Whether the output padding is written (flags) is set by the launcher.
 __host__ __device__ inline size_t chain_ws_layout(void* base, int B, int Lmax, ChainWs* w,
                                                   bool per_residue = false, bool step = false) {
     const int tmax = ws_tmax(Lmax);
@@ -128,6 +130,7 @@ __host__ __device__ inline size_t chain_ws_layout(void* base, int B, int Lmax, C
         w->lstate = step ? reinterpret_cast<float*>(c + lstate) : nullptr;
         w->tmax = tmax;
         w->slots = (int)slots;
+        w->flags = 0;
     }
     return o;
 }

@@ -98,6 +98,11 @@ def test_host_argument_checks_return_before_any_launch(lib):
     assert lib.tpl_backbone_forward(None, None, 0, 8, None, None, 0, None, None) == 0
     assert lib.tpl_lrmsd_forward(None, None, None, 0, 8, None, None, 0, None) == 0
     assert lib.tpl_lrmsd_forward(None, None, None, 2, 6, None, None, 0, None) == 2
+    # launch options: unknown flags, schedule or backward mode -> TPL_ERR_INVALID_ARG
+    from paper_1812_01108_gb300 import Opts
+    for bad in ({"flags": 0x2}, {"flags": -1}, {"schedule": 9}, {"bwd_mode": 5}, {"threads": -8}):
+        assert lib.tpl_backbone_forward(None, None, 1, 8, None, None, 0, ctypes.byref(Opts(**bad)), None) == 1
+        assert b"unknown" in lib.tpl_last_error() or b"negative" in lib.tpl_last_error()
 
 
 def test_workspace_sizes(lib):

@@ -32,15 +32,15 @@ def _inputs(lengths, seed, Lmax=None):
     return a, g
 
 
-def _run_fp32(a, lengths, g, opts=None, bwd_opts=None):
+def _run_fp32(a, lengths, g, opts=None, bwd_opts=None, fill=float("nan")):
     d = require_gpu()
     A = dev(a, d)
     Ln = dev(lengths, d)
     B, _, Lmax = a.shape
-    coords = torch.full((B, 3 * Lmax, 3), float("nan"), device=d)
+    coords = torch.full((B, 3 * Lmax, 3), fill, device=d)
     ws = torch.empty(tpl.tpl_backbone_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
     tpl.tpl_backbone_forward(A, Ln, coords, ws, opts)
-    ga = torch.full_like(A, float("nan"))
+    ga = torch.full_like(A, fill)
     tpl.tpl_backbone_backward(A, Ln, coords, dev(g, d), ga, ws, bwd_opts if bwd_opts is not None else opts)
     torch.cuda.synchronize()
     return host(coords), host(ga)
@@ -113,6 +113,24 @@ def test_results_do_not_depend_on_the_schedule(reference):
     c1, g1 = _run_fp32(a, LENGTHS, g, {"schedule": tpl.SCHED_LONGEST_FIRST})
     c2, g2 = _run_fp32(a, LENGTHS, g, {"schedule": tpl.SCHED_BATCH_ORDER})
     assert np.array_equal(c1, c2) and np.array_equal(g1, g2)
+
+
+@pytest.mark.parametrize("sched", [tpl.SCHED_PACKED, tpl.SCHED_LONGEST_FIRST])
+@pytest.mark.parametrize("bwd", [tpl.BWD_FROM_COORDS, tpl.BWD_RECOMPUTE])
+def test_padding_flag_changes_nothing_but_the_padding(reference, sched, bwd):
+    """FLAG_PADDING_ZEROED: on outputs the caller zeroed, every element equals
+    the default call's; on NaN-filled outputs the real residues still do (the
+    backward reads no padding of the coordinates) and only padding may differ."""
+    a, g, _, _ = reference
+    o = {"threads": 128, "res_per_thread": 4, "schedule": sched}
+    of = dict(o, flags=tpl.FLAG_PADDING_ZEROED)
+    c0, g0 = _run_fp32(a, LENGTHS, g, o, dict(o, bwd_mode=bwd))
+    c1, g1 = _run_fp32(a, LENGTHS, g, of, dict(of, bwd_mode=bwd), fill=0.0)
+    assert np.array_equal(c0, c1) and np.array_equal(g0, g1)
+    c2, g2 = _run_fp32(a, LENGTHS, g, of, dict(of, bwd_mode=bwd))
+    for b, L in enumerate(LENGTHS):
+        assert np.array_equal(c2[b, :3 * L], c0[b, :3 * L])
+        assert np.array_equal(g2[b, :, :L], g0[b, :, :L])
 
 
 def test_fp64_per_chain_form_matches_oracle(reference):

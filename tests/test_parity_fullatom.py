@@ -33,15 +33,15 @@ def _inputs(lengths, seed, omega_noise=0.0):
     return a, seq, g, Amax
 
 
-def _run_fp32(a, seq, lengths, g, Amax, opts=None, from_coords=False):
+def _run_fp32(a, seq, lengths, g, Amax, opts=None, from_coords=False, fill=float("nan")):
     d = require_gpu()
     A, S, Ln = dev(a, d), dev(seq, d), dev(lengths, d)
     B, _, Lmax = a.shape
-    coords = torch.full((B, Amax, 3), float("nan"), device=d)
+    coords = torch.full((B, Amax, 3), fill, device=d)
     na = torch.full((B,), -1, dtype=torch.int32, device=d)
     ws = torch.empty(tpl.tpl_fullatom_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
     tpl.tpl_fullatom_forward(A, S, Ln, coords, na, ws, opts)
-    ga = torch.full_like(A, float("nan"))
+    ga = torch.full_like(A, fill)
     tpl.tpl_fullatom_backward(A, S, Ln, coords if from_coords else None, dev(g, d), ga, ws, opts)
     torch.cuda.synchronize()
     return host(coords), host(na), host(ga)
@@ -86,6 +86,24 @@ def test_schedule_independent_and_deterministic(reference, shape, from_coords):
     r3 = _run_fp32(a, seq, LENGTHS, g, Amax, dict(o, schedule=tpl.SCHED_BATCH_ORDER), from_coords)
     for x, y, z in zip(r1, r2, r3):
         assert np.array_equal(x, y) and np.array_equal(y, z)
+
+
+@pytest.mark.parametrize("shape,from_coords", [((384, 1), True), ((192, 2), True), ((256, 1), False)])
+def test_padding_flag_changes_nothing_but_the_padding(reference, shape, from_coords):
+    """FLAG_PADDING_ZEROED: on outputs the caller zeroed, every element equals
+    the default call's; on NaN-filled outputs the real atoms and residues
+    still do and only padding may differ."""
+    a, seq, g, Amax, c64, na64, _ = reference
+    o = {"threads": shape[0], "res_per_thread": shape[1]}
+    of = dict(o, flags=tpl.FLAG_PADDING_ZEROED)
+    r0 = _run_fp32(a, seq, LENGTHS, g, Amax, o, from_coords)
+    r1 = _run_fp32(a, seq, LENGTHS, g, Amax, of, from_coords, fill=0.0)
+    assert all(np.array_equal(x, y) for x, y in zip(r0, r1))
+    c2, na2, g2 = _run_fp32(a, seq, LENGTHS, g, Amax, of, from_coords)
+    assert np.array_equal(na2, na64)
+    for b, L in enumerate(LENGTHS):
+        assert np.array_equal(c2[b, :na64[b]], r0[0][b, :na64[b]])
+        assert np.array_equal(g2[b, :, :L], r0[2][b, :, :L])
 
 
 def test_fp64_per_chain_form_matches_oracle(reference):
