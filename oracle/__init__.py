@@ -65,6 +65,8 @@ def _load():
             I = ctypes.c_int
             lib.oracle_backbone_forward.argtypes = [P, P, I, I, P]
             lib.oracle_backbone_backward.argtypes = [P, P, I, I, P, P]
+            lib.oracle_backbone_forward_o.argtypes = [P, P, I, I, P, P]
+            lib.oracle_backbone_backward_o.argtypes = [P, P, I, I, P, P, P]
             lib.oracle_fullatom_forward.argtypes = [P, P, P, I, I, I, P, P]
             lib.oracle_fullatom_backward.argtypes = [P, P, P, I, I, I, P, P]
             lib.oracle_fullatom_chain_atoms.argtypes = [P, I]
@@ -119,6 +121,32 @@ def backbone_backward(angles, lengths, grad_coords):
     out = np.zeros((B, 3, Lmax), np.float64)
     _check(_load().oracle_backbone_backward(_p(a), _p(ln), B, Lmax, _p(g), _p(out)),
            "backbone_backward")
+    return out
+
+
+def backbone_forward_o(angles, lengths):
+    """Backbone with the carbonyl O: (coords [B,3*Lmax,3], O [B,Lmax,3]); O_j rigid
+    in the frame of C_j after psi_j (bond C-O, angle CA-C-O, dihedral
+    N-CA-C-O = psi_j + 180); Section 3 with the full-atom tables' O."""
+    a = _f64(angles)
+    ln = _i32(lengths)
+    B, _, Lmax = a.shape
+    out = np.zeros((B, 3 * Lmax, 3), np.float64)
+    o = np.zeros((B, Lmax, 3), np.float64)
+    _check(_load().oracle_backbone_forward_o(_p(a), _p(ln), B, Lmax, _p(out), _p(o)), "backbone_forward_o")
+    return out, o
+
+
+def backbone_backward_o(angles, lengths, grad_coords, grad_o):
+    """Eq. 2 with the O atoms among the moved atoms: dL/d(phi, psi, omega)."""
+    a = _f64(angles)
+    ln = _i32(lengths)
+    g = _f64(grad_coords)
+    go = _f64(grad_o)
+    B, _, Lmax = a.shape
+    out = np.zeros((B, 3, Lmax), np.float64)
+    _check(_load().oracle_backbone_backward_o(_p(a), _p(ln), B, Lmax, _p(g), _p(go), _p(out)),
+           "backbone_backward_o")
     return out
 
 

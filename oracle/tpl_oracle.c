@@ -703,6 +703,83 @@ int oracle_fullatom_backward(const double* angles, const uint8_t* seq, const int
 }
 
 /* ------------------------------------------------------------------ */
+/* Section 3 backbone with the carbonyl O of each residue              */
+/* ------------------------------------------------------------------ */
+
+/* The paper's backbone model places N, CA and C only.  The carbonyl O of
+ * residue j is rigid in the frame M_{3j+2} of C_j (after the psi_j rotation),
+ * where the full-atom residue tables put it: bond C-O, angle CA-C-O,
+ * dihedral N-CA-C-O = psi_j + 180 (so it lies in the plane of CA_j, C_j and
+ * N_{j+1}, opposite N_{j+1}): O_j = M_{3j+2} r0_O. */
+static void backbone_o_local(double* r0) {
+    frame_child(O_BOND, O_ANGLE_DEG * DEG, O_DIHEDRAL_OFFSET_DEG * DEG, r0);
+}
+
+int oracle_backbone_forward_o(const double* angles, const int32_t* lengths, int B, int Lmax,
+                              double* coords, double* o_coords) {
+    if (oracle_backbone_forward(angles, lengths, B, Lmax, coords)) return 1;
+    double* M = (double*)malloc((size_t)(3 * (Lmax > 0 ? Lmax : 1)) * 16 * sizeof(double));
+    if (!M) return 2;
+    double r0[3];
+    backbone_o_local(r0);
+    for (int b = 0; b < B; ++b) {
+        int L = lengths[b];
+        double* o = o_coords + (size_t)b * Lmax * 3;
+        memset(o, 0, (size_t)Lmax * 3 * sizeof(double));
+        backbone_frames(angles + (size_t)b * 3 * Lmax, Lmax, L, M);
+        for (int j = 0; j < L; ++j) mat_apply_point(M + 16 * (3 * j + 2), r0, o + 3 * j);
+    }
+    free(M);
+    return 0;
+}
+
+/* Eq. 2 with the O atoms among the moved atoms: O_j moves with every angle of
+ * the nodes 0 .. 3j+2 (up to and including psi_j). */
+int oracle_backbone_backward_o(const double* angles, const int32_t* lengths, int B, int Lmax,
+                               const double* grad_coords, const double* grad_o, double* grad_angles) {
+    if (check_dims(B, Lmax)) return 1;
+    double* M = (double*)malloc((size_t)(3 * (Lmax > 0 ? Lmax : 1)) * 16 * sizeof(double));
+    double* O = (double*)malloc((size_t)(Lmax > 0 ? Lmax : 1) * 3 * sizeof(double));
+    if (!M || !O) { free(M); free(O); return 2; }
+    double r0[3];
+    backbone_o_local(r0);
+    for (int b = 0; b < B; ++b) {
+        int L = lengths[b];
+        if (L < 0 || L > Lmax) { free(M); free(O); return 1; }
+        const double* ang = angles + (size_t)b * 3 * Lmax;
+        const double* g = grad_coords + (size_t)b * 3 * Lmax * 3;
+        const double* go = grad_o + (size_t)b * Lmax * 3;
+        double* ga = grad_angles + (size_t)b * 3 * Lmax;
+        memset(ga, 0, (size_t)3 * Lmax * sizeof(double));
+        backbone_frames(ang, Lmax, L, M);
+        for (int j = 0; j < L; ++j) mat_apply_point(M + 16 * (3 * j + 2), r0, O + 3 * j);
+        for (int j = 0; j < L; ++j)
+            for (int k = 0; k < 3; ++k) {
+                int node = 3 * j + k;
+                if (node == 0) continue; /* R_0 = I carries no angle */
+                double alpha = ang[BB_ROW[k] * Lmax + j];
+                double F[16], dr[3];
+                make_lever(M + 16 * (node - 1), alpha, BB_THETA[k], BB_D[k], M + 16 * node, F);
+                double s = 0.0;
+                for (int i = node; i < 3 * L; ++i) {
+                    double r[3] = {M[16 * i + 3], M[16 * i + 7], M[16 * i + 11]};
+                    lever_apply(F, r, dr);
+                    s += g[3 * i + 0] * dr[0] + g[3 * i + 1] * dr[1] + g[3 * i + 2] * dr[2];
+                }
+                for (int jo = 0; jo < L; ++jo) {
+                    if (3 * jo + 2 < node) continue;
+                    lever_apply(F, O + 3 * jo, dr);
+                    s += go[3 * jo + 0] * dr[0] + go[3 * jo + 1] * dr[1] + go[3 * jo + 2] * dr[2];
+                }
+                ga[BB_ROW[k] * Lmax + j] = s;
+            }
+    }
+    free(M);
+    free(O);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Section 4: LRMSD                                                    */
 /* ------------------------------------------------------------------ */
 

@@ -41,6 +41,18 @@ int oracle_backbone_backward(const double* angles, const int32_t* lengths,
                              int B, int Lmax, const double* grad_coords,
                              double* grad_angles);
 
+/* Section 3 with the carbonyl O of each residue (not placed by the paper's
+ * backbone model): O_j rigid in the frame of C_j after psi_j, bond C-O, angle
+ * CA-C-O and dihedral N-CA-C-O = psi_j + 180 as in the full-atom tables.
+ * coords as oracle_backbone_forward; o_coords [B][Lmax][3]. */
+int oracle_backbone_forward_o(const double* angles, const int32_t* lengths, int B, int Lmax,
+                              double* coords, double* o_coords);
+
+/* Eq. 2 with the O atoms moved by every angle up to their residue's psi:
+ * grad_coords [B][3*Lmax][3], grad_o [B][Lmax][3]. */
+int oracle_backbone_backward_o(const double* angles, const int32_t* lengths, int B, int Lmax,
+                               const double* grad_coords, const double* grad_o, double* grad_angles);
+
 /* Section 2: graph of cumulative transforms M_1 = M_0 R_1(phi),
  * side-chain frames M_0 R_1 R' R(chi1) ..., M_3 = M_1 R_3(psi),
  * next M_0 = M_3 R_4(omega); atoms r = M_g r0. */
