@@ -48,7 +48,7 @@ METRIC = "residues/s fwd+bwd at FP32 err≤2e-3 Å vs plain FP64 GPU form; HBM r
 METRIC_LRMSD = "atoms/s LRMSD fwd+bwd vs plain FP64 GPU form; HBM roofline %"
 
 DEFAULT_BATCH = {"training_step": 256, "backbone_uneven": 4096, "lrmsd_batch": 16384,
-                 "backbone_stress": 64}
+                 "backbone_stress": 64, "length_sweep": 32}
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a C-ABI
 # call's kernels from one ncu capture, per unit processed (residue or atom),
@@ -59,6 +59,10 @@ TRAFFIC = {
     # kernels take none); cold-cache captures of one launch.  Filled from the
     # captures of the current kernels (profiles/).
 }
+
+
+# launch shapes of the backbone training-step kernel
+STEP_SHAPES = [(128, 4), (256, 4), (256, 2), (128, 2), (512, 2)]
 
 
 def parse(argv=None):
@@ -76,7 +80,7 @@ def parse(argv=None):
                    help="chain backward: read the forward's coordinates, rebuild frames, or (backbone) "
                         "the paper's O(L^2) sums from the coordinates")
     p.add_argument("--fusion", default="backward", choices=["step", "backward", "none"],
-                   help="training step: fused step (two calls), fused backward (three calls), "
+                   help="training step: fused step (full atom: two calls; backbone: one call), fused backward (three calls), "
                         "or separate calls (four)")
     p.add_argument("--unfused", action="store_true", help="same as --fusion none")
     p.add_argument("--no-autotune", action="store_true",
@@ -278,9 +282,54 @@ def cpu_baseline(args, d, unit, budget_s=12.0):
                       f"{t:.1f} s, single thread"}
 
 
+def run_reference_sweep(args):
+    """The oracle's backward (the paper's O(L^2) lever sums, FP64, one thread)
+    on one chain per length of the sweep, each length bounded to a few seconds."""
+    import time
+
+    import oracle
+    import workloads
+
+    oracle.build()
+    rows, total = [], 0.0
+    for L in SWEEP_LENGTHS:
+        if total > 60.0:
+            break
+        rng = workloads.rng_for(6, salt=L)
+        lengths = np.full(1, L, np.int32)
+        a = workloads.backbone_angles(lengths, rng)
+        g = workloads.upstream_grad((1, 3 * L, 3), rng)
+        t0 = time.perf_counter()
+        oracle.backbone_backward(a, lengths, g)
+        t1 = time.perf_counter()
+        fa, seq = workloads.fullatom_inputs(lengths, rng)
+        Amax = workloads.pad_to(oracle.max_atoms(seq, lengths))
+        gf = workloads.upstream_grad((1, Amax, 3), rng)
+        oracle.fullatom_backward(fa, seq, lengths, gf)
+        t2 = time.perf_counter()
+        rows.append({"L": L, "backbone_backward_ms": 1e3 * (t1 - t0), "fullatom_backward_ms": 1e3 * (t2 - t1)})
+        total += t2 - t0
+    last = rows[-1]
+    value = last["L"] / (last["fullatom_backward_ms"] * 1e-3)
+    line = {
+        "impl": "reference", "metric": "fullatom_backward_residues_per_s_at_longest", "value": value,
+        "unit": "residues/s", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": last["fullatom_backward_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "length_sweep", "batch": 1, "lengths": [r["L"] for r in rows]},
+        "sweep": rows,
+        "cpu_baseline": {"value": value, "unit": "residues/s", "cores": 1, "kind": "oracle",
+                         "sample": "one chain per length, single thread, lengths until 60 s"},
+        "e2e": {"value": value, "unit": "residues/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
+        return
+    if args.workload == "length_sweep":
+        run_reference_sweep(args)
         return
     import oracle
 
@@ -335,7 +384,7 @@ class Step:
     """
 
 
-def cold_pick(torch, dev, cands, tuned, calls_for, reps=20):
+def cold_pick(torch, dev, cands, tuned, calls_for, reps=20, labels=("autotuned", "default")):
     """The fastest of the candidate options for a step made of calls_for(o),
     each captured as a CUDA graph and timed with L2 flushed before every
     replay (the protocol of the timed region)."""
@@ -363,8 +412,7 @@ def cold_pick(torch, dev, cands, tuned, calls_for, reps=20):
         times.append(best)
         del g
     i = int(np.argmin(times))
-    tuned = dict(tuned, cold_ms={"autotuned": times[0], "default": times[1]},
-                 chosen="autotuned" if i == 0 else "default")
+    tuned = dict(tuned, cold_ms=dict(zip(labels, times)), chosen=labels[i])
     return cands[i], tuned
 
 
@@ -535,8 +583,20 @@ def setup_backbone_uneven(args, tpl, torch, dev, d):
     tpl.tpl_backbone_forward(torch.from_numpy(ta).to(dev), Ln, target, bb_ws, opts)
     torch.cuda.synchronize()
     tuned = None
+    step_fused = args.fusion == "step" and args.bwd == "coords"
+    st_ws = None
+    if step_fused:
+        st_ws = torch.empty(tpl.tpl_backbone_lrmsd_workspace_size(B, Lmax), dtype=torch.uint8, device=dev)
+        if opts.res_per_thread == 0 and opts.threads == 0:
+            opts.threads, opts.res_per_thread = 128, 4
     if not args.no_autotune and not args.threads and not args.res_per_thread:
-        if args.bwd == "coords" and not args.unfused:
+        if step_fused:
+            # the training-step shapes, timed as the step is timed
+            cands = [tpl.Opts(threads=t, res_per_thread=k, schedule=tpl.SCHED_PACKED) for t, k in STEP_SHAPES]
+            opts, tuned = cold_pick(torch, dev, cands, {}, lambda o: [
+                lambda: tpl.tpl_backbone_lrmsd_step(A, Ln, target, wgt, coords, lr, gang, st_ws, o)],
+                labels=[f"{t}x{k}" for t, k in STEP_SHAPES])
+        elif args.bwd == "coords" and not args.unfused:
             # the three calls of the timed step
             opts, tms = tpl.tpl_backbone_lrmsd_autotune(A, Ln, coords, target, na, wgt, lr, lr_ws, gang, bb_ws)
             tuned = {"threads": opts.threads, "res_per_thread": opts.res_per_thread,
@@ -558,7 +618,17 @@ def setup_backbone_uneven(args, tpl, torch, dev, d):
     st.kernels = {"backbone_forward": ["schedule_kernel", "bb_fwd_kernel"],
                   "lrmsd_forward": lrmsd_forward_kernels(tpl, B)}
     st.alg = {"backbone_forward": 48 * res, "lrmsd_forward": 24 * n_atoms}
-    if args.unfused or args.bwd != "coords":
+    if step_fused:
+        # one call: whole chains in one CTA each (pack or one tile); longer
+        # chains add the eigen-solve and backward launches
+        st.calls = [("lrmsd_step",
+                     lambda: tpl.tpl_backbone_lrmsd_step(A, Ln, target, wgt, coords, lr, gang, st_ws, opts))]
+        tile = opts.threads * opts.res_per_thread
+        st.kernels = {"lrmsd_step": ["schedule_kernel", "bb_step_kernel"] +
+                      (["lrmsd_solve_tiles_kernel", "bb_bwd_kernel"] if Lmax > tile else [])}
+        # angles 12 in, angle gradient 12 out per residue; target 12 in, coordinates 12 out per atom
+        st.alg = {"lrmsd_step": 24 * res + 24 * n_atoms}
+    elif args.unfused or args.bwd != "coords":
         st.calls = [
             ("backbone_forward", lambda: tpl.tpl_backbone_forward(A, Ln, coords, bb_ws, opts)),
             ("lrmsd_forward", lambda: tpl.tpl_lrmsd_forward(coords, target, na, lr, lr_ws)),
@@ -592,10 +662,15 @@ def setup_backbone_uneven(args, tpl, torch, dev, d):
                        "backbone_backward": args.bwd,
                        "autotuned": tuned,
                        "lrmsd_backward": "separate call" if len(st.calls) == 4 else
-                                         "formed inside the backbone backward"}
+                                         "formed inside the backbone backward" if len(st.calls) == 3 else
+                                         "one training-step call"}
     st.h2d = [(A, torch.from_numpy(a).pin_memory()), (Ln, torch.from_numpy(lengths).pin_memory()),
               (na, torch.from_numpy(na_host).pin_memory()), (target, target.cpu().pin_memory())]
-    st.h2d_late = {2: 1, 3: 1}  # atom counts and target are first read by the LRMSD forward
+    if step_fused:  # one call reads everything; the atom counts are not an input
+        st.h2d = [st.h2d[0], st.h2d[1], st.h2d[3]]
+        st.h2d_late = {}
+    else:
+        st.h2d_late = {2: 1, 3: 1}  # atom counts and target are first read by the LRMSD forward
     st.outputs = {"coords": coords, "target": target, "lrmsd": lr, "grad_angles": gang, "weights": wgt}
     st.d2h = (torch.empty((B,), dtype=torch.float32).pin_memory(), lr)
 
@@ -893,6 +968,122 @@ def measure(args, workload, tpl, torch, dev, rank, world, local, flush):
 EXTRA_WORKLOADS = ("backbone_uneven", "lrmsd_batch")
 
 
+# ----------------------------------------------------------------------------- length sweep
+SWEEP_LENGTHS = (64, 128, 256, 512, 1024, 2048, 4096)
+
+
+def _flushed_ms(torch, fn, flush, reps):
+    """Median of reps launches of fn, each after an L2 flush, timed with CUDA
+    events on the current stream."""
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def _slope(ls, ts):
+    """Least-squares exponent of t ~ L^k over the sweep's upper half."""
+    h = len(ls) // 2
+    x, y = np.log(np.array(ls[h:], float)), np.log(np.array(ts[h:], float))
+    return float(np.polyfit(x, y, 1)[0]) if len(x) >= 2 else None
+
+
+def run_length_sweep(args):
+    """The scan forward and backward against the paper's O(L^2) backward forms
+    (Eq. 2 summed per (angle, atom); Eq. 1 depth first), for both models, at
+    growing chain length and a fixed batch: the shapes of the paper's timing
+    figures.  Inputs are seeded synthetic chains of one length."""
+    import torch
+
+    import paper_1812_01108_gb300 as tpl
+    import workloads
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (there is no CPU path)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    tpl.load_library()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    B, reps = args.batch, max(3, args.steps)
+    sweep = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    for L in SWEEP_LENGTHS:
+        rng = workloads.rng_for(6, salt=L)
+        lengths = np.full(B, L, np.int32)
+        Ln = torch.from_numpy(lengths).to(dev)
+        row = {"L": L}
+        # backbone
+        a = workloads.backbone_angles(lengths, rng)
+        A = torch.from_numpy(a).to(dev)
+        c = torch.zeros((B, 3 * L, 3), device=dev)
+        g = torch.from_numpy(workloads.upstream_grad((B, 3 * L, 3), rng)).to(dev)
+        ga = torch.zeros_like(A)
+        gq = torch.zeros_like(A)
+        ws = torch.empty(tpl.tpl_backbone_workspace_size(B, L), dtype=torch.uint8, device=dev)
+        o = tpl.Opts(bwd_mode=tpl.BWD_FROM_COORDS)
+        row["backbone_forward_ms"] = _flushed_ms(torch, lambda: tpl.tpl_backbone_forward(A, Ln, c, ws, o), flush, reps)
+        row["backbone_backward_scan_ms"] = _flushed_ms(
+            torch, lambda: tpl.tpl_backbone_backward(A, Ln, c, g, ga, ws, o), flush, reps)
+        row["backbone_backward_quadratic_ms"] = _flushed_ms(
+            torch, lambda: tpl.tpl_backbone_backward_quadratic(Ln, c, g, gq), flush, reps)
+        torch.cuda.synchronize()
+        row["backbone_scan_vs_quadratic_rel"] = float(torch.linalg.vector_norm(ga - gq) /
+                                                      torch.linalg.vector_norm(gq))
+        del A, c, g, ga, gq, ws
+        # full atom
+        fa, seq = workloads.fullatom_inputs(lengths, rng)
+        Amax = workloads.pad_to(tpl.fullatom_max_atoms(seq, lengths))
+        A = torch.from_numpy(fa).to(dev)
+        S = torch.from_numpy(seq).to(dev)
+        c = torch.zeros((B, Amax, 3), device=dev)
+        na = torch.zeros((B,), dtype=torch.int32, device=dev)
+        g = torch.from_numpy(workloads.upstream_grad((B, Amax, 3), rng)).to(dev)
+        ga = torch.zeros_like(A)
+        gq = torch.zeros_like(A)
+        ws = torch.empty(tpl.tpl_fullatom_workspace_size(B, L), dtype=torch.uint8, device=dev)
+        row["atoms_per_chain"] = int(tpl.fullatom_max_atoms(seq, lengths))
+        row["fullatom_forward_ms"] = _flushed_ms(
+            torch, lambda: tpl.tpl_fullatom_forward(A, S, Ln, c, na, ws, o), flush, reps)
+        row["fullatom_backward_scan_ms"] = _flushed_ms(
+            torch, lambda: tpl.tpl_fullatom_backward(A, S, Ln, c, g, ga, ws, o), flush, reps)
+        row["fullatom_backward_quadratic_ms"] = _flushed_ms(
+            torch, lambda: tpl.tpl_fullatom_backward_quadratic(S, Ln, c, g, gq), flush, reps)
+        torch.cuda.synchronize()
+        row["fullatom_scan_vs_quadratic_rel"] = float(torch.linalg.vector_norm(ga - gq) /
+                                                      torch.linalg.vector_norm(gq))
+        del A, S, c, na, g, ga, gq, ws
+        torch.cuda.empty_cache()
+        sweep.append(row)
+    clk = clocks.stop()
+    ls = [r["L"] for r in sweep]
+    exps = {k[:-3]: _slope(ls, [r[k] for r in sweep]) for k in sweep[0] if k.endswith("_ms")}
+    last = sweep[-1]
+    ms = last["fullatom_forward_ms"] + last["fullatom_backward_scan_ms"]
+    line = {
+        "metric": "fullatom_fwd_bwd_residues_per_s_at_longest", "value": B * last["L"] / (ms * 1e-3),
+        "unit": "residues/s", "n_gpus": 1, "steps": reps, "warmup": 1, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "length_sweep", "batch": B, "lengths": list(SWEEP_LENGTHS),
+                   "backward_input": "forward coordinates", "l2": "flushed before every timed call"},
+        "sweep": sweep, "time_exponent_upper_half": exps, "clocks": clk,
+        # per length and timed repetition: backbone forward 2 (work list, scan),
+        # scan backward 1, quadratic 1; full atom the same
+        "gpu_launches": 8 * reps * len(SWEEP_LENGTHS),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def run_tpl(args):
     import torch
 
@@ -945,6 +1136,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "length_sweep":
+        run_length_sweep(args)
     else:
         run_tpl(args)
 

@@ -151,6 +151,28 @@ tpl_status tpl_backbone_backward(const float* angles, const int32_t* lengths, in
 /* Full-atom model (paper Section 2)                                         */
 /* ------------------------------------------------------------------------ */
 
+/* The backbone with the carbonyl O of every residue (the paper's backbone
+ * model places N, CA and C only).  O_j is rigid in the frame of C_j after the
+ * psi_j transform, where the full-atom tables put it (Section 2): bond C-O
+ * 1.231 A, angle CA-C-O 120.1 degrees, dihedral N-CA-C-O = psi_j + 180, so
+ * it lies in the plane of CA_j, C_j and N_{j+1}, opposite N_{j+1}; psi of the
+ * last residue now moves an atom.  The scan places O with the residue's other
+ * atoms (one more point per residue, 12 bytes written) and the backward
+ * counts it among the atoms each angle moves (O_j after C_j: moved by every
+ * angle up to psi_j).
+ *   coords as tpl_backbone_forward; o_coords [B][Lmax][3] out (forward), in
+ *   (backward with FROM_COORDS); grad_o [B][Lmax][3] in.
+ *   Launch shapes 128 x 1, 2, 4 and 256 x 4 (default 128 x 4); workspace,
+ *   schedule, bwd_mode and flags as tpl_backbone_forward / _backward (the
+ *   backward with FROM_COORDS reads coords and o_coords; RECOMPUTE neither). */
+tpl_status tpl_backbone_forward_o(const float* angles, const int32_t* lengths, int B, int Lmax, float* coords,
+                                  float* o_coords, void* workspace, size_t workspace_bytes, const tpl_opts* opts,
+                                  tpl_stream stream);
+tpl_status tpl_backbone_backward_o(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                   const float* coords, const float* o_coords, const float* grad_coords,
+                                   const float* grad_o, float* grad_angles, void* workspace, size_t workspace_bytes,
+                                   const tpl_opts* opts, tpl_stream stream);
+
 /* The paper's own O(L^2) evaluation of Eq. 2 (Section 3): every (angle,
  * atom) term dL/dalpha_q = g_k . (M_{q-1} dR_q M_q^{-1} r_k), k >= q, summed
  * directly -- written as u_q . sum_{k >= q} (r_k - r_q) x g_k with u_q the unit
@@ -161,6 +183,22 @@ tpl_status tpl_backbone_backward(const float* angles, const int32_t* lengths, in
  *   omega_0).  B <= 65535.  Needs no workspace. */
 tpl_status tpl_backbone_backward_quadratic(const int32_t* lengths, int B, int Lmax, const float* coords,
                                            const float* grad_coords, float* grad_angles, tpl_stream stream);
+
+/* The paper's depth-first evaluation of Eq. 1 (Section 2): for every angle,
+ * the sum over the atoms it moves of g_k . (u x (r_k - p)) = u . ((r_k - p)
+ * x g_k), u the unit axis and p a point on it, with no suffix scan -- O(L)
+ * work per backbone angle, O(L^2) per chain: a comparator for
+ * tpl_fullatom_backward (same result to rounding).  Angle j of a residue
+ * moves the later residues and, in its own residue: phi all atoms but N,
+ * psi C and O, omega all atoms, chi_k the side-chain groups k and beyond.
+ *   seq, lengths, coords [B][Amax][3] (the full-atom forward's output),
+ *   grad_coords the same shape; grad_angles [B][7][Lmax] out (zeros at
+ *   padding, for omega_0 and for the chi angles a residue type lacks).
+ *   B <= 65535.  Needs no workspace.  A chain with more atoms than Amax gets
+ *   a zero gradient (the forward flags it). */
+tpl_status tpl_fullatom_backward_quadratic(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
+                                           const float* coords, const float* grad_coords, float* grad_angles,
+                                           tpl_stream stream);
 
 /* Workspace of the full-atom calls; the same contract as the backbone's (the
  * backward reuses the forward's schedule and tile-start frames). */
@@ -214,6 +252,30 @@ tpl_status tpl_fullatom_lrmsd_backward(const uint8_t* seq, const int32_t* length
                                        const float* coords, const float* target, const int32_t* num_atoms,
                                        const float* grad_lrmsd, float* lrmsd, float* grad_angles, void* workspace,
                                        size_t workspace_bytes, const tpl_opts* opts, tpl_stream stream);
+
+/* Training step of the backbone model on the LRMSD loss (Section 3 forward,
+ * Section 4 LRMSD, its gradient chained into Eq. 2, as the paper's training
+ * does; the paper has no fused form), in one call:
+ *   coords [B][3 Lmax][3] = the backbone forward (as tpl_backbone_forward);
+ *   lrmsd [B] = LRMSD(coords[b], target[b]) over the 3 lengths[b] atoms;
+ *   grad_angles [B][3][Lmax] = d(sum_b grad_lrmsd[b] LRMSD_b) / d(angles).
+ * The results equal tpl_backbone_forward, tpl_lrmsd_forward (P = B, Nmax =
+ * 3 Lmax, num_atoms = 3 lengths) and tpl_backbone_backward_lrmsd up to
+ * rounding.  target [B][3 Lmax][3] and grad_lrmsd [B] are inputs; a chain
+ * of at most one tile (threads x res_per_thread residues) is done by one CTA
+ * with its coordinates and target in shared memory, so a batch with Lmax
+ * at most one tile takes two kernel launches (work list, step).  Longer
+ * chains add an eigen-solve launch and a backward launch.  workspace:
+ * tpl_backbone_lrmsd_workspace_size(B, Lmax) bytes.  opts: launch shapes
+ * 128 x 2, 128 x 4 (default), 256 x 2, 256 x 4, 512 x 2; bwd_mode RECOMPUTE
+ * is rejected (the gradient is formed from the coordinates); the schedule
+ * and TPL_FLAG_PADDING_ZEROED as for the chain calls.  A chain whose LRMSD
+ * is 0 gets a zero gradient and sets TPL_STATUS_ZERO_LRMSD. */
+size_t tpl_backbone_lrmsd_workspace_size(int B, int Lmax);
+tpl_status tpl_backbone_lrmsd_step(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                   const float* target, const float* grad_lrmsd, float* coords, float* lrmsd,
+                                   float* grad_angles, void* workspace, size_t workspace_bytes,
+                                   const tpl_opts* opts, tpl_stream stream);
 
 /* Backbone form of tpl_fullatom_backward_lrmsd below (Eq. 2 instead of
  * Eq. 1): grad_angles = d(sum_b grad_lrmsd[b] LRMSD(coords[b], target[b])) /

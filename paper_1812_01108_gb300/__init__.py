@@ -95,6 +95,8 @@ def load_library():
             "tpl_fullatom_backward_lrmsd": ([P, P, P, I, I, I, P, P, P, P, Z, P, P, Z, O, P], I),
             "tpl_backbone_backward_lrmsd": ([P, P, I, I, P, P, P, P, Z, P, P, Z, O, P], I),
             "tpl_fullatom_lrmsd_workspace_size": ([I, I], Z),
+            "tpl_backbone_lrmsd_workspace_size": ([I, I], Z),
+            "tpl_backbone_lrmsd_step": ([P, P, I, I, P, P, P, P, P, P, Z, O, P], I),
             "tpl_fullatom_lrmsd_forward": ([P, P, P, I, I, I, P, P, P, P, Z, O, P], I),
             "tpl_fullatom_lrmsd_backward": ([P, P, I, I, I, P, P, P, P, P, P, P, Z, O, P], I),
             "tpl_lrmsd_forward": ([P, P, P, I, I, P, P, Z, P], I),
@@ -116,6 +118,9 @@ def load_library():
             "tpl_fullatom_autotune": ([P, P, P, I, I, I, P, P, P, P, P, Z, I, O, F, P], I),
             "tpl_lrmsd_forward_launches": ([I], I),
             "tpl_backbone_backward_quadratic": ([P, I, I, P, P, P, P], I),
+            "tpl_backbone_forward_o": ([P, P, I, I, P, P, P, Z, O, P], I),
+            "tpl_backbone_backward_o": ([P, P, I, I, P, P, P, P, P, P, Z, O, P], I),
+            "tpl_fullatom_backward_quadratic": ([P, P, I, I, I, P, P, P, P], I),
             "tpl_backbone_lrmsd_autotune": ([P, P, I, I, P, P, P, P, P, P, Z, P, P, Z, O, F, P], I),
             "tpl_fullatom_lrmsd_autotune": ([P, P, P, I, I, I, P, P, P, P, P, P, Z, P, P, Z, O, F, P], I),
             "tpl_last_error": ([], ctypes.c_char_p),
@@ -298,6 +303,23 @@ def tpl_fullatom_lrmsd_autotune(angles, seq, lengths, coords, num_atoms, target,
     return best, ms.value
 
 
+def tpl_backbone_lrmsd_workspace_size(B, Lmax):
+    return int(load_library().tpl_backbone_lrmsd_workspace_size(B, Lmax))
+
+
+def tpl_backbone_lrmsd_step(angles, lengths, target, grad_lrmsd, coords, lrmsd, grad_angles, workspace,
+                            opts=None, stream=None):
+    """Backbone training step on the LRMSD loss: fills coords, lrmsd and
+    grad_angles = d(sum_b grad_lrmsd[b] LRMSD_b) / d(angles) in one call."""
+    B, _, Lmax = angles.shape
+    _check("tpl_backbone_lrmsd_step", load_library().tpl_backbone_lrmsd_step(
+        _ptr(_cuda(angles, torch.float32, "angles")), _ptr(_cuda(lengths, torch.int32, "lengths")),
+        B, Lmax, _ptr(_cuda(target, torch.float32, "target")),
+        _ptr(_cuda(grad_lrmsd, torch.float32, "grad_lrmsd")), _ptr(_cuda(coords, torch.float32, "coords")),
+        _ptr(_cuda(lrmsd, torch.float32, "lrmsd")), _ptr(_cuda(grad_angles, torch.float32, "grad_angles")),
+        _ptr(workspace), workspace.numel() * workspace.element_size(), _opts(opts), _stream(angles, stream)))
+
+
 def tpl_fullatom_lrmsd_workspace_size(B, Lmax):
     return int(load_library().tpl_fullatom_lrmsd_workspace_size(B, Lmax))
 
@@ -330,6 +352,27 @@ def tpl_fullatom_lrmsd_backward(seq, lengths, coords, target, num_atoms, grad_lr
         _ptr(workspace), workspace.numel() * workspace.element_size(), _opts(opts), _stream(coords, stream)))
 
 
+def tpl_backbone_forward_o(angles, lengths, coords, o_coords, workspace, opts=None, stream=None):
+    """Backbone forward that also places each residue's carbonyl O (o_coords [B, Lmax, 3])."""
+    B, _, Lmax = angles.shape
+    _check("tpl_backbone_forward_o", load_library().tpl_backbone_forward_o(
+        _ptr(_cuda(angles, torch.float32, "angles")), _ptr(_cuda(lengths, torch.int32, "lengths")), B, Lmax,
+        _ptr(_cuda(coords, torch.float32, "coords")), _ptr(_cuda(o_coords, torch.float32, "o_coords")),
+        _ptr(workspace), workspace.numel() * workspace.element_size(), _opts(opts), _stream(angles, stream)))
+
+
+def tpl_backbone_backward_o(angles, lengths, coords, o_coords, grad_coords, grad_o, grad_angles, workspace,
+                            opts=None, stream=None):
+    """Backbone backward with the O atoms among the moved atoms (grad_o [B, Lmax, 3])."""
+    B, _, Lmax = angles.shape
+    _check("tpl_backbone_backward_o", load_library().tpl_backbone_backward_o(
+        _ptr(_cuda(angles, torch.float32, "angles")), _ptr(_cuda(lengths, torch.int32, "lengths")), B, Lmax,
+        _ptr(coords), _ptr(o_coords),
+        _ptr(_cuda(grad_coords, torch.float32, "grad_coords")), _ptr(_cuda(grad_o, torch.float32, "grad_o")),
+        _ptr(_cuda(grad_angles, torch.float32, "grad_angles")), _ptr(workspace),
+        workspace.numel() * workspace.element_size(), _opts(opts), _stream(angles, stream)))
+
+
 def tpl_backbone_backward_quadratic(lengths, coords, grad_coords, grad_angles, stream=None):
     """The paper's O(L^2) form of the backbone backward (every angle-atom term
     summed directly), a comparator for tpl_backbone_backward."""
@@ -337,6 +380,17 @@ def tpl_backbone_backward_quadratic(lengths, coords, grad_coords, grad_angles, s
     _check("tpl_backbone_backward_quadratic", load_library().tpl_backbone_backward_quadratic(
         _ptr(_cuda(lengths, torch.int32, "lengths")), B, Lmax, _ptr(_cuda(coords, torch.float32, "coords")),
         _ptr(_cuda(grad_coords, torch.float32, "grad_coords")),
+        _ptr(_cuda(grad_angles, torch.float32, "grad_angles")), _stream(grad_angles, stream)))
+
+
+def tpl_fullatom_backward_quadratic(seq, lengths, coords, grad_coords, grad_angles, stream=None):
+    """The paper's depth-first O(L^2) form of the full-atom backward (each angle
+    sums over the atoms it moves), a comparator for tpl_fullatom_backward."""
+    B, _, Lmax = grad_angles.shape
+    Amax = coords.shape[1]
+    _check("tpl_fullatom_backward_quadratic", load_library().tpl_fullatom_backward_quadratic(
+        _ptr(_cuda(seq, torch.uint8, "seq")), _ptr(_cuda(lengths, torch.int32, "lengths")), B, Lmax, Amax,
+        _ptr(_cuda(coords, torch.float32, "coords")), _ptr(_cuda(grad_coords, torch.float32, "grad_coords")),
         _ptr(_cuda(grad_angles, torch.float32, "grad_angles")), _stream(grad_angles, stream)))
 
 
@@ -530,6 +584,34 @@ class BackboneFn(torch.autograd.Function):
         return ga, None, None
 
 
+class BackboneOFn(torch.autograd.Function):
+    """Section 3 with each residue's carbonyl O: angles [B,3,Lmax] ->
+    (N/CA/C coordinates [B,3*Lmax,3], O [B,Lmax,3])."""
+
+    @staticmethod
+    def forward(ctx, angles, lengths, opts=None):
+        B, _, Lmax = angles.shape
+        coords = torch.empty((B, 3 * Lmax, 3), dtype=torch.float32, device=angles.device)
+        o = torch.empty((B, Lmax, 3), dtype=torch.float32, device=angles.device)
+        ws = _workspace(tpl_backbone_workspace_size(B, Lmax), angles.device)
+        tpl_backbone_forward_o(angles, lengths, coords, o, ws, opts)
+        ctx.save_for_backward(angles, lengths, coords, o, ws)
+        ctx.opts = opts
+        return coords, o
+
+    @staticmethod
+    def backward(ctx, grad_coords, grad_o):
+        angles, lengths, coords, o, ws = ctx.saved_tensors
+        if grad_coords is None:
+            grad_coords = torch.zeros_like(coords)
+        if grad_o is None:
+            grad_o = torch.zeros_like(o)
+        ga = torch.empty_like(angles)
+        tpl_backbone_backward_o(angles, lengths, coords, o, grad_coords.contiguous(), grad_o.contiguous(), ga,
+                                ws, ctx.opts)
+        return ga, None, None
+
+
 class FullAtomFn(torch.autograd.Function):
     """Section 2: angles [B,7,Lmax] + sequence -> heavy-atom coordinates [B,Amax,3]."""
 
@@ -577,6 +659,11 @@ class LRMSDFn(torch.autograd.Function):
 
 def backbone(angles, lengths, opts=None):
     return BackboneFn.apply(angles, lengths, opts)
+
+
+def backbone_with_o(angles, lengths, opts=None):
+    """Differentiable backbone with carbonyl O: (coords, o)."""
+    return BackboneOFn.apply(angles, lengths, opts)
 
 
 def fullatom(angles, seq, lengths, Amax, opts=None):

@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -47,94 +48,133 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 
 // ---------------------------------------------------------------------------
-// K8: the work list.  One CTA.  Chain order: batch order, or longest first by
-// a counting sort on 64 length buckets.  In packed mode a chain of at most one
-// tile goes instead to the class m = min(8, tile / slots), the number of such
-// chains that fit one tile (slots = length rounded up to the granule); the
-// classes follow the long chains, m ascending, and every m consecutive chains
-// of a class form one packed entry.  Then the entries per thread, an
-// exclusive scan, and the entries.  It also zeroes the forward look-back
-// flags and work counter.
+// K8: the work list.  CTA 0 builds it; the other CTAs of the launch zero the
+// forward look-back flags (and the fused step's done flags), which from one
+// SM alone would take longer than the sort.
+// Chain order: batch order, or longest first by a stable counting sort on 64
+// length buckets.  In packed mode a chain of at most one tile goes instead to
+// the class m = min(8, tile / slots), the number of such chains that fit one
+// tile (slots = length rounded up to the granule); the classes follow the
+// long chains, m ascending, and every m consecutive chains of a class form
+// one packed entry.  The sort: each warp counts the keys of a contiguous run
+// of chains, one scan over (key, warp) gives every warp its first position
+// per key, and each warp walks its run again placing its chains (so chains of
+// equal key keep batch order).  Then the entries per thread, an exclusive
+// scan, and the entries.  The work is issue-bound on one SM: every chain's
+// key is computed once and kept in shared memory with its length.
 // ---------------------------------------------------------------------------
 constexpr int kBuckets = 64;
 constexpr int kKeys = kBuckets + kMaxPack;
 constexpr int kSchedThreads = 1024;
 constexpr int kSchedWarps = kSchedThreads / 32;
-// The first kSchedCache chains' lengths and order entries are kept in shared
-// memory: the per-thread passes over the ordered chains read them in a
-// dependent sequence, which from global memory costs a round trip each.
-constexpr int kSchedCache = 8192;
+constexpr int kSchedCache = 16384;  // chains whose length, key and order entry stay in shared memory
+constexpr int kZeroPerCta = 4 * kSchedThreads;
+static_assert(kKeys < 127, "keys fit 7 bits with 127 left for lanes past the run");  // int4 words zeroed per flag-zeroing CTA and pass
+
+__device__ __forceinline__ int sched_key(int L, int Lmax, int tile, int mode, int granule) {
+    if (mode == kSchedPacked && L <= tile) {  // chains per packed tile, 1..kMaxPack
+        const int slots = (L + granule - 1) / granule * granule;
+        return kBuckets - 1 + (slots == 0 ? kMaxPack : min(kMaxPack, tile / slots));
+    }
+    const int bucket = Lmax < (1 << 24) ? (L * kBuckets) / (Lmax + 1)
+                                        : (int)(((long long)L * kBuckets) / ((long long)Lmax + 1));
+    return kBuckets - 1 - bucket;
+}
+
+__device__ __forceinline__ int sched_len(const int32_t* lengths, int b, int Lmax) {
+    const int L = lengths[b];
+    return L < 0 ? 0 : (L > Lmax ? Lmax : L);
+}
 
 __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* __restrict__ lengths,
                                                                  int B, int Lmax, int tile, int mode,
                                                                  int granule, bool balanced, ChainWs ws) {
-    __shared__ int hist[kKeys];
+    if (blockIdx.x > 0) {  // flag zeroing, 16 bytes at a time (the regions are 256-byte aligned)
+        const int n = B * ws.tmax;
+        const size_t stride = (size_t)(gridDim.x - 1) * kSchedThreads;
+        const size_t i0 = (size_t)(blockIdx.x - 1) * kSchedThreads + threadIdx.x;
+        int4* f4 = reinterpret_cast<int4*>(ws.fflag);
+        for (size_t i = i0; i < (size_t)n / 4; i += stride) f4[i] = make_int4(0, 0, 0, 0);
+        if (i0 < (size_t)(n & 3)) ws.fflag[(n & ~3) + i0] = 0;
+        if (ws.tdone) {  // fused training step: the backward's per-tile done flags
+            int4* d4 = reinterpret_cast<int4*>(ws.tdone);
+            for (size_t i = i0; i < (size_t)n / 4; i += stride) d4[i] = make_int4(0, 0, 0, 0);
+            if (i0 < (size_t)(n & 3)) ws.tdone[(n & ~3) + i0] = 0;
+        }
+        return;
+    }
     __shared__ int s_start[kKeys + 1];
-    __shared__ int s_run[kKeys];
-    __shared__ int s_wcnt[kSchedWarps][kKeys];
+    __shared__ int s_wcnt[kSchedWarps][kKeys];  // per warp: key counts, then next position per key
     __shared__ int s_part[33];
-    extern __shared__ int s_cache[];  // [ncache] lengths, [ncache] order entries
+    extern __shared__ int s_cache[];  // [ncache] lengths, [ncache] order entries, [ncache] keys (bytes)
     const int ncache = B < kSchedCache ? B : kSchedCache;
     int* s_len = s_cache;
     int* s_ord = s_cache + ncache;
+    unsigned char* s_key = reinterpret_cast<unsigned char*>(s_cache + 2 * ncache);
     int* order = ws.order;
-    for (int b = threadIdx.x; b < ncache; b += kSchedThreads) {
-        const int L = lengths[b];
-        s_len[b] = L < 0 ? 0 : (L > Lmax ? Lmax : L);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    // four independent loads in flight per thread, then the keys
+    for (int b0 = 0; b0 < ncache; b0 += 4 * kSchedThreads) {
+        int L[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int b = b0 + q * kSchedThreads + threadIdx.x;
+            L[q] = b < ncache ? sched_len(lengths, b, Lmax) : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int b = b0 + q * kSchedThreads + threadIdx.x;
+            if (b < ncache) {
+                s_len[b] = L[q];
+                s_key[b] = (unsigned char)sched_key(L[q], Lmax, tile, mode, granule);
+            }
+        }
     }
-    {  // zero the forward flags, 16 bytes at a time (the region is 256-byte aligned)
-        const int n = B * ws.tmax;
-        int4* f4 = reinterpret_cast<int4*>(ws.fflag);
-        for (int i = threadIdx.x; i < n / 4; i += kSchedThreads) f4[i] = make_int4(0, 0, 0, 0);
-        for (int i = (n & ~3) + threadIdx.x; i < n; i += kSchedThreads) ws.fflag[i] = 0;
-        if (ws.tdone)  // fused training step: the backward's per-tile done flags
-            for (int i = threadIdx.x; i < n; i += kSchedThreads) ws.tdone[i] = 0;
-    }
+    for (int i = threadIdx.x; i < kSchedWarps * kKeys; i += kSchedThreads) (&s_wcnt[0][0])[i] = 0;
     __syncthreads();
-    auto len = [&](int b) {
-        if (b < ncache) return s_len[b];
-        const int L = lengths[b];
-        return L < 0 ? 0 : (L > Lmax ? Lmax : L);
+    auto len = [&](int b) { return b < ncache ? s_len[b] : sched_len(lengths, b, Lmax); };
+    auto key = [&](int b) {
+        return b < ncache ? (int)s_key[b] : sched_key(sched_len(lengths, b, Lmax), Lmax, tile, mode, granule);
     };
     auto set_order = [&](int i, int b) {
         order[i] = b;
         if (i < ncache) s_ord[i] = b;
     };
     auto ord = [&](int i) { return i < ncache ? s_ord[i] : order[i]; };
-    auto is_short = [&](int b) { return mode == kSchedPacked && len(b) <= tile; };
-    auto pack_class = [&](int b) {  // chains per packed tile, 1..kMaxPack
-        const int slots = (len(b) + granule - 1) / granule * granule;
-        return slots == 0 ? kMaxPack : min(kMaxPack, tile / slots);
-    };
-    auto key = [&](int b) {
-        if (is_short(b)) return kBuckets + pack_class(b) - 1;
-        return kBuckets - 1 - (int)(((long long)len(b) * kBuckets) / ((long long)Lmax + 1));
-    };
     if (mode != kSchedBatch) {
-        // stable counting sort by key: chains of equal key keep batch order, so
-        // the schedule (and the packs) do not depend on timing
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const unsigned lt = (1u << lane) - 1u;
-        if (threadIdx.x < kKeys) {
-            hist[threadIdx.x] = 0;
-            s_run[threadIdx.x] = 0;
-        }
-        __syncthreads();
-        // key counts: one atomic per distinct key of a warp
-        for (int b0 = 0; b0 < B; b0 += kSchedThreads) {
-            const int b = b0 + threadIdx.x;
-            const int k = b < B ? key(b) : -1;
+        // the run of chains of this warp
+        const int per_w = (B + kSchedWarps - 1) / kSchedWarps;
+        const int w0 = warp * per_w, w1 = min(B, w0 + per_w);
+        // 1. key counts of the run: one shared-memory add per distinct key of 32 chains
+        for (int c0 = w0; c0 < w1; c0 += 32) {
+            const int b = c0 + lane;
+            const int k = b < w1 ? key(b) : -1;
             const unsigned peers = __match_any_sync(0xffffffffu, k);
-            if (k >= 0 && (peers & lt) == 0) atomicAdd(&hist[k], __popc(peers));
+            if (k >= 0 && (peers & lt) == 0) s_wcnt[warp][k] += __popc(peers);
+            __syncwarp();
         }
         __syncthreads();
-        if (threadIdx.x < 32) {  // exclusive scan of the key counts, kKeys <= 128: 4 per lane
+        // 2. per key, exclusive scan over the warps (warp w scans keys w, w + 32, ...)
+        for (int k = warp; k < kKeys; k += kSchedWarps) {
+            const int c = s_wcnt[lane][k];
+            int inc = c;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, inc, off);
+                if (lane >= off) inc += y;
+            }
+            s_wcnt[lane][k] = inc - c;
+            if (lane == 31) s_start[k] = inc;  // the key's count, scanned below
+        }
+        __syncthreads();
+        if (warp == 0) {  // exclusive scan of the key counts, kKeys <= 128: 4 per lane
             static_assert(kKeys <= 128, "key scan covers 128 keys");
             int c[4], sum = 0;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int k = 4 * lane + q;
-                c[q] = k < kKeys ? hist[k] : 0;
+                c[q] = k < kKeys ? s_start[k] : 0;
                 sum += c[q];
             }
             int inc = sum;
@@ -143,6 +183,7 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
                 const int y = __shfl_up_sync(0xffffffffu, inc, off);
                 if (lane >= off) inc += y;
             }
+            __syncwarp();
             int run = inc - sum;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -153,31 +194,16 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
             if (lane == 31) s_start[kKeys] = inc;
         }
         __syncthreads();
-        // positions, 1024 chains at a time: rank among equal keys = chains of
-        // that key in earlier rounds + in earlier warps of this round + in
-        // earlier lanes of this warp
-        for (int b0 = 0; b0 < B; b0 += kSchedThreads) {
-            const int b = b0 + threadIdx.x;
-            const int k = b < B ? key(b) : -1;
+        // 3. positions: key start + this warp's first position within the key
+        //    + the chains of the key earlier in the run
+        for (int c0 = w0; c0 < w1; c0 += 32) {
+            const int b = c0 + lane;
+            const int k = b < w1 ? key(b) : -1;
             const unsigned peers = __match_any_sync(0xffffffffu, k);
-            for (int i = threadIdx.x; i < kSchedWarps * kKeys; i += kSchedThreads) (&s_wcnt[0][0])[i] = 0;
-            __syncthreads();
-            if (k >= 0 && (peers & lt) == 0) s_wcnt[warp][k] = __popc(peers);
-            __syncthreads();
-            if (threadIdx.x < kKeys) {  // exclusive prefix over the warps, per key
-                int run = 0;
-                for (int w = 0; w < kSchedWarps; ++w) {
-                    const int c = s_wcnt[w][threadIdx.x];
-                    s_wcnt[w][threadIdx.x] = run;
-                    run += c;
-                }
-                hist[threadIdx.x] = run;  // this round's count of the key
-            }
-            __syncthreads();
-            if (k >= 0) set_order(s_start[k] + s_run[k] + s_wcnt[warp][k] + __popc(peers & lt), b);
-            __syncthreads();
-            if (threadIdx.x < kKeys) s_run[threadIdx.x] += hist[threadIdx.x];
-            __syncthreads();
+            if (k >= 0) set_order(s_start[k] + s_wcnt[warp][k] + __popc(peers & lt), b);
+            __syncwarp();
+            if (k >= 0 && (peers & lt) == 0) s_wcnt[warp][k] += __popc(peers);
+            __syncwarp();
         }
     } else {
         for (int b = threadIdx.x; b < B; b += kSchedThreads) set_order(b, b);
@@ -186,23 +212,20 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
     // each thread owns a contiguous run of the ordered chains
     const int per = (B + kSchedThreads - 1) / kSchedThreads;
     const int i0 = threadIdx.x * per, i1 = min(B, i0 + per);
-    auto ntiles = [&](int b) {
-        const int L = len(b);
+    auto ntiles = [&](int L) {
         if (balanced) return fa_num_tiles(L, tile);
         return L > 0 ? (L + tile - 1) / tile : 1;  // an empty chain still gets one tile (zero fill)
     };
     // entries that start at order position i: a long chain's tiles, or one
     // packed entry at every m-th chain of a class
-    auto entries = [&](int i) {
-        const int b = ord(i);
-        if (!is_short(b)) return ntiles(b);
-        const int m = pack_class(b);
-        return ((i - s_start[kBuckets + m - 1]) % m) == 0 ? 1 : 0;
+    auto entries = [&](int i, int b) {
+        const int k = key(b);
+        if (mode != kSchedPacked || k < kBuckets) return ntiles(len(b));
+        return ((i - s_start[k]) % (k - kBuckets + 1)) == 0 ? 1 : 0;
     };
     int mine = 0;
-    for (int i = i0; i < i1; ++i) mine += entries(i);
+    for (int i = i0; i < i1; ++i) mine += entries(i, ord(i));
     // block-wide exclusive scan of `mine`: warp shuffles, then the warp totals
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int inc = mine;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -226,13 +249,13 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
     int base = s_part[warp] + inc - mine;
     for (int i = i0; i < i1; ++i) {
         const int b = ord(i);
-        if (is_short(b)) {
-            const int m = pack_class(b);
-            const int k = kBuckets + m - 1;
+        const int k = key(b);
+        if (mode == kSchedPacked && k >= kBuckets) {
+            const int m = k - kBuckets + 1;
             if (((i - s_start[k]) % m) == 0) ws.tiles[base++] = make_int2(-1 - i, min(m, s_start[k + 1] - i));
         } else {
-            const int n = ntiles(b);
-            for (int k = 0; k < n; ++k) ws.tiles[base + k] = make_int2(b, k);
+            const int n = ntiles(len(b));
+            for (int q = 0; q < n; ++q) ws.tiles[base + q] = make_int2(b, q);
             base += n;
         }
     }
@@ -342,6 +365,10 @@ __global__ void selftest_wait_kernel(const int* flag) {
     if (threadIdx.x == 0) wait_flag(flag);
 }
 
+// Dynamic shared memory of the sort CTA for n cached chains: lengths and
+// order entries (ints), keys (bytes).
+static size_t sched_smem(int n) { return (size_t)n * (2 * sizeof(int) + 1); }
+
 cudaError_t launch_schedule(const int32_t* lengths, int B, int Lmax, int tile, int mode, int granule,
                             const ChainWs& ws, cudaStream_t s, bool balanced) {
     // the shared-memory limit is raised once per device (not during a capture after the first call)
@@ -352,12 +379,15 @@ cudaError_t launch_schedule(const int32_t* lengths, int B, int Lmax, int tile, i
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!raised[dev]) {
         e = cudaFuncSetAttribute(schedule_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 2 * kSchedCache * (int)sizeof(int));
+                                 (int)sched_smem(kSchedCache));
         if (e != cudaSuccess) return e;
         raised[dev] = true;
     }
-    const size_t smem = 2 * (size_t)(B < kSchedCache ? B : kSchedCache) * sizeof(int);
-    schedule_kernel<<<1, kSchedThreads, smem, s>>>(lengths, B, Lmax, tile, mode, granule, balanced, ws);
+    // CTA 0 sorts; the others zero the flags (one pass of kZeroPerCta words each)
+    const size_t words = ((size_t)B * ws.tmax + 3) / 4;
+    const int zero_ctas = (int)std::min<size_t>(148, (words + kZeroPerCta - 1) / kZeroPerCta);
+    schedule_kernel<<<1 + std::max(zero_ctas, 1), kSchedThreads, sched_smem(B < kSchedCache ? B : kSchedCache), s>>>(
+        lengths, B, Lmax, tile, mode, granule, balanced, ws);
     return cudaGetLastError();
 }
 
@@ -505,6 +535,8 @@ size_t tpl_backbone_workspace_size(int B, int Lmax) { return chain_ws_bytes(B, L
 
 size_t tpl_fullatom_workspace_size(int B, int Lmax) { return chain_ws_bytes(B, Lmax, true, false); }
 
+size_t tpl_backbone_lrmsd_workspace_size(int B, int Lmax) { return chain_ws_bytes(B, Lmax, false, true); }
+
 size_t tpl_lrmsd_workspace_size(int P, int Nmax) {
     if (P <= 0 || Nmax < 0) return 256;
     return lrmsd_ws_bytes(P, Nmax);
@@ -556,6 +588,50 @@ tpl_status tpl_backbone_backward(const float* angles, const int32_t* lengths, in
     return ok();
 }
 
+tpl_status tpl_backbone_forward_o(const float* angles, const int32_t* lengths, int B, int Lmax, float* coords,
+                                  float* o_coords, void* workspace, size_t workspace_bytes, const tpl_opts* opts,
+                                  tpl_stream stream) {
+    tpl_opts o = resolve(opts);
+    tpl_status st = check_opts(o);
+    if (st) return st;
+    const void* ptrs[4] = {angles, lengths, coords, o_coords};
+    if ((st = check_chain_args(B, Lmax, ptrs, 4))) return st;
+    if (B == 0) return ok();
+    LaunchCfg cfg = backbone_cfg(o);
+    if (!backbone_o_cfg_supported(cfg.threads, cfg.res_per_thread))
+        return fail(TPL_ERR_INVALID_ARG, "launch %d x %d not supported with the O atoms", cfg.threads,
+                    cfg.res_per_thread);
+    if ((st = check_ws(workspace, workspace_bytes, tpl_backbone_workspace_size(B, Lmax)))) return st;
+    cudaError_t e = launch_backbone_forward_o(angles, lengths, B, Lmax, coords, o_coords, sched_mode(o, true),
+                                              workspace, cfg, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "backbone_forward_o");
+    return ok();
+}
+
+tpl_status tpl_backbone_backward_o(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                   const float* coords, const float* o_coords, const float* grad_coords,
+                                   const float* grad_o, float* grad_angles, void* workspace, size_t workspace_bytes,
+                                   const tpl_opts* opts, tpl_stream stream) {
+    tpl_opts o = resolve(opts);
+    tpl_status st = check_opts(o);
+    if (st) return st;
+    const bool from_coords = o.bwd_mode == TPL_BWD_FROM_COORDS;
+    const void* ptrs[7] = {angles, lengths, grad_coords, grad_o, grad_angles,
+                           from_coords ? (const void*)coords : angles, from_coords ? (const void*)o_coords : angles};
+    if ((st = check_chain_args(B, Lmax, ptrs, 7))) return st;
+    if (B == 0) return ok();
+    LaunchCfg cfg = backbone_cfg(o);
+    if (!backbone_o_cfg_supported(cfg.threads, cfg.res_per_thread))
+        return fail(TPL_ERR_INVALID_ARG, "launch %d x %d not supported with the O atoms", cfg.threads,
+                    cfg.res_per_thread);
+    if ((st = check_ws(workspace, workspace_bytes, tpl_backbone_workspace_size(B, Lmax)))) return st;
+    cudaError_t e = launch_backbone_backward_o(angles, lengths, B, Lmax, coords, o_coords, grad_coords, grad_o,
+                                               grad_angles, from_coords, workspace, cfg,
+                                               reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "backbone_backward_o");
+    return ok();
+}
+
 tpl_status tpl_backbone_backward_quadratic(const int32_t* lengths, int B, int Lmax, const float* coords,
                                            const float* grad_coords, float* grad_angles, tpl_stream stream) {
     const void* ptrs[4] = {lengths, coords, grad_coords, grad_angles};
@@ -566,6 +642,21 @@ tpl_status tpl_backbone_backward_quadratic(const int32_t* lengths, int B, int Lm
     cudaError_t e = launch_backbone_backward_quadratic(lengths, B, Lmax, coords, grad_coords, grad_angles,
                                                        reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "backbone_backward_quadratic");
+    return ok();
+}
+
+tpl_status tpl_fullatom_backward_quadratic(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
+                                           const float* coords, const float* grad_coords, float* grad_angles,
+                                           tpl_stream stream) {
+    const void* ptrs[5] = {seq, lengths, coords, grad_coords, grad_angles};
+    tpl_status st = check_chain_args(B, Lmax, ptrs, 5);
+    if (st) return st;
+    if (Amax < 0 || Amax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Amax=%d must be a multiple of 4", Amax);
+    if (B == 0) return ok();
+    if (B > 65535) return fail(TPL_ERR_BAD_SHAPE, "B=%d above 65535 chains per call", B);
+    cudaError_t e = launch_fullatom_backward_quadratic(seq, lengths, B, Lmax, Amax, coords, grad_coords,
+                                                       grad_angles, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "fullatom_backward_quadratic");
     return ok();
 }
 
@@ -631,6 +722,30 @@ tpl_status tpl_fullatom_lrmsd_backward(const uint8_t* seq, const int32_t* length
                                                    Lmax, Amax, grad_angles, workspace, cfg,
                                                    reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "fullatom_lrmsd_backward");
+    return ok();
+}
+
+tpl_status tpl_backbone_lrmsd_step(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                   const float* target, const float* grad_lrmsd, float* coords, float* lrmsd,
+                                   float* grad_angles, void* workspace, size_t workspace_bytes,
+                                   const tpl_opts* opts, tpl_stream stream) {
+    tpl_opts o = resolve(opts);
+    tpl_status st = check_opts(o);
+    if (st) return st;
+    const void* ptrs[7] = {angles, lengths, target, grad_lrmsd, coords, lrmsd, grad_angles};
+    if ((st = check_chain_args(B, Lmax, ptrs, 7))) return st;
+    if (B == 0) return ok();
+    if (o.bwd_mode == TPL_BWD_RECOMPUTE)
+        return fail(TPL_ERR_INVALID_ARG, "the training step forms its gradient from the coordinates (no RECOMPUTE)");
+    LaunchCfg cfg = backbone_cfg(o);
+    if (!backbone_step_cfg_supported(cfg.threads, cfg.res_per_thread))
+        return fail(TPL_ERR_INVALID_ARG, "launch shape %d threads x %d residues not supported by the training step",
+                    cfg.threads, cfg.res_per_thread);
+    if ((st = check_ws(workspace, workspace_bytes, tpl_backbone_lrmsd_workspace_size(B, Lmax)))) return st;
+    cudaError_t e = launch_backbone_lrmsd_step(angles, lengths, B, Lmax, target, grad_lrmsd, coords, lrmsd,
+                                               grad_angles, sched_mode(o, true), workspace, cfg,
+                                               reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "backbone_lrmsd_step");
     return ok();
 }
 

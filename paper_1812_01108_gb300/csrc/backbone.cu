@@ -20,6 +20,7 @@
 #include "tables.h"
 #include "sched.cuh"
 #include "tpl_common.cuh"
+#include "lrmsd_solve.cuh"
 
 namespace tpl {
 
@@ -102,10 +103,12 @@ __device__ __forceinline__ void store_stage(float* s, const float (&v)[9 * K]) {
 __device__ __forceinline__ constexpr int row_of(int k) { return k == 0 ? 2 : (k == 1 ? 0 : 1); }
 
 // Product of the 3K transforms of a thread's residues j0 .. j0+K-1 (R_0 = I;
-// residues past L are identities) and the local atom positions it places.
-template <int K>
+// residues past L are identities) and the local atom positions it places;
+// WITH_O: also each residue's carbonyl O, rigid in the frame of C after psi.
+template <int K, bool WITH_O = false>
 __device__ __forceinline__ Rigid thread_product(const float* __restrict__ ang, int j0, int L, int Lmax,
-                                                const BackboneConst& bc, float3 (&pos)[3 * K]) {
+                                                const BackboneConst& bc, float3 (&pos)[3 * K],
+                                                float3* opos = nullptr) {
     float a[3][K];
     load_row<K>(ang, j0, Lmax, a[0]);
     load_row<K>(ang + Lmax, j0, Lmax, a[1]);
@@ -123,19 +126,74 @@ __device__ __forceinline__ Rigid thread_product(const float* __restrict__ ang, i
             }
             pos[3 * k + at] = A.t;
         }
+        if constexpr (WITH_O) opos[k] = point_apply(A, make_float3(bc.o[0], bc.o[1], bc.o[2]));
     }
     if (j0 < L) rigid_reortho(A);  // the scan composes orthonormal operands
     return A;
 }
 
+// A thread's K residues of carbonyl O (3K floats from residue j0 of a row of
+// [Lmax][3]), zeros past L; 16/8/4-byte stores for K = 4/2/1.
+template <int K>
+__device__ __forceinline__ void store_o(float* __restrict__ row, int j0, int L, int Lmax, const Rigid& E,
+                                        const float3 (&opos)[K]) {
+    if (j0 >= Lmax) return;
+    float v[3 * K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float3 r = point_apply(E, opos[k]);
+        const bool ok = j0 + k < L;
+        v[3 * k] = ok ? r.x : 0.f;
+        v[3 * k + 1] = ok ? r.y : 0.f;
+        v[3 * k + 2] = ok ? r.z : 0.f;
+    }
+    float* p = row + 3 * (size_t)j0;
+    if constexpr (K == 4) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            reinterpret_cast<float4*>(p)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    } else if constexpr (K == 2) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) reinterpret_cast<float2*>(p)[i] = make_float2(v[2 * i], v[2 * i + 1]);
+    } else {
+        p[0] = v[0]; p[1] = v[1]; p[2] = v[2];
+    }
+}
+
+// K floats of O (3K) of a thread's residues, zeros when !ok.
+template <int K>
+__device__ __forceinline__ void load_o(const float* __restrict__ p, bool ok, float (&v)[3 * K]) {
+    if (!ok) {
+#pragma unroll
+        for (int i = 0; i < 3 * K; ++i) v[i] = 0.f;
+        return;
+    }
+    if constexpr (K == 4) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float4 q = __ldg(reinterpret_cast<const float4*>(p) + i);
+            v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
+        }
+    } else if constexpr (K == 2) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const float2 q = __ldg(reinterpret_cast<const float2*>(p) + i);
+            v[2 * i] = q.x; v[2 * i + 1] = q.y;
+        }
+    } else {
+        v[0] = __ldg(p); v[1] = __ldg(p + 1); v[2] = __ldg(p + 2);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // K1: forward.  One tile (NT*K residues) per step of a persistent CTA.
+// WITH_O: also the carbonyl O of every residue into o_coords [B][Lmax][3].
 // ---------------------------------------------------------------------------
-template <int NT, int K>
+template <int NT, int K, bool WITH_O = false>
 __global__ void __launch_bounds__(NT, 768 / NT) bb_fwd_kernel(const float* __restrict__ angles,
                                                     const int32_t* __restrict__ lengths, int Lmax,
                                                     float* __restrict__ coords, ChainWs ws,
-                                                    BackboneConst bc) {
+                                                    BackboneConst bc, float* __restrict__ o_coords) {
     constexpr int NW = NT / 32;
     constexpr int TILE = NT * K;
     __shared__ RigidS s_rig[NW + 1];
@@ -157,10 +215,11 @@ __global__ void __launch_bounds__(NT, 768 / NT) bb_fwd_kernel(const float* __res
             const int b = ci >= 0 ? s_pack.b[ci] : 0;
             const int L = ci >= 0 ? s_pack.len[ci] : 0;
             const int j0 = ci >= 0 ? slot - s_pack.off[ci] : Lmax;  // Lmax: nothing to load
-            float3 pos[3 * K];
-            const Rigid A = thread_product<K>(angles + (size_t)b * 3 * Lmax, j0, L, Lmax, bc, pos);
+            float3 pos[3 * K], opos[K];
+            const Rigid A = thread_product<K, WITH_O>(angles + (size_t)b * 3 * Lmax, j0, L, Lmax, bc, pos, opos);
             const Rigid E = block_seg_scan_rigid<NT>(A, ci < 0 || j0 == 0, s_rig, s_cnt);
             const int requested = request_tile(ws.hdr + kHdrFwdNext);
+            if constexpr (WITH_O) store_o<K>(o_coords + (size_t)b * 3 * Lmax, j0, L, Lmax, E, opos);
             float vv[9 * K];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -195,8 +254,14 @@ __global__ void __launch_bounds__(NT, 768 / NT) bb_fwd_kernel(const float* __res
                                             e + 2 < n9 ? s_out[o9 + e + 2] : 0.f, 0.f);
                 }
                 const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (!(ws.flags & TPL_FLAG_PADDING_ZEROED))
+                if (!(ws.flags & TPL_FLAG_PADDING_ZEROED)) {
                     for (int q = ((n9 + 3) >> 2) + threadIdx.x; q < 9 * Lmax / 4; q += NT) dst[q] = z;
+                    if constexpr (WITH_O) {  // O rows past the chain's slots
+                        float* orow = o_coords + (size_t)s_pack.b[i] * 3 * Lmax;
+                        for (int q = 3 * (s_pack.off[i + 1] - s_pack.off[i]) + threadIdx.x; q < 3 * Lmax; q += NT)
+                            orow[q] = 0.f;
+                    }
+                }
             }
             v = next_tile(requested, &s_v);
             continue;
@@ -209,8 +274,8 @@ __global__ void __launch_bounds__(NT, 768 / NT) bb_fwd_kernel(const float* __res
         float* out = coords + (size_t)b * 9 * Lmax;
         const int tile0 = t * TILE;
         const int j0 = tile0 + threadIdx.x * K;
-        float3 pos[3 * K];
-        const Rigid A = thread_product<K>(ang, j0, L, Lmax, bc, pos);
+        float3 pos[3 * K], opos[K];
+        const Rigid A = thread_product<K, WITH_O>(ang, j0, L, Lmax, bc, pos, opos);
         Rigid E, Tot;
         int ce, ctot;
         block_scan_rigid_count<NT>(A, 0, s_rig, s_cnt, E, ce, Tot, ctot);
@@ -222,6 +287,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) bb_fwd_kernel(const float* __res
         const int requested = request_tile(ws.hdr + kHdrFwdNext);
         if (threadIdx.x == 0) store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, 0);
         E = rigid_mul(P, E);
+        if constexpr (WITH_O) store_o<K>(o_coords + (size_t)b * 3 * Lmax, j0, L, Lmax, E, opos);
         float vv[9 * K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -248,6 +314,10 @@ __global__ void __launch_bounds__(NT, 768 / NT) bb_fwd_kernel(const float* __res
             float4* o4 = reinterpret_cast<float4*>(out);
             for (int i = min(Lmax, T * TILE) * 9 / 4 + threadIdx.x; i < Lmax * 9 / 4; i += NT)
                 o4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if constexpr (WITH_O) {
+                float* orow = o_coords + (size_t)b * 3 * Lmax;
+                for (int i = 3 * min(Lmax, T * TILE) + threadIdx.x; i < 3 * Lmax; i += NT) orow[i] = 0.f;
+            }
         }
         v = next_tile(requested, &s_v);
     }
@@ -289,14 +359,29 @@ __device__ __forceinline__ bool ws_matches(const ChainWs& ws, int tile, int B, i
 // ---------------------------------------------------------------------------
 // LR (with FROM_COORDS): the coordinate gradient is the LRMSD gradient,
 // formed from the coordinates, the target and the LRMSD state.
-template <int NT, int K, bool FROM_COORDS, bool LR>
+// RES (with LR, the training step's chains of more than one tile): the LRMSD
+// gradient is formed without its 1 / (N LRMSD) factor, each tile also sums
+// its atoms' squared residuals, and the chain's first tile -- taken last --
+// waits for the chain's other tiles, forms LRMSD (FP64 over the tiles) and
+// rescales the chain's angle gradients.  Entries of whole chains are skipped
+// (the step kernel has done them).
+// WITH_O (not with LR): the carbonyl O atoms are among the moved atoms, O_j
+// after C_j (moved by every angle up to psi_j), with gradient grad_o and, for
+// FROM_COORDS, positions o_coords ([B][Lmax][3] each).
+template <int NT, int K, bool FROM_COORDS, bool LR, bool RES = false, bool WITH_O = false>
 __global__ void __launch_bounds__(NT, 512 / NT) bb_bwd_kernel(const float* __restrict__ angles,
                                                     const int32_t* __restrict__ lengths, int B,
                                                     int Lmax, const float* __restrict__ coords,
                                                     const float* __restrict__ grad_coords,
                                                     float* __restrict__ grad_angles, ChainWs ws,
-                                                    LrmsdGrad lg, BackboneConst bc) {
+                                                    LrmsdGrad lg, BackboneConst bc,
+                                                    const float* __restrict__ o_coords = nullptr,
+                                                    const float* __restrict__ grad_o = nullptr) {
     static_assert(FROM_COORDS || !LR, "the LRMSD gradient needs the coordinates");
+    static_assert(!(LR && WITH_O), "the LRMSD gradient covers N, CA and C only");
+    static_assert(LR || !RES, "the residual sums belong to the LRMSD gradient");
+    __shared__ float s_res[NT / 32];
+    __shared__ float s_scale;
     constexpr int NW = NT / 32;
     constexpr int TILE = NT * K;
     __shared__ RigidS s_rig[NW + 1];
@@ -339,9 +424,16 @@ __global__ void __launch_bounds__(NT, 512 / NT) bb_bwd_kernel(const float* __res
             t = T - 1 - ct.y;
             j0 = t * TILE + threadIdx.x * K;
         }
+        if constexpr (RES) {
+            if (pack || T == 1) {  // a whole chain: done by the step kernel
+                v = next_tile(request_tile(counter), &s_v);
+                continue;
+            }
+        }
         const int slot0 = b * ws.tmax;
         const float* ang = angles + (size_t)b * 3 * Lmax;
         const float* g_in = grad_coords + (size_t)b * 9 * Lmax;
+        float res_acc = 0.f;  // RES: this thread's squared residuals
         int requested = 0;
         float* ga = grad_angles + (size_t)b * 3 * Lmax;
 
@@ -357,18 +449,22 @@ __global__ void __launch_bounds__(NT, 512 / NT) bb_bwd_kernel(const float* __res
             const float3 u2 = make_float3(__ldg(st + 6), __ldg(st + 7), __ldg(st + 8));
             const float3 xc = make_float3(__ldg(st + 9), __ldg(st + 10), __ldg(st + 11));
             const float3 yc = make_float3(__ldg(st + 12), __ldg(st + 13), __ldg(st + 14));
-            const float w = __ldg(lg.grad_lrmsd + b) * __ldg(st + 15);
+            const float w = __ldg(lg.grad_lrmsd + b) * (RES ? 1.f : __ldg(st + 15));
 #pragma unroll
             for (int q = 0; q < 3 * K; ++q) {
                 const float3 xp = f3_sub(make_float3(x[3 * q], x[3 * q + 1], x[3 * q + 2]), xc);
                 const float3 yp = f3_sub(make_float3(y[3 * q], y[3 * q + 1], y[3 * q + 2]), yc);
-                g[3 * q] = w * (yp.x - f3_dot(u0, xp));
-                g[3 * q + 1] = w * (yp.y - f3_dot(u1, xp));
-                g[3 * q + 2] = w * (yp.z - f3_dot(u2, xp));
+                const float3 d = make_float3(yp.x - f3_dot(u0, xp), yp.y - f3_dot(u1, xp), yp.z - f3_dot(u2, xp));
+                g[3 * q] = w * d.x;
+                g[3 * q + 1] = w * d.y;
+                g[3 * q + 2] = w * d.z;
+                if (RES && j0 + q / 3 < L) res_acc += f3_dot(d, d);
             }
         } else {
             load_atoms<K>(g_in + 9 * (size_t)min(j0, Lmax - K), j0 < Lmax, g);
         }
+        float go[WITH_O ? 3 * K : 1];  // the thread's O gradients
+        if constexpr (WITH_O) load_o<K>(grad_o + (size_t)b * 3 * Lmax + 3 * (size_t)min(j0, Lmax - K), j0 < Lmax, go);
         Sum6 own = sum6_zero();
         float gr[3][K];
         // (sum r x g, sum g) over the later atoms of the chain, from the block
@@ -382,7 +478,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) bb_bwd_kernel(const float* __res
                 if (threadIdx.x == NT - 32) publish_suffix_agg(ws, slot0 + t, total);
                 after = sum6_add(after, gather_suffix(ws, slot0, t, T));  // every warp gathers it
             }
-            requested = request_tile(counter);  // after the last wait of this tile
+            // after the last wait of this tile (the step's first tile waits
+            // once more, at its end, and asks then)
+            if (!(RES && t == 0)) requested = request_tile(counter);
             return after;
         };
         if constexpr (!FROM_COORDS) {
@@ -412,6 +510,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) bb_bwd_kernel(const float* __res
                         own.c = f3_add(own.c, f3_cross(M.t, gi));
                         own.g = f3_add(own.g, gi);
                     }
+                    if constexpr (WITH_O) {  // M: the frame of C after psi
+                        const float3 ro = point_apply(M, make_float3(bc.o[0], bc.o[1], bc.o[2]));
+                        const float3 gi = make_float3(go[3 * k], go[3 * k + 1], go[3 * k + 2]);
+                        own.c = f3_add(own.c, f3_cross(ro, gi));
+                        own.g = f3_add(own.g, gi);
+                    }
                 }
             }
             // pass 2: gradients, atoms ascending with S = sum over atoms >= current
@@ -434,6 +538,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) bb_bwd_kernel(const float* __res
                     }
                     gr[row_of(at)][k] = val;
                 }
+                if constexpr (WITH_O) {  // O_j, after C_j
+                    if (j < L) {
+                        const float3 ro = point_apply(M, make_float3(bc.o[0], bc.o[1], bc.o[2]));
+                        const float3 gi = make_float3(go[3 * k], go[3 * k + 1], go[3 * k + 2]);
+                        S.c = f3_sub(S.c, f3_cross(ro, gi));
+                        S.g = f3_sub(S.g, gi);
+                    }
+                }
             }
         } else {
             const float* r_in = coords + (size_t)b * 9 * Lmax;
@@ -449,6 +561,18 @@ __global__ void __launch_bounds__(NT, 512 / NT) bb_bwd_kernel(const float* __res
                     own.c = f3_add(own.c, f3_cross(ri, gi));
                     own.g = f3_add(own.g, gi);
                 }
+            }
+            float ro[WITH_O ? 3 * K : 1];
+            if constexpr (WITH_O) {
+                load_o<K>(o_coords + (size_t)b * 3 * Lmax + 3 * (size_t)min(j0, Lmax - K), j0 < Lmax, ro);
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    if (j0 + k < L) {
+                        const float3 oi = make_float3(ro[3 * k], ro[3 * k + 1], ro[3 * k + 2]);
+                        const float3 gi = make_float3(go[3 * k], go[3 * k + 1], go[3 * k + 2]);
+                        own.c = f3_add(own.c, f3_cross(oi, gi));
+                        own.g = f3_add(own.g, gi);
+                    }
             }
             Sum6 S = sum6_add(later_sums(own), own);
 #pragma unroll
@@ -472,6 +596,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) bb_bwd_kernel(const float* __res
                     prev = ri;
                     gr[row_of(at)][k] = val;
                 }
+                if constexpr (WITH_O) {  // O_j, after C_j
+                    if (j < L) {
+                        const float3 oi = make_float3(ro[3 * k], ro[3 * k + 1], ro[3 * k + 2]);
+                        const float3 gi = make_float3(go[3 * k], go[3 * k + 1], go[3 * k + 2]);
+                        S.c = f3_sub(S.c, f3_cross(oi, gi));
+                        S.g = f3_sub(S.g, gi);
+                    }
+                }
             }
         }
         store_row<K>(ga, j0, Lmax, gr[0]);
@@ -493,6 +625,43 @@ __global__ void __launch_bounds__(NT, 512 / NT) bb_bwd_kernel(const float* __res
                 ga[i] = 0.f;
                 ga[Lmax + i] = 0.f;
                 ga[2 * Lmax + i] = 0.f;
+            }
+        }
+        if constexpr (RES) {
+            // this tile's residual sum, then "done" once every thread's
+            // gradient writes are in
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) res_acc += __shfl_xor_sync(0xffffffffu, res_acc, o);
+            if ((threadIdx.x & 31) == 0) s_res[threadIdx.x >> 5] = res_acc;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float tot = 0.f;
+                for (int w2 = 0; w2 < NT / 32; ++w2) tot += s_res[w2];
+                ws.tres[slot0 + t] = tot;
+                __threadfence();
+                flag_release(ws.tdone + slot0 + t, 1);
+            }
+            if (t == 0) {
+                // the chain's LRMSD from its tiles' residual sums (fixed order,
+                // FP64), then the factor 1 / (N LRMSD) on all its gradients
+                if (threadIdx.x == 0) {
+                    double sum = 0.0;
+                    for (int tp = 0; tp < T; ++tp) {
+                        if (tp > 0) wait_flag(ws.tdone + slot0 + tp);
+                        sum += (double)__ldcg(ws.tres + slot0 + tp);
+                    }
+                    float lr, scale;
+                    lrmsd_from_sum(sum, 3 * L, lr, scale);
+                    lg.lrmsd_out[b] = lr;
+                    s_scale = scale;
+                }
+                __syncthreads();
+                const float sc = s_scale;
+                for (int i = threadIdx.x; i < 3 * L; i += NT) {
+                    float* q = ga + (i / L) * Lmax + (i % L);
+                    *q = __ldcg(q) * sc;
+                }
+                requested = request_tile(counter);
             }
         }
         v = next_tile(requested, &s_v);
@@ -547,6 +716,376 @@ __global__ void __launch_bounds__(kQNT) bb_bwd_quadratic_kernel(const int32_t* _
         const int j = q / 3, at = q % 3;
         const float val = (q > 0 && q < na) ? f3_dot(u, c) : 0.f;
         grad_angles[(size_t)b * 3 * Lmax + row_of(at) * Lmax + j] = val;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K1s: the backbone training step on the LRMSD loss (Section 4 chained into
+// Eq. 2): coordinates, LRMSD_b and the gradient of sum_b w_b LRMSD_b with
+// respect to the angles.  A work-list entry that holds whole chains (a pack
+// of short chains, or a chain of one tile) runs the whole step in its CTA
+// with the chains' coordinates and target atoms in shared memory: forward
+// scan, the 17 LRMSD moments of each chain, the eigen-solve (one quad of
+// warp 0 per chain), the residual sum and LRMSD (FP64 over the threads),
+// each atom's gradient w_b (y' - U x') / (N LRMSD), and the segmented suffix
+// scan of Eq. 2.  HBM traffic per residue: angles in (12 B), target in (36),
+// coordinates out (36), angle gradient out (12).  A tile of a longer chain
+// only runs the forward and reduces its tile's moments; the eigen-solve and
+// the backward of such chains follow in two more launches.
+// ---------------------------------------------------------------------------
+
+// Sums over the threads of each pack member (sid = member index, -1 for none)
+// of F values: member i's totals in tot[i * F .. i * F + F).  Segments are
+// contiguous thread ranges: a shuffle suffix scan within each warp (lanes of
+// equal sid), the head lane of each segment in a warp writes the warp's
+// partial, and the partials are added over the warps in order.  Fixed order,
+// two barriers.  s_part holds NW * kMaxPack * F values.
+template <int NT, int F, typename T>
+__device__ __forceinline__ void pack_member_sums(T (&v)[F], int sid, T* s_part, T* tot, int m) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int so = __shfl_down_sync(0xffffffffu, sid, off);
+#pragma unroll
+        for (int q = 0; q < F; ++q) {
+            const T y = __shfl_down_sync(0xffffffffu, v[q], off);
+            if (lane + off < 32 && so == sid) v[q] += y;
+        }
+    }
+    const int sp = __shfl_up_sync(0xffffffffu, sid, 1);
+    const bool head = sid >= 0 && (lane == 0 || sp != sid);
+    T* mine = s_part + (size_t)warp * kMaxPack * F;
+    for (int i = lane; i < kMaxPack * F; i += 32) mine[i] = T(0);
+    __syncwarp();
+    if (head)
+#pragma unroll
+        for (int q = 0; q < F; ++q) mine[sid * F + q] = v[q];
+    __syncthreads();
+    for (int i = threadIdx.x; i < m * F; i += NT) {
+        T x = T(0);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) x += s_part[(size_t)w * kMaxPack * F + i];
+        tot[i] = x;
+    }
+    __syncthreads();
+}
+
+// Copies n floats from global `src` (16-byte aligned) to shared `dst` at a
+// float offset that may not be a multiple of 4.
+template <int NT>
+__device__ __forceinline__ void stage_in(float* dst, const float* __restrict__ src, int n) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    const int full = n >> 2;
+    if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+        float4* d4 = reinterpret_cast<float4*>(dst);
+        for (int q = threadIdx.x; q < full; q += NT) d4[q] = __ldg(s4 + q);
+    } else {
+        for (int q = threadIdx.x; q < full; q += NT) {
+            const float4 v = __ldg(s4 + q);
+            dst[4 * q] = v.x; dst[4 * q + 1] = v.y; dst[4 * q + 2] = v.z; dst[4 * q + 3] = v.w;
+        }
+    }
+    for (int i = 4 * full + threadIdx.x; i < n; i += NT) dst[i] = __ldg(src + i);
+}
+
+// Writes each pack member's row of n9 = 9 len floats from the stage (slot
+// offsets o9 = 9 off) to `out` rows of 9 Lmax floats, with the zero padding
+// past it unless the caller keeps the padding zero.
+template <int NT>
+__device__ __forceinline__ void store_pack_rows(float* __restrict__ out, const float* s_out, const PackS& pk,
+                                                int m, int Lmax, bool write_padding) {
+    for (int i = 0; i < m; ++i) {
+        const int n9 = 9 * pk.len[i], o9 = 9 * pk.off[i];
+        float4* dst = reinterpret_cast<float4*>(out + (size_t)pk.b[i] * 9 * Lmax);
+        const int full = n9 >> 2;
+        if ((o9 & 3) == 0) {
+            const float4* src = reinterpret_cast<const float4*>(s_out + o9);
+            for (int q = threadIdx.x; q < full; q += NT) dst[q] = src[q];
+        } else {
+            for (int q = threadIdx.x; q < full; q += NT) {
+                const float* e = s_out + o9 + 4 * q;
+                dst[q] = make_float4(e[0], e[1], e[2], e[3]);
+            }
+        }
+        if ((n9 & 3) && threadIdx.x == 0) {
+            const int e = 4 * full;
+            dst[full] = make_float4(s_out[o9 + e], e + 1 < n9 ? s_out[o9 + e + 1] : 0.f,
+                                    e + 2 < n9 ? s_out[o9 + e + 2] : 0.f, 0.f);
+        }
+        if (write_padding)
+            for (int q = ((n9 + 3) >> 2) + threadIdx.x; q < 9 * Lmax / 4; q += NT)
+                dst[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// The 17 moments of atoms y (coordinates) against x (target): sum dx, sum dy,
+// sum dx dy^T, sum |dx|^2, sum |dy|^2 with dx = x - x0, dy = y (the chain's
+// first atom is the origin, R_0 = I).
+__device__ __forceinline__ void add_moments(float (&m)[kMom], float3 x, float3 x0, float3 dy) {
+    const float3 dx = f3_sub(x, x0);
+    m[0] += dx.x; m[1] += dx.y; m[2] += dx.z;
+    m[3] += dy.x; m[4] += dy.y; m[5] += dy.z;
+    m[6] = fmaf(dx.x, dy.x, m[6]); m[7] = fmaf(dx.x, dy.y, m[7]); m[8] = fmaf(dx.x, dy.z, m[8]);
+    m[9] = fmaf(dx.y, dy.x, m[9]); m[10] = fmaf(dx.y, dy.y, m[10]); m[11] = fmaf(dx.y, dy.z, m[11]);
+    m[12] = fmaf(dx.z, dy.x, m[12]); m[13] = fmaf(dx.z, dy.y, m[13]); m[14] = fmaf(dx.z, dy.z, m[14]);
+    m[15] += f3_dot(dx, dx);
+    m[16] += f3_dot(dy, dy);
+}
+
+__device__ __forceinline__ float3 ld3(const float* p) { return make_float3(p[0], p[1], p[2]); }
+
+template <int NT, int K>
+constexpr int step_min_blocks() { return NT >= 512 ? 1 : (NT >= 256 ? 2 : 3); }
+
+// Dynamic shared memory of K1s: the tile's coordinates and target atoms.
+template <int NT, int K>
+constexpr size_t step_smem() { return 2 * (size_t)9 * NT * K * sizeof(float); }
+
+template <int NT, int K>
+__global__ void __launch_bounds__(NT, step_min_blocks<NT, K>()) bb_step_kernel(
+    const float* __restrict__ angles, const int32_t* __restrict__ lengths, int Lmax,
+    const float* __restrict__ target, const float* __restrict__ grad_lrmsd, float* __restrict__ coords,
+    float* __restrict__ lrmsd, float* __restrict__ grad_angles, ChainWs ws, BackboneConst bc) {
+    constexpr int NW = NT / 32;
+    constexpr int TILE = NT * K;
+    __shared__ RigidS s_rig[NW + 1];
+    __shared__ int s_cnt[NW + 1];
+    __shared__ float s6[6 * (NW + 1)];
+    __shared__ int s_v;
+    __shared__ PackS s_pack;
+    __shared__ float s_part[NW * kMaxPack * kMom];
+    __shared__ float s_tot[kMaxPack * kMom];
+    __shared__ double s_dpart[NW * kMaxPack];
+    __shared__ double s_dtot[kMaxPack];
+    __shared__ __align__(16) float s_state[kMaxPack * 16];
+    __shared__ float s_w[kMaxPack];
+    extern __shared__ float4 s_dyn[];
+    float* s_out = reinterpret_cast<float*>(s_dyn);  // [9 TILE] coordinates of the tile
+    float* s_tgt = s_out + 9 * TILE;                 // [9 TILE] target atoms of the tile
+    const bool write_padding = !(ws.flags & TPL_FLAG_PADDING_ZEROED);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    const int ntiles = ws.hdr[kHdrTiles];
+    int v = take_tile(ws.hdr + kHdrFwdNext, &s_v);
+    while (v < ntiles) {
+        const int2 ct = ws.tiles[v];
+        int m = 1, T = 1, L = 0, b = 0;
+        if (ct.x < 0) {
+            m = ct.y;
+            load_pack<K>(ws, lengths, Lmax, -1 - ct.x, m, s_pack);
+        } else {
+            b = ct.x;
+            L = clamp_length(lengths, b, Lmax);
+            T = L > 0 ? (L + TILE - 1) / TILE : 1;
+            if (T == 1) {  // one whole chain: a pack of one
+                if (threadIdx.x == 0) {
+                    s_pack.b[0] = b;
+                    s_pack.len[0] = L;
+                    s_pack.off[0] = 0;
+                    s_pack.off[1] = (L + K - 1) / K * K;
+                }
+                __syncthreads();
+            }
+        }
+        if (T == 1) {
+            // ---- the whole step for the entry's chains ----
+            const int slot = threadIdx.x * K;
+            const int ci = pack_member(s_pack, m, slot);
+            b = ci >= 0 ? s_pack.b[ci] : 0;
+            L = ci >= 0 ? s_pack.len[ci] : 0;
+            const int j0 = ci >= 0 ? slot - s_pack.off[ci] : Lmax;  // Lmax: nothing to load or store
+            for (int i = 0; i < m; ++i)
+                stage_in<NT>(s_tgt + 9 * s_pack.off[i], target + (size_t)s_pack.b[i] * 9 * Lmax, 9 * s_pack.len[i]);
+            float3 pos[3 * K];
+            const Rigid A = thread_product<K>(angles + (size_t)b * 3 * Lmax, j0, L, Lmax, bc, pos);
+            const Rigid E = block_seg_scan_rigid<NT>(A, ci < 0 || j0 == 0, s_rig, s_cnt);
+            const int requested = request_tile(ws.hdr + kHdrFwdNext);
+            {
+                float vv[9 * K];
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+#pragma unroll
+                    for (int at = 0; at < 3; ++at) {
+                        const float3 r = point_apply(E, pos[3 * k + at]);
+                        vv[9 * k + 3 * at + 0] = r.x;
+                        vv[9 * k + 3 * at + 1] = r.y;
+                        vv[9 * k + 3 * at + 2] = r.z;
+                    }
+                store_stage<K>(s_out + threadIdx.x * 9 * K, vv);
+            }
+            __syncthreads();
+            store_pack_rows<NT>(coords, s_out, s_pack, m, Lmax, write_padding);
+            const float* my_r = s_out + 9 * slot;  // this thread's atoms
+            const float* my_x = s_tgt + 9 * slot;
+            const int nres = ci >= 0 ? max(0, min(K, L - j0)) : 0;  // real residues of this thread
+            // moments of each chain
+            {
+                float mom[kMom];
+#pragma unroll
+                for (int q = 0; q < kMom; ++q) mom[q] = 0.f;
+                if (nres > 0) {
+                    const float3 x0 = ld3(s_tgt + 9 * s_pack.off[ci]);
+#pragma unroll
+                    for (int q = 0; q < 3 * K; ++q)
+                        if (q < 3 * nres) add_moments(mom, ld3(my_x + 3 * q), x0, ld3(my_r + 3 * q));
+                }
+                pack_member_sums<NT, kMom>(mom, ci, s_part, s_tot, m);
+            }
+            // eigen-solve: member i on lanes 4 i .. 4 i + 3 of warp 0
+            if (warp == 0) {
+                const int i = lane >> 2;
+                const bool active = i < m;
+                const int ii = active ? i : 0;
+                float S[kSlot];
+#pragma unroll
+                for (int q = 0; q < kSlot; ++q) S[q] = q < kMom ? s_tot[ii * kMom + q] : 0.f;
+                const float* x0p = s_tgt + 9 * s_pack.off[ii];
+                const float* y0p = s_out + 9 * s_pack.off[ii];
+                const float x0[3] = {x0p[0], x0p[1], x0p[2]}, y0[3] = {y0p[0], y0p[1], y0p[2]};
+                quad_eigen_solve(S, x0, y0, 3 * s_pack.len[ii], lane & 3, lane, active, s_state + 16 * ii);
+            }
+            __syncthreads();
+            // residuals and LRMSD of each chain (FP32 per thread, FP64 over the threads)
+            const PairState ps = load_state_shared(s_state + 16 * (ci >= 0 ? ci : 0));
+            {
+                float acc = 0.f;
+#pragma unroll
+                for (int q = 0; q < 3 * K; ++q)
+                    if (q < 3 * nres) {
+                        const float3 d = residual(ps, ld3(my_x + 3 * q), ld3(my_r + 3 * q));
+                        acc += f3_dot(d, d);
+                    }
+                double dv[1] = {(double)acc};
+                pack_member_sums<NT, 1>(dv, ci, s_dpart, s_dtot, m);
+            }
+            if (threadIdx.x < m) {
+                const int i = threadIdx.x;
+                float lr, scale;
+                lrmsd_from_sum(s_dtot[i], 3 * s_pack.len[i], lr, scale);
+                lrmsd[s_pack.b[i]] = lr;
+                s_w[i] = __ldg(grad_lrmsd + s_pack.b[i]) * scale;
+            }
+            __syncthreads();
+            // each atom's gradient, then the backward of Eq. 2 (segmented suffix scan)
+            const float w = ci >= 0 ? s_w[ci] : 0.f;
+            float g[9 * K];
+            Sum6 own = sum6_zero();
+#pragma unroll
+            for (int q = 0; q < 3 * K; ++q) {
+                float3 gi = make_float3(0.f, 0.f, 0.f);
+                if (q < 3 * nres) {
+                    const float3 ri = ld3(my_r + 3 * q);
+                    gi = f3_scale(w, residual(ps, ld3(my_x + 3 * q), ri));
+                    own.c = f3_add(own.c, f3_cross(ri, gi));
+                    own.g = f3_add(own.g, gi);
+                }
+                g[3 * q] = gi.x; g[3 * q + 1] = gi.y; g[3 * q + 2] = gi.z;
+            }
+            const bool tail = ci < 0 || slot + K >= s_pack.off[ci + 1];
+            Sum6 S = sum6_add(block_seg_suffix_sum6<NT>(own, tail, s6, s_cnt), own);
+            float gr[3][K];
+            float3 prev = (j0 > 0 && ci >= 0) ? ld3(my_r - 3) : make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+#pragma unroll
+                for (int at = 0; at < 3; ++at) {
+                    const int q = 3 * k + at;
+                    float val = 0.f;
+                    const float3 ri = ld3(my_r + 3 * q);
+                    if (k < nres) {
+                        const float3 gi = make_float3(g[3 * q], g[3 * q + 1], g[3 * q + 2]);
+                        if (j0 + k > 0 || at > 0) {
+                            float3 u = f3_sub(ri, prev);
+                            u = f3_scale(rsqrtf(f3_dot(u, u)), u);
+                            val = f3_dot(u, f3_sub(S.c, f3_cross(ri, S.g)));
+                        }
+                        S.c = f3_sub(S.c, f3_cross(ri, gi));
+                        S.g = f3_sub(S.g, gi);
+                    }
+                    prev = ri;
+                    gr[row_of(at)][k] = val;
+                }
+            }
+            float* ga = grad_angles + (size_t)b * 3 * Lmax;
+            store_row<K>(ga, j0, Lmax, gr[0]);
+            store_row<K>(ga + Lmax, j0, Lmax, gr[1]);
+            store_row<K>(ga + 2 * Lmax, j0, Lmax, gr[2]);
+            if (write_padding)  // rows past each chain's slots
+                for (int i = 0; i < m; ++i) {
+                    float* gi = grad_angles + (size_t)s_pack.b[i] * 3 * Lmax;
+                    for (int j = s_pack.off[i + 1] - s_pack.off[i] + threadIdx.x; j < Lmax; j += NT) {
+                        gi[j] = 0.f;
+                        gi[Lmax + j] = 0.f;
+                        gi[2 * Lmax + j] = 0.f;
+                    }
+                }
+            v = next_tile(requested, &s_v);
+            continue;
+        }
+        // ---- a tile of a longer chain: forward and the tile's moments ----
+        const int t = ct.y;
+        const int slot0 = b * ws.tmax;
+        float* out = coords + (size_t)b * 9 * Lmax;
+        const int tile0 = t * TILE;
+        const int j0 = tile0 + threadIdx.x * K;
+        const int nst = min(TILE, L - tile0);  // residues of the chain in this tile
+        stage_in<NT>(s_tgt, target + (size_t)b * 9 * Lmax + 9 * (size_t)tile0, 9 * nst);
+        float3 pos[3 * K];
+        const Rigid A = thread_product<K>(angles + (size_t)b * 3 * Lmax, j0, L, Lmax, bc, pos);
+        Rigid E, Tot;
+        int ce, ctot;
+        block_scan_rigid_count<NT>(A, 0, s_rig, s_cnt, E, ce, Tot, ctot);
+        if (threadIdx.x == NT - 32) publish_prefix_agg(ws, slot0 + t, Tot, 0);
+        int pc;
+        const Rigid P = gather_prefix(ws, slot0, t, pc);  // every warp gathers it
+        const int requested = request_tile(ws.hdr + kHdrFwdNext);
+        E = rigid_mul(P, E);
+        {
+            float vv[9 * K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const bool valid = j0 + k < L;
+#pragma unroll
+                for (int at = 0; at < 3; ++at) {
+                    const float3 r = point_apply(E, pos[3 * k + at]);
+                    vv[9 * k + 3 * at + 0] = valid ? r.x : 0.f;
+                    vv[9 * k + 3 * at + 1] = valid ? r.y : 0.f;
+                    vv[9 * k + 3 * at + 2] = valid ? r.z : 0.f;
+                }
+            }
+            store_stage<K>(s_out + threadIdx.x * 9 * K, vv);
+        }
+        __syncthreads();
+        const int nres_out = write_padding ? min(TILE, Lmax - tile0) : min(TILE, (nst + 3) & ~3);  // multiple of 4
+        {
+            float4* dst = reinterpret_cast<float4*>(out + 9 * (size_t)tile0);
+            const float4* src = reinterpret_cast<const float4*>(s_out);
+            for (int i = threadIdx.x; i < nres_out * 9 / 4; i += NT) dst[i] = src[i];
+            if (t == T - 1 && write_padding) {  // zero the residues past the last tile
+                float4* o4 = reinterpret_cast<float4*>(out);
+                for (int i = min(Lmax, T * TILE) * 9 / 4 + threadIdx.x; i < Lmax * 9 / 4; i += NT)
+                    o4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        {
+            float mom[kMom];
+#pragma unroll
+            for (int q = 0; q < kMom; ++q) mom[q] = 0.f;
+            const int nres = max(0, min(K, L - j0));
+            if (nres > 0) {
+                const float* tg = target + (size_t)b * 9 * Lmax;
+                const float3 x0 = make_float3(__ldg(tg), __ldg(tg + 1), __ldg(tg + 2));
+                const float* my_r = s_out + 9 * threadIdx.x * K;
+                const float* my_x = s_tgt + 9 * threadIdx.x * K;
+#pragma unroll
+                for (int q = 0; q < 3 * K; ++q)
+                    if (q < 3 * nres) add_moments(mom, ld3(my_x + 3 * q), x0, ld3(my_r + 3 * q));
+            }
+            pack_member_sums<NT, kMom>(mom, nres > 0 ? 0 : -1, s_part, s_tot, 1);
+            if (threadIdx.x < kMom) ws.tmom[(size_t)(slot0 + t) * kSlot + threadIdx.x] = s_tot[threadIdx.x];
+        }
+        v = next_tile(requested, &s_v);
     }
 }
 
@@ -626,7 +1165,7 @@ template <int NT, int K>
 cudaError_t fwd_t(const float* angles, const int32_t* lengths, int B, int Lmax, float* coords,
                   const ChainWs& ws, cudaStream_t s) {
     const int grid = persistent_grid((const void*)bb_fwd_kernel<NT, K>, NT, 0);
-    bb_fwd_kernel<NT, K><<<grid, NT, 0, s>>>(angles, lengths, Lmax, coords, ws, backbone_const());
+    bb_fwd_kernel<NT, K><<<grid, NT, 0, s>>>(angles, lengths, Lmax, coords, ws, backbone_const(), nullptr);
     return cudaGetLastError();
 }
 
@@ -650,7 +1189,126 @@ cudaError_t bwd_t(const float* angles, const int32_t* lengths, int B, int Lmax,
     return cudaGetLastError();
 }
 
+template <int NT, int K>
+cudaError_t fwd_o_t(const float* angles, const int32_t* lengths, int Lmax, float* coords, float* o_coords,
+                    const ChainWs& ws, cudaStream_t s) {
+    const int grid = persistent_grid((const void*)bb_fwd_kernel<NT, K, true>, NT, 0);
+    bb_fwd_kernel<NT, K, true><<<grid, NT, 0, s>>>(angles, lengths, Lmax, coords, ws, backbone_const(), o_coords);
+    return cudaGetLastError();
+}
+
+template <int NT, int K>
+cudaError_t bwd_o_t(const float* angles, const int32_t* lengths, int B, int Lmax, const float* coords,
+                    const float* o_coords, const float* grad_coords, const float* grad_o, float* grad_angles,
+                    bool from_coords, const ChainWs& ws, cudaStream_t s) {
+    const LrmsdGrad none{nullptr, nullptr, nullptr};
+    if (from_coords) {
+        const int grid = persistent_grid((const void*)bb_bwd_kernel<NT, K, true, false, false, true>, NT, 0);
+        bb_bwd_kernel<NT, K, true, false, false, true><<<grid, NT, 0, s>>>(
+            angles, lengths, B, Lmax, coords, grad_coords, grad_angles, ws, none, backbone_const(), o_coords, grad_o);
+    } else {
+        const int grid = persistent_grid((const void*)bb_bwd_kernel<NT, K, false, false, false, true>, NT, 0);
+        bb_bwd_kernel<NT, K, false, false, false, true><<<grid, NT, 0, s>>>(
+            angles, lengths, B, Lmax, coords, grad_coords, grad_angles, ws, none, backbone_const(), nullptr, grad_o);
+    }
+    return cudaGetLastError();
+}
+
+template <int NT, int K>
+cudaError_t step_t(const float* angles, const int32_t* lengths, int B, int Lmax, const float* target,
+                   const float* grad_lrmsd, float* coords, float* lrmsd, float* grad_angles, const ChainWs& ws,
+                   cudaStream_t s) {
+    constexpr int TILE = NT * K;
+    const size_t smem = step_smem<NT, K>();
+    static bool done[64] = {false};
+    cudaError_t e = smem_attr_once(bb_step_kernel<NT, K>, (int)smem, done);
+    if (e != cudaSuccess) return e;
+    const int grid = persistent_grid((const void*)bb_step_kernel<NT, K>, NT, smem);
+    bb_step_kernel<NT, K><<<grid, NT, smem, s>>>(angles, lengths, Lmax, target, grad_lrmsd, coords, lrmsd,
+                                                 grad_angles, ws, backbone_const());
+    e = cudaGetLastError();
+    if (e != cudaSuccess || Lmax <= TILE) return e;  // every chain was whole: the step is done
+    // chains of more than one tile: eigen-solve from the tile moments, then
+    // the backward with the residual sums
+    e = reset_backward_flags(ws, s);
+    if (e != cudaSuccess) return e;
+    e = launch_lrmsd_solve_tiles(coords, target, nullptr, B, 3 * Lmax, ws.tmom, ws.tmax, lengths, TILE, Lmax,
+                                 ws.lstate, s, false, 2);
+    if (e != cudaSuccess) return e;
+    const LrmsdGrad lg{target, ws.lstate, grad_lrmsd, lrmsd, nullptr};
+    const int bgrid = persistent_grid((const void*)bb_bwd_kernel<NT, K, true, true, true>, NT, 0);
+    bb_bwd_kernel<NT, K, true, true, true><<<bgrid, NT, 0, s>>>(angles, lengths, B, Lmax, coords, nullptr,
+                                                                grad_angles, ws, lg, backbone_const());
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+bool backbone_step_cfg_supported(int threads, int k) {
+    return (threads == 128 && (k == 2 || k == 4)) || (threads == 256 && (k == 2 || k == 4)) ||
+           (threads == 512 && k == 2);
+}
+
+bool backbone_o_cfg_supported(int threads, int k) {
+    return (threads == 128 && (k == 1 || k == 2 || k == 4)) || (threads == 256 && k == 4);
+}
+
+#define TPL_BB_O_DISPATCH(FN, ...)                                            \
+    switch (cfg.threads * 8 + cfg.res_per_thread) {                           \
+        case 128 * 8 + 1: return FN<128, 1>(__VA_ARGS__);                     \
+        case 128 * 8 + 2: return FN<128, 2>(__VA_ARGS__);                     \
+        case 128 * 8 + 4: return FN<128, 4>(__VA_ARGS__);                     \
+        case 256 * 8 + 4: return FN<256, 4>(__VA_ARGS__);                     \
+        default: return cudaErrorInvalidValue;                                \
+    }
+
+cudaError_t launch_backbone_forward_o(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                      float* coords, float* o_coords, int sched_mode, void* workspace,
+                                      LaunchCfg cfg, cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    ChainWs ws;
+    chain_ws_layout(workspace, B, Lmax, &ws);
+    ws.flags = cfg.flags;
+    cudaError_t e = launch_schedule(lengths, B, Lmax, cfg.threads * cfg.res_per_thread, sched_mode,
+                                    cfg.res_per_thread, ws, s);
+    if (e != cudaSuccess) return e;
+    TPL_BB_O_DISPATCH(fwd_o_t, angles, lengths, Lmax, coords, o_coords, ws, s)
+}
+
+cudaError_t launch_backbone_backward_o(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                       const float* coords, const float* o_coords, const float* grad_coords,
+                                       const float* grad_o, float* grad_angles, bool from_coords,
+                                       void* workspace, LaunchCfg cfg, cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    ChainWs ws;
+    chain_ws_layout(workspace, B, Lmax, &ws);
+    ws.flags = cfg.flags;
+    cudaError_t e = reset_backward_flags(ws, s);
+    if (e != cudaSuccess) return e;
+    TPL_BB_O_DISPATCH(bwd_o_t, angles, lengths, B, Lmax, coords, o_coords, grad_coords, grad_o, grad_angles,
+                      from_coords, ws, s)
+}
+
+cudaError_t launch_backbone_lrmsd_step(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                       const float* target, const float* grad_lrmsd, float* coords,
+                                       float* lrmsd, float* grad_angles, int sched_mode, void* workspace,
+                                       LaunchCfg cfg, cudaStream_t s) {
+    if (B == 0) return cudaSuccess;
+    ChainWs ws;
+    chain_ws_layout(workspace, B, Lmax, &ws, false, true);
+    ws.flags = cfg.flags;
+    cudaError_t e = launch_schedule(lengths, B, Lmax, cfg.threads * cfg.res_per_thread, sched_mode,
+                                    cfg.res_per_thread, ws, s);
+    if (e != cudaSuccess) return e;
+    switch (cfg.threads * 8 + cfg.res_per_thread) {
+        case 128 * 8 + 2: return step_t<128, 2>(angles, lengths, B, Lmax, target, grad_lrmsd, coords, lrmsd, grad_angles, ws, s);
+        case 128 * 8 + 4: return step_t<128, 4>(angles, lengths, B, Lmax, target, grad_lrmsd, coords, lrmsd, grad_angles, ws, s);
+        case 256 * 8 + 2: return step_t<256, 2>(angles, lengths, B, Lmax, target, grad_lrmsd, coords, lrmsd, grad_angles, ws, s);
+        case 256 * 8 + 4: return step_t<256, 4>(angles, lengths, B, Lmax, target, grad_lrmsd, coords, lrmsd, grad_angles, ws, s);
+        case 512 * 8 + 2: return step_t<512, 2>(angles, lengths, B, Lmax, target, grad_lrmsd, coords, lrmsd, grad_angles, ws, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 bool backbone_cfg_supported(int threads, int k) {
     return (threads == 64 || threads == 128 || threads == 256 || threads == 512) &&

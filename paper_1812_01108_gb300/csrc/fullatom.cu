@@ -1021,6 +1021,130 @@ __global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ an
 }
 
 // ---------------------------------------------------------------------------
+// K4q: the paper's depth-first form of Eq. 1 as a comparator: each angle's
+// derivative sums, over every atom that the angle moves, the lever term
+// g_k . (u x (r_k - p)) = u . ((r_k - p) x g_k), from the forward's
+// coordinates -- O(L) work per backbone angle, O(L^2) per chain.  One thread
+// per (residue, angle): kQRes residues x 7 angles per CTA; the CTA walks the
+// chain's atoms from its first residue on in shared-memory tiles.  An angle
+// of residue j moves every atom of the later residues (phi, psi, omega) and,
+// in residue j: phi and omega all atoms, psi the C and O group, chi_k the
+// side-chain groups k and beyond.  Axes and pivots as in K4'.
+// ---------------------------------------------------------------------------
+constexpr int kQNT = 128;
+constexpr int kQRes = kQNT / 7;  // 18 residues, 126 angle slots
+
+__global__ void __launch_bounds__(kQNT) fa_bwd_quadratic_kernel(
+    const uint8_t* __restrict__ seq, const int32_t* __restrict__ lengths, int Lmax, int Amax,
+    const float* __restrict__ coords, const float* __restrict__ grad_coords, float* __restrict__ grad_angles,
+    const __grid_constant__ FaTable tab) {
+    __shared__ float3 s_r[kQNT], s_g[kQNT];
+    __shared__ int s_first[kQRes + 1];  // first atom of the CTA's residues (and past the last)
+    __shared__ int s_red[kQNT / 32];
+    const int b = blockIdx.y;
+    const int L = clamp_length(lengths, b, Lmax);
+    const int j0 = blockIdx.x * kQRes;
+    const uint8_t* sq = seq + (size_t)b * Lmax;
+    auto type_of = [&](int j) {
+        const int c = sq[j];
+        if (c >= kNumTypes) {
+            flag_status(TPL_STATUS_BAD_RESIDUE);
+            return kGlyCode;
+        }
+        return c;
+    };
+    // atoms before residue j0 (block sum), then the CTA's residues (thread 0)
+    int before = 0;
+    for (int j = threadIdx.x; j < min(j0, L); j += kQNT) before += tab.n_atoms[type_of(j)];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = before;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int a = 0;
+        for (int w = 0; w < kQNT / 32; ++w) a += s_red[w];
+        for (int q = 0; q <= kQRes; ++q) {
+            s_first[q] = a;
+            if (j0 + q < L) a += tab.n_atoms[type_of(j0 + q)];
+        }
+    }
+    __syncthreads();
+    const int a_begin = s_first[0];
+    int a_end = 0;  // atoms of the chain
+    {
+        int rest = 0;
+        for (int j = j0 + kQRes + threadIdx.x; j < L; j += kQNT) rest += tab.n_atoms[type_of(j)];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rest += __shfl_xor_sync(0xffffffffu, rest, o);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = rest;
+        __syncthreads();
+        for (int w = 0; w < kQNT / 32; ++w) a_end += s_red[w];
+        a_end += s_first[kQRes];
+    }
+    const bool over = a_end > Amax;  // flagged by the forward; nothing is read past Amax
+    const int jl = threadIdx.x / 7, ang = threadIdx.x % 7;  // ang: 0 phi, 1 psi, 2 omega, 3.. chi
+    const int j = j0 + jl;
+    const float* r_in = coords + (size_t)b * Amax * 3;
+    const float* g_in = grad_coords + (size_t)b * Amax * 3;
+    bool active = jl < kQRes && j < L && !over;
+    int ty = kGlyCode, a0 = 0, a1 = 0;
+    unsigned groups = 0x7fu;  // rigid groups of residue j the angle moves (bit g: group g)
+    float3 u = make_float3(0.f, 0.f, 0.f), p = u;
+    if (active) {
+        ty = type_of(j);
+        a0 = s_first[jl];
+        a1 = s_first[jl + 1];
+        auto at = [&](int i) { return make_float3(r_in[3 * i], r_in[3 * i + 1], r_in[3 * i + 2]); };
+        if (ang == 0) {  // phi: N -> CA, all but N
+            p = at(a0 + 1);
+            u = f3_sub(p, at(a0));
+            groups = 0x7eu;
+        } else if (ang == 1) {  // psi: CA -> C, the C and O group
+            p = at(a0 + 2);
+            u = f3_sub(p, at(a0 + 1));
+            groups = 0x04u;
+        } else if (ang == 2) {  // omega: C_{j-1} -> N_j (omega_0: R_0 = I, no angle)
+            active = j > 0;
+            if (active) {
+                p = at(a0);
+                u = f3_sub(p, at(a0 - tab.n_atoms[type_of(j - 1)] + 2));
+            }
+        } else {  // chi_k, k = ang - 3: origin of group k-1 (CA for k = 0) -> origin of group k
+            const int k = ang - 3;
+            active = k < tab.n_chi[ty];
+            if (active) {
+                p = at(a0 + tab.origin[ty][k]);
+                u = f3_sub(p, at(a0 + (k == 0 ? 1 : tab.origin[ty][k - 1])));
+                groups = 0x7fu & ~((1u << (3 + k)) - 1u);
+            }
+        }
+        if (active) u = f3_scale(rsqrtf(f3_dot(u, u)), u);
+    }
+    // chi angles move atoms of their own residue only
+    const int a_stop = active ? (ang >= 3 ? a1 : a_end) : 0;
+    float3 c = make_float3(0.f, 0.f, 0.f);  // sum over moved atoms of (r_k - p) x g_k
+    const int a_last = over ? a_begin : a_end;
+    for (int t0 = a_begin; t0 < a_last; t0 += kQNT) {
+        const int k = t0 + threadIdx.x;
+        __syncthreads();
+        s_r[threadIdx.x] = k < a_last ? make_float3(r_in[3 * k], r_in[3 * k + 1], r_in[3 * k + 2])
+                                      : make_float3(0.f, 0.f, 0.f);
+        s_g[threadIdx.x] = k < a_last ? make_float3(g_in[3 * k], g_in[3 * k + 1], g_in[3 * k + 2])
+                                      : make_float3(0.f, 0.f, 0.f);
+        __syncthreads();
+        const int lo = max(t0, a0), hi = min(t0 + kQNT, a_stop);
+        for (int m = lo; m < hi; ++m) {
+            // atoms of residue j: only the groups the angle moves
+            if (m < a1 && !((groups >> tab.atom_grp[ty][m - a0]) & 1u)) continue;
+            c = f3_add(c, f3_cross(f3_sub(s_r[m - t0], p), s_g[m - t0]));
+        }
+    }
+    if (jl < kQRes && j < Lmax)
+        grad_angles[(size_t)b * 7 * Lmax + (size_t)ang * Lmax + j] = active ? f3_dot(u, c) : 0.f;
+}
+
+// ---------------------------------------------------------------------------
 // K7: plain FP64 per-chain forms (one CTA per chain, thread 0 serial).
 // ---------------------------------------------------------------------------
 struct Frame64 {
@@ -1200,17 +1324,6 @@ __global__ void fa_bwd_ref64_kernel(const uint8_t* __restrict__ seq,
 
 // The dynamic shared-memory limit is raised once per device and kernel, so no
 // attribute call happens during a stream capture after the first launch.
-template <typename K>
-cudaError_t smem_attr_once(K kernel, int bytes, bool* done_per_device) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (done_per_device[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) done_per_device[dev] = true;
-    return e;
-}
 
 template <int NT, int K, bool LM>
 cudaError_t fa_fwd_t(const float* angles, const uint8_t* seq, const int32_t* lengths, int Lmax,
@@ -1372,7 +1485,7 @@ cudaError_t launch_fullatom_lrmsd_forward(const float* angles, const uint8_t* se
     e = fa_forward_shape<true>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, cfg, s, target);
     if (e != cudaSuccess) return e;
     return launch_lrmsd_solve_tiles(coords, target, num_atoms, B, Amax, ws.tmom, ws.tmax, lengths, tile,
-                                    Lmax, ws.lstate, s);
+                                    Lmax, ws.lstate, s, true, 1);
 }
 
 cudaError_t launch_fullatom_lrmsd_backward(const uint8_t* seq, const int32_t* lengths, const float* coords,
@@ -1387,6 +1500,16 @@ cudaError_t launch_fullatom_lrmsd_backward(const uint8_t* seq, const int32_t* le
     if (e != cudaSuccess) return e;
     LrmsdGrad lg{target, ws.lstate, grad_lrmsd, lrmsd, num_atoms};
     return fa_backward_shape<true, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, cfg, s);
+}
+
+cudaError_t launch_fullatom_backward_quadratic(const uint8_t* seq, const int32_t* lengths, int B, int Lmax,
+                                              int Amax, const float* coords, const float* grad_coords,
+                                              float* grad_angles, cudaStream_t s) {
+    if (B == 0 || Lmax == 0) return cudaSuccess;
+    const dim3 grid((Lmax + kQRes - 1) / kQRes, B);
+    fa_bwd_quadratic_kernel<<<grid, kQNT, 0, s>>>(seq, lengths, Lmax, Amax, coords, grad_coords, grad_angles,
+                                                  fa_table());
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fullatom_backward_ref64(const double* angles, const uint8_t* seq,

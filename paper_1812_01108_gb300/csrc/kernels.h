@@ -39,6 +39,18 @@ cudaError_t launch_backbone_backward(const float* angles, const int32_t* lengths
                                      float* grad_angles, bool from_coords, void* workspace,
                                      LaunchCfg cfg, cudaStream_t s);
 
+// K1 / K2 with the carbonyl O of every residue: o_coords [B][Lmax][3] out of
+// the forward; the backward adds grad_o on those atoms (o_coords read with
+// from_coords).
+bool backbone_o_cfg_supported(int threads, int res_per_thread);
+cudaError_t launch_backbone_forward_o(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                      float* coords, float* o_coords, int sched_mode, void* workspace,
+                                      LaunchCfg cfg, cudaStream_t s);
+cudaError_t launch_backbone_backward_o(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                       const float* coords, const float* o_coords, const float* grad_coords,
+                                       const float* grad_o, float* grad_angles, bool from_coords,
+                                       void* workspace, LaunchCfg cfg, cudaStream_t s);
+
 // K2 with the LRMSD gradient formed in place of a coordinate-gradient input
 // (P = B pairs of Nmax = 3 Lmax atoms).
 cudaError_t launch_backbone_backward_lrmsd(const float* angles, const int32_t* lengths, int B, int Lmax,
@@ -59,6 +71,12 @@ cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
                                      float* grad_angles, bool from_coords, void* workspace,
                                      LaunchCfg cfg, cudaStream_t s);
 
+// K4q: the paper's depth-first O(L^2) form of Eq. 1 from the forward's
+// coordinates (comparator).
+cudaError_t launch_fullatom_backward_quadratic(const uint8_t* seq, const int32_t* lengths, int B, int Lmax,
+                                              int Amax, const float* coords, const float* grad_coords,
+                                              float* grad_angles, cudaStream_t s);
+
 // K4 with the LRMSD gradient formed in place of a coordinate-gradient input:
 // the gradient of sum_b grad_lrmsd[b] LRMSD(coords[b], target[b]).
 cudaError_t launch_fullatom_backward_lrmsd(const uint8_t* seq, const int32_t* lengths, int B, int Lmax,
@@ -68,12 +86,23 @@ cudaError_t launch_fullatom_backward_lrmsd(const uint8_t* seq, const int32_t* le
                                           cudaStream_t s);
 
 // The eigen-solve of K5 on per-tile moment partials (slot = chain * tiles_max
-// + tile, 20 floats each; tiles of `tile` residues of chain p): the fused
-// training step.  Writes the per-pair state (16 floats per pair).
+// + tile, 20 floats each; chain p cut into balanced full-atom tiles or into
+// tiles of `tile` residues): the fused training steps.  Writes the per-pair
+// state (16 floats per pair) of the chains of at least min_tiles tiles.
+// num_atoms null: chain p has 3 lengths[p] atoms (backbone).
 cudaError_t launch_lrmsd_solve_tiles(const float* input, const float* target, const int32_t* num_atoms,
                                      int P, int Nmax, const float* tile_moments, int tiles_max,
                                      const int32_t* lengths, int tile, int Lmax, float* state,
-                                     cudaStream_t s);
+                                     cudaStream_t s, bool balanced, int min_tiles);
+
+// Training step of the backbone model on the LRMSD loss (K1s, workspace of
+// chain_ws_bytes(B, Lmax, false, true)): coordinates, LRMSD per chain and the
+// gradient of sum_b grad_lrmsd[b] LRMSD_b.
+bool backbone_step_cfg_supported(int threads, int res_per_thread);
+cudaError_t launch_backbone_lrmsd_step(const float* angles, const int32_t* lengths, int B, int Lmax,
+                                       const float* target, const float* grad_lrmsd, float* coords,
+                                       float* lrmsd, float* grad_angles, int sched_mode, void* workspace,
+                                       LaunchCfg cfg, cudaStream_t s);
 
 // Fused training step on the full-atom model with the LRMSD loss (workspace of
 // chain_ws_bytes(B, Lmax, true, true)): forward = schedule, forward with

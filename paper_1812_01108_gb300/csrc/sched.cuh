@@ -373,6 +373,20 @@ __device__ __forceinline__ int next_tile(int requested, int* s_v) {
     return *s_v;
 }
 
+// Host side: raises a kernel's dynamic shared memory limit once per device
+// (not again during a graph capture after the first call).
+template <typename K>
+cudaError_t smem_attr_once(K kernel, int bytes, bool* done_per_device) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (done_per_device[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done_per_device[dev] = true;
+    return e;
+}
+
 // Host side: schedule kernel (api.cu).
 // Chain order of the schedule: batch order, longest first, or longest first
 // with the chains of at most one tile packed several per tile (granule =

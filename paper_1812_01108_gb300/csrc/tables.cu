@@ -217,6 +217,8 @@ void build() {
     F.rp_s = (float)D.rp_s;
     V3 o = frame_child(kOBond, kOAngle * kDeg, kODih * kDeg);
     F.o_r0 = make_float4((float)o.x, (float)o.y, (float)o.z, 3.f);
+    D.bb.o[0] = o.x; D.bb.o[1] = o.y; D.bb.o[2] = o.z;
+    F.bb.o[0] = (float)o.x; F.bb.o[1] = (float)o.y; F.bb.o[2] = (float)o.z;
 
     for (int t = 0; t < kNumTypes; ++t) {
         const ResDef& R = kRes[t];

@@ -17,9 +17,11 @@ constexpr int kGlyCode = 7;
 // 2 (C, psi) is R(angle, theta_k, d_k).
 struct BackboneConst {
     float ct[3], st[3], d[3];
+    float o[3];  // carbonyl O in the frame of C after psi (the full-atom tables' O)
 };
 struct BackboneConstD {
     double ct[3], st[3], d[3];
+    double o[3];
 };
 
 // FP32 table for the scan kernels.  Side-chain atoms are listed by group

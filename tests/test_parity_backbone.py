@@ -159,6 +159,61 @@ def test_autograd_function_and_gradcheck_direction():
     assert rel_err(host(A.grad), g64) <= GRAD_TOL
 
 
+@pytest.fixture(scope="module")
+def reference_o():
+    a, g = _inputs(LENGTHS, 61)
+    rng = np.random.default_rng(62)
+    go = workloads.upstream_grad((len(LENGTHS), a.shape[2], 3), rng, valid=LENGTHS)
+    c64, o64 = oracle.backbone_forward_o(a, LENGTHS)
+    return a, g, go, c64, o64, oracle.backbone_backward_o(a, LENGTHS, g, go)
+
+
+@pytest.mark.parametrize("threads,k,sched", [(128, 4, tpl.SCHED_PACKED), (128, 1, tpl.SCHED_PACKED),
+                                             (128, 2, tpl.SCHED_LONGEST_FIRST), (256, 4, tpl.SCHED_BATCH_ORDER)])
+@pytest.mark.parametrize("bwd", [tpl.BWD_FROM_COORDS, tpl.BWD_RECOMPUTE])
+def test_backbone_with_o_matches_the_oracle(reference_o, threads, k, sched, bwd):
+    """The carbonyl O placed in the scan and counted in the backward (O_j after
+    C_j), against the oracle; N/CA/C bit-identical to the plain forward."""
+    d = require_gpu()
+    a, g, go, c64, o64, g64 = reference_o
+    B, _, Lmax = a.shape
+    A, Ln = dev(a, d), dev(LENGTHS, d)
+    opts = {"threads": threads, "res_per_thread": k, "schedule": sched, "bwd_mode": bwd}
+    ws = torch.empty(tpl.tpl_backbone_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    c = torch.full((B, 3 * Lmax, 3), float("nan"), device=d)
+    o = torch.full((B, Lmax, 3), float("nan"), device=d)
+    tpl.tpl_backbone_forward_o(A, Ln, c, o, ws, opts)
+    ga = torch.full_like(A, float("nan"))
+    tpl.tpl_backbone_backward_o(A, Ln, c, o, dev(g, d), dev(go, d), ga, ws, opts)
+    c_plain = torch.full_like(c, float("nan"))
+    ws2 = torch.empty_like(ws)
+    tpl.tpl_backbone_forward(A, Ln, c_plain, ws2, opts)
+    torch.cuda.synchronize()
+    c, o, ga = host(c), host(o), host(ga)
+    assert np.array_equal(c, host(c_plain))
+    assert np.abs(o - o64).max() <= COORD_TOL and np.abs(c - c64).max() <= COORD_TOL
+    assert rel_err(ga, g64) <= GRAD_TOL
+    for b, L in enumerate(LENGTHS):
+        assert np.all(o[b, L:] == 0) and np.all(ga[b, :, L:] == 0)
+
+
+def test_backbone_with_o_autograd_and_rejected_shapes():
+    d = require_gpu()
+    lengths = np.array([40, 17, 1], np.int32)
+    a, g = _inputs(lengths, 5)
+    rng = np.random.default_rng(6)
+    go = workloads.upstream_grad((3, a.shape[2], 3), rng, valid=lengths)
+    A = dev(a, d).requires_grad_(True)
+    coords, o = tpl.backbone_with_o(A, dev(lengths, d))
+    ((coords * dev(g, d)).sum() + (o * dev(go, d)).sum()).backward()
+    assert rel_err(host(A.grad), oracle.backbone_backward_o(a, lengths, g, go)) <= GRAD_TOL
+    B, _, Lmax = a.shape
+    ws = torch.empty(tpl.tpl_backbone_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    with pytest.raises(tpl.TplError):
+        tpl.tpl_backbone_forward_o(A.detach(), dev(lengths, d), torch.empty((B, 3 * Lmax, 3), device=d),
+                                   torch.empty((B, Lmax, 3), device=d), ws, {"threads": 512, "res_per_thread": 2})
+
+
 @pytest.mark.parametrize("bwd", [tpl.BWD_FROM_COORDS, tpl.BWD_RECOMPUTE])
 def test_long_chains_precision_stress(bwd):
     """4 chains x 10000 residues (the precision-stress shape at reduced batch).
@@ -300,6 +355,90 @@ def test_fused_lrmsd_backward_equals_the_two_calls_and_the_oracle(threads, k, sc
     assert rel_err(f[m], ga64[m]) <= GRAD_TOL
     for b, L in enumerate(lengths):
         assert np.all(f[b, :, L:] == 0)
+
+
+def _step_inputs(seed, n=40, Lmax=900):
+    rng = np.random.default_rng(seed)
+    lengths = workloads.lengths_loguniform(n, 1, Lmax, rng)
+    lengths[:4] = [0, 1, 2, Lmax]
+    a, _ = _inputs(lengths, seed + 1, Lmax=Lmax)
+    ta = workloads.perturb_angles(a, lengths, rng)
+    return a, ta, lengths
+
+
+def _run_step(a, ta, lengths, opts, fill=0.0, w=None):
+    d = require_gpu()
+    B, _, Lmax = a.shape
+    A, Ln = dev(a, d), dev(lengths, d)
+    tgt = torch.zeros((B, 3 * Lmax, 3), device=d)
+    ws0 = torch.empty(tpl.tpl_backbone_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    tpl.tpl_backbone_forward(dev(ta, d), Ln, tgt, ws0)
+    if w is None:
+        w = np.linspace(-1.0, 2.0, B).astype(np.float32)
+    W = dev(w, d)
+    ws = torch.empty(tpl.tpl_backbone_lrmsd_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    coords = torch.full((B, 3 * Lmax, 3), fill, device=d)
+    lr = torch.full((B,), float("nan"), device=d)
+    ga = torch.full_like(A, fill)
+    tpl.tpl_backbone_lrmsd_step(A, Ln, tgt, W, coords, lr, ga, ws, opts)
+    torch.cuda.synchronize()
+    return host(coords), host(lr), host(ga), host(tgt), w
+
+
+@pytest.mark.parametrize("threads,k,sched", [(128, 4, tpl.SCHED_PACKED), (256, 4, tpl.SCHED_PACKED),
+                                             (128, 2, tpl.SCHED_LONGEST_FIRST), (512, 2, tpl.SCHED_PACKED),
+                                             (256, 2, tpl.SCHED_BATCH_ORDER)])
+def test_training_step_matches_the_separate_calls_and_the_oracle(threads, k, sched):
+    """tpl_backbone_lrmsd_step: chains done whole in one CTA (packs, one-tile
+    chains) and chains of several tiles (tile moments, eigen-solve, backward
+    with residual sums) against the three separate calls and the oracle chain
+    (Section 3 forward, Section 4 LRMSD and gradient, Eq. 2)."""
+    d = require_gpu()
+    a, ta, lengths = _step_inputs(51)
+    B, _, Lmax = a.shape
+    opts = {"threads": threads, "res_per_thread": k, "schedule": sched}
+    c, lr, ga, tgt, w = _run_step(a, ta, lengths, opts, fill=float("nan"))
+    # the separate calls
+    A, Ln = dev(a, d), dev(lengths, d)
+    ws = torch.empty(tpl.tpl_backbone_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    c2 = torch.zeros((B, 3 * Lmax, 3), device=d)
+    tpl.tpl_backbone_forward(A, Ln, c2, ws, opts)
+    na = dev((3 * lengths).astype(np.int32), d)
+    lr2 = torch.zeros((B,), device=d)
+    lr_ws = torch.empty(tpl.tpl_lrmsd_workspace_size(B, 3 * Lmax), dtype=torch.uint8, device=d)
+    T = dev(tgt, d)
+    tpl.tpl_lrmsd_forward(c2, T, na, lr2, lr_ws)
+    ga2 = torch.zeros_like(A)
+    tpl.tpl_backbone_backward_lrmsd(A, Ln, c2, T, dev(w, d), lr_ws, ga2, ws, opts)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(c)) and np.all(np.isfinite(ga)) and np.all(np.isfinite(lr))
+    assert np.abs(c - host(c2)).max() <= 1e-4
+    assert np.abs(lr - host(lr2)).max() <= 1e-5
+    m = lengths >= 2  # a one-residue chain is congruent to its target: no gradient
+    # both FP32 paths, their LRMSD moments summed in different orders
+    assert rel_err(ga[m], host(ga2)[m]) <= GRAD_TOL
+    # the oracle chain
+    assert np.abs(c - oracle.backbone_forward(a, lengths)).max() <= COORD_TOL
+    assert np.abs(lr - oracle.lrmsd_forward(c, tgt, 3 * lengths)).max() <= 1e-5
+    g64 = oracle.lrmsd_backward(w.astype(np.float64), c, tgt, 3 * lengths)
+    assert rel_err(ga[m], oracle.backbone_backward(a, lengths, g64)[m]) <= GRAD_TOL
+    for b, L in enumerate(lengths):
+        assert np.all(c[b, 3 * L:] == 0) and np.all(ga[b, :, L:] == 0)
+
+
+def test_training_step_padding_flag_and_shape_checks():
+    """FLAG_PADDING_ZEROED leaves the real residues unchanged; RECOMPUTE and
+    unsupported shapes are rejected before any launch."""
+    a, ta, lengths = _step_inputs(53, n=24, Lmax=600)
+    o = {"threads": 128, "res_per_thread": 4}
+    c0, lr0, g0, _, _ = _run_step(a, ta, lengths, o)
+    c1, lr1, g1, _, _ = _run_step(a, ta, lengths, dict(o, flags=tpl.FLAG_PADDING_ZEROED), fill=float("nan"))
+    assert np.array_equal(lr0, lr1)
+    for b, L in enumerate(lengths):
+        assert np.array_equal(c1[b, :3 * L], c0[b, :3 * L]) and np.array_equal(g1[b, :, :L], g0[b, :, :L])
+    for bad in ({"bwd_mode": tpl.BWD_RECOMPUTE}, {"threads": 64, "res_per_thread": 1}, {"threads": 512, "res_per_thread": 4}):
+        with pytest.raises(tpl.TplError):
+            _run_step(a, ta, lengths, bad)
 
 
 def test_packed_schedule_is_deterministic():

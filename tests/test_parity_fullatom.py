@@ -332,6 +332,29 @@ def test_fused_training_step_matches_the_separate_calls_and_the_oracle(shape):
         assert np.all(host(g2)[b, :, L:] == 0)
 
 
+def test_quadratic_comparator_matches_the_scan_and_the_oracle(reference):
+    """tpl_fullatom_backward_quadratic (the paper's depth-first O(L^2) sums of
+    Eq. 1) against the scan backward and the oracle, chains of every length of
+    the reference batch (several CTAs of 18 residues, ragged ends)."""
+    d = require_gpu()
+    a, seq, g, Amax, c64, na64, g64 = reference
+    c32, na32, ga_scan = _run_fp32(a, seq, LENGTHS, g, Amax, {"threads": 256, "res_per_thread": 1}, True)
+    ga = torch.full((len(LENGTHS), 7, a.shape[2]), float("nan"), device=d)
+    tpl.tpl_fullatom_backward_quadratic(dev(seq, d), dev(LENGTHS, d), dev(c32, d), dev(g, d), ga)
+    torch.cuda.synchronize()
+    q = host(ga)
+    assert np.all(np.isfinite(q))
+    assert rel_err(q, g64) <= GRAD_TOL
+    assert rel_err(q, ga_scan) <= GRAD_TOL
+    for b, L in enumerate(LENGTHS):
+        assert np.all(q[b, :, L:] == 0)
+        for j in range(L):
+            nchi = tpl.residue_table(int(seq[b, j]))[2]
+            assert np.all(q[b, 3 + nchi:, j] == 0)
+        if L:
+            assert q[b, 2, 0] == 0
+
+
 @pytest.mark.parametrize("from_coords", [False, True])
 def test_free_omega_cis_and_trans(from_coords):
     """omega per residue trans (pi +- 0.1), cis (0 +- 0.1) or uniform: the
