@@ -228,7 +228,9 @@ int oracle_backbone_backward(const double* angles, const int32_t* lengths, int B
 /* Section 2: full-atom residue tables (authored internal coordinates) */
 /* ------------------------------------------------------------------ */
 
-#define NRES 20
+#define NRES 20    /* amino acids, codes 0..19 */
+#define BB_ONLY 20 /* code 20: a residue with its backbone N, CA, C only (the Section 3 model) */
+#define NCODES 21
 #define MAXSC 10   /* side-chain atoms per residue (TRP) */
 #define MAXAT 14   /* heavy atoms per residue (TRP) */
 #define MAXGRP 4
@@ -382,7 +384,12 @@ typedef struct {
     double grp_d[MAXGRP];
 } residue_tab;
 
-static residue_tab TAB[NRES];
+static residue_tab TAB[NCODES];
+
+/* Code 20 places only the three atoms of the Section 3 backbone, so a chain
+ * of such residues is the backbone model and a batch may mix both models. */
+static const residue_def RES_BB = {"BB", 0, 0, {0.0}, 0, {{0}}};
+static const residue_def* res_def(int code) { return code < NRES ? &RES[code] : &RES_BB; }
 static int TAB_READY = 0;
 
 static int sc_index(const residue_def* rd, const char* name) {
@@ -427,15 +434,15 @@ static void frame_child(double d, double angle, double delta, double* out) {
 
 static void build_tables(void) {
     if (TAB_READY) return;
-    for (int t = 0; t < NRES; ++t) {
-        const residue_def* rd = &RES[t];
+    for (int t = 0; t < NCODES; ++t) {
+        const residue_def* rd = res_def(t);
         residue_tab* tb = &TAB[t];
         memset(tb, 0, sizeof(*tb));
         const char* bb[4] = {"N", "CA", "C", "O"};
         for (int k = 0; k < 4; ++k) strcpy(tb->names[k], bb[k]);
         tb->group[0] = 0; tb->group[1] = 1; tb->group[2] = 2; tb->group[3] = 2;
         frame_child(O_BOND, O_ANGLE_DEG * DEG, O_DIHEDRAL_OFFSET_DEG * DEG, tb->r0[3]);
-        tb->n_atoms = 4 + rd->n_sc;
+        tb->n_atoms = (t == BB_ONLY) ? 3 : 4 + rd->n_sc; /* no O for the backbone-only code */
 
         /* Local positions of the atoms of each group in that group's frame. */
         double local[MAXSC][3];
@@ -490,16 +497,16 @@ static void build_tables(void) {
 }
 
 int oracle_residue_info(int code, char* three_letter4, int* n_atoms, int* n_chi) {
-    if (code < 0 || code >= NRES) return 1;
+    if (code < 0 || code >= NCODES) return 1;
     build_tables();
-    if (three_letter4) { strncpy(three_letter4, RES[code].three, 3); three_letter4[3] = 0; }
+    if (three_letter4) { strncpy(three_letter4, res_def(code)->three, 3); three_letter4[3] = 0; }
     if (n_atoms) *n_atoms = TAB[code].n_atoms;
-    if (n_chi) *n_chi = RES[code].n_chi;
+    if (n_chi) *n_chi = res_def(code)->n_chi;
     return 0;
 }
 
 int oracle_residue_atom(int code, int idx, char* name8, int* group) {
-    if (code < 0 || code >= NRES) return 1;
+    if (code < 0 || code >= NCODES) return 1;
     build_tables();
     if (idx < 0 || idx >= TAB[code].n_atoms) return 1;
     if (name8) strcpy(name8, TAB[code].names[idx]);
@@ -508,7 +515,7 @@ int oracle_residue_atom(int code, int idx, char* name8, int* group) {
 }
 
 int oracle_residue_atom_r0(int code, int idx, double* r0) {
-    if (code < 0 || code >= NRES) return 1;
+    if (code < 0 || code >= NCODES) return 1;
     build_tables();
     if (idx < 0 || idx >= TAB[code].n_atoms) return 1;
     memcpy(r0, TAB[code].r0[idx], 3 * sizeof(double));
@@ -519,7 +526,7 @@ int oracle_fullatom_chain_atoms(const uint8_t* seq, int length) {
     build_tables();
     int n = 0;
     for (int j = 0; j < length; ++j) {
-        if (seq[j] >= NRES) return -1;
+        if (seq[j] >= NCODES) return -1;
         n += TAB[seq[j]].n_atoms;
     }
     return n;
@@ -546,7 +553,7 @@ static void fullatom_frames(const double* ang, const uint8_t* seq, int Lmax, int
     mat_identity(cur);
     mat_rot_x(RPRIME_DEG * DEG, Rp);
     for (int j = 0; j < L; ++j) {
-        const residue_def* rd = &RES[seq[j]];
+        const residue_def* rd = res_def(seq[j]);
         const residue_tab* tb = &TAB[seq[j]];
         residue_frames* f = &F[j];
         memcpy(f->M0, cur, sizeof(cur));
@@ -580,7 +587,7 @@ static const double* group_frame(const residue_frames* f, int g) {
 
 static int check_seq(const uint8_t* seq, int L) {
     for (int j = 0; j < L; ++j)
-        if (seq[j] >= NRES) return 1;
+        if (seq[j] >= NCODES) return 1;
     return 0;
 }
 
@@ -640,7 +647,7 @@ int oracle_fullatom_backward(const double* angles, const uint8_t* seq, const int
             off[j + 1] = off[j] + tb->n_atoms;
         }
         for (int j = 0; j < L; ++j) {
-            const residue_def* rd = &RES[s[j]];
+            const residue_def* rd = res_def(s[j]);
             const residue_tab* tb = &TAB[s[j]];
             double Fm[16], dr[3];
             /* phi_j: node M_1 = M_0 R_1(phi); children: every atom of residue j but N,

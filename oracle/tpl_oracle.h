@@ -16,7 +16,8 @@
  *   full-atom coords  [B][Amax][3]
  *   sequences         [B][Lmax] uint8 residue codes 0..19 (ALA ARG ASN ASP
  *                     CYS GLN GLU GLY HIS ILE LEU LYS MET PHE PRO SER THR TRP
- *                     TYR VAL)
+ *                     TYR VAL) and 20 = backbone only (N, CA, C: the Section 3
+ *                     model), so one batch may mix both models
  *   LRMSD clouds      [P][Nmax][3]
  * Padding (residue >= length, atom >= num_atoms) is ignored on input and
  * written as 0 on output.  Functions return 0 on success, nonzero on a bad
