@@ -15,7 +15,7 @@
  *    allocation, and may be captured in a CUDA graph.
  *  - Errors the host can see (bad sizes, NULL pointers, misalignment, short
  *    workspace) are returned at once and nothing is launched.  Errors that
- *    depend on device data (a residue code >= 20, a length outside [0, Lmax],
+ *    depend on device data (a residue code > 20, a length outside [0, Lmax],
  *    a chain with more atoms than Amax) set bits of a per-device status word
  *    that tpl_get_status() reads and clears; outputs of the affected chain are
  *    then unspecified but no access leaves the caller's buffers.
@@ -31,7 +31,11 @@
  *  - backbone coords  [B][3*Lmax][3] atoms N, CA, C of each residue (Angstrom)
  *  - full-atom angles [B][7][Lmax]  rows phi, psi, omega, chi1, chi2, chi3, chi4
  *  - sequence         [B][Lmax] uint8 residue codes 0..19 = ALA ARG ASN ASP CYS
- *                     GLN GLU GLY HIS ILE LEU LYS MET PHE PRO SER THR TRP TYR VAL
+ *                     GLN GLU GLY HIS ILE LEU LYS MET PHE PRO SER THR TRP TYR VAL;
+ *                     20 = BB, a residue with the Section 3 backbone N, CA, C
+ *                     only (no O, no side chain): a chain of BB residues is the
+ *                     backbone model, so one full-atom call runs a batch that
+ *                     mixes both models (chain by chain or residue by residue)
  *  - full-atom coords [B][Amax][3] heavy atoms, residue by residue, each residue
  *                     N, CA, C, O then its side chain (tpl_residue_atom order)
  *  - LRMSD clouds     [P][Nmax][3]
@@ -69,7 +73,7 @@ typedef int tpl_status;
 #define TPL_ERR_NO_DEVICE 6        /* no usable CUDA device */
 
 /* Bits of the device status word (tpl_get_status). */
-#define TPL_STATUS_BAD_RESIDUE 0x1 /* a residue code >= 20 was read */
+#define TPL_STATUS_BAD_RESIDUE 0x1 /* a residue code > 20 was read */
 #define TPL_STATUS_BAD_LENGTH 0x2  /* a length < 0 or > Lmax, or num_atoms outside [0, Nmax] */
 #define TPL_STATUS_TOO_MANY_ATOMS 0x4 /* a chain needs more than Amax atoms */
 #define TPL_STATUS_ZERO_LRMSD 0x8  /* an LRMSD below 1e-12 A: its gradient is set to 0 */
@@ -397,7 +401,7 @@ tpl_status tpl_lrmsd_backward_ref64(const double* grad_lrmsd, const double* inpu
 /* Host helpers: residue tables, sizes, status                               */
 /* ------------------------------------------------------------------------ */
 
-/* Residue `code` (0..19): three-letter name (4 bytes with NUL), heavy-atom
+/* Residue `code` (0..20): three-letter name (4 bytes with NUL), heavy-atom
  * count and number of free chi angles (Section 2: up to 7 angles per
  * residue).  Host only, no CUDA call. */
 tpl_status tpl_residue_table(int code, char* three_letter, int* n_atoms, int* n_chi);

@@ -439,8 +439,10 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
                 put(0, M0.t);  // N = M_0 0
                 put(1, M1.t);  // CA = M_1 0
                 put(2, M3.t);  // C = M_3 0
-                const float4 o = s_tab.o_r0;
-                put(3, point_apply(M3, make_float3(o.x, o.y, o.z)));
+                if (ty != kBackboneCode) {  // O (a backbone-only residue has none)
+                    const float4 o = s_tab.o_r0;
+                    put(3, point_apply(M3, make_float3(o.x, o.y, o.z)));
+                }
                 // side-chain groups: S_k = S_{k-1} R(chi_k), S_0 = M_1 R'; atoms r = S_k r0
                 Rigid S = M1;
                 rigid_mul_Rx(S, s_tab.rp_c, s_tab.rp_s);
@@ -693,11 +695,14 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
                 Sum6 s = sum6_zero();
                 if constexpr (KEEP) {
                     Sum6 ns = sum6_zero(), co = sum6_zero(), ca = sum6_zero();
-                    const float3 rN = Rp(a), rCA = Rp(a + 1), rC = Rp(a + 2), rO = Rp(a + 3);
+                    const float3 rN = Rp(a), rCA = Rp(a + 1), rC = Rp(a + 2);
                     add(ns, rN, G(a, rN, &res_acc));
                     add(ca, rCA, G(a + 1, rCA, &res_acc));
                     add(co, rC, G(a + 2, rC, &res_acc));
-                    add(co, rO, G(a + 3, rO, &res_acc));
+                    if (nat > 3) {  // O (a backbone-only residue has none)
+                        const float3 rO = Rp(a + 3);
+                        add(co, rO, G(a + 3, rO, &res_acc));
+                    }
                     s = sum6_add(sum6_add(ns, ca), co);
                     nkeep[k] = ns;
                     cokeep[k] = co;
@@ -706,7 +711,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
                     rkeep[k][2] = rC;
                 } else {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {  // N, CA, C, O
+                    for (int q = 0; q < min(4, nat); ++q) {  // N, CA, C, O
                         const float3 r = Rp(a + q);
                         add(s, r, G(a + q, r, &res_acc));
                     }
@@ -782,12 +787,14 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
                     rN = Rp(a);
                     rCA = Rp(a + 1);
                     rC = Rp(a + 2);
-                    const float3 rO = Rp(a + 3);
                     nsum = sum6_zero();
                     co = sum6_zero();
                     add(nsum, rN, G(a, rN, nullptr));
                     add(co, rC, G(a + 2, rC, nullptr));
-                    add(co, rO, G(a + 3, rO, nullptr));
+                    if (type[k] != kBackboneCode) {  // O
+                        const float3 rO = Rp(a + 3);
+                        add(co, rO, G(a + 3, rO, nullptr));
+                    }
                 }
                 Sum6 x = sum6_add(co, A);
                 gpsi[k] = f3_dot(unit3(f3_sub(rC, rCA)), f3_sub(x.c, f3_cross(rC, x.g)));
@@ -946,8 +953,10 @@ __global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ an
             u_psi = M3.c0;
             p_psi = M3.t;
             add(csum, M3.t, gat(2));
-            const float4 o = s_tab.o_r0;
-            add(csum, point_apply(M3, make_float3(o.x, o.y, o.z)), gat(3));
+            if (type != kBackboneCode) {  // O
+                const float4 o = s_tab.o_r0;
+                add(csum, point_apply(M3, make_float3(o.x, o.y, o.z)), gat(3));
+            }
             Rigid S = M1;
             rigid_mul_Rx(S, s_tab.rp_c, s_tab.rp_s);
             const int ng = s_tab.n_groups[type], nchi = s_tab.n_chi[type];

@@ -42,7 +42,7 @@ struct ResDef {
     IC side[kMaxSide];
 };
 
-const ResDef kRes[kNumTypes] = {
+const ResDef kRes[kNumAminoAcids] = {
     {"ALA", 0, 1, {0.0}, 1, {{"CB", 1, 1, 0, 2, 1.521, 110.4, 0.0, 0}}},
     {"ARG", 4, 4, {0}, 7,
      {{"CB", 1, 1, 0, 2, 1.530, 110.5, 0.0, 0},
@@ -151,6 +151,11 @@ const ResDef kRes[kNumTypes] = {
       {"CG2", 1, 4, 1, 0, 1.521, 110.5, -122.9, 1}}},
 };
 
+// Residue code 20 places the backbone's N, CA and C only: a chain of such
+// residues is the Section 3 model, so one batch can hold both models.
+const ResDef kResBackbone = {"BB", 0, 0, {0.0}, 0, {}};
+const ResDef& res_def(int code) { return code < kNumAminoAcids ? kRes[code] : kResBackbone; }
+
 const char* kBackboneNames[4] = {"N", "CA", "C", "O"};
 
 // Backbone, Section 3: theta = pi - {2.1186, 1.9391, 2.0610}, d = {1.330, 1.460, 1.525}
@@ -221,8 +226,8 @@ void build() {
     F.bb.o[0] = (float)o.x; F.bb.o[1] = (float)o.y; F.bb.o[2] = (float)o.z;
 
     for (int t = 0; t < kNumTypes; ++t) {
-        const ResDef& R = kRes[t];
-        const int n_atoms = 4 + R.n_side;
+        const ResDef& R = res_def(t);
+        const int n_atoms = t == kBackboneCode ? 3 : 4 + R.n_side;  // no O on a backbone-only residue
         D.n_atoms[t] = F.n_atoms[t] = (uint8_t)n_atoms;
         D.n_chi[t] = F.n_chi[t] = (uint8_t)R.n_chi;
         D.n_groups[t] = F.n_groups[t] = (uint8_t)R.n_groups;
@@ -303,13 +308,13 @@ BackboneConst backbone_const() { return built().f.bb; }
 BackboneConstD backbone_const_d() { return built().d.bb; }
 
 const char* residue_three(int code) {
-    return (code >= 0 && code < kNumTypes) ? kRes[code].three : nullptr;
+    return (code >= 0 && code < kNumTypes) ? res_def(code).three : nullptr;
 }
 
 const char* residue_atom_name(int code, int idx) {
     if (code < 0 || code >= kNumTypes) return nullptr;
-    if (idx < 0 || idx >= 4 + kRes[code].n_side) return nullptr;
-    return idx < 4 ? kBackboneNames[idx] : kRes[code].side[idx - 4].name;
+    if (idx < 0 || idx >= fa_table().n_atoms[code]) return nullptr;
+    return idx < 4 ? kBackboneNames[idx] : res_def(code).side[idx - 4].name;
 }
 
 }  // namespace tpl

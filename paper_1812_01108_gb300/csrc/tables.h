@@ -7,7 +7,9 @@
 
 namespace tpl {
 
-constexpr int kNumTypes = 20;
+constexpr int kNumAminoAcids = 20;  // residue codes 0..19
+constexpr int kBackboneCode = 20;   // residue code 20: N, CA, C only (the Section 3 backbone)
+constexpr int kNumTypes = 21;
 constexpr int kMaxAtoms = 14;    // heavy atoms per residue (TRP)
 constexpr int kMaxSide = 10;     // side-chain atoms per residue (TRP)
 constexpr int kMaxGroups = 4;    // side-chain rigid groups (chi1..chi4)

@@ -44,7 +44,7 @@ def test_residue_tables_bit_exact_with_oracle(lib):
     lib.tpl_residue_table.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.tpl_residue_atom.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p]
-    for code in range(20):
+    for code in range(21):  # 0..19 amino acids, 20 the backbone-only residue
         three = ctypes.create_string_buffer(4)
         na, nc = ctypes.c_int(), ctypes.c_int()
         assert lib.tpl_residue_table(code, three, ctypes.byref(na), ctypes.byref(nc)) == 0
@@ -59,7 +59,7 @@ def test_residue_tables_bit_exact_with_oracle(lib):
             assert grp.value == o_groups[i]
             # standard-frame positions: independently computed, FP32 vs FP64
             assert np.allclose(np.array(r0[:]), o_r0[i], atol=2e-6), (code, o_names[i])
-    assert lib.tpl_residue_table(20, None, None, None) != 0
+    assert lib.tpl_residue_table(21, None, None, None) != 0
 
 
 def test_chain_atom_counts_bit_exact_with_oracle(lib):

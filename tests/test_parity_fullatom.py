@@ -332,6 +332,58 @@ def test_fused_training_step_matches_the_separate_calls_and_the_oracle(shape):
         assert np.all(host(g2)[b, :, L:] == 0)
 
 
+def _mixed_inputs(seed):
+    """Full-atom chains, backbone-only chains (code 20) and chains that mix
+    both residue by residue, in one batch."""
+    rng = np.random.default_rng(seed)
+    lengths = np.array([0, 1, 37, 256, 257, 500, 700, 129, 64, 3], np.int32)
+    Lmax = 700
+    a, seq = workloads.fullatom_inputs(lengths, rng, Lmax=Lmax)
+    seq[1::3] = 20                      # whole backbone-only chains
+    seq[2::3, ::2] = 20                 # every other residue backbone-only
+    a[:, 2] += rng.normal(0, 0.2, size=a[:, 2].shape).astype(np.float32)
+    a *= (np.arange(Lmax)[None, :] < lengths[:, None])[:, None, :]
+    Amax = workloads.pad_to(max(oracle.max_atoms(seq, lengths), 1))
+    g = workloads.upstream_grad((len(lengths), Amax, 3), rng)
+    return a, seq, lengths, g, Amax
+
+
+@pytest.mark.parametrize("shape,from_coords", [((384, 1), True), ((192, 2), True), ((64, 4), True),
+                                               ((256, 1), False)])
+def test_mixed_backbone_and_fullatom_batch(shape, from_coords):
+    """One persistent launch over a batch mixing both models (residue code 20
+    places N, CA, C only) against the oracle; backbone-only chains also equal
+    the backbone kernel's coordinates."""
+    d = require_gpu()
+    a, seq, lengths, g, Amax = _mixed_inputs(71)
+    c64, na64 = oracle.fullatom_forward(a, seq, lengths, Amax)
+    g = (g * (np.arange(Amax)[None, :] < na64[:, None])[:, :, None]).astype(np.float32)
+    g64 = oracle.fullatom_backward(a, seq, lengths, g)
+    c32, na32, ga32 = _run_fp32(a, seq, lengths, g, Amax, {"threads": shape[0], "res_per_thread": shape[1]},
+                                from_coords)
+    assert np.array_equal(na32, na64)
+    assert np.abs(c32 - c64).max() <= COORD_TOL
+    assert rel_err(ga32, g64) <= GRAD_TOL
+    for b, L in enumerate(lengths):
+        assert np.all(c32[b, na64[b]:] == 0) and np.all(ga32[b, :, L:] == 0)
+    # whole backbone-only chains against the backbone kernel
+    bb = [b for b in range(1, len(lengths), 3)]
+    ab = np.ascontiguousarray(a[bb, :3])
+    cb = host(_backbone_coords(ab, lengths[bb], d))
+    for i, b in enumerate(bb):
+        n = 3 * lengths[b]
+        assert np.abs(c32[b, :n] - cb[i, :n]).max() <= COORD_TOL
+
+
+def _backbone_coords(a, lengths, d):
+    B, _, Lmax = a.shape
+    c = torch.zeros((B, 3 * Lmax, 3), device=d)
+    ws = torch.empty(tpl.tpl_backbone_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    tpl.tpl_backbone_forward(dev(a, d), dev(lengths, d), c, ws)
+    torch.cuda.synchronize()
+    return c
+
+
 def test_quadratic_comparator_matches_the_scan_and_the_oracle(reference):
     """tpl_fullatom_backward_quadratic (the paper's depth-first O(L^2) sums of
     Eq. 1) against the scan backward and the oracle, chains of every length of

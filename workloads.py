@@ -29,6 +29,7 @@ import numpy as np
 
 SEED_BASE = 1812_01108
 N_RESIDUE_TYPES = 20
+BACKBONE_ONLY = 20  # residue code of a residue with its backbone N, CA, C only
 
 
 def rng_for(index: int, salt: int = 0) -> np.random.Generator:
