@@ -771,24 +771,6 @@ __device__ __forceinline__ void pack_member_sums(T (&v)[F], int sid, T* s_part, 
     __syncthreads();
 }
 
-// Copies n floats from global `src` (16-byte aligned) to shared `dst` at a
-// float offset that may not be a multiple of 4.
-template <int NT>
-__device__ __forceinline__ void stage_in(float* dst, const float* __restrict__ src, int n) {
-    const float4* s4 = reinterpret_cast<const float4*>(src);
-    const int full = n >> 2;
-    if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
-        float4* d4 = reinterpret_cast<float4*>(dst);
-        for (int q = threadIdx.x; q < full; q += NT) d4[q] = __ldg(s4 + q);
-    } else {
-        for (int q = threadIdx.x; q < full; q += NT) {
-            const float4 v = __ldg(s4 + q);
-            dst[4 * q] = v.x; dst[4 * q + 1] = v.y; dst[4 * q + 2] = v.z; dst[4 * q + 3] = v.w;
-        }
-    }
-    for (int i = 4 * full + threadIdx.x; i < n; i += NT) dst[i] = __ldg(src + i);
-}
-
 // Writes each pack member's row of n9 = 9 len floats from the stage (slot
 // offsets o9 = 9 off) to `out` rows of 9 Lmax floats, with the zero padding
 // past it unless the caller keeps the padding zero.
@@ -836,11 +818,13 @@ __device__ __forceinline__ void add_moments(float (&m)[kMom], float3 x, float3 x
 __device__ __forceinline__ float3 ld3(const float* p) { return make_float3(p[0], p[1], p[2]); }
 
 template <int NT, int K>
-constexpr int step_min_blocks() { return NT >= 512 ? 1 : (NT >= 256 ? 2 : 3); }
+constexpr int step_min_blocks() { return NT >= 512 ? 1 : (NT >= 256 ? 3 : 4); }
 
-// Dynamic shared memory of K1s: the tile's coordinates and target atoms.
+// Dynamic shared memory of K1s: the tile's coordinates (the target atoms are
+// read from global memory, each thread its own, and stay in L1 across the
+// passes; staging them too would halve the CTAs per SM).
 template <int NT, int K>
-constexpr size_t step_smem() { return 2 * (size_t)9 * NT * K * sizeof(float); }
+constexpr size_t step_smem() { return (size_t)9 * NT * K * sizeof(float); }
 
 template <int NT, int K>
 __global__ void __launch_bounds__(NT, step_min_blocks<NT, K>()) bb_step_kernel(
@@ -862,7 +846,6 @@ __global__ void __launch_bounds__(NT, step_min_blocks<NT, K>()) bb_step_kernel(
     __shared__ float s_w[kMaxPack];
     extern __shared__ float4 s_dyn[];
     float* s_out = reinterpret_cast<float*>(s_dyn);  // [9 TILE] coordinates of the tile
-    float* s_tgt = s_out + 9 * TILE;                 // [9 TILE] target atoms of the tile
     const bool write_padding = !(ws.flags & TPL_FLAG_PADDING_ZEROED);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
@@ -895,8 +878,6 @@ __global__ void __launch_bounds__(NT, step_min_blocks<NT, K>()) bb_step_kernel(
             b = ci >= 0 ? s_pack.b[ci] : 0;
             L = ci >= 0 ? s_pack.len[ci] : 0;
             const int j0 = ci >= 0 ? slot - s_pack.off[ci] : Lmax;  // Lmax: nothing to load or store
-            for (int i = 0; i < m; ++i)
-                stage_in<NT>(s_tgt + 9 * s_pack.off[i], target + (size_t)s_pack.b[i] * 9 * Lmax, 9 * s_pack.len[i]);
             float3 pos[3 * K];
             const Rigid A = thread_product<K>(angles + (size_t)b * 3 * Lmax, j0, L, Lmax, bc, pos);
             const Rigid E = block_seg_scan_rigid<NT>(A, ci < 0 || j0 == 0, s_rig, s_cnt);
@@ -917,7 +898,8 @@ __global__ void __launch_bounds__(NT, step_min_blocks<NT, K>()) bb_step_kernel(
             __syncthreads();
             store_pack_rows<NT>(coords, s_out, s_pack, m, Lmax, write_padding);
             const float* my_r = s_out + 9 * slot;  // this thread's atoms
-            const float* my_x = s_tgt + 9 * slot;
+            const float* tg = target + (size_t)b * 9 * Lmax;  // the chain's target
+            const float* my_x = tg + 9 * (size_t)min(j0, Lmax - K);
             const int nres = ci >= 0 ? max(0, min(K, L - j0)) : 0;  // real residues of this thread
             // moments of each chain
             {
@@ -925,7 +907,7 @@ __global__ void __launch_bounds__(NT, step_min_blocks<NT, K>()) bb_step_kernel(
 #pragma unroll
                 for (int q = 0; q < kMom; ++q) mom[q] = 0.f;
                 if (nres > 0) {
-                    const float3 x0 = ld3(s_tgt + 9 * s_pack.off[ci]);
+                    const float3 x0 = make_float3(__ldg(tg), __ldg(tg + 1), __ldg(tg + 2));
 #pragma unroll
                     for (int q = 0; q < 3 * K; ++q)
                         if (q < 3 * nres) add_moments(mom, ld3(my_x + 3 * q), x0, ld3(my_r + 3 * q));
@@ -940,7 +922,7 @@ __global__ void __launch_bounds__(NT, step_min_blocks<NT, K>()) bb_step_kernel(
                 float S[kSlot];
 #pragma unroll
                 for (int q = 0; q < kSlot; ++q) S[q] = q < kMom ? s_tot[ii * kMom + q] : 0.f;
-                const float* x0p = s_tgt + 9 * s_pack.off[ii];
+                const float* x0p = target + (size_t)s_pack.b[ii] * 9 * Lmax;
                 const float* y0p = s_out + 9 * s_pack.off[ii];
                 const float x0[3] = {x0p[0], x0p[1], x0p[2]}, y0[3] = {y0p[0], y0p[1], y0p[2]};
                 quad_eigen_solve(S, x0, y0, 3 * s_pack.len[ii], lane & 3, lane, active, s_state + 16 * ii);
@@ -968,19 +950,18 @@ __global__ void __launch_bounds__(NT, step_min_blocks<NT, K>()) bb_step_kernel(
             }
             __syncthreads();
             // each atom's gradient, then the backward of Eq. 2 (segmented suffix scan)
+            // (the atom gradients are formed again from shared memory in the
+            // walk below rather than kept in registers)
             const float w = ci >= 0 ? s_w[ci] : 0.f;
-            float g[9 * K];
             Sum6 own = sum6_zero();
 #pragma unroll
             for (int q = 0; q < 3 * K; ++q) {
-                float3 gi = make_float3(0.f, 0.f, 0.f);
                 if (q < 3 * nres) {
                     const float3 ri = ld3(my_r + 3 * q);
-                    gi = f3_scale(w, residual(ps, ld3(my_x + 3 * q), ri));
+                    const float3 gi = f3_scale(w, residual(ps, ld3(my_x + 3 * q), ri));
                     own.c = f3_add(own.c, f3_cross(ri, gi));
                     own.g = f3_add(own.g, gi);
                 }
-                g[3 * q] = gi.x; g[3 * q + 1] = gi.y; g[3 * q + 2] = gi.z;
             }
             const bool tail = ci < 0 || slot + K >= s_pack.off[ci + 1];
             Sum6 S = sum6_add(block_seg_suffix_sum6<NT>(own, tail, s6, s_cnt), own);
@@ -994,7 +975,7 @@ __global__ void __launch_bounds__(NT, step_min_blocks<NT, K>()) bb_step_kernel(
                     float val = 0.f;
                     const float3 ri = ld3(my_r + 3 * q);
                     if (k < nres) {
-                        const float3 gi = make_float3(g[3 * q], g[3 * q + 1], g[3 * q + 2]);
+                        const float3 gi = f3_scale(w, residual(ps, ld3(my_x + 3 * q), ri));
                         if (j0 + k > 0 || at > 0) {
                             float3 u = f3_sub(ri, prev);
                             u = f3_scale(rsqrtf(f3_dot(u, u)), u);
@@ -1029,8 +1010,6 @@ __global__ void __launch_bounds__(NT, step_min_blocks<NT, K>()) bb_step_kernel(
         float* out = coords + (size_t)b * 9 * Lmax;
         const int tile0 = t * TILE;
         const int j0 = tile0 + threadIdx.x * K;
-        const int nst = min(TILE, L - tile0);  // residues of the chain in this tile
-        stage_in<NT>(s_tgt, target + (size_t)b * 9 * Lmax + 9 * (size_t)tile0, 9 * nst);
         float3 pos[3 * K];
         const Rigid A = thread_product<K>(angles + (size_t)b * 3 * Lmax, j0, L, Lmax, bc, pos);
         Rigid E, Tot;
@@ -1057,7 +1036,7 @@ __global__ void __launch_bounds__(NT, step_min_blocks<NT, K>()) bb_step_kernel(
             store_stage<K>(s_out + threadIdx.x * 9 * K, vv);
         }
         __syncthreads();
-        const int nres_out = write_padding ? min(TILE, Lmax - tile0) : min(TILE, (nst + 3) & ~3);  // multiple of 4
+        const int nres_out = write_padding ? min(TILE, Lmax - tile0) : min(TILE, (L - tile0 + 3) & ~3);  // multiple of 4
         {
             float4* dst = reinterpret_cast<float4*>(out + 9 * (size_t)tile0);
             const float4* src = reinterpret_cast<const float4*>(s_out);
@@ -1077,7 +1056,7 @@ __global__ void __launch_bounds__(NT, step_min_blocks<NT, K>()) bb_step_kernel(
                 const float* tg = target + (size_t)b * 9 * Lmax;
                 const float3 x0 = make_float3(__ldg(tg), __ldg(tg + 1), __ldg(tg + 2));
                 const float* my_r = s_out + 9 * threadIdx.x * K;
-                const float* my_x = s_tgt + 9 * threadIdx.x * K;
+                const float* my_x = tg + 9 * (size_t)j0;
 #pragma unroll
                 for (int q = 0; q < 3 * K; ++q)
                     if (q < 3 * nres) add_moments(mom, ld3(my_x + 3 * q), x0, ld3(my_r + 3 * q));
