@@ -61,8 +61,15 @@ DEFAULT_BATCH = {"training_step": 256, "backbone_uneven": 4096, "lrmsd_batch": 1
 # An entry is removed when one of its kernels changes after the capture.
 TRAFFIC = {
     # (per-unit DRAM bytes, unit, profile, launch shape of the capture or None if the
-    # kernels take none); cold-cache captures of one launch.  Filled from the
-    # captures of the current kernels (profiles/).
+    # kernels take none); cold-cache captures of one launch.
+    # Full-atom kernels captured at 4096 chains x 700 residues (coordinates above L2),
+    # scaled by residues processed.
+    ("training_step", "fullatom_forward"): (
+        321330432 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
+        "threads=384,res_per_thread=1"),
+    ("training_step", "lrmsd_fullatom_backward"): (
+        663435776 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
+        "threads=384,res_per_thread=1"),
 }
 
 
