@@ -11,6 +11,9 @@ Workloads (``--workload``):
                   Unit: residues/s.
   lrmsd_batch     16384 coordinate-set pairs of U{100..5000} atoms: LRMSD
                   forward + backward.  Unit: atoms/s (atoms of the input side).
+  fullatom_short  the training step on 4096 full-atom chains of log-uniform
+                  lengths in [16, 128] (short chains: packed several per CTA when
+                  the autotuner picks the packed schedule).  Unit: residues/s.
   mixed_batch     the training step on 256 chains x 700 residues where every
                   other chain is backbone-only (residue code 20: N, CA, C), both
                   models in the same persistent launches.  Unit: residues/s.
@@ -53,7 +56,7 @@ METRIC = "residues/s fwd+bwd at FP32 err≤2e-3 Å vs plain FP64 GPU form; HBM r
 METRIC_LRMSD = "atoms/s LRMSD fwd+bwd vs plain FP64 GPU form; HBM roofline %"
 
 DEFAULT_BATCH = {"training_step": 256, "backbone_uneven": 4096, "lrmsd_batch": 16384,
-                 "backbone_stress": 64, "length_sweep": 32, "mixed_batch": 256}
+                 "backbone_stress": 64, "length_sweep": 32, "mixed_batch": 256, "fullatom_short": 4096}
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of a C-ABI
 # call's kernels from one ncu capture, per unit processed (residue or atom),
@@ -145,6 +148,12 @@ def make_inputs(args, rank):
     """Seeded host arrays of the workload (one batch per rank)."""
     import workloads
 
+    if args.workload == "fullatom_short":
+        rng = workloads.rng_for(7, salt=rank)
+        lengths = workloads.lengths_loguniform(args.batch, 16, 128, rng)
+        a, seq = workloads.fullatom_inputs(lengths, rng, Lmax=128)
+        ta = workloads.perturb_angles(a, lengths, rng, rows=(0, 1, 3, 4, 5, 6))
+        return {"angles": a, "seq": seq, "lengths": lengths, "target_angles": ta}
     if args.workload in ("training_step", "mixed_batch"):
         rng = workloads.rng_for(4, salt=rank)
         lengths = np.full(args.batch, args.length, np.int32)
@@ -178,6 +187,11 @@ def describe(args, world):
                         "uniform residue types, phi/psi/chi ~ U[-pi,pi], omega = pi; forward -> "
                         "LRMSD to N(0,0.1 rad)-perturbed targets -> backward",
             "global_batch": B * world, "seq_len": args.length})
+    if args.workload == "fullatom_short":
+        return (METRIC, "residues/s", {
+            "workload": f"full-atom training step, {B} chains per GPU, lengths log-uniform in [16,128], "
+                        "uniform residue types; forward -> LRMSD to N(0,0.1 rad)-perturbed targets -> backward",
+            "global_batch": B * world, "seq_len": 128})
     if args.workload == "mixed_batch":
         return (METRIC, "residues/s", {
             "workload": f"mixed training step, {B} chains x {args.length} residues per GPU, every other "
@@ -256,7 +270,7 @@ def oracle_step(args, d, n):
     import oracle
 
     s = slice(0, n)
-    if args.workload in ("training_step", "mixed_batch"):
+    if args.workload in ("training_step", "mixed_batch", "fullatom_short"):
         a, seq, L, ta = d["angles"][s], d["seq"][s], d["lengths"][s], d["target_angles"][s]
         Amax = oracle.max_atoms(seq, L)
         t0 = time.perf_counter()
@@ -799,6 +813,7 @@ def errors(torch, c32, c64, g32, g64, lr32, lr64, prefix_atoms=None):
 
 
 SETUP = {"training_step": setup_training_step, "mixed_batch": setup_training_step,
+         "fullatom_short": setup_training_step,
          "backbone_uneven": setup_backbone_uneven,
          "backbone_stress": setup_backbone_uneven, "lrmsd_batch": setup_lrmsd_batch}
 

@@ -90,8 +90,13 @@ typedef struct CUstream_st* tpl_stream; /* same type as cudaStream_t */
 #define TPL_SCHED_LONGEST_FIRST 1 /* chains sorted by length, longest first */
 #define TPL_SCHED_BATCH_ORDER 2   /* chains in batch order */
 #define TPL_SCHED_PACKED 3        /* longest first, and chains of at most one tile packed
-                                     several per tile (backbone; the full-atom calls
-                                     treat it as LONGEST_FIRST) */
+                                     up to 8 per tile (chains per CTA > 1).  Full atom:
+                                     the backward must read the coordinates (a packed
+                                     forward with TPL_BWD_RECOMPUTE is rejected; a
+                                     backward that rebuilds frames on a packed workspace
+                                     sets TPL_STATUS_BAD_WORKSPACE and writes zeros for
+                                     those chains); the two-call training step treats
+                                     it as LONGEST_FIRST */
 
 /* Launch options; a NULL pointer means all zeros (everything automatic). */
 /* tpl_opts.flags */

@@ -321,6 +321,7 @@ LaunchCfg fullatom_cfg(const tpl_opts& o) {
                 break;
             }
     c.flags = o.flags;
+    c.packed = o.schedule == TPL_SCHED_PACKED;
     return c;
 }
 
@@ -674,9 +675,14 @@ tpl_status tpl_fullatom_forward(const float* angles, const uint8_t* seq, const i
     LaunchCfg cfg = fullatom_cfg(o);
     if ((st = check_fullatom_cfg(cfg))) return st;
     if ((st = check_ws(workspace, workspace_bytes, tpl_fullatom_workspace_size(B, Lmax)))) return st;
+    // packed (chains per CTA > 1) only on request, and only for a backward that
+    // reads the coordinates (rebuilding frames works per tile of one chain)
+    if (o.schedule == TPL_SCHED_PACKED && o.bwd_mode == TPL_BWD_RECOMPUTE)
+        return fail(TPL_ERR_INVALID_ARG, "a packed full-atom schedule needs the FROM_COORDS backward");
+    const int mode = o.schedule == TPL_SCHED_PACKED ? kSchedPacked : sched_mode(o, false);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = launch_fullatom_forward(angles, seq, lengths, B, Lmax, Amax, coords, num_atoms,
-                                            sched_mode(o, false), workspace, cfg, s);
+                                            mode, workspace, cfg, s);
     if (e != cudaSuccess) return cuda_fail(e, "fullatom_forward");
     return ok();
 }
@@ -1040,8 +1046,10 @@ int backbone_candidates(int bwd_mode, tpl_opts* cands) {
 int fullatom_candidates(int bwd_mode, tpl_opts* cands) {
     int n = 0;
     const int shapes[7][2] = {{128, 1}, {256, 1}, {384, 1}, {128, 2}, {192, 2}, {64, 4}, {192, 4}};
-    const int sch[2] = {TPL_SCHED_BATCH_ORDER, TPL_SCHED_LONGEST_FIRST};
-    for (int si = 0; si < 2; ++si)
+    // packed schedules (chains per CTA > 1) need a backward that reads the coordinates
+    const int sch[3] = {TPL_SCHED_BATCH_ORDER, TPL_SCHED_LONGEST_FIRST, TPL_SCHED_PACKED};
+    const int nsch = bwd_mode == TPL_BWD_RECOMPUTE ? 2 : 3;
+    for (int si = 0; si < nsch; ++si)
         for (int ti = 0; ti < 7; ++ti) {
             tpl_opts o;
             memset(&o, 0, sizeof(o));
@@ -1098,7 +1106,7 @@ tpl_status tpl_fullatom_autotune(const float* angles, const uint8_t* seq, const 
                                  size_t workspace_bytes, int bwd_mode, tpl_opts* best, float* best_ms,
                                  tpl_stream stream) {
     if (!best) return fail(TPL_ERR_INVALID_ARG, "best is NULL");
-    tpl_opts cands[20];
+    tpl_opts cands[32];
     const int n = fullatom_candidates(bwd_mode, cands);
     return tune(cands, n, reinterpret_cast<cudaStream_t>(stream), [&](const tpl_opts& o, tpl_stream ts) {
         tpl_status st = tpl_fullatom_forward(angles, seq, lengths, B, Lmax, Amax, coords, num_atoms, workspace,
@@ -1115,7 +1123,7 @@ tpl_status tpl_fullatom_lrmsd_autotune(const float* angles, const uint8_t* seq, 
                                        size_t lrmsd_workspace_bytes, float* grad_angles, void* workspace,
                                        size_t workspace_bytes, tpl_opts* best, float* best_ms, tpl_stream stream) {
     if (!best) return fail(TPL_ERR_INVALID_ARG, "best is NULL");
-    tpl_opts cands[20];
+    tpl_opts cands[32];
     const int n = fullatom_candidates(TPL_BWD_FROM_COORDS, cands);
     return tune(cands, n, reinterpret_cast<cudaStream_t>(stream), [&](const tpl_opts& o, tpl_stream ts) {
         tpl_status st = tpl_fullatom_forward(angles, seq, lengths, B, Lmax, Amax, coords, num_atoms, workspace,

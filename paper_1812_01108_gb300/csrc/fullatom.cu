@@ -315,7 +315,9 @@ __device__ __forceinline__ void tile_record(const ChainWs& ws, int slot, int& fi
 // dx = x - x_0 (x the target, x_0 its first atom) and dy = y (the chain's
 // first atom, N of residue 0, is the origin: R_0 = I).
 // ---------------------------------------------------------------------------
-template <int NT, int K, bool LM>
+// PACK: the work list may hold packs of whole short chains (segmented scans,
+// per-chain stores); compiled separately so that tiles of one chain pay nothing.
+template <int NT, int K, bool LM, bool PACK>
 __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
     const float* __restrict__ angles, const uint8_t* __restrict__ seq,
     const int32_t* __restrict__ lengths, int Lmax, int Amax, float* __restrict__ coords,
@@ -330,6 +332,9 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
     __shared__ int s_v, s_next;
     __shared__ float4 s_start[4];  // tile-start frame and its first atom
     __shared__ float s_mom[LM ? NW : 1][17];
+    __shared__ PackS s_pack;                            // a pack of whole short chains
+    __shared__ int s_cnt2[NW + 1], s_fl2[NW + 1];
+    __shared__ int s_mtot[kMaxPack], s_mbase[kMaxPack + 1];  // atoms per member, stage offsets
     extern __shared__ float4 s_dyn[];
     float* stage = reinterpret_cast<float*>(s_dyn);  // the tile's atoms, 3 floats each
 
@@ -338,14 +343,25 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
     int v = take_tile(ws.hdr + kHdrFwdNext, &s_v);
     while (v < ntiles) {
         const int2 ct = ws.tiles[v];
-        const int b = ct.x, t = ct.y;
-        const int L = clamp_length(lengths, b, Lmax);
-        const int T = fa_num_tiles(L, TILE);
-        const int s0 = fa_tile_start(L, T, t), s1 = fa_tile_start(L, T, t + 1);
+        // a tile of one chain, or (chains per CTA > 1) a pack of whole chains,
+        // each in its own slots of K residues, scanned as segments
+        const bool pack = PACK && ct.x < 0;
+        int m = 0, ci = -1;
+        if (pack) {
+            m = ct.y;
+            if (threadIdx.x < kMaxPack) s_mtot[threadIdx.x] = 0;
+            load_pack<K>(ws, lengths, Lmax, -1 - ct.x, m, s_pack);
+            ci = pack_member(s_pack, m, threadIdx.x * K);
+        }
+        const int b = pack ? s_pack.b[ci >= 0 ? ci : 0] : ct.x;
+        const int t = pack ? 0 : ct.y;
+        const int L = pack ? (ci >= 0 ? s_pack.len[ci] : 0) : clamp_length(lengths, b, Lmax);
+        const int T = pack ? 1 : fa_num_tiles(L, TILE);
+        const int s0 = pack ? 0 : fa_tile_start(L, T, t), s1 = pack ? L : fa_tile_start(L, T, t + 1);
         const int slot0 = b * ws.tmax;
         const float* ang = angles + (size_t)b * 7 * Lmax;
         float* out = coords + (size_t)b * Amax * 3;
-        const int j0 = s0 + threadIdx.x * K;
+        const int j0 = pack ? (ci >= 0 ? threadIdx.x * K - s_pack.off[ci] : 0) : s0 + threadIdx.x * K;
 
         // 1. inputs of the thread's residues, every angle row up front
         int type[K];
@@ -392,6 +408,28 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
         // 2. tile-local frame of the first residue and its first atom
         Rigid X, Tot;
         int a0, tile_atoms;
+        if (pack) {
+            // segments: no look-back, each chain starts at R_0 = I and atom 0
+            const bool head = ci < 0 || j0 == 0;
+            X = block_seg_scan_rigid<NT>(A, head, s_rig, s_cnt);
+            a0 = block_seg_scan_count<NT>(cnt, head, s_cnt2, s_fl2);
+            if (ci >= 0 && threadIdx.x * K + K >= s_pack.off[ci + 1]) s_mtot[ci] = a0 + cnt;  // the chain's last thread
+            if (threadIdx.x == 0) s_next = request_tile(ws.hdr + kHdrFwdNext);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int sb = 0;
+                for (int i = 0; i < m; ++i) {
+                    s_mbase[i] = sb;
+                    sb += s_mtot[i];
+                }
+                s_mbase[m] = sb;
+            }
+            if (threadIdx.x < m)  // the record the backward reads: first atom 0, the chain's atom count
+                store_rigid_g(ws.start + 4 * (size_t)s_pack.b[threadIdx.x] * ws.tmax, rigid_identity(), 0,
+                              s_mtot[threadIdx.x]);
+            __syncthreads();
+            tile_atoms = ci >= 0 ? s_mtot[ci] : 0;
+        } else {
         block_scan_rigid_count<NT>(A, cnt, s_rig, s_cnt, X, a0, Tot, tile_atoms);
         if (threadIdx.x == NT - 32 && t + 1 < T) publish_prefix_agg(ws, slot0 + t, Tot, tile_atoms);
 
@@ -406,15 +444,18 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
             }
         }
         __syncthreads();
-        int pc;
-        const Rigid P = load_rigid_prev(s_start, pc);
+        }
+        int pc = 0;
+        const Rigid P = pack ? rigid_identity() : load_rigid_prev(s_start, pc);
         const int requested = s_next;
         const int end_atom = pc + tile_atoms;
         const int nout = max(0, min(end_atom, Amax) - pc);
         // the tile's atoms go through the stage unless they do not fit in it
-        const bool staged = tile_atoms <= CAP;
-        float* dst = staged ? stage : out + 3 * (size_t)pc;
-        const int lim = staged ? CAP : Amax - pc;  // tile atoms at or past it are not written
+        // (a pack: every member's atoms, one after the other)
+        const bool staged = pack ? s_mbase[m] <= CAP : tile_atoms <= CAP;
+        const int sbase = pack && ci >= 0 ? s_mbase[ci] : 0;
+        float* dst = staged ? stage + 3 * sbase : out + 3 * (size_t)pc;
+        const int lim = staged ? CAP - sbase : Amax - pc;  // tile atoms at or past it are not written
 
         // 4. atoms in the chain's frame
         if (j0 < s1) {
@@ -500,14 +541,28 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
                 }
             }
         }
-        if (end_atom > Amax && threadIdx.x == 0) flag_status(TPL_STATUS_TOO_MANY_ATOMS);
         // 5. the stage out
+        if (pack) {  // member by member (block-wide loops)
+            for (int i = 0; i < m; ++i) {
+                const int n = s_mtot[i];
+                float* oi = coords + (size_t)s_pack.b[i] * Amax * 3;
+                if (staged) store_range<NT>(oi, stage + 3 * s_mbase[i], 0, 3 * min(n, Amax));
+                if (threadIdx.x == 0) {
+                    num_atoms[s_pack.b[i]] = n;
+                    if (n > Amax) flag_status(TPL_STATUS_TOO_MANY_ATOMS);
+                }
+                if (!(ws.flags & TPL_FLAG_PADDING_ZEROED)) zero_range<NT>(oi, 3 * min(n, Amax), 3 * Amax);
+            }
+        } else {
+        if (end_atom > Amax && threadIdx.x == 0) flag_status(TPL_STATUS_TOO_MANY_ATOMS);
         if (staged) store_range<NT>(out, stage, 3 * pc, 3 * (pc + nout));
         if (t == T - 1) {
             if (threadIdx.x == 0) num_atoms[b] = end_atom;
             if (!(ws.flags & TPL_FLAG_PADDING_ZEROED)) zero_range<NT>(out, 3 * min(end_atom, Amax), 3 * Amax);
         }
+        }
         if constexpr (LM) {
+          if (!pack) {  // (the fused step's schedule has no packs)
             const float* tg = target + (size_t)b * Amax * 3;
             const float3 x0 = make_float3(__ldg(tg), __ldg(tg + 1), __ldg(tg + 2));
             // the tile's coordinates: the stage, or (tiles that bypass it) this
@@ -546,6 +601,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
                 for (int w = 0; w < NW; ++w) x += s_mom[w][threadIdx.x];
                 ws.tmom[(size_t)(slot0 + t) * 20 + threadIdx.x] = x;
             }
+          }
         }
         v = next_tile(requested, &s_v);
     }
@@ -578,7 +634,7 @@ __device__ __forceinline__ float3 unit3(float3 v) { return f3_scale(rsqrtf(f3_do
 // last -- waits for the chain's other tiles, forms LRMSD in FP64 and rescales
 // the chain's angle gradients.
 // ---------------------------------------------------------------------------
-template <int NT, int K, bool LR, bool RES>
+template <int NT, int K, bool LR, bool RES, bool PACK>
 __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kernel(
     const uint8_t* __restrict__ seq, const int32_t* __restrict__ lengths, int B, int Lmax, int Amax,
     const float* __restrict__ coords, const float* __restrict__ grad_coords,
@@ -592,6 +648,9 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
     __shared__ int s_v, s_next;
     __shared__ float s_res[NW];
     __shared__ float s_scale;
+    __shared__ PackS s_pack;  // a pack of whole short chains
+    __shared__ int s_fl[NW + 1];
+    __shared__ int s_mn[kMaxPack], s_mbase[kMaxPack + 1];  // atoms per member, stage offsets (floats)
     extern __shared__ float4 s_dyn[];
     float* st_r = reinterpret_cast<float*>(s_dyn);  // the tile's coordinates
 
@@ -607,25 +666,65 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
     int v = take_tile(counter, &s_v);
     while (v < ntiles) {
         const int2 ct = ws.tiles[v];
-        const int b = ct.x;
-        const int L = clamp_length(lengths, b, Lmax);
-        const int T = fa_num_tiles(L, TILE);
-        const int t = T - 1 - ct.y;  // last tile first
-        const int s0 = fa_tile_start(L, T, t), s1 = fa_tile_start(L, T, t + 1);
+        // a tile of one chain (the chain's tiles taken last to first), or a
+        // pack of whole chains in slots of K residues (segmented sums)
+        if (ct.x < 0 && (RES || !PACK)) {
+            // a pack, but this backward was not built for packs (the forward
+            // ran with another schedule than these options name)
+            if (threadIdx.x == 0) flag_status(TPL_STATUS_BAD_WORKSPACE);
+            for (int i = 0; i < ct.y; ++i) {
+                float* gi = grad_angles + (size_t)ws.order[-1 - ct.x + i] * 7 * Lmax;
+                for (int q = threadIdx.x; q < 7 * Lmax; q += NT) gi[q] = 0.f;
+            }
+            v = next_tile(request_tile(counter), &s_v);
+            continue;
+        }
+        const bool pack = PACK && ct.x < 0;
+        int m = 0, ci = -1;
+        if (pack) {
+            m = ct.y;
+            load_pack<K>(ws, lengths, Lmax, -1 - ct.x, m, s_pack);
+            ci = pack_member(s_pack, m, threadIdx.x * K);
+            if (threadIdx.x == 0) {
+                int sb = 0;
+                for (int i = 0; i < m; ++i) {
+                    int pc_i, n_i;
+                    tile_record(ws, s_pack.b[i] * ws.tmax, pc_i, n_i);
+                    s_mn[i] = min(n_i, Amax);
+                    s_mbase[i] = sb;
+                    sb += (3 * s_mn[i] + 3) & ~3;  // each member 16-byte aligned in the stage
+                }
+                s_mbase[m] = sb;
+            }
+            __syncthreads();
+        }
+        const int b = pack ? s_pack.b[ci >= 0 ? ci : 0] : ct.x;
+        const int L = pack ? (ci >= 0 ? s_pack.len[ci] : 0) : clamp_length(lengths, b, Lmax);
+        const int T = pack ? 1 : fa_num_tiles(L, TILE);
+        const int t = pack ? 0 : T - 1 - ct.y;  // last tile first
+        const int s0 = pack ? 0 : fa_tile_start(L, T, t), s1 = pack ? L : fa_tile_start(L, T, t + 1);
         const int slot0 = b * ws.tmax;
         const float* r_in = coords + (size_t)b * Amax * 3;
         float* ga = grad_angles + (size_t)b * 7 * Lmax;
 
         // 1. the tile's coordinates into the stage (unless they do not fit)
-        int pc, n;
-        tile_record(ws, slot0 + t, pc, n);
+        int pc = 0, n = 0;
+        if (!pack) tile_record(ws, slot0 + t, pc, n);
+        else if (ci >= 0) n = s_mn[ci];
         const int a_end = min(pc + n, Amax);  // the tile's atoms present in the output
-        const bool staged = n <= CAP;
-        if (staged) async_copy_range<NT>(r_in, st_r, 3 * pc, 3 * a_end);
+        const bool staged = pack ? s_mbase[m] <= 3 * CAP : n <= CAP;
+        if (staged) {
+            if (pack) {
+                for (int i = 0; i < m; ++i)
+                    async_copy_range<NT>(coords + (size_t)s_pack.b[i] * Amax * 3, st_r + s_mbase[i], 0, 3 * s_mn[i]);
+            } else {
+                async_copy_range<NT>(r_in, st_r, 3 * pc, 3 * a_end);
+            }
+        }
         // atom a is at rb[rofs + 3 a]
-        const float* rb = staged ? st_r : r_in;
-        const int rofs = staged ? ((3 * pc) & 3) - 3 * pc : 0;
-        const int j0 = s0 + threadIdx.x * K;
+        const float* rb = staged ? st_r + (pack && ci >= 0 ? s_mbase[ci] : 0) : r_in;
+        const int rofs = staged && !pack ? ((3 * pc) & 3) - 3 * pc : 0;
+        const int j0 = pack ? (ci >= 0 ? threadIdx.x * K - s_pack.off[ci] : 0) : s0 + threadIdx.x * K;
         int type[K], a0[K];
         if (j0 < s1) {
             load_k<K>(seq + (size_t)b * Lmax + j0, type);
@@ -748,6 +847,14 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
 
         // 3. sums over the later threads of the tile and the chain's later tiles
         Sum6 after, total;
+        if (pack) {  // within each chain only: tail flags at the chains' last threads
+            const bool tail = ci < 0 || threadIdx.x * K + K >= s_pack.off[ci + 1];
+            after = block_seg_suffix_sum6<NT>(tsum, tail, s6, s_fl);
+            if (threadIdx.x == 0) {
+                for (int q = 0; q < 6; ++q) s_later[q] = 0.f;
+                s_next = request_tile(counter);
+            }
+        } else {
         block_suffix_sum6<NT>(tsum, s6, after, total);
         if (threadIdx.x == NT - 32 && t > 0) publish_suffix_agg(ws, slot0 + t, total);
         if (threadIdx.x < 32) {
@@ -759,6 +866,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
                 // fused step still waits for the chain's other tiles: it asks later)
                 s_next = (RES && t == 0) ? 0 : request_tile(counter);
             }
+        }
         }
         __syncthreads();
         int requested = s_next;
@@ -819,7 +927,15 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
             store_k<K>(ga + Lmax + j0, gpsi);
             store_k<K>(ga + 2 * Lmax + j0, gomg);
         }
-        if (t == T - 1 && !(ws.flags & TPL_FLAG_PADDING_ZEROED)) {  // rows past the chain's last residue
+        if (pack) {
+            if (!(ws.flags & TPL_FLAG_PADDING_ZEROED))  // rows past each chain's last residue
+                for (int i = 0; i < m; ++i) {
+                    float* gi = grad_angles + (size_t)s_pack.b[i] * 7 * Lmax;
+                    for (int jj = s_pack.len[i] + threadIdx.x; jj < Lmax; jj += NT)
+#pragma unroll
+                        for (int r = 0; r < 7; ++r) gi[r * Lmax + jj] = 0.f;
+                }
+        } else if (t == T - 1 && !(ws.flags & TPL_FLAG_PADDING_ZEROED)) {  // rows past the chain's last residue
             for (int i = L + threadIdx.x; i < Lmax; i += NT)
 #pragma unroll
                 for (int r = 0; r < 7; ++r) ga[r * Lmax + i] = 0.f;
@@ -899,6 +1015,17 @@ __global__ void __launch_bounds__(NT) fa_bwd_kernel(const float* __restrict__ an
     int v = take_tile(counter, &s_v);
     while (v < ntiles) {
         const int2 ct = ws.tiles[v];
+        if (ct.x < 0) {
+            // a pack of whole chains (a packed forward): frames are rebuilt per
+            // tile of one chain only -- the packed backward reads the coordinates
+            if (threadIdx.x == 0) flag_status(TPL_STATUS_BAD_WORKSPACE);
+            for (int i = 0; i < ct.y; ++i) {
+                float* gi = grad_angles + (size_t)ws.order[-1 - ct.x + i] * 7 * Lmax;
+                for (int q = threadIdx.x; q < 7 * Lmax; q += NT) gi[q] = 0.f;
+            }
+            v = next_tile(request_tile(counter), &s_v);
+            continue;
+        }
         const int b = ct.x;
         const int L = clamp_length(lengths, b, Lmax);
         const int T = fa_num_tiles(L, NT);
@@ -1334,31 +1461,31 @@ __global__ void fa_bwd_ref64_kernel(const uint8_t* __restrict__ seq,
 // The dynamic shared-memory limit is raised once per device and kernel, so no
 // attribute call happens during a stream capture after the first launch.
 
-template <int NT, int K, bool LM>
+template <int NT, int K, bool LM, bool PACK>
 cudaError_t fa_fwd_t(const float* angles, const uint8_t* seq, const int32_t* lengths, int Lmax,
                      int Amax, float* coords, int32_t* num_atoms, const ChainWs& ws,
                      cudaStream_t s, const float* target) {
     const size_t smem = fa_smem<NT, K>();
     static bool done[64] = {false};
-    cudaError_t e = smem_attr_once(fa_fwd_kernel<NT, K, LM>, (int)smem, done);
+    cudaError_t e = smem_attr_once(fa_fwd_kernel<NT, K, LM, PACK>, (int)smem, done);
     if (e != cudaSuccess) return e;
-    const int grid = persistent_grid((const void*)fa_fwd_kernel<NT, K, LM>, NT, smem);
-    fa_fwd_kernel<NT, K, LM><<<grid, NT, smem, s>>>(angles, seq, lengths, Lmax, Amax, coords, num_atoms,
-                                                    ws, target, fa_table());
+    const int grid = persistent_grid((const void*)fa_fwd_kernel<NT, K, LM, PACK>, NT, smem);
+    fa_fwd_kernel<NT, K, LM, PACK><<<grid, NT, smem, s>>>(angles, seq, lengths, Lmax, Amax, coords, num_atoms,
+                                                          ws, target, fa_table());
     return cudaGetLastError();
 }
 
-template <int NT, int K, bool LR, bool RES>
+template <int NT, int K, bool LR, bool RES, bool PACK>
 cudaError_t fa_bwd_coords_t(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
                             const float* coords, const float* grad_coords, float* grad_angles,
                             const ChainWs& ws, LrmsdGrad lg, cudaStream_t s) {
     const size_t smem = fa_smem<NT, K>();
     static bool done[64] = {false};
-    cudaError_t e = smem_attr_once(fa_bwd_coords_kernel<NT, K, LR, RES>, (int)smem, done);
+    cudaError_t e = smem_attr_once(fa_bwd_coords_kernel<NT, K, LR, RES, PACK>, (int)smem, done);
     if (e != cudaSuccess) return e;
-    const int grid = persistent_grid((const void*)fa_bwd_coords_kernel<NT, K, LR, RES>, NT, smem);
-    fa_bwd_coords_kernel<NT, K, LR, RES><<<grid, NT, smem, s>>>(seq, lengths, B, Lmax, Amax, coords, grad_coords,
-                                                                   grad_angles, ws, lg, fa_table());
+    const int grid = persistent_grid((const void*)fa_bwd_coords_kernel<NT, K, LR, RES, PACK>, NT, smem);
+    fa_bwd_coords_kernel<NT, K, LR, RES, PACK><<<grid, NT, smem, s>>>(seq, lengths, B, Lmax, Amax, coords,
+                                                                      grad_coords, grad_angles, ws, lg, fa_table());
     return cudaGetLastError();
 }
 
@@ -1390,12 +1517,12 @@ bool fullatom_cfg_supported(int threads, int k) {
     return false;
 }
 
-#define TPL_FA_CASE_FWD(NT, K) case NT * 8 + K: e = fa_fwd_t<NT, K, LMV>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s, target); break;
-#define TPL_FA_CASE_BWD(NT, K) case NT * 8 + K: return fa_bwd_coords_t<NT, K, LRV, RESV>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, lg, s);
+#define TPL_FA_CASE_FWD(NT, K) case NT * 8 + K: e = fa_fwd_t<NT, K, LMV, PACKV>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s, target); break;
+#define TPL_FA_CASE_BWD(NT, K) case NT * 8 + K: return fa_bwd_coords_t<NT, K, LRV, RESV, PACKV>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, lg, s);
 
 namespace {
 
-template <bool LMV>
+template <bool LMV, bool PACKV>
 cudaError_t fa_forward_shape(const float* angles, const uint8_t* seq, const int32_t* lengths, int Lmax, int Amax,
                              float* coords, int32_t* num_atoms, const ChainWs& ws, LaunchCfg cfg, cudaStream_t s,
                              const float* target) {
@@ -1407,7 +1534,7 @@ cudaError_t fa_forward_shape(const float* angles, const uint8_t* seq, const int3
     return e;
 }
 
-template <bool LRV, bool RESV>
+template <bool LRV, bool RESV, bool PACKV>
 cudaError_t fa_backward_shape(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
                               const float* coords, const float* grad_coords, float* grad_angles,
                               const ChainWs& ws, LrmsdGrad lg, LaunchCfg cfg, cudaStream_t s) {
@@ -1427,9 +1554,12 @@ cudaError_t launch_fullatom_forward(const float* angles, const uint8_t* seq,
     ChainWs ws;
     chain_ws_layout(workspace, B, Lmax, &ws, true);
     ws.flags = cfg.flags;
-    cudaError_t e = launch_schedule(lengths, B, Lmax, cfg.threads * cfg.res_per_thread, sched_mode, 1, ws, s, true);
+    cudaError_t e = launch_schedule(lengths, B, Lmax, cfg.threads * cfg.res_per_thread, sched_mode,
+                                    cfg.res_per_thread, ws, s, true);
     if (e != cudaSuccess) return e;
-    return fa_forward_shape<false>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, cfg, s, nullptr);
+    if (sched_mode == kSchedPacked)
+        return fa_forward_shape<false, true>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, cfg, s, nullptr);
+    return fa_forward_shape<false, false>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, cfg, s, nullptr);
 }
 
 cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
@@ -1443,9 +1573,12 @@ cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
     ws.flags = cfg.flags;
     cudaError_t e = reset_backward_flags(ws, s);
     if (e != cudaSuccess) return e;
+    if (from_coords && cfg.packed)
+        return fa_backward_shape<false, false, true>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles,
+                                                     ws, LrmsdGrad{}, cfg, s);
     if (from_coords)
-        return fa_backward_shape<false, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws,
-                                               LrmsdGrad{}, cfg, s);
+        return fa_backward_shape<false, false, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles,
+                                                      ws, LrmsdGrad{}, cfg, s);
     // frames rebuilt from the angles: one residue per thread
     if (cfg.res_per_thread != 1) return cudaErrorInvalidValue;
     switch (cfg.threads) {
@@ -1477,7 +1610,11 @@ cudaError_t launch_fullatom_backward_lrmsd(const uint8_t* seq, const int32_t* le
     cudaError_t e = reset_backward_flags(ws, s);
     if (e != cudaSuccess) return e;
     const LrmsdGrad lg{target, lrmsd_state, grad_lrmsd};
-    return fa_backward_shape<true, false>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, cfg, s);
+    if (cfg.packed)
+        return fa_backward_shape<true, false, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg,
+                                                    cfg, s);
+    return fa_backward_shape<true, false, false>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg,
+                                                 cfg, s);
 }
 
 cudaError_t launch_fullatom_lrmsd_forward(const float* angles, const uint8_t* seq, const int32_t* lengths,
@@ -1491,7 +1628,7 @@ cudaError_t launch_fullatom_lrmsd_forward(const float* angles, const uint8_t* se
     const int tile = cfg.threads * cfg.res_per_thread;
     cudaError_t e = launch_schedule(lengths, B, Lmax, tile, sched_mode, 1, ws, s, true);
     if (e != cudaSuccess) return e;
-    e = fa_forward_shape<true>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, cfg, s, target);
+    e = fa_forward_shape<true, false>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, cfg, s, target);
     if (e != cudaSuccess) return e;
     return launch_lrmsd_solve_tiles(coords, target, num_atoms, B, Amax, ws.tmom, ws.tmax, lengths, tile,
                                     Lmax, ws.lstate, s, true, 1);
@@ -1508,7 +1645,8 @@ cudaError_t launch_fullatom_lrmsd_backward(const uint8_t* seq, const int32_t* le
     cudaError_t e = reset_backward_flags(ws, s);
     if (e != cudaSuccess) return e;
     LrmsdGrad lg{target, ws.lstate, grad_lrmsd, lrmsd, num_atoms};
-    return fa_backward_shape<true, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg, cfg, s);
+    return fa_backward_shape<true, true, false>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg,
+                                                cfg, s);
 }
 
 cudaError_t launch_fullatom_backward_quadratic(const uint8_t* seq, const int32_t* lengths, int B, int Lmax,

@@ -14,6 +14,7 @@ struct LaunchCfg {
     int threads;        // CTA size
     int res_per_thread; // consecutive residues per thread (tile = threads * res_per_thread)
     int flags = 0;      // TPL_FLAG_*
+    bool packed = false;  // full atom: the work list may hold packs of whole chains
 };
 
 // Bytes of the chain workspace (tile list, look-back flags and aggregates,

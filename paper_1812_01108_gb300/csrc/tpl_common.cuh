@@ -291,6 +291,59 @@ __device__ __forceinline__ Rigid block_seg_scan_rigid(const Rigid& x, bool head,
 }
 
 // ---------------------------------------------------------------------------
+// Segmented block-wide exclusive scan of ints (same segments as above): the
+// sum over the earlier threads back to the segment's head (0 at a head).
+// Two __syncthreads; s_val / s_flag hold NW+1 entries.
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ int block_seg_scan_count(int x, bool head, int* s_val, int* s_flag) {
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    int inc = x;
+    int fl = head ? 1 : 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, off);
+        const int fy = __shfl_up_sync(0xffffffffu, fl, off);
+        if (lane >= off) {
+            if (!fl) inc += y;
+            fl |= fy;
+        }
+    }
+    if (lane == 31) {
+        s_val[warp] = inc;
+        s_flag[warp] = fl;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int w = (lane < NW) ? s_val[lane] : 0;
+        int wf = (lane < NW) ? s_flag[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < NW; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, off);
+            const int fy = __shfl_up_sync(0xffffffffu, wf, off);
+            if (lane >= off) {
+                if (!wf) w += y;
+                wf |= fy;
+            }
+        }
+        int wex = __shfl_up_sync(0xffffffffu, w, 1);
+        if (lane == 0) wex = 0;
+        if (lane < NW) s_val[lane] = wex;
+    }
+    __syncthreads();
+    int lex = __shfl_up_sync(0xffffffffu, inc, 1);
+    int lexf = __shfl_up_sync(0xffffffffu, fl, 1);
+    if (lane == 0) {
+        lex = 0;
+        lexf = 0;
+    }
+    if (head) return 0;
+    return lexf ? lex : s_val[warp] + lex;
+}
+
+// ---------------------------------------------------------------------------
 // Block-wide exclusive REVERSE (suffix) scan of a 6-float sum (r x g, g):
 // `after` = sum over threads with a larger index; `total` = sum over all
 // threads.  scratch: NW+1 float[6].  Two __syncthreads.

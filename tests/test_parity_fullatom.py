@@ -178,6 +178,95 @@ def test_tiles_whose_atoms_overflow_the_stage_match_the_oracle():
         assert rel_err(ga32, g64) <= GRAD_TOL
 
 
+def _short_chain_inputs(seed, trp=False):
+    """Many chains shorter than a tile (packed several per CTA), empty and
+    one-residue chains, and a few chains longer than a tile."""
+    rng = np.random.default_rng(seed)
+    lengths = rng.integers(1, 120, size=48).astype(np.int32)
+    lengths[:6] = [0, 1, 2, 383, 384, 700]
+    a, seq = workloads.fullatom_inputs(lengths, rng, Lmax=700)
+    if trp:  # 14 atoms per residue: packs whose atoms overflow the stage
+        seq[:] = 17
+    a[:, 2] += rng.normal(0, 0.2, size=a[:, 2].shape).astype(np.float32)
+    a *= (np.arange(700)[None, :] < lengths[:, None])[:, None, :]
+    Amax = workloads.pad_to(oracle.max_atoms(seq, lengths))
+    c64, na64 = oracle.fullatom_forward(a, seq, lengths, Amax)
+    g = workloads.upstream_grad((len(lengths), Amax, 3), rng)
+    g = (g * (np.arange(Amax)[None, :] < na64[:, None])[:, :, None]).astype(np.float32)
+    return a, seq, lengths, g, Amax, c64, na64, oracle.fullatom_backward(a, seq, lengths, g)
+
+
+@pytest.mark.parametrize("shape,trp", [((384, 1), False), ((128, 2), False), ((192, 4), False), ((64, 4), False),
+                                       ((384, 1), True), ((128, 2), True)])
+def test_packed_short_chains_match_the_oracle(shape, trp):
+    """Chains per CTA > 1 in the full-atom kernels (SCHED_PACKED): segmented
+    scans, per-chain stores, the backward from the coordinates; with all-TRP
+    chains the packs overflow the stage and go straight to global memory."""
+    a, seq, lengths, g, Amax, c64, na64, g64 = _short_chain_inputs(81 + shape[0], trp)
+    opts = {"threads": shape[0], "res_per_thread": shape[1], "schedule": tpl.SCHED_PACKED}
+    c32, na32, ga32 = _run_fp32(a, seq, lengths, g, Amax, opts, from_coords=True)
+    assert np.array_equal(na32, na64)
+    assert np.abs(c32 - c64).max() <= COORD_TOL
+    assert rel_err(ga32, g64) <= GRAD_TOL
+    for b, L in enumerate(lengths):
+        assert np.all(c32[b, na64[b]:] == 0) and np.all(ga32[b, :, L:] == 0)
+    # the padding flag: identical real rows on NaN-filled outputs
+    c2, na2, g2 = _run_fp32(a, seq, lengths, g, Amax, dict(opts, flags=tpl.FLAG_PADDING_ZEROED), True)
+    for b, L in enumerate(lengths):
+        assert np.array_equal(c2[b, :na64[b]], c32[b, :na64[b]]) and np.array_equal(g2[b, :, :L], ga32[b, :, :L])
+
+
+def test_packed_lrmsd_backward_matches_the_oracle():
+    """The LRMSD gradient formed inside the packed full-atom backward."""
+    d = require_gpu()
+    a, seq, lengths, _, Amax, c64, na64, _ = _short_chain_inputs(91)
+    rng = np.random.default_rng(92)
+    ta = workloads.perturb_angles(a, lengths, rng, rows=(0, 1, 3, 4, 5, 6))
+    B, _, Lmax = a.shape
+    opts = {"threads": 192, "res_per_thread": 2, "schedule": tpl.SCHED_PACKED}
+    A, S, Ln = dev(a, d), dev(seq, d), dev(lengths, d)
+    ws = torch.empty(tpl.tpl_fullatom_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    tgt = torch.zeros((B, Amax, 3), device=d)
+    na = torch.zeros((B,), dtype=torch.int32, device=d)
+    tpl.tpl_fullatom_forward(dev(ta, d), S, Ln, tgt, na, ws, opts)
+    c = torch.zeros_like(tgt)
+    tpl.tpl_fullatom_forward(A, S, Ln, c, na, ws, opts)
+    lr = torch.zeros((B,), device=d)
+    lr_ws = torch.empty(tpl.tpl_lrmsd_workspace_size(B, Amax), dtype=torch.uint8, device=d)
+    tpl.tpl_lrmsd_forward(c, tgt, na, lr, lr_ws)
+    w = dev(np.linspace(-1.0, 2.0, B).astype(np.float32), d)
+    ga = torch.full_like(A, float("nan"))
+    tpl.tpl_fullatom_backward_lrmsd(A, S, Ln, c, tgt, w, lr_ws, ga, ws, opts)
+    torch.cuda.synchronize()
+    gc64 = oracle.lrmsd_backward(host(w).astype(np.float64), host(c), host(tgt), na64)
+    g64 = oracle.fullatom_backward(a, seq, lengths, gc64)
+    m = lengths >= 2
+    assert rel_err(host(ga)[m], g64[m]) <= GRAD_TOL
+
+
+def test_packed_schedule_needs_the_coordinate_backward():
+    """A packed forward with RECOMPUTE is rejected; a backward that rebuilds
+    frames on a packed workspace flags it and writes zeros."""
+    d = require_gpu()
+    a, seq, lengths, g, Amax, *_ = _short_chain_inputs(95)
+    B, _, Lmax = a.shape
+    A, S, Ln = dev(a, d), dev(seq, d), dev(lengths, d)
+    ws = torch.empty(tpl.tpl_fullatom_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+    c = torch.zeros((B, Amax, 3), device=d)
+    na = torch.zeros((B,), dtype=torch.int32, device=d)
+    with pytest.raises(tpl.TplError):
+        tpl.tpl_fullatom_forward(A, S, Ln, c, na, ws, {"threads": 128, "res_per_thread": 1,
+                                                       "schedule": tpl.SCHED_PACKED, "bwd_mode": tpl.BWD_RECOMPUTE})
+    tpl.tpl_get_status()
+    o = {"threads": 128, "res_per_thread": 1, "schedule": tpl.SCHED_PACKED}
+    tpl.tpl_fullatom_forward(A, S, Ln, c, na, ws, o)
+    ga = torch.full_like(A, float("nan"))
+    tpl.tpl_fullatom_backward(A, S, Ln, None, dev(g, d), ga, ws, dict(o, bwd_mode=tpl.BWD_RECOMPUTE))
+    torch.cuda.synchronize()
+    assert tpl.tpl_get_status() & tpl.STATUS_BAD_WORKSPACE
+    assert np.all(np.isfinite(host(ga)))
+
+
 def test_recompute_needs_one_residue_per_thread():
     d = require_gpu()
     lengths = np.array([40], np.int32)
