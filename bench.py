@@ -76,6 +76,9 @@ TRAFFIC = {
 }
 
 
+# --schedule: TPL_SCHED_* of the chain calls
+SCHEDULES = {"auto": 0, "longest": 1, "batch": 2, "packed": 3}
+
 # launch shapes of the backbone training-step kernel
 STEP_SHAPES = [(128, 4), (256, 4), (256, 2), (128, 2), (512, 2)]
 
@@ -102,6 +105,8 @@ def parse(argv=None):
                    help="use the library's default launch shape instead of the autotuner's pick")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 per-chain comparison")
+    p.add_argument("--schedule", default="auto", choices=sorted(SCHEDULES),
+                   help="work-list schedule of the chain calls (anything but auto skips the autotuner)")
     p.add_argument("--write-padding", action="store_true",
                    help="chain calls write their outputs' padding every call (default: the bench "
                         "zeroes the output buffers once and passes TPL_FLAG_PADDING_ZEROED)")
@@ -456,7 +461,7 @@ def setup_training_step(args, tpl, torch, dev, d):
     a, seq, lengths, ta = d["angles"], d["seq"], d["lengths"], d["target_angles"]
     B, Lmax = a.shape[0], a.shape[2]
     Amax = workloads.pad_to(tpl.fullatom_max_atoms(seq, lengths))
-    opts = tpl.Opts(threads=args.threads, res_per_thread=args.res_per_thread,
+    opts = tpl.Opts(threads=args.threads, res_per_thread=args.res_per_thread, schedule=SCHEDULES[args.schedule],
                     bwd_mode=tpl.BWD_FROM_COORDS if args.bwd == "coords" else tpl.BWD_RECOMPUTE)
     A = torch.from_numpy(a).to(dev)
     S = torch.from_numpy(seq).to(dev)
@@ -477,7 +482,7 @@ def setup_training_step(args, tpl, torch, dev, d):
     n_atoms = int(na_t.sum().item())
     tuned = None
     gtune = None
-    if not args.no_autotune and not args.threads:
+    if not args.no_autotune and not args.threads and args.schedule == "auto":
         if args.bwd == "coords" and args.fusion == "backward":
             # the three calls of the timed step
             opts, tms = tpl.tpl_fullatom_lrmsd_autotune(A, S, Ln, coords, na, target, wgt, lr, lr_ws, gang, fa_ws)
@@ -600,7 +605,7 @@ def setup_training_step(args, tpl, torch, dev, d):
 def setup_backbone_uneven(args, tpl, torch, dev, d):
     a, lengths, ta = d["angles"], d["lengths"], d["target_angles"]
     B, Lmax = a.shape[0], a.shape[2]
-    opts = tpl.Opts(threads=args.threads, res_per_thread=args.res_per_thread,
+    opts = tpl.Opts(threads=args.threads, res_per_thread=args.res_per_thread, schedule=SCHEDULES[args.schedule],
                     bwd_mode=tpl.BWD_FROM_COORDS if args.bwd == "coords" else tpl.BWD_RECOMPUTE)
     A = torch.from_numpy(a).to(dev)
     Ln = torch.from_numpy(lengths).to(dev)
@@ -623,7 +628,7 @@ def setup_backbone_uneven(args, tpl, torch, dev, d):
         st_ws = torch.empty(tpl.tpl_backbone_lrmsd_workspace_size(B, Lmax), dtype=torch.uint8, device=dev)
         if opts.res_per_thread == 0 and opts.threads == 0:
             opts.threads, opts.res_per_thread = 128, 4
-    if not args.no_autotune and not args.threads and not args.res_per_thread:
+    if not args.no_autotune and not args.threads and not args.res_per_thread and args.schedule == "auto":
         if step_fused:
             # the training-step shapes, timed as the step is timed
             cands = [tpl.Opts(threads=t, res_per_thread=k, schedule=tpl.SCHED_PACKED) for t, k in STEP_SHAPES]
