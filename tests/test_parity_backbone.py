@@ -197,6 +197,33 @@ def test_backbone_with_o_matches_the_oracle(reference_o, threads, k, sched, bwd)
         assert np.all(o[b, L:] == 0) and np.all(ga[b, :, L:] == 0)
 
 
+def test_backbone_with_o_padding_flag():
+    """FLAG_PADDING_ZEROED on the O calls: real residues unchanged on NaN-filled outputs."""
+    d = require_gpu()
+    lengths = np.array([0, 1, 70, 513, 300], np.int32)
+    a, g = _inputs(lengths, 7, Lmax=520)
+    rng = np.random.default_rng(8)
+    go = workloads.upstream_grad((len(lengths), a.shape[2], 3), rng, valid=lengths)
+    B, _, Lmax = a.shape
+    A, Ln = dev(a, d), dev(lengths, d)
+    out = []
+    for flags, fill in ((0, 0.0), (tpl.FLAG_PADDING_ZEROED, float("nan"))):
+        opts = {"threads": 128, "res_per_thread": 4, "flags": flags, "bwd_mode": tpl.BWD_FROM_COORDS}
+        ws = torch.empty(tpl.tpl_backbone_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
+        c = torch.full((B, 3 * Lmax, 3), fill, device=d)
+        o = torch.full((B, Lmax, 3), fill, device=d)
+        tpl.tpl_backbone_forward_o(A, Ln, c, o, ws, opts)
+        ga = torch.full_like(A, fill)
+        tpl.tpl_backbone_backward_o(A, Ln, c, o, dev(g, d), dev(go, d), ga, ws, opts)
+        torch.cuda.synchronize()
+        out.append((host(c), host(o), host(ga)))
+    (c0, o0, g0), (c1, o1, g1) = out
+    for b, L in enumerate(lengths):
+        assert np.array_equal(c1[b, :3 * L], c0[b, :3 * L]) and np.array_equal(o1[b, :L], o0[b, :L])
+        assert np.array_equal(g1[b, :, :L], g0[b, :, :L])
+        assert np.all(o0[b, L:] == 0) and np.all(g0[b, :, L:] == 0)
+
+
 def test_backbone_with_o_autograd_and_rejected_shapes():
     d = require_gpu()
     lengths = np.array([40, 17, 1], np.int32)
