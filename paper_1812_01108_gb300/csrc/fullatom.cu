@@ -323,6 +323,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
     const int32_t* __restrict__ lengths, int Lmax, int Amax, float* __restrict__ coords,
     int32_t* __restrict__ num_atoms, ChainWs ws, const float* __restrict__ target,
     const __grid_constant__ FaTable tab) {
+    static_assert(!(LM && PACK), "the fused step's schedule has no packs");
     constexpr int NW = NT / 32;
     constexpr int TILE = NT * K;
     constexpr int CAP = fa_stage_atoms<NT, K>();
@@ -430,20 +431,20 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
             __syncthreads();
             tile_atoms = ci >= 0 ? s_mtot[ci] : 0;
         } else {
-        block_scan_rigid_count<NT>(A, cnt, s_rig, s_cnt, X, a0, Tot, tile_atoms);
-        if (threadIdx.x == NT - 32 && t + 1 < T) publish_prefix_agg(ws, slot0 + t, Tot, tile_atoms);
+            block_scan_rigid_count<NT>(A, cnt, s_rig, s_cnt, X, a0, Tot, tile_atoms);
+            if (threadIdx.x == NT - 32 && t + 1 < T) publish_prefix_agg(ws, slot0 + t, Tot, tile_atoms);
 
-        // 3. frame at the tile start and its first atom (one warp)
-        if (threadIdx.x < 32) {
-            int pc = 0;
-            const Rigid P = gather_prefix(ws, slot0, t, pc);
-            if (threadIdx.x == 0) {
-                s_next = request_tile(ws.hdr + kHdrFwdNext);  // after the last wait of this tile
-                store_rigid_g(s_start, P, pc, tile_atoms);
-                store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, pc, tile_atoms);
+            // 3. frame at the tile start and its first atom (one warp)
+            if (threadIdx.x < 32) {
+                int pc = 0;
+                const Rigid P = gather_prefix(ws, slot0, t, pc);
+                if (threadIdx.x == 0) {
+                    s_next = request_tile(ws.hdr + kHdrFwdNext);  // after the last wait of this tile
+                    store_rigid_g(s_start, P, pc, tile_atoms);
+                    store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, pc, tile_atoms);
+                }
             }
-        }
-        __syncthreads();
+            __syncthreads();
         }
         int pc = 0;
         const Rigid P = pack ? rigid_identity() : load_rigid_prev(s_start, pc);
@@ -554,15 +555,14 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
                 if (!(ws.flags & TPL_FLAG_PADDING_ZEROED)) zero_range<NT>(oi, 3 * min(n, Amax), 3 * Amax);
             }
         } else {
-        if (end_atom > Amax && threadIdx.x == 0) flag_status(TPL_STATUS_TOO_MANY_ATOMS);
-        if (staged) store_range<NT>(out, stage, 3 * pc, 3 * (pc + nout));
-        if (t == T - 1) {
-            if (threadIdx.x == 0) num_atoms[b] = end_atom;
-            if (!(ws.flags & TPL_FLAG_PADDING_ZEROED)) zero_range<NT>(out, 3 * min(end_atom, Amax), 3 * Amax);
+            if (end_atom > Amax && threadIdx.x == 0) flag_status(TPL_STATUS_TOO_MANY_ATOMS);
+            if (staged) store_range<NT>(out, stage, 3 * pc, 3 * (pc + nout));
+            if (t == T - 1) {
+                if (threadIdx.x == 0) num_atoms[b] = end_atom;
+                if (!(ws.flags & TPL_FLAG_PADDING_ZEROED)) zero_range<NT>(out, 3 * min(end_atom, Amax), 3 * Amax);
+            }
         }
-        }
-        if constexpr (LM) {
-          if (!pack) {  // (the fused step's schedule has no packs)
+        if constexpr (LM) {  // (never with PACK: the fused step's schedule has no packs)
             const float* tg = target + (size_t)b * Amax * 3;
             const float3 x0 = make_float3(__ldg(tg), __ldg(tg + 1), __ldg(tg + 2));
             // the tile's coordinates: the stage, or (tiles that bypass it) this
@@ -601,7 +601,6 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
                 for (int w = 0; w < NW; ++w) x += s_mom[w][threadIdx.x];
                 ws.tmom[(size_t)(slot0 + t) * 20 + threadIdx.x] = x;
             }
-          }
         }
         v = next_tile(requested, &s_v);
     }
@@ -855,18 +854,18 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
                 s_next = request_tile(counter);
             }
         } else {
-        block_suffix_sum6<NT>(tsum, s6, after, total);
-        if (threadIdx.x == NT - 32 && t > 0) publish_suffix_agg(ws, slot0 + t, total);
-        if (threadIdx.x < 32) {
-            const Sum6 later = gather_suffix(ws, slot0, t, T);
-            if (threadIdx.x == 0) {
-                s_later[0] = later.c.x; s_later[1] = later.c.y; s_later[2] = later.c.z;
-                s_later[3] = later.g.x; s_later[4] = later.g.y; s_later[5] = later.g.z;
-                // after the last wait of this tile (the chain's first tile of a
-                // fused step still waits for the chain's other tiles: it asks later)
-                s_next = (RES && t == 0) ? 0 : request_tile(counter);
+            block_suffix_sum6<NT>(tsum, s6, after, total);
+            if (threadIdx.x == NT - 32 && t > 0) publish_suffix_agg(ws, slot0 + t, total);
+            if (threadIdx.x < 32) {
+                const Sum6 later = gather_suffix(ws, slot0, t, T);
+                if (threadIdx.x == 0) {
+                    s_later[0] = later.c.x; s_later[1] = later.c.y; s_later[2] = later.c.z;
+                    s_later[3] = later.g.x; s_later[4] = later.g.y; s_later[5] = later.g.z;
+                    // after the last wait of this tile (the chain's first tile of a
+                    // fused step still waits for the chain's other tiles: it asks later)
+                    s_next = (RES && t == 0) ? 0 : request_tile(counter);
+                }
             }
-        }
         }
         __syncthreads();
         int requested = s_next;
