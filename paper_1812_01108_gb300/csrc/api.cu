@@ -65,11 +65,11 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 // ---------------------------------------------------------------------------
 constexpr int kBuckets = 64;
 constexpr int kKeys = kBuckets + kMaxPack;
+constexpr int kSchedThreadsSmall = 256;  // batches of at most kSchedSmallB chains
 constexpr int kSchedThreads = 1024;
-constexpr int kSchedWarps = kSchedThreads / 32;
+constexpr int kSchedSmallB = 1024;
 constexpr int kSchedCache = 16384;  // chains whose length, key and order entry stay in shared memory
-constexpr int kZeroPerCta = 4 * kSchedThreads;
-static_assert(kKeys < 127, "keys fit 7 bits with 127 left for lanes past the run");  // int4 words zeroed per flag-zeroing CTA and pass
+constexpr int kZeroPerCta = 4 * kSchedThreadsSmall;  // int4 words zeroed per flag-zeroing CTA and pass
 
 __device__ __forceinline__ int sched_key(int L, int Lmax, int tile, int mode, int granule) {
     if (mode == kSchedPacked && L <= tile) {  // chains per packed tile, 1..kMaxPack
@@ -86,13 +86,14 @@ __device__ __forceinline__ int sched_len(const int32_t* lengths, int b, int Lmax
     return L < 0 ? 0 : (L > Lmax ? Lmax : L);
 }
 
-__global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* __restrict__ lengths,
+template <int NTS>
+__global__ void __launch_bounds__(NTS) schedule_kernel(const int32_t* __restrict__ lengths,
                                                                  int B, int Lmax, int tile, int mode,
                                                                  int granule, bool balanced, ChainWs ws) {
     if (blockIdx.x > 0) {  // flag zeroing, 16 bytes at a time (the regions are 256-byte aligned)
         const int n = B * ws.tmax;
-        const size_t stride = (size_t)(gridDim.x - 1) * kSchedThreads;
-        const size_t i0 = (size_t)(blockIdx.x - 1) * kSchedThreads + threadIdx.x;
+        const size_t stride = (size_t)(gridDim.x - 1) * NTS;
+        const size_t i0 = (size_t)(blockIdx.x - 1) * NTS + threadIdx.x;
         int4* f4 = reinterpret_cast<int4*>(ws.fflag);
         for (size_t i = i0; i < (size_t)n / 4; i += stride) f4[i] = make_int4(0, 0, 0, 0);
         if (i0 < (size_t)(n & 3)) ws.fflag[(n & ~3) + i0] = 0;
@@ -104,6 +105,7 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
         return;
     }
     __shared__ int s_start[kKeys + 1];
+    constexpr int kSchedWarps = NTS / 32;
     __shared__ int s_wcnt[kSchedWarps][kKeys];  // per warp: key counts, then next position per key
     __shared__ int s_part[33];
     extern __shared__ int s_cache[];  // [ncache] lengths, [ncache] order entries, [ncache] keys (bytes)
@@ -115,23 +117,23 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     // four independent loads in flight per thread, then the keys
-    for (int b0 = 0; b0 < ncache; b0 += 4 * kSchedThreads) {
+    for (int b0 = 0; b0 < ncache; b0 += 4 * NTS) {
         int L[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int b = b0 + q * kSchedThreads + threadIdx.x;
+            const int b = b0 + q * NTS + threadIdx.x;
             L[q] = b < ncache ? sched_len(lengths, b, Lmax) : 0;
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int b = b0 + q * kSchedThreads + threadIdx.x;
+            const int b = b0 + q * NTS + threadIdx.x;
             if (b < ncache) {
                 s_len[b] = L[q];
                 s_key[b] = (unsigned char)sched_key(L[q], Lmax, tile, mode, granule);
             }
         }
     }
-    for (int i = threadIdx.x; i < kSchedWarps * kKeys; i += kSchedThreads) (&s_wcnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kSchedWarps * kKeys; i += NTS) (&s_wcnt[0][0])[i] = 0;
     __syncthreads();
     auto len = [&](int b) { return b < ncache ? s_len[b] : sched_len(lengths, b, Lmax); };
     auto key = [&](int b) {
@@ -157,14 +159,14 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
         __syncthreads();
         // 2. per key, exclusive scan over the warps (warp w scans keys w, w + 32, ...)
         for (int k = warp; k < kKeys; k += kSchedWarps) {
-            const int c = s_wcnt[lane][k];
+            const int c = lane < kSchedWarps ? s_wcnt[lane][k] : 0;
             int inc = c;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, inc, off);
                 if (lane >= off) inc += y;
             }
-            s_wcnt[lane][k] = inc - c;
+            if (lane < kSchedWarps) s_wcnt[lane][k] = inc - c;
             if (lane == 31) s_start[k] = inc;  // the key's count, scanned below
         }
         __syncthreads();
@@ -206,11 +208,11 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
             __syncwarp();
         }
     } else {
-        for (int b = threadIdx.x; b < B; b += kSchedThreads) set_order(b, b);
+        for (int b = threadIdx.x; b < B; b += NTS) set_order(b, b);
     }
     __syncthreads();
     // each thread owns a contiguous run of the ordered chains
-    const int per = (B + kSchedThreads - 1) / kSchedThreads;
+    const int per = (B + NTS - 1) / NTS;
     const int i0 = threadIdx.x * per, i1 = min(B, i0 + per);
     auto ntiles = [&](int L) {
         if (balanced) return fa_num_tiles(L, tile);
@@ -235,14 +237,14 @@ __global__ void __launch_bounds__(kSchedThreads) schedule_kernel(const int32_t* 
     if (lane == 31) s_part[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-        const int w = s_part[lane];
+        const int w = lane < kSchedWarps ? s_part[lane] : 0;
         int wi = w;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, wi, off);
             if (lane >= off) wi += y;
         }
-        s_part[lane] = wi - w;  // exclusive prefix of warp totals
+        if (lane < kSchedWarps) s_part[lane] = wi - w;  // exclusive prefix of warp totals
         if (lane == 31) s_part[32] = wi;
     }
     __syncthreads();
@@ -379,7 +381,7 @@ cudaError_t launch_schedule(const int32_t* lengths, int B, int Lmax, int tile, i
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!raised[dev]) {
-        e = cudaFuncSetAttribute(schedule_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(schedule_kernel<kSchedThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sched_smem(kSchedCache));
         if (e != cudaSuccess) return e;
         raised[dev] = true;
@@ -387,8 +389,15 @@ cudaError_t launch_schedule(const int32_t* lengths, int B, int Lmax, int tile, i
     // CTA 0 sorts; the others zero the flags (one pass of kZeroPerCta words each)
     const size_t words = ((size_t)B * ws.tmax + 3) / 4;
     const int zero_ctas = (int)std::min<size_t>(148, (words + kZeroPerCta - 1) / kZeroPerCta);
-    schedule_kernel<<<1 + std::max(zero_ctas, 1), kSchedThreads, sched_smem(B < kSchedCache ? B : kSchedCache), s>>>(
-        lengths, B, Lmax, tile, mode, granule, balanced, ws);
+    // a small batch sorts with fewer threads (fewer warps to synchronise; a few
+    // chains per thread either way); its shared memory stays under 48 KB
+    if (B <= kSchedSmallB)
+        schedule_kernel<kSchedThreadsSmall><<<1 + std::max(zero_ctas, 1), kSchedThreadsSmall, sched_smem(B), s>>>(
+            lengths, B, Lmax, tile, mode, granule, balanced, ws);
+    else
+        schedule_kernel<kSchedThreads><<<1 + std::max(zero_ctas, 1), kSchedThreads,
+                                         sched_smem(B < kSchedCache ? B : kSchedCache), s>>>(
+            lengths, B, Lmax, tile, mode, granule, balanced, ws);
     return cudaGetLastError();
 }
 
