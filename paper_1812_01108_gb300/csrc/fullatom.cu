@@ -183,6 +183,75 @@ __device__ __forceinline__ void async_copy_range(const float* __restrict__ glob,
     for (int i = tail + threadIdx.x; i < g1; i += NT) cp_async4(stage + off + i - g0, glob + i);
 }
 
+// Bulk copies through the TMA engine (cp.async.bulk, not tensor-mapped): one
+// thread moves a 16-byte aligned run of global memory into this CTA's shared
+// memory, and an mbarrier counts the bytes in.  Every wait is bounded.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One thread: the barrier's next phase expects `bytes`, and the copy delivers
+// them.  The fence orders this CTA's earlier generic accesses to the stage
+// before the async-proxy writes.
+__device__ __forceinline__ void bulk_load(float* dst, const float* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned phase) {
+    unsigned done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done)
+                 : "r"(smem_addr(bar)), "r"(phase)
+                 : "memory");
+    return done != 0;
+}
+
+// Bounded wait for the phase to complete; a give-up sets TPL_STATUS_TIMEOUT
+// and then waits once more (bounded) so that no copy lands after the CTA has
+// moved on if it can be helped.
+__device__ __forceinline__ void mbar_wait(uint64_t* bar, unsigned phase) {
+    for (int round = 0; round < 2; ++round) {
+        for (int it = 0; it < kSpinLimit; ++it) {
+            if (mbar_test(bar, phase)) return;
+            if (it >= kSpinFast) __nanosleep(100);
+        }
+        if (round == 0 && threadIdx.x == 0) flag_status(TPL_STATUS_TIMEOUT);
+    }
+}
+
+// async_copy_range with the 16-byte aligned middle moved by one bulk copy:
+// stage[off + i - g0] <- glob[i], off = g0 mod 4.  Returns whether a bulk copy
+// was issued (the same answer in every thread); the caller then waits on `bar`.
+template <int NT>
+__device__ __forceinline__ bool bulk_copy_range(const float* __restrict__ glob, float* __restrict__ stage, int g0,
+                                                int g1, uint64_t* bar) {
+    if (g1 <= g0) return false;
+    const int off = g0 & 3;
+    const int head = min(g1, (g0 + 3) & ~3);
+    const int tail = max(head, g1 & ~3);
+    for (int i = g0 + threadIdx.x; i < head; i += NT) cp_async4(stage + off + i - g0, glob + i);
+    for (int i = tail + threadIdx.x; i < g1; i += NT) cp_async4(stage + off + i - g0, glob + i);
+    if (tail <= head) return false;
+    float* dst = stage + off + head - g0;  // a multiple of 4 floats from the 16-byte aligned stage
+    const float* src = glob + head;        // 16-byte aligned: the row is, and head is a multiple of 4
+    const unsigned bytes = 4u * (unsigned)(tail - head);
+    if (((smem_addr(dst) | (unsigned)reinterpret_cast<uintptr_t>(src)) & 15u) != 0u) {  // (not expected)
+        for (int i = head + threadIdx.x; i < tail; i += NT) cp_async4(stage + off + i - g0, glob + i);
+        return false;
+    }
+    if (threadIdx.x == 0) bulk_load(dst, src, bytes, bar);
+    return true;
+}
+
 template <int NT>
 __device__ __forceinline__ void zero_range(float* __restrict__ glob, int g0, int g1) {
     if (g1 <= g0) return;
@@ -650,6 +719,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
     __shared__ PackS s_pack;  // a pack of whole short chains
     __shared__ int s_fl[NW + 1];
     __shared__ int s_mn[kMaxPack], s_mbase[kMaxPack + 1];  // atoms per member, stage offsets (floats)
+    __shared__ __align__(8) uint64_t s_bar;  // completes when a tile's bulk copy has landed
     extern __shared__ float4 s_dyn[];
     float* st_r = reinterpret_cast<float*>(s_dyn);  // the tile's coordinates
 
@@ -660,6 +730,8 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
         return;
     }
     load_table(s_tab, tab);
+    if (threadIdx.x == 0) mbar_init(&s_bar);  // visible after take_tile's barrier
+    unsigned bphase = 0;                      // the barrier phase the next bulk copy completes
     const int ntiles = ws.hdr[kHdrTiles];
     int* counter = ws.bflag + ws.slots;
     int v = take_tile(counter, &s_v);
@@ -712,12 +784,13 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
         else if (ci >= 0) n = s_mn[ci];
         const int a_end = min(pc + n, Amax);  // the tile's atoms present in the output
         const bool staged = pack ? s_mbase[m] <= 3 * CAP : n <= CAP;
+        bool bulk = false;  // the tile's aligned middle comes in by one bulk copy
         if (staged) {
             if (pack) {
                 for (int i = 0; i < m; ++i)
                     async_copy_range<NT>(coords + (size_t)s_pack.b[i] * Amax * 3, st_r + s_mbase[i], 0, 3 * s_mn[i]);
             } else {
-                async_copy_range<NT>(r_in, st_r, 3 * pc, 3 * a_end);
+                bulk = bulk_copy_range<NT>(r_in, st_r, 3 * pc, 3 * a_end, &s_bar);
             }
         }
         // atom a is at rb[rofs + 3 a]
@@ -759,6 +832,10 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
             s.g = f3_add(s.g, g);
         };
         cp_async_wait_all();
+        if (bulk) {
+            mbar_wait(&s_bar, bphase);
+            bphase ^= 1u;
+        }
         __syncthreads();
 
         // 2. residue sums and chi gradients; with up to two residues per thread
