@@ -188,6 +188,10 @@ __device__ __forceinline__ void async_copy_range(const float* __restrict__ glob,
 // memory, and an mbarrier counts the bytes in.  Every wait is bounded.
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+// Orders this thread's generic shared-memory accesses before later
+// async-proxy (bulk copy) accesses to the same memory.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -250,6 +254,42 @@ __device__ __forceinline__ bool bulk_copy_range(const float* __restrict__ glob, 
     }
     if (threadIdx.x == 0) bulk_load(dst, src, bytes, bar);
     return true;
+}
+
+// Bulk store (TMA engine) of a 16-byte aligned run of this CTA's shared
+// memory to global memory, issued by one thread into a bulk group.  Before the
+// run is overwritten the thread waits for the group's reads
+// (bulk_store_wait_read); before the kernel ends, for its writes.
+__device__ __forceinline__ void bulk_store(float* dst, const float* src, unsigned bytes) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_addr(src)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_store_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// store_range for a stage laid out as stage[off + i - g0] <-> glob[i], off =
+// g0 mod 4: the ragged ends by the threads, the 16-byte aligned middle by one
+// bulk store (which runs on while the CTA goes on to its next tile).
+template <int NT>
+__device__ __forceinline__ void bulk_store_range(float* __restrict__ glob, const float* __restrict__ stage, int g0,
+                                                 int g1) {
+    if (g1 <= g0) return;
+    const int off = g0 & 3;
+    const int head = min(g1, (g0 + 3) & ~3);
+    const int tail = max(head, g1 & ~3);
+    for (int i = g0 + threadIdx.x; i < head; i += NT) glob[i] = stage[off + i - g0];
+    for (int i = tail + threadIdx.x; i < g1; i += NT) glob[i] = stage[off + i - g0];
+    if (tail <= head) return;
+    const float* src = stage + off + head - g0;
+    float* dst = glob + head;
+    if (((smem_addr(src) | (unsigned)reinterpret_cast<uintptr_t>(dst)) & 15u) != 0u) {  // (not expected)
+        for (int i = head + threadIdx.x; i < tail; i += NT) glob[i] = stage[off + i - g0];
+        return;
+    }
+    if (threadIdx.x == 0) bulk_store(dst, src, 4u * (unsigned)(tail - head));
 }
 
 template <int NT>
@@ -493,6 +533,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
                     sb += s_mtot[i];
                 }
                 s_mbase[m] = sb;
+                bulk_store_wait_read();  // the previous tile's stage is read out before it is refilled
             }
             if (threadIdx.x < m)  // the record the backward reads: first atom 0, the chain's atom count
                 store_rigid_g(ws.start + 4 * (size_t)s_pack.b[threadIdx.x] * ws.tmax, rigid_identity(), 0,
@@ -511,6 +552,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
                     s_next = request_tile(ws.hdr + kHdrFwdNext);  // after the last wait of this tile
                     store_rigid_g(s_start, P, pc, tile_atoms);
                     store_rigid_g(ws.start + 4 * (size_t)(slot0 + t), P, pc, tile_atoms);
+                    bulk_store_wait_read();  // the previous tile's stage is read out before it is refilled
                 }
             }
             __syncthreads();
@@ -524,7 +566,10 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
         // (a pack: every member's atoms, one after the other)
         const bool staged = pack ? s_mbase[m] <= CAP : tile_atoms <= CAP;
         const int sbase = pack && ci >= 0 ? s_mbase[ci] : 0;
-        float* dst = staged ? stage + 3 * sbase : out + 3 * (size_t)pc;
+        // a tile's stage starts at float (3 pc) mod 4, so that its 16-byte
+        // aligned middle maps onto 16-byte aligned global memory (bulk store)
+        const int soff = pack ? 0 : (3 * pc) & 3;
+        float* dst = staged ? stage + soff + 3 * sbase : out + 3 * (size_t)pc;
         const int lim = staged ? CAP - sbase : Amax - pc;  // tile atoms at or past it are not written
 
         // 4. atoms in the chain's frame
@@ -590,6 +635,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
             // of 4; past the chain's end the entries are unused)
             store_k<K>(ws.ratom + (size_t)b * Lmax + j0, ra);
         }
+        fence_proxy_async();  // the stage writes, ordered before the bulk store that reads them
         __syncthreads();
         {
             // the next tile's angle rows and sequence into L2 while this tile is stored
@@ -625,7 +671,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
             }
         } else {
             if (end_atom > Amax && threadIdx.x == 0) flag_status(TPL_STATUS_TOO_MANY_ATOMS);
-            if (staged) store_range<NT>(out, stage, 3 * pc, 3 * (pc + nout));
+            if (staged) bulk_store_range<NT>(out, stage, 3 * pc, 3 * (pc + nout));
             if (t == T - 1) {
                 if (threadIdx.x == 0) num_atoms[b] = end_atom;
                 if (!(ws.flags & TPL_FLAG_PADDING_ZEROED)) zero_range<NT>(out, 3 * min(end_atom, Amax), 3 * Amax);
@@ -636,7 +682,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
             const float3 x0 = make_float3(__ldg(tg), __ldg(tg + 1), __ldg(tg + 2));
             // the tile's coordinates: the stage, or (tiles that bypass it) this
             // CTA's own global writes, visible after the barrier above
-            const float* ys = staged ? stage : out + 3 * (size_t)pc;
+            const float* ys = staged ? stage + soff : out + 3 * (size_t)pc;
             float m[17];
 #pragma unroll
             for (int q = 0; q < 17; ++q) m[q] = 0.f;
@@ -673,6 +719,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
         }
         v = next_tile(requested, &s_v);
     }
+    if (threadIdx.x == 0) bulk_store_wait_all();  // the last tile's bulk store is in global memory
 }
 
 
@@ -1054,6 +1101,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
                 requested = request_tile(counter);
             }
         }
+        fence_proxy_async();  // this tile's stage reads, ordered before the next tile's bulk copy
         v = next_tile(requested, &s_v);
     }
 }
