@@ -20,6 +20,7 @@
 #include "tables.h"
 #include "sched.cuh"
 #include "tpl_common.cuh"
+#include "bulk.cuh"
 #include "lrmsd_solve.cuh"
 
 namespace tpl {
@@ -206,6 +207,9 @@ __global__ void __launch_bounds__(NT, 768 / NT) bb_fwd_kernel(const float* __res
     int v = take_tile(ws.hdr + kHdrFwdNext, &s_v);
     while (v < ntiles) {
         const int2 ct = ws.tiles[v];
+        // the previous entry's bulk store has read the stage before it is refilled
+        // (the entry's block scan barriers order this before every stage write)
+        if (threadIdx.x == 0) bulk_store_wait_read();
         if (ct.x < 0) {
             // a pack of whole short chains: segmented scan, no look-back
             const int m = ct.y;
@@ -232,6 +236,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) bb_fwd_kernel(const float* __res
                 }
             }
             store_stage<K>(s_out + threadIdx.x * 9 * K, vv);
+            fence_proxy_async();  // the stage writes, before the bulk store reads them
             __syncthreads();
             // each chain's whole row: its atoms from the stage (16-byte copies when
             // the stage offset allows), the float4 that straddles the end, zeros
@@ -239,7 +244,10 @@ __global__ void __launch_bounds__(NT, 768 / NT) bb_fwd_kernel(const float* __res
                 const int n9 = 9 * s_pack.len[i], o9 = 9 * s_pack.off[i];
                 float4* dst = reinterpret_cast<float4*>(coords + (size_t)s_pack.b[i] * 9 * Lmax);
                 const int full = n9 >> 2;
-                if ((o9 & 3) == 0) {
+                if (full > 0 && ((smem_addr(s_out + o9) | (unsigned)reinterpret_cast<uintptr_t>(dst)) & 15u) == 0u) {
+                    // one bulk store (TMA engine) that runs on while the CTA goes on
+                    if (threadIdx.x == 0) bulk_store(reinterpret_cast<float*>(dst), s_out + o9, 16u * (unsigned)full);
+                } else if ((o9 & 3) == 0) {
                     const float4* src = reinterpret_cast<const float4*>(s_out + o9);
                     for (int q = threadIdx.x; q < full; q += NT) dst[q] = src[q];
                 } else {
@@ -301,15 +309,20 @@ __global__ void __launch_bounds__(NT, 768 / NT) bb_fwd_kernel(const float* __res
             }
         }
         store_stage<K>(s_out + threadIdx.x * 9 * K, vv);
+        fence_proxy_async();  // the stage writes, before the bulk store reads them
         __syncthreads();
         // with the padding kept zero by the caller, the stores stop at the
         // chain's last residue (rounded up to 4 residues: the stage holds
         // zeros past it)
         const int nres = (ws.flags & TPL_FLAG_PADDING_ZEROED) ? min(TILE, (L - tile0 + 3) & ~3)
                                                              : min(TILE, Lmax - tile0);  // multiple of 4
-        float4* dst = reinterpret_cast<float4*>(out + 9 * (size_t)tile0);
-        const float4* src = reinterpret_cast<const float4*>(s_out);
-        for (int i = threadIdx.x; i < nres * 9 / 4; i += NT) dst[i] = src[i];
+        float* dst = out + 9 * (size_t)tile0;  // 16-byte aligned: tile0 and nres are multiples of 4
+        if (nres > 0 && ((smem_addr(s_out) | (unsigned)reinterpret_cast<uintptr_t>(dst)) & 15u) == 0u) {
+            if (threadIdx.x == 0) bulk_store(dst, s_out, 36u * (unsigned)nres);  // runs on into the next tile
+        } else {
+            const float4* src = reinterpret_cast<const float4*>(s_out);
+            for (int i = threadIdx.x; i < nres * 9 / 4; i += NT) reinterpret_cast<float4*>(dst)[i] = src[i];
+        }
         if (t == T - 1 && !(ws.flags & TPL_FLAG_PADDING_ZEROED)) {  // zero the residues past the last tile
             float4* o4 = reinterpret_cast<float4*>(out);
             for (int i = min(Lmax, T * TILE) * 9 / 4 + threadIdx.x; i < Lmax * 9 / 4; i += NT)
@@ -321,6 +334,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) bb_fwd_kernel(const float* __res
         }
         v = next_tile(requested, &s_v);
     }
+    if (threadIdx.x == 0) bulk_store_wait_all();  // the last stores are in global memory
 }
 
 // Local product of a thread's K residues (no positions), sin/cos cached.
