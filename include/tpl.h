@@ -329,8 +329,11 @@ size_t tpl_lrmsd_workspace_size(int P, int Nmax);
 
 /* Section 4: LRMSD(x = target, y = input) = min over rigid motions of
  * sqrt(sum |x_i - M y_i|^2 / N) by the quaternion method: centroids, R =
- * sum x' y'^T, the 4x4 matrix T(R), its largest eigenpair (lambda, q) refined
- * to about 48 bits (double-float), U(q); the value sum(|x'|^2 + |y'|^2) -
+ * sum x' y'^T, the 4x4 matrix T(R), its largest eigenpair (lambda, q) from
+ * an FP32 estimate (Newton on the characteristic polynomial and an adjugate
+ * column, or cyclic Jacobi where lambda is nearly double) and one refinement
+ * of q against the exact T (compensated double-float products and sums),
+ * U(q); the value sum(|x'|^2 + |y'|^2) -
  * 2 lambda is evaluated in the equivalent residual form sum |y'_i - U x'_i|^2
  * (FP64 final reduction).
  *   input, target [P][Nmax][3], num_atoms [P] int32 in; lrmsd [P] float out. */

@@ -8,8 +8,9 @@
 //    eigenpair of the 4x4 matrix T(R) in FP32 (Newton's method on the
 //    characteristic polynomial, as in the quaternion-characteristic-polynomial
 //    approach of Theobald, Acta Cryst. A61 (2005) 478, then an adjugate
-//    column) and refines it in double-float FP32 arithmetic, about 48 bits
-//    (Rayleigh quotient of T, adjugate of T - lambda I), then U(q);
+//    column; cyclic Jacobi where lambda_max is nearly double), refines the
+//    eigenvector once against the exact T (compensated products and sums),
+//    then U(q);
 //  - residuals: LRMSD^2 = (sum |x'|^2 + |y'|^2 - 2 lambda)/N equals sum |y'_i -
 //    U x'_i|^2 / N at the optimum; the residual form has no cancellation, so
 //    it is summed in FP32 per thread and in FP64 over the warps.  The clouds

@@ -11,11 +11,6 @@ namespace {
 constexpr int kMom = 17;     // sum dx (3), sum dy (3), sum dx dy^T (9), sum |dx|^2, sum |dy|^2
 constexpr int kSlot = 20;    // floats per chunk partial (5 float4)
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kRqPasses = 4;          // most Rayleigh-quotient passes of the eigen-solve
-constexpr float kNearDouble = 1e-4f;  // |adjugate column|^2 below which another pass runs
-constexpr int kPowerSteps = 24;       // power iterations when the adjugate passes fail (double eigenvalue)
-constexpr float kEigenResidual2 = 1e-18f;  // |T q - lambda q|^2 above which they run
-constexpr float kSuspectAdj = 5e-2f;       // FP32 adjugate diagonal below which the result is checked
 
 __device__ __forceinline__ int checked_atoms(int n, int Nmax) {
     if (n < 0 || n > Nmax) {
@@ -60,6 +55,75 @@ __device__ __forceinline__ T quad_sum(T v, int sub) {
 // ---------------------------------------------------------------------------
 // Eigen-solve of T(R) (part of K5)
 // ---------------------------------------------------------------------------
+// Double-float ("double-word") arithmetic on the FP32 pipe: a value is the
+// unevaluated sum hi + lo of two floats, |lo| <= ulp(hi) / 2, about 48
+// significant bits.  The building blocks are the classical error-free
+// transformations -- Knuth's TwoSum, the FMA form of Dekker's TwoProduct,
+// Dekker's Fast2Sum -- combined into the double-word sum and product
+// analysed by Joldes, Muller and Popescu (ACM TOMS 44 (2017) 1).  The
+// round-to-nearest intrinsics keep the compiler from contracting or
+// reordering them.  FP64 issues at a small fraction of the FP32 rate on this
+// GPU, so the solve uses this form where it needs more than FP32.
+// ---------------------------------------------------------------------------
+struct DF {
+    float hi, lo;
+};
+
+// exact a + b (Knuth)
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return DF{s, e};
+}
+
+// exact a + b for |a| >= |b| (Dekker)
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// exact a * b (FMA)
+__device__ __forceinline__ DF two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return DF{p, fmaf(a, b, -p)};
+}
+
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+    DF s = two_sum(x.hi, y.hi);
+    const DF t = two_sum(x.lo, y.lo);
+    s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+
+__device__ __forceinline__ DF df_neg(DF x) { return DF{-x.hi, -x.lo}; }
+__device__ __forceinline__ DF df_sub(DF x, DF y) { return df_add(x, df_neg(y)); }
+__device__ __forceinline__ DF df_twice(DF x) { return DF{__fmul_rn(2.f, x.hi), __fmul_rn(2.f, x.lo)}; }
+
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+    const DF p = two_prod(x.hi, y.hi);
+    const float e = fmaf(x.lo, y.lo, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo)));
+    return fast_two_sum(p.hi, e);
+}
+
+__device__ __forceinline__ DF df_mul_f(DF x, float y) {
+    const DF p = two_prod(x.hi, y);
+    return fast_two_sum(p.hi, fmaf(x.lo, y, p.lo));
+}
+
+// 1 / sqrt(x) for x > 0: FP32 estimate, one Newton step s (3 - x s^2) / 2 with
+// the residual 1 - x s^2 in double-float
+__device__ __forceinline__ DF df_rsqrt(DF x) {
+    const float s0 = rsqrtf(x.hi);
+    const DF e = df_sub(DF{1.f, 0.f}, df_mul_f(df_mul_f(x, s0), s0));
+    return fast_two_sum(s0, __fmul_rn(__fmul_rn(0.5f, s0), e.hi));
+}
+
+// a + b + c to double-float accuracy
+__device__ __forceinline__ DF df_sum3(float a, float b, float c) { return df_add(two_sum(a, b), DF{c, 0.f}); }
+
+__device__ __forceinline__ float df_round(DF x) { return __fadd_rn(x.hi, x.lo); }
+
 // Adjugate of a symmetric 4x4 (float): the same Laplace expansion in FP32,
 // used only for the starting eigenvector.
 __device__ __forceinline__ float adjugate4f(float a00, float a01, float a02, float a03, float a11,
@@ -140,107 +204,99 @@ __device__ __forceinline__ void fp32_eigen_estimate(const float (&r)[9], float e
     }
 }
 
-// ---------------------------------------------------------------------------
-// Double-float ("double-word") arithmetic on the FP32 pipe: a value is the
-// unevaluated sum hi + lo of two floats, |lo| <= ulp(hi) / 2, about 48
-// significant bits.  The building blocks are the classical error-free
-// transformations -- Knuth's TwoSum, the FMA form of Dekker's TwoProduct,
-// Dekker's Fast2Sum -- combined into the double-word sum, product and
-// quotient analysed by Joldes, Muller and Popescu (ACM TOMS 44 (2017) 1).
-// The round-to-nearest intrinsics keep the compiler from contracting or
-// reordering them.  FP64 issues at a small fraction of the FP32 rate on this
-// GPU, so the eigen-solve refines in this form instead.
-// ---------------------------------------------------------------------------
-struct DF {
-    float hi, lo;
-};
-
-__device__ __forceinline__ DF df_zero() { return DF{0.f, 0.f}; }
-
-// exact a + b (Knuth)
-__device__ __forceinline__ DF two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return DF{s, e};
+// One rotation of the cyclic Jacobi method on the symmetric 4x4 a (both
+// triangles kept), zeroing a[P][Q], with the rotation accumulated into the
+// columns of v (Jacobi 1846).  With d = a_qq - a_pp and b = 2 a_pq the
+// tangent of the rotation angle is the smaller root of t^2 + 2 (d / b) t - 1
+// = 0, t = sgn(d) b / (|d| + sqrt(d^2 + b^2)), which needs no division by the
+// small a_pq; cos = 1 / sqrt(1 + t^2), sin = t cos.  The rotation need not
+// zero a_pq to the last bit: the eigenvector is refined against the exact T
+// afterwards.  An entry below 1e-18 is left alone (T is scaled to O(1), so it
+// is rounding noise, and b^2 must not underflow).
+template <int P, int Q>
+__device__ __forceinline__ void jacobi_rotate(float (&a)[4][4], float (&v)[4][4]) {
+    const float apq = a[P][Q];
+    if (!(fabsf(apq) > 1e-18f)) return;
+    const float d = a[Q][Q] - a[P][P], b = 2.f * apq;
+    const float h = fmaf(d, d, b * b);
+    const float t = __fdividef(copysignf(1.f, d) * b, fabsf(d) + h * rsqrtf(h));
+    const float c = rsqrtf(fmaf(t, t, 1.f)), s = t * c;
+    a[P][P] = fmaf(-t, apq, a[P][P]);
+    a[Q][Q] = fmaf(t, apq, a[Q][Q]);
+    a[P][Q] = a[Q][P] = 0.f;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        if (r == P || r == Q) continue;
+        const float g = a[r][P], e = a[r][Q];
+        a[r][P] = a[P][r] = c * g - s * e;
+        a[r][Q] = a[Q][r] = fmaf(s, g, c * e);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const float g = v[r][P], e = v[r][Q];
+        v[r][P] = c * g - s * e;
+        v[r][Q] = fmaf(s, g, c * e);
+    }
 }
 
-// exact a + b for |a| >= |b| (Dekker)
-__device__ __forceinline__ DF fast_two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b);
-    return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+constexpr float kSuspectAdj = 5e-2f;  // FP32 adjugate diagonal below which Jacobi takes over
+constexpr int kJacobiSweeps = 4;       // most sweeps (six rotations each)
+constexpr float kJacobiOff = 1e-7f;    // largest off-diagonal entry that ends the sweeps
+constexpr float kRefineRatio = 0.1f;   // largest |correction| along another eigenvector
+
+// y = T q row by row as Dot2 sums (Ogita, Rump and Oishi, SIAM J. Sci.
+// Comput. 26 (2005) 1955): T's entries are exact double-floats of the FP32 R,
+// each product hi * q split by TwoProduct, the running sum by TwoSum, all
+// error terms (and lo * q) carried in a second float.  ys + yc is T q with
+// about twice the FP32 precision.
+__device__ __forceinline__ void dot2_rows(const DF (&T)[4][4], const float (&q)[4], float (&ys)[4],
+                                          float (&yc)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float s = 0.f, c = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const DF p = two_prod(T[i][j].hi, q[j]);
+            const DF t = two_sum(s, p.hi);
+            s = t.hi;
+            c = __fadd_rn(c, __fadd_rn(t.lo, p.lo));
+            c = fmaf(T[i][j].lo, q[j], c);
+        }
+        ys[i] = s;
+        yc[i] = c;
+    }
 }
 
-// exact a * b (FMA)
-__device__ __forceinline__ DF two_prod(float a, float b) {
-    const float p = __fmul_rn(a, b);
-    return DF{p, fmaf(a, b, -p)};
-}
-
-__device__ __forceinline__ DF df_add(DF x, DF y) {
-    DF s = two_sum(x.hi, y.hi);
-    const DF t = two_sum(x.lo, y.lo);
-    s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
-    return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
-}
-
-__device__ __forceinline__ DF df_neg(DF x) { return DF{-x.hi, -x.lo}; }
-__device__ __forceinline__ DF df_sub(DF x, DF y) { return df_add(x, df_neg(y)); }
-__device__ __forceinline__ DF df_twice(DF x) { return DF{__fmul_rn(2.f, x.hi), __fmul_rn(2.f, x.lo)}; }
-
-__device__ __forceinline__ DF df_mul(DF x, DF y) {
-    const DF p = two_prod(x.hi, y.hi);
-    const float e = fmaf(x.lo, y.lo, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo)));
-    return fast_two_sum(p.hi, e);
-}
-
-__device__ __forceinline__ DF df_mul_f(DF x, float y) {
-    const DF p = two_prod(x.hi, y);
-    return fast_two_sum(p.hi, fmaf(x.lo, y, p.lo));
-}
-
-// x / y: FP32 quotient, then one correction with the double-float remainder
-__device__ __forceinline__ DF df_div(DF x, DF y) {
-    const float q1 = __fdiv_rn(x.hi, y.hi);
-    const DF r = df_sub(x, df_mul_f(y, q1));
-    const float q2 = __fdiv_rn(r.hi, y.hi);
-    return fast_two_sum(q1, q2);
-}
-
-// 1 / sqrt(x) for x > 0: FP32 estimate, one Newton step s (3 - x s^2) / 2 with
-// the residual 1 - x s^2 in double-float
-__device__ __forceinline__ DF df_rsqrt(DF x) {
-    const float s0 = rsqrtf(x.hi);
-    const DF e = df_sub(DF{1.f, 0.f}, df_mul_f(df_mul_f(x, s0), s0));
-    return fast_two_sum(s0, __fmul_rn(__fmul_rn(0.5f, s0), e.hi));
-}
-
-// a + b + c to double-float accuracy
-__device__ __forceinline__ DF df_sum3(float a, float b, float c) { return df_add(two_sum(a, b), DF{c, 0.f}); }
-
-__device__ __forceinline__ float df_round(DF x) { return __fadd_rn(x.hi, x.lo); }
-
-__device__ __forceinline__ DF df_shfl_xor(DF x, int m) {
-    return DF{__shfl_xor_sync(0xffffffffu, x.hi, m), __shfl_xor_sync(0xffffffffu, x.lo, m)};
-}
-__device__ __forceinline__ DF df_shfl(DF x, int src) {
-    return DF{__shfl_sync(0xffffffffu, x.hi, src), __shfl_sync(0xffffffffu, x.lo, src)};
-}
-
-__device__ __forceinline__ DF pick4(int i, DF a, DF b, DF c, DF d) {
-    return i == 0 ? a : (i == 1 ? b : (i == 2 ? c : d));
-}
-
-
-// Eigen-solve of one pair by the four lanes of a quad (sub = lane & 3), from
-// the summed moments S: lane i forms row i of T q for the Rayleigh quotient,
-// cofactor (jb, i) of the adjugate row and row i of U, so the dependent
-// double-float chain is about a quarter as long; the FP32 estimate runs in
-// all four lanes alike.  Every lane of the warp must call it (quad shuffles); only lanes with
-// `store` write the pair's state st: U (9), xc (3), yc (3), 0.
+// Eigen-solve of one pair from the summed moments S by each lane of a quad
+// (sub = lane & 3; the four lanes hold the same moments and compute the same
+// eigenpair, so no lane waits on another): centre the moments, scale R to
+// |R|_F = 1, then
+//  1. an FP32 estimate q of the eigenvector of the largest eigenvalue: Newton
+//     on the characteristic polynomial and a column of the adjugate of
+//     T - lambda I (fp32_eigen_estimate).  Where that column is small (a
+//     nearly double lambda_max: collinear or two-fold symmetric clouds, two
+//     atoms) the adjugate is rounding noise, and all eigenpairs come from
+//     cyclic Jacobi in FP32 instead (two disjoint rotations at a time, at most
+//     four sweeps), q the eigenvector of the largest one;
+//  2. one refinement of q against the exact T: y = T q by compensated dot
+//     products (dot2_rows), mu = q . y, the residual r = y - mu q, and the
+//     correction dq with (T - mu I + q q^T) dq = -r, dq orthogonal to q to
+//     first order.  On the estimate's path that matrix is well conditioned (its
+//     eigenvalues are lambda_i - mu, i > 1, and about 1) and is solved in FP32
+//     through its adjugate.  On Jacobi's path dq = sum_i v_i (v_i . r) / (mu -
+//     lambda_i) over the other eigenvectors, leaving out a term whose
+//     correction would not be small (|v_i . r| >= 0.1 |mu - lambda_i|:
+//     lambda_i within rounding of lambda_max, where every vector of the
+//     eigenspace is optimal).  The error of q goes from the FP32 solve's to
+//     about its square;
+//  3. q + dq normalised in double-float and row sub of U(q) (Section 4)
+//     formed in double-float and rounded once.
+// Only lanes with `store` write the pair's state st: U (9), xc (3), yc (3), 0
+// (lanes 0-2 a row of U each, lane 3 the centroids).
 __device__ __forceinline__ void quad_eigen_solve(const float (&S)[kSlot], const float (&x0)[3],
                                                  const float (&y0)[3], int n, int sub, int lane,
                                                  bool store, float* __restrict__ st) {
+    (void)lane;
     float xc[3] = {0.f, 0.f, 0.f}, yc[3] = {0.f, 0.f, 0.f}, r[9], e0 = 0.f;
 #pragma unroll
     for (int k = 0; k < 9; ++k) r[k] = 0.f;
@@ -266,144 +322,118 @@ __device__ __forceinline__ void quad_eigen_solve(const float (&S)[kSlot], const 
 #pragma unroll
     for (int k = 0; k < 9; ++k) fro = fmaf(r[k], r[k], fro);
     const bool solve = n > 0 && fro > 0.f;  // else U = I (one atom, or all atoms coincide)
-    const float sc = solve ? rsqrtf(fro) : 0.f;
+    DF qd[4] = {DF{1.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}, DF{0.f, 0.f}};
+    if (solve) {
+        const float sc = rsqrtf(fro);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) r[k] *= sc;
-    float lam = 0.f, qf[4] = {1.f, 0.f, 0.f, 0.f};
-    int jb = 0;
-    float adj = 1.f;
-    if (solve) fp32_eigen_estimate(r, e0 * sc, lam, qf, jb, adj);
-    const bool suspect = solve && adj < kSuspectAdj;  // a (nearly) double lambda_max
-    // ---- refinement in double-float arithmetic (about 48 significant bits),
-    // every lane of the warp together from here on
-    DF T[4][4];
-    T[0][0] = df_sum3(r[0], r[4], r[8]);
-    T[0][1] = T[1][0] = two_sum(r[5], -r[7]);
-    T[0][2] = T[2][0] = two_sum(r[6], -r[2]);
-    T[0][3] = T[3][0] = two_sum(r[1], -r[3]);
-    T[1][1] = df_sum3(r[0], -r[4], -r[8]);
-    T[1][2] = T[2][1] = two_sum(r[1], r[3]);
-    T[1][3] = T[3][1] = two_sum(r[2], r[6]);
-    T[2][2] = df_sum3(-r[0], r[4], -r[8]);
-    T[2][3] = T[3][2] = two_sum(r[5], r[7]);
-    T[3][3] = df_sum3(-r[0], -r[4], r[8]);
-    // Rayleigh-quotient passes: lambda = q.T q / q.q at the current estimate,
-    // then q = row jb of adj(T - lambda I) (lane sub forms its entry).  One pass
-    // is exact to rounding when the largest eigenvalue is well separated (the
-    // adjugate column is then of order one, |R|_F being 1).  When it is (nearly)
-    // double -- collinear clouds, where any turn about the line fits as well --
-    // the FP32 estimate can lean towards the other eigenvectors, and each further
-    // pass squares that error; passes repeat while the column stays small.
-    // Every lane runs every pass (full-warp shuffles); a quad keeps the pass
-    // results only while it still needs them.
-    DF qv[4] = {DF{qf[0], 0.f}, DF{qf[1], 0.f}, DF{qf[2], 0.f}, DF{qf[3], 0.f}};
-    int jv = jb;
-    bool need = true, ok = false;
-    const int base = lane & ~3;
-    for (int pass = 0; pass < kRqPasses; ++pass) {
-        if (!__any_sync(kFull, need)) break;
-        DF w = df_zero();
+        for (int k = 0; k < 9; ++k) r[k] *= sc;
+        // T(R) as exact double-floats of the FP32 entries
+        DF T[4][4];
+        T[0][0] = df_sum3(r[0], r[4], r[8]);
+        T[0][1] = T[1][0] = two_sum(r[5], -r[7]);
+        T[0][2] = T[2][0] = two_sum(r[6], -r[2]);
+        T[0][3] = T[3][0] = two_sum(r[1], -r[3]);
+        T[1][1] = df_sum3(r[0], -r[4], -r[8]);
+        T[1][2] = T[2][1] = two_sum(r[1], r[3]);
+        T[1][3] = T[3][1] = two_sum(r[2], r[6]);
+        T[2][2] = df_sum3(-r[0], r[4], -r[8]);
+        T[2][3] = T[3][2] = two_sum(r[5], r[7]);
+        T[3][3] = df_sum3(-r[0], -r[4], r[8]);
+        float lam, qf[4], adj;
+        int jb;
+        fp32_eigen_estimate(r, e0 * sc, lam, qf, jb, adj);
+        float q[4], dq[4] = {0.f, 0.f, 0.f, 0.f};
+        if (adj >= kSuspectAdj) {
+            // 1. the adjugate column, normalised
+            const float nq = rsqrtf(fmaf(qf[0], qf[0], fmaf(qf[1], qf[1], fmaf(qf[2], qf[2], qf[3] * qf[3]))));
 #pragma unroll
-        for (int k = 0; k < 4; ++k) w = df_add(w, df_mul(pick4(sub, T[0][k], T[1][k], T[2][k], T[3][k]), qv[k]));
-        DF num = df_mul(w, pick4(sub, qv[0], qv[1], qv[2], qv[3]));
-        num = df_add(num, df_shfl_xor(num, 1));
-        num = df_add(num, df_shfl_xor(num, 2));
-        DF den = df_mul(qv[0], qv[0]);
+            for (int i = 0; i < 4; ++i) q[i] = qf[i] * nq;
+            // 2. refinement through (T - mu I + q q^T)
+            float ys[4], yr[4];
+            dot2_rows(T, q, ys, yr);
+            float mu = 0.f;
 #pragma unroll
-        for (int k = 1; k < 4; ++k) den = df_add(den, df_mul(qv[k], qv[k]));
-        const DF lam2 = den.hi > 0.f ? df_div(num, den) : df_zero();
-        // cofactor (jv, sub) of A = T - lambda I: rows other than jv, columns other than sub
-        DF M[3][3];
+            for (int i = 0; i < 4; ++i) mu = fmaf(q[i], ys[i], mu);
+            float res[4];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int ri = k < jv ? k : k + 1;
-            DF row[4];
+            for (int i = 0; i < 4; ++i) res[i] = fmaf(-mu, q[i], ys[i]) + yr[i];
+            float m[16];
+            const float det = adjugate4f(
+                T[0][0].hi - mu + q[0] * q[0], T[0][1].hi + q[0] * q[1], T[0][2].hi + q[0] * q[2],
+                T[0][3].hi + q[0] * q[3], T[1][1].hi - mu + q[1] * q[1], T[1][2].hi + q[1] * q[2],
+                T[1][3].hi + q[1] * q[3], T[2][2].hi - mu + q[2] * q[2], T[2][3].hi + q[2] * q[3],
+                T[3][3].hi - mu + q[3] * q[3], m);
+            const float idet = -__frcp_rn(det);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                row[c] = pick4(ri, T[0][c], T[1][c], T[2][c], T[3][c]);
-                if (c == ri) row[c] = df_sub(row[c], lam2);
-            }
-            M[k][0] = sub == 0 ? row[1] : row[0];
-            M[k][1] = sub <= 1 ? row[2] : row[1];
-            M[k][2] = sub <= 2 ? row[3] : row[2];
-        }
-        DF qc = df_sub(df_mul(M[0][0], df_sub(df_mul(M[1][1], M[2][2]), df_mul(M[1][2], M[2][1]))),
-                       df_mul(M[0][1], df_sub(df_mul(M[1][0], M[2][2]), df_mul(M[1][2], M[2][0]))));
-        qc = df_add(qc, df_mul(M[0][2], df_sub(df_mul(M[1][0], M[2][1]), df_mul(M[1][1], M[2][0]))));
-        if ((jv + sub) & 1) qc = df_neg(qc);
-        DF nn = df_mul(qc, qc);
-        nn = df_add(nn, df_shfl_xor(nn, 1));
-        nn = df_add(nn, df_shfl_xor(nn, 2));
-        const bool ok_p = solve && nn.hi > 0.f;
-        const DF qn = ok_p ? df_mul(qc, df_rsqrt(nn)) : df_zero();
-        DF qg[4];
+            for (int i = 0; i < 4; ++i)
+                dq[i] = idet * fmaf(m[4 * i], res[0], fmaf(m[4 * i + 1], res[1], fmaf(m[4 * i + 2], res[2], m[4 * i + 3] * res[3])));
+        } else {
+            // 1. cyclic Jacobi
+            float a[4][4], v[4][4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) qg[k] = df_shfl(qn, base + k);
-        if (need) {
-            ok = ok_p;
+            for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) qv[k] = qg[k];
-            need = ok_p && nn.hi < kNearDouble;
-            // next cofactor row: the largest entry of the estimate
-            jv = 0;
-#pragma unroll
-            for (int k = 1; k < 4; ++k)
-                if (fabsf(qv[k].hi) > fabsf(pick4(jv, qv[0], qv[1], qv[2], qv[3]).hi)) jv = k;
-        }
-    }
-    // The passes stop once the adjugate column is not small, which presumes
-    // that lambda was already close to lambda_max.  When the FP32 estimate's
-    // eigenvector is rounding noise -- lambda_max exactly double, as for two
-    // atoms or collinear atoms (R of rank one) -- the Rayleigh quotient of
-    // that noise is not, and the adjugate column is then a mixture of
-    // eigenvectors.  So when the FP32 adjugate was small (the sign of a
-    // double root) the result is checked by its eigen-residual |T q -
-    // (q.T q) q|; a pair that fails the check takes power iterations of
-    // T + 2 I (positive definite: |R|_F = 1 bounds the eigenvalues of T by
-    // sqrt(3)), which reach the eigenspace of lambda_max at a ratio of at
-    // most (lambda_3 + 2) / (lambda_max + 2) per step; any vector of that
-    // space is optimal.
-    bool redo = false;
-    if (__any_sync(kFull, suspect)) {
-        DF w = df_zero();
-#pragma unroll
-        for (int k = 0; k < 4; ++k) w = df_add(w, df_mul(pick4(sub, T[0][k], T[1][k], T[2][k], T[3][k]), qv[k]));
-        const DF qs = pick4(sub, qv[0], qv[1], qv[2], qv[3]);
-        DF num = df_mul(w, qs);
-        num = df_add(num, df_shfl_xor(num, 1));
-        num = df_add(num, df_shfl_xor(num, 2));
-        const DF r = df_sub(w, df_mul(num, qs));  // q has unit length
-        DF rr = df_mul(r, r);
-        rr = df_add(rr, df_shfl_xor(rr, 1));
-        rr = df_add(rr, df_shfl_xor(rr, 2));
-        redo = suspect && (!ok || rr.hi > kEigenResidual2);
-    }
-    if (__any_sync(kFull, redo)) {
-        DF pq[4] = {qv[0], qv[1], qv[2], qv[3]};
-        if (!ok) pq[0] = DF{1.f, 0.f}, pq[1] = pq[2] = pq[3] = DF{0.5f, 0.f};
+                for (int j = 0; j < 4; ++j) {
+                    a[i][j] = T[i][j].hi;
+                    v[i][j] = i == j ? 1.f : 0.f;
+                }
 #pragma unroll 1
-        for (int it = 0; it < kPowerSteps; ++it) {
-            DF w = df_mul_f(pick4(sub, pq[0], pq[1], pq[2], pq[3]), 2.f);
+            for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
+                jacobi_rotate<0, 1>(a, v);
+                jacobi_rotate<2, 3>(a, v);
+                jacobi_rotate<0, 2>(a, v);
+                jacobi_rotate<1, 3>(a, v);
+                jacobi_rotate<0, 3>(a, v);
+                jacobi_rotate<1, 2>(a, v);
+                const float off = fmaxf(fmaxf(fmaxf(fabsf(a[0][1]), fabsf(a[0][2])), fmaxf(fabsf(a[0][3]), fabsf(a[1][2]))),
+                                        fmaxf(fabsf(a[1][3]), fabsf(a[2][3])));
+                if (off < kJacobiOff) break;
+            }
+            int kb = 0;
+            float best = a[0][0];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) w = df_add(w, df_mul(pick4(sub, T[0][k], T[1][k], T[2][k], T[3][k]), pq[k]));
-            DF nn = df_mul(w, w);
-            nn = df_add(nn, df_shfl_xor(nn, 1));
-            nn = df_add(nn, df_shfl_xor(nn, 2));
-            const DF wn = nn.hi > 0.f ? df_mul(w, df_rsqrt(nn)) : df_zero();
+            for (int i = 1; i < 4; ++i)
+                if (a[i][i] > best) {
+                    best = a[i][i];
+                    kb = i;
+                }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) pq[k] = df_shfl(wn, base + k);
+            for (int i = 0; i < 4; ++i) q[i] = kb == 0 ? v[i][0] : (kb == 1 ? v[i][1] : (kb == 2 ? v[i][2] : v[i][3]));
+            // 2. refinement along the other eigenvectors
+            float ys[4], yr[4];
+            dot2_rows(T, q, ys, yr);
+            float mu = 0.f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) mu = fmaf(q[i], ys[i], mu);
+            float res[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) res[i] = fmaf(-mu, q[i], ys[i]) + yr[i];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (e == kb) continue;
+                float w = 0.f;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) w = fmaf(v[i][e], res[i], w);
+                const float den = mu - a[e][e];
+                if (fabsf(w) < kRefineRatio * fabsf(den)) {
+                    const float coef = __fdividef(w, den);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) dq[i] = fmaf(coef, v[i][e], dq[i]);
+                }
+            }
         }
-        if (redo && (pq[0].hi != 0.f || pq[1].hi != 0.f || pq[2].hi != 0.f || pq[3].hi != 0.f)) {
+        // 3. q + dq as double-floats, normalised
+        DF nn = DF{0.f, 0.f};
 #pragma unroll
-            for (int k = 0; k < 4; ++k) qv[k] = pq[k];
-            ok = true;
+        for (int i = 0; i < 4; ++i) {
+            qd[i] = two_sum(q[i], dq[i]);
+            nn = df_add(nn, df_mul(qd[i], qd[i]));
         }
+        const DF is = df_rsqrt(nn);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) qd[i] = df_mul(qd[i], is);
     }
-    DF q0 = qv[0], q1 = qv[1], q2 = qv[2], q3 = qv[3];
-    if (!ok) {
-        q0 = DF{1.f, 0.f};
-        q1 = q2 = q3 = df_zero();
-    }
+    const DF q0 = qd[0], q1 = qd[1], q2 = qd[2], q3 = qd[3];
     // row sub of U(q) (Section 4), formed in double-float and rounded once
     const DF a = df_mul(q0, q0), bq = df_mul(q1, q1), c = df_mul(q2, q2), d = df_mul(q3, q3);
     DF u0, u1, u2;
