@@ -518,16 +518,17 @@ def setup_training_step(args, tpl, torch, dev, d):
     st.alg = {"fullatom_forward": res * (28 + 1) + 12 * n_atoms, "lrmsd_forward": 24 * n_atoms}
     st_ws = None
     if args.fusion == "step" and args.bwd == "coords":
-        # forward with the LRMSD moments in its tiles + eigen-solve; backward with
-        # the LRMSD gradient, residuals and LRMSD (one workspace for both)
+        # forward with the LRMSD moments in its tiles, then per chain the eigen-solve
+        # and the residual pass (LRMSD out); backward with the LRMSD gradient
+        # formed inside (one workspace for both)
         st_ws = torch.empty(tpl.tpl_fullatom_lrmsd_workspace_size(B, Lmax), dtype=torch.uint8, device=dev)
         st.calls = [
             ("lrmsd_step_forward",
-             lambda: tpl.tpl_fullatom_lrmsd_forward(A, S, Ln, target, coords, na, st_ws, opts)),
+             lambda: tpl.tpl_fullatom_lrmsd_forward(A, S, Ln, target, coords, na, lr, st_ws, opts)),
             ("lrmsd_step_backward",
-             lambda: tpl.tpl_fullatom_lrmsd_backward(S, Ln, coords, target, na, wgt, lr, gang, st_ws, opts)),
+             lambda: tpl.tpl_fullatom_lrmsd_backward(S, Ln, coords, target, wgt, gang, st_ws, opts)),
         ]
-        st.kernels = {"lrmsd_step_forward": ["schedule_kernel", "fa_fwd_kernel", "lrmsd_solve_tiles_kernel"],
+        st.kernels = {"lrmsd_step_forward": ["schedule_kernel", "fa_fwd_kernel", "lrmsd_parts_kernel"],
                       "lrmsd_step_backward": ["fa_bwd_coords_kernel"]}
         # forward: angles and sequence in, coordinates out, target read for the moments;
         # backward: angles and sequence in, angle gradient out, coordinates and target read

@@ -242,25 +242,25 @@ tpl_status tpl_fullatom_backward(const float* angles, const uint8_t* seq, const 
  * two calls that share one workspace (the paper has no fused form; the
  * results equal tpl_fullatom_forward, tpl_lrmsd_forward with P = B and
  * Nmax = Amax, and tpl_fullatom_backward_lrmsd):
- *  - tpl_fullatom_lrmsd_forward: coords and num_atoms as tpl_fullatom_forward;
- *    each tile also reduces its atoms' LRMSD moments against target
- *    [B][Amax][3], and the eigen-solve leaves U and the centroids of every
- *    chain in the workspace.
+ *  - tpl_fullatom_lrmsd_forward: coords and num_atoms as tpl_fullatom_forward,
+ *    lrmsd [B] = LRMSD(coords[b], target[b]) out: each tile also reduces its
+ *    atoms' LRMSD moments against target [B][Amax][3]; then one CTA per chain
+ *    sums its tiles' moments, solves for U and sums the squared residuals
+ *    over the chain's atoms (FP64 final sum), leaving U, the centroids and
+ *    1 / (N LRMSD) in the workspace (three kernel launches).
  *  - tpl_fullatom_lrmsd_backward: grad_angles = d(sum_b grad_lrmsd[b]
- *    LRMSD_b) / d(angles) and lrmsd[b] = LRMSD(coords[b], target[b]): the
- *    backward forms each atom's LRMSD gradient and squared residual, and the
- *    chain's first tile forms LRMSD (FP64 sum) and applies 1 / (N LRMSD).
- *    coords, target and num_atoms are those of the forward call.
- * The loss value comes out of the backward, with the gradient. */
+ *    LRMSD_b) / d(angles), each atom's LRMSD gradient formed inside the
+ *    full-atom backward.  coords and target are those of the forward call.
+ * Options as tpl_fullatom_forward; the schedule takes no packs here. */
 size_t tpl_fullatom_lrmsd_workspace_size(int B, int Lmax);
 tpl_status tpl_fullatom_lrmsd_forward(const float* angles, const uint8_t* seq, const int32_t* lengths, int B,
                                       int Lmax, int Amax, const float* target, float* coords, int32_t* num_atoms,
-                                      void* workspace, size_t workspace_bytes, const tpl_opts* opts,
+                                      float* lrmsd, void* workspace, size_t workspace_bytes, const tpl_opts* opts,
                                       tpl_stream stream);
 tpl_status tpl_fullatom_lrmsd_backward(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
-                                       const float* coords, const float* target, const int32_t* num_atoms,
-                                       const float* grad_lrmsd, float* lrmsd, float* grad_angles, void* workspace,
-                                       size_t workspace_bytes, const tpl_opts* opts, tpl_stream stream);
+                                       const float* coords, const float* target, const float* grad_lrmsd,
+                                       float* grad_angles, void* workspace, size_t workspace_bytes,
+                                       const tpl_opts* opts, tpl_stream stream);
 
 /* Training step of the backbone model on the LRMSD loss (Section 3 forward,
  * Section 4 LRMSD, its gradient chained into Eq. 2, as the paper's training

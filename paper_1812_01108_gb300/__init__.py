@@ -97,8 +97,8 @@ def load_library():
             "tpl_fullatom_lrmsd_workspace_size": ([I, I], Z),
             "tpl_backbone_lrmsd_workspace_size": ([I, I], Z),
             "tpl_backbone_lrmsd_step": ([P, P, I, I, P, P, P, P, P, P, Z, O, P], I),
-            "tpl_fullatom_lrmsd_forward": ([P, P, P, I, I, I, P, P, P, P, Z, O, P], I),
-            "tpl_fullatom_lrmsd_backward": ([P, P, I, I, I, P, P, P, P, P, P, P, Z, O, P], I),
+            "tpl_fullatom_lrmsd_forward": ([P, P, P, I, I, I, P, P, P, P, P, Z, O, P], I),
+            "tpl_fullatom_lrmsd_backward": ([P, P, I, I, I, P, P, P, P, P, Z, O, P], I),
             "tpl_lrmsd_forward": ([P, P, P, I, I, P, P, Z, P], I),
             "tpl_lrmsd_backward": ([P, P, P, P, I, I, P, P, Z, P], I),
             "tpl_lrmsd_forward_noalloc": ([P, P, P, I, I, P, P], I),
@@ -324,31 +324,29 @@ def tpl_fullatom_lrmsd_workspace_size(B, Lmax):
     return int(load_library().tpl_fullatom_lrmsd_workspace_size(B, Lmax))
 
 
-def tpl_fullatom_lrmsd_forward(angles, seq, lengths, target, coords, num_atoms, workspace, opts=None,
+def tpl_fullatom_lrmsd_forward(angles, seq, lengths, target, coords, num_atoms, lrmsd_out, workspace, opts=None,
                                stream=None):
-    """Fused training step, forward: coordinates, atom counts, and the LRMSD
-    moments and rotation against ``target`` left in ``workspace``."""
+    """Fused training step, forward: coordinates, atom counts and the LRMSD
+    against ``target``; the rotation and the gradient scale stay in ``workspace``."""
     B, _, Lmax = angles.shape
     Amax = coords.shape[1]
     _check("tpl_fullatom_lrmsd_forward", load_library().tpl_fullatom_lrmsd_forward(
         _ptr(_cuda(angles, torch.float32, "angles")), _ptr(_cuda(seq, torch.uint8, "seq")),
         _ptr(_cuda(lengths, torch.int32, "lengths")), B, Lmax, Amax,
         _ptr(_cuda(target, torch.float32, "target")), _ptr(_cuda(coords, torch.float32, "coords")),
-        _ptr(_cuda(num_atoms, torch.int32, "num_atoms")), _ptr(workspace),
-        workspace.numel() * workspace.element_size(), _opts(opts), _stream(angles, stream)))
+        _ptr(_cuda(num_atoms, torch.int32, "num_atoms")), _ptr(_cuda(lrmsd_out, torch.float32, "lrmsd")),
+        _ptr(workspace), workspace.numel() * workspace.element_size(), _opts(opts), _stream(angles, stream)))
 
 
-def tpl_fullatom_lrmsd_backward(seq, lengths, coords, target, num_atoms, grad_lrmsd, lrmsd_out,
-                                grad_angles, workspace, opts=None, stream=None):
-    """Fused training step, backward: angle gradients of sum_b grad_lrmsd[b] *
-    LRMSD_b and the LRMSD values."""
+def tpl_fullatom_lrmsd_backward(seq, lengths, coords, target, grad_lrmsd, grad_angles, workspace, opts=None,
+                                stream=None):
+    """Fused training step, backward: angle gradients of sum_b grad_lrmsd[b] * LRMSD_b."""
     B, Lmax = seq.shape
     Amax = coords.shape[1]
     _check("tpl_fullatom_lrmsd_backward", load_library().tpl_fullatom_lrmsd_backward(
         _ptr(_cuda(seq, torch.uint8, "seq")), _ptr(_cuda(lengths, torch.int32, "lengths")), B, Lmax, Amax,
         _ptr(_cuda(coords, torch.float32, "coords")), _ptr(_cuda(target, torch.float32, "target")),
-        _ptr(_cuda(num_atoms, torch.int32, "num_atoms")), _ptr(_cuda(grad_lrmsd, torch.float32, "grad_lrmsd")),
-        _ptr(_cuda(lrmsd_out, torch.float32, "lrmsd")), _ptr(_cuda(grad_angles, torch.float32, "grad_angles")),
+        _ptr(_cuda(grad_lrmsd, torch.float32, "grad_lrmsd")), _ptr(_cuda(grad_angles, torch.float32, "grad_angles")),
         _ptr(workspace), workspace.numel() * workspace.element_size(), _opts(opts), _stream(coords, stream)))
 
 

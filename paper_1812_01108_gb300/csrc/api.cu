@@ -700,42 +700,41 @@ size_t tpl_fullatom_lrmsd_workspace_size(int B, int Lmax) { return chain_ws_byte
 
 tpl_status tpl_fullatom_lrmsd_forward(const float* angles, const uint8_t* seq, const int32_t* lengths, int B,
                                       int Lmax, int Amax, const float* target, float* coords, int32_t* num_atoms,
-                                      void* workspace, size_t workspace_bytes, const tpl_opts* opts,
+                                      float* lrmsd, void* workspace, size_t workspace_bytes, const tpl_opts* opts,
                                       tpl_stream stream) {
     tpl_opts o = resolve(opts);
     tpl_status st = check_opts(o);
     if (st) return st;
-    const void* ptrs[6] = {angles, seq, lengths, target, coords, num_atoms};
-    if ((st = check_chain_args(B, Lmax, ptrs, 6))) return st;
+    const void* ptrs[7] = {angles, seq, lengths, target, coords, num_atoms, lrmsd};
+    if ((st = check_chain_args(B, Lmax, ptrs, 7))) return st;
     if (Amax < 0 || Amax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Amax=%d must be a multiple of 4", Amax);
     if (B == 0) return ok();
     LaunchCfg cfg = fullatom_cfg(o);
     if ((st = check_fullatom_cfg(cfg))) return st;
     if ((st = check_ws(workspace, workspace_bytes, tpl_fullatom_lrmsd_workspace_size(B, Lmax)))) return st;
     cudaError_t e = launch_fullatom_lrmsd_forward(angles, seq, lengths, target, B, Lmax, Amax, coords, num_atoms,
-                                                  sched_mode(o, false), workspace, cfg,
+                                                  lrmsd, sched_mode(o, false), workspace, cfg,
                                                   reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "fullatom_lrmsd_forward");
     return ok();
 }
 
 tpl_status tpl_fullatom_lrmsd_backward(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
-                                       const float* coords, const float* target, const int32_t* num_atoms,
-                                       const float* grad_lrmsd, float* lrmsd, float* grad_angles, void* workspace,
-                                       size_t workspace_bytes, const tpl_opts* opts, tpl_stream stream) {
+                                       const float* coords, const float* target, const float* grad_lrmsd,
+                                       float* grad_angles, void* workspace, size_t workspace_bytes,
+                                       const tpl_opts* opts, tpl_stream stream) {
     tpl_opts o = resolve(opts);
     tpl_status st = check_opts(o);
     if (st) return st;
-    const void* ptrs[8] = {seq, lengths, coords, target, num_atoms, grad_lrmsd, lrmsd, grad_angles};
-    if ((st = check_chain_args(B, Lmax, ptrs, 8))) return st;
+    const void* ptrs[6] = {seq, lengths, coords, target, grad_lrmsd, grad_angles};
+    if ((st = check_chain_args(B, Lmax, ptrs, 6))) return st;
     if (Amax < 0 || Amax % 4 != 0) return fail(TPL_ERR_BAD_SHAPE, "Amax=%d must be a multiple of 4", Amax);
     if (B == 0) return ok();
     LaunchCfg cfg = fullatom_cfg(o);
     if ((st = check_fullatom_cfg(cfg))) return st;
     if ((st = check_ws(workspace, workspace_bytes, tpl_fullatom_lrmsd_workspace_size(B, Lmax)))) return st;
-    cudaError_t e = launch_fullatom_lrmsd_backward(seq, lengths, coords, target, grad_lrmsd, num_atoms, lrmsd, B,
-                                                   Lmax, Amax, grad_angles, workspace, cfg,
-                                                   reinterpret_cast<cudaStream_t>(stream));
+    cudaError_t e = launch_fullatom_lrmsd_backward(seq, lengths, coords, target, grad_lrmsd, B, Lmax, Amax,
+                                                   grad_angles, workspace, cfg, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "fullatom_lrmsd_backward");
     return ok();
 }

@@ -681,13 +681,8 @@ __device__ __forceinline__ float3 unit3(float3 v) { return f3_scale(rsqrtf(f3_do
 //     atoms of the chain;
 //  4. each thread walks its residues back, adding each residue's sums, and
 //     forms phi, psi and omega from them and from its N, C and O terms.
-// RES (with LR, the fused training step): the LRMSD gradient is formed
-// without its 1 / (N LRMSD) factor, each tile also sums its atoms' squared
-// residuals |y' - U x'|^2 (Section 4), and the chain's first tile -- taken
-// last -- waits for the chain's other tiles, forms LRMSD in FP64 and rescales
-// the chain's angle gradients.
 // ---------------------------------------------------------------------------
-template <int NT, int K, bool LR, bool RES, bool PACK>
+template <int NT, int K, bool LR, bool PACK>
 __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kernel(
     const uint8_t* __restrict__ seq, const int32_t* __restrict__ lengths, int B, int Lmax, int Amax,
     const float* __restrict__ coords, const float* __restrict__ grad_coords,
@@ -699,8 +694,6 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
     __shared__ float s6[6 * (NW + 1)];
     __shared__ float s_later[6];
     __shared__ int s_v, s_next;
-    __shared__ float s_res[NW];
-    __shared__ float s_scale;
     __shared__ PackS s_pack;  // a pack of whole short chains
     __shared__ int s_fl[NW + 1];
     __shared__ int s_mn[kMaxPack], s_mbase[kMaxPack + 1];  // atoms per member, stage offsets (floats)
@@ -724,7 +717,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
         const int2 ct = ws.tiles[v];
         // a tile of one chain (the chain's tiles taken last to first), or a
         // pack of whole chains in slots of K residues (segmented sums)
-        if (ct.x < 0 && (RES || !PACK)) {
+        if (ct.x < 0 && !PACK) {
             // a pack, but this backward was not built for packs (the forward
             // ran with another schedule than these options name)
             if (threadIdx.x == 0) flag_status(TPL_STATUS_BAD_WORKSPACE);
@@ -798,18 +791,17 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
             u2 = make_float3(__ldg(st + 6), __ldg(st + 7), __ldg(st + 8));
             xc = make_float3(__ldg(st + 9), __ldg(st + 10), __ldg(st + 11));
             yc = make_float3(__ldg(st + 12), __ldg(st + 13), __ldg(st + 14));
-            w = __ldg(lg.grad_lrmsd + b) * (RES ? 1.f : __ldg(st + 15));
+            w = __ldg(lg.grad_lrmsd + b) * __ldg(st + 15);
         }
         auto Rp = [&](int a) { return make_float3(rb[rofs + 3 * a], rb[rofs + 3 * a + 1], rb[rofs + 3 * a + 2]); };
         // the coordinate gradient of atom a at position r: read, or formed from
-        // the LRMSD state (and, for RES, its squared residual added to *res)
-        auto G = [&](int a, float3 r, float* res) {
+        // the LRMSD state
+        auto G = [&](int a, float3 r) {
             const float* src = LR ? lg.target + ((size_t)b * Amax + a) * 3 : grad_coords + ((size_t)b * Amax + a) * 3;
             const float3 v3 = make_float3(__ldg(src), __ldg(src + 1), __ldg(src + 2));
             if constexpr (!LR) return v3;
             const float3 xp = f3_sub(v3, xc), yp = f3_sub(r, yc);
             const float3 d = make_float3(yp.x - f3_dot(u0, xp), yp.y - f3_dot(u1, xp), yp.z - f3_dot(u2, xp));
-            if (RES && res) *res += f3_dot(d, d);
             return f3_scale(w, d);
         };
         auto add = [](Sum6& s, float3 r, float3 g) {
@@ -827,7 +819,6 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
         // the N and C, O sums and the axis atoms are kept for step 4, with more
         // they are formed again there
         constexpr bool KEEP = K <= 2;
-        float res_acc = 0.f;  // RES: this thread's squared residuals
         Sum6 own[K];
         Sum6 tsum = sum6_zero();
         bool in_range[K];
@@ -856,12 +847,12 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
                 if constexpr (KEEP) {
                     Sum6 ns = sum6_zero(), co = sum6_zero(), ca = sum6_zero();
                     const float3 rN = Rp(a), rCA = Rp(a + 1), rC = Rp(a + 2);
-                    add(ns, rN, G(a, rN, &res_acc));
-                    add(ca, rCA, G(a + 1, rCA, &res_acc));
-                    add(co, rC, G(a + 2, rC, &res_acc));
+                    add(ns, rN, G(a, rN));
+                    add(ca, rCA, G(a + 1, rCA));
+                    add(co, rC, G(a + 2, rC));
                     if (nat > 3) {  // O (a backbone-only residue has none)
                         const float3 rO = Rp(a + 3);
-                        add(co, rO, G(a + 3, rO, &res_acc));
+                        add(co, rO, G(a + 3, rO));
                     }
                     s = sum6_add(sum6_add(ns, ca), co);
                     nkeep[k] = ns;
@@ -873,7 +864,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
 #pragma unroll
                     for (int q = 0; q < min(4, nat); ++q) {  // N, CA, C, O
                         const float3 r = Rp(a + q);
-                        add(s, r, G(a + q, r, &res_acc));
+                        add(s, r, G(a + q, r));
                     }
                 }
                 // side chain, entries in decreasing group order: suffix over groups
@@ -883,7 +874,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
                     const int wv = (int)s_tab.side[ty][e].w;
                     const int grp = wv >> 4;
                     const float3 r = Rp(a + (wv & 15));
-                    add(suf, r, G(a + (wv & 15), r, &res_acc));
+                    add(suf, r, G(a + (wv & 15), r));
                     const bool last_of_group = (e == 0) || (((int)s_tab.side[ty][e - 1].w >> 4) != grp);
                     if (last_of_group && grp <= nchi) {
                         const int o1 = s_tab.origin[ty][grp - 1];
@@ -923,14 +914,12 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
                 if (threadIdx.x == 0) {
                     s_later[0] = later.c.x; s_later[1] = later.c.y; s_later[2] = later.c.z;
                     s_later[3] = later.g.x; s_later[4] = later.g.y; s_later[5] = later.g.z;
-                    // after the last wait of this tile (the chain's first tile of a
-                    // fused step still waits for the chain's other tiles: it asks later)
-                    s_next = (RES && t == 0) ? 0 : request_tile(counter);
+                    s_next = request_tile(counter);  // after the last wait of this tile
                 }
             }
         }
         __syncthreads();
-        int requested = s_next;
+        const int requested = s_next;
         Sum6 A;
         A.c = f3_add(after.c, make_float3(s_later[0], s_later[1], s_later[2]));
         A.g = f3_add(after.g, make_float3(s_later[3], s_later[4], s_later[5]));
@@ -958,11 +947,11 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
                     rC = Rp(a + 2);
                     nsum = sum6_zero();
                     co = sum6_zero();
-                    add(nsum, rN, G(a, rN, nullptr));
-                    add(co, rC, G(a + 2, rC, nullptr));
+                    add(nsum, rN, G(a, rN));
+                    add(co, rC, G(a + 2, rC));
                     if (type[k] != kBackboneCode) {  // O
                         const float3 rO = Rp(a + 3);
-                        add(co, rO, G(a + 3, rO, nullptr));
+                        add(co, rO, G(a + 3, rO));
                     }
                 }
                 Sum6 x = sum6_add(co, A);
@@ -1000,44 +989,6 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
             for (int i = L + threadIdx.x; i < Lmax; i += NT)
 #pragma unroll
                 for (int r = 0; r < 7; ++r) ga[r * Lmax + i] = 0.f;
-        }
-        if constexpr (RES) {
-            // this tile's residual sum, then "done" once every thread's
-            // gradient writes are in
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) res_acc += __shfl_xor_sync(0xffffffffu, res_acc, o);
-            if ((threadIdx.x & 31) == 0) s_res[threadIdx.x >> 5] = res_acc;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                float tot = 0.f;
-                for (int w2 = 0; w2 < NW; ++w2) tot += s_res[w2];
-                ws.tres[slot0 + t] = tot;
-                __threadfence();
-                flag_release(ws.tdone + slot0 + t, 1);
-            }
-            if (t == 0) {
-                // the chain's LRMSD from its tiles' residual sums (fixed order,
-                // FP64), then the factor 1 / (N LRMSD) on all its gradients
-                if (threadIdx.x == 0) {
-                    double sum = 0.0;
-                    for (int tp = 0; tp < T; ++tp) {
-                        if (tp > 0) wait_flag(ws.tdone + slot0 + tp);
-                        sum += (double)__ldcg(ws.tres + slot0 + tp);
-                    }
-                    const int na = lg.num_atoms[b] < Amax ? lg.num_atoms[b] : Amax;
-                    float lr, scale;
-                    lrmsd_from_sum(sum, na, lr, scale);
-                    lg.lrmsd_out[b] = lr;
-                    s_scale = scale;
-                }
-                __syncthreads();
-                const float sc = s_scale;
-                for (int i = threadIdx.x; i < 7 * L; i += NT) {
-                    float* q = ga + (i / L) * Lmax + (i % L);
-                    *q = __ldcg(q) * sc;
-                }
-                requested = request_tile(counter);
-            }
         }
         fence_proxy_async();  // this tile's stage reads, ordered before the next tile's bulk copy
         v = next_tile(requested, &s_v);
@@ -1537,16 +1488,16 @@ cudaError_t fa_fwd_t(const float* angles, const uint8_t* seq, const int32_t* len
     return cudaGetLastError();
 }
 
-template <int NT, int K, bool LR, bool RES, bool PACK>
+template <int NT, int K, bool LR, bool PACK>
 cudaError_t fa_bwd_coords_t(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
                             const float* coords, const float* grad_coords, float* grad_angles,
                             const ChainWs& ws, LrmsdGrad lg, cudaStream_t s) {
     const size_t smem = fa_smem<NT, K>();
     static bool done[64] = {false};
-    cudaError_t e = smem_attr_once(fa_bwd_coords_kernel<NT, K, LR, RES, PACK>, (int)smem, done);
+    cudaError_t e = smem_attr_once(fa_bwd_coords_kernel<NT, K, LR, PACK>, (int)smem, done);
     if (e != cudaSuccess) return e;
-    const int grid = persistent_grid((const void*)fa_bwd_coords_kernel<NT, K, LR, RES, PACK>, NT, smem);
-    fa_bwd_coords_kernel<NT, K, LR, RES, PACK><<<grid, NT, smem, s>>>(seq, lengths, B, Lmax, Amax, coords,
+    const int grid = persistent_grid((const void*)fa_bwd_coords_kernel<NT, K, LR, PACK>, NT, smem);
+    fa_bwd_coords_kernel<NT, K, LR, PACK><<<grid, NT, smem, s>>>(seq, lengths, B, Lmax, Amax, coords,
                                                                       grad_coords, grad_angles, ws, lg, fa_table());
     return cudaGetLastError();
 }
@@ -1580,7 +1531,7 @@ bool fullatom_cfg_supported(int threads, int k) {
 }
 
 #define TPL_FA_CASE_FWD(NT, K) case NT * 8 + K: e = fa_fwd_t<NT, K, LMV, PACKV>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, s, target); break;
-#define TPL_FA_CASE_BWD(NT, K) case NT * 8 + K: return fa_bwd_coords_t<NT, K, LRV, RESV, PACKV>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, lg, s);
+#define TPL_FA_CASE_BWD(NT, K) case NT * 8 + K: return fa_bwd_coords_t<NT, K, LRV, PACKV>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles, ws, lg, s);
 
 namespace {
 
@@ -1596,7 +1547,7 @@ cudaError_t fa_forward_shape(const float* angles, const uint8_t* seq, const int3
     return e;
 }
 
-template <bool LRV, bool RESV, bool PACKV>
+template <bool LRV, bool PACKV>
 cudaError_t fa_backward_shape(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
                               const float* coords, const float* grad_coords, float* grad_angles,
                               const ChainWs& ws, LrmsdGrad lg, LaunchCfg cfg, cudaStream_t s) {
@@ -1636,10 +1587,10 @@ cudaError_t launch_fullatom_backward(const float* angles, const uint8_t* seq,
     cudaError_t e = reset_backward_flags(ws, s);
     if (e != cudaSuccess) return e;
     if (from_coords && cfg.packed)
-        return fa_backward_shape<false, false, true>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles,
+        return fa_backward_shape<false, true>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles,
                                                      ws, LrmsdGrad{}, cfg, s);
     if (from_coords)
-        return fa_backward_shape<false, false, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles,
+        return fa_backward_shape<false, false>(seq, lengths, B, Lmax, Amax, coords, grad_coords, grad_angles,
                                                       ws, LrmsdGrad{}, cfg, s);
     // frames rebuilt from the angles: one residue per thread
     if (cfg.res_per_thread != 1) return cudaErrorInvalidValue;
@@ -1673,16 +1624,16 @@ cudaError_t launch_fullatom_backward_lrmsd(const uint8_t* seq, const int32_t* le
     if (e != cudaSuccess) return e;
     const LrmsdGrad lg{target, lrmsd_state, grad_lrmsd};
     if (cfg.packed)
-        return fa_backward_shape<true, false, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg,
+        return fa_backward_shape<true, true>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg,
                                                     cfg, s);
-    return fa_backward_shape<true, false, false>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg,
+    return fa_backward_shape<true, false>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg,
                                                  cfg, s);
 }
 
 cudaError_t launch_fullatom_lrmsd_forward(const float* angles, const uint8_t* seq, const int32_t* lengths,
                                           const float* target, int B, int Lmax, int Amax, float* coords,
-                                          int32_t* num_atoms, int sched_mode, void* workspace, LaunchCfg cfg,
-                                          cudaStream_t s) {
+                                          int32_t* num_atoms, float* lrmsd, int sched_mode, void* workspace,
+                                          LaunchCfg cfg, cudaStream_t s) {
     if (B == 0) return cudaSuccess;
     ChainWs ws;
     chain_ws_layout(workspace, B, Lmax, &ws, true, true);
@@ -1692,23 +1643,23 @@ cudaError_t launch_fullatom_lrmsd_forward(const float* angles, const uint8_t* se
     if (e != cudaSuccess) return e;
     e = fa_forward_shape<true, false>(angles, seq, lengths, Lmax, Amax, coords, num_atoms, ws, cfg, s, target);
     if (e != cudaSuccess) return e;
-    return launch_lrmsd_solve_tiles(coords, target, num_atoms, B, Amax, ws.tmom, ws.tmax, lengths, tile,
-                                    Lmax, ws.lstate, s, true, 1);
+    return launch_lrmsd_parts(coords, target, num_atoms, B, Amax, ws.tmom, ws.tmax, lengths, tile, Lmax, ws.lstate,
+                              lrmsd, s);
 }
 
 cudaError_t launch_fullatom_lrmsd_backward(const uint8_t* seq, const int32_t* lengths, const float* coords,
-                                           const float* target, const float* grad_lrmsd,
-                                           const int32_t* num_atoms, float* lrmsd, int B, int Lmax, int Amax,
-                                           float* grad_angles, void* workspace, LaunchCfg cfg, cudaStream_t s) {
+                                           const float* target, const float* grad_lrmsd, int B, int Lmax,
+                                           int Amax, float* grad_angles, void* workspace, LaunchCfg cfg,
+                                           cudaStream_t s) {
     if (B == 0) return cudaSuccess;
     ChainWs ws;
     chain_ws_layout(workspace, B, Lmax, &ws, true, true);
     ws.flags = cfg.flags;
     cudaError_t e = reset_backward_flags(ws, s);
     if (e != cudaSuccess) return e;
-    LrmsdGrad lg{target, ws.lstate, grad_lrmsd, lrmsd, num_atoms};
-    return fa_backward_shape<true, true, false>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg,
-                                                cfg, s);
+    const LrmsdGrad lg{target, ws.lstate, grad_lrmsd};
+    return fa_backward_shape<true, false>(seq, lengths, B, Lmax, Amax, coords, nullptr, grad_angles, ws, lg,
+                                                 cfg, s);
 }
 
 cudaError_t launch_fullatom_backward_quadratic(const uint8_t* seq, const int32_t* lengths, int B, int Lmax,

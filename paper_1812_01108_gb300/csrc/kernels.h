@@ -91,6 +91,11 @@ cudaError_t launch_fullatom_backward_lrmsd(const uint8_t* seq, const int32_t* le
 // tiles of `tile` residues): the fused training steps.  Writes the per-pair
 // state (16 floats per pair) of the chains of at least min_tiles tiles.
 // num_atoms null: chain p has 3 lengths[p] atoms (backbone).
+// Fused full-atom step: per chain, its tile moments summed, the eigen-solve, the
+// residual pass over its atoms; state (as tpl_lrmsd_forward's) and lrmsd out.
+cudaError_t launch_lrmsd_parts(const float* input, const float* target, const int32_t* num_atoms, int P,
+                               int Nmax, const float* tile_moments, int tiles_max, const int32_t* lengths, int tile,
+                               int Lmax, float* state, float* lrmsd, cudaStream_t s);
 cudaError_t launch_lrmsd_solve_tiles(const float* input, const float* target, const int32_t* num_atoms,
                                      int P, int Nmax, const float* tile_moments, int tiles_max,
                                      const int32_t* lengths, int tile, int Lmax, float* state,
@@ -107,16 +112,17 @@ cudaError_t launch_backbone_lrmsd_step(const float* angles, const int32_t* lengt
 
 // Fused training step on the full-atom model with the LRMSD loss (workspace of
 // chain_ws_bytes(B, Lmax, true, true)): forward = schedule, forward with
-// per-tile LRMSD moments, eigen-solve; backward = the LRMSD gradient formed in
-// the full-atom backward with the residual sums and the final 1 / (N LRMSD).
+// per-tile LRMSD moments, per chain the eigen-solve and the residual pass
+// (LRMSD out); backward = the full-atom backward with the LRMSD gradient
+// formed inside.
 cudaError_t launch_fullatom_lrmsd_forward(const float* angles, const uint8_t* seq, const int32_t* lengths,
                                           const float* target, int B, int Lmax, int Amax, float* coords,
-                                          int32_t* num_atoms, int sched_mode, void* workspace, LaunchCfg cfg,
-                                          cudaStream_t s);
+                                          int32_t* num_atoms, float* lrmsd, int sched_mode, void* workspace,
+                                          LaunchCfg cfg, cudaStream_t s);
 cudaError_t launch_fullatom_lrmsd_backward(const uint8_t* seq, const int32_t* lengths, const float* coords,
-                                           const float* target, const float* grad_lrmsd,
-                                           const int32_t* num_atoms, float* lrmsd, int B, int Lmax, int Amax,
-                                           float* grad_angles, void* workspace, LaunchCfg cfg, cudaStream_t s);
+                                           const float* target, const float* grad_lrmsd, int B, int Lmax,
+                                           int Amax, float* grad_angles, void* workspace, LaunchCfg cfg,
+                                           cudaStream_t s);
 
 // K5 / K6: LRMSD.  The workspace layout is private to lrmsd.cu.
 size_t lrmsd_ws_bytes(int P, int Nmax);

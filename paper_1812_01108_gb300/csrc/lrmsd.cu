@@ -70,16 +70,67 @@ __global__ void __launch_bounds__(32) lrmsd_solve_tiles_kernel(
 
 // ---------------------------------------------------------------------------
 // K5: the whole forward of a pair in one CTA: moments, eigen-solve by one quad
-// of warp 0, residual sum and LRMSD, with block barriers between the steps.
-// Two shapes: 256 threads with four groups of four atoms per thread in
-// flight (two CTAs per SM) for batches that fit one wave, and a compact one,
-// 128 threads with one group (eight CTAs per SM), for larger batches: about
-// 1200 pairs are then in flight, their clouds (tens of MB) stay in L2, and
-// the residual pass reads them from there instead of from HBM, while other
-// CTAs on the SM stream while one CTA's quad solves.
+// of one warp, residual sum and LRMSD, with block barriers between the steps.
+// The solving warp is the pair index modulo the CTA's warps: the CTAs an SM
+// holds then solve on different schedulers.  Two shapes: 256 threads with
+// four groups of four atoms per thread in flight (two CTAs per SM) for
+// batches that fit one wave, and a compact one, 128 threads with two groups
+// (six CTAs per SM), for larger batches: about 900 pairs are then in flight,
+// their clouds (tens of MB) stay in L2, and the residual pass reads them from
+// there instead of from HBM, while other CTAs on the SM stream while one
+// CTA's quad solves.
 // ---------------------------------------------------------------------------
 constexpr int kPNT = 256;
 constexpr int kCNT = 128;  // compact shape
+
+// The residual pass and the state of one pair, by the whole CTA after the
+// eigen-solve left U and the centroids in s_st: sum |y'_i - U x'_i|^2 (FP32
+// per thread, FP64 over the warps), LRMSD and 1 / (N LRMSD); G groups of four
+// atoms per thread in flight.  Ends with the state written (16 floats).
+template <int NT, int G>
+__device__ __forceinline__ void residual_pass(const float* __restrict__ x, const float* __restrict__ y, int n,
+                                              const float* s_st, double* s_res, float* __restrict__ state_p,
+                                              float* __restrict__ lrmsd_p) {
+    constexpr int NW = NT / 32;
+    constexpr int kBatch = 4 * G * NT;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const PairState ps = load_state_shared(s_st);
+    float acc = 0.f;
+    for (int base = 0; base < n; base += kBatch) {
+        float3 xv[G][4], yv[G][4];
+#pragma unroll
+        for (int s = 0; s < G; ++s) {
+            const int i0 = base + 4 * (threadIdx.x + NT * s);
+            if (i0 < n) {
+                load4(x + 3 * (size_t)i0, xv[s]);
+                load4(y + 3 * (size_t)i0, yv[s]);
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < G; ++s) {
+            const int i0 = base + 4 * (threadIdx.x + NT * s);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (i0 + q < n) {
+                    const float3 d = residual(ps, xv[s][q], yv[s][q]);
+                    acc += f3_dot(d, d);
+                }
+        }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) s_res[warp] = (double)acc;
+    __syncthreads();
+    if (threadIdx.x < 15) state_p[threadIdx.x] = s_st[threadIdx.x];
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) sum += s_res[w];
+        float lr, scale;
+        lrmsd_from_sum(sum, n, lr, scale);
+        state_p[15] = scale;
+        *lrmsd_p = lr;
+    }
+}
 
 template <int NT, int G, int MINB>
 __global__ void __launch_bounds__(NT, MINB) lrmsd_pair_kernel(
@@ -143,7 +194,7 @@ __global__ void __launch_bounds__(NT, MINB) lrmsd_pair_kernel(
         if (lane == 0) s_mom[warp][k] = v;
     }
     __syncthreads();
-    if (warp == 0) {
+    if (warp == (p & (NW - 1))) {  // differs from pair to pair: co-resident CTAs solve on different schedulers
         // lane k < kMom sums moment k over the warps (fixed order), then every
         // lane takes all of them
         float v = 0.f;
@@ -157,42 +208,36 @@ __global__ void __launch_bounds__(NT, MINB) lrmsd_pair_kernel(
         quad_eigen_solve(S, x0, y0, n, lane & 3, lane, lane < 4, s_st);
     }
     __syncthreads();
-    const PairState ps = load_state_shared(s_st);
-    float acc = 0.f;
-    for (int base = 0; base < n; base += kBatch) {
-        float3 xv[G][4], yv[G][4];
-#pragma unroll
-        for (int s = 0; s < G; ++s) {
-            const int i0 = base + 4 * (threadIdx.x + kPNT * s);
-            if (i0 < n) {
-                load4(x + 3 * (size_t)i0, xv[s]);
-                load4(y + 3 * (size_t)i0, yv[s]);
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < G; ++s) {
-            const int i0 = base + 4 * (threadIdx.x + kPNT * s);
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (i0 + q < n) {
-                    const float3 d = residual(ps, xv[s][q], yv[s][q]);
-                    acc += f3_dot(d, d);
-                }
-        }
+    residual_pass<NT, G>(x, y, n, s_st, s_res, state + 16 * (size_t)p, lrmsd + p);
+}
+
+// K5p: the LRMSD of the fused full-atom step from the forward's per-tile
+// moments (the forward reduced each tile's atoms against the target): one CTA
+// per chain; one quad of one warp sums the chain's tile partials in order and
+// solves, then the CTA sums the squared residuals over the chain's atoms,
+// which the forward has just written and read, so they come from L2.
+template <int NT, int G>
+__global__ void __launch_bounds__(NT) lrmsd_parts_kernel(
+    const float* __restrict__ input, const float* __restrict__ target, const int32_t* __restrict__ num_atoms,
+    int P, int Nmax, const float* __restrict__ part1, int tiles_max, const int32_t* __restrict__ lengths,
+    int tile, int Lmax, float* __restrict__ state, float* __restrict__ lrmsd) {
+    __shared__ double s_res[NT / 32];
+    __shared__ __align__(16) float s_st[16];
+    const int p = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const float* x = target + (size_t)p * Nmax * 3;
+    const float* y = input + (size_t)p * Nmax * 3;
+    const int n = pair_atoms(num_atoms, p, Nmax);
+    if ((threadIdx.x >> 5) == (p & (NT / 32 - 1))) {  // solves of co-resident CTAs on different schedulers
+        const int L = min(max(lengths[p], 0), Lmax);
+        float x0[3], y0[3];
+        first_atoms(x, y, n, x0, y0);
+        float S[kSlot];
+        quad_sum_partials(part1 + (size_t)p * tiles_max * kSlot, fa_num_tiles(L, tile), lane & 3, S);
+        quad_eigen_solve(S, x0, y0, n, lane & 3, lane, lane < 4, s_st);
     }
-    acc = warp_sum(acc);
-    if (lane == 0) s_res[warp] = (double)acc;
     __syncthreads();
-    if (threadIdx.x < 15) state[16 * (size_t)p + threadIdx.x] = s_st[threadIdx.x];
-    if (threadIdx.x == 0) {
-        double sum = 0.0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) sum += s_res[w];
-        float lr, scale;
-        lrmsd_from_sum(sum, n, lr, scale);
-        state[16 * (size_t)p + 15] = scale;
-        lrmsd[p] = lr;
-    }
+    residual_pass<NT, G>(x, y, n, s_st, s_res, state + 16 * (size_t)p, lrmsd + p);
 }
 
 // ---------------------------------------------------------------------------
@@ -401,6 +446,15 @@ cudaError_t launch_lrmsd_solve_tiles(const float* input, const float* target, co
     lrmsd_solve_tiles_kernel<<<(4 * P + 31) / 32, 32, 0, s>>>(input, target, num_atoms, P, Nmax, tile_moments,
                                                              tiles_max, state, lengths, tile, Lmax, balanced,
                                                              min_tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lrmsd_parts(const float* input, const float* target, const int32_t* num_atoms, int P,
+                               int Nmax, const float* tile_moments, int tiles_max, const int32_t* lengths, int tile,
+                               int Lmax, float* state, float* lrmsd, cudaStream_t s) {
+    if (P == 0) return cudaSuccess;
+    lrmsd_parts_kernel<kPNT, 4><<<P, kPNT, 0, s>>>(input, target, num_atoms, P, Nmax, tile_moments, tiles_max,
+                                                   lengths, tile, Lmax, state, lrmsd);
     return cudaGetLastError();
 }
 

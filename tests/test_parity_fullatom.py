@@ -373,7 +373,8 @@ def test_fused_lrmsd_backward_equals_the_two_calls_and_the_oracle(shape):
 @pytest.mark.parametrize("shape", [(384, 1), (192, 2), (64, 4)])
 def test_fused_training_step_matches_the_separate_calls_and_the_oracle(shape):
     """tpl_fullatom_lrmsd_forward / _backward (moments in the forward's tiles,
-    residuals and the 1 / (N LRMSD) factor in the backward) against
+    then per chain the eigen-solve and the residual pass; the LRMSD gradient
+    formed in the backward) against
     tpl_fullatom_forward + tpl_lrmsd_forward + tpl_fullatom_backward_lrmsd and
     against the oracle chain on the same FP32 coordinates."""
     d = require_gpu()
@@ -402,10 +403,10 @@ def test_fused_training_step_matches_the_separate_calls_and_the_oracle(shape):
     st_ws = torch.empty(tpl.tpl_fullatom_lrmsd_workspace_size(B, Lmax), dtype=torch.uint8, device=d)
     c2 = torch.full_like(tgt, float("nan"))
     n2 = torch.full((B,), -1, dtype=torch.int32, device=d)
-    tpl.tpl_fullatom_lrmsd_forward(A, S, Ln, tgt, c2, n2, st_ws, opts)
     l2 = torch.full((B,), float("nan"), device=d)
+    tpl.tpl_fullatom_lrmsd_forward(A, S, Ln, tgt, c2, n2, l2, st_ws, opts)
     g2 = torch.full_like(A, float("nan"))
-    tpl.tpl_fullatom_lrmsd_backward(S, Ln, c2, tgt, n2, w, l2, g2, st_ws, opts)
+    tpl.tpl_fullatom_lrmsd_backward(S, Ln, c2, tgt, w, g2, st_ws, opts)
     torch.cuda.synchronize()
     assert tpl.tpl_get_status() & ~tpl.STATUS_ZERO_LRMSD == 0
     assert np.array_equal(host(c1), host(c2)) and np.array_equal(host(na), host(n2))

@@ -1,5 +1,5 @@
-"""LRMSD (Section 4): FP32 kernels with the FP64 eigen-solve, and the FP64
-per-pair form, against the FP64 CPU oracle.  Tolerances: LRMSD max-abs <= 1e-5 A;
+"""LRMSD (Section 4): FP32 kernels (an FP32 eigen-solve refined once against
+the exact T), and the FP64 per-pair form, against the FP64 CPU oracle.  Tolerances: LRMSD max-abs <= 1e-5 A;
 gradient ||g32 - g64|| / ||g64|| <= 1e-4 per pair; FP64 form 1e-9.
 """
 import numpy as np
