@@ -68,11 +68,23 @@ TRAFFIC = {
     # Full-atom kernels captured at 4096 chains x 700 residues (coordinates above L2),
     # scaled by residues processed.
     ("training_step", "fullatom_forward"): (
-        321330432 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
+        319054336 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
         "threads=384,res_per_thread=1"),
     ("training_step", "lrmsd_fullatom_backward"): (
-        663435776 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
+        661793280 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
         "threads=384,res_per_thread=1"),
+    # the uneven backbone batch itself (1302424 residues), shape 256 x 4
+    ("backbone_uneven", "backbone_forward"): (
+        19462656 / 1302424, "residue", "profiles/backbone_kernels_backbone_uneven_4096.md",
+        "threads=256,res_per_thread=4"),
+    ("backbone_uneven", "lrmsd_backbone_backward"): (
+        101150976 / 1302424, "residue", "profiles/backbone_kernels_backbone_uneven_4096.md",
+        "threads=256,res_per_thread=4"),
+    # LRMSD kernels captured on 4096 pairs (10499521 atoms), scaled by atoms
+    ("lrmsd_batch", "lrmsd_forward"): (
+        273839872 / 10499521, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md", None),
+    ("lrmsd_batch", "lrmsd_backward"): (
+        449672960 / 10499521, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md", None),
 }
 
 
