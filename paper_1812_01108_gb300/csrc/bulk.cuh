@@ -35,6 +35,21 @@ __device__ __forceinline__ void bulk_load(float* dst, const float* src, unsigned
                  : "memory");
 }
 
+// Two bulk copies counted by one barrier phase: one arrival that expects the
+// bytes of both.
+__device__ __forceinline__ void bulk_load2(float* dst1, const float* src1, float* dst2, const float* src2,
+                                           unsigned bytes, uint64_t* bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(2u * bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst1)), "l"(src1), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst2)), "l"(src2), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned phase) {
     unsigned done;
     asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"

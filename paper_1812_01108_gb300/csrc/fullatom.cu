@@ -208,6 +208,42 @@ __device__ __forceinline__ bool bulk_copy_range(const float* __restrict__ glob, 
     return true;
 }
 
+// bulk_copy_range for two arrays of the same layout at the same range (the
+// tile's coordinates and their gradient or target), into two stages: both
+// aligned middles come in under one barrier phase.
+template <int NT>
+__device__ __forceinline__ bool bulk_copy_range2(const float* __restrict__ glob1, float* __restrict__ stage1,
+                                                 const float* __restrict__ glob2, float* __restrict__ stage2, int g0,
+                                                 int g1, uint64_t* bar) {
+    if (g1 <= g0) return false;
+    const int off = g0 & 3;
+    const int head = min(g1, (g0 + 3) & ~3);
+    const int tail = max(head, g1 & ~3);
+    for (int i = g0 + threadIdx.x; i < head; i += NT) {
+        cp_async4(stage1 + off + i - g0, glob1 + i);
+        cp_async4(stage2 + off + i - g0, glob2 + i);
+    }
+    for (int i = tail + threadIdx.x; i < g1; i += NT) {
+        cp_async4(stage1 + off + i - g0, glob1 + i);
+        cp_async4(stage2 + off + i - g0, glob2 + i);
+    }
+    if (tail <= head) return false;
+    float* dst1 = stage1 + off + head - g0;
+    float* dst2 = stage2 + off + head - g0;
+    const float* src1 = glob1 + head;
+    const float* src2 = glob2 + head;
+    if (((smem_addr(dst1) | smem_addr(dst2) | (unsigned)reinterpret_cast<uintptr_t>(src1) |
+          (unsigned)reinterpret_cast<uintptr_t>(src2)) & 15u) != 0u) {  // (not expected)
+        for (int i = head + threadIdx.x; i < tail; i += NT) {
+            cp_async4(stage1 + off + i - g0, glob1 + i);
+            cp_async4(stage2 + off + i - g0, glob2 + i);
+        }
+        return false;
+    }
+    if (threadIdx.x == 0) bulk_load2(dst1, src1, dst2, src2, 4u * (unsigned)(tail - head), bar);
+    return true;
+}
+
 // store_range for a stage laid out as stage[off + i - g0] <-> glob[i], off =
 // g0 mod 4: the ragged ends by the threads, the 16-byte aligned middle by one
 // bulk store (which runs on while the CTA goes on to its next tile).
@@ -267,6 +303,13 @@ __host__ __device__ constexpr size_t fa_smem() {
     return (size_t)(4 + 3 * fa_stage_atoms<NT, K>()) * sizeof(float);
 }
 
+// The coordinate-reading backward stages a tile's coordinates and, beside
+// them, its coordinate gradient (or target): two stages.
+template <int NT, int K>
+__host__ __device__ constexpr size_t fa_bwd_smem() {
+    return 2 * fa_smem<NT, K>();
+}
+
 // CTAs per SM the kernels are compiled for: what shared memory allows (227 KB
 // per SM; the residue table and the scan scratch take about 7 KB per CTA),
 // capped by a register budget per thread that grows with K.
@@ -274,10 +317,11 @@ template <int K>
 __host__ __device__ constexpr int fa_reg_budget() {
     return K == 1 ? 80 : (K == 2 ? 96 : 160);
 }
-template <int NT, int K>
+template <int NT, int K, bool BWD = false>
 __host__ __device__ constexpr int fa_min_blocks() {
-    return (227 * 1024 / (int)(fa_smem<NT, K>() + 7 * 1024)) < (65536 / (NT * fa_reg_budget<K>()))
-               ? (227 * 1024 / (int)(fa_smem<NT, K>() + 7 * 1024))
+    return (227 * 1024 / (int)((BWD ? fa_bwd_smem<NT, K>() : fa_smem<NT, K>()) + 7 * 1024)) <
+                   (65536 / (NT * fa_reg_budget<K>()))
+               ? (227 * 1024 / (int)((BWD ? fa_bwd_smem<NT, K>() : fa_smem<NT, K>()) + 7 * 1024))
                : (65536 / (NT * fa_reg_budget<K>()));
 }
 
@@ -669,7 +713,8 @@ __device__ __forceinline__ float3 unit3(float3 v) { return f3_scale(rsqrtf(f3_do
 // origins come from atom positions (phi: N->CA, psi: CA->C, omega: C_{j-1}->N_j,
 // chi_k: origin of group k-1 -> origin of group k).  One tile per step of a
 // persistent CTA, the tiles of a chain taken last to first:
-//  1. the tile's coordinates are staged with coalesced asynchronous copies
+//  1. the tile's coordinates and, in a second stage, their gradient (with LR
+//     the target) come into shared memory by bulk copies of the TMA engine
 //     (the forward recorded each tile's first atom and atom count, and every
 //     residue's first atom);
 //  2. each thread walks its K residues: every atom's gradient (read, or the
@@ -683,7 +728,7 @@ __device__ __forceinline__ float3 unit3(float3 v) { return f3_scale(rsqrtf(f3_do
 //     forms phi, psi and omega from them and from its N, C and O terms.
 // ---------------------------------------------------------------------------
 template <int NT, int K, bool LR, bool PACK>
-__global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kernel(
+__global__ void __launch_bounds__(NT, (fa_min_blocks<NT, K, true>())) fa_bwd_coords_kernel(
     const uint8_t* __restrict__ seq, const int32_t* __restrict__ lengths, int B, int Lmax, int Amax,
     const float* __restrict__ coords, const float* __restrict__ grad_coords,
     float* __restrict__ grad_angles, ChainWs ws, LrmsdGrad lg, const __grid_constant__ FaTable tab) {
@@ -700,6 +745,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
     __shared__ __align__(8) uint64_t s_bar;  // completes when a tile's bulk copy has landed
     extern __shared__ float4 s_dyn[];
     float* st_r = reinterpret_cast<float*>(s_dyn);  // the tile's coordinates
+    float* st_g = st_r + fa_smem<NT, K>() / sizeof(float);  // their gradient (or target), same layout
 
     if (!ws_matches(ws, TILE, B, Lmax)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) flag_status(TPL_STATUS_BAD_WORKSPACE);
@@ -768,9 +814,11 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
                 for (int i = 0; i < m; ++i)
                     async_copy_range<NT>(coords + (size_t)s_pack.b[i] * Amax * 3, st_r + s_mbase[i], 0, 3 * s_mn[i]);
             } else {
-                bulk = bulk_copy_range<NT>(r_in, st_r, 3 * pc, 3 * a_end, &s_bar);
+                const float* g_in = (LR ? lg.target : grad_coords) + (size_t)b * Amax * 3;
+                bulk = bulk_copy_range2<NT>(r_in, st_r, g_in, st_g, 3 * pc, 3 * a_end, &s_bar);
             }
         }
+        const bool staged_g = staged && !pack;  // G comes from st_g at the coordinates' offsets
         // atom a is at rb[rofs + 3 a]
         const float* rb = staged ? st_r + (pack && ci >= 0 ? s_mbase[ci] : 0) : r_in;
         const int rofs = staged && !pack ? ((3 * pc) & 3) - 3 * pc : 0;
@@ -797,8 +845,13 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_bwd_coords_kern
         // the coordinate gradient of atom a at position r: read, or formed from
         // the LRMSD state
         auto G = [&](int a, float3 r) {
-            const float* src = LR ? lg.target + ((size_t)b * Amax + a) * 3 : grad_coords + ((size_t)b * Amax + a) * 3;
-            const float3 v3 = make_float3(__ldg(src), __ldg(src + 1), __ldg(src + 2));
+            float3 v3;
+            if (staged_g) {
+                v3 = make_float3(st_g[rofs + 3 * a], st_g[rofs + 3 * a + 1], st_g[rofs + 3 * a + 2]);
+            } else {
+                const float* src = LR ? lg.target + ((size_t)b * Amax + a) * 3 : grad_coords + ((size_t)b * Amax + a) * 3;
+                v3 = make_float3(__ldg(src), __ldg(src + 1), __ldg(src + 2));
+            }
             if constexpr (!LR) return v3;
             const float3 xp = f3_sub(v3, xc), yp = f3_sub(r, yc);
             const float3 d = make_float3(yp.x - f3_dot(u0, xp), yp.y - f3_dot(u1, xp), yp.z - f3_dot(u2, xp));
@@ -1492,7 +1545,7 @@ template <int NT, int K, bool LR, bool PACK>
 cudaError_t fa_bwd_coords_t(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
                             const float* coords, const float* grad_coords, float* grad_angles,
                             const ChainWs& ws, LrmsdGrad lg, cudaStream_t s) {
-    const size_t smem = fa_smem<NT, K>();
+    const size_t smem = fa_bwd_smem<NT, K>();
     static bool done[64] = {false};
     cudaError_t e = smem_attr_once(fa_bwd_coords_kernel<NT, K, LR, PACK>, (int)smem, done);
     if (e != cudaSuccess) return e;
