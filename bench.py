@@ -63,28 +63,33 @@ DEFAULT_BATCH = {"training_step": 256, "backbone_uneven": 4096, "lrmsd_batch": 1
 # keyed by (workload, call), with the profile summary that holds the capture.
 # An entry is removed when one of its kernels changes after the capture.
 TRAFFIC = {
-    # (per-unit DRAM bytes, unit, profile, launch shape of the capture or None if the
-    # kernels take none); cold-cache captures of one launch.
+    # (workload, call) -> entries (per-unit DRAM bytes, unit, profile, launch shape of the
+    # capture or None if the kernels take none); cold-cache captures of one launch.  The
+    # entry whose shape matches the step's launch shape is used.
     # Full-atom kernels captured at 4096 chains x 700 residues (coordinates above L2),
     # scaled by residues processed.
-    ("training_step", "fullatom_forward"): (
-        319054336 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
-        "threads=384,res_per_thread=1"),
-    ("training_step", "lrmsd_fullatom_backward"): (
-        661793280 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
-        "threads=384,res_per_thread=1"),
+    ("training_step", "fullatom_forward"): [
+        (319050496 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
+         "threads=384,res_per_thread=1"),
+        (319648000 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
+         "threads=256,res_per_thread=1")],
+    ("training_step", "lrmsd_fullatom_backward"): [
+        (661392896 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
+         "threads=384,res_per_thread=1"),
+        (662288896 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
+         "threads=256,res_per_thread=1")],
     # the uneven backbone batch itself (1302424 residues), shape 256 x 4
-    ("backbone_uneven", "backbone_forward"): (
-        19462656 / 1302424, "residue", "profiles/backbone_kernels_backbone_uneven_4096.md",
-        "threads=256,res_per_thread=4"),
-    ("backbone_uneven", "lrmsd_backbone_backward"): (
-        101150976 / 1302424, "residue", "profiles/backbone_kernels_backbone_uneven_4096.md",
-        "threads=256,res_per_thread=4"),
+    ("backbone_uneven", "backbone_forward"): [
+        (19462656 / 1302424, "residue", "profiles/backbone_kernels_backbone_uneven_4096.md",
+         "threads=256,res_per_thread=4")],
+    ("backbone_uneven", "lrmsd_backbone_backward"): [
+        (101150976 / 1302424, "residue", "profiles/backbone_kernels_backbone_uneven_4096.md",
+         "threads=256,res_per_thread=4")],
     # LRMSD kernels captured on 4096 pairs (10499521 atoms), scaled by atoms
-    ("lrmsd_batch", "lrmsd_forward"): (
-        273839872 / 10499521, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md", None),
-    ("lrmsd_batch", "lrmsd_backward"): (
-        449672960 / 10499521, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md", None),
+    ("lrmsd_batch", "lrmsd_forward"): [
+        (273839872 / 10499521, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md", None)],
+    ("lrmsd_batch", "lrmsd_backward"): [
+        (449672960 / 10499521, "atom", "profiles/lrmsd_kernels_lrmsd_batch_4096.md", None)],
 }
 
 
@@ -926,9 +931,8 @@ def measure(args, workload, tpl, torch, dev, rank, world, local, flush):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = st.alg[dom] / (mean_ms[names.index(dom)] * 1e-3) / 1e9
-    tr = TRAFFIC.get((workload, dom))
-    if tr is not None and tr[3] is not None and tr[3] != st.shape:
-        tr = None  # captured at another launch shape
+    # a capture at the step's launch shape (or one that takes no shape)
+    tr = next((e for e in TRAFFIC.get((workload, dom), []) if e[3] is None or e[3] == st.shape), None)
     traffic = None
     if tr is not None:
         traffic = tr[0] * (st.atoms if tr[1] == "atom" else st.units)
