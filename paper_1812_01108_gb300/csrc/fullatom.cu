@@ -304,7 +304,8 @@ __host__ __device__ constexpr size_t fa_smem() {
 }
 
 // The coordinate-reading backward stages a tile's coordinates and, beside
-// them, its coordinate gradient (or target): two stages.
+// them, its coordinate gradient (or target); the forward that reduces the
+// LRMSD moments stages the tile's target beside its atoms: two stages.
 template <int NT, int K>
 __host__ __device__ constexpr size_t fa_bwd_smem() {
     return 2 * fa_smem<NT, K>();
@@ -404,12 +405,15 @@ __device__ __forceinline__ void tile_record(const ChainWs& ws, int slot, int& fi
 // LM: also reduce, per tile, the LRMSD moments (Section 4) of the tile's atoms
 // against `target`: sum dx, sum dy, sum dx dy^T, sum |dx|^2, sum |dy|^2 with
 // dx = x - x_0 (x the target, x_0 its first atom) and dy = y (the chain's
-// first atom, N of residue 0, is the origin: R_0 = I).
+// first atom, N of residue 0, is the origin: R_0 = I).  The tile's target rows
+// come into a second stage by a bulk copy issued once the tile's first atom is
+// known, which runs while the atoms are placed; the moments are summed from
+// the two stages.
 // ---------------------------------------------------------------------------
 // PACK: the work list may hold packs of whole short chains (segmented scans,
 // per-chain stores); compiled separately so that tiles of one chain pay nothing.
 template <int NT, int K, bool LM, bool PACK>
-__global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
+__global__ void __launch_bounds__(NT, (fa_min_blocks<NT, K, LM>())) fa_fwd_kernel(
     const float* __restrict__ angles, const uint8_t* __restrict__ seq,
     const int32_t* __restrict__ lengths, int Lmax, int Amax, float* __restrict__ coords,
     int32_t* __restrict__ num_atoms, ChainWs ws, const float* __restrict__ target,
@@ -427,10 +431,14 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
     __shared__ PackS s_pack;                            // a pack of whole short chains
     __shared__ int s_cnt2[NW + 1], s_fl2[NW + 1];
     __shared__ int s_mtot[kMaxPack], s_mbase[kMaxPack + 1];  // atoms per member, stage offsets
+    __shared__ __align__(8) uint64_t s_bar;  // LM: completes when the tile's target has landed
     extern __shared__ float4 s_dyn[];
     float* stage = reinterpret_cast<float*>(s_dyn);  // the tile's atoms, 3 floats each
+    float* stage_t = stage + fa_smem<NT, K>() / sizeof(float);  // LM: the tile's target, same layout
 
     load_table(s_tab, tab);
+    if (LM && threadIdx.x == 0) mbar_init(&s_bar);  // visible after take_tile's barrier
+    unsigned bphase = 0;                             // the barrier phase the next target copy completes
     const int ntiles = ws.hdr[kHdrTiles];
     int v = take_tile(ws.hdr + kHdrFwdNext, &s_v);
     while (v < ntiles) {
@@ -553,6 +561,12 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
         const int soff = pack ? 0 : (3 * pc) & 3;
         float* dst = staged ? stage + soff + 3 * sbase : out + 3 * (size_t)pc;
         const int lim = staged ? CAP - sbase : Amax - pc;  // tile atoms at or past it are not written
+        // LM: the tile's target rows come into their own stage (same layout) by a
+        // bulk copy that runs while the atoms are placed
+        bool lm_bulk = false;
+        if constexpr (LM) {
+            if (staged) lm_bulk = bulk_copy_range<NT>(target + (size_t)b * Amax * 3, stage_t, 3 * pc, 3 * (pc + nout), &s_bar);
+        }
 
         // 4. atoms in the chain's frame
         if (j0 < s1) {
@@ -617,6 +631,13 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
             // of 4; past the chain's end the entries are unused)
             store_k<K>(ws.ratom + (size_t)b * Lmax + j0, ra);
         }
+        if constexpr (LM) {
+            if (staged) cp_async_wait_all();  // the ragged ends of the target rows
+            if (lm_bulk) {
+                mbar_wait(&s_bar, bphase);
+                bphase ^= 1u;
+            }
+        }
         fence_proxy_async();  // the stage writes, ordered before the bulk store that reads them
         __syncthreads();
         {
@@ -665,12 +686,12 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
             // the tile's coordinates: the stage, or (tiles that bypass it) this
             // CTA's own global writes, visible after the barrier above
             const float* ys = staged ? stage + soff : out + 3 * (size_t)pc;
+            const float* xs = staged ? stage_t + soff : tg + 3 * (size_t)pc;  // the target: its stage, or global
             float m[17];
 #pragma unroll
             for (int q = 0; q < 17; ++q) m[q] = 0.f;
             for (int a = threadIdx.x; a < nout; a += NT) {
-                const float* xa = tg + 3 * (size_t)(pc + a);
-                const float3 dx = make_float3(__ldg(xa) - x0.x, __ldg(xa + 1) - x0.y, __ldg(xa + 2) - x0.z);
+                const float3 dx = make_float3(xs[3 * a] - x0.x, xs[3 * a + 1] - x0.y, xs[3 * a + 2] - x0.z);
                 const float3 dy = make_float3(ys[3 * a], ys[3 * a + 1], ys[3 * a + 2]);
                 m[0] += dx.x; m[1] += dx.y; m[2] += dx.z;
                 m[3] += dy.x; m[4] += dy.y; m[5] += dy.z;
@@ -680,6 +701,7 @@ __global__ void __launch_bounds__(NT, fa_min_blocks<NT, K>()) fa_fwd_kernel(
                 m[15] += f3_dot(dx, dx);
                 m[16] += f3_dot(dy, dy);
             }
+            fence_proxy_async();  // the target stage's reads, ordered before the next tile's bulk copy
             // block sum: warp shuffles, then the warp sums in a fixed order
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -1531,7 +1553,7 @@ template <int NT, int K, bool LM, bool PACK>
 cudaError_t fa_fwd_t(const float* angles, const uint8_t* seq, const int32_t* lengths, int Lmax,
                      int Amax, float* coords, int32_t* num_atoms, const ChainWs& ws,
                      cudaStream_t s, const float* target) {
-    const size_t smem = fa_smem<NT, K>();
+    const size_t smem = LM ? fa_bwd_smem<NT, K>() : fa_smem<NT, K>();
     static bool done[64] = {false};
     cudaError_t e = smem_attr_once(fa_fwd_kernel<NT, K, LM, PACK>, (int)smem, done);
     if (e != cudaSuccess) return e;
