@@ -363,7 +363,9 @@ __device__ __forceinline__ void quad_eigen_solve(const float (&S)[kSlot], const 
                 T[0][3].hi + q[0] * q[3], T[1][1].hi - mu + q[1] * q[1], T[1][2].hi + q[1] * q[2],
                 T[1][3].hi + q[1] * q[3], T[2][2].hi - mu + q[2] * q[2], T[2][3].hi + q[2] * q[3],
                 T[3][3].hi - mu + q[3] * q[3], m);
-            const float idet = -__frcp_rn(det);
+            // (the adjugate path runs only for a well separated lambda_max, so det
+            // is of order one; an exact zero would leave q unrefined)
+            const float idet = fabsf(det) > 1e-30f ? -__frcp_rn(det) : 0.f;
 #pragma unroll
             for (int i = 0; i < 4; ++i)
                 dq[i] = idet * fmaf(m[4 * i], res[0], fmaf(m[4 * i + 1], res[1], fmaf(m[4 * i + 2], res[2], m[4 * i + 3] * res[3])));
