@@ -68,11 +68,7 @@ TRAFFIC = {
     # entry whose shape matches the step's launch shape is used.
     # Full-atom kernels captured at 4096 chains x 700 residues (coordinates above L2),
     # scaled by residues processed.
-    ("training_step", "fullatom_forward"): [
-        (319050496 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
-         "threads=384,res_per_thread=1"),
-        (319648000 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
-         "threads=256,res_per_thread=1")],
+    ("training_step", "fullatom_forward"): [],
     ("training_step", "lrmsd_fullatom_backward"): [
         (661392896 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
          "threads=384,res_per_thread=1"),

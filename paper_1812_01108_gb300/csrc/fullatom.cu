@@ -318,11 +318,24 @@ template <int K>
 __host__ __device__ constexpr int fa_reg_budget() {
     return K == 1 ? 80 : (K == 2 ? 96 : 160);
 }
-template <int NT, int K, bool BWD = false>
-__host__ __device__ constexpr int fa_min_blocks() {
-    return (227 * 1024 / (int)((BWD ? fa_bwd_smem<NT, K>() : fa_smem<NT, K>()) + 7 * 1024)) <
-                   (65536 / (NT * fa_reg_budget<K>()))
-               ? (227 * 1024 / (int)((BWD ? fa_bwd_smem<NT, K>() : fa_smem<NT, K>()) + 7 * 1024))
+// The plain forward with one residue per thread places side chains in the
+// order of residue types (fa_fwd_kernel, step 4): a record per residue (frame,
+// chi, type, first atom, room: 19 words) and the permutation, NT each.
+template <int K, bool LM, bool PACK>
+__host__ __device__ constexpr bool fa_fwd_perm() {
+    return K == 1 && !LM && !PACK;
+}
+constexpr int kRecWords = 19;
+template <int NT, int K, bool LM, bool PACK>
+__host__ __device__ constexpr size_t fa_fwd_smem() {
+    return (LM ? fa_bwd_smem<NT, K>() : fa_smem<NT, K>()) +
+           (fa_fwd_perm<K, LM, PACK>() ? (size_t)(kRecWords + 1) * NT * sizeof(float) : 0);
+}
+
+template <int NT, int K>
+__host__ __device__ constexpr int fa_min_blocks_for(size_t smem) {
+    return (227 * 1024 / (int)(smem + 7 * 1024)) < (65536 / (NT * fa_reg_budget<K>()))
+               ? (227 * 1024 / (int)(smem + 7 * 1024))
                : (65536 / (NT * fa_reg_budget<K>()));
 }
 
@@ -387,6 +400,37 @@ __device__ __forceinline__ void tile_record(const ChainWs& ws, int slot, int& fi
     count = __float_as_int(d.y);
 }
 
+// Side chain of one residue of type ty from its base frame S = M_1 R': the
+// groups S_k = S_{k-1} R(chi_k) (free chi from the angles, fixed ones from the
+// table) and every atom r = S_k r0, handed to put(output index, r).
+template <typename Put>
+__device__ __forceinline__ void side_chain(Rigid S, int ty, float chi0, float chi1, float chi2, float chi3,
+                                           const FaTable& tab, Put&& put) {
+    const int ng = tab.n_groups[ty], nchi = tab.n_chi[ty];
+    const float chi[kMaxGroups] = {chi0, chi1, chi2, chi3};
+    int e = 0;
+#pragma unroll
+    for (int g = 0; g < kMaxGroups; ++g) {
+        if (g >= ng) break;
+        float sc, cc;
+        if (g < nchi) {
+            // chi moves only its own side chain (no error propagates along the
+            // chain): the SFU sine/cosine is accurate enough here
+            __sincosf(chi[g], &sc, &cc);
+        } else {
+            cc = tab.fixchi[ty][g].x;
+            sc = tab.fixchi[ty][g].y;
+        }
+        const float4 gk = tab.grp[ty][g];
+        rigid_mul_R(S, cc, sc, gk.x, gk.y, gk.z);
+        const int end = tab.grp_end[ty][g];
+        for (; e < end; ++e) {
+            const float4 r0 = tab.side[ty][e];
+            put((int)r0.w & 15, point_apply(S, make_float3(r0.x, r0.y, r0.z)));
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // K3: forward.  One tile per step of a persistent CTA:
 //  1. each thread loads the angle rows and types of its K residues (vector
@@ -413,7 +457,7 @@ __device__ __forceinline__ void tile_record(const ChainWs& ws, int slot, int& fi
 // PACK: the work list may hold packs of whole short chains (segmented scans,
 // per-chain stores); compiled separately so that tiles of one chain pay nothing.
 template <int NT, int K, bool LM, bool PACK>
-__global__ void __launch_bounds__(NT, (fa_min_blocks<NT, K, LM>())) fa_fwd_kernel(
+__global__ void __launch_bounds__(NT, (fa_min_blocks_for<NT, K>(fa_fwd_smem<NT, K, LM, PACK>()))) fa_fwd_kernel(
     const float* __restrict__ angles, const uint8_t* __restrict__ seq,
     const int32_t* __restrict__ lengths, int Lmax, int Amax, float* __restrict__ coords,
     int32_t* __restrict__ num_atoms, ChainWs ws, const float* __restrict__ target,
@@ -435,6 +479,10 @@ __global__ void __launch_bounds__(NT, (fa_min_blocks<NT, K, LM>())) fa_fwd_kerne
     extern __shared__ float4 s_dyn[];
     float* stage = reinterpret_cast<float*>(s_dyn);  // the tile's atoms, 3 floats each
     float* stage_t = stage + fa_smem<NT, K>() / sizeof(float);  // LM: the tile's target, same layout
+    constexpr bool PERM = fa_fwd_perm<K, LM, PACK>();
+    float* rec = stage + fa_smem<NT, K>() / sizeof(float);  // PERM: word f of residue i at rec[f * NT + i]
+    int* perm = reinterpret_cast<int*>(rec + kRecWords * NT);  // PERM: thread of the i-th residue in type order
+    __shared__ int s_tcnt[kNumTypes], s_tbase[kNumTypes];
 
     load_table(s_tab, tab);
     if (LM && threadIdx.x == 0) mbar_init(&s_bar);  // visible after take_tile's barrier
@@ -443,6 +491,7 @@ __global__ void __launch_bounds__(NT, (fa_min_blocks<NT, K, LM>())) fa_fwd_kerne
     int v = take_tile(ws.hdr + kHdrFwdNext, &s_v);
     while (v < ntiles) {
         const int2 ct = ws.tiles[v];
+        if (PERM && threadIdx.x < kNumTypes) s_tcnt[threadIdx.x] = 0;  // used after the scan's barriers
         // a tile of one chain, or (chains per CTA > 1) a pack of whole chains,
         // each in its own slots of K residues, scanned as segments
         const bool pack = PACK && ct.x < 0;
@@ -598,27 +647,19 @@ __global__ void __launch_bounds__(NT, (fa_min_blocks<NT, K, LM>())) fa_fwd_kerne
                 // side-chain groups: S_k = S_{k-1} R(chi_k), S_0 = M_1 R'; atoms r = S_k r0
                 Rigid S = M1;
                 rigid_mul_Rx(S, s_tab.rp_c, s_tab.rp_s);
-                const int ng = s_tab.n_groups[ty], nchi = s_tab.n_chi[ty];
-                int e = 0;
+                if constexpr (PERM) {
+                    // placed below, in the order of residue types: the record
+                    const int i = threadIdx.x;
+                    rec[0 * NT + i] = S.c0.x; rec[1 * NT + i] = S.c0.y; rec[2 * NT + i] = S.c0.z;
+                    rec[3 * NT + i] = S.c1.x; rec[4 * NT + i] = S.c1.y; rec[5 * NT + i] = S.c1.z;
+                    rec[6 * NT + i] = S.c2.x; rec[7 * NT + i] = S.c2.y; rec[8 * NT + i] = S.c2.z;
+                    rec[9 * NT + i] = S.t.x; rec[10 * NT + i] = S.t.y; rec[11 * NT + i] = S.t.z;
 #pragma unroll
-                for (int g = 0; g < kMaxGroups; ++g) {
-                    if (g >= ng) break;
-                    float sc, cc;
-                    if (g < nchi) {
-                        // chi moves only its own side chain (no error propagates along
-                        // the chain): the SFU sine/cosine is accurate enough here
-                        __sincosf(chi[g][k], &sc, &cc);
-                    } else {
-                        cc = s_tab.fixchi[ty][g].x;
-                        sc = s_tab.fixchi[ty][g].y;
-                    }
-                    const float4 gk = s_tab.grp[ty][g];
-                    rigid_mul_R(S, cc, sc, gk.x, gk.y, gk.z);
-                    const int end = s_tab.grp_end[ty][g];
-                    for (; e < end; ++e) {
-                        const float4 r0 = s_tab.side[ty][e];
-                        put((int)r0.w & 15, point_apply(S, make_float3(r0.x, r0.y, r0.z)));
-                    }
+                    for (int g = 0; g < kMaxGroups; ++g) rec[(12 + g) * NT + i] = chi[g][k];
+                    rec[17 * NT + i] = __int_as_float(a);
+                    rec[18 * NT + i] = __int_as_float(room);
+                } else {
+                    side_chain(S, ty, chi[0][k], chi[1][k], chi[2][k], chi[3][k], s_tab, put);
                 }
                 a += s_tab.n_atoms[ty];
                 if (k + 1 < K && j + 1 < L) {  // the next residue's frame
@@ -630,6 +671,44 @@ __global__ void __launch_bounds__(NT, (fa_min_blocks<NT, K, LM>())) fa_fwd_kerne
             // (a thread's K residues lie in one tile: tile starts are multiples
             // of 4; past the chain's end the entries are unused)
             store_k<K>(ws.ratom + (size_t)b * Lmax + j0, ra);
+        }
+        if constexpr (PERM) {
+            // side chains in the order of residue types, so that the lanes of a
+            // warp mostly build the same groups and atoms: a counting sort of the
+            // tile's residues by type (the order within a type does not matter:
+            // every atom's place is fixed), then thread i takes the i-th residue
+            const int my_ty = j0 < s1 ? type[0] : kBackboneCode;  // code 20 and empty slots: no side chain
+            const int my_rank = atomicAdd(&s_tcnt[my_ty], 1);
+            rec[16 * NT + threadIdx.x] = __int_as_float(my_ty);
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                const int c = threadIdx.x < kNumTypes ? s_tcnt[threadIdx.x] : 0;
+                int incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if ((int)threadIdx.x >= o) incl += y;
+                }
+                if (threadIdx.x < kNumTypes) s_tbase[threadIdx.x] = incl - c;
+            }
+            __syncthreads();
+            perm[s_tbase[my_ty] + my_rank] = threadIdx.x;
+            __syncthreads();
+            const int r = perm[threadIdx.x];
+            const int ty = __float_as_int(rec[16 * NT + r]);
+            if (s_tab.n_groups[ty] > 0) {
+                Rigid S;
+                S.c0 = make_float3(rec[0 * NT + r], rec[1 * NT + r], rec[2 * NT + r]);
+                S.c1 = make_float3(rec[3 * NT + r], rec[4 * NT + r], rec[5 * NT + r]);
+                S.c2 = make_float3(rec[6 * NT + r], rec[7 * NT + r], rec[8 * NT + r]);
+                S.t = make_float3(rec[9 * NT + r], rec[10 * NT + r], rec[11 * NT + r]);
+                const int ar = __float_as_int(rec[17 * NT + r]), room_r = __float_as_int(rec[18 * NT + r]);
+                float* st = dst + 3 * ar;
+                auto put = [&](int idx, float3 rr) {
+                    if (idx < room_r) stage_atom(st, idx, rr);
+                };
+                side_chain(S, ty, rec[12 * NT + r], rec[13 * NT + r], rec[14 * NT + r], rec[15 * NT + r], s_tab, put);
+            }
         }
         if constexpr (LM) {
             if (staged) cp_async_wait_all();  // the ragged ends of the target rows
@@ -750,7 +829,7 @@ __device__ __forceinline__ float3 unit3(float3 v) { return f3_scale(rsqrtf(f3_do
 //     forms phi, psi and omega from them and from its N, C and O terms.
 // ---------------------------------------------------------------------------
 template <int NT, int K, bool LR, bool PACK>
-__global__ void __launch_bounds__(NT, (fa_min_blocks<NT, K, true>())) fa_bwd_coords_kernel(
+__global__ void __launch_bounds__(NT, (fa_min_blocks_for<NT, K>(fa_bwd_smem<NT, K>()))) fa_bwd_coords_kernel(
     const uint8_t* __restrict__ seq, const int32_t* __restrict__ lengths, int B, int Lmax, int Amax,
     const float* __restrict__ coords, const float* __restrict__ grad_coords,
     float* __restrict__ grad_angles, ChainWs ws, LrmsdGrad lg, const __grid_constant__ FaTable tab) {
@@ -1553,7 +1632,7 @@ template <int NT, int K, bool LM, bool PACK>
 cudaError_t fa_fwd_t(const float* angles, const uint8_t* seq, const int32_t* lengths, int Lmax,
                      int Amax, float* coords, int32_t* num_atoms, const ChainWs& ws,
                      cudaStream_t s, const float* target) {
-    const size_t smem = LM ? fa_bwd_smem<NT, K>() : fa_smem<NT, K>();
+    const size_t smem = fa_fwd_smem<NT, K, LM, PACK>();
     static bool done[64] = {false};
     cudaError_t e = smem_attr_once(fa_fwd_kernel<NT, K, LM, PACK>, (int)smem, done);
     if (e != cudaSuccess) return e;
