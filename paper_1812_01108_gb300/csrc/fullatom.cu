@@ -332,6 +332,18 @@ __host__ __device__ constexpr size_t fa_fwd_smem() {
            (fa_fwd_perm<K, LM, PACK>() ? (size_t)(kRecWords + 1) * NT * sizeof(float) : 0);
 }
 
+// The coordinate-reading backward with one residue per thread also sums side
+// chains in the order of residue types: type, first atom and the permutation
+// (NT ints each) and each residue's side-chain sums (6 NT floats).
+template <int K, bool PACK>
+__host__ __device__ constexpr bool fa_bwd_perm() {
+    return K == 1 && !PACK;
+}
+template <int NT, int K, bool PACK>
+__host__ __device__ constexpr size_t fa_bwd_coords_smem() {
+    return fa_bwd_smem<NT, K>() + (fa_bwd_perm<K, PACK>() ? (size_t)9 * NT * sizeof(float) : 0);
+}
+
 template <int NT, int K>
 __host__ __device__ constexpr int fa_min_blocks_for(size_t smem) {
     return (227 * 1024 / (int)(smem + 7 * 1024)) < (65536 / (NT * fa_reg_budget<K>()))
@@ -808,6 +820,35 @@ __global__ void __launch_bounds__(NT, (fa_min_blocks_for<NT, K>(fa_fwd_smem<NT, 
 
 __device__ __forceinline__ float3 unit3(float3 v) { return f3_scale(rsqrtf(f3_dot(v, v)), v); }
 
+// Side-chain part of a residue's backward (Eq. 1): its atoms in decreasing
+// group order, the running suffix (sum r x g, sum g) over the groups, and each
+// free chi's gradient u . (sum r x g - p x sum g) at the end of its group, into
+// gchi[group][k].  Returns the residue's side-chain sums.  Rp(a) and G(a, r)
+// give atom a's position and coordinate gradient; add accumulates a Sum6.
+template <int K, typename RpF, typename GF, typename AddF>
+__device__ __forceinline__ Sum6 side_chain_sums(int ty, int a, int nat, float (&gchi)[kMaxGroups][K], int k,
+                                                const FaTable& tab, RpF& Rp, GF& G, AddF& add) {
+    const int nchi = tab.n_chi[ty];
+    Sum6 suf = sum6_zero();
+    for (int e = nat - 5; e >= 0; --e) {
+        const int wv = (int)tab.side[ty][e].w;
+        const int grp = wv >> 4;
+        const float3 r = Rp(a + (wv & 15));
+        add(suf, r, G(a + (wv & 15), r));
+        const bool last_of_group = (e == 0) || (((int)tab.side[ty][e - 1].w >> 4) != grp);
+        if (last_of_group && grp <= nchi) {
+            const int o1 = tab.origin[ty][grp - 1];
+            const int o0 = grp >= 2 ? tab.origin[ty][grp - 2] : 1;
+            const float3 p = Rp(a + o1);
+            const float val = f3_dot(unit3(f3_sub(p, Rp(a + o0))), f3_sub(suf.c, f3_cross(p, suf.g)));
+#pragma unroll
+            for (int c = 0; c < kMaxGroups; ++c)
+                if (c == grp - 1) gchi[c][k] = val;
+        }
+    }
+    return suf;
+}
+
 // ---------------------------------------------------------------------------
 // K4': backward from the forward's coordinates.  For a frame with x axis u and
 // origin p, dL/dalpha = u . sum_{k downstream} (r_k - p) x g_k; axes and
@@ -829,7 +870,7 @@ __device__ __forceinline__ float3 unit3(float3 v) { return f3_scale(rsqrtf(f3_do
 //     forms phi, psi and omega from them and from its N, C and O terms.
 // ---------------------------------------------------------------------------
 template <int NT, int K, bool LR, bool PACK>
-__global__ void __launch_bounds__(NT, (fa_min_blocks_for<NT, K>(fa_bwd_smem<NT, K>()))) fa_bwd_coords_kernel(
+__global__ void __launch_bounds__(NT, (fa_min_blocks_for<NT, K>(fa_bwd_coords_smem<NT, K, PACK>()))) fa_bwd_coords_kernel(
     const uint8_t* __restrict__ seq, const int32_t* __restrict__ lengths, int B, int Lmax, int Amax,
     const float* __restrict__ coords, const float* __restrict__ grad_coords,
     float* __restrict__ grad_angles, ChainWs ws, LrmsdGrad lg, const __grid_constant__ FaTable tab) {
@@ -847,6 +888,12 @@ __global__ void __launch_bounds__(NT, (fa_min_blocks_for<NT, K>(fa_bwd_smem<NT, 
     extern __shared__ float4 s_dyn[];
     float* st_r = reinterpret_cast<float*>(s_dyn);  // the tile's coordinates
     float* st_g = st_r + fa_smem<NT, K>() / sizeof(float);  // their gradient (or target), same layout
+    constexpr bool PERM = fa_bwd_perm<K, PACK>();
+    int* s_rty = reinterpret_cast<int*>(st_r + 2 * fa_smem<NT, K>() / sizeof(float));  // PERM: residue type
+    int* s_ra = s_rty + NT;                                  // PERM: first atom
+    int* s_perm = s_ra + NT;                                 // PERM: thread of the i-th residue in type order
+    float* s_suf = reinterpret_cast<float*>(s_perm + NT);    // PERM: side-chain sums, word q at q * NT + i
+    __shared__ int s_tcnt[kNumTypes], s_tbase[kNumTypes];
 
     if (!ws_matches(ws, TILE, B, Lmax)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) flag_status(TPL_STATUS_BAD_WORKSPACE);
@@ -862,6 +909,7 @@ __global__ void __launch_bounds__(NT, (fa_min_blocks_for<NT, K>(fa_bwd_smem<NT, 
     int v = take_tile(counter, &s_v);
     while (v < ntiles) {
         const int2 ct = ws.tiles[v];
+        if (PERM && threadIdx.x < kNumTypes) s_tcnt[threadIdx.x] = 0;  // used after the staging barrier
         // a tile of one chain (the chain's tiles taken last to first), or a
         // pack of whole chains in slots of K residues (segmented sums)
         if (ct.x < 0 && !PACK) {
@@ -1021,32 +1069,62 @@ __global__ void __launch_bounds__(NT, (fa_min_blocks_for<NT, K>(fa_bwd_smem<NT, 
                         add(s, r, G(a + q, r));
                     }
                 }
-                // side chain, entries in decreasing group order: suffix over groups
-                const int nchi = s_tab.n_chi[ty];
-                Sum6 suf = sum6_zero();
-                for (int e = nat - 5; e >= 0; --e) {
-                    const int wv = (int)s_tab.side[ty][e].w;
-                    const int grp = wv >> 4;
-                    const float3 r = Rp(a + (wv & 15));
-                    add(suf, r, G(a + (wv & 15), r));
-                    const bool last_of_group = (e == 0) || (((int)s_tab.side[ty][e - 1].w >> 4) != grp);
-                    if (last_of_group && grp <= nchi) {
-                        const int o1 = s_tab.origin[ty][grp - 1];
-                        const int o0 = grp >= 2 ? s_tab.origin[ty][grp - 2] : 1;
-                        const float3 p = Rp(a + o1);
-                        const float val = f3_dot(unit3(f3_sub(p, Rp(a + o0))), f3_sub(suf.c, f3_cross(p, suf.g)));
-#pragma unroll
-                        for (int c = 0; c < kMaxGroups; ++c)
-                            if (c == grp - 1) gchi[c][k] = val;
-                    }
+                if constexpr (PERM) {
+                    own[k] = s;  // the side chain's sums are added after the type-ordered pass
+                } else {
+                    const Sum6 suf = side_chain_sums(ty, a, nat, gchi, k, s_tab, Rp, G, add);
+                    own[k] = sum6_add(s, suf);
+                    tsum = sum6_add(tsum, own[k]);
                 }
-                own[k] = sum6_add(s, suf);
-                tsum = sum6_add(tsum, own[k]);
+            }
+        }
+        if constexpr (PERM) {
+            // side chains in the order of residue types (as in the forward):
+            // thread i takes the i-th residue, writes its chi gradients and hands
+            // its side-chain sums back through shared memory
+            const int my_ty = (j0 < s1 && in_range[0]) ? type[0] : kBackboneCode;  // code 20: no side chain
+            const int my_rank = atomicAdd(&s_tcnt[my_ty], 1);
+            s_rty[threadIdx.x] = my_ty;
+            s_ra[threadIdx.x] = j0 < s1 ? a0[0] : 0;
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                const int c = threadIdx.x < kNumTypes ? s_tcnt[threadIdx.x] : 0;
+                int incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if ((int)threadIdx.x >= o) incl += y;
+                }
+                if (threadIdx.x < kNumTypes) s_tbase[threadIdx.x] = incl - c;
+            }
+            __syncthreads();
+            s_perm[s_tbase[my_ty] + my_rank] = threadIdx.x;
+            __syncthreads();
+            const int r = s_perm[threadIdx.x];
+            const int ty = s_rty[r];
+            const int jr = s0 + r;  // the residue (one per thread)
+            float gc[kMaxGroups][1] = {{0.f}, {0.f}, {0.f}, {0.f}};
+            Sum6 suf = sum6_zero();
+            if (ty != kBackboneCode) suf = side_chain_sums(ty, s_ra[r], (int)s_tab.n_atoms[ty], gc, 0, s_tab, Rp, G, add);
+            if (jr < s1) {
+#pragma unroll
+                for (int c = 0; c < kMaxGroups; ++c) ga[(3 + c) * Lmax + jr] = gc[c][0];
+            }
+            s_suf[0 * NT + r] = suf.c.x; s_suf[1 * NT + r] = suf.c.y; s_suf[2 * NT + r] = suf.c.z;
+            s_suf[3 * NT + r] = suf.g.x; s_suf[4 * NT + r] = suf.g.y; s_suf[5 * NT + r] = suf.g.z;
+            __syncthreads();
+            if (j0 < s1 && in_range[0]) {
+                const int i = threadIdx.x;
+                Sum6 sc;
+                sc.c = make_float3(s_suf[0 * NT + i], s_suf[1 * NT + i], s_suf[2 * NT + i]);
+                sc.g = make_float3(s_suf[3 * NT + i], s_suf[4 * NT + i], s_suf[5 * NT + i]);
+                own[0] = sum6_add(own[0], sc);
+                tsum = own[0];
             }
         }
         // A thread's K residues lie in one tile (tile starts are multiples of 4),
         // except past the chain's end, where the last tile writes zeros anyway.
-        if (j0 < s1) {
+        if (!PERM && j0 < s1) {
 #pragma unroll
             for (int c = 0; c < kMaxGroups; ++c) store_k<K>(ga + (3 + c) * Lmax + j0, gchi[c]);
         }
@@ -1646,7 +1724,7 @@ template <int NT, int K, bool LR, bool PACK>
 cudaError_t fa_bwd_coords_t(const uint8_t* seq, const int32_t* lengths, int B, int Lmax, int Amax,
                             const float* coords, const float* grad_coords, float* grad_angles,
                             const ChainWs& ws, LrmsdGrad lg, cudaStream_t s) {
-    const size_t smem = fa_bwd_smem<NT, K>();
+    const size_t smem = fa_bwd_coords_smem<NT, K, PACK>();
     static bool done[64] = {false};
     cudaError_t e = smem_attr_once(fa_bwd_coords_kernel<NT, K, LR, PACK>, (int)smem, done);
     if (e != cudaSuccess) return e;
