@@ -68,8 +68,16 @@ TRAFFIC = {
     # entry whose shape matches the step's launch shape is used.
     # Full-atom kernels captured at 4096 chains x 700 residues (coordinates above L2),
     # scaled by residues processed.
-    ("training_step", "fullatom_forward"): [],
-    ("training_step", "lrmsd_fullatom_backward"): [],
+    ("training_step", "fullatom_forward"): [
+        (320464128 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
+         "threads=384,res_per_thread=1"),
+        (321153024 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
+         "threads=256,res_per_thread=1")],
+    ("training_step", "lrmsd_fullatom_backward"): [
+        (661773312 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
+         "threads=384,res_per_thread=1"),
+        (662446848 / 2867200, "residue", "profiles/fa_kernels_training_step_256x700.md",
+         "threads=256,res_per_thread=1")],
     # the uneven backbone batch itself (1302424 residues), shape 256 x 4
     ("backbone_uneven", "backbone_forward"): [
         (19462656 / 1302424, "residue", "profiles/backbone_kernels_backbone_uneven_4096.md",
