@@ -8,11 +8,12 @@
 // R_3(psi_j) R_4(omega_{j+1}) is scanned across the tile (exclusive prefix =
 // M_0 of residue j, the frame of its N, relative to the tile start), together
 // with an exclusive scan of the per-residue atom counts (the residue's first
-// output atom).  Each thread then builds M_1, M_3 and the side-chain frames
-// M_1 R' R(chi_1) R(chi_2) ... and places its atoms r = M_g r0 into a
-// shared-memory stage; once the look-back has given the tile's start frame it
-// is applied in place and the CTA writes the stage out with 16-byte stores.
-// The residue tables live in shared memory.
+// output atom).  Once the look-back has given the tile's start frame, each
+// thread composes it in, builds M_1, M_3 and the side-chain frames M_1 R'
+// R(chi_1) R(chi_2) ... and places the atoms r = M_g r0 into a shared-memory
+// stage (with one residue per thread the side chains are built in the order
+// of residue types, so that a warp's lanes run the same loops); the stage goes
+// out by a bulk store.  The residue tables live in shared memory.
 //
 // K4 fa_bwd_coords_kernel / fa_bwd_kernel: Eq. 1 as suffix sums.  For a frame
 // with x axis u and origin p, dL/dalpha = u . sum_{k downstream} (r_k - p) x
@@ -20,8 +21,10 @@
 // groups); phi, psi and omega add the sum over all later residues, a reverse
 // suffix scan of (sum r x g, sum g) across the tile plus the suffix of the
 // later tiles (look-back, tiles of a chain taken last to first).  Axes and
-// origins come from the forward's coordinates (fa_bwd_coords_kernel) or from
-// frames recomputed from the angles and the tile-start frames (fa_bwd_kernel).
+// origins come from the forward's coordinates (fa_bwd_coords_kernel, whose
+// side-chain sums run in the order of residue types like the forward's) or
+// from frames recomputed from the angles and the tile-start frames
+// (fa_bwd_kernel).
 #include "kernels.h"
 #include "sched.cuh"
 #include "tables.h"
