@@ -458,8 +458,11 @@ __device__ __forceinline__ void side_chain(Rigid S, int ty, float chi0, float ch
 //     start; the identity for a chain's first tile, R_0 = I);
 //  4. each thread walks its residues in the chain's frame: N = M_0 0, CA =
 //     M_1 0, C and O from M_3, the side-chain groups S_0 = M_1 R', S_k =
-//     S_{k-1} R(chi_k), placing every atom r = M_g r0 into the stage;
-//  5. the stage goes out with 16-byte stores.
+//     S_{k-1} R(chi_k), placing every atom r = M_g r0 into the stage.  With
+//     one residue per thread (PERM) a residue leaves its side-chain record
+//     in shared memory instead, a counting sort orders the tile's residues by
+//     type, and thread i builds the side chain of the i-th;
+//  5. the stage goes out by a bulk store (its ragged ends by the threads).
 // The residue tables live in shared memory.
 // LM: also reduce, per tile, the LRMSD moments (Section 4) of the tile's atoms
 // against `target`: sum dx, sum dy, sum dx dy^T, sum |dx|^2, sum |dy|^2 with
