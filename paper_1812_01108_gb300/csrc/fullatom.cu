@@ -335,23 +335,29 @@ __host__ __device__ constexpr size_t fa_fwd_smem() {
            (fa_fwd_perm<K, LM, PACK>() ? (size_t)(kRecWords + 1) * NT * sizeof(float) : 0);
 }
 
-// The coordinate-reading backward with one residue per thread also sums side
-// chains in the order of residue types: type, first atom and the permutation
-// (NT ints each) and each residue's side-chain sums (6 NT floats).
-template <int K, bool PACK>
-__host__ __device__ constexpr bool fa_bwd_perm() {
-    return K == 1 && !PACK;
-}
-template <int NT, int K, bool PACK>
-__host__ __device__ constexpr size_t fa_bwd_coords_smem() {
-    return fa_bwd_smem<NT, K>() + (fa_bwd_perm<K, PACK>() ? (size_t)9 * NT * sizeof(float) : 0);
-}
-
 template <int NT, int K>
 __host__ __device__ constexpr int fa_min_blocks_for(size_t smem) {
     return (227 * 1024 / (int)(smem + 7 * 1024)) < (65536 / (NT * fa_reg_budget<K>()))
                ? (227 * 1024 / (int)(smem + 7 * 1024))
                : (65536 / (NT * fa_reg_budget<K>()));
+}
+
+// The coordinate-reading backward with one residue per thread also sums side
+// chains in the order of residue types: type, first atom and the permutation
+// (NT ints each) and each residue's side-chain sums (6 NT floats) -- for the
+// shapes whose CTAs per SM that shared memory leaves unchanged (at 256 threads
+// it would cost a CTA per SM, and the sort then loses: 365 against 328 us per
+// backward at 4096 x 700).
+constexpr size_t fa_bwd_perm_bytes(int NT) { return (size_t)9 * NT * sizeof(float); }
+template <int NT, int K, bool PACK>
+__host__ __device__ constexpr bool fa_bwd_perm() {
+    return K == 1 && !PACK &&
+           fa_min_blocks_for<NT, K>(fa_bwd_smem<NT, K>() + fa_bwd_perm_bytes(NT)) ==
+               fa_min_blocks_for<NT, K>(fa_bwd_smem<NT, K>());
+}
+template <int NT, int K, bool PACK>
+__host__ __device__ constexpr size_t fa_bwd_coords_smem() {
+    return fa_bwd_smem<NT, K>() + (fa_bwd_perm<NT, K, PACK>() ? fa_bwd_perm_bytes(NT) : 0);
 }
 
 // K consecutive floats (bytes) at p, 4K-byte (K-byte) aligned.
@@ -894,7 +900,7 @@ __global__ void __launch_bounds__(NT, (fa_min_blocks_for<NT, K>(fa_bwd_coords_sm
     extern __shared__ float4 s_dyn[];
     float* st_r = reinterpret_cast<float*>(s_dyn);  // the tile's coordinates
     float* st_g = st_r + fa_smem<NT, K>() / sizeof(float);  // their gradient (or target), same layout
-    constexpr bool PERM = fa_bwd_perm<K, PACK>();
+    constexpr bool PERM = fa_bwd_perm<NT, K, PACK>();
     int* s_rty = reinterpret_cast<int*>(st_r + 2 * fa_smem<NT, K>() / sizeof(float));  // PERM: residue type
     int* s_ra = s_rty + NT;                                  // PERM: first atom
     int* s_perm = s_ra + NT;                                 // PERM: thread of the i-th residue in type order
