@@ -22,7 +22,8 @@
 // suffix scan of (sum r x g, sum g) across the tile plus the suffix of the
 // later tiles (look-back, tiles of a chain taken last to first).  Axes and
 // origins come from the forward's coordinates (fa_bwd_coords_kernel, whose
-// side-chain sums run in the order of residue types like the forward's) or
+// side-chain sums run in the order of residue types like the forward's where
+// that keeps its CTAs per SM) or
 // from frames recomputed from the angles and the tile-start frames
 // (fa_bwd_kernel).
 #include "kernels.h"
